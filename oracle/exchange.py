@@ -1,0 +1,181 @@
+"""Yin <-> Yang Schwarz boundary exchange (oracle; test infrastructure).
+
+Sec. 4: the solution on each patch uses boundary data interpolated from the
+currently available solution on the other patch (Algorithm steps 1, 3 and 7).
+The interpolation order is not stated; the reading used is tensor bilinear
+interpolation in the donor's local (theta', phi') at the same radius (both
+patches share the radial grid), which is second-order accurate.
+
+Geometry: a point with local unit vector x of one patch has local unit vector
+M x in the other patch (M is its own inverse).  A vector with donor-local
+spherical components (v_r, v_th', v_ph') has target components
+v_r (radial directions coincide) and, tangentially,
+  v_t = (e_t . M e_th') v_th' + (e_t . M e_ph') v_ph'   for e_t = e_th or e_ph.
+
+Target points of each patch (logical indices, see grid.py):
+  T      : theta-ghost rows j in {-1, Nth} (k interior) and phi-ghost
+           columns k in {-1, Nph} (j interior), every radial cell;
+  u_r    : the same (j, k) points, interior radial faces; wall faces carry
+           the wall value;
+  u_th   : edge faces j in {0, Nth} (k interior) and phi-ghosts k in {-1, Nph}
+           at interior faces j in [1, Nth);
+  u_ph   : edge faces k in {0, Nph} (j interior) and theta-ghosts j in {-1, Nth}
+           at interior faces k in [1, Nph);
+  p      : the outermost ring of interior cells (j in {0, Nth-1} or
+           k in {0, Nph-1}), overwritten after the pressure update (step 7).
+Radial ghosts of cell-centred quantities are reflections 2 g - x_0 about the
+wall value g.  Every donor stencil lies strictly inside the donor's unknowns
+(and, for the pressure ring, off the donor's ring); building a table checks
+this and raises if the grid is too coarse for it.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .grid import C, PH, R, TH, M, e_phi, e_theta, sph_to_unit, unit_to_sph
+
+
+def _target_points(g, kind):
+    """Logical (j, k) target points in the (theta, phi) plane."""
+    Nt, Np = g.Nth, g.Nph
+    pts = []
+    if kind in ("T", "ur"):
+        pts += [(j, k) for j in (-1, Nt) for k in range(Np)]
+        pts += [(j, k) for k in (-1, Np) for j in range(Nt)]
+    elif kind == "uth":
+        pts += [(j, k) for j in (0, Nt) for k in range(Np)]
+        pts += [(j, k) for k in (-1, Np) for j in range(1, Nt)]
+    elif kind == "uph":
+        pts += [(j, k) for k in (0, Np) for j in range(Nt)]
+        pts += [(j, k) for j in (-1, Nt) for k in range(1, Np)]
+    elif kind == "p":
+        ring = set()
+        for k in range(Np):
+            ring.add((0, k))
+            ring.add((Nt - 1, k))
+        for j in range(Nt):
+            ring.add((j, 0))
+            ring.add((j, Np - 1))
+        pts = sorted(ring)
+    else:
+        raise ValueError(kind)
+    return np.array([p[0] for p in pts]), np.array([p[1] for p in pts])
+
+
+def _angles(g, loc, j, k):
+    th = g.th_f(j) if loc == TH else g.th_c(j)
+    ph = g.ph_f(k) if loc == PH else g.ph_c(k)
+    return th, ph
+
+
+def _stencil(g, loc, th, ph, strict_ring=False):
+    """Bilinear stencil of donor quantity at ``loc`` for donor angles (th, ph):
+    base indices (j0, k0) and weights (wj, wk) along theta and phi."""
+    jf = (th - g.th0) / g.hth - (0.0 if loc == TH else 0.5)
+    kf = (ph - g.ph0) / g.hph - (0.0 if loc == PH else 0.5)
+    j0 = np.floor(jf).astype(np.int64)
+    k0 = np.floor(kf).astype(np.int64)
+    # allowed base ranges: the stencil (j0, j0+1) x (k0, k0+1) must be unknowns
+    jlo, jhi = (1, g.Nth - 1) if loc == TH else (0, g.Nth - 1)
+    klo, khi = (1, g.Nph - 1) if loc == PH else (0, g.Nph - 1)
+    if strict_ring:
+        jlo, jhi, klo, khi = jlo + 1, jhi - 1, klo + 1, khi - 1
+    if (j0 < jlo).any() or (j0 + 1 > jhi).any() or (k0 < klo).any() or (k0 + 1 > khi).any():
+        raise ValueError("exchange donor stencil leaves the donor interior: grid too coarse")
+    return j0, k0, jf - j0, kf - k0
+
+
+class ExchangeTables:
+    """Per-target donor stencils and rotations; identical for both patches."""
+
+    def __init__(self, g):
+        self.g = g
+        self.tab = {}
+        for kind, loc in (("T", C), ("ur", R), ("uth", TH), ("uph", PH), ("p", C)):
+            j, k = _target_points(g, kind)
+            th, ph = _angles(g, loc, j, k)
+            x = sph_to_unit(th, ph)
+            xd = x @ M.T
+            thd, phd = unit_to_sph(xd)
+            entry = {"j": j, "k": k}
+            if kind in ("T", "ur", "p"):
+                entry["s"] = _stencil(g, C, thd, phd, strict_ring=(kind == "p"))
+            else:
+                entry["st"] = _stencil(g, TH, thd, phd)
+                entry["sp"] = _stencil(g, PH, thd, phd)
+                e_t = e_theta(th, ph) if kind == "uth" else e_phi(th, ph)
+                Met = e_theta(thd, phd) @ M.T
+                Mep = e_phi(thd, phd) @ M.T
+                entry["rot"] = (np.sum(e_t * Met, axis=-1), np.sum(e_t * Mep, axis=-1))
+            self.tab[kind] = entry
+
+
+def _interp(a_donor, st, i_slice):
+    """Bilinear interpolation of padded donor array a_donor[i, j, k] at the
+    stencils st for every radial index of i_slice -> shape (ni, npts)."""
+    j0, k0, wj, wk = st
+    A = a_donor[i_slice]
+    J, K = j0 + 1, k0 + 1
+    return ((1 - wj) * (1 - wk) * A[:, J, K] + (1 - wj) * wk * A[:, J, K + 1]
+            + wj * (1 - wk) * A[:, J + 1, K] + wj * wk * A[:, J + 1, K + 1])
+
+
+def exchange_into(tables, target, fields, patches, T_walls=(0.0, 0.0)):
+    """Fill the boundary values of the listed target ``patches`` from the other
+    patch, for the state dict ``fields`` (padded arrays with keys 'T' and the
+    velocity lists 'u1', 'u2').  Donor values are read from a snapshot taken
+    before any write, so both patches may be filled at once (additive Schwarz)."""
+    g = tables.g
+    tab = tables.tab
+    Nr = g.Nr
+    src = {"T": fields["T"].copy(), "u1": [u.copy() for u in fields["u1"]],
+           "u2": [u.copy() for u in fields["u2"]]}
+    cells = slice(1, Nr + 1)          # logical i in [0, Nr)
+    ifaces = slice(2, Nr + 1)         # logical r-faces i in [1, Nr)
+    for p in patches:
+        d = 1 - p
+        e = tab["T"]
+        target["T"][p][cells, e["j"] + 1, e["k"] + 1] = _interp(src["T"][d], e["s"], cells)
+        for key in ("u1", "u2"):
+            U, S = target[key], src[key]
+            e = tab["ur"]
+            U[0][p][ifaces, e["j"] + 1, e["k"] + 1] = _interp(S[0][d], e["s"], ifaces)
+            for kind, comp in (("uth", 1), ("uph", 2)):
+                e = tab[kind]
+                vt = _interp(S[1][d], e["st"], cells)
+                vp = _interp(S[2][d], e["sp"], cells)
+                U[comp][p][cells, e["j"] + 1, e["k"] + 1] = e["rot"][0] * vt + e["rot"][1] * vp
+    wall_ghosts(g, target, patches, T_walls)
+
+
+def wall_ghosts(g, fields, patches, T_walls=(0.0, 0.0)):
+    """Radial wall data: u_r on the wall faces is the wall value (0); cell-centred
+    quantities get the reflection ghost 2 g - x_0 on their unknown columns."""
+    Nr, Nt, Np = g.Nr, g.Nth, g.Nph
+    for p in patches:
+        T = fields["T"][p]
+        T[0, 1:Nt + 1, 1:Np + 1] = 2.0 * T_walls[0] - T[1, 1:Nt + 1, 1:Np + 1]
+        T[Nr + 1, 1:Nt + 1, 1:Np + 1] = 2.0 * T_walls[1] - T[Nr, 1:Nt + 1, 1:Np + 1]
+        for key in ("u1", "u2"):
+            U = fields[key]
+            U[0][p][1, :, :] = 0.0
+            U[0][p][Nr + 1, :, :] = 0.0
+            ut = U[1][p]
+            ut[0, 2:Nt + 1, 1:Np + 1] = -ut[1, 2:Nt + 1, 1:Np + 1]
+            ut[Nr + 1, 2:Nt + 1, 1:Np + 1] = -ut[Nr, 2:Nt + 1, 1:Np + 1]
+            up = U[2][p]
+            up[0, 1:Nt + 1, 2:Np + 1] = -up[1, 1:Nt + 1, 2:Np + 1]
+            up[Nr + 1, 1:Nt + 1, 2:Np + 1] = -up[Nr, 1:Nt + 1, 2:Np + 1]
+
+
+def pressure_ring(tables, P, patches):
+    """Step 7: overwrite the outermost ring of interior pressure cells of each
+    listed patch by interpolation of the other patch's pressure (padded array
+    P of both patches).  Donor stencils avoid the donor's ring, so both patches
+    may be updated at once."""
+    g = tables.g
+    e = tables.tab["p"]
+    cells = slice(1, g.Nr + 1)
+    src = P.copy()
+    for p in patches:
+        P[p][cells, e["j"] + 1, e["k"] + 1] = _interp(src[1 - p], e["s"], cells)
