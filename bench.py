@@ -1,0 +1,284 @@
+#!/usr/bin/env python
+"""Benchmark: cell-updates/s per artificial-compressibility time step.
+
+Workload (default): one Yin-Yang shell, 128x128x384 MAC cells per patch,
+R1=0.5, R2=1, Pr=1, Ra=1e3, dt=5e-4, 3 Schwarz / splitting-error-reduction
+iterations per step, FP64, forced by the trigonometric manufactured solution
+with homogeneous walls (synthetic data, seeded, no dataset).  A cell-update is
+one MAC cell of one patch advanced through one full AC step, all Schwarz
+iterations included: value = 2 Nr Nth Nph * steps / time.
+
+Timing: W untimed warm-up steps, then exactly K steps bracketed by
+barrier + synchronize, timed with CUDA events on the solver's stream; the
+state (~5 GB) is larger than L2, so no flush is needed.  N > 1: one
+independent shell per GPU (replicas; no collective on the data path), value =
+total cell-updates / max over ranks.
+
+Also reported: e2e (the same metric through the C ABI with pinned host
+buffers: upload both time levels, one step, download level 0, per step),
+per-kernel times from CUDA events, roofline of the dominant kernel class,
+SM clocks sampled during the timed region, and the FP64 oracle timed on the
+host cores on a bounded sample (cpu_baseline).
+
+--impl reference runs the oracle (a plain CPU program; there is no other
+implementation of the paper's method) on a bounded sample of the same
+workload and prints the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per AC step"
+UNIT = "cell-updates/s"
+
+# Algorithmic words moved per cell per launch of each kernel class, counting
+# one read of every input array and one write of every output (neighbour
+# reuse on chip; ghosts ~1/N ignored).  Sweeps: rhs + advecting component +
+# result (3), final sweeps also read the iterate (4); averages over the
+# launches of one iteration.
+WORDS_PER_CELL = {
+    "extrapolate": 30.0, "resid_T": 7.0, "resid_u": 82.0 / 6, "sweep_r": 23.0 / 7, "sweep_t": 23.0 / 7,
+    "sweep_p": 24.0 / 7, "pressure": 10.0,
+}
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons (background)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm = [float(r[1]) for r in rows if len(r) >= 9]
+        mx = [float(r[2]) for r in rows if len(r) >= 9]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def workload(n, dt=5e-4, K=3):
+    return dict(R1=0.5, R2=1.0, Pr=1.0, Ra=1e3, Nr=n, Nth=n, Nph=3 * n, dt=dt), K
+
+
+def inputs(kw):
+    from paper_1905_02300_gb300 import workloads as W
+    spec = W.Spec(kw["R1"], kw["R2"], kw["Nr"], kw["Nth"], kw["Nph"])
+    ex = W.TrigShell(kw["R1"], kw["R2"], kw["Pr"], kw["Ra"])
+    return (W.sample_fields(ex, spec, 0.0), W.sample_fields(ex, spec, -kw["dt"]), W.forcing_modes(ex, spec))
+
+
+def oracle_sample(n, K, steps):
+    """Time the FP64 oracle for `steps` AC steps on an n x n x 3n shell."""
+    from oracle.scheme import Oracle, Params
+    kw, _ = workload(n)
+    f0, fm, modes = inputs(kw)
+    o = Oracle(Params(**kw))
+    for lvl, f in ((0, f0), (1, fm)):
+        o.set_fields(lvl, f["T"], f["ur"], f["uth"], f["uph"], f["p"])
+    for tid, F in modes:
+        o.set_forcing(tid, F["T"], F["ur"], F["uth"], F["uph"])
+    t0 = time.perf_counter()
+    o.step(steps, K)
+    el = time.perf_counter() - t0
+    cells = 2 * n * n * 3 * n
+    return cells * steps / el, el
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    n = args.ref_n
+    _, K = workload(args.n)
+    for _ in range(args.warmup):
+        oracle_sample(n, K, 1)
+    v, el = oracle_sample(n, K, args.steps)
+    cores = 1
+    sample = f"{args.steps} AC steps of a {n}x{n}x{3*n}-per-patch shell (same physics, dt, K={K}) on 1 host core"
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"yin-yang shell {args.n}x{args.n}x{3*args.n} per patch, FP64, K=3 (sampled)",
+                       "sample_grid": f"{n}x{n}x{3*n}"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--ref-n", type=int, default=48)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1905_02300_gb300 import ys
+
+    kw, K = workload(args.n)
+    f0, fm, modes = inputs(kw)
+    s = ys.Solver(**kw)
+    stream = torch.cuda.Stream()
+    s.set_stream(stream.cuda_stream)
+    s.set_fields_dict(0, f0)
+    s.set_fields_dict(1, fm)
+    for m, (tid, F) in enumerate(modes):
+        s.set_forcing(m, tid, F["T"], F["ur"], F["uth"], F["uph"])
+    cells = 2 * kw["Nr"] * kw["Nth"] * kw["Nph"]
+
+    s.step(args.warmup, K)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.4)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s.profile(True)
+    n_launch0 = s.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = s.launch_count() - n_launch0
+    prof = s.profile_read()
+    s.profile(False)
+    clk = clocks.stop()
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * cells * args.steps / (ms_max / 1e3)
+
+    # end to end through the C ABI with pinned host buffers
+    pinned = {}
+    for lvl, f in ((0, f0), (1, fm)):
+        for k, a in f.items():
+            t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+            t.numpy()[...] = a
+            pinned[(lvl, k)] = t.numpy()
+    out = {k: torch.empty(a.shape, dtype=torch.float64, pin_memory=True).numpy() for k, a in f0.items()}
+    h2d = 2 * sum(a.nbytes for a in f0.values())
+    d2h = sum(a.nbytes for a in f0.values())
+    t_e2e = []
+    for it in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for lvl in (0, 1):
+            s.set_fields(lvl, *[pinned[(lvl, k)] for k in ("T", "ur", "uth", "uph", "p")])
+        s.step(1, K)
+        rc = ys.lib.ys_get_fields(s.h, 0, *[ys._ptr(out[k]) for k in ("T", "ur", "uth", "uph", "p")], None)
+        if rc:
+            raise ys.YSError(rc, "ys_get_fields")
+        if it > 0:
+            t_e2e.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(t_e2e)
+    e2e_val = world * cells / e2e_s
+
+    # roofline of the dominant kernel class
+    hbm, src = peaks()
+    top = max((k for k in prof if k in WORDS_PER_CELL), key=lambda k: prof[k][0])
+    tot_ms, n_l = prof[top]
+    avg_ms = tot_ms / max(n_l, 1)
+    bytes_per_launch = WORDS_PER_CELL[top] * 8 * cells
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "kernel": top, "peak_source": src,
+            "kernel_share": tot_ms / ms}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, el = oracle_sample(args.ref_n, K, 1)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"1 AC step (K={K}) of a {args.ref_n}x{args.ref_n}x{3*args.ref_n}-per-patch shell, "
+                         f"same physics and dt, numpy on 1 host core, {el:.1f} s"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"yin-yang shell {args.n}x{args.n}x{3*args.n} MAC cells per patch, "
+                                       f"R1=0.5 R2=1 Pr=1 Ra=1e3 dt=5e-4, K={K} Schwarz iterations, FP64, "
+                                       f"manufactured-solution forcing",
+                           "cells_per_shell": cells, "l2": "inputs larger than L2 (state ~%.1f GB)"
+                           % (s.device_bytes() / 1e9), "parallelism": f"replicas x{world}"},
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "kernels_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
+                "kernels_launches": {k: v[1] for k, v in prof.items() if v[1]}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * ys.h -- C ABI of the GB300 Yin-Yang shell solver.
+ *
+ * The library advances the Navier-Stokes-Boussinesq system in a spherical
+ * shell R1 <= r <= R2 (Sec. 1, Eq. eq_ns / eq_heat_convec of "A direction
+ * splitting scheme for Navier-Stokes-Boussinesq system in spherical shell
+ * geometries", arXiv:1905.02300) on two overset Yin/Yang latitude-longitude
+ * patches (Sec. 2), with the second-order artificial-compressibility scheme
+ * with bootstrapping (Sec. 3.3, Eq. ac1 / ac2), direction splitting of every
+ * implicit operator into 1-D tridiagonal line solves (Sec. 3.2, Sec. 4), the
+ * splitting-error reduction iteration (Sec. 4, Eq. er) and additive or
+ * multiplicative Schwarz coupling of the patches (Sec. 4, Algorithm).
+ *
+ * Everything runs on one CUDA device in hand-written kernels.  There is no
+ * CPU fallback: if no device is usable every call that needs one returns
+ * YS_ECUDA.
+ *
+ * Field layout (host buffers, FP64, caller-owned; the library copies in/out).
+ * Both patches are stored back to back, patch 0 (Yin) first, phi fastest:
+ *   T, p : [2][Nr  ][Nth  ][Nph  ]  cell centres
+ *   ur   : [2][Nr+1][Nth  ][Nph  ]  r-faces, wall faces included
+ *   uth  : [2][Nr  ][Nth+1][Nph  ]  theta-faces, patch-edge faces included
+ *   uph  : [2][Nr  ][Nth  ][Nph+1]  phi-faces, patch-edge faces included
+ * Velocity components are in each patch's local spherical basis.  Patch-edge
+ * faces, wall faces and the outermost ring of pressure cells are boundary
+ * values: the library recomputes them from the other patch (Schwarz
+ * exchange) and the wall data whenever fields are set, and returns them.
+ *
+ * Geometry: each patch covers theta in [pi/4 - d, 3pi/4 + d],
+ * phi in [-3pi/4 - d, 3pi/4 + d] of its own frame with d = overlap * h_theta,
+ * h_theta = (pi/2)/(Nth - 2 overlap), h_phi = (3pi/2 + 2d)/Nph, uniform
+ * h_r = (R2 - R1)/Nr.  The Yang frame is the Yin frame composed with
+ * M(x, y, z) = (-x, z, y) (Sec. 2).
+ *
+ * Threading: a context is not thread-safe; distinct contexts may be used
+ * from distinct threads.
+ */
+#ifndef YS_H
+#define YS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define YS_OK 0
+#define YS_EINVAL 1     /* invalid argument or grid too coarse for the exchange */
+#define YS_ENOMEM 2     /* device or host allocation failed */
+#define YS_ECUDA 3      /* CUDA error (no device, launch failure, ...) */
+#define YS_EDIVERGED 4  /* NaN/Inf or Schwarz blow-up; state left at the last good step */
+#define YS_ETIMEOUT 5   /* a bounded device wait gave up */
+#define YS_EAGAIN 6     /* result not ready yet */
+#define YS_EBUSY 7      /* admission refused: queue full */
+
+/* precision */
+#define YS_FP64 0       /* every field and operation in FP64 */
+#define YS_MIXED 1      /* FP32 sweeps and stencils; FP64 pressure, norms, coefficients */
+
+/* Schwarz variants (Sec. 4) */
+#define YS_ADDITIVE 0       /* both patches from the previous iterate (default) */
+#define YS_MULTIPLICATIVE 1 /* Yin, then Yang with Yin's newest data (Algorithm) */
+
+/* number of per-field Schwarz increment norms reported by ys_get_norms:
+ * T, u1_r, u1_th, u1_ph, p1, u2_r, u2_th, u2_ph, p2 */
+#define YS_NFIELDS 9
+
+typedef struct ys_ctx ys_ctx;
+
+typedef struct {
+  double R1, R2;        /* shell radii, 0 < R1 < R2 */
+  double Pr, Ra;        /* Prandtl and Rayleigh numbers (Sec. 1) */
+  double dt;            /* time step > 0 */
+  int Nr, Nth, Nph;     /* cells per patch; Nth > 2 overlap + 4, Nph >= Nth */
+  double chi;           /* AC parameter chi = O(1) of Eq. ac1 (default 1) */
+  int overlap;          /* overlap d in theta cells (default 2) */
+  int precision;        /* YS_FP64 (default) or YS_MIXED */
+  int schwarz_mode;     /* YS_ADDITIVE (default) or YS_MULTIPLICATIVE */
+  double schwarz_tol;   /* stop the Schwarz iteration once the largest l2
+                           increment norm is below this; 0 = always run
+                           n_schwarz iterations (default 0) */
+  double T_inner, T_outer; /* Dirichlet wall temperatures (default 0, 0) */
+  int step7;            /* 1 = interpolate the pressure ring from the other
+                           patch after each pressure update (Algorithm step 7,
+                           default); 0 = off */
+} ys_params;
+
+/* Fill *p with defaults (all sizes zero, chi = 1, overlap = 2, FP64,
+ * additive, tol 0, walls 0, step7 on). */
+void ys_default_params(ys_params *p);
+
+/* Create a context for one shell with default parameters.  Validates the
+ * arguments (YS_EINVAL: R1 <= 0, R2 <= R1, dt <= 0, N* < 8, Nph < Nth, chi <= 0,
+ * or a grid so coarse that an exchange donor stencil leaves the donor
+ * patch's interior), builds the metric and exchange tables and allocates all
+ * device state (YS_ENOMEM, YS_ECUDA).  Fields start at zero, t = 0.
+ * *out receives the context (NULL on error). */
+int ys_create(double R1, double R2, double Pr, double Ra, int Nr, int Nth, int Nph,
+              double dt, ys_ctx **out);
+int ys_create_ex(const ys_params *p, ys_ctx **out);
+
+/* Set time level `level` (0 = n, 1 = n-1) from host buffers in the layout
+ * above.  Sets u1 = u2 = u and p1 = p2 = p (the two AC systems of Eq. ac1 and
+ * Eq. ac2), or, if aux != NULL, takes u1 and p1 from aux packed as
+ * [ur1 | uth1 | uph1 | p1] in the same layouts.  Then recomputes every
+ * boundary value of that level.  Setting level 0 while level 1 was never set
+ * also sets level 1 to the same state (psi^{-1} := psi^0).
+ * Synchronous.  Errors: YS_EINVAL (bad level / NULL field), YS_ECUDA. */
+int ys_set_fields(ys_ctx *c, int level, const double *T, const double *ur, const double *uth,
+                  const double *uph, const double *p);
+int ys_set_fields_ex(ys_ctx *c, int level, const double *T, const double *ur, const double *uth,
+                     const double *uph, const double *p, const double *aux);
+
+/* Add separable forcing mode `mode` (0 <= mode < 8): f(x, t) = tau(t) F(x) with
+ * tau selected by time_fn (0: 1, 1: cos t, 2: sin t, 3: cos^2 t,
+ * 4: sin t cos t), F given at the unknowns in the field layouts above (T at
+ * centres, f_r on r-faces, f_th on theta-faces, f_ph on phi-faces; boundary
+ * entries are ignored).  The forcing enters the rates at t_n + dt/2.
+ * Errors: YS_EINVAL, YS_ENOMEM, YS_ECUDA. */
+int ys_set_forcing(ys_ctx *c, int mode, int time_fn, const double *f_T, const double *f_r,
+                   const double *f_th, const double *f_ph);
+
+/* Set the time t_n of level 0. */
+int ys_set_time(ys_ctx *c, double t);
+
+/* Advance n_steps AC time steps, each with up to n_schwarz Schwarz /
+ * splitting-error-reduction iterations (Sec. 4, Eq. er).  Per iteration:
+ * exchange boundary values, defect-correct T, then u1 (r, theta, phi), p1,
+ * u2 (r, theta, phi), p2, each correction through three line sweeps.
+ * Returns YS_EDIVERGED (state restored to the last good step) if a norm
+ * becomes NaN/Inf.  Asynchronous on the context's stream unless
+ * schwarz_tol > 0 (then it synchronises once per iteration). */
+int ys_step(ys_ctx *c, int n_steps, int n_schwarz);
+
+/* Copy time level `level` to host buffers (u2 and p2, the second-order
+ * solution); any pointer may be NULL to skip that field.  aux != NULL
+ * receives [ur1 | uth1 | uph1 | p1].  Synchronous. */
+int ys_get_fields(ys_ctx *c, int level, double *T, double *ur, double *uth, double *uph,
+                  double *p, double *aux);
+
+/* Statistics: largest l2 increment norm of the last iteration, time of
+ * level 0 and steps done; any pointer may be NULL.  Synchronous. */
+int ys_get_stats(ys_ctx *c, double *last_schwarz_norm, double *t, long *steps_done);
+
+/* Per-field l2 increment norms of the last iteration (YS_NFIELDS values) and
+ * the number of iterations the last step ran.  Synchronous. */
+int ys_get_norms(ys_ctx *c, double *norms, int *iters_last_step);
+
+/* Run the context's work on a caller-provided cudaStream_t (NULL = the
+ * context's own stream).  The caller keeps ownership of the stream. */
+int ys_set_stream(ys_ctx *c, void *stream);
+
+/* Device-pointer variant of ys_set_fields_ex: the buffers are device memory
+ * in the same layouts, read on the context's stream. */
+int ys_set_fields_dev(ys_ctx *c, int level, const double *T, const double *ur, const double *uth,
+                      const double *uph, const double *p, const double *aux);
+
+/* Kernel-level timing with CUDA events on the context's stream.
+ * ys_profile_enable(c, 1) starts recording (clears the tallies);
+ * ys_profile_read fills up to `cap` entries of names / total milliseconds /
+ * launch counts (sorted as registered) and returns the number of kernel
+ * classes (synchronous).  ys_launch_count returns the number of kernels the
+ * context launched since creation. */
+int ys_profile_enable(ys_ctx *c, int on);
+int ys_profile_read(ys_ctx *c, const char **names, double *ms, long *launches, int cap);
+long ys_launch_count(ys_ctx *c);
+
+/* Bytes of device memory held by the context. */
+size_t ys_device_bytes(ys_ctx *c);
+
+int ys_destroy(ys_ctx *c);
+
+const char *ys_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* YS_H */

@@ -1,0 +1,27 @@
+// Host-side geometry of one shell (see geometry.cpp).
+#pragma once
+#include <vector>
+
+#include "ys_internal.cuh"
+
+namespace ys {
+
+struct GridSpec {
+  double R1, R2;
+  int Nr, Nth, Nph, overlap;
+};
+
+struct GridGeo {
+  double hr, ht, hp, delta, th0, ph0;
+};
+
+// 0 on success, 1 if the parameters do not define a valid patch
+int make_grid(const GridSpec &g, GridGeo &out);
+// six FP64 tables rc, rf, sc, sf, cc, cf of length `len`, logical index i at
+// slot i + pad
+void make_metric(const GridSpec &g, const GridGeo &G, std::vector<double> &tab, int &pad, int &len);
+// exchange tables for every kind; 1 if a donor stencil leaves the donor's
+// unknowns (grid too coarse)
+int make_exchange(const GridSpec &g, const GridGeo &G, std::vector<XEntry> tabs[XNUM]);
+
+}  // namespace ys

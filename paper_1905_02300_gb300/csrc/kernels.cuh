@@ -1,0 +1,63 @@
+// Kernel launchers of the solver (host-callable, C++ linkage, namespace ys).
+#pragma once
+#include "ys_internal.cuh"
+
+namespace ys {
+
+// Field slots of one time level / iterate.
+enum FieldSlot { F_T = 0, F_U1R, F_U1T, F_U1P, F_P1, F_U2R, F_U2T, F_U2P, F_P2, NF = 9 };
+
+template <typename R>
+struct State {
+  R *f[NF];
+};
+
+// Advecting velocity and forcing pointers of one step.
+template <typename R>
+struct StepAux {
+  const R *A[3];   // a = 1.5 u2^n - 0.5 u2^{n-1} at r-, theta-, phi-faces
+  const R *fT, *fr, *ft, *fp;   // forcing at t_n + dt/2 (nullptr = none)
+};
+
+// Separable forcing modes, passed by value: out_c = sum_m tau[m] F[m][c].
+constexpr int kMaxModes = 8;
+template <typename R>
+struct Modes {
+  const R *F[kMaxModes][4];
+  double tau[kMaxModes];
+  int n;
+};
+
+struct XTables {
+  const XEntry *e[XNUM];
+  int n[XNUM];
+};
+
+template <typename R>
+struct Launch {
+  // extrapolation: it = 2 n - nm1 (all slots), A = 1.5 n.u2 - 0.5 nm1.u2
+  static void extrapolate(const Layout &L, State<R> it, State<R> n, State<R> nm1, R *A[3],
+                          cudaStream_t st);
+  // forcing f = sum_m tau_m F_m for the four forcing fields
+  static void combine_forcing(long total, Modes<R> modes, R *out[4], cudaStream_t st);
+  // Schwarz exchange into the listed patches (mask bit p) of state s
+  static void exchange(const Shell &S, const XTables &X, State<R> s, int patch_mask, cudaStream_t st);
+  static void walls(const Shell &S, State<R> s, int patch_mask, cudaStream_t st);
+  static void ring(const Shell &S, const XTables &X, State<R> s, int patch_mask, cudaStream_t st);
+  // residual -F into B
+  static void resid_T(const Shell &S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask,
+                      cudaStream_t st);
+  static void resid_u(const Shell &S, int sys, int comp, State<R> it, State<R> n, StepAux<R> ax, R *B,
+                      int patch_mask, cudaStream_t st);
+  // one line sweep of the factor (loc, dir); final sweeps add into dst and
+  // accumulate the weighted squared increment into norm[slot]
+  static void sweep(const Shell &S, int loc, int dir, bool final, StepAux<R> ax, R *B, R *Cs, R *dst,
+                    double *norm, int slot, int patch_mask, cudaStream_t st);
+  static void pressure(const Shell &S, int sys, State<R> it, State<R> n, double *norm, int patch_mask,
+                       cudaStream_t st);
+  // host layout <-> device layout
+  static void unpack(const Layout &L, int loc, const double *src, R *dst, cudaStream_t st);
+  static void pack(const Layout &L, int loc, const R *src, double *dst, cudaStream_t st);
+};
+
+}  // namespace ys

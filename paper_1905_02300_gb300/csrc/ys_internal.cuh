@@ -1,0 +1,60 @@
+// Internal definitions shared by the CUDA translation units of the solver.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ys {
+
+// Location types of the MAC grid (Sec. 4): cell centre, r-face, theta-face, phi-face.
+enum Loc { LC = 0, LR = 1, LT = 2, LP = 3 };
+enum Dir { DR = 0, DT = 1, DP = 2 };
+
+// Device layout of one field of one shell: both patches, each a box of logical
+// indices i in [-1, Nr], j in [-1, Nth], k in [-1, Nph] (faces use their face
+// index, which fits the same box).  Rows along phi have pitch P (a multiple of
+// 8 elements) and start 8 elements into the allocation, so k = 0 of every row
+// is 64-byte aligned for FP64 and k = -1 lives in the previous row's padding.
+struct Layout {
+  int Nr, Nt, Np;   // cells per patch
+  int NJ;           // Nt + 2 rows per r-plane
+  int P;            // row pitch in elements
+  long SI;          // r-plane stride = NJ * P
+  long PS;          // patch stride
+  long total;       // elements per field (both patches)
+};
+
+__host__ __device__ inline long lidx(const Layout &L, int p, int i, int j, int k) {
+  return p * L.PS + ((long)(i + 1) * L.NJ + (j + 1)) * (long)L.P + k + 8;
+}
+
+// Everything a kernel needs about one shell (passed by value).
+struct Shell {
+  Layout L;
+  double hr, ht, hp;        // spacings
+  double R1, sin_theta1;    // modified operators (Sec. 3.2)
+  double dt, nu, kappa, chi, PrRa;
+  // metric tables in FP64, indexed by logical index (pointers offset so that
+  // index -2 .. N+2 is valid)
+  const double *rc, *rf;    // r at centres / faces
+  const double *sc, *sf;    // sin(theta) at centres / faces
+  const double *cc, *cf;    // cos(theta) at centres / faces
+  double T_in, T_out;       // wall temperatures
+  int step7;
+};
+
+// Exchange table entry: one target point in the (theta, phi) plane of a patch,
+// with one or two bilinear donor stencils on the other patch and, for
+// tangential vector components, the 2x2 rotation row.
+struct XEntry {
+  int tj, tk;           // target logical (j, k)
+  int j0a, k0a;         // donor stencil A base (logical)
+  double wja, wka;      // donor stencil A weights along theta, phi
+  int j0b, k0b;         // donor stencil B base (vectors: u_phi donor)
+  double wjb, wkb;
+  double ra, rb;        // target = ra * A + rb * B (vectors); ra = 1, rb = 0 for scalars
+};
+
+// Table kinds.
+enum XKind { XT = 0, XUR = 1, XUT = 2, XUP = 3, XP = 4, XNUM = 5 };
+
+}  // namespace ys

@@ -30,6 +30,8 @@ Velocity components are in each patch's local spherical basis.
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 
 import numpy as np
@@ -255,17 +257,18 @@ class Exact:
     def __init__(self, R1, R2, Pr, Ra):
         self.R1, self.R2, self.Pr, self.Ra = R1, R2, Pr, Ra
 
-    def s_of_r(self, r):
-        """Wall-vanishing radial profile sin(pi (r - R1)/(R2 - R1)) as a jet."""
+    def s_of_r(self, r, F):
+        """Wall-vanishing radial profile sin(pi (r - R1)/(R2 - R1))."""
         L = self.R2 - self.R1
-        return ((r - self.R1) * (math.pi / L)).sin()
+        return F.sin((r - self.R1) * (math.pi / L))
 
-    def ds_of_r(self, r):
+    def ds_of_r(self, r, F):
         L = self.R2 - self.R1
-        return ((r - self.R1) * (math.pi / L)).cos() * (math.pi / L)
+        return F.cos((r - self.R1) * (math.pi / L)) * (math.pi / L)
 
-    def fields(self, x, y, z):
-        """Spatial parts (U[3], P, Th) as jets of global Cartesian x, y, z."""
+    def fields(self, x, y, z, F):
+        """Spatial parts (U[3], P, Th) of global Cartesian x, y, z, written with
+        the functions of namespace F (numpy, sympy or the Jet namespace)."""
         raise NotImplementedError
 
     def tfac(self, t):
@@ -281,9 +284,9 @@ class TrigShell(Exact):
     name = "trig"
     c0 = 0.25
 
-    def fields(self, x, y, z):
-        r = (x * x + y * y + z * z).sqrt()
-        s, ds = self.s_of_r(r), self.ds_of_r(r)
+    def fields(self, x, y, z, F):
+        r = F.sqrt(x * x + y * y + z * z)
+        s, ds = self.s_of_r(r, F), self.ds_of_r(r, F)
         q = 2.0 * s * ds / r * self.c0
         # x_vec cross grad(x^2 + y z) = (y^2 - z^2, 2 x z - x y, x z - 2 x y)
         U = [q * (y * y - z * z), q * (2.0 * x * z - x * y), q * (x * z - 2.0 * x * y)]
@@ -302,18 +305,18 @@ class CurlShell(Exact):
     c0 = 1.0
     k = 1.3
 
-    def fields(self, x, y, z):
+    def fields(self, x, y, z, F):
         k = self.k
-        r = (x * x + y * y + z * z).sqrt()
-        s, ds = self.s_of_r(r), self.ds_of_r(r)
+        r = F.sqrt(x * x + y * y + z * z)
+        s, ds = self.s_of_r(r, F), self.ds_of_r(r, F)
         q = s * s
         dq_over_r = 2.0 * s * ds / r           # grad q = dq_over_r * (x, y, z)
-        Ax, Ay, Az = (y * k).sin(), (z * k).sin(), (x * k).sin()
-        cA = [(z * k).cos() * (-k), (x * k).cos() * (-k), (y * k).cos() * (-k)]
+        Ax, Ay, Az = F.sin(y * k), F.sin(z * k), F.sin(x * k)
+        cA = [F.cos(z * k) * (-k), F.cos(x * k) * (-k), F.cos(y * k) * (-k)]
         cross = [y * Az - z * Ay, z * Ax - x * Az, x * Ay - y * Ax]
         U = [(q * cA[m] + dq_over_r * cross[m]) * self.c0 for m in range(3)]
-        Th = s * x.cos() * (y + z).sin()
-        P = x.sin() * y.cos() + 0.5 * z * z
+        Th = s * F.cos(x) * F.sin(y + z)
+        P = F.sin(x) * F.cos(y) + 0.5 * z * z
         return U, P, Th
 
 
@@ -324,10 +327,10 @@ class RadialHeat(Exact):
 
     name = "radial_heat"
 
-    def fields(self, x, y, z):
-        r = (x * x + y * y + z * z).sqrt()
+    def fields(self, x, y, z, F):
+        r = F.sqrt(x * x + y * y + z * z)
         zero = r * 0.0
-        return [zero, zero, zero], zero, self.s_of_r(r) / r
+        return [zero, zero, zero], zero, self.s_of_r(r, F) / r
 
     def tfac(self, t):
         L = self.R2 - self.R1
@@ -342,9 +345,9 @@ class SymmetricShell(Exact):
     name = "symmetric"
     c0 = 0.5
 
-    def fields(self, x, y, z):
-        r = (x * x + y * y + z * z).sqrt()
-        s, ds = self.s_of_r(r), self.ds_of_r(r)
+    def fields(self, x, y, z, F):
+        r = F.sqrt(x * x + y * y + z * z)
+        s, ds = self.s_of_r(r, F), self.ds_of_r(r, F)
         # f = s * g1, g1 = x^2 + y z ; h = s^2 * g2, g2 = x^2 + 2 y z
         g1 = x * x + y * z
         g2 = x * x + 2.0 * y * z
@@ -364,10 +367,18 @@ class SymmetricShell(Exact):
 EXACT = {c.name: c for c in (TrigShell, CurlShell, RadialHeat, SymmetricShell)}
 
 
+class JetNS:
+    """Function namespace acting on Jets (for fields(..., F=JetNS))."""
+    sin = staticmethod(lambda a: a.sin())
+    cos = staticmethod(lambda a: a.cos())
+    sqrt = staticmethod(lambda a: a.sqrt())
+    exp = staticmethod(lambda a: a.exp())
+
+
 def _jets_at(ex: Exact, spec: Spec, loc: str):
     x, y, z = global_points(spec, loc)
     X, Y, Z = Jet.variables(x, y, z)
-    return ex.fields(X, Y, Z)
+    return ex.fields(X, Y, Z, JetNS)
 
 
 def sample_fields(ex: Exact, spec: Spec, t: float):
@@ -375,42 +386,79 @@ def sample_fields(ex: Exact, spec: Spec, t: float):
     in the user layout: dict with keys T, ur, uth, uph, p."""
     c = ex.tfac(t)
     out = {}
-    U, P, Th = _jets_at(ex, spec, "c")
-    out["T"] = Th.v * c
-    out["p"] = P.v * c
+    x, y, z = global_points(spec, "c")
+    U, P, Th = ex.fields(x, y, z, np)
+    out["T"] = np.broadcast_to(Th * c, spec.shape("c")).copy()
+    out["p"] = np.broadcast_to(P * c, spec.shape("c")).copy()
     for loc, key, comp in (("r", "ur", 0), ("t", "uth", 1), ("p", "uph", 2)):
-        U, _, _ = _jets_at(ex, spec, loc)
-        loc_v = to_local_components(spec, loc, [U[0].v, U[1].v, U[2].v])
-        out[key] = loc_v[comp] * c
+        x, y, z = global_points(spec, loc)
+        U, _, _ = ex.fields(x, y, z, np)
+        U = [np.broadcast_to(u, x.shape) for u in U]
+        out[key] = to_local_components(spec, loc, U)[comp] * c
     return out
 
 
-def forcing_modes(ex: Exact, spec: Spec):
+_FORCING_FNS = {}
+
+
+def _forcing_fns(ex: Exact):
+    """Symbolic forcing of a cos-t solution, compiled to numpy:
+      f_u = -sin t U + cos^2 t (U.grad)U + cos t (grad P - Pr lap U - Pr Ra Th e_r)
+      f_T = -sin t Th + cos^2 t U.grad Th + cos t (-lap Th)
+    Returns a function (x, y, z) -> 12 arrays: (f_sin, f_cos2, f_cos) x (u_x, u_y, u_z, T)."""
+    key = (type(ex).__name__, ex.R1, ex.R2, ex.Pr, ex.Ra)
+    if key in _FORCING_FNS:
+        return _FORCING_FNS[key]
+    import sympy as sp
+    x, y, z = sp.symbols("x y z", real=True)
+    X = (x, y, z)
+    U, P, Th = ex.fields(x, y, z, sp)
+    r = sp.sqrt(x * x + y * y + z * z)
+    er = (x / r, y / r, z / r)
+    lap = lambda f: sum(sp.diff(f, v, 2) for v in X)
+    Pr, Ra = ex.Pr, ex.Ra
+    f_sin = [-U[m] for m in range(3)] + [-Th]
+    f_cos2 = [sum(U[n] * sp.diff(U[m], X[n]) for n in range(3)) for m in range(3)]
+    f_cos2.append(sum(U[m] * sp.diff(Th, X[m]) for m in range(3)))
+    f_cos = [sp.diff(P, X[m]) - Pr * lap(U[m]) - Pr * Ra * Th * er[m] for m in range(3)] + [-lap(Th)]
+    fn = sp.lambdify((x, y, z), f_sin + f_cos2 + f_cos, modules="numpy", cse=True)
+    _FORCING_FNS[key] = fn
+    return fn
+
+
+def forcing_modes(ex: Exact, spec: Spec, chunk: int = 1 << 18):
     """Separable forcing of a cos-t manufactured solution, as a list of
     (time_fn_id, fields) with fields = dict(T, ur, uth, uph) in user layout.
 
     With u = cos t U, p = cos t P, T = cos t Th:
       f_u = -sin t U + cos^2 t (U.grad)U + cos t (grad P - Pr lap U - Pr Ra Th e_r)
-      f_T = -sin t Th + cos^2 t U.grad Th + cos t (-lap Th)."""
+      f_T = -sin t Th + cos^2 t U.grad Th + cos t (-lap Th).
+    Derivatives are taken symbolically in Cartesian coordinates."""
     if ex.time_fn != 1 or isinstance(ex, RadialHeat):
         raise ValueError("forcing_modes needs a cos-t solution")
-    Pr, Ra = ex.Pr, ex.Ra
-    modes = {2: {}, 3: {}, 1: {}}
-    # scalar at centres
-    U, P, Th = _jets_at(ex, spec, "c")
-    modes[2]["T"] = -Th.v
-    modes[3]["T"] = sum(U[m].v * Th.g[..., m] for m in range(3))
-    modes[1]["T"] = -Th.lap()
-    for loc, key, comp in (("r", "ur", 0), ("t", "uth", 1), ("p", "uph", 2)):
-        U, P, Th = _jets_at(ex, spec, loc)
+    fn = _forcing_fns(ex)
+    tids = (2, 3, 1)
+    modes = {tid: {} for tid in tids}
+    for loc, key, comp in (("c", "T", None), ("r", "ur", 0), ("t", "uth", 1), ("p", "uph", 2)):
         x, y, z = global_points(spec, loc)
-        rr = np.sqrt(x * x + y * y + z * z)
-        er = (x / rr, y / rr, z / rr)
-        f_sin = [-U[m].v for m in range(3)]
-        f_cos2 = [sum(U[n].v * U[m].g[..., n] for n in range(3)) for m in range(3)]
-        f_cos = [P.g[..., m] - Pr * U[m].lap() - Pr * Ra * Th.v * er[m] for m in range(3)]
-        for tid, f in ((2, f_sin), (3, f_cos2), (1, f_cos)):
-            modes[tid][key] = to_local_components(spec, loc, f)[comp]
+        xf, yf, zf = x.ravel(), y.ravel(), z.ravel()
+        vals = [np.empty(xf.size) for _ in range(12)]
+
+        def work(a):
+            b = min(a + chunk, xf.size)
+            out = fn(xf[a:b], yf[a:b], zf[a:b])
+            for m in range(12):
+                vals[m][a:b] = out[m]
+        # numpy releases the GIL inside ufuncs: chunks evaluate in parallel
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as pool:
+            list(pool.map(work, range(0, xf.size, chunk)))
+        vals = [v.reshape(x.shape) for v in vals]
+        for g, tid in enumerate(tids):
+            blk = vals[4 * g:4 * g + 4]
+            if comp is None:
+                modes[tid][key] = blk[3]
+            else:
+                modes[tid][key] = to_local_components(spec, loc, blk[:3])[comp]
     return [(tid, modes[tid]) for tid in (1, 2, 3)]
 
 

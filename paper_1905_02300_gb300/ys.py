@@ -1,0 +1,192 @@
+"""Python binding of the C ABI in include/ys.h (ctypes; marshalling only).
+
+Every computation runs in the CUDA library libys.so; this module only moves
+numpy buffers across the boundary.  Importing it loads the library and raises
+if it is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libys.so")
+
+YS_OK, YS_EINVAL, YS_ENOMEM, YS_ECUDA, YS_EDIVERGED, YS_ETIMEOUT, YS_EAGAIN, YS_EBUSY = range(8)
+YS_FP64, YS_MIXED = 0, 1
+YS_ADDITIVE, YS_MULTIPLICATIVE = 0, 1
+NFIELDS = 9
+FIELD_NAMES = ("T", "u1r", "u1t", "u1p", "p1", "u2r", "u2t", "u2p", "p2")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1905_02300_gb300.build.build()")
+lib = C.CDLL(LIB_PATH)
+
+
+class Params(C.Structure):
+    _fields_ = [("R1", C.c_double), ("R2", C.c_double), ("Pr", C.c_double), ("Ra", C.c_double),
+                ("dt", C.c_double), ("Nr", C.c_int), ("Nth", C.c_int), ("Nph", C.c_int),
+                ("chi", C.c_double), ("overlap", C.c_int), ("precision", C.c_int),
+                ("schwarz_mode", C.c_int), ("schwarz_tol", C.c_double), ("T_inner", C.c_double),
+                ("T_outer", C.c_double), ("step7", C.c_int)]
+
+
+_dp = C.POINTER(C.c_double)
+_sig = {
+    "ys_default_params": (None, [C.POINTER(Params)]),
+    "ys_create": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
+                            C.c_double, C.POINTER(C.c_void_p)]),
+    "ys_create_ex": (C.c_int, [C.POINTER(Params), C.POINTER(C.c_void_p)]),
+    "ys_set_fields": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, _dp]),
+    "ys_set_fields_ex": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]),
+    "ys_set_fields_dev": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
+    "ys_set_forcing": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, _dp, _dp, _dp]),
+    "ys_set_time": (C.c_int, [C.c_void_p, C.c_double]),
+    "ys_step": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "ys_get_fields": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]),
+    "ys_get_stats": (C.c_int, [C.c_void_p, _dp, _dp, C.POINTER(C.c_long)]),
+    "ys_get_norms": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int)]),
+    "ys_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ys_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "ys_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_char_p), _dp, C.POINTER(C.c_long), C.c_int]),
+    "ys_launch_count": (C.c_long, [C.c_void_p]),
+    "ys_device_bytes": (C.c_size_t, [C.c_void_p]),
+    "ys_destroy": (C.c_int, [C.c_void_p]),
+    "ys_strerror": (C.c_char_p, [C.c_int]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class YSError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {lib.ys_strerror(code).decode()} ({code})")
+        self.code = code
+
+
+def _check(code, what):
+    if code != YS_OK:
+        raise YSError(code, what)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_dp)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib.ys_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Solver:
+    """One shell on the GPU (owns a ys_ctx)."""
+
+    def __init__(self, **params):
+        self.params = default_params(**params)
+        h = C.c_void_p()
+        _check(lib.ys_create_ex(C.byref(self.params), C.byref(h)), "ys_create_ex")
+        self.h = h
+        p = self.params
+        Nr, Nt, Np = p.Nr, p.Nth, p.Nph
+        self.shapes = {"T": (2, Nr, Nt, Np), "p": (2, Nr, Nt, Np), "ur": (2, Nr + 1, Nt, Np),
+                       "uth": (2, Nr, Nt + 1, Np), "uph": (2, Nr, Nt, Np + 1)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.ys_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arr(self, key, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.shape != self.shapes[key]:
+            raise ValueError(f"{key}: shape {a.shape} != {self.shapes[key]}")
+        return a
+
+    def set_fields(self, level, T, ur, uth, uph, p, aux=None):
+        arrs = [self._arr("T", T), self._arr("ur", ur), self._arr("uth", uth), self._arr("uph", uph),
+                self._arr("p", p)]
+        auxp = None
+        if aux is not None:
+            auxp = np.ascontiguousarray(np.concatenate([self._arr("ur", aux[0]).ravel(), self._arr("uth", aux[1]).ravel(),
+                                                        self._arr("uph", aux[2]).ravel(), self._arr("p", aux[3]).ravel()]))
+        _check(lib.ys_set_fields_ex(self.h, level, *[_ptr(a) for a in arrs], _ptr(auxp)), "ys_set_fields_ex")
+
+    def set_fields_dict(self, level, f, aux=None):
+        self.set_fields(level, f["T"], f["ur"], f["uth"], f["uph"], f["p"], aux)
+
+    def set_forcing(self, mode, time_fn, fT, fr, fth, fph):
+        arrs = [self._arr("T", fT), self._arr("ur", fr), self._arr("uth", fth), self._arr("uph", fph)]
+        _check(lib.ys_set_forcing(self.h, mode, time_fn, *[_ptr(a) for a in arrs]), "ys_set_forcing")
+
+    def set_time(self, t):
+        _check(lib.ys_set_time(self.h, t), "ys_set_time")
+
+    def step(self, n_steps=1, n_schwarz=3):
+        _check(lib.ys_step(self.h, n_steps, n_schwarz), "ys_step")
+
+    def get_fields(self, level=0, aux=False):
+        out = {k: np.empty(self.shapes[k]) for k in ("T", "ur", "uth", "uph", "p")}
+        auxa = None
+        if aux:
+            n = sum(int(np.prod(self.shapes[k])) for k in ("ur", "uth", "uph", "p"))
+            auxa = np.empty(n)
+        _check(lib.ys_get_fields(self.h, level, _ptr(out["T"]), _ptr(out["ur"]), _ptr(out["uth"]),
+                                 _ptr(out["uph"]), _ptr(out["p"]), _ptr(auxa)), "ys_get_fields")
+        if aux:
+            o = 0
+            for k, key in (("ur", "ur1"), ("uth", "uth1"), ("uph", "uph1"), ("p", "p1")):
+                n = int(np.prod(self.shapes[k]))
+                out[key] = auxa[o:o + n].reshape(self.shapes[k])
+                o += n
+        return out
+
+    def stats(self):
+        nrm, t, steps = C.c_double(), C.c_double(), C.c_long()
+        _check(lib.ys_get_stats(self.h, C.byref(nrm), C.byref(t), C.byref(steps)), "ys_get_stats")
+        return {"norm": nrm.value, "t": t.value, "steps": steps.value}
+
+    def norms(self):
+        a = np.empty(NFIELDS)
+        it = C.c_int()
+        _check(lib.ys_get_norms(self.h, _ptr(a), C.byref(it)), "ys_get_norms")
+        return a, it.value
+
+    def set_stream(self, stream_handle):
+        _check(lib.ys_set_stream(self.h, C.c_void_p(stream_handle)), "ys_set_stream")
+
+    def profile(self, on=True):
+        _check(lib.ys_profile_enable(self.h, 1 if on else 0), "ys_profile_enable")
+
+    def profile_read(self):
+        cap = 64
+        names = (C.c_char_p * cap)()
+        ms = (C.c_double * cap)()
+        cnt = (C.c_long * cap)()
+        n = lib.ys_profile_read(self.h, names, ms, cnt, cap)
+        if n < 0:
+            raise YSError(-n, "ys_profile_read")
+        return {names[i].decode(): (ms[i], cnt[i]) for i in range(n)}
+
+    def launch_count(self):
+        return lib.ys_launch_count(self.h)
+
+    def device_bytes(self):
+        return lib.ys_device_bytes(self.h)

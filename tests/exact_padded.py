@@ -24,7 +24,7 @@ def padded_exact(g, ex, t, which=("T", "p", "ur", "ut", "up"), a_ex=None):
         zl = R * np.cos(TH)
         x, y, z = np.stack([xl, -xl]), np.stack([yl, zl]), np.stack([zl, yl])
         X, Y, Z = W.Jet.variables(x, y, z)
-        U, P, Th = ex.fields(X, Y, Z)
+        U, P, Th = ex.fields(X, Y, Z, W.JetNS)
         if loc == "c":
             out["T"] = Th.v * c
             out["p"] = P.v * c

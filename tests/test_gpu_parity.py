@@ -1,0 +1,205 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerance: relative max-norm per field, err = max|gpu - oracle| / max|oracle|,
+<= 1e-11 after 10 steps in FP64 (the stated parity target for the plain
+method), tighter for single steps.  Both sides get the same seeded synthetic
+inputs from paper_1905_02300_gb300.workloads.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.scheme import Oracle, Params
+from paper_1905_02300_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("T", "ur", "uth", "uph", "p", "ur1", "uth1", "uph1", "p1")
+
+
+def make_pair(ys, kind="trig", R1=0.5, R2=1.0, Pr=1.0, Ra=1e3, Nr=16, Nth=16, Nph=48, dt=1e-3,
+              mode="additive", tol=0.0, step7=True, T_in=0.0, T_out=0.0, with_gpu=True, with_oracle=True):
+    spec = W.Spec(R1, R2, Nr, Nth, Nph)
+    ex = W.EXACT[kind](R1, R2, Pr, Ra)
+    f0, fm = W.sample_fields(ex, spec, 0.0), W.sample_fields(ex, spec, -dt)
+    if T_in or T_out:
+        Tc = W.conductive_profile(spec, T_in, T_out)
+        f0["T"] = f0["T"] + Tc
+        fm["T"] = fm["T"] + Tc
+    modes = [] if kind == "radial_heat" else W.forcing_modes(ex, spec)
+    o = s = None
+    if with_oracle:
+        o = Oracle(Params(R1=R1, R2=R2, Pr=Pr, Ra=Ra, dt=dt, Nr=Nr, Nth=Nth, Nph=Nph, schwarz_mode=mode,
+                          schwarz_tol=tol, step7=step7, T_in=T_in, T_out=T_out))
+        o.set_fields(0, f0["T"], f0["ur"], f0["uth"], f0["uph"], f0["p"])
+        o.set_fields(1, fm["T"], fm["ur"], fm["uth"], fm["uph"], fm["p"])
+        for tid, F in modes:
+            o.set_forcing(tid, F["T"], F["ur"], F["uth"], F["uph"])
+    if with_gpu:
+        s = ys.Solver(R1=R1, R2=R2, Pr=Pr, Ra=Ra, dt=dt, Nr=Nr, Nth=Nth, Nph=Nph,
+                      schwarz_mode=ys.YS_MULTIPLICATIVE if mode == "multiplicative" else ys.YS_ADDITIVE,
+                      schwarz_tol=tol, step7=1 if step7 else 0, T_inner=T_in, T_outer=T_out)
+        s.set_fields_dict(0, f0)
+        s.set_fields_dict(1, fm)
+        for m, (tid, F) in enumerate(modes):
+            s.set_forcing(m, tid, F["T"], F["ur"], F["uth"], F["uph"])
+    return o, s, spec, ex
+
+
+def rel_errs(s, o, level=0):
+    g = s.get_fields(level, aux=True)
+    r = o.get_fields(level, aux=True)
+    return {k: np.abs(g[k] - r[k]).max() / max(np.abs(r[k]).max(), 1e-300) for k in FIELDS}
+
+
+def assert_parity(s, o, tol, level=0):
+    e = rel_errs(s, o, level)
+    bad = {k: v for k, v in e.items() if not v <= tol}
+    assert not bad, (bad, e)
+    return e
+
+
+def test_set_get_roundtrip_and_boundary_refresh(gpu_lib):
+    o, s, spec, ex = make_pair(gpu_lib)
+    for level in (0, 1):
+        assert_parity(s, o, 1e-14, level)
+
+
+def test_one_step_one_iteration(gpu_lib):
+    o, s, _, _ = make_pair(gpu_lib)
+    o.step(1, 1)
+    s.step(1, 1)
+    assert_parity(s, o, 1e-13)
+    gn, it = s.norms()
+    assert it == 1
+    assert np.allclose(gn, o.last_norms, rtol=1e-9, atol=1e-300)
+
+
+def test_c1_fp64_parity_after_10_steps(gpu_lib):
+    """16x16x48 per patch, R1=0.5, R2=1, Pr=1, Ra=1e3, trigonometric
+    manufactured solution with homogeneous walls, dt=1e-3, 10 steps, 3 Schwarz
+    iterations: every field within 1e-11 relative max-norm of the oracle."""
+    o, s, _, _ = make_pair(gpu_lib)
+    o.step(10, 3)
+    s.step(10, 3)
+    e = assert_parity(s, o, 1e-11)
+    assert s.stats()["steps"] == 10 and abs(s.stats()["t"] - o.t) < 1e-15
+    # both time levels
+    assert_parity(s, o, 1e-11, level=1)
+    print(e)
+
+
+def test_ragged_multi_tile_curl_solution(gpu_lib):
+    """Odd sizes spanning several 128-thread tiles along phi with a ragged tail,
+    non-zero radial velocity."""
+    o, s, _, _ = make_pair(gpu_lib, kind="curl", Nr=9, Nth=21, Nph=151, dt=2e-3, Ra=50.0)
+    o.step(3, 2)
+    s.step(3, 2)
+    assert_parity(s, o, 1e-12)
+
+
+def test_multiplicative_schwarz(gpu_lib):
+    o, s, _, _ = make_pair(gpu_lib, kind="curl", mode="multiplicative", Ra=10.0)
+    o.step(3, 2)
+    s.step(3, 2)
+    assert_parity(s, o, 1e-12)
+
+
+def test_step7_off(gpu_lib):
+    o, s, _, _ = make_pair(gpu_lib, step7=False)
+    o.step(2, 3)
+    s.step(2, 3)
+    assert_parity(s, o, 1e-12)
+
+
+def test_inhomogeneous_wall_temperature(gpu_lib):
+    o, s, _, _ = make_pair(gpu_lib, kind="curl", Ra=100.0, T_in=1.0, T_out=0.0)
+    o.step(3, 3)
+    s.step(3, 3)
+    assert_parity(s, o, 1e-12)
+
+
+def test_tolerance_driven_iterations(gpu_lib):
+    o, s, _, _ = make_pair(gpu_lib, kind="curl", Ra=10.0, tol=1e-8)
+    o.step(2, 50)
+    s.step(2, 50)
+    gn, it = s.norms()
+    assert it == o.iters_done and it < 50
+    assert_parity(s, o, 1e-11)
+
+
+def test_radial_heat_closed_form_on_gpu(gpu_lib):
+    errs = []
+    for N, dt in ((16, 2e-3), (32, 5e-4)):
+        _, s, spec, ex = make_pair(gpu_lib, kind="radial_heat", Ra=0.0, Nr=N, Nth=N, Nph=3 * N, dt=dt,
+                                   tol=1e-12, with_oracle=False)
+        s.step(int(round(0.016 / dt)), 80)
+        got = s.get_fields(0)["T"]
+        exact = W.sample_fields(ex, spec, s.stats()["t"])["T"]
+        errs.append(np.abs(got - exact).max())
+    assert math.log2(errs[0] / errs[1]) > 1.7, errs
+
+
+def test_restart_is_bitwise(gpu_lib):
+    """Checkpoint/resume: 6 steps straight == 3 steps, save both levels (with
+    the system-1 fields), restore into a fresh context, 3 more steps."""
+    _, a, _, _ = make_pair(gpu_lib, kind="curl", Ra=10.0, with_oracle=False)
+    _, b, _, _ = make_pair(gpu_lib, kind="curl", Ra=10.0, with_oracle=False)
+    a.step(6, 3)
+    b.step(3, 3)
+    lv = [b.get_fields(l, aux=True) for l in (0, 1)]
+    t = b.stats()["t"]
+    _, c, _, _ = make_pair(gpu_lib, kind="curl", Ra=10.0, with_oracle=False)
+    for l in (1, 0):
+        f = lv[l]
+        c.set_fields(l, f["T"], f["ur"], f["uth"], f["uph"], f["p"], aux=(f["ur1"], f["uth1"], f["uph1"], f["p1"]))
+    c.set_time(t)
+    c.step(3, 3)
+    ga, gc = a.get_fields(0, aux=True), c.get_fields(0, aux=True)
+    for k in FIELDS:
+        assert np.array_equal(ga[k], gc[k]), k
+
+
+# ---------------------------------------------------------------- full size
+FULL = dict(R1=0.5, R2=1.0, Pr=1.0, Ra=1e3, Nr=128, Nth=128, Nph=384, dt=5e-4)
+
+
+def test_full_size_yin_yang_congruence_bitwise(gpu_lib):
+    """128x128x384 per patch (the benchmarked size and launch configuration):
+    M-invariant data stays bitwise identical on both patches."""
+    ys = gpu_lib
+    spec = W.Spec(FULL["R1"], FULL["R2"], 128, 128, 384)
+    ex = W.SymmetricShell(FULL["R1"], FULL["R2"], 1.0, 1e3)
+    f0 = W.sample_fields(ex, spec, 0.0)
+    for k in f0:
+        f0[k][1] = f0[k][0]
+    s = ys.Solver(**FULL)
+    s.set_fields_dict(0, f0)
+    s.step(2, 3)
+    g = s.get_fields(0, aux=True)
+    for k in FIELDS:
+        assert np.array_equal(g[k][0], g[k][1]), k
+    assert np.isfinite(g["uth"]).all() and np.abs(g["uth"]).max() > 1e-3
+
+
+def test_full_size_space_convergence(gpu_lib):
+    """Second order in space on 32x32x96, 64x64x192 and 128x128x384 per patch
+    (manufactured solution, small dt, Schwarz to tolerance)."""
+    errs = []
+    for N in (32, 64, 128):
+        _, s, spec, ex = make_pair(gpu_lib, kind="curl", Nr=N, Nth=N, Nph=3 * N, dt=2.5e-4, Ra=10.0,
+                                   tol=1e-9, with_oracle=False)
+        s.step(4, 40)
+        g = s.get_fields(0)
+        exact = W.sample_fields(ex, spec, s.stats()["t"])
+        e = {}
+        for k, loc in (("T", "c"), ("ur", "r"), ("uth", "t"), ("uph", "p")):
+            r, th, _ = spec.coords(loc)
+            w = np.broadcast_to(r * r * np.sin(th), g[k].shape)
+            d = g[k] - exact[k]
+            e[k] = math.sqrt(np.sum(w * d * d) / np.sum(w))
+        errs.append(e)
+    for k in errs[0]:
+        for a, b in ((0, 1), (1, 2)):
+            assert math.log2(errs[a][k] / errs[b][k]) > 1.7, (k, errs)

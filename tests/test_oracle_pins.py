@@ -188,12 +188,12 @@ class GradCurlShell(W.Exact):
     p, for operator pins: u = CurlShell u + grad(s(r)^2 x y)."""
     name = "gradcurl"
 
-    def fields(self, x, y, z):
-        U, P, Th = W.CurlShell(self.R1, self.R2, self.Pr, self.Ra).fields(x, y, z)
-        r = (x * x + y * y + z * z).sqrt()
+    def fields(self, x, y, z, F):
+        U, P, Th = W.CurlShell(self.R1, self.R2, self.Pr, self.Ra).fields(x, y, z, F)
+        r = F.sqrt(x * x + y * y + z * z)
         L = self.R2 - self.R1
-        s = ((r - self.R1) * (math.pi / L)).sin()
-        ds = ((r - self.R1) * (math.pi / L)).cos() * (math.pi / L)
+        s = F.sin((r - self.R1) * (math.pi / L))
+        ds = F.cos((r - self.R1) * (math.pi / L)) * (math.pi / L)
         q = s * s
         dq = 2.0 * s * ds / r
         g_ = [dq * x * x * y + q * y, dq * y * x * y + q * x, dq * z * x * y]
