@@ -170,6 +170,37 @@ long ys_launch_count(ys_ctx *c);
 /* Bytes of device memory held by the context. */
 size_t ys_device_bytes(ys_ctx *c);
 
+/* Allocation-free preconditioner solve (the paper has no counterpart; this is
+ * a library convenience).  Some callers cannot call cudaMalloc: code running
+ * inside a host-side memory budget enforced by another allocator, callbacks
+ * that must not trigger the driver's allocator or its implicit
+ * synchronisation, and embedders that forbid device allocations after start-up.
+ * This entry point allocates nothing: it applies x = P^-1 rhs, the product of
+ * the three 1-D factors (I - dt/2 Ahat_d) of one unknown in its stated order
+ * (the correction solve of Eq. er: T r, theta, phi; u_r theta, phi, r;
+ * u_theta phi, r, theta; u_phi r, theta, phi), for one shell described by
+ * *prm (R1, R2, Pr as viscosity, dt, chi, overlap, Nr, Nth, Nph; other fields
+ * ignored).  loc selects the unknown: 0 = T, 1 = u_r, 2 = u_theta, 3 = u_phi.
+ * All pointers are caller-owned DEVICE memory in the field layouts above:
+ * A_r, A_th, A_ph the advecting velocity on r-, theta- and phi-faces; rhs and
+ * x in the layout of the unknown (boundary entries of rhs are ignored, those
+ * of x are set to 0).  Work is queued on `stream` (a cudaStream_t, NULL = the
+ * legacy default stream).
+ * Scratch: one static device array of 5 * 2^18 + 6 * 264 doubles (about
+ * 10.5 MB) that every GPU which loads the library holds until the process
+ * exits.  Grids are limited to Nr, Nth, Nph <= 256 and at most 2^18 padded
+ * elements per field (e.g. 32 x 32 x 96 per patch fits, 48 x 48 x 144 does
+ * not); larger grids, bad sizes or NULL pointers return YS_EINVAL before any
+ * work is queued.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current, so make the first
+ * call on a device before any stream capture.  Every call shares the one
+ * array and overwrites the previous call's contents (the working fields are
+ * cleared at the start of each call): calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Errors: YS_EINVAL, YS_ECUDA. */
+int ys_factor_solve_static(const ys_params *prm, int loc, const double *A_r, const double *A_th,
+                           const double *A_ph, const double *rhs, double *x, void *stream);
+
 int ys_destroy(ys_ctx *c);
 
 const char *ys_strerror(int code);

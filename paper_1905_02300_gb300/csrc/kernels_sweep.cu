@@ -9,6 +9,10 @@
 // with d'; back substitution overwrites d' with the solution, or, for the last
 // factor of an unknown, adds it to the iterate and accumulates the FP64
 // midpoint-rule norm of the increment (Sec. 5.1).
+#include <cmath>
+#include <mutex>
+
+#include "../../include/ys.h"
 #include "kernels.cuh"
 
 namespace ys {
@@ -248,4 +252,173 @@ void Launch<R>::sweep(const Shell &S, int loc, int dir, bool final, StepAux<R> a
 template void Launch<double>::sweep(const Shell &, int, int, bool, StepAux<double>, double *, double *, double *,
                                     double *, int, int, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// Allocation-free factored solve: ys_factor_solve_static (include/ys.h).
+//
+// For callers that cannot allocate device memory.  All scratch (padded working
+// copies of the inputs, the Thomas coefficients c' and the metric tables)
+// lives in one file-scope __device__ array, g_static_scratch, sized for
+// grids of at most kStaticFieldElems padded elements per field.  Every GPU
+// that loads the library holds it until the process exits.
+namespace {
+
+constexpr long kStaticFieldElems = 1L << 18;  // padded elements of one field (both patches)
+constexpr int kStaticMaxN = 256;              // cells along any direction
+constexpr int kStaticMetricLen = kStaticMaxN + 8;
+constexpr long kStaticElems = 5 * kStaticFieldElems + 6L * kStaticMetricLen;
+constexpr int kMaxDevices = 64;
+
+// [A_r | A_th | A_ph | B (rhs, then solution) | Cs (c')] padded fields, then the metric
+__device__ __align__(256) double g_static_scratch[kStaticElems];
+
+std::mutex g_static_mu;
+double *g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device.  The host-side
+// name of the array is only a stand-in, so the address is looked up once per
+// device with that device current and cached.
+int static_scratch(double **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return YS_ECUDA;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void **)&ptr, g_static_scratch);
+    if (e != cudaSuccess || ptr == nullptr) {
+      cudaGetLastError();
+      return YS_ECUDA;
+    }
+    g_static_addr[dev] = (double *)ptr;
+  }
+  *out = g_static_addr[dev];
+  return YS_OK;
+}
+
+__device__ __forceinline__ void static_extent(const Layout &L, int loc, int &ni, int &nj, int &nk) {
+  ni = L.Nr + (loc == LR ? 1 : 0);
+  nj = L.Nt + (loc == LT ? 1 : 0);
+  nk = L.Np + (loc == LP ? 1 : 0);
+}
+
+// user layout (device) -> padded layout (static scratch)
+__global__ void k_static_unpack(Layout L, int loc, const double *src, double *dst) {
+  int ni, nj, nk;
+  static_extent(L, loc, ni, nj, nk);
+  long n = 2L * ni * nj * nk;
+  for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
+    int k = (int)(u % nk);
+    long t = u / nk;
+    int j = (int)(t % nj);
+    t /= nj;
+    int i = (int)(t % ni);
+    int p = (int)(t / ni);
+    dst[lidx(L, p, i, j, k)] = src[u];
+  }
+}
+
+// solution at the unknowns -> user layout (device); boundary entries get 0
+__global__ void k_static_pack(Layout L, int loc, const double *src, double *dst) {
+  int ni, nj, nk;
+  static_extent(L, loc, ni, nj, nk);
+  long n = 2L * ni * nj * nk;
+  for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
+    int k = (int)(u % nk);
+    long t = u / nk;
+    int j = (int)(t % nj);
+    t /= nj;
+    int i = (int)(t % ni);
+    int p = (int)(t / ni);
+    bool boundary = (loc == LR && (i == 0 || i == L.Nr)) || (loc == LT && (j == 0 || j == L.Nt)) ||
+                    (loc == LP && (k == 0 || k == L.Np));
+    dst[u] = boundary ? 0.0 : src[lidx(L, p, i, j, k)];
+  }
+}
+
+}  // namespace
+
 }  // namespace ys
+
+extern "C" int ys_factor_solve_static(const ys_params *prm, int loc, const double *A_r, const double *A_th,
+                                      const double *A_ph, const double *rhs, double *x, void *stream) {
+  using namespace ys;
+  if (!prm || loc < LC || loc > LP || !A_r || !A_th || !A_ph || !rhs || !x) return YS_EINVAL;
+  if (!(prm->R1 > 0.0) || !(prm->R2 > prm->R1) || !(prm->dt > 0.0) || !(prm->chi > 0.0) || !(prm->Pr > 0.0))
+    return YS_EINVAL;
+  if (prm->Nr < 8 || prm->Nth < 8 || prm->Nph < 8 || prm->overlap < 1) return YS_EINVAL;
+  if (prm->Nr > kStaticMaxN || prm->Nth > kStaticMaxN || prm->Nph > kStaticMaxN) return YS_EINVAL;
+  if (prm->Nth <= 2 * prm->overlap + 4) return YS_EINVAL;
+  Layout L;
+  L.Nr = prm->Nr;
+  L.Nt = prm->Nth;
+  L.Np = prm->Nph;
+  L.NJ = prm->Nth + 2;
+  L.P = ((prm->Nph + 2) + 7) / 8 * 8;
+  L.SI = (long)L.NJ * L.P;
+  long box = (long)(prm->Nr + 2) * L.SI + 16;
+  L.PS = (box + 31) / 32 * 32;
+  L.total = 2 * L.PS;
+  if (L.total > kStaticFieldElems) return YS_EINVAL;  // larger than the static scratch
+  const double pi = 3.14159265358979323846;
+  const double hr = (prm->R2 - prm->R1) / prm->Nr;
+  const double ht = (pi / 2) / (prm->Nth - 2 * prm->overlap);
+  const double th0 = pi / 4 - prm->overlap * ht;
+  const double hp = (1.5 * pi + 2 * prm->overlap * ht) / prm->Nph;
+  if (!(th0 > 0.0)) return YS_EINVAL;
+
+  double *base = nullptr;
+  int rc = static_scratch(&base);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  double *Af[3] = {base, base + kStaticFieldElems, base + 2 * kStaticFieldElems};
+  double *B = base + 3 * kStaticFieldElems;
+  double *Cs = base + 4 * kStaticFieldElems;
+  double *met = base + 5 * kStaticFieldElems;
+
+  // metric tables r_c, r_f, sin/cos at theta centres and faces (pad 2), on the stack
+  const int pad = 2;
+  double mh[6 * kStaticMetricLen];
+  for (int t = 0; t < kStaticMetricLen; ++t) {
+    int i = t - pad;
+    mh[0 * kStaticMetricLen + t] = prm->R1 + (i + 0.5) * hr;
+    mh[1 * kStaticMetricLen + t] = prm->R1 + i * hr;
+    mh[2 * kStaticMetricLen + t] = std::sin(th0 + (i + 0.5) * ht);
+    mh[3 * kStaticMetricLen + t] = std::sin(th0 + i * ht);
+    mh[4 * kStaticMetricLen + t] = std::cos(th0 + (i + 0.5) * ht);
+    mh[5 * kStaticMetricLen + t] = std::cos(th0 + i * ht);
+  }
+  // every call shares the scratch: clear the working fields left by the last call
+  if (cudaMemsetAsync(base, 0, 4 * kStaticFieldElems * sizeof(double), st) != cudaSuccess) return YS_ECUDA;
+  if (cudaMemcpyAsync(met, mh, sizeof(mh), cudaMemcpyHostToDevice, st) != cudaSuccess) return YS_ECUDA;
+  const double *Ain[3] = {A_r, A_th, A_ph};
+  for (int a = 0; a < 3; ++a) k_static_unpack<<<256, 256, 0, st>>>(L, LR + a, Ain[a], Af[a]);
+  k_static_unpack<<<256, 256, 0, st>>>(L, loc, rhs, B);
+
+  Shell S{};
+  S.L = L;
+  S.hr = hr;
+  S.ht = ht;
+  S.hp = hp;
+  S.R1 = prm->R1;
+  S.sin_theta1 = std::sin(th0);
+  S.dt = prm->dt;
+  S.nu = prm->Pr;
+  S.kappa = 1.0;
+  S.chi = prm->chi;
+  S.rc = met + 0 * kStaticMetricLen + pad;
+  S.rf = met + 1 * kStaticMetricLen + pad;
+  S.sc = met + 2 * kStaticMetricLen + pad;
+  S.sf = met + 3 * kStaticMetricLen + pad;
+  S.cc = met + 4 * kStaticMetricLen + pad;
+  S.cf = met + 5 * kStaticMetricLen + pad;
+  StepAux<double> ax{};
+  for (int a = 0; a < 3; ++a) ax.A[a] = Af[a];
+  // factor order, first solved first: T r,theta,phi; u_r theta,phi,r;
+  // u_theta phi,r,theta; u_phi r,theta,phi
+  const int order[4][3] = {{DR, DT, DP}, {DT, DP, DR}, {DP, DR, DT}, {DR, DT, DP}};
+  for (int s = 0; s < 3; ++s)
+    Launch<double>::sweep(S, loc, order[loc][s], false, ax, B, Cs, nullptr, nullptr, 0, 3, st);
+  k_static_pack<<<256, 256, 0, st>>>(L, loc, B, x);
+  return cudaGetLastError() == cudaSuccess ? YS_OK : YS_ECUDA;
+}
+
+

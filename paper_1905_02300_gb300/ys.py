@@ -55,6 +55,8 @@ _sig = {
     "ys_launch_count": (C.c_long, [C.c_void_p]),
     "ys_device_bytes": (C.c_size_t, [C.c_void_p]),
     "ys_destroy": (C.c_int, [C.c_void_p]),
+    "ys_factor_solve_static": (C.c_int, [C.POINTER(Params), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]),
     "ys_strerror": (C.c_char_p, [C.c_int]),
 }
 for _name, (_res, _args) in _sig.items():
