@@ -44,13 +44,18 @@ UNIT = "cell-updates/s"
 
 # Algorithmic words moved per cell per launch of each kernel class, counting
 # one read of every input array and one write of every output (neighbour
-# reuse on chip; ghosts ~1/N ignored).  Sweeps: rhs + advecting component +
-# result (3), final sweeps also read the iterate (4); averages over the
-# launches of one iteration.
+# reuse on chip; ghosts ~1/N ignored).  Line solves (k_solve, classes sweep_*):
+# rhs + the three stored LU factors + result = 5, a final factor also reads and
+# writes the iterate = 6; averaged over one iteration's launches.  factorize:
+# advecting component in, three factors out = 4.  See the design doc.
 WORDS_PER_CELL = {
-    "extrapolate": 30.0, "resid_T": 7.0, "resid_u": 82.0 / 6, "sweep_r": 23.0 / 7, "sweep_t": 23.0 / 7,
-    "sweep_p": 24.0 / 7, "pressure": 10.0,
+    "extrapolate": 30.0, "resid_T": 7.0, "resid_u": 82.0 / 6, "sweep_r": 37.0 / 7, "sweep_t": 37.0 / 7,
+    "sweep_p": 38.0 / 7, "pressure": 10.0, "factorize": 4.0,
 }
+# FP64 operations per cell (hand count of the kernel formulas, FMA = 2) for the
+# ALU-bound FP64 kernels; a division counts as one operation.
+FLOPS_PER_CELL = {"resid_T": 80.0, "resid_u": 200.0, "pressure": 50.0, "factorize": 70.0}
+FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of GB300 (profiling recipe)
 
 
 def env_rank():
@@ -244,16 +249,33 @@ def main():
     e2e_s = statistics.median(t_e2e)
     e2e_val = world * cells / e2e_s
 
-    # roofline of the dominant kernel class
+    # roofline of the dominant kernel: the three line-solve classes are one
+    # kernel (k_solve)
     hbm, src = peaks()
-    top = max((k for k in prof if k in WORDS_PER_CELL), key=lambda k: prof[k][0])
-    tot_ms, n_l = prof[top]
-    avg_ms = tot_ms / max(n_l, 1)
-    bytes_per_launch = WORDS_PER_CELL[top] * 8 * cells
-    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "kernel": top, "peak_source": src,
-            "kernel_share": tot_ms / ms}
+    merged = {}
+    for k, (t_ms, n_l) in prof.items():
+        key = "solve" if k.startswith("sweep_") else k
+        w = WORDS_PER_CELL.get(k)
+        b = (w * 8 * cells * n_l) if w is not None else 0.0
+        m = merged.setdefault(key, [0.0, 0, 0.0, 0.0])
+        m[0] += t_ms
+        m[1] += n_l
+        m[2] += b
+        m[3] += FLOPS_PER_CELL.get(k, 0.0) * cells * n_l
+    top = max((k for k in merged if merged[k][1]), key=lambda k: merged[k][0])
+    t_ms, n_l, tot_bytes, tot_flops = merged[top]
+    gbs = tot_bytes / (t_ms * 1e-3) / 1e9
+    tfl = tot_flops / (t_ms * 1e-3) / 1e12
+    if tot_flops and tfl / FP64_PEAK_TFLOPS > gbs / hbm:
+        roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None, "kernel": top,
+                "peak_source": "nominal FP64 (no FP64 figure in MEASURED_PEAKS.json)",
+                "hbm_gbs": gbs, "hbm_frac": gbs / hbm}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": None, "kernel": top, "peak_source": src}
+    roof["kernel_share"] = t_ms / sum(v[0] for v in prof.values())
+    roof["launches"] = n_l
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

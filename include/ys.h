@@ -186,7 +186,7 @@ size_t ys_device_bytes(ys_ctx *c);
  * x in the layout of the unknown (boundary entries of rhs are ignored, those
  * of x are set to 0).  Work is queued on `stream` (a cudaStream_t, NULL = the
  * legacy default stream).
- * Scratch: one static device array of 5 * 2^18 + 6 * 264 doubles (about
+ * Scratch: one static device array of 5 * 2^18 + 10 * 264 doubles (about
  * 10.5 MB) that every GPU which loads the library holds until the process
  * exits.  Grids are limited to Nr, Nth, Nph <= 256 and at most 2^18 padded
  * elements per field (e.g. 32 x 32 x 96 per patch fits, 48 x 48 x 144 does

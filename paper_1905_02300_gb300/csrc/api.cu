@@ -21,10 +21,11 @@ namespace {
 // kernel classes for timing
 enum KClass {
   K_EXTRAP = 0, K_FORCE, K_EXCH, K_WALLS, K_RING, K_RES_T, K_RES_U, K_SWEEP_R, K_SWEEP_T, K_SWEEP_P, K_PRES,
-  K_PACK, K_NUM
+  K_PACK, K_FACTOR, K_NUM
 };
 const char *kClassNames[K_NUM] = {"extrapolate", "forcing",  "exchange", "walls",   "ring",     "resid_T",
-                                  "resid_u",     "sweep_r",  "sweep_t",  "sweep_p", "pressure", "pack"};
+                                  "resid_u",     "sweep_r",  "sweep_t",  "sweep_p", "pressure", "pack",
+                                  "factorize"};
 
 struct ProfRec {
   int cls;
@@ -47,6 +48,9 @@ struct ys_ctx {
   double *A[3];
   double *fcomb[4];
   double *B, *Cs;
+  // per-step LU factors of the 12 (unknown, direction) line operators:
+  // fac[loc][dir][0..2] = lo, 1/pivot, c'
+  double *fac[4][3][3];
   double *metric = nullptr;
   XEntry *xdev = nullptr;
   XTables X;
@@ -148,26 +152,37 @@ const int kOrder[4][3] = {
 };
 const int kSweepClass[3] = {K_SWEEP_R, K_SWEEP_T, K_SWEEP_P};
 
-void solve_unknown(ys_ctx *c, int loc, int slot, StepAux<double> ax, int mask) {
+void solve_unknown(ys_ctx *c, int loc, int slot, int mask) {
   State<double> &it = c->lev[2];
   for (int s = 0; s < 3; ++s) {
     int dir = kOrder[loc][s];
     bool fin = (s == 2);
+    double *const *F = c->fac[loc][dir];
     LAUNCH(c, kSweepClass[dir], 1,
-           Launch<double>::sweep(c->S, loc, dir, fin, ax, c->B, c->Cs, it.f[slot], c->norm, slot, mask, c->stream));
+           Launch<double>::solve(c->S, loc, dir, fin, F[0], F[1], F[2], c->B, it.f[slot], c->norm, slot, mask,
+                                 c->stream));
   }
+}
+
+// LU factors of every line operator for this step (they depend only on a)
+void factorize_all(ys_ctx *c, StepAux<double> ax) {
+  for (int loc = LC; loc <= LP; ++loc)
+    for (int dir = DR; dir <= DP; ++dir) {
+      double *const *F = c->fac[loc][dir];
+      LAUNCH(c, K_FACTOR, 1, Launch<double>::factorize(c->S, loc, dir, ax, F[0], F[1], F[2], 3, c->stream));
+    }
 }
 
 // one defect-correction pass over T, u1, p1, u2, p2 on the masked patches
 void iterate(ys_ctx *c, StepAux<double> ax, int mask) {
   State<double> &it = c->lev[2], &n = c->lev[0];
   LAUNCH(c, K_RES_T, 1, Launch<double>::resid_T(c->S, it, n, ax, c->B, mask, c->stream));
-  solve_unknown(c, LC, F_T, ax, mask);
+  solve_unknown(c, LC, F_T, mask);
   for (int sys = 1; sys <= 2; ++sys) {
     int o = (sys == 1) ? 0 : 4;
     for (int comp = 0; comp < 3; ++comp) {
       LAUNCH(c, K_RES_U, 1, Launch<double>::resid_u(c->S, sys, comp, it, n, ax, c->B, mask, c->stream));
-      solve_unknown(c, LR + comp, F_U1R + comp + o, ax, mask);
+      solve_unknown(c, LR + comp, F_U1R + comp + o, mask);
     }
     LAUNCH(c, K_PRES, 1, Launch<double>::pressure(c->S, sys, it, n, c->norm, mask, c->stream));
   }
@@ -274,7 +289,7 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   std::vector<double> met;
   int pad, len;
   make_metric(gs, G, met, pad, len);
-  size_t nfields = 3 * NF + 3 + 4 + 2;
+  size_t nfields = 3 * NF + 3 + 4 + 2 + 36;
   size_t field_bytes = (size_t)L.total * sizeof(double);
   size_t xcount = 0;
   for (int k = 0; k < XNUM; ++k) xcount += xt[k].size();
@@ -312,6 +327,9 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   for (int a = 0; a < 4; ++a) c->fcomb[a] = c->fields + (fi++) * L.total;
   c->B = c->fields + (fi++) * L.total;
   c->Cs = c->fields + (fi++) * L.total;
+  for (int loc = 0; loc < 4; ++loc)
+    for (int dir = 0; dir < 3; ++dir)
+      for (int a = 0; a < 3; ++a) c->fac[loc][dir][a] = c->fields + (fi++) * L.total;
   c->metric = (double *)(base + off_metric);
   c->xdev = (XEntry *)(base + off_x);
   c->norm = (double *)(base + off_norm);
@@ -343,6 +361,16 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   S.sf = c->metric + 3 * len + pad;
   S.cc = c->metric + 4 * len + pad;
   S.cf = c->metric + 5 * len + pad;
+  S.irc = c->metric + 6 * len + pad;
+  S.irf = c->metric + 7 * len + pad;
+  S.isc = c->metric + 8 * len + pad;
+  S.isf = c->metric + 9 * len + pad;
+  S.ihr = 1.0 / G.hr;
+  S.iht = 1.0 / G.ht;
+  S.ihp = 1.0 / G.hp;
+  S.i2chi = 1.0 / (2.0 * p->chi);
+  S.iR1sq = 1.0 / (p->R1 * p->R1);
+  S.cphi = 1.0 / (p->R1 * p->R1 * S.sin_theta1 * S.sin_theta1 * G.hp * G.hp);
   S.T_in = p->T_inner;
   S.T_out = p->T_outer;
   S.step7 = p->step7;
@@ -464,6 +492,7 @@ int ys_step(ys_ctx *c, int n_steps, int n_schwarz) {
       ax.ft = c->fcomb[2];
       ax.fp = c->fcomb[3];
     }
+    factorize_all(c, ax);
     c->iters_last = 0;
     for (int k = 1; k <= n_schwarz; ++k) {
       cudaMemsetAsync(c->norm, 0, YS_NFIELDS * sizeof(double), c->stream);

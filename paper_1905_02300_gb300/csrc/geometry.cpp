@@ -24,21 +24,27 @@ int make_grid(const GridSpec &g, GridGeo &out) {
 }
 
 void make_metric(const GridSpec &g, const GridGeo &G, std::vector<double> &tab, int &pad, int &len) {
-  // six tables (rc, rf, sc, sf, cc, cf), each indexed by logical index with
-  // `pad` slots below 0
+  // kMetricTables tables (rc, rf, sc, sf, cc, cf and the reciprocals of rc,
+  // rf, sc, sf), each indexed by logical index with `pad` slots below 0
   pad = 2;
   int n = (g.Nr > g.Nth ? g.Nr : g.Nth) + 2 * pad + 2;
   len = n;
-  tab.assign(6 * (size_t)n, 0.0);
+  tab.assign(kMetricTables * (size_t)n, 0.0);
+  auto inv = [](double v) { return v != 0.0 ? 1.0 / v : 0.0; };
   for (int t = 0; t < n; ++t) {
     int i = t - pad;
-    tab[0 * n + t] = g.R1 + (i + 0.5) * G.hr;
-    tab[1 * n + t] = g.R1 + i * G.hr;
+    double rc = g.R1 + (i + 0.5) * G.hr, rf = g.R1 + i * G.hr;
     double thc = G.th0 + (i + 0.5) * G.ht, thf = G.th0 + i * G.ht;
+    tab[0 * n + t] = rc;
+    tab[1 * n + t] = rf;
     tab[2 * n + t] = std::sin(thc);
     tab[3 * n + t] = std::sin(thf);
     tab[4 * n + t] = std::cos(thc);
     tab[5 * n + t] = std::cos(thf);
+    tab[6 * n + t] = inv(rc);
+    tab[7 * n + t] = inv(rf);
+    tab[8 * n + t] = inv(std::sin(thc));
+    tab[9 * n + t] = inv(std::sin(thf));
   }
 }
 

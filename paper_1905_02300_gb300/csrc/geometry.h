@@ -17,8 +17,8 @@ struct GridGeo {
 
 // 0 on success, 1 if the parameters do not define a valid patch
 int make_grid(const GridSpec &g, GridGeo &out);
-// six FP64 tables rc, rf, sc, sf, cc, cf of length `len`, logical index i at
-// slot i + pad
+// kMetricTables FP64 tables rc, rf, sc, sf, cc, cf, 1/rc, 1/rf, 1/sc, 1/sf of
+// length `len`, logical index i at slot i + pad
 void make_metric(const GridSpec &g, const GridGeo &G, std::vector<double> &tab, int &pad, int &len);
 // exchange tables for every kind; 1 if a donor stencil leaves the donor's
 // unknowns (grid too coarse)

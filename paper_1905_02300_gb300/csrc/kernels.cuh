@@ -53,6 +53,12 @@ struct Launch {
   // accumulate the weighted squared increment into norm[slot]
   static void sweep(const Shell &S, int loc, int dir, bool final, StepAux<R> ax, R *B, R *Cs, R *dst,
                     double *norm, int slot, int patch_mask, cudaStream_t st);
+  // per-step LU factorisation of the factor (loc, dir) into (Lo, Iv, Cp)
+  static void factorize(const Shell &S, int loc, int dir, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask,
+                        cudaStream_t st);
+  // line solve with a stored factorisation (same conventions as sweep)
+  static void solve(const Shell &S, int loc, int dir, bool final, const R *Lo, const R *Iv, const R *Cp, R *B,
+                    R *dst, double *norm, int slot, int patch_mask, cudaStream_t st);
   static void pressure(const Shell &S, int sys, State<R> it, State<R> n, double *norm, int patch_mask,
                        cudaStream_t st);
   // host layout <-> device layout

@@ -22,13 +22,13 @@ __device__ __forceinline__ double H(const R *a, const R *b, long q) {
 
 template <typename R>
 __device__ __forceinline__ double avg4(const R *a, long q1, long q2, long q3, long q4) {
-  return (((double)a[q1] + (double)a[q2]) + (double)a[q3] + (double)a[q4]) / 4.0;
+  return (((double)a[q1] + (double)a[q2]) + (double)a[q3] + (double)a[q4]) * 0.25;
 }
 
 // half-level average of 4 points of a pair of arrays
 template <typename R>
 __device__ __forceinline__ double havg4(const R *a, const R *b, long q1, long q2, long q3, long q4) {
-  return ((H(a, b, q1) + H(a, b, q2)) + H(a, b, q3) + H(a, b, q4)) / 4.0;
+  return ((H(a, b, q1) + H(a, b, q2)) + H(a, b, q3) + H(a, b, q4)) * 0.25;
 }
 
 // region of unknowns of a location type, logical half-open ranges
@@ -63,11 +63,11 @@ template <typename R>
 __device__ __forceinline__ double divh(const Shell &S, const R *ri, const R *rn, const R *ti, const R *tn,
                                        const R *pi, const R *pn, int i, int j, long q) {
   const Layout &L = S.L;
-  double r = S.rc[i], s = S.sc[j];
-  double d_r = (S.rf[i + 1] * S.rf[i + 1] * H(ri, rn, q + L.SI) - S.rf[i] * S.rf[i] * H(ri, rn, q)) /
-               (r * r * S.hr);
-  double d_t = (S.sf[j + 1] * H(ti, tn, q + L.P) - S.sf[j] * H(ti, tn, q)) / (r * s * S.ht);
-  double d_p = (H(pi, pn, q + 1) - H(pi, pn, q)) / (r * s * S.hp);
+  double ir = S.irc[i], is = S.isc[j];
+  double d_r = (S.rf[i + 1] * S.rf[i + 1] * H(ri, rn, q + L.SI) - S.rf[i] * S.rf[i] * H(ri, rn, q)) *
+               (ir * ir * S.ihr);
+  double d_t = (S.sf[j + 1] * H(ti, tn, q + L.P) - S.sf[j] * H(ti, tn, q)) * (ir * is * S.iht);
+  double d_p = (H(pi, pn, q + 1) - H(pi, pn, q)) * (ir * is * S.ihp);
   return d_r + d_t + d_p;
 }
 
@@ -107,19 +107,20 @@ __global__ void k_resid_T(Shell S, State<R> it, State<R> n, StepAux<R> ax, R *B,
   if (!decode_point(L, LC, patch_mask, p, i, j, k)) return;
   long q = lidx(L, p, i, j, k);
   const R *a = it.f[F_T], *b = n.f[F_T];
-  double r = S.rc[i], s = S.sc[j];
-  double hr = S.hr, ht = S.ht, hp = S.hp;
+  const double ir = S.irc[i], is = S.isc[j], ir2 = ir * ir;
+  const double ihr = S.ihr, iht = S.iht, ihp = S.ihp;
   double X0 = H(a, b, q);
   double Xrp = H(a, b, q + L.SI), Xrm = H(a, b, q - L.SI);
   double Xtp = H(a, b, q + L.P), Xtm = H(a, b, q - L.P);
   double Xpp = H(a, b, q + 1), Xpm = H(a, b, q - 1);
-  double Drr = (S.rf[i + 1] * S.rf[i + 1] * (Xrp - X0) - S.rf[i] * S.rf[i] * (X0 - Xrm)) / (r * r * hr * hr);
-  double Dtt = (S.sf[j + 1] * (Xtp - X0) - S.sf[j] * (X0 - Xtm)) / (r * r * s * ht * ht);
-  double Dpp = (Xpp - 2.0 * X0 + Xpm) / (r * r * s * s * hp * hp);
-  double ar = ((double)ax.A[0][q] + (double)ax.A[0][q + L.SI]) / 2.0;
-  double at = ((double)ax.A[1][q] + (double)ax.A[1][q + L.P]) / 2.0;
-  double ap = ((double)ax.A[2][q] + (double)ax.A[2][q + 1]) / 2.0;
-  double adv = ar * (Xrp - Xrm) / (2 * hr) + at * (Xtp - Xtm) / (2 * r * ht) + ap * (Xpp - Xpm) / (2 * r * s * hp);
+  double Drr = (S.rf[i + 1] * S.rf[i + 1] * (Xrp - X0) - S.rf[i] * S.rf[i] * (X0 - Xrm)) * (ir2 * ihr * ihr);
+  double Dtt = (S.sf[j + 1] * (Xtp - X0) - S.sf[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
+  double Dpp = (Xpp - 2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
+  double ar = ((double)ax.A[0][q] + (double)ax.A[0][q + L.SI]) * 0.5;
+  double at = ((double)ax.A[1][q] + (double)ax.A[1][q + L.P]) * 0.5;
+  double ap = ((double)ax.A[2][q] + (double)ax.A[2][q + 1]) * 0.5;
+  double adv = ar * (Xrp - Xrm) * (0.5 * ihr) + at * (Xtp - Xtm) * (0.5 * ir * iht) +
+               ap * (Xpp - Xpm) * (0.5 * ir * is * ihp);
   double f = ax.fT ? (double)ax.fT[q] : 0.0;
   double rate = S.kappa * (Drr + Dtt + Dpp) - adv + f;
   B[q] = (R)(S.dt * rate - ((double)a[q] - (double)b[q]));
@@ -142,32 +143,32 @@ __global__ void k_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R>
   const R *xi = it.f[F_U1R + o], *xn = n.f[F_U1R + o];
   const R *yi = it.f[F_U1T + o], *yn = n.f[F_U1T + o];
   const R *zi = it.f[F_U1P + o], *zn = n.f[F_U1P + o];
-  double r = S.rf[i], s = S.sc[j];
-  double hr = S.hr, ht = S.ht, hp = S.hp;
+  const double ir = S.irf[i], is = S.isc[j], ir2 = ir * ir;
+  const double ihr = S.ihr, iht = S.iht, ihp = S.ihp;
   const long SI = L.SI, P = L.P;
   double X0 = H(xi, xn, q);
   double Xrp = H(xi, xn, q + SI), Xrm = H(xi, xn, q - SI);
   double Xtp = H(xi, xn, q + P), Xtm = H(xi, xn, q - P);
   double Xpp = H(xi, xn, q + 1), Xpm = H(xi, xn, q - 1);
-  double Drr = (S.rc[i] * S.rc[i] * (Xrp - X0) - S.rc[i - 1] * S.rc[i - 1] * (X0 - Xrm)) / (r * r * hr * hr);
-  double Dtt = (S.sf[j + 1] * (Xtp - X0) - S.sf[j] * (X0 - Xtm)) / (r * r * s * ht * ht);
-  double Dpp = (Xpp - 2.0 * X0 + Xpm) / (r * r * s * s * hp * hp);
-  double extra = -2.0 * X0 / (r * r) +
-                 2.0 / (r * r * r) * (S.rf[i + 1] * S.rf[i + 1] * Xrp - S.rf[i - 1] * S.rf[i - 1] * Xrm) / (2 * hr);
+  double Drr = (S.rc[i] * S.rc[i] * (Xrp - X0) - S.rc[i - 1] * S.rc[i - 1] * (X0 - Xrm)) * (ir2 * ihr * ihr);
+  double Dtt = (S.sf[j + 1] * (Xtp - X0) - S.sf[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
+  double Dpp = (Xpp - 2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
+  double extra = -2.0 * X0 * ir2 +
+                 2.0 * ir2 * ir * (S.rf[i + 1] * S.rf[i + 1] * Xrp - S.rf[i - 1] * S.rf[i - 1] * Xrm) * (0.5 * ihr);
   double ar = (double)ax.A[0][q];
   double at = avg4(ax.A[1], q - SI, q - SI + P, q, q + P);
   double ap = avg4(ax.A[2], q - SI, q - SI + 1, q, q + 1);
   double bt = havg4(yi, yn, q - SI, q - SI + P, q, q + P);
   double bp = havg4(zi, zn, q - SI, q - SI + 1, q, q + 1);
-  double adv = ar * (Xrp - Xrm) / (2 * hr) + at * (Xtp - Xtm) / (2 * r * ht) + ap * (Xpp - Xpm) / (2 * r * s * hp) -
-               (at * bt + ap * bp) / r;
-  double gradP = (pres(it, n, sys, q) - pres(it, n, sys, q - SI)) / hr;
+  double adv = ar * (Xrp - Xrm) * (0.5 * ihr) + at * (Xtp - Xtm) * (0.5 * ir * iht) +
+               ap * (Xpp - Xpm) * (0.5 * ir * is * ihp) - (at * bt + ap * bp) * ir;
+  double gradP = (pres(it, n, sys, q) - pres(it, n, sys, q - SI)) * ihr;
   double Dc = divh(S, xi, xn, yi, yn, zi, zn, i, j, q);
   double Dm = divh(S, xi, xn, yi, yn, zi, zn, i - 1, j, q - SI);
-  double gdiv = (Dc - Dm) / hr;
+  double gdiv = (Dc - Dm) * ihr;
   double buoy = S.PrRa * 0.5 * (H(it.f[F_T], n.f[F_T], q - SI) + H(it.f[F_T], n.f[F_T], q));
   double f = ax.fr ? (double)ax.fr[q] : 0.0;
-  double rate = S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv / (2 * S.chi) + buoy + f;
+  double rate = S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * S.i2chi + buoy + f;
   B[q] = (R)(S.dt * rate - ((double)xi[q] - (double)xn[q]));
 }
 
@@ -181,38 +182,38 @@ __global__ void k_resid_ut(Shell S, int sys, State<R> it, State<R> n, StepAux<R>
   const R *wi = it.f[F_U1R + o], *wn = n.f[F_U1R + o];
   const R *xi = it.f[F_U1T + o], *xn = n.f[F_U1T + o];
   const R *zi = it.f[F_U1P + o], *zn = n.f[F_U1P + o];
-  double r = S.rc[i], s = S.sf[j], c = S.cf[j];
-  double hr = S.hr, ht = S.ht, hp = S.hp;
+  const double ir = S.irc[i], is = S.isf[j], c = S.cf[j], ir2 = ir * ir;
+  const double ihr = S.ihr, iht = S.iht, ihp = S.ihp;
   const long SI = L.SI, P = L.P;
   double X0 = H(xi, xn, q);
   double Xrp = H(xi, xn, q + SI), Xrm = H(xi, xn, q - SI);
   double Xtp = H(xi, xn, q + P), Xtm = H(xi, xn, q - P);
   double Xpp = H(xi, xn, q + 1), Xpm = H(xi, xn, q - 1);
-  double Drr = (S.rf[i + 1] * S.rf[i + 1] * (Xrp - X0) - S.rf[i] * S.rf[i] * (X0 - Xrm)) / (r * r * hr * hr);
-  double Dtt = (S.sc[j] * (Xtp - X0) - S.sc[j - 1] * (X0 - Xtm)) / (r * r * s * ht * ht);
-  double Dpp = (Xpp - 2.0 * X0 + Xpm) / (r * r * s * s * hp * hp);
+  double Drr = (S.rf[i + 1] * S.rf[i + 1] * (Xrp - X0) - S.rf[i] * S.rf[i] * (X0 - Xrm)) * (ir2 * ihr * ihr);
+  double Dtt = (S.sc[j] * (Xtp - X0) - S.sc[j - 1] * (X0 - Xtm)) * (ir2 * is * iht * iht);
+  double Dpp = (Xpp - 2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
   double W_j = 0.5 * (H(wi, wn, q) + H(wi, wn, q + SI));
   double W_jm = 0.5 * (H(wi, wn, q - P) + H(wi, wn, q - P + SI));
-  double dW = (W_j - W_jm) / ht;
-  double qj = (S.rf[i + 1] * S.rf[i + 1] * H(wi, wn, q + SI) - S.rf[i] * S.rf[i] * H(wi, wn, q)) / hr;
-  double qjm = (S.rf[i + 1] * S.rf[i + 1] * H(wi, wn, q + SI - P) - S.rf[i] * S.rf[i] * H(wi, wn, q - P)) / hr;
+  double dW = (W_j - W_jm) * iht;
+  double qj = (S.rf[i + 1] * S.rf[i + 1] * H(wi, wn, q + SI) - S.rf[i] * S.rf[i] * H(wi, wn, q)) * ihr;
+  double qjm = (S.rf[i + 1] * S.rf[i + 1] * H(wi, wn, q + SI - P) - S.rf[i] * S.rf[i] * H(wi, wn, q - P)) * ihr;
   double drr2W = 0.5 * (qj + qjm);
-  double extra = -X0 / (r * r * s * s) +
-                 2.0 * c / (r * r * s * s) * (S.sf[j + 1] * Xtp - S.sf[j - 1] * Xtm) / (2 * ht) +
-                 2.0 / (r * r) * dW + 2.0 * c / (r * r * r * s) * drr2W;
+  double extra = -X0 * ir2 * is * is +
+                 2.0 * c * ir2 * is * is * (S.sf[j + 1] * Xtp - S.sf[j - 1] * Xtm) * (0.5 * iht) +
+                 2.0 * ir2 * dW + 2.0 * c * ir2 * ir * is * drr2W;
   double ar = avg4(ax.A[0], q - P, q - P + SI, q, q + SI);
   double at = (double)ax.A[1][q];
   double ap = avg4(ax.A[2], q - P, q - P + 1, q, q + 1);
   double br = havg4(wi, wn, q - P, q - P + SI, q, q + SI);
   double bp = havg4(zi, zn, q - P, q - P + 1, q, q + 1);
-  double adv = ar * (Xrp - Xrm) / (2 * hr) + at * (Xtp - Xtm) / (2 * r * ht) + ap * (Xpp - Xpm) / (2 * r * s * hp) +
-               (at * br - ap * bp * c / s) / r;
-  double gradP = (pres(it, n, sys, q) - pres(it, n, sys, q - P)) / (r * ht);
+  double adv = ar * (Xrp - Xrm) * (0.5 * ihr) + at * (Xtp - Xtm) * (0.5 * ir * iht) +
+               ap * (Xpp - Xpm) * (0.5 * ir * is * ihp) + (at * br - ap * bp * c * is) * ir;
+  double gradP = (pres(it, n, sys, q) - pres(it, n, sys, q - P)) * (ir * iht);
   double Dc = divh(S, wi, wn, xi, xn, zi, zn, i, j, q);
   double Dm = divh(S, wi, wn, xi, xn, zi, zn, i, j - 1, q - P);
-  double gdiv = (Dc - Dm) / (r * ht);
+  double gdiv = (Dc - Dm) * (ir * iht);
   double f = ax.ft ? (double)ax.ft[q] : 0.0;
-  double rate = S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv / (2 * S.chi) + f;
+  double rate = S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * S.i2chi + f;
   B[q] = (R)(S.dt * rate - ((double)xi[q] - (double)xn[q]));
 }
 
@@ -226,35 +227,35 @@ __global__ void k_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R>
   const R *wi = it.f[F_U1R + o], *wn = n.f[F_U1R + o];
   const R *yi = it.f[F_U1T + o], *yn = n.f[F_U1T + o];
   const R *xi = it.f[F_U1P + o], *xn = n.f[F_U1P + o];
-  double r = S.rc[i], s = S.sc[j], c = S.cc[j];
-  double hr = S.hr, ht = S.ht, hp = S.hp;
+  const double ir = S.irc[i], is = S.isc[j], c = S.cc[j], ir2 = ir * ir;
+  const double ihr = S.ihr, iht = S.iht, ihp = S.ihp;
   const long SI = L.SI, P = L.P;
   double X0 = H(xi, xn, q);
   double Xrp = H(xi, xn, q + SI), Xrm = H(xi, xn, q - SI);
   double Xtp = H(xi, xn, q + P), Xtm = H(xi, xn, q - P);
   double Xpp = H(xi, xn, q + 1), Xpm = H(xi, xn, q - 1);
-  double Drr = (S.rf[i + 1] * S.rf[i + 1] * (Xrp - X0) - S.rf[i] * S.rf[i] * (X0 - Xrm)) / (r * r * hr * hr);
-  double Dtt = (S.sf[j + 1] * (Xtp - X0) - S.sf[j] * (X0 - Xtm)) / (r * r * s * ht * ht);
-  double Dpp = (Xpp - 2.0 * X0 + Xpm) / (r * r * s * s * hp * hp);
+  double Drr = (S.rf[i + 1] * S.rf[i + 1] * (Xrp - X0) - S.rf[i] * S.rf[i] * (X0 - Xrm)) * (ir2 * ihr * ihr);
+  double Dtt = (S.sf[j + 1] * (Xtp - X0) - S.sf[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
+  double Dpp = (Xpp - 2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
   double W_k = 0.5 * (H(wi, wn, q) + H(wi, wn, q + SI));
   double W_km = 0.5 * (H(wi, wn, q - 1) + H(wi, wn, q - 1 + SI));
   double Y_k = 0.5 * (H(yi, yn, q) + H(yi, yn, q + P));
   double Y_km = 0.5 * (H(yi, yn, q - 1) + H(yi, yn, q - 1 + P));
-  double extra = -X0 / (r * r * s * s) + 2.0 / (r * r * s) * (W_k - W_km) / hp +
-                 2.0 * c / (r * r * s * s) * (Y_k - Y_km) / hp;
+  double extra = -X0 * ir2 * is * is + 2.0 * ir2 * is * (W_k - W_km) * ihp +
+                 2.0 * c * ir2 * is * is * (Y_k - Y_km) * ihp;
   double ar = avg4(ax.A[0], q - 1, q - 1 + SI, q, q + SI);
   double at = avg4(ax.A[1], q - 1, q - 1 + P, q, q + P);
   double ap = (double)ax.A[2][q];
   double br = havg4(wi, wn, q - 1, q - 1 + SI, q, q + SI);
   double bt = havg4(yi, yn, q - 1, q - 1 + P, q, q + P);
-  double adv = ar * (Xrp - Xrm) / (2 * hr) + at * (Xtp - Xtm) / (2 * r * ht) + ap * (Xpp - Xpm) / (2 * r * s * hp) +
-               (ap * br + ap * bt * c / s) / r;
-  double gradP = (pres(it, n, sys, q) - pres(it, n, sys, q - 1)) / (r * s * hp);
+  double adv = ar * (Xrp - Xrm) * (0.5 * ihr) + at * (Xtp - Xtm) * (0.5 * ir * iht) +
+               ap * (Xpp - Xpm) * (0.5 * ir * is * ihp) + (ap * br + ap * bt * c * is) * ir;
+  double gradP = (pres(it, n, sys, q) - pres(it, n, sys, q - 1)) * (ir * is * ihp);
   double Dc = divh(S, wi, wn, yi, yn, xi, xn, i, j, q);
   double Dm = divh(S, wi, wn, yi, yn, xi, xn, i, j, q - 1);
-  double gdiv = (Dc - Dm) / (r * s * hp);
+  double gdiv = (Dc - Dm) * (ir * is * ihp);
   double f = ax.fp ? (double)ax.fp[q] : 0.0;
-  double rate = S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv / (2 * S.chi) + f;
+  double rate = S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * S.i2chi + f;
   B[q] = (R)(S.dt * rate - ((double)xi[q] - (double)xn[q]));
 }
 
@@ -273,10 +274,10 @@ __global__ void k_pressure(Shell S, int sys, State<R> it, State<R> n, double *no
     double pnew;
     R *dst;
     if (sys == 1) {
-      pnew = (double)n.f[F_P1][q] - D / S.chi;
+      pnew = (double)n.f[F_P1][q] - D * (2.0 * S.i2chi);
       dst = it.f[F_P1];
     } else {
-      pnew = (double)n.f[F_P2][q] + ((double)it.f[F_P1][q] - (double)n.f[F_P1][q]) - D / S.chi;
+      pnew = (double)n.f[F_P2][q] + ((double)it.f[F_P1][q] - (double)n.f[F_P1][q]) - D * (2.0 * S.i2chi);
       dst = it.f[F_P2];
     }
     double c = pnew - (double)dst[q];

@@ -23,7 +23,7 @@ constexpr int TPB = 128;
 
 template <typename R>
 __device__ __forceinline__ double avg4(const R *a, long q1, long q2, long q3, long q4) {
-  return (((double)a[q1] + (double)a[q2]) + (double)a[q3] + (double)a[q4]) / 4.0;
+  return (((double)a[q1] + (double)a[q2]) + (double)a[q3] + (double)a[q4]) * 0.25;
 }
 
 // Advecting velocity (a_r, a_th, a_ph) at a point of location `loc`: own
@@ -35,9 +35,9 @@ __device__ __forceinline__ void advecting(const Shell &S, const StepAux<R> &ax, 
   const R *A0 = ax.A[0], *A1 = ax.A[1], *A2 = ax.A[2];
   switch (loc) {
     case LC:
-      ar = ((double)A0[q] + (double)A0[q + SI]) / 2.0;
-      at = ((double)A1[q] + (double)A1[q + P]) / 2.0;
-      ap = ((double)A2[q] + (double)A2[q + 1]) / 2.0;
+      ar = ((double)A0[q] + (double)A0[q + SI]) * 0.5;
+      at = ((double)A1[q] + (double)A1[q + P]) * 0.5;
+      ap = ((double)A2[q] + (double)A2[q + 1]) * 0.5;
       break;
     case LR:
       ar = (double)A0[q];
@@ -57,72 +57,71 @@ __device__ __forceinline__ void advecting(const Shell &S, const StepAux<R> &ax, 
   }
 }
 
-// Coefficients (lo, di, up) of (I - dt/2 Ahat_dir) at point (i, j, k) of `loc`.
+// Coefficients (lo, di, up) of (I - dt/2 Ahat_dir) at point (i, j, k) of `loc`
+// (divisions replaced by FP64 reciprocal metric tables).
 template <typename R>
 __device__ __forceinline__ void coef(const Shell &S, const StepAux<R> &ax, int loc, int dir, int i, int j, long q,
                                      double &lo, double &di, double &up) {
-  const double hr = S.hr, ht = S.ht, hp = S.hp, R1 = S.R1;
+  const double ihr = S.ihr, iht = S.iht, ihp = S.ihp;
   const double nu = (loc == LC) ? S.kappa : S.nu;
   double ar, at, ap;
   advecting(S, ax, loc, q, ar, at, ap);
-  const double r = (loc == LR) ? S.rf[i] : S.rc[i];
-  const double s = (loc == LT) ? S.sf[j] : S.sc[j];
+  const double ir = (loc == LR) ? S.irf[i] : S.irc[i];
+  const double is = (loc == LT) ? S.isf[j] : S.isc[j];
+  const double ir2 = ir * ir;
   double cm, c0, cp;
   if (dir == DR) {
     double cp_d, cm_d;
     if (loc == LR) {
-      cp_d = S.rc[i] * S.rc[i] / (r * r * hr * hr);
-      cm_d = S.rc[i - 1] * S.rc[i - 1] / (r * r * hr * hr);
+      cp_d = S.rc[i] * S.rc[i] * (ir2 * ihr * ihr);
+      cm_d = S.rc[i - 1] * S.rc[i - 1] * (ir2 * ihr * ihr);
     } else {
-      cp_d = S.rf[i + 1] * S.rf[i + 1] / (r * r * hr * hr);
-      cm_d = S.rf[i] * S.rf[i] / (r * r * hr * hr);
+      cp_d = S.rf[i + 1] * S.rf[i + 1] * (ir2 * ihr * ihr);
+      cm_d = S.rf[i] * S.rf[i] * (ir2 * ihr * ihr);
     }
-    cm = nu * cm_d + ar / (2 * hr);
+    cm = nu * cm_d + ar * (0.5 * ihr);
     c0 = -nu * (cp_d + cm_d);
-    cp = nu * cp_d - ar / (2 * hr);
+    cp = nu * cp_d - ar * (0.5 * ihr);
     if (loc == LR) {
-      cm = cm - nu * 2.0 * S.rf[i - 1] * S.rf[i - 1] / (r * r * r * 2 * hr);
-      cp = cp + nu * 2.0 * S.rf[i + 1] * S.rf[i + 1] / (r * r * r * 2 * hr);
-      c0 = c0 - nu * 2.0 / (r * r);
-      const double k = 1.0 / (2 * S.chi);
-      cm = cm + k * S.rf[i - 1] * S.rf[i - 1] / (S.rc[i - 1] * S.rc[i - 1] * hr * hr);
-      c0 = c0 - k * (S.rf[i] * S.rf[i] / (S.rc[i] * S.rc[i] * hr * hr) +
-                     S.rf[i] * S.rf[i] / (S.rc[i - 1] * S.rc[i - 1] * hr * hr));
-      cp = cp + k * S.rf[i + 1] * S.rf[i + 1] / (S.rc[i] * S.rc[i] * hr * hr);
+      cm = cm - nu * S.rf[i - 1] * S.rf[i - 1] * (ir2 * ir * ihr);
+      cp = cp + nu * S.rf[i + 1] * S.rf[i + 1] * (ir2 * ir * ihr);
+      c0 = c0 - nu * 2.0 * ir2;
+      const double k = S.i2chi, irm = S.irc[i - 1], irc = S.irc[i];
+      cm = cm + k * S.rf[i - 1] * S.rf[i - 1] * (irm * irm * ihr * ihr);
+      c0 = c0 - k * (S.rf[i] * S.rf[i] * (irc * irc * ihr * ihr) + S.rf[i] * S.rf[i] * (irm * irm * ihr * ihr));
+      cp = cp + k * S.rf[i + 1] * S.rf[i + 1] * (irc * irc * ihr * ihr);
     }
   } else if (dir == DT) {
     double cp_d, cm_d;
     if (loc == LT) {
-      cp_d = S.sc[j] / (R1 * R1 * s * ht * ht);
-      cm_d = S.sc[j - 1] / (R1 * R1 * s * ht * ht);
+      cp_d = S.sc[j] * (S.iR1sq * is * iht * iht);
+      cm_d = S.sc[j - 1] * (S.iR1sq * is * iht * iht);
     } else {
-      cp_d = S.sf[j + 1] / (R1 * R1 * s * ht * ht);
-      cm_d = S.sf[j] / (R1 * R1 * s * ht * ht);
+      cp_d = S.sf[j + 1] * (S.iR1sq * is * iht * iht);
+      cm_d = S.sf[j] * (S.iR1sq * is * iht * iht);
     }
-    cm = nu * cm_d + at / (2 * r * ht);
+    cm = nu * cm_d + at * (0.5 * ir * iht);
     c0 = -nu * (cp_d + cm_d);
-    cp = nu * cp_d - at / (2 * r * ht);
+    cp = nu * cp_d - at * (0.5 * ir * iht);
     if (loc == LT) {
-      const double c = S.cf[j];
-      const double qq = 2.0 * c / (r * r * s * s) / (2 * ht);
+      const double c = S.cf[j], s = S.sf[j];
+      const double qq = c * ir2 * is * is * iht;
       cm = cm - nu * qq * S.sf[j - 1];
       cp = cp + nu * qq * S.sf[j + 1];
-      c0 = c0 - nu / (r * r * s * s);
-      const double k = 1.0 / (2 * S.chi);
-      cp = cp + k * S.sf[j + 1] / (r * r * S.sc[j] * ht * ht);
-      c0 = c0 - k * (s / (r * r * S.sc[j] * ht * ht) + s / (r * r * S.sc[j - 1] * ht * ht));
-      cm = cm + k * S.sf[j - 1] / (r * r * S.sc[j - 1] * ht * ht);
+      c0 = c0 - nu * ir2 * is * is;
+      const double k = S.i2chi, isc0 = S.isc[j], iscm = S.isc[j - 1];
+      cp = cp + k * S.sf[j + 1] * (ir2 * isc0 * iht * iht);
+      c0 = c0 - k * (s * (ir2 * isc0 * iht * iht) + s * (ir2 * iscm * iht * iht));
+      cm = cm + k * S.sf[j - 1] * (ir2 * iscm * iht * iht);
     }
   } else {
-    const double s1 = S.sin_theta1;
-    const double cpm = 1.0 / (R1 * R1 * s1 * s1 * hp * hp);
-    cm = nu * cpm + ap / (2 * r * s * hp);
+    const double cpm = S.cphi;
+    cm = nu * cpm + ap * (0.5 * ir * is * ihp);
     c0 = -2.0 * nu * cpm;
-    cp = nu * cpm - ap / (2 * r * s * hp);
+    cp = nu * cpm - ap * (0.5 * ir * is * ihp);
     if (loc == LP) {
-      c0 = c0 - nu / (r * r * s * s);
-      const double k = 1.0 / (2 * S.chi);
-      const double qq = k / (r * r * s * s * hp * hp);
+      c0 = c0 - nu * ir2 * is * is;
+      const double qq = S.i2chi * ir2 * is * is * ihp * ihp;
       cm = cm + qq;
       c0 = c0 - 2.0 * qq;
       cp = cp + qq;
@@ -133,59 +132,68 @@ __device__ __forceinline__ void coef(const Shell &S, const StepAux<R> &ax, int l
   up = -0.5 * S.dt * cp;
 }
 
+// Line of a (loc, dir) sweep: thread (lane, row) -> patch p, first point
+// (i, j, k), row range [m0, m1) and element stride along the line.  Lanes run
+// along phi for r- and theta-sweeps (coalesced) and along theta for
+// phi-sweeps.
+struct Line {
+  int p, i, j, k, m0, m1;
+  long step;
+  bool valid;
+};
+
+__device__ __forceinline__ Line decode_line(const Layout &L, int loc, int dir, int lane, int row) {
+  const int i0 = (loc == LR) ? 1 : 0, i1 = L.Nr;
+  const int j0 = (loc == LT) ? 1 : 0, j1 = L.Nt;
+  const int k0 = (loc == LP) ? 1 : 0, k1 = L.Np;
+  Line ln;
+  if (dir == DR) {
+    int nj = j1 - j0;
+    ln.k = k0 + lane;
+    ln.j = j0 + row % nj;
+    ln.p = row / nj;
+    ln.i = i0;
+    ln.valid = ln.k < k1;
+    ln.m0 = i0;
+    ln.m1 = i1;
+    ln.step = L.SI;
+  } else if (dir == DT) {
+    int ni = i1 - i0;
+    ln.k = k0 + lane;
+    ln.i = i0 + row % ni;
+    ln.p = row / ni;
+    ln.j = j0;
+    ln.valid = ln.k < k1;
+    ln.m0 = j0;
+    ln.m1 = j1;
+    ln.step = L.P;
+  } else {
+    int ni = i1 - i0;
+    ln.j = j0 + lane;
+    ln.i = i0 + row % ni;
+    ln.p = row / ni;
+    ln.k = k0;
+    ln.valid = ln.j < j1;
+    ln.m0 = k0;
+    ln.m1 = k1;
+    ln.step = 1;
+  }
+  return ln;
+}
+
 template <typename R>
 __global__ void k_sweep(Shell S, int loc, int dir, int final, StepAux<R> ax, R *B, R *Cs, R *dst, double *norm,
                         int slot, int patch_mask) {
   const Layout &L = S.L;
-  // unknown ranges of loc
-  const int i0 = (loc == LR) ? 1 : 0, i1 = L.Nr;
-  const int j0 = (loc == LT) ? 1 : 0, j1 = L.Nt;
-  const int k0 = (loc == LP) ? 1 : 0, k1 = L.Np;
-  // line decode: x runs along the fastest index that is not the sweep direction
-  int p, i = 0, j = 0, k = 0;
-  int m0, m1;
-  long step;
-  int lane = blockIdx.x * blockDim.x + threadIdx.x;
-  int row = blockIdx.y;
-  bool valid;
-  if (dir == DR) {
-    k = k0 + lane;
-    int nj = j1 - j0;
-    j = j0 + row % nj;
-    p = row / nj;
-    valid = k < k1;
-    m0 = i0;
-    m1 = i1;
-    step = L.SI;
-    i = i0;
-  } else if (dir == DT) {
-    k = k0 + lane;
-    int ni = i1 - i0;
-    i = i0 + row % ni;
-    p = row / ni;
-    valid = k < k1;
-    m0 = j0;
-    m1 = j1;
-    step = L.P;
-    j = j0;
-  } else {
-    j = j0 + lane;
-    int ni = i1 - i0;
-    i = i0 + row % ni;
-    p = row / ni;
-    valid = j < j1;
-    m0 = k0;
-    m1 = k1;
-    step = 1;
-    k = k0;
-  }
+  const Line ln = decode_line(L, loc, dir, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
+  const int m0 = ln.m0, m1 = ln.m1, i = ln.i, j = ln.j;
+  const long step = ln.step;
   double contrib = 0.0;
-  if (valid && ((patch_mask >> p) & 1)) {
+  if (ln.valid && ((patch_mask >> ln.p) & 1)) {
     const bool reflect = (dir == DR) && (loc != LR);
-    const long qa = lidx(L, p, i, j, k);
     // forward elimination
     double cprev = 0.0, dprev = 0.0;
-    long q = qa;
+    long q = lidx(L, ln.p, ln.i, ln.j, ln.k);
     for (int m = m0; m < m1; ++m, q += step) {
       int ii = (dir == DR) ? m : i, jj = (dir == DT) ? m : j;
       double lo, di, up;
@@ -230,25 +238,116 @@ __global__ void k_sweep(Shell S, int loc, int dir, int final, StepAux<R> ax, R *
   }
 }
 
+// Per-step LU factorisation of one factor (I - dt/2 Ahat_dir) of `loc` on
+// every line: the line matrices depend only on the advecting velocity, fixed
+// for the whole step, so both AC systems and every Schwarz iteration reuse
+// them.  Row m stores the sub-diagonal lo_m, the reciprocal pivot
+// 1/(di_m - lo_m c'_{m-1}) and c'_m = up_m / pivot_m.
+template <typename R>
+__global__ void k_factorize(Shell S, int loc, int dir, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask) {
+  const Layout &L = S.L;
+  const Line ln = decode_line(L, loc, dir, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
+  if (!ln.valid || !((patch_mask >> ln.p) & 1)) return;
+  const bool reflect = (dir == DR) && (loc != LR);
+  double cprev = 0.0;
+  long q = lidx(L, ln.p, ln.i, ln.j, ln.k);
+  for (int m = ln.m0; m < ln.m1; ++m, q += ln.step) {
+    int ii = (dir == DR) ? m : ln.i, jj = (dir == DT) ? m : ln.j;
+    double lo, di, up;
+    coef(S, ax, loc, dir, ii, jj, q, lo, di, up);
+    if (m == ln.m0) {
+      if (reflect) di -= lo;
+      lo = 0.0;
+    }
+    if (m == ln.m1 - 1) {
+      if (reflect) di -= up;
+      up = 0.0;
+    }
+    double inv = 1.0 / (di - lo * cprev);
+    double c = up * inv;
+    Lo[q] = (R)lo;
+    Iv[q] = (R)inv;
+    Cp[q] = (R)c;
+    cprev = c;
+  }
+}
+
+// Thomas solve with a stored factorisation: forward d'_m = (b_m - lo_m d'_{m-1})
+// / pivot_m, back x_m = d'_m - c'_m x_{m+1}.  Non-final factors leave x in B;
+// the final factor of an unknown adds x to the iterate and accumulates the
+// FP64 midpoint-rule norm of the increment (Sec. 5.1).
+template <typename R>
+__global__ void k_solve(Shell S, int loc, int dir, int final, const R *__restrict__ Lo, const R *__restrict__ Iv,
+                        const R *__restrict__ Cp, R *B, R *dst, double *norm, int slot, int patch_mask) {
+  const Layout &L = S.L;
+  const Line ln = decode_line(L, loc, dir, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
+  double contrib = 0.0;
+  if (ln.valid && ((patch_mask >> ln.p) & 1)) {
+    const long step = ln.step;
+    long q = lidx(L, ln.p, ln.i, ln.j, ln.k);
+    double d = 0.0;
+    for (int m = ln.m0; m < ln.m1; ++m, q += step) {
+      d = ((double)B[q] - (double)Lo[q] * d) * (double)Iv[q];
+      B[q] = (R)d;
+    }
+    q -= step;
+    double x = d;
+    for (int m = ln.m1 - 1;; --m) {
+      if (final) {
+        dst[q] = (R)((double)dst[q] + x);
+        int ii = (dir == DR) ? m : ln.i, jj = (dir == DT) ? m : ln.j;
+        double r = (loc == LR) ? S.rf[ii] : S.rc[ii];
+        double s = (loc == LT) ? S.sf[jj] : S.sc[jj];
+        contrib += r * r * s * S.hr * S.ht * S.hp * x * x;
+      } else {
+        B[q] = (R)x;
+      }
+      if (m == ln.m0) break;
+      q -= step;
+      x = (double)B[q] - (double)Cp[q] * x;
+    }
+  }
+  if (final) {
+    for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, off);
+    if ((threadIdx.x & 31) == 0 && contrib != 0.0) atomicAdd(&norm[slot], contrib);
+  }
+}
+
+dim3 line_grid(const Layout &L, int loc, int dir) {
+  int ni = L.Nr - (loc == LR ? 1 : 0);
+  int nj = L.Nt - (loc == LT ? 1 : 0);
+  int nk = L.Np - (loc == LP ? 1 : 0);
+  if (dir == DR) return dim3((nk + TPB - 1) / TPB, 2 * nj);
+  if (dir == DT) return dim3((nk + TPB - 1) / TPB, 2 * ni);
+  return dim3((nj + TPB - 1) / TPB, 2 * ni);
+}
+
 }  // namespace
 
 template <typename R>
 void Launch<R>::sweep(const Shell &S, int loc, int dir, bool final, StepAux<R> ax, R *B, R *Cs, R *dst,
                       double *norm, int slot, int patch_mask, cudaStream_t st) {
-  const Layout &L = S.L;
-  int ni = L.Nr - (loc == LR ? 1 : 0);
-  int nj = L.Nt - (loc == LT ? 1 : 0);
-  int nk = L.Np - (loc == LP ? 1 : 0);
-  dim3 grid;
-  if (dir == DR)
-    grid = dim3((nk + TPB - 1) / TPB, 2 * nj);
-  else if (dir == DT)
-    grid = dim3((nk + TPB - 1) / TPB, 2 * ni);
-  else
-    grid = dim3((nj + TPB - 1) / TPB, 2 * ni);
-  k_sweep<R><<<grid, TPB, 0, st>>>(S, loc, dir, final ? 1 : 0, ax, B, Cs, dst, norm, slot, patch_mask);
+  k_sweep<R><<<line_grid(S.L, loc, dir), TPB, 0, st>>>(S, loc, dir, final ? 1 : 0, ax, B, Cs, dst, norm, slot,
+                                                        patch_mask);
 }
 
+template <typename R>
+void Launch<R>::factorize(const Shell &S, int loc, int dir, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask,
+                          cudaStream_t st) {
+  k_factorize<R><<<line_grid(S.L, loc, dir), TPB, 0, st>>>(S, loc, dir, ax, Lo, Iv, Cp, patch_mask);
+}
+
+template <typename R>
+void Launch<R>::solve(const Shell &S, int loc, int dir, bool final, const R *Lo, const R *Iv, const R *Cp, R *B,
+                      R *dst, double *norm, int slot, int patch_mask, cudaStream_t st) {
+  k_solve<R><<<line_grid(S.L, loc, dir), TPB, 0, st>>>(S, loc, dir, final ? 1 : 0, Lo, Iv, Cp, B, dst, norm, slot,
+                                                        patch_mask);
+}
+
+template void Launch<double>::factorize(const Shell &, int, int, StepAux<double>, double *, double *, double *,
+                                        int, cudaStream_t);
+template void Launch<double>::solve(const Shell &, int, int, bool, const double *, const double *, const double *,
+                                    double *, double *, double *, int, int, cudaStream_t);
 template void Launch<double>::sweep(const Shell &, int, int, bool, StepAux<double>, double *, double *, double *,
                                     double *, int, int, cudaStream_t);
 
@@ -265,7 +364,7 @@ namespace {
 constexpr long kStaticFieldElems = 1L << 18;  // padded elements of one field (both patches)
 constexpr int kStaticMaxN = 256;              // cells along any direction
 constexpr int kStaticMetricLen = kStaticMaxN + 8;
-constexpr long kStaticElems = 5 * kStaticFieldElems + 6L * kStaticMetricLen;
+constexpr long kStaticElems = 5 * kStaticFieldElems + (long)kMetricTables * kStaticMetricLen;
 constexpr int kMaxDevices = 64;
 
 // [A_r | A_th | A_ph | B (rhs, then solution) | Cs (c')] padded fields, then the metric
@@ -376,15 +475,21 @@ extern "C" int ys_factor_solve_static(const ys_params *prm, int loc, const doubl
 
   // metric tables r_c, r_f, sin/cos at theta centres and faces (pad 2), on the stack
   const int pad = 2;
-  double mh[6 * kStaticMetricLen];
+  double mh[kMetricTables * kStaticMetricLen];
   for (int t = 0; t < kStaticMetricLen; ++t) {
     int i = t - pad;
-    mh[0 * kStaticMetricLen + t] = prm->R1 + (i + 0.5) * hr;
-    mh[1 * kStaticMetricLen + t] = prm->R1 + i * hr;
-    mh[2 * kStaticMetricLen + t] = std::sin(th0 + (i + 0.5) * ht);
-    mh[3 * kStaticMetricLen + t] = std::sin(th0 + i * ht);
+    double rc = prm->R1 + (i + 0.5) * hr, rf = prm->R1 + i * hr;
+    double sc = std::sin(th0 + (i + 0.5) * ht), sf = std::sin(th0 + i * ht);
+    mh[0 * kStaticMetricLen + t] = rc;
+    mh[1 * kStaticMetricLen + t] = rf;
+    mh[2 * kStaticMetricLen + t] = sc;
+    mh[3 * kStaticMetricLen + t] = sf;
     mh[4 * kStaticMetricLen + t] = std::cos(th0 + (i + 0.5) * ht);
     mh[5 * kStaticMetricLen + t] = std::cos(th0 + i * ht);
+    mh[6 * kStaticMetricLen + t] = rc != 0.0 ? 1.0 / rc : 0.0;
+    mh[7 * kStaticMetricLen + t] = rf != 0.0 ? 1.0 / rf : 0.0;
+    mh[8 * kStaticMetricLen + t] = sc != 0.0 ? 1.0 / sc : 0.0;
+    mh[9 * kStaticMetricLen + t] = sf != 0.0 ? 1.0 / sf : 0.0;
   }
   // every call shares the scratch: clear the working fields left by the last call
   if (cudaMemsetAsync(base, 0, 4 * kStaticFieldElems * sizeof(double), st) != cudaSuccess) return YS_ECUDA;
@@ -410,6 +515,16 @@ extern "C" int ys_factor_solve_static(const ys_params *prm, int loc, const doubl
   S.sf = met + 3 * kStaticMetricLen + pad;
   S.cc = met + 4 * kStaticMetricLen + pad;
   S.cf = met + 5 * kStaticMetricLen + pad;
+  S.irc = met + 6 * kStaticMetricLen + pad;
+  S.irf = met + 7 * kStaticMetricLen + pad;
+  S.isc = met + 8 * kStaticMetricLen + pad;
+  S.isf = met + 9 * kStaticMetricLen + pad;
+  S.ihr = 1.0 / hr;
+  S.iht = 1.0 / ht;
+  S.ihp = 1.0 / hp;
+  S.i2chi = 1.0 / (2.0 * prm->chi);
+  S.iR1sq = 1.0 / (prm->R1 * prm->R1);
+  S.cphi = 1.0 / (prm->R1 * prm->R1 * S.sin_theta1 * S.sin_theta1 * hp * hp);
   StepAux<double> ax{};
   for (int a = 0; a < 3; ++a) ax.A[a] = Af[a];
   // factor order, first solved first: T r,theta,phi; u_r theta,phi,r;

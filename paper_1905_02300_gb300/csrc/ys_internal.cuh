@@ -38,9 +38,18 @@ struct Shell {
   const double *rc, *rf;    // r at centres / faces
   const double *sc, *sf;    // sin(theta) at centres / faces
   const double *cc, *cf;    // cos(theta) at centres / faces
+  const double *irc, *irf;  // 1/r at centres / faces
+  const double *isc, *isf;  // 1/sin(theta) at centres / faces
+  double ihr, iht, ihp;     // 1/h_r, 1/h_theta, 1/h_phi
+  double i2chi;             // 1/(2 chi)
+  double iR1sq;             // 1/R1^2 (modified theta operator)
+  double cphi;              // 1/(R1^2 sin^2(theta_1) h_phi^2) (modified phi operator)
   double T_in, T_out;       // wall temperatures
   int step7;
 };
+
+// Number of FP64 metric tables (rc, rf, sc, sf, cc, cf, irc, irf, isc, isf).
+constexpr int kMetricTables = 10;
 
 // Exchange table entry: one target point in the (theta, phi) plane of a patch,
 // with one or two bilinear donor stencils on the other patch and, for
