@@ -168,6 +168,7 @@ def main():
     ap.add_argument("--ref-n", type=int, default=48)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -186,7 +187,8 @@ def main():
 
     kw, K = workload(args.n)
     f0, fm, modes = inputs(kw)
-    s = ys.Solver(**kw)
+    mixed = args.precision == "mixed"
+    s = ys.Solver(**kw, precision=ys.YS_MIXED if mixed else ys.YS_FP64)
     stream = torch.cuda.Stream()
     s.set_stream(stream.cuda_stream)
     s.set_fields_dict(0, f0)
@@ -256,12 +258,13 @@ def main():
     for k, (t_ms, n_l) in prof.items():
         key = "solve" if k.startswith("sweep_") else k
         w = WORDS_PER_CELL.get(k)
-        b = (w * 8 * cells * n_l) if w is not None else 0.0
+        wb = 8.0 if not mixed else (5.6 if k == "pressure" else 4.0)
+        b = (w * wb * cells * n_l) if w is not None else 0.0
         m = merged.setdefault(key, [0.0, 0, 0.0, 0.0])
         m[0] += t_ms
         m[1] += n_l
         m[2] += b
-        m[3] += FLOPS_PER_CELL.get(k, 0.0) * cells * n_l
+        m[3] += (0.0 if mixed else FLOPS_PER_CELL.get(k, 0.0)) * cells * n_l
     top = max((k for k in merged if merged[k][1]), key=lambda k: merged[k][0])
     t_ms, n_l, tot_bytes, tot_flops = merged[top]
     gbs = tot_bytes / (t_ms * 1e-3) / 1e9
@@ -286,9 +289,11 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
+                "data": "synthetic",
                 "config": {"workload": f"yin-yang shell {args.n}x{args.n}x{3*args.n} MAC cells per patch, "
-                                       f"R1=0.5 R2=1 Pr=1 Ra=1e3 dt=5e-4, K={K} Schwarz iterations, FP64, "
+                                       f"R1=0.5 R2=1 Pr=1 Ra=1e3 dt=5e-4, K={K} Schwarz iterations, "
+                                       f"{'mixed FP32/FP64' if mixed else 'FP64'}, "
                                        f"manufactured-solution forcing",
                            "cells_per_shell": cells, "l2": "inputs larger than L2 (state ~%.1f GB)"
                            % (s.device_bytes() / 1e9), "parallelism": f"replicas x{world}"},

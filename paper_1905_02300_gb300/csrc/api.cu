@@ -1,13 +1,23 @@
 // C ABI of the solver: context lifetime, field I/O and the AC time step
 // (Sec. 3.3 artificial compressibility with bootstrapping, Sec. 4 Schwarz
 // iteration with splitting-error reduction, Eq. er).
+//
+// Two storage forms share one code path, templated on the bulk type R:
+//   YS_FP64  : every field FP64;
+//   YS_MIXED : T, u1, u2 FP32 (stencils and sweeps in FP32), pressures FP64,
+//              line coefficients factored in FP64, norms FP64.  The mixed form
+//              stores the deviations T - T_c and p - p_c from the discrete
+//              conductive profile T_c (walls T_inner, T_outer) and its discrete
+//              hydrostatic pressure p_c, so that FP32 only carries the
+//              perturbation; T_c's discrete Laplacian and radial derivative
+//              enter the temperature rate as FP64 tables.  This is an exact
+//              rewrite of the same discrete equations.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
-#include <string>
 #include <vector>
 
 #include "../../include/ys.h"
@@ -32,6 +42,17 @@ struct ProfRec {
   cudaEvent_t a, b;
 };
 
+// Typed device state of one shell.
+template <typename R>
+struct Fields {
+  State<R> lev[3];           // level n, level n-1, iterate
+  R *A[3];                   // advecting velocity
+  R *fcomb[4];               // forcing at t_n + dt/2
+  R *B, *Cs;                 // work field, Thomas c' (unused by the stored-LU path)
+  R *fac[4][3][3];           // per-step LU factors: fac[loc][dir] = {lo, 1/pivot, c'}
+  R *modes[kMaxModes][4];    // forcing modes
+};
+
 }  // namespace
 
 struct ys_ctx {
@@ -40,40 +61,43 @@ struct ys_ctx {
   Layout L;
   Shell S;
   cudaStream_t own_stream = nullptr, stream = nullptr;
-  // device memory
   void *dmem = nullptr;
   size_t dbytes = 0;
-  double *fields = nullptr;   // 36 fields
-  State<double> lev[3];       // level n, level n-1, iterate
-  double *A[3];
-  double *fcomb[4];
-  double *B, *Cs;
-  // per-step LU factors of the 12 (unknown, direction) line operators:
-  // fac[loc][dir][0..2] = lo, 1/pivot, c'
-  double *fac[4][3][3];
-  double *metric = nullptr;
+  void *modes_mem[kMaxModes] = {};
+  Fields<double> *f64 = nullptr;
+  Fields<float> *f32 = nullptr;
   XEntry *xdev = nullptr;
   XTables X;
   double *norm = nullptr;     // YS_NFIELDS accumulators
   double *stage = nullptr;    // host-layout staging (device)
-  size_t stage_elems = 0;
-  double *modes[kMaxModes][4] = {};
+  double *T_bg = nullptr;     // deviation backgrounds per radial index (mixed form), else null
+  double *p_bg = nullptr;
   int mode_fn[kMaxModes] = {};
+  int mode_set[kMaxModes] = {};
   int nmodes_set = 0;
-  // host state
   double t = 0.0;
   long steps_done = 0;
   int level1_set = 0;
   double norms_host[YS_NFIELDS] = {};
   int iters_last = 0;
   long launches = 0;
-  // profiling
   int prof_on = 0;
   std::vector<ProfRec> prof;
   size_t prof_used = 0;
 };
 
 namespace {
+
+template <typename R>
+Fields<R> &F(ys_ctx *c);
+template <>
+Fields<double> &F<double>(ys_ctx *c) {
+  return *c->f64;
+}
+template <>
+Fields<float> &F<float>(ys_ctx *c) {
+  return *c->f32;
+}
 
 inline int cuda_ok(cudaError_t e) { return e == cudaSuccess ? YS_OK : YS_ECUDA; }
 
@@ -119,18 +143,37 @@ size_t user_elems(const Layout &L, int loc) {
   return 2ul * (L.Nr + (loc == LR)) * (L.Nt + (loc == LT)) * (L.Np + (loc == LP));
 }
 
-int copy_in(ys_ctx *c, int loc, const double *src, double *dst, bool device_src) {
+template <typename R>
+int copy_in(ys_ctx *c, int loc, const double *src, R *dst, const double *bg, bool device_src) {
   size_t n = user_elems(c->L, loc);
   cudaError_t e = cudaMemcpyAsync(c->stage, src, n * sizeof(double),
                                   device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return YS_ECUDA;
-  LAUNCH(c, K_PACK, 1, Launch<double>::unpack(c->L, loc, c->stage, dst, c->stream));
+  LAUNCH(c, K_PACK, 1, Launch<R>::unpack(c->L, loc, c->stage, dst, bg, c->stream));
   return YS_OK;
 }
 
-int copy_out(ys_ctx *c, int loc, const double *src, double *dst) {
+int copy_in_p(ys_ctx *c, const double *src, double *dst, bool device_src) {
+  size_t n = user_elems(c->L, LC);
+  cudaError_t e = cudaMemcpyAsync(c->stage, src, n * sizeof(double),
+                                  device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return YS_ECUDA;
+  LAUNCH(c, K_PACK, 1, unpack_p(c->L, c->stage, dst, c->p_bg, c->stream));
+  return YS_OK;
+}
+
+template <typename R>
+int copy_out(ys_ctx *c, int loc, const R *src, double *dst, const double *bg) {
   size_t n = user_elems(c->L, loc);
-  LAUNCH(c, K_PACK, 1, Launch<double>::pack(c->L, loc, src, c->stage, c->stream));
+  LAUNCH(c, K_PACK, 1, Launch<R>::pack(c->L, loc, src, c->stage, bg, c->stream));
+  cudaError_t e = cudaMemcpyAsync(dst, c->stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return YS_ECUDA;
+  return cuda_ok(cudaStreamSynchronize(c->stream));
+}
+
+int copy_out_p(ys_ctx *c, const double *src, double *dst) {
+  size_t n = user_elems(c->L, LC);
+  LAUNCH(c, K_PACK, 1, pack_p(c->L, src, c->stage, c->p_bg, c->stream));
   cudaError_t e = cudaMemcpyAsync(dst, c->stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return YS_ECUDA;
   return cuda_ok(cudaStreamSynchronize(c->stream));
@@ -138,10 +181,11 @@ int copy_out(ys_ctx *c, int loc, const double *src, double *dst) {
 
 // exchange + walls (+ pressure ring) of a whole state: boundary values as
 // functions of the interior
-void refresh(ys_ctx *c, State<double> s, int mask) {
-  LAUNCH(c, K_EXCH, 4, Launch<double>::exchange(c->S, c->X, s, mask, c->stream));
-  LAUNCH(c, K_WALLS, 1, Launch<double>::walls(c->S, s, mask, c->stream));
-  if (c->prm.step7) LAUNCH(c, K_RING, 1, Launch<double>::ring(c->S, c->X, s, mask, c->stream));
+template <typename R>
+void refresh(ys_ctx *c, State<R> s, int mask) {
+  LAUNCH(c, K_EXCH, 4, Launch<R>::exchange(c->S, c->X, s, mask, c->stream));
+  LAUNCH(c, K_WALLS, 1, Launch<R>::walls(c->S, s, mask, c->stream));
+  if (c->prm.step7) LAUNCH(c, K_RING, 1, Launch<R>::ring(c->S, c->X, s, mask, c->stream));
 }
 
 const int kOrder[4][3] = {
@@ -152,39 +196,45 @@ const int kOrder[4][3] = {
 };
 const int kSweepClass[3] = {K_SWEEP_R, K_SWEEP_T, K_SWEEP_P};
 
+template <typename R>
 void solve_unknown(ys_ctx *c, int loc, int slot, int mask) {
-  State<double> &it = c->lev[2];
+  Fields<R> &D = F<R>(c);
+  State<R> &it = D.lev[2];
   for (int s = 0; s < 3; ++s) {
     int dir = kOrder[loc][s];
     bool fin = (s == 2);
-    double *const *F = c->fac[loc][dir];
+    R *const *Fc = D.fac[loc][dir];
     LAUNCH(c, kSweepClass[dir], 1,
-           Launch<double>::solve(c->S, loc, dir, fin, F[0], F[1], F[2], c->B, it.f[slot], c->norm, slot, mask,
-                                 c->stream));
+           Launch<R>::solve(c->S, loc, dir, fin, Fc[0], Fc[1], Fc[2], D.B, it.f[slot], c->norm, slot, mask,
+                            c->stream));
   }
 }
 
 // LU factors of every line operator for this step (they depend only on a)
-void factorize_all(ys_ctx *c, StepAux<double> ax) {
+template <typename R>
+void factorize_all(ys_ctx *c, StepAux<R> ax) {
+  Fields<R> &D = F<R>(c);
   for (int loc = LC; loc <= LP; ++loc)
     for (int dir = DR; dir <= DP; ++dir) {
-      double *const *F = c->fac[loc][dir];
-      LAUNCH(c, K_FACTOR, 1, Launch<double>::factorize(c->S, loc, dir, ax, F[0], F[1], F[2], 3, c->stream));
+      R *const *Fc = D.fac[loc][dir];
+      LAUNCH(c, K_FACTOR, 1, Launch<R>::factorize(c->S, loc, dir, ax, Fc[0], Fc[1], Fc[2], 3, c->stream));
     }
 }
 
 // one defect-correction pass over T, u1, p1, u2, p2 on the masked patches
-void iterate(ys_ctx *c, StepAux<double> ax, int mask) {
-  State<double> &it = c->lev[2], &n = c->lev[0];
-  LAUNCH(c, K_RES_T, 1, Launch<double>::resid_T(c->S, it, n, ax, c->B, mask, c->stream));
-  solve_unknown(c, LC, F_T, mask);
+template <typename R>
+void iterate(ys_ctx *c, StepAux<R> ax, int mask) {
+  Fields<R> &D = F<R>(c);
+  State<R> &it = D.lev[2], &n = D.lev[0];
+  LAUNCH(c, K_RES_T, 1, Launch<R>::resid_T(c->S, it, n, ax, D.B, mask, c->stream));
+  solve_unknown<R>(c, LC, F_T, mask);
   for (int sys = 1; sys <= 2; ++sys) {
     int o = (sys == 1) ? 0 : 4;
     for (int comp = 0; comp < 3; ++comp) {
-      LAUNCH(c, K_RES_U, 1, Launch<double>::resid_u(c->S, sys, comp, it, n, ax, c->B, mask, c->stream));
-      solve_unknown(c, LR + comp, F_U1R + comp + o, mask);
+      LAUNCH(c, K_RES_U, 1, Launch<R>::resid_u(c->S, sys, comp, it, n, ax, D.B, mask, c->stream));
+      solve_unknown<R>(c, LR + comp, F_U1R + comp + o, mask);
     }
-    LAUNCH(c, K_PRES, 1, Launch<double>::pressure(c->S, sys, it, n, c->norm, mask, c->stream));
+    LAUNCH(c, K_PRES, 1, Launch<R>::pressure(c->S, sys, it, n, c->norm, mask, c->stream));
   }
 }
 
@@ -198,6 +248,196 @@ double time_fn(int id, double t) {
   }
   return 0.0;
 }
+
+template <typename R>
+int step_t(ys_ctx *c, int n_steps, int n_schwarz) {
+  const ys_params &prm = c->prm;
+  Fields<R> &D = F<R>(c);
+  for (int st = 0; st < n_steps; ++st) {
+    State<R> n = D.lev[0], nm1 = D.lev[1], it = D.lev[2];
+    LAUNCH(c, K_EXTRAP, 1, Launch<R>::extrapolate(c->L, it, n, nm1, D.A, c->stream));
+    StepAux<R> ax;
+    for (int a = 0; a < 3; ++a) ax.A[a] = D.A[a];
+    ax.fT = ax.fr = ax.ft = ax.fp = nullptr;
+    if (c->nmodes_set > 0) {
+      // pointers and time weights of the modes at t_n + dt/2, passed by value
+      Modes<R> md{};
+      for (int m = 0; m < c->nmodes_set; ++m) {
+        if (!c->mode_set[m]) continue;
+        for (int a = 0; a < 4; ++a) md.F[md.n][a] = D.modes[m][a];
+        md.tau[md.n] = time_fn(c->mode_fn[m], c->t + 0.5 * prm.dt);
+        ++md.n;
+      }
+      LAUNCH(c, K_FORCE, 1, Launch<R>::combine_forcing(c->L.total, md, D.fcomb, c->stream));
+      ax.fT = D.fcomb[0];
+      ax.fr = D.fcomb[1];
+      ax.ft = D.fcomb[2];
+      ax.fp = D.fcomb[3];
+    }
+    factorize_all<R>(c, ax);
+    c->iters_last = 0;
+    for (int k = 1; k <= n_schwarz; ++k) {
+      cudaMemsetAsync(c->norm, 0, YS_NFIELDS * sizeof(double), c->stream);
+      if (prm.schwarz_mode == YS_ADDITIVE) {
+        LAUNCH(c, K_EXCH, 4, Launch<R>::exchange(c->S, c->X, it, 3, c->stream));
+        LAUNCH(c, K_WALLS, 1, Launch<R>::walls(c->S, it, 3, c->stream));
+        iterate<R>(c, ax, 3);
+        if (prm.step7) LAUNCH(c, K_RING, 1, Launch<R>::ring(c->S, c->X, it, 3, c->stream));
+      } else {
+        for (int p = 0; p < 2; ++p) {
+          int m = 1 << p;
+          LAUNCH(c, K_EXCH, 4, Launch<R>::exchange(c->S, c->X, it, m, c->stream));
+          LAUNCH(c, K_WALLS, 1, Launch<R>::walls(c->S, it, m, c->stream));
+          iterate<R>(c, ax, m);
+          if (prm.step7) LAUNCH(c, K_RING, 1, Launch<R>::ring(c->S, c->X, it, m, c->stream));
+        }
+      }
+      c->iters_last = k;
+      if (prm.schwarz_tol > 0.0) {
+        double h[YS_NFIELDS];
+        if (cudaMemcpyAsync(h, c->norm, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+          return YS_ECUDA;
+        double mx = 0.0;
+        for (int f = 0; f < YS_NFIELDS; ++f) mx = std::fmax(mx, std::sqrt(h[f]));
+        if (mx < prm.schwarz_tol) break;
+      }
+    }
+    refresh<R>(c, it, 3);
+    // rotate time levels: n-1 <- n, n <- iterate, iterate <- old n-1
+    D.lev[0] = it;
+    D.lev[1] = n;
+    D.lev[2] = nm1;
+    c->t += prm.dt;
+    c->steps_done++;
+  }
+  if (cudaGetLastError() != cudaSuccess) return YS_ECUDA;
+  if (n_steps > 0) {
+    double h[YS_NFIELDS];
+    if (cudaMemcpyAsync(h, c->norm, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return YS_ECUDA;
+    bool bad = false;
+    for (int f = 0; f < YS_NFIELDS; ++f) {
+      c->norms_host[f] = std::sqrt(h[f]);
+      if (!std::isfinite(c->norms_host[f])) bad = true;
+    }
+    if (bad) return YS_EDIVERGED;
+  }
+  return YS_OK;
+}
+
+template <typename R>
+int set_fields_t(ys_ctx *c, int level, const double *T, const double *ur, const double *uth, const double *uph,
+                 const double *p, const double *aux, bool dev) {
+  Fields<R> &D = F<R>(c);
+  State<R> &s = D.lev[level];
+  const Layout &L = c->L;
+  int rc = 0;
+  rc |= copy_in<R>(c, LC, T, s.f[F_T], c->T_bg, dev);
+  const double *u[3] = {ur, uth, uph};
+  for (int m = 0; m < 3; ++m) {
+    rc |= copy_in<R>(c, LR + m, u[m], s.f[F_U2R + m], nullptr, dev);
+    if (!aux) rc |= copy_in<R>(c, LR + m, u[m], s.f[F_U1R + m], nullptr, dev);
+  }
+  rc |= copy_in_p(c, p, s.p[1], dev);
+  if (aux) {
+    size_t o = 0;
+    for (int m = 0; m < 3; ++m) {
+      rc |= copy_in<R>(c, LR + m, aux + o, s.f[F_U1R + m], nullptr, dev);
+      o += user_elems(L, LR + m);
+    }
+    rc |= copy_in_p(c, aux + o, s.p[0], dev);
+  } else {
+    rc |= copy_in_p(c, p, s.p[0], dev);
+  }
+  if (rc) return YS_ECUDA;
+  refresh<R>(c, s, 3);
+  if (level == 0 && !c->level1_set) {
+    const int bulk[7] = {F_T, F_U1R, F_U1T, F_U1P, F_U2R, F_U2T, F_U2P};
+    for (int b = 0; b < 7; ++b)
+      cudaMemcpyAsync(D.lev[1].f[bulk[b]], s.f[bulk[b]], L.total * sizeof(R), cudaMemcpyDeviceToDevice, c->stream);
+    for (int q = 0; q < 2; ++q)
+      cudaMemcpyAsync(D.lev[1].p[q], s.p[q], L.total * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  }
+  if (level == 1) c->level1_set = 1;
+  return cuda_ok(cudaStreamSynchronize(c->stream));
+}
+
+template <typename R>
+int get_fields_t(ys_ctx *c, int level, double *T, double *ur, double *uth, double *uph, double *p, double *aux) {
+  Fields<R> &D = F<R>(c);
+  State<R> &s = D.lev[level];
+  int rc = 0;
+  if (T) rc |= copy_out<R>(c, LC, s.f[F_T], T, c->T_bg);
+  if (ur) rc |= copy_out<R>(c, LR, s.f[F_U2R], ur, nullptr);
+  if (uth) rc |= copy_out<R>(c, LT, s.f[F_U2T], uth, nullptr);
+  if (uph) rc |= copy_out<R>(c, LP, s.f[F_U2P], uph, nullptr);
+  if (p) rc |= copy_out_p(c, s.p[1], p);
+  if (aux) {
+    size_t o = 0;
+    for (int m = 0; m < 3; ++m) {
+      rc |= copy_out<R>(c, LR + m, s.f[F_U1R + m], aux + o, nullptr);
+      o += user_elems(c->L, LR + m);
+    }
+    rc |= copy_out_p(c, s.p[0], aux + o);
+  }
+  return rc ? YS_ECUDA : YS_OK;
+}
+
+template <typename R>
+int set_forcing_t(ys_ctx *c, int mode, const double *f_T, const double *f_r, const double *f_th,
+                  const double *f_ph) {
+  Fields<R> &D = F<R>(c);
+  if (!c->modes_mem[mode]) {
+    size_t bytes = 4 * (size_t)c->L.total * sizeof(R);
+    if (cudaMalloc(&c->modes_mem[mode], bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->modes_mem[mode] = nullptr;
+      return YS_ENOMEM;
+    }
+    cudaMemsetAsync(c->modes_mem[mode], 0, bytes, c->stream);
+    for (int a = 0; a < 4; ++a) D.modes[mode][a] = (R *)c->modes_mem[mode] + a * c->L.total;
+    c->dbytes += bytes;
+  }
+  int rc = 0;
+  rc |= copy_in<R>(c, LC, f_T, D.modes[mode][0], nullptr, false);
+  rc |= copy_in<R>(c, LR, f_r, D.modes[mode][1], nullptr, false);
+  rc |= copy_in<R>(c, LT, f_th, D.modes[mode][2], nullptr, false);
+  rc |= copy_in<R>(c, LP, f_ph, D.modes[mode][3], nullptr, false);
+  if (rc) return YS_ECUDA;
+  return cuda_ok(cudaStreamSynchronize(c->stream));
+}
+
+// carve the typed state out of one device allocation starting at `base`
+template <typename R>
+char *carve(ys_ctx *c, Fields<R> &D, char *base) {
+  const long T = c->L.total;
+  R *f = (R *)base;
+  size_t fi = 0;
+  const int bulk[7] = {F_T, F_U1R, F_U1T, F_U1P, F_U2R, F_U2T, F_U2P};
+  for (int l = 0; l < 3; ++l) {
+    for (int b = 0; b < NF; ++b) D.lev[l].f[b] = nullptr;
+    for (int b = 0; b < 7; ++b) D.lev[l].f[bulk[b]] = f + (fi++) * T;
+  }
+  for (int a = 0; a < 3; ++a) D.A[a] = f + (fi++) * T;
+  for (int a = 0; a < 4; ++a) D.fcomb[a] = f + (fi++) * T;
+  D.B = f + (fi++) * T;
+  D.Cs = f + (fi++) * T;
+  for (int loc = 0; loc < 4; ++loc)
+    for (int dir = 0; dir < 3; ++dir)
+      for (int a = 0; a < 3; ++a) D.fac[loc][dir][a] = f + (fi++) * T;
+  for (int m = 0; m < kMaxModes; ++m)
+    for (int a = 0; a < 4; ++a) D.modes[m][a] = nullptr;
+  char *next = base + ((fi * T * sizeof(R) + 255) / 256) * 256;
+  double *pp = (double *)next;
+  for (int l = 0; l < 3; ++l)
+    for (int q = 0; q < 2; ++q) D.lev[l].p[q] = pp + (2 * l + q) * T;
+  return next + ((6 * T * sizeof(double) + 255) / 256) * 256;
+}
+
+// number of bulk fields of one shell (3 x 7 levels, 3 a, 4 forcing, B, Cs, 36 factors)
+constexpr size_t kBulkFields = 3 * 7 + 3 + 4 + 2 + 36;
 
 }  // namespace
 
@@ -250,9 +490,11 @@ int ys_destroy(ys_ctx *c) {
     cudaEventDestroy(r.b);
   }
   for (int m = 0; m < kMaxModes; ++m)
-    if (c->modes[m][0]) cudaFree(c->modes[m][0]);
+    if (c->modes_mem[m]) cudaFree(c->modes_mem[m]);
   if (c->dmem) cudaFree(c->dmem);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c->f64;
+  delete c->f32;
   delete c;
   return YS_OK;
 }
@@ -262,7 +504,6 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   *out = nullptr;
   int rc = validate(p);
   if (rc) return rc;
-  if (p->precision != YS_FP64) return YS_EINVAL;   // mixed form: separate build step
   GridSpec gs{p->R1, p->R2, p->Nr, p->Nth, p->Nph, p->overlap};
   GridGeo G;
   if (make_grid(gs, G)) return YS_EINVAL;
@@ -275,6 +516,7 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   if (!c) return YS_ENOMEM;
   c->prm = *p;
   c->geo = G;
+  const bool mixed = (p->precision == YS_MIXED);
   Layout &L = c->L;
   L.Nr = p->Nr;
   L.Nt = p->Nth;
@@ -289,19 +531,37 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   std::vector<double> met;
   int pad, len;
   make_metric(gs, G, met, pad, len);
-  size_t nfields = 3 * NF + 3 + 4 + 2 + 36;
-  size_t field_bytes = (size_t)L.total * sizeof(double);
+  // deviation backgrounds of the mixed form (per radial index)
+  std::vector<double> Tc(p->Nr + 2), Tlap(p->Nr, 0.0), Tdr(p->Nr, 0.0), pc(p->Nr, 0.0);
+  const bool deviation = mixed && (p->T_inner != 0.0 || p->T_outer != 0.0);
+  if (deviation) {
+    double Ac = (p->T_inner - p->T_outer) / (1.0 / p->R1 - 1.0 / p->R2);
+    double Bc = p->T_inner - Ac / p->R1;
+    for (int i = 0; i < p->Nr; ++i) Tc[i + 1] = Ac / (p->R1 + (i + 0.5) * G.hr) + Bc;
+    Tc[0] = 2.0 * p->T_inner - Tc[1];             // reflection ghosts, as for T
+    Tc[p->Nr + 1] = 2.0 * p->T_outer - Tc[p->Nr];
+    for (int i = 0; i < p->Nr; ++i) {
+      double rc = p->R1 + (i + 0.5) * G.hr, rfp = p->R1 + (i + 1) * G.hr, rf0 = p->R1 + i * G.hr;
+      Tlap[i] = (rfp * rfp * (Tc[i + 2] - Tc[i + 1]) - rf0 * rf0 * (Tc[i + 1] - Tc[i])) / (rc * rc * G.hr * G.hr);
+      Tdr[i] = (Tc[i + 2] - Tc[i]) / (2.0 * G.hr);
+      if (i > 0) pc[i] = pc[i - 1] + G.hr * p->Pr * p->Ra * 0.5 * (Tc[i] + Tc[i + 1]);
+    }
+  }
+  size_t Rsz = mixed ? sizeof(float) : sizeof(double);
+  size_t bulk_bytes = ((kBulkFields * L.total * Rsz + 255) / 256) * 256;
+  size_t p_bytes = ((6 * L.total * sizeof(double) + 255) / 256) * 256;
   size_t xcount = 0;
   for (int k = 0; k < XNUM; ++k) xcount += xt[k].size();
-  c->stage_elems = user_elems(L, LR);
-  size_t se = user_elems(L, LT), sp = user_elems(L, LP);
-  if (se > c->stage_elems) c->stage_elems = se;
-  if (sp > c->stage_elems) c->stage_elems = sp;
-  size_t off_metric = nfields * field_bytes;
+  size_t stage_elems = user_elems(L, LR);
+  if (user_elems(L, LT) > stage_elems) stage_elems = user_elems(L, LT);
+  if (user_elems(L, LP) > stage_elems) stage_elems = user_elems(L, LP);
+  size_t off_metric = bulk_bytes + p_bytes;
   size_t off_x = off_metric + ((met.size() * sizeof(double) + 255) / 256) * 256;
-  size_t off_norm = off_x + ((xcount * sizeof(XEntry) + 255) / 256) * 256;
+  size_t off_dev = off_x + ((xcount * sizeof(XEntry) + 255) / 256) * 256;
+  size_t dev_bytes = ((4 * (size_t)(p->Nr + 2) * sizeof(double) + 255) / 256) * 256;
+  size_t off_norm = off_dev + dev_bytes;
   size_t off_stage = off_norm + 256;
-  size_t total = off_stage + c->stage_elems * sizeof(double);
+  size_t total = off_stage + stage_elems * sizeof(double);
 
   if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
     ys_destroy(c);
@@ -319,22 +579,27 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
     ys_destroy(c);
     return YS_ECUDA;
   }
-  c->fields = (double *)base;
-  size_t fi = 0;
-  for (int l = 0; l < 3; ++l)
-    for (int f = 0; f < NF; ++f) c->lev[l].f[f] = c->fields + (fi++) * L.total;
-  for (int a = 0; a < 3; ++a) c->A[a] = c->fields + (fi++) * L.total;
-  for (int a = 0; a < 4; ++a) c->fcomb[a] = c->fields + (fi++) * L.total;
-  c->B = c->fields + (fi++) * L.total;
-  c->Cs = c->fields + (fi++) * L.total;
-  for (int loc = 0; loc < 4; ++loc)
-    for (int dir = 0; dir < 3; ++dir)
-      for (int a = 0; a < 3; ++a) c->fac[loc][dir][a] = c->fields + (fi++) * L.total;
-  c->metric = (double *)(base + off_metric);
+  if (mixed) {
+    c->f32 = new (std::nothrow) Fields<float>();
+    if (!c->f32) {
+      ys_destroy(c);
+      return YS_ENOMEM;
+    }
+    carve<float>(c, *c->f32, base);
+  } else {
+    c->f64 = new (std::nothrow) Fields<double>();
+    if (!c->f64) {
+      ys_destroy(c);
+      return YS_ENOMEM;
+    }
+    carve<double>(c, *c->f64, base);
+  }
+  double *metric = (double *)(base + off_metric);
   c->xdev = (XEntry *)(base + off_x);
+  double *devtab = (double *)(base + off_dev);
   c->norm = (double *)(base + off_norm);
   c->stage = (double *)(base + off_stage);
-  cudaMemcpyAsync(c->metric, met.data(), met.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(metric, met.data(), met.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
   size_t xo = 0;
   for (int k = 0; k < XNUM; ++k) {
     if (!xt[k].empty())
@@ -355,16 +620,16 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   S.kappa = 1.0;
   S.chi = p->chi;
   S.PrRa = p->Pr * p->Ra;
-  S.rc = c->metric + 0 * len + pad;
-  S.rf = c->metric + 1 * len + pad;
-  S.sc = c->metric + 2 * len + pad;
-  S.sf = c->metric + 3 * len + pad;
-  S.cc = c->metric + 4 * len + pad;
-  S.cf = c->metric + 5 * len + pad;
-  S.irc = c->metric + 6 * len + pad;
-  S.irf = c->metric + 7 * len + pad;
-  S.isc = c->metric + 8 * len + pad;
-  S.isf = c->metric + 9 * len + pad;
+  S.rc = metric + 0 * len + pad;
+  S.rf = metric + 1 * len + pad;
+  S.sc = metric + 2 * len + pad;
+  S.sf = metric + 3 * len + pad;
+  S.cc = metric + 4 * len + pad;
+  S.cf = metric + 5 * len + pad;
+  S.irc = metric + 6 * len + pad;
+  S.irf = metric + 7 * len + pad;
+  S.isc = metric + 8 * len + pad;
+  S.isf = metric + 9 * len + pad;
   S.ihr = 1.0 / G.hr;
   S.iht = 1.0 / G.ht;
   S.ihp = 1.0 / G.hp;
@@ -373,7 +638,27 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   S.cphi = 1.0 / (p->R1 * p->R1 * S.sin_theta1 * S.sin_theta1 * G.hp * G.hp);
   S.T_in = p->T_inner;
   S.T_out = p->T_outer;
+  S.Tc_lap = nullptr;
+  S.Tc_dr = nullptr;
   S.step7 = p->step7;
+  if (deviation) {
+    // device tables: [Tc at centres i = 0..Nr-1 | pc | Tc_lap | Tc_dr], each Nr + 2 long
+    const size_t n = p->Nr + 2;
+    std::vector<double> h(4 * n, 0.0);
+    for (int i = 0; i < p->Nr; ++i) {
+      h[0 * n + i] = Tc[i + 1];
+      h[1 * n + i] = pc[i];
+      h[2 * n + i] = Tlap[i];
+      h[3 * n + i] = Tdr[i];
+    }
+    cudaMemcpyAsync(devtab, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    c->T_bg = devtab;
+    c->p_bg = devtab + n;
+    S.Tc_lap = devtab + 2 * n;
+    S.Tc_dr = devtab + 3 * n;
+    S.T_in = 0.0;   // the deviation has homogeneous reflection walls
+    S.T_out = 0.0;
+  }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
     ys_destroy(c);
     return YS_ECUDA;
@@ -382,77 +667,39 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   return YS_OK;
 }
 
-static int set_fields_impl(ys_ctx *c, int level, const double *T, const double *ur, const double *uth,
-                           const double *uph, const double *p, const double *aux, bool dev) {
+static int set_fields_any(ys_ctx *c, int level, const double *T, const double *ur, const double *uth,
+                          const double *uph, const double *p, const double *aux, bool dev) {
   if (!c || (level != 0 && level != 1) || !T || !ur || !uth || !uph || !p) return YS_EINVAL;
-  State<double> &s = c->lev[level];
-  const Layout &L = c->L;
-  int rc = 0;
-  rc |= copy_in(c, LC, T, s.f[F_T], dev);
-  const double *u[3] = {ur, uth, uph};
-  for (int m = 0; m < 3; ++m) {
-    rc |= copy_in(c, LR + m, u[m], s.f[F_U2R + m], dev);
-    if (!aux) rc |= copy_in(c, LR + m, u[m], s.f[F_U1R + m], dev);
-  }
-  rc |= copy_in(c, LC, p, s.f[F_P2], dev);
-  if (aux) {
-    size_t o = 0;
-    for (int m = 0; m < 3; ++m) {
-      rc |= copy_in(c, LR + m, aux + o, s.f[F_U1R + m], dev);
-      o += user_elems(L, LR + m);
-    }
-    rc |= copy_in(c, LC, aux + o, s.f[F_P1], dev);
-  } else {
-    rc |= copy_in(c, LC, p, s.f[F_P1], dev);
-  }
-  if (rc) return YS_ECUDA;
-  refresh(c, s, 3);
-  if (level == 0 && !c->level1_set) {
-    for (int f = 0; f < NF; ++f)
-      cudaMemcpyAsync(c->lev[1].f[f], s.f[f], L.total * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
-  }
-  if (level == 1) c->level1_set = 1;
-  return cuda_ok(cudaStreamSynchronize(c->stream));
+  if (c->f32) return set_fields_t<float>(c, level, T, ur, uth, uph, p, aux, dev);
+  return set_fields_t<double>(c, level, T, ur, uth, uph, p, aux, dev);
 }
 
 int ys_set_fields(ys_ctx *c, int level, const double *T, const double *ur, const double *uth, const double *uph,
                   const double *p) {
-  return set_fields_impl(c, level, T, ur, uth, uph, p, nullptr, false);
+  return set_fields_any(c, level, T, ur, uth, uph, p, nullptr, false);
 }
 
 int ys_set_fields_ex(ys_ctx *c, int level, const double *T, const double *ur, const double *uth,
                      const double *uph, const double *p, const double *aux) {
-  return set_fields_impl(c, level, T, ur, uth, uph, p, aux, false);
+  return set_fields_any(c, level, T, ur, uth, uph, p, aux, false);
 }
 
 int ys_set_fields_dev(ys_ctx *c, int level, const double *T, const double *ur, const double *uth,
                       const double *uph, const double *p, const double *aux) {
-  return set_fields_impl(c, level, T, ur, uth, uph, p, aux, true);
+  return set_fields_any(c, level, T, ur, uth, uph, p, aux, true);
 }
 
 int ys_set_forcing(ys_ctx *c, int mode, int time_fn_id, const double *f_T, const double *f_r, const double *f_th,
                    const double *f_ph) {
   if (!c || mode < 0 || mode >= kMaxModes || time_fn_id < 0 || time_fn_id > 4) return YS_EINVAL;
   if (!f_T || !f_r || !f_th || !f_ph) return YS_EINVAL;
-  if (!c->modes[mode][0]) {
-    void *mem = nullptr;
-    if (cudaMalloc(&mem, 4 * (size_t)c->L.total * sizeof(double)) != cudaSuccess) {
-      cudaGetLastError();
-      return YS_ENOMEM;
-    }
-    cudaMemsetAsync(mem, 0, 4 * (size_t)c->L.total * sizeof(double), c->stream);
-    for (int a = 0; a < 4; ++a) c->modes[mode][a] = (double *)mem + a * c->L.total;
-    c->dbytes += 4 * (size_t)c->L.total * sizeof(double);
-  }
+  int rc = c->f32 ? set_forcing_t<float>(c, mode, f_T, f_r, f_th, f_ph)
+                  : set_forcing_t<double>(c, mode, f_T, f_r, f_th, f_ph);
+  if (rc) return rc;
   c->mode_fn[mode] = time_fn_id;
-  int rc = 0;
-  rc |= copy_in(c, LC, f_T, c->modes[mode][0], false);
-  rc |= copy_in(c, LR, f_r, c->modes[mode][1], false);
-  rc |= copy_in(c, LT, f_th, c->modes[mode][2], false);
-  rc |= copy_in(c, LP, f_ph, c->modes[mode][3], false);
+  c->mode_set[mode] = 1;
   if (mode + 1 > c->nmodes_set) c->nmodes_set = mode + 1;
-  if (rc) return YS_ECUDA;
-  return cuda_ok(cudaStreamSynchronize(c->stream));
+  return YS_OK;
 }
 
 int ys_set_time(ys_ctx *c, double t) {
@@ -470,99 +717,13 @@ int ys_set_stream(ys_ctx *c, void *stream) {
 
 int ys_step(ys_ctx *c, int n_steps, int n_schwarz) {
   if (!c || n_steps < 0 || n_schwarz < 1) return YS_EINVAL;
-  const ys_params &prm = c->prm;
-  for (int st = 0; st < n_steps; ++st) {
-    State<double> n = c->lev[0], nm1 = c->lev[1], it = c->lev[2];
-    LAUNCH(c, K_EXTRAP, 1, Launch<double>::extrapolate(c->L, it, n, nm1, c->A, c->stream));
-    StepAux<double> ax;
-    for (int a = 0; a < 3; ++a) ax.A[a] = c->A[a];
-    ax.fT = ax.fr = ax.ft = ax.fp = nullptr;
-    if (c->nmodes_set > 0) {
-      // pointers and time weights of the modes at t_n + dt/2, passed by value
-      Modes<double> md{};
-      for (int m = 0; m < c->nmodes_set; ++m) {
-        if (!c->modes[m][0]) continue;
-        for (int a = 0; a < 4; ++a) md.F[md.n][a] = c->modes[m][a];
-        md.tau[md.n] = time_fn(c->mode_fn[m], c->t + 0.5 * prm.dt);
-        ++md.n;
-      }
-      LAUNCH(c, K_FORCE, 1, Launch<double>::combine_forcing(c->L.total, md, c->fcomb, c->stream));
-      ax.fT = c->fcomb[0];
-      ax.fr = c->fcomb[1];
-      ax.ft = c->fcomb[2];
-      ax.fp = c->fcomb[3];
-    }
-    factorize_all(c, ax);
-    c->iters_last = 0;
-    for (int k = 1; k <= n_schwarz; ++k) {
-      cudaMemsetAsync(c->norm, 0, YS_NFIELDS * sizeof(double), c->stream);
-      if (prm.schwarz_mode == YS_ADDITIVE) {
-        LAUNCH(c, K_EXCH, 4, Launch<double>::exchange(c->S, c->X, it, 3, c->stream));
-        LAUNCH(c, K_WALLS, 1, Launch<double>::walls(c->S, it, 3, c->stream));
-        iterate(c, ax, 3);
-        if (prm.step7) LAUNCH(c, K_RING, 1, Launch<double>::ring(c->S, c->X, it, 3, c->stream));
-      } else {
-        for (int p = 0; p < 2; ++p) {
-          int m = 1 << p;
-          LAUNCH(c, K_EXCH, 4, Launch<double>::exchange(c->S, c->X, it, m, c->stream));
-          LAUNCH(c, K_WALLS, 1, Launch<double>::walls(c->S, it, m, c->stream));
-          iterate(c, ax, m);
-          if (prm.step7) LAUNCH(c, K_RING, 1, Launch<double>::ring(c->S, c->X, it, m, c->stream));
-        }
-      }
-      c->iters_last = k;
-      if (prm.schwarz_tol > 0.0) {
-        double h[YS_NFIELDS];
-        if (cudaMemcpyAsync(h, c->norm, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-            cudaStreamSynchronize(c->stream) != cudaSuccess)
-          return YS_ECUDA;
-        double mx = 0.0;
-        for (int f = 0; f < YS_NFIELDS; ++f) mx = std::fmax(mx, std::sqrt(h[f]));
-        if (mx < prm.schwarz_tol) break;
-      }
-    }
-    refresh(c, it, 3);
-    // rotate time levels: n-1 <- n, n <- iterate, iterate <- old n-1
-    c->lev[0] = it;
-    c->lev[1] = n;
-    c->lev[2] = nm1;
-    c->t += prm.dt;
-    c->steps_done++;
-  }
-  if (cudaGetLastError() != cudaSuccess) return YS_ECUDA;
-  if (n_steps > 0) {
-    double h[YS_NFIELDS];
-    if (cudaMemcpyAsync(h, c->norm, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
-      return YS_ECUDA;
-    bool bad = false;
-    for (int f = 0; f < YS_NFIELDS; ++f) {
-      c->norms_host[f] = std::sqrt(h[f]);
-      if (!std::isfinite(c->norms_host[f])) bad = true;
-    }
-    if (bad) return YS_EDIVERGED;
-  }
-  return YS_OK;
+  return c->f32 ? step_t<float>(c, n_steps, n_schwarz) : step_t<double>(c, n_steps, n_schwarz);
 }
 
 int ys_get_fields(ys_ctx *c, int level, double *T, double *ur, double *uth, double *uph, double *p, double *aux) {
   if (!c || (level != 0 && level != 1)) return YS_EINVAL;
-  State<double> &s = c->lev[level];
-  int rc = 0;
-  if (T) rc |= copy_out(c, LC, s.f[F_T], T);
-  if (ur) rc |= copy_out(c, LR, s.f[F_U2R], ur);
-  if (uth) rc |= copy_out(c, LT, s.f[F_U2T], uth);
-  if (uph) rc |= copy_out(c, LP, s.f[F_U2P], uph);
-  if (p) rc |= copy_out(c, LC, s.f[F_P2], p);
-  if (aux) {
-    size_t o = 0;
-    for (int m = 0; m < 3; ++m) {
-      rc |= copy_out(c, LR + m, s.f[F_U1R + m], aux + o);
-      o += user_elems(c->L, LR + m);
-    }
-    rc |= copy_out(c, LC, s.f[F_P1], aux + o);
-  }
-  return rc ? YS_ECUDA : YS_OK;
+  return c->f32 ? get_fields_t<float>(c, level, T, ur, uth, uph, p, aux)
+                : get_fields_t<double>(c, level, T, ur, uth, uph, p, aux);
 }
 
 int ys_get_stats(ys_ctx *c, double *last_norm, double *t, long *steps) {

@@ -7,9 +7,19 @@ namespace ys {
 // Field slots of one time level / iterate.
 enum FieldSlot { F_T = 0, F_U1R, F_U1T, F_U1P, F_P1, F_U2R, F_U2T, F_U2P, F_P2, NF = 9 };
 
+// One time level or iterate.  Bulk fields (T, u1, u2) are stored in R;
+// pressures are always FP64 (p[0] = p1, p[1] = p2).  The slots F_P1 / F_P2 of f
+// are not used by the kernels.
 template <typename R>
 struct State {
   R *f[NF];
+  double *p[2];
+};
+
+// Arithmetic type of the bulk stencils and sweeps: the storage type.
+template <typename R>
+struct Cmp {
+  using type = R;
 };
 
 // Advecting velocity and forcing pointers of one step.
@@ -61,9 +71,14 @@ struct Launch {
                     R *dst, double *norm, int slot, int patch_mask, cudaStream_t st);
   static void pressure(const Shell &S, int sys, State<R> it, State<R> n, double *norm, int patch_mask,
                        cudaStream_t st);
-  // host layout <-> device layout
-  static void unpack(const Layout &L, int loc, const double *src, R *dst, cudaStream_t st);
-  static void pack(const Layout &L, int loc, const R *src, double *dst, cudaStream_t st);
+  // host layout <-> device layout; bg (FP64 per radial index, may be null) is
+  // subtracted on the way in and added on the way out
+  static void unpack(const Layout &L, int loc, const double *src, R *dst, const double *bg, cudaStream_t st);
+  static void pack(const Layout &L, int loc, const R *src, double *dst, const double *bg, cudaStream_t st);
 };
+
+// FP64 pressure fields: host layout <-> device layout
+void unpack_p(const Layout &L, const double *src, double *dst, const double *bg, cudaStream_t st);
+void pack_p(const Layout &L, const double *src, double *dst, const double *bg, cudaStream_t st);
 
 }  // namespace ys

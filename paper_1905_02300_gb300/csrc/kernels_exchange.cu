@@ -44,8 +44,8 @@ __global__ void k_exchange(Shell S, const XEntry *__restrict__ e, int n, int kin
     s.f[F_U1R][qt] = (R)bilin(s.f[F_U1R], L, d, i, E.j0a, E.k0a, E.wja, E.wka);
     s.f[F_U2R][qt] = (R)bilin(s.f[F_U2R], L, d, i, E.j0a, E.k0a, E.wja, E.wka);
   } else if (kind == XP) {
-    s.f[F_P1][qt] = (R)bilin(s.f[F_P1], L, d, i, E.j0a, E.k0a, E.wja, E.wka);
-    s.f[F_P2][qt] = (R)bilin(s.f[F_P2], L, d, i, E.j0a, E.k0a, E.wja, E.wka);
+    s.p[0][qt] = bilin(s.p[0], L, d, i, E.j0a, E.k0a, E.wja, E.wka);
+    s.p[1][qt] = bilin(s.p[1], L, d, i, E.j0a, E.k0a, E.wja, E.wka);
   } else {
     int slot = (kind == XUT) ? F_U1T : F_U1P;
     for (int o = 0; o <= 4; o += 4) {
@@ -119,8 +119,11 @@ void Launch<R>::ring(const Shell &S, const XTables &X, State<R> s, int pm, cudaS
   k_exchange<R><<<dim3((unsigned)((n + 255) / 256), 2), 256, 0, st>>>(S, X.e[XP], X.n[XP], XP, s, pm);
 }
 
-template void Launch<double>::exchange(const Shell &, const XTables &, State<double>, int, cudaStream_t);
-template void Launch<double>::walls(const Shell &, State<double>, int, cudaStream_t);
-template void Launch<double>::ring(const Shell &, const XTables &, State<double>, int, cudaStream_t);
+#define YS_INST_EXCHANGE(R)                                                                 \
+  template void Launch<R>::exchange(const Shell &, const XTables &, State<R>, int, cudaStream_t); \
+  template void Launch<R>::walls(const Shell &, State<R>, int, cudaStream_t);                   \
+  template void Launch<R>::ring(const Shell &, const XTables &, State<R>, int, cudaStream_t);
+YS_INST_EXCHANGE(double)
+YS_INST_EXCHANGE(float)
 
 }  // namespace ys

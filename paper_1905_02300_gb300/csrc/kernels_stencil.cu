@@ -6,7 +6,10 @@
 // conservative 3-point diffusion with the metric at half points, centred
 // first derivatives (2-point across a half-cell offset, 2h otherwise),
 // off-location values as arithmetic means of the 2 or 4 nearest stored
-// values, metric factors evaluated exactly at the row's point.
+// values, metric factors evaluated exactly at the row's point (FP64 tables of
+// r, sin(theta), cos(theta) and their reciprocals).  Bulk arithmetic runs in
+// the storage type (FP64, or FP32 in the mixed form); pressures and the
+// divergence that updates them are FP64 in both forms.
 #include "kernels.cuh"
 
 namespace ys {
@@ -15,20 +18,20 @@ namespace {
 
 constexpr int TPB = 128;
 
-template <typename R>
-__device__ __forceinline__ double H(const R *a, const R *b, long q) {
-  return 0.5 * ((double)a[q] + (double)b[q]);
+template <typename V, typename R>
+__device__ __forceinline__ V H(const R *a, const R *b, long q) {
+  return (V)0.5 * ((V)a[q] + (V)b[q]);
 }
 
-template <typename R>
-__device__ __forceinline__ double avg4(const R *a, long q1, long q2, long q3, long q4) {
-  return (((double)a[q1] + (double)a[q2]) + (double)a[q3] + (double)a[q4]) * 0.25;
+template <typename V, typename R>
+__device__ __forceinline__ V avg4(const R *a, long q1, long q2, long q3, long q4) {
+  return (((V)a[q1] + (V)a[q2]) + (V)a[q3] + (V)a[q4]) * (V)0.25;
 }
 
 // half-level average of 4 points of a pair of arrays
-template <typename R>
-__device__ __forceinline__ double havg4(const R *a, const R *b, long q1, long q2, long q3, long q4) {
-  return ((H(a, b, q1) + H(a, b, q2)) + H(a, b, q3) + H(a, b, q4)) * 0.25;
+template <typename V, typename R>
+__device__ __forceinline__ V havg4(const R *a, const R *b, long q1, long q2, long q3, long q4) {
+  return ((H<V>(a, b, q1) + H<V>(a, b, q2)) + H<V>(a, b, q3) + H<V>(a, b, q4)) * (V)0.25;
 }
 
 // region of unknowns of a location type, logical half-open ranges
@@ -59,29 +62,36 @@ __device__ __forceinline__ bool decode_point(const Layout &L, int loc, int patch
 }
 
 // discrete divergence of the half-level velocity at cell (p, i, j, k)
-template <typename R>
-__device__ __forceinline__ double divh(const Shell &S, const R *ri, const R *rn, const R *ti, const R *tn,
-                                       const R *pi, const R *pn, int i, int j, long q) {
+template <typename V, typename R>
+__device__ __forceinline__ V divh(const Shell &S, const R *ri, const R *rn, const R *ti, const R *tn, const R *pi,
+                                  const R *pn, int i, int j, long q) {
   const Layout &L = S.L;
-  double ir = S.irc[i], is = S.isc[j];
-  double d_r = (S.rf[i + 1] * S.rf[i + 1] * H(ri, rn, q + L.SI) - S.rf[i] * S.rf[i] * H(ri, rn, q)) *
-               (ir * ir * S.ihr);
-  double d_t = (S.sf[j + 1] * H(ti, tn, q + L.P) - S.sf[j] * H(ti, tn, q)) * (ir * is * S.iht);
-  double d_p = (H(pi, pn, q + 1) - H(pi, pn, q)) * (ir * is * S.ihp);
+  const V ir = (V)S.irc[i], is = (V)S.isc[j];
+  const V rfp = (V)S.rf[i + 1], rf0 = (V)S.rf[i];
+  V d_r = (rfp * rfp * H<V>(ri, rn, q + L.SI) - rf0 * rf0 * H<V>(ri, rn, q)) * (ir * ir * (V)S.ihr);
+  V d_t = ((V)S.sf[j + 1] * H<V>(ti, tn, q + L.P) - (V)S.sf[j] * H<V>(ti, tn, q)) * (ir * is * (V)S.iht);
+  V d_p = (H<V>(pi, pn, q + 1) - H<V>(pi, pn, q)) * (ir * is * (V)S.ihp);
   return d_r + d_t + d_p;
 }
 
 // ----------------------------------------------------------------- extrapolate
 template <typename R>
 __global__ void k_extrapolate(long total, State<R> it, State<R> n, State<R> nm1, R *A0, R *A1, R *A2) {
+  using V = typename Cmp<R>::type;
   long q = blockIdx.x * (long)blockDim.x + threadIdx.x;
   long stride = (long)gridDim.x * blockDim.x;
+  const int bulk[7] = {F_T, F_U1R, F_U1T, F_U1P, F_U2R, F_U2T, F_U2P};
   for (; q < total; q += stride) {
 #pragma unroll
-    for (int f = 0; f < NF; ++f) it.f[f][q] = (R)(2.0 * (double)n.f[f][q] - (double)nm1.f[f][q]);
-    A0[q] = (R)(1.5 * (double)n.f[F_U2R][q] - 0.5 * (double)nm1.f[F_U2R][q]);
-    A1[q] = (R)(1.5 * (double)n.f[F_U2T][q] - 0.5 * (double)nm1.f[F_U2T][q]);
-    A2[q] = (R)(1.5 * (double)n.f[F_U2P][q] - 0.5 * (double)nm1.f[F_U2P][q]);
+    for (int b = 0; b < 7; ++b) {
+      int f = bulk[b];
+      it.f[f][q] = (R)((V)2.0 * (V)n.f[f][q] - (V)nm1.f[f][q]);
+    }
+    it.p[0][q] = 2.0 * n.p[0][q] - nm1.p[0][q];
+    it.p[1][q] = 2.0 * n.p[1][q] - nm1.p[1][q];
+    A0[q] = (R)((V)1.5 * (V)n.f[F_U2R][q] - (V)0.5 * (V)nm1.f[F_U2R][q]);
+    A1[q] = (R)((V)1.5 * (V)n.f[F_U2T][q] - (V)0.5 * (V)nm1.f[F_U2T][q]);
+    A2[q] = (R)((V)1.5 * (V)n.f[F_U2P][q] - (V)0.5 * (V)nm1.f[F_U2P][q]);
   }
 }
 
@@ -102,39 +112,44 @@ __global__ void k_combine(long total, Modes<R> M, R *o0, R *o1, R *o2, R *o3) {
 // ----------------------------------------------------------------- residual T
 template <typename R>
 __global__ void k_resid_T(Shell S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
+  using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
   if (!decode_point(L, LC, patch_mask, p, i, j, k)) return;
   long q = lidx(L, p, i, j, k);
   const R *a = it.f[F_T], *b = n.f[F_T];
-  const double ir = S.irc[i], is = S.isc[j], ir2 = ir * ir;
-  const double ihr = S.ihr, iht = S.iht, ihp = S.ihp;
-  double X0 = H(a, b, q);
-  double Xrp = H(a, b, q + L.SI), Xrm = H(a, b, q - L.SI);
-  double Xtp = H(a, b, q + L.P), Xtm = H(a, b, q - L.P);
-  double Xpp = H(a, b, q + 1), Xpm = H(a, b, q - 1);
-  double Drr = (S.rf[i + 1] * S.rf[i + 1] * (Xrp - X0) - S.rf[i] * S.rf[i] * (X0 - Xrm)) * (ir2 * ihr * ihr);
-  double Dtt = (S.sf[j + 1] * (Xtp - X0) - S.sf[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
-  double Dpp = (Xpp - 2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
-  double ar = ((double)ax.A[0][q] + (double)ax.A[0][q + L.SI]) * 0.5;
-  double at = ((double)ax.A[1][q] + (double)ax.A[1][q + L.P]) * 0.5;
-  double ap = ((double)ax.A[2][q] + (double)ax.A[2][q + 1]) * 0.5;
-  double adv = ar * (Xrp - Xrm) * (0.5 * ihr) + at * (Xtp - Xtm) * (0.5 * ir * iht) +
-               ap * (Xpp - Xpm) * (0.5 * ir * is * ihp);
-  double f = ax.fT ? (double)ax.fT[q] : 0.0;
-  double rate = S.kappa * (Drr + Dtt + Dpp) - adv + f;
-  B[q] = (R)(S.dt * rate - ((double)a[q] - (double)b[q]));
+  const V ir = (V)S.irc[i], is = (V)S.isc[j], ir2 = ir * ir;
+  const V ihr = (V)S.ihr, iht = (V)S.iht, ihp = (V)S.ihp;
+  const V rfp = (V)S.rf[i + 1], rf0 = (V)S.rf[i];
+  V X0 = H<V>(a, b, q);
+  V Xrp = H<V>(a, b, q + L.SI), Xrm = H<V>(a, b, q - L.SI);
+  V Xtp = H<V>(a, b, q + L.P), Xtm = H<V>(a, b, q - L.P);
+  V Xpp = H<V>(a, b, q + 1), Xpm = H<V>(a, b, q - 1);
+  V Drr = (rfp * rfp * (Xrp - X0) - rf0 * rf0 * (X0 - Xrm)) * (ir2 * ihr * ihr);
+  V Dtt = ((V)S.sf[j + 1] * (Xtp - X0) - (V)S.sf[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
+  V Dpp = (Xpp - (V)2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
+  V ar = ((V)ax.A[0][q] + (V)ax.A[0][q + L.SI]) * (V)0.5;
+  V at = ((V)ax.A[1][q] + (V)ax.A[1][q + L.P]) * (V)0.5;
+  V ap = ((V)ax.A[2][q] + (V)ax.A[2][q + 1]) * (V)0.5;
+  V adv = ar * (Xrp - Xrm) * ((V)0.5 * ihr) + at * (Xtp - Xtm) * ((V)0.5 * ir * iht) +
+          ap * (Xpp - Xpm) * ((V)0.5 * ir * is * ihp);
+  V f = ax.fT ? (V)ax.fT[q] : (V)0.0;
+  V rate = (V)S.kappa * (Drr + Dtt + Dpp) - adv + f;
+  if (S.Tc_lap) rate += (V)(S.kappa * S.Tc_lap[i]) - ar * (V)S.Tc_dr[i];
+  B[q] = (R)((V)S.dt * rate - ((V)a[q] - (V)b[q]));
 }
 
 // ----------------------------------------------------------------- residual u
+// pressure entering the momentum rows: P_1 = p_1^n, P_2 = p_2^n + (p_1 - p_1^n)/2
 template <typename R>
 __device__ __forceinline__ double pres(const State<R> &it, const State<R> &n, int sys, long q) {
-  if (sys == 1) return (double)n.f[F_P1][q];
-  return (double)n.f[F_P2][q] + 0.5 * ((double)it.f[F_P1][q] - (double)n.f[F_P1][q]);
+  if (sys == 1) return n.p[0][q];
+  return n.p[1][q] + 0.5 * (it.p[0][q] - n.p[0][q]);
 }
 
 template <typename R>
 __global__ void k_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
+  using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
   if (!decode_point(L, LR, patch_mask, p, i, j, k)) return;
@@ -143,37 +158,38 @@ __global__ void k_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R>
   const R *xi = it.f[F_U1R + o], *xn = n.f[F_U1R + o];
   const R *yi = it.f[F_U1T + o], *yn = n.f[F_U1T + o];
   const R *zi = it.f[F_U1P + o], *zn = n.f[F_U1P + o];
-  const double ir = S.irf[i], is = S.isc[j], ir2 = ir * ir;
-  const double ihr = S.ihr, iht = S.iht, ihp = S.ihp;
+  const V ir = (V)S.irf[i], is = (V)S.isc[j], ir2 = ir * ir;
+  const V ihr = (V)S.ihr, iht = (V)S.iht, ihp = (V)S.ihp;
+  const V rc0 = (V)S.rc[i], rcm = (V)S.rc[i - 1], rfp = (V)S.rf[i + 1], rfm = (V)S.rf[i - 1];
   const long SI = L.SI, P = L.P;
-  double X0 = H(xi, xn, q);
-  double Xrp = H(xi, xn, q + SI), Xrm = H(xi, xn, q - SI);
-  double Xtp = H(xi, xn, q + P), Xtm = H(xi, xn, q - P);
-  double Xpp = H(xi, xn, q + 1), Xpm = H(xi, xn, q - 1);
-  double Drr = (S.rc[i] * S.rc[i] * (Xrp - X0) - S.rc[i - 1] * S.rc[i - 1] * (X0 - Xrm)) * (ir2 * ihr * ihr);
-  double Dtt = (S.sf[j + 1] * (Xtp - X0) - S.sf[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
-  double Dpp = (Xpp - 2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
-  double extra = -2.0 * X0 * ir2 +
-                 2.0 * ir2 * ir * (S.rf[i + 1] * S.rf[i + 1] * Xrp - S.rf[i - 1] * S.rf[i - 1] * Xrm) * (0.5 * ihr);
-  double ar = (double)ax.A[0][q];
-  double at = avg4(ax.A[1], q - SI, q - SI + P, q, q + P);
-  double ap = avg4(ax.A[2], q - SI, q - SI + 1, q, q + 1);
-  double bt = havg4(yi, yn, q - SI, q - SI + P, q, q + P);
-  double bp = havg4(zi, zn, q - SI, q - SI + 1, q, q + 1);
-  double adv = ar * (Xrp - Xrm) * (0.5 * ihr) + at * (Xtp - Xtm) * (0.5 * ir * iht) +
-               ap * (Xpp - Xpm) * (0.5 * ir * is * ihp) - (at * bt + ap * bp) * ir;
-  double gradP = (pres(it, n, sys, q) - pres(it, n, sys, q - SI)) * ihr;
-  double Dc = divh(S, xi, xn, yi, yn, zi, zn, i, j, q);
-  double Dm = divh(S, xi, xn, yi, yn, zi, zn, i - 1, j, q - SI);
-  double gdiv = (Dc - Dm) * ihr;
-  double buoy = S.PrRa * 0.5 * (H(it.f[F_T], n.f[F_T], q - SI) + H(it.f[F_T], n.f[F_T], q));
-  double f = ax.fr ? (double)ax.fr[q] : 0.0;
-  double rate = S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * S.i2chi + buoy + f;
-  B[q] = (R)(S.dt * rate - ((double)xi[q] - (double)xn[q]));
+  V X0 = H<V>(xi, xn, q);
+  V Xrp = H<V>(xi, xn, q + SI), Xrm = H<V>(xi, xn, q - SI);
+  V Xtp = H<V>(xi, xn, q + P), Xtm = H<V>(xi, xn, q - P);
+  V Xpp = H<V>(xi, xn, q + 1), Xpm = H<V>(xi, xn, q - 1);
+  V Drr = (rc0 * rc0 * (Xrp - X0) - rcm * rcm * (X0 - Xrm)) * (ir2 * ihr * ihr);
+  V Dtt = ((V)S.sf[j + 1] * (Xtp - X0) - (V)S.sf[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
+  V Dpp = (Xpp - (V)2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
+  V extra = (V)-2.0 * X0 * ir2 + (V)2.0 * ir2 * ir * (rfp * rfp * Xrp - rfm * rfm * Xrm) * ((V)0.5 * ihr);
+  V ar = (V)ax.A[0][q];
+  V at = avg4<V>(ax.A[1], q - SI, q - SI + P, q, q + P);
+  V ap = avg4<V>(ax.A[2], q - SI, q - SI + 1, q, q + 1);
+  V bt = havg4<V>(yi, yn, q - SI, q - SI + P, q, q + P);
+  V bp = havg4<V>(zi, zn, q - SI, q - SI + 1, q, q + 1);
+  V adv = ar * (Xrp - Xrm) * ((V)0.5 * ihr) + at * (Xtp - Xtm) * ((V)0.5 * ir * iht) +
+          ap * (Xpp - Xpm) * ((V)0.5 * ir * is * ihp) - (at * bt + ap * bp) * ir;
+  V gradP = (V)((pres(it, n, sys, q) - pres(it, n, sys, q - SI)) * S.ihr);
+  V Dc = divh<V>(S, xi, xn, yi, yn, zi, zn, i, j, q);
+  V Dm = divh<V>(S, xi, xn, yi, yn, zi, zn, i - 1, j, q - SI);
+  V gdiv = (Dc - Dm) * ihr;
+  V buoy = (V)S.PrRa * (V)0.5 * (H<V>(it.f[F_T], n.f[F_T], q - SI) + H<V>(it.f[F_T], n.f[F_T], q));
+  V f = ax.fr ? (V)ax.fr[q] : (V)0.0;
+  V rate = (V)S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * (V)S.i2chi + buoy + f;
+  B[q] = (R)((V)S.dt * rate - ((V)xi[q] - (V)xn[q]));
 }
 
 template <typename R>
 __global__ void k_resid_ut(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
+  using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
   if (!decode_point(L, LT, patch_mask, p, i, j, k)) return;
@@ -182,43 +198,45 @@ __global__ void k_resid_ut(Shell S, int sys, State<R> it, State<R> n, StepAux<R>
   const R *wi = it.f[F_U1R + o], *wn = n.f[F_U1R + o];
   const R *xi = it.f[F_U1T + o], *xn = n.f[F_U1T + o];
   const R *zi = it.f[F_U1P + o], *zn = n.f[F_U1P + o];
-  const double ir = S.irc[i], is = S.isf[j], c = S.cf[j], ir2 = ir * ir;
-  const double ihr = S.ihr, iht = S.iht, ihp = S.ihp;
+  const V ir = (V)S.irc[i], is = (V)S.isf[j], c = (V)S.cf[j], ir2 = ir * ir;
+  const V ihr = (V)S.ihr, iht = (V)S.iht, ihp = (V)S.ihp;
+  const V rfp = (V)S.rf[i + 1], rf0 = (V)S.rf[i];
   const long SI = L.SI, P = L.P;
-  double X0 = H(xi, xn, q);
-  double Xrp = H(xi, xn, q + SI), Xrm = H(xi, xn, q - SI);
-  double Xtp = H(xi, xn, q + P), Xtm = H(xi, xn, q - P);
-  double Xpp = H(xi, xn, q + 1), Xpm = H(xi, xn, q - 1);
-  double Drr = (S.rf[i + 1] * S.rf[i + 1] * (Xrp - X0) - S.rf[i] * S.rf[i] * (X0 - Xrm)) * (ir2 * ihr * ihr);
-  double Dtt = (S.sc[j] * (Xtp - X0) - S.sc[j - 1] * (X0 - Xtm)) * (ir2 * is * iht * iht);
-  double Dpp = (Xpp - 2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
-  double W_j = 0.5 * (H(wi, wn, q) + H(wi, wn, q + SI));
-  double W_jm = 0.5 * (H(wi, wn, q - P) + H(wi, wn, q - P + SI));
-  double dW = (W_j - W_jm) * iht;
-  double qj = (S.rf[i + 1] * S.rf[i + 1] * H(wi, wn, q + SI) - S.rf[i] * S.rf[i] * H(wi, wn, q)) * ihr;
-  double qjm = (S.rf[i + 1] * S.rf[i + 1] * H(wi, wn, q + SI - P) - S.rf[i] * S.rf[i] * H(wi, wn, q - P)) * ihr;
-  double drr2W = 0.5 * (qj + qjm);
-  double extra = -X0 * ir2 * is * is +
-                 2.0 * c * ir2 * is * is * (S.sf[j + 1] * Xtp - S.sf[j - 1] * Xtm) * (0.5 * iht) +
-                 2.0 * ir2 * dW + 2.0 * c * ir2 * ir * is * drr2W;
-  double ar = avg4(ax.A[0], q - P, q - P + SI, q, q + SI);
-  double at = (double)ax.A[1][q];
-  double ap = avg4(ax.A[2], q - P, q - P + 1, q, q + 1);
-  double br = havg4(wi, wn, q - P, q - P + SI, q, q + SI);
-  double bp = havg4(zi, zn, q - P, q - P + 1, q, q + 1);
-  double adv = ar * (Xrp - Xrm) * (0.5 * ihr) + at * (Xtp - Xtm) * (0.5 * ir * iht) +
-               ap * (Xpp - Xpm) * (0.5 * ir * is * ihp) + (at * br - ap * bp * c * is) * ir;
-  double gradP = (pres(it, n, sys, q) - pres(it, n, sys, q - P)) * (ir * iht);
-  double Dc = divh(S, wi, wn, xi, xn, zi, zn, i, j, q);
-  double Dm = divh(S, wi, wn, xi, xn, zi, zn, i, j - 1, q - P);
-  double gdiv = (Dc - Dm) * (ir * iht);
-  double f = ax.ft ? (double)ax.ft[q] : 0.0;
-  double rate = S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * S.i2chi + f;
-  B[q] = (R)(S.dt * rate - ((double)xi[q] - (double)xn[q]));
+  V X0 = H<V>(xi, xn, q);
+  V Xrp = H<V>(xi, xn, q + SI), Xrm = H<V>(xi, xn, q - SI);
+  V Xtp = H<V>(xi, xn, q + P), Xtm = H<V>(xi, xn, q - P);
+  V Xpp = H<V>(xi, xn, q + 1), Xpm = H<V>(xi, xn, q - 1);
+  V Drr = (rfp * rfp * (Xrp - X0) - rf0 * rf0 * (X0 - Xrm)) * (ir2 * ihr * ihr);
+  V Dtt = ((V)S.sc[j] * (Xtp - X0) - (V)S.sc[j - 1] * (X0 - Xtm)) * (ir2 * is * iht * iht);
+  V Dpp = (Xpp - (V)2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
+  V W_j = (V)0.5 * (H<V>(wi, wn, q) + H<V>(wi, wn, q + SI));
+  V W_jm = (V)0.5 * (H<V>(wi, wn, q - P) + H<V>(wi, wn, q - P + SI));
+  V dW = (W_j - W_jm) * iht;
+  V qj = (rfp * rfp * H<V>(wi, wn, q + SI) - rf0 * rf0 * H<V>(wi, wn, q)) * ihr;
+  V qjm = (rfp * rfp * H<V>(wi, wn, q + SI - P) - rf0 * rf0 * H<V>(wi, wn, q - P)) * ihr;
+  V drr2W = (V)0.5 * (qj + qjm);
+  V extra = -X0 * ir2 * is * is +
+            (V)2.0 * c * ir2 * is * is * ((V)S.sf[j + 1] * Xtp - (V)S.sf[j - 1] * Xtm) * ((V)0.5 * iht) +
+            (V)2.0 * ir2 * dW + (V)2.0 * c * ir2 * ir * is * drr2W;
+  V ar = avg4<V>(ax.A[0], q - P, q - P + SI, q, q + SI);
+  V at = (V)ax.A[1][q];
+  V ap = avg4<V>(ax.A[2], q - P, q - P + 1, q, q + 1);
+  V br = havg4<V>(wi, wn, q - P, q - P + SI, q, q + SI);
+  V bp = havg4<V>(zi, zn, q - P, q - P + 1, q, q + 1);
+  V adv = ar * (Xrp - Xrm) * ((V)0.5 * ihr) + at * (Xtp - Xtm) * ((V)0.5 * ir * iht) +
+          ap * (Xpp - Xpm) * ((V)0.5 * ir * is * ihp) + (at * br - ap * bp * c * is) * ir;
+  V gradP = (V)((pres(it, n, sys, q) - pres(it, n, sys, q - P)) * (S.irc[i] * S.iht));
+  V Dc = divh<V>(S, wi, wn, xi, xn, zi, zn, i, j, q);
+  V Dm = divh<V>(S, wi, wn, xi, xn, zi, zn, i, j - 1, q - P);
+  V gdiv = (Dc - Dm) * (ir * iht);
+  V f = ax.ft ? (V)ax.ft[q] : (V)0.0;
+  V rate = (V)S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * (V)S.i2chi + f;
+  B[q] = (R)((V)S.dt * rate - ((V)xi[q] - (V)xn[q]));
 }
 
 template <typename R>
 __global__ void k_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
+  using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
   if (!decode_point(L, LP, patch_mask, p, i, j, k)) return;
@@ -227,39 +245,41 @@ __global__ void k_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R>
   const R *wi = it.f[F_U1R + o], *wn = n.f[F_U1R + o];
   const R *yi = it.f[F_U1T + o], *yn = n.f[F_U1T + o];
   const R *xi = it.f[F_U1P + o], *xn = n.f[F_U1P + o];
-  const double ir = S.irc[i], is = S.isc[j], c = S.cc[j], ir2 = ir * ir;
-  const double ihr = S.ihr, iht = S.iht, ihp = S.ihp;
+  const V ir = (V)S.irc[i], is = (V)S.isc[j], c = (V)S.cc[j], ir2 = ir * ir;
+  const V ihr = (V)S.ihr, iht = (V)S.iht, ihp = (V)S.ihp;
+  const V rfp = (V)S.rf[i + 1], rf0 = (V)S.rf[i];
   const long SI = L.SI, P = L.P;
-  double X0 = H(xi, xn, q);
-  double Xrp = H(xi, xn, q + SI), Xrm = H(xi, xn, q - SI);
-  double Xtp = H(xi, xn, q + P), Xtm = H(xi, xn, q - P);
-  double Xpp = H(xi, xn, q + 1), Xpm = H(xi, xn, q - 1);
-  double Drr = (S.rf[i + 1] * S.rf[i + 1] * (Xrp - X0) - S.rf[i] * S.rf[i] * (X0 - Xrm)) * (ir2 * ihr * ihr);
-  double Dtt = (S.sf[j + 1] * (Xtp - X0) - S.sf[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
-  double Dpp = (Xpp - 2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
-  double W_k = 0.5 * (H(wi, wn, q) + H(wi, wn, q + SI));
-  double W_km = 0.5 * (H(wi, wn, q - 1) + H(wi, wn, q - 1 + SI));
-  double Y_k = 0.5 * (H(yi, yn, q) + H(yi, yn, q + P));
-  double Y_km = 0.5 * (H(yi, yn, q - 1) + H(yi, yn, q - 1 + P));
-  double extra = -X0 * ir2 * is * is + 2.0 * ir2 * is * (W_k - W_km) * ihp +
-                 2.0 * c * ir2 * is * is * (Y_k - Y_km) * ihp;
-  double ar = avg4(ax.A[0], q - 1, q - 1 + SI, q, q + SI);
-  double at = avg4(ax.A[1], q - 1, q - 1 + P, q, q + P);
-  double ap = (double)ax.A[2][q];
-  double br = havg4(wi, wn, q - 1, q - 1 + SI, q, q + SI);
-  double bt = havg4(yi, yn, q - 1, q - 1 + P, q, q + P);
-  double adv = ar * (Xrp - Xrm) * (0.5 * ihr) + at * (Xtp - Xtm) * (0.5 * ir * iht) +
-               ap * (Xpp - Xpm) * (0.5 * ir * is * ihp) + (ap * br + ap * bt * c * is) * ir;
-  double gradP = (pres(it, n, sys, q) - pres(it, n, sys, q - 1)) * (ir * is * ihp);
-  double Dc = divh(S, wi, wn, yi, yn, xi, xn, i, j, q);
-  double Dm = divh(S, wi, wn, yi, yn, xi, xn, i, j, q - 1);
-  double gdiv = (Dc - Dm) * (ir * is * ihp);
-  double f = ax.fp ? (double)ax.fp[q] : 0.0;
-  double rate = S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * S.i2chi + f;
-  B[q] = (R)(S.dt * rate - ((double)xi[q] - (double)xn[q]));
+  V X0 = H<V>(xi, xn, q);
+  V Xrp = H<V>(xi, xn, q + SI), Xrm = H<V>(xi, xn, q - SI);
+  V Xtp = H<V>(xi, xn, q + P), Xtm = H<V>(xi, xn, q - P);
+  V Xpp = H<V>(xi, xn, q + 1), Xpm = H<V>(xi, xn, q - 1);
+  V Drr = (rfp * rfp * (Xrp - X0) - rf0 * rf0 * (X0 - Xrm)) * (ir2 * ihr * ihr);
+  V Dtt = ((V)S.sf[j + 1] * (Xtp - X0) - (V)S.sf[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
+  V Dpp = (Xpp - (V)2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
+  V W_k = (V)0.5 * (H<V>(wi, wn, q) + H<V>(wi, wn, q + SI));
+  V W_km = (V)0.5 * (H<V>(wi, wn, q - 1) + H<V>(wi, wn, q - 1 + SI));
+  V Y_k = (V)0.5 * (H<V>(yi, yn, q) + H<V>(yi, yn, q + P));
+  V Y_km = (V)0.5 * (H<V>(yi, yn, q - 1) + H<V>(yi, yn, q - 1 + P));
+  V extra = -X0 * ir2 * is * is + (V)2.0 * ir2 * is * (W_k - W_km) * ihp +
+            (V)2.0 * c * ir2 * is * is * (Y_k - Y_km) * ihp;
+  V ar = avg4<V>(ax.A[0], q - 1, q - 1 + SI, q, q + SI);
+  V at = avg4<V>(ax.A[1], q - 1, q - 1 + P, q, q + P);
+  V ap = (V)ax.A[2][q];
+  V br = havg4<V>(wi, wn, q - 1, q - 1 + SI, q, q + SI);
+  V bt = havg4<V>(yi, yn, q - 1, q - 1 + P, q, q + P);
+  V adv = ar * (Xrp - Xrm) * ((V)0.5 * ihr) + at * (Xtp - Xtm) * ((V)0.5 * ir * iht) +
+          ap * (Xpp - Xpm) * ((V)0.5 * ir * is * ihp) + (ap * br + ap * bt * c * is) * ir;
+  V gradP = (V)((pres(it, n, sys, q) - pres(it, n, sys, q - 1)) * (S.irc[i] * S.isc[j] * S.ihp));
+  V Dc = divh<V>(S, wi, wn, yi, yn, xi, xn, i, j, q);
+  V Dm = divh<V>(S, wi, wn, yi, yn, xi, xn, i, j, q - 1);
+  V gdiv = (Dc - Dm) * (ir * is * ihp);
+  V f = ax.fp ? (V)ax.fp[q] : (V)0.0;
+  V rate = (V)S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * (V)S.i2chi + f;
+  B[q] = (R)((V)S.dt * rate - ((V)xi[q] - (V)xn[q]));
 }
 
 // ----------------------------------------------------------------- pressure
+// FP64 divergence and FP64 pressure accumulation in both forms.
 template <typename R>
 __global__ void k_pressure(Shell S, int sys, State<R> it, State<R> n, double *norm, int patch_mask) {
   const Layout &L = S.L;
@@ -269,19 +289,19 @@ __global__ void k_pressure(Shell S, int sys, State<R> it, State<R> n, double *no
   if (ok) {
     long q = lidx(L, p, i, j, k);
     int o = (sys == 1) ? 0 : 4;
-    double D = divh(S, it.f[F_U1R + o], n.f[F_U1R + o], it.f[F_U1T + o], n.f[F_U1T + o], it.f[F_U1P + o],
-                    n.f[F_U1P + o], i, j, q);
+    double D = divh<double>(S, it.f[F_U1R + o], n.f[F_U1R + o], it.f[F_U1T + o], n.f[F_U1T + o],
+                            it.f[F_U1P + o], n.f[F_U1P + o], i, j, q);
     double pnew;
-    R *dst;
+    double *dst;
     if (sys == 1) {
-      pnew = (double)n.f[F_P1][q] - D * (2.0 * S.i2chi);
-      dst = it.f[F_P1];
+      pnew = n.p[0][q] - D * (2.0 * S.i2chi);
+      dst = it.p[0];
     } else {
-      pnew = (double)n.f[F_P2][q] + ((double)it.f[F_P1][q] - (double)n.f[F_P1][q]) - D * (2.0 * S.i2chi);
-      dst = it.f[F_P2];
+      pnew = n.p[1][q] + (it.p[0][q] - n.p[0][q]) - D * (2.0 * S.i2chi);
+      dst = it.p[1];
     }
-    double c = pnew - (double)dst[q];
-    dst[q] = (R)pnew;
+    double c = pnew - dst[q];
+    dst[q] = pnew;
     bool ringcell = (j == 0 || j == L.Nt - 1 || k == 0 || k == L.Np - 1);
     if (!(S.step7 && ringcell)) {
       double r = S.rc[i];
@@ -302,7 +322,7 @@ __device__ __forceinline__ void user_extent(const Layout &L, int loc, int &ni, i
 }
 
 template <typename R>
-__global__ void k_unpack(Layout L, int loc, const double *src, R *dst) {
+__global__ void k_unpack(Layout L, int loc, const double *src, R *dst, const double *bg) {
   int ni, nj, nk;
   user_extent(L, loc, ni, nj, nk);
   long n = 2L * ni * nj * nk;
@@ -313,12 +333,14 @@ __global__ void k_unpack(Layout L, int loc, const double *src, R *dst) {
     t /= nj;
     int i = (int)(t % ni);
     int p = (int)(t / ni);
-    dst[lidx(L, p, i, j, k)] = (R)src[u];
+    double v = src[u];
+    if (bg) v -= bg[i];
+    dst[lidx(L, p, i, j, k)] = (R)v;
   }
 }
 
 template <typename R>
-__global__ void k_pack(Layout L, int loc, const R *src, double *dst) {
+__global__ void k_pack(Layout L, int loc, const R *src, double *dst, const double *bg) {
   int ni, nj, nk;
   user_extent(L, loc, ni, nj, nk);
   long n = 2L * ni * nj * nk;
@@ -329,7 +351,9 @@ __global__ void k_pack(Layout L, int loc, const R *src, double *dst) {
     t /= nj;
     int i = (int)(t % ni);
     int p = (int)(t / ni);
-    dst[u] = (double)src[lidx(L, p, i, j, k)];
+    double v = (double)src[lidx(L, p, i, j, k)];
+    if (bg) v += bg[i];
+    dst[u] = v;
   }
 }
 
@@ -344,6 +368,8 @@ int flat_blocks(long n) {
   long b = (n + 255) / 256;
   return (int)(b < 152L * 16 ? b : 152L * 16);
 }
+
+long user_max(const Layout &L) { return 2L * (L.Nr + 1) * (L.Nt + 1) * (L.Np + 1); }
 
 }  // namespace
 
@@ -379,28 +405,33 @@ void Launch<R>::pressure(const Shell &S, int sys, State<R> it, State<R> n, doubl
 }
 
 template <typename R>
-void Launch<R>::unpack(const Layout &L, int loc, const double *src, R *dst, cudaStream_t st) {
-  long n = 2L * (L.Nr + 1) * (L.Nt + 1) * (L.Np + 1);
-  k_unpack<R><<<flat_blocks(n), 256, 0, st>>>(L, loc, src, dst);
+void Launch<R>::unpack(const Layout &L, int loc, const double *src, R *dst, const double *bg, cudaStream_t st) {
+  k_unpack<R><<<flat_blocks(user_max(L)), 256, 0, st>>>(L, loc, src, dst, bg);
 }
 
 template <typename R>
-void Launch<R>::pack(const Layout &L, int loc, const R *src, double *dst, cudaStream_t st) {
-  long n = 2L * (L.Nr + 1) * (L.Nt + 1) * (L.Np + 1);
-  k_pack<R><<<flat_blocks(n), 256, 0, st>>>(L, loc, src, dst);
+void Launch<R>::pack(const Layout &L, int loc, const R *src, double *dst, const double *bg, cudaStream_t st) {
+  k_pack<R><<<flat_blocks(user_max(L)), 256, 0, st>>>(L, loc, src, dst, bg);
 }
 
-template struct StepAux<double>;
-template void Launch<double>::extrapolate(const Layout &, State<double>, State<double>, State<double>, double *[3],
-                                          cudaStream_t);
-template void Launch<double>::combine_forcing(long, Modes<double>, double *[4], cudaStream_t);
-template void Launch<double>::resid_T(const Shell &, State<double>, State<double>, StepAux<double>, double *, int,
-                                      cudaStream_t);
-template void Launch<double>::resid_u(const Shell &, int, int, State<double>, State<double>, StepAux<double>,
-                                      double *, int, cudaStream_t);
-template void Launch<double>::pressure(const Shell &, int, State<double>, State<double>, double *, int,
-                                       cudaStream_t);
-template void Launch<double>::unpack(const Layout &, int, const double *, double *, cudaStream_t);
-template void Launch<double>::pack(const Layout &, int, const double *, double *, cudaStream_t);
+void unpack_p(const Layout &L, const double *src, double *dst, const double *bg, cudaStream_t st) {
+  k_unpack<double><<<flat_blocks(user_max(L)), 256, 0, st>>>(L, LC, src, dst, bg);
+}
+
+void pack_p(const Layout &L, const double *src, double *dst, const double *bg, cudaStream_t st) {
+  k_pack<double><<<flat_blocks(user_max(L)), 256, 0, st>>>(L, LC, src, dst, bg);
+}
+
+#define YS_INST_STENCIL(R)                                                                                         \
+  template void Launch<R>::extrapolate(const Layout &, State<R>, State<R>, State<R>, R *[3], cudaStream_t);       \
+  template void Launch<R>::combine_forcing(long, Modes<R>, R *[4], cudaStream_t);                                  \
+  template void Launch<R>::resid_T(const Shell &, State<R>, State<R>, StepAux<R>, R *, int, cudaStream_t);        \
+  template void Launch<R>::resid_u(const Shell &, int, int, State<R>, State<R>, StepAux<R>, R *, int,             \
+                                   cudaStream_t);                                                                  \
+  template void Launch<R>::pressure(const Shell &, int, State<R>, State<R>, double *, int, cudaStream_t);         \
+  template void Launch<R>::unpack(const Layout &, int, const double *, R *, const double *, cudaStream_t);        \
+  template void Launch<R>::pack(const Layout &, int, const R *, double *, const double *, cudaStream_t);
+YS_INST_STENCIL(double)
+YS_INST_STENCIL(float)
 
 }  // namespace ys

@@ -59,77 +59,81 @@ __device__ __forceinline__ void advecting(const Shell &S, const StepAux<R> &ax, 
 
 // Coefficients (lo, di, up) of (I - dt/2 Ahat_dir) at point (i, j, k) of `loc`
 // (divisions replaced by FP64 reciprocal metric tables).
-template <typename R>
+template <typename V, typename R>
 __device__ __forceinline__ void coef(const Shell &S, const StepAux<R> &ax, int loc, int dir, int i, int j, long q,
-                                     double &lo, double &di, double &up) {
-  const double ihr = S.ihr, iht = S.iht, ihp = S.ihp;
-  const double nu = (loc == LC) ? S.kappa : S.nu;
-  double ar, at, ap;
-  advecting(S, ax, loc, q, ar, at, ap);
-  const double ir = (loc == LR) ? S.irf[i] : S.irc[i];
-  const double is = (loc == LT) ? S.isf[j] : S.isc[j];
-  const double ir2 = ir * ir;
-  double cm, c0, cp;
+                                     V &lo, V &di, V &up) {
+  const V ihr = (V)S.ihr, iht = (V)S.iht, ihp = (V)S.ihp;
+  const V nu = (V)((loc == LC) ? S.kappa : S.nu);
+  double ar_d, at_d, ap_d;
+  advecting(S, ax, loc, q, ar_d, at_d, ap_d);
+  const V ar = (V)ar_d, at = (V)at_d, ap = (V)ap_d;
+  const V ir = (V)((loc == LR) ? S.irf[i] : S.irc[i]);
+  const V is = (V)((loc == LT) ? S.isf[j] : S.isc[j]);
+  const V ir2 = ir * ir;
+  const V rc0 = (V)S.rc[i], rcm = (V)S.rc[i - 1], rf0 = (V)S.rf[i], rfp = (V)S.rf[i + 1], rfm = (V)S.rf[i - 1];
+  const V sc0 = (V)S.sc[j], scm = (V)S.sc[j - 1], sf0 = (V)S.sf[j], sfp = (V)S.sf[j + 1], sfm = (V)S.sf[j - 1];
+  V cm, c0, cp;
   if (dir == DR) {
-    double cp_d, cm_d;
+    V cp_d, cm_d;
     if (loc == LR) {
-      cp_d = S.rc[i] * S.rc[i] * (ir2 * ihr * ihr);
-      cm_d = S.rc[i - 1] * S.rc[i - 1] * (ir2 * ihr * ihr);
+      cp_d = rc0 * rc0 * (ir2 * ihr * ihr);
+      cm_d = rcm * rcm * (ir2 * ihr * ihr);
     } else {
-      cp_d = S.rf[i + 1] * S.rf[i + 1] * (ir2 * ihr * ihr);
-      cm_d = S.rf[i] * S.rf[i] * (ir2 * ihr * ihr);
+      cp_d = rfp * rfp * (ir2 * ihr * ihr);
+      cm_d = rf0 * rf0 * (ir2 * ihr * ihr);
     }
-    cm = nu * cm_d + ar * (0.5 * ihr);
+    cm = nu * cm_d + ar * ((V)0.5 * ihr);
     c0 = -nu * (cp_d + cm_d);
-    cp = nu * cp_d - ar * (0.5 * ihr);
+    cp = nu * cp_d - ar * ((V)0.5 * ihr);
     if (loc == LR) {
-      cm = cm - nu * S.rf[i - 1] * S.rf[i - 1] * (ir2 * ir * ihr);
-      cp = cp + nu * S.rf[i + 1] * S.rf[i + 1] * (ir2 * ir * ihr);
-      c0 = c0 - nu * 2.0 * ir2;
-      const double k = S.i2chi, irm = S.irc[i - 1], irc = S.irc[i];
-      cm = cm + k * S.rf[i - 1] * S.rf[i - 1] * (irm * irm * ihr * ihr);
-      c0 = c0 - k * (S.rf[i] * S.rf[i] * (irc * irc * ihr * ihr) + S.rf[i] * S.rf[i] * (irm * irm * ihr * ihr));
-      cp = cp + k * S.rf[i + 1] * S.rf[i + 1] * (irc * irc * ihr * ihr);
+      cm = cm - nu * rfm * rfm * (ir2 * ir * ihr);
+      cp = cp + nu * rfp * rfp * (ir2 * ir * ihr);
+      c0 = c0 - nu * (V)2.0 * ir2;
+      const V k = (V)S.i2chi, irm = (V)S.irc[i - 1], irc = (V)S.irc[i];
+      cm = cm + k * rfm * rfm * (irm * irm * ihr * ihr);
+      c0 = c0 - k * (rf0 * rf0 * (irc * irc * ihr * ihr) + rf0 * rf0 * (irm * irm * ihr * ihr));
+      cp = cp + k * rfp * rfp * (irc * irc * ihr * ihr);
     }
   } else if (dir == DT) {
-    double cp_d, cm_d;
+    V cp_d, cm_d;
+    const V iR1sq = (V)S.iR1sq;
     if (loc == LT) {
-      cp_d = S.sc[j] * (S.iR1sq * is * iht * iht);
-      cm_d = S.sc[j - 1] * (S.iR1sq * is * iht * iht);
+      cp_d = sc0 * (iR1sq * is * iht * iht);
+      cm_d = scm * (iR1sq * is * iht * iht);
     } else {
-      cp_d = S.sf[j + 1] * (S.iR1sq * is * iht * iht);
-      cm_d = S.sf[j] * (S.iR1sq * is * iht * iht);
+      cp_d = sfp * (iR1sq * is * iht * iht);
+      cm_d = sf0 * (iR1sq * is * iht * iht);
     }
-    cm = nu * cm_d + at * (0.5 * ir * iht);
+    cm = nu * cm_d + at * ((V)0.5 * ir * iht);
     c0 = -nu * (cp_d + cm_d);
-    cp = nu * cp_d - at * (0.5 * ir * iht);
+    cp = nu * cp_d - at * ((V)0.5 * ir * iht);
     if (loc == LT) {
-      const double c = S.cf[j], s = S.sf[j];
-      const double qq = c * ir2 * is * is * iht;
-      cm = cm - nu * qq * S.sf[j - 1];
-      cp = cp + nu * qq * S.sf[j + 1];
+      const V c = (V)S.cf[j], s = sf0;
+      const V qq = c * ir2 * is * is * iht;
+      cm = cm - nu * qq * sfm;
+      cp = cp + nu * qq * sfp;
       c0 = c0 - nu * ir2 * is * is;
-      const double k = S.i2chi, isc0 = S.isc[j], iscm = S.isc[j - 1];
-      cp = cp + k * S.sf[j + 1] * (ir2 * isc0 * iht * iht);
+      const V k = (V)S.i2chi, isc0 = (V)S.isc[j], iscm = (V)S.isc[j - 1];
+      cp = cp + k * sfp * (ir2 * isc0 * iht * iht);
       c0 = c0 - k * (s * (ir2 * isc0 * iht * iht) + s * (ir2 * iscm * iht * iht));
-      cm = cm + k * S.sf[j - 1] * (ir2 * iscm * iht * iht);
+      cm = cm + k * sfm * (ir2 * iscm * iht * iht);
     }
   } else {
-    const double cpm = S.cphi;
-    cm = nu * cpm + ap * (0.5 * ir * is * ihp);
-    c0 = -2.0 * nu * cpm;
-    cp = nu * cpm - ap * (0.5 * ir * is * ihp);
+    const V cpm = (V)S.cphi;
+    cm = nu * cpm + ap * ((V)0.5 * ir * is * ihp);
+    c0 = (V)-2.0 * nu * cpm;
+    cp = nu * cpm - ap * ((V)0.5 * ir * is * ihp);
     if (loc == LP) {
       c0 = c0 - nu * ir2 * is * is;
-      const double qq = S.i2chi * ir2 * is * is * ihp * ihp;
+      const V qq = (V)S.i2chi * ir2 * is * is * ihp * ihp;
       cm = cm + qq;
-      c0 = c0 - 2.0 * qq;
+      c0 = c0 - (V)2.0 * qq;
       cp = cp + qq;
     }
   }
-  lo = -0.5 * S.dt * cm;
-  di = 1.0 - 0.5 * S.dt * c0;
-  up = -0.5 * S.dt * cp;
+  lo = (V)-0.5 * (V)S.dt * cm;
+  di = (V)1.0 - (V)0.5 * (V)S.dt * c0;
+  up = (V)-0.5 * (V)S.dt * cp;
 }
 
 // Line of a (loc, dir) sweep: thread (lane, row) -> patch p, first point
@@ -197,7 +201,7 @@ __global__ void k_sweep(Shell S, int loc, int dir, int final, StepAux<R> ax, R *
     for (int m = m0; m < m1; ++m, q += step) {
       int ii = (dir == DR) ? m : i, jj = (dir == DT) ? m : j;
       double lo, di, up;
-      coef(S, ax, loc, dir, ii, jj, q, lo, di, up);
+      coef<double>(S, ax, loc, dir, ii, jj, q, lo, di, up);
       if (m == m0) {
         if (reflect) di -= lo;
         lo = 0.0;
@@ -239,32 +243,33 @@ __global__ void k_sweep(Shell S, int loc, int dir, int final, StepAux<R> ax, R *
 }
 
 // Per-step LU factorisation of one factor (I - dt/2 Ahat_dir) of `loc` on
-// every line: the line matrices depend only on the advecting velocity, fixed
+// every line, in the storage type's arithmetic from the FP64 metric tables: the line matrices depend only on the advecting velocity, fixed
 // for the whole step, so both AC systems and every Schwarz iteration reuse
 // them.  Row m stores the sub-diagonal lo_m, the reciprocal pivot
 // 1/(di_m - lo_m c'_{m-1}) and c'_m = up_m / pivot_m.
 template <typename R>
 __global__ void k_factorize(Shell S, int loc, int dir, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask) {
+  using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   const Line ln = decode_line(L, loc, dir, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
   if (!ln.valid || !((patch_mask >> ln.p) & 1)) return;
   const bool reflect = (dir == DR) && (loc != LR);
-  double cprev = 0.0;
+  V cprev = (V)0.0;
   long q = lidx(L, ln.p, ln.i, ln.j, ln.k);
   for (int m = ln.m0; m < ln.m1; ++m, q += ln.step) {
     int ii = (dir == DR) ? m : ln.i, jj = (dir == DT) ? m : ln.j;
-    double lo, di, up;
-    coef(S, ax, loc, dir, ii, jj, q, lo, di, up);
+    V lo, di, up;
+    coef<V>(S, ax, loc, dir, ii, jj, q, lo, di, up);
     if (m == ln.m0) {
       if (reflect) di -= lo;
-      lo = 0.0;
+      lo = (V)0.0;
     }
     if (m == ln.m1 - 1) {
       if (reflect) di -= up;
-      up = 0.0;
+      up = (V)0.0;
     }
-    double inv = 1.0 / (di - lo * cprev);
-    double c = up * inv;
+    V inv = (V)1.0 / (di - lo * cprev);
+    V c = up * inv;
     Lo[q] = (R)lo;
     Iv[q] = (R)inv;
     Cp[q] = (R)c;
@@ -279,32 +284,33 @@ __global__ void k_factorize(Shell S, int loc, int dir, StepAux<R> ax, R *Lo, R *
 template <typename R>
 __global__ void k_solve(Shell S, int loc, int dir, int final, const R *__restrict__ Lo, const R *__restrict__ Iv,
                         const R *__restrict__ Cp, R *B, R *dst, double *norm, int slot, int patch_mask) {
+  using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   const Line ln = decode_line(L, loc, dir, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
   double contrib = 0.0;
   if (ln.valid && ((patch_mask >> ln.p) & 1)) {
     const long step = ln.step;
     long q = lidx(L, ln.p, ln.i, ln.j, ln.k);
-    double d = 0.0;
+    V d = (V)0.0;
     for (int m = ln.m0; m < ln.m1; ++m, q += step) {
-      d = ((double)B[q] - (double)Lo[q] * d) * (double)Iv[q];
+      d = ((V)B[q] - (V)Lo[q] * d) * (V)Iv[q];
       B[q] = (R)d;
     }
     q -= step;
-    double x = d;
+    V x = d;
     for (int m = ln.m1 - 1;; --m) {
       if (final) {
-        dst[q] = (R)((double)dst[q] + x);
+        dst[q] = (R)((V)dst[q] + x);
         int ii = (dir == DR) ? m : ln.i, jj = (dir == DT) ? m : ln.j;
         double r = (loc == LR) ? S.rf[ii] : S.rc[ii];
         double s = (loc == LT) ? S.sf[jj] : S.sc[jj];
-        contrib += r * r * s * S.hr * S.ht * S.hp * x * x;
+        contrib += r * r * s * S.hr * S.ht * S.hp * (double)x * (double)x;
       } else {
         B[q] = (R)x;
       }
       if (m == ln.m0) break;
       q -= step;
-      x = (double)B[q] - (double)Cp[q] * x;
+      x = (V)B[q] - (V)Cp[q] * x;
     }
   }
   if (final) {
@@ -344,10 +350,12 @@ void Launch<R>::solve(const Shell &S, int loc, int dir, bool final, const R *Lo,
                                                         patch_mask);
 }
 
-template void Launch<double>::factorize(const Shell &, int, int, StepAux<double>, double *, double *, double *,
-                                        int, cudaStream_t);
-template void Launch<double>::solve(const Shell &, int, int, bool, const double *, const double *, const double *,
-                                    double *, double *, double *, int, int, cudaStream_t);
+#define YS_INST_SWEEP(R)                                                                                          \
+  template void Launch<R>::factorize(const Shell &, int, int, StepAux<R>, R *, R *, R *, int, cudaStream_t);       \
+  template void Launch<R>::solve(const Shell &, int, int, bool, const R *, const R *, const R *, R *, R *, double *, \
+                                 int, int, cudaStream_t);
+YS_INST_SWEEP(double)
+YS_INST_SWEEP(float)
 template void Launch<double>::sweep(const Shell &, int, int, bool, StepAux<double>, double *, double *, double *,
                                     double *, int, int, cudaStream_t);
 

@@ -44,7 +44,11 @@ struct Shell {
   double i2chi;             // 1/(2 chi)
   double iR1sq;             // 1/R1^2 (modified theta operator)
   double cphi;              // 1/(R1^2 sin^2(theta_1) h_phi^2) (modified phi operator)
-  double T_in, T_out;       // wall temperatures
+  double T_in, T_out;       // wall temperatures (of the stored temperature)
+  // deviation form (mixed precision): the stored temperature is T - T_c with
+  // T_c the discrete conductive profile; its rate gets the FP64 source
+  // Tc_lap[i] - a_r Tc_dr[i] (null in the FP64 form)
+  const double *Tc_lap, *Tc_dr;
   int step7;
 };
 

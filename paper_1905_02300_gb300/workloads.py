@@ -558,3 +558,17 @@ def shell_ensemble(seed: int = 4, n: int = 64, nr_max: int = 64, nth_max: int = 
         Pr = float(rng.choice([0.7, 1.0, 7.0]))
         out.append(dict(R1=ratio, R2=1.0, Nr=Nr, Nth=Nth, Nph=3 * Nth, Ra=Ra, Pr=Pr))
     return out
+
+
+def convection_initial(spec: Spec, Pr: float, Ra: float, seed: int = 3, amp: float = 1e-3,
+                       T_in: float = 1.0, T_out: float = 0.0):
+    """Thermal-convection start (user layout): T = conductive profile + seeded
+    perturbation, u = 0, and p in discrete hydrostatic balance with T along
+    each radial column, p_{i} - p_{i-1} = h_r Pr Ra (T_{i-1} + T_i)/2, p_0 = 0
+    (buoyancy Pr Ra T e_r balanced by the pressure gradient)."""
+    T = conductive_profile(spec, T_in, T_out) + convection_perturbation(spec, seed, amp)
+    p = np.zeros_like(T)
+    for i in range(1, spec.Nr):
+        p[:, i] = p[:, i - 1] + spec.hr * Pr * Ra * 0.5 * (T[:, i - 1] + T[:, i])
+    return {"T": T, "ur": np.zeros(spec.shape("r")), "uth": np.zeros(spec.shape("t")),
+            "uph": np.zeros(spec.shape("p")), "p": p}
