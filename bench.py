@@ -36,6 +36,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -135,6 +137,177 @@ def oracle_sample(n, K, steps):
     return cells * steps / el, el
 
 
+def ensemble_shells(seed, n, nr_max, nth_max, ys, precision):
+    """Seeded uneven shells (config c4 distribution): convection start with a
+    hot inner wall, dt = 0.5 h_min^2 per shell, h_min the smallest of h_r,
+    R1 h_theta and R1 sin(theta_1) h_phi (inside the fixed-iteration stability
+    limit dt < chi h^2)."""
+    from paper_1905_02300_gb300 import workloads as W
+    out = []
+    for idx, sp in enumerate(W.shell_ensemble(seed=seed, n=n, nr_max=nr_max, nth_max=nth_max)):
+        spec = W.Spec(sp["R1"], sp["R2"], sp["Nr"], sp["Nth"], sp["Nph"])
+        hmin = min(spec.hr, sp["R1"] * spec.hth, sp["R1"] * math.sin(spec.th0) * spec.hph)
+        kw = dict(R1=sp["R1"], R2=sp["R2"], Pr=sp["Pr"], Ra=sp["Ra"], Nr=sp["Nr"], Nth=sp["Nth"], Nph=sp["Nph"],
+                  dt=0.5 * hmin * hmin, T_inner=1.0, T_outer=0.0, precision=precision)
+        out.append((kw, W.convection_initial(spec, sp["Pr"], sp["Ra"], seed=seed + idx, kmax=3)))
+    return out
+
+
+def run_ensemble(args):
+    """Config c4: 64 uneven shells in one batch (one launch per kernel class,
+    one CUDA graph per step, autotuned lines per block), mixed precision,
+    against the plain single-shell FP64 path running the same shells one at a
+    time."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1905_02300_gb300 import ys
+    torch.cuda.set_device(0)
+    shells = ensemble_shells(4, 64, 64, 96, ys, ys.YS_MIXED)
+    cells = sum(2 * kw["Nr"] * kw["Nth"] * kw["Nph"] for kw, _ in shells)
+    b = ys.Batch(len(shells), precision=ys.YS_MIXED, n_schwarz=3)
+    solvers = []
+    for kw, f0 in shells:
+        s = ys.Solver(**kw)
+        s.set_fields_dict(0, f0)
+        b.add(s)
+        solvers.append(s)
+    chosen = b.autotune(trial_steps=2)
+    b.step(args.warmup)
+    b.sync()
+    st = torch.cuda.ExternalStream(b.stream_handle())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    e0.record(st)
+    b.step(args.steps)
+    e1.record(st)
+    b.sync()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    value = cells * args.steps / (ms / 1e3)
+    finite = all(np.isfinite(b.norms(slot)).all() for slot in list(b.members))
+    # plain FP64 single-shell path, one shell at a time, same shells
+    t_fp64 = 0.0
+    for kw, f0 in shells:
+        kw64 = dict(kw, precision=ys.YS_FP64)
+        s = ys.Solver(**kw64)
+        s.set_fields_dict(0, f0)
+        s.step(1, 3)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        sst = torch.cuda.Stream()
+        s.set_stream(sst.cuda_stream)
+        ev[0].record(sst)
+        s.step(args.steps, 3)
+        ev[1].record(sst)
+        torch.cuda.synchronize()
+        t_fp64 += ev[0].elapsed_time(ev[1]) / 1e3
+        s.close()
+    fp64_value = cells * args.steps / t_fp64
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"ensemble of {len(shells)} seeded uneven shells (Nr 16-64, Nth 16-96, "
+                                   f"Nph=3Nth, R1/R2 0.35-0.6, Ra 1e3-1e6, Pr 0.7/1/7), K=3, mixed FP32/FP64, "
+                                   f"one batched launch per kernel class, CUDA graph per step",
+                       "cells_total": cells, "lines_per_block": chosen,
+                       "launches_per_step": b.launches_per_step()},
+            "plain_fp64_one_at_a_time": {"value": fp64_value, "unit": UNIT},
+            "speedup_vs_plain_fp64": value / fp64_value, "all_finite": bool(finite), "clocks": clk}
+    print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
+def run_serving(args):
+    """Config c5, scaled: Poisson arrivals of shell simulations from the c4
+    distribution (Nr <= 64, Nth <= 96), N ~ U{20..80} steps, at 0.8 of the
+    measured batched capacity; p50/p99 time to completion and aggregate
+    cell-updates/s against the same trace served FIFO one at a time by the
+    plain FP64 path (replayed with each request's measured FP64 run time)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1905_02300_gb300 import ys
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(5)
+    R = args.requests
+    shells = ensemble_shells(5, R, 64, 96, ys, ys.YS_MIXED)
+    steps = [int(rng.integers(20, 81)) for _ in range(R)]
+    work = [2 * kw["Nr"] * kw["Nth"] * kw["Nph"] * n for (kw, _), n in zip(shells, steps)]
+    # batched capacity estimate from a short batch of the same shells
+    b = ys.Batch(R, precision=ys.YS_MIXED, n_schwarz=3)
+    for kw, f0 in shells[:16]:
+        s = ys.Solver(**kw)
+        s.set_fields_dict(0, f0)
+        b.add(s)
+    b.step(2)
+    b.sync()
+    t0 = time.perf_counter()
+    b.step(5)
+    b.sync()
+    cap = sum(2 * kw["Nr"] * kw["Nth"] * kw["Nph"] for kw, _ in shells[:16]) * 5 / (time.perf_counter() - t0)
+    b.close()
+    lam = 0.8 * cap / float(np.mean(work))           # requests per second
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=R))
+    srv = ys.Server(hbm_budget_bytes=64 << 30, max_slots=R)
+    tickets = [None] * R
+    done = {}
+    t_start = time.perf_counter()
+    i = 0
+    while len(done) < R:
+        now = time.perf_counter() - t_start
+        while i < R and arrivals[i] <= now:
+            kw, f0 = shells[i]
+            tickets[i] = srv.submit(f0, steps[i], **kw)
+            i += 1
+        for j in range(i):
+            if j in done:
+                continue
+            st_, f, lat, rc = srv.poll(tickets[j])
+            if st_ >= 2:
+                done[j] = (st_, lat, rc)
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t_start
+    stats = srv.stats()
+    srv.close()
+    lats = np.array([done[j][1] for j in range(R)])
+    ok = sum(1 for j in range(R) if done[j][0] == 2)
+    # FIFO one at a time with the plain FP64 path: measured run time per request
+    run_t = []
+    for (kw, f0), n in zip(shells, steps):
+        s = ys.Solver(**dict(kw, precision=ys.YS_FP64))
+        s.set_fields_dict(0, f0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(n, 3)
+        s.stats()
+        run_t.append(time.perf_counter() - t0)
+        s.close()
+    free_at, fifo_lat = 0.0, []
+    for a, rt in zip(arrivals, run_t):
+        start = max(a, free_at)
+        free_at = start + rt
+        fifo_lat.append(free_at - a)
+    fifo_lat = np.array(fifo_lat)
+    line = {"metric": "served p50/p99 time to completion; cell-updates/s", "unit": "s",
+            "value": float(np.percentile(lats, 50)), "p50_s": float(np.percentile(lats, 50)),
+            "p99_s": float(np.percentile(lats, 99)), "higher_is_better": False, "n_gpus": 1,
+            "requests": R, "completed": ok, "aggregate_cell_updates_per_s": float(sum(work) / wall),
+            "arrival_rate_per_s": lam, "batched_capacity_estimate": cap,
+            "fifo_plain_fp64": {"p50_s": float(np.percentile(fifo_lat, 50)),
+                                "p99_s": float(np.percentile(fifo_lat, 99)),
+                                "aggregate_cell_updates_per_s": float(sum(work) / max(free_at, arrivals[-1]))},
+            "data": "synthetic", "dtype": "f32+f64",
+            "config": {"workload": f"{R} Poisson-arriving shells (c4 distribution, seed 5), N in [20, 80] steps, "
+                                   f"K=3, mixed FP32/FP64, continuous batching"},
+            "server_steps": stats["steps"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -169,9 +342,16 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="shell", choices=["shell", "ensemble", "serving"])
+    ap.add_argument("--requests", type=int, default=32)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble":
+        import numpy as np  # noqa: F401
+        return run_ensemble(args)
+    if args.workload == "serving":
+        return run_serving(args)
 
     import numpy as np
     import torch

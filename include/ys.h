@@ -203,6 +203,69 @@ int ys_factor_solve_static(const ys_params *prm, int loc, const double *A_r, con
 
 int ys_destroy(ys_ctx *c);
 
+/* ------------------------------------------------------------------------
+ * Batched ensembles.  A batch advances many independent shells (contexts
+ * created with ys_create_ex and filled with ys_set_fields, uneven sizes,
+ * Ra, Pr allowed) together: every kernel class of the AC step is one launch
+ * over all member shells, and a whole step is replayed from one captured CUDA
+ * graph that stays valid while shells join and leave.  Members must share the
+ * batch's precision, use additive Schwarz and have no forcing modes; all run
+ * n_schwarz iterations per step.  A shell's fields do not depend on the other
+ * members (bitwise).  While a context is in a batch only the batch steps it. */
+typedef struct ys_batch ys_batch;
+
+/* capacity: 1..4096 slots; precision YS_FP64 or YS_MIXED; n_schwarz >= 1. */
+int ys_batch_create(int capacity, int precision, int n_schwarz, ys_batch **out);
+/* Add a context; *slot receives its slot.  YS_EBUSY when full, YS_EINVAL on a
+ * precision / mode / forcing mismatch.  The caller keeps ownership. */
+int ys_batch_add(ys_batch *b, ys_ctx *c, int *slot);
+/* Remove the shell in `slot`; its context (time, step count, levels) is
+ * brought up to date and returned in *c for ys_get_fields or ys_step. */
+int ys_batch_remove(ys_batch *b, int slot, ys_ctx **c);
+/* Advance every member n_steps steps (asynchronous on the batch's stream). */
+int ys_batch_step(ys_batch *b, int n_steps);
+int ys_batch_sync(ys_batch *b);
+/* l2 increment norms (YS_NFIELDS) of the member's last iteration. */
+int ys_batch_norms(ys_batch *b, int slot, double *norms);
+/* Threads per block of the line-solve launches (lines per block): 32, 64,
+ * 128 (default) or 256. */
+int ys_batch_set_line_threads(ys_batch *b, int threads);
+/* Time trial_steps steps with each lines-per-block choice and keep the
+ * fastest; the trial steps advance the members.  *chosen gets the choice. */
+int ys_batch_autotune(ys_batch *b, int trial_steps, int *chosen);
+/* kernel launches in one batched step (independent of the member count) */
+long ys_batch_launches_per_step(ys_batch *b);
+/* the cudaStream_t the batch runs on (for event timing by the caller) */
+void *ys_batch_stream(ys_batch *b);
+int ys_batch_destroy(ys_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Serving with continuous batching.  Requests (one shell simulation each)
+ * are admitted first come first served while a slot is free and the
+ * device-memory footprint of the admitted shells stays within
+ * hbm_budget_bytes; a worker thread advances all admitted shells one batched
+ * step at a time, admits waiting requests and retires finished ones at every
+ * step boundary.  Thread-safe.  The first request fixes the precision and
+ * n_schwarz of the server; later requests must match (YS_EINVAL). */
+typedef struct ys_server ys_server;
+
+int ys_server_create(size_t hbm_budget_bytes, int max_slots, ys_server **out);
+/* Queue a simulation: parameters (additive Schwarz, schwarz_tol 0), initial
+ * fields packed as [T | ur | uth | uph | p] in the field layouts above
+ * (copied), number of steps.  *ticket identifies it.  YS_EBUSY when the queue
+ * is full; YS_EINVAL if it can never fit the budget. */
+int ys_submit(ys_server *s, const ys_params *p, const double *init_fields, int n_steps, int n_schwarz,
+              uint64_t *ticket);
+/* State of a request: *state = 0 queued, 1 running, 2 done, 3 failed.  Returns
+ * YS_EAGAIN until it is done; when done, copies level 0 packed like the input
+ * to out_fields (if not NULL) and the time from submission to completion to
+ * *latency_s.  A failed request (e.g. NaN data) returns its error code; other
+ * requests are not affected. */
+int ys_poll(ys_server *s, uint64_t ticket, int *state, double *out_fields, double *latency_s);
+/* Batched steps run, cell-updates done, requests running and queued. */
+int ys_server_stats(ys_server *s, long *steps_run, double *cell_updates, int *running, int *queued);
+int ys_server_destroy(ys_server *s);
+
 const char *ys_strerror(int code);
 
 #ifdef __cplusplus

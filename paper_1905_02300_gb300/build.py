@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libys.so")
-SOURCES = ["api.cu", "kernels_stencil.cu", "kernels_sweep.cu", "kernels_exchange.cu", "geometry.cpp"]
+SOURCES = ["api.cu", "batch.cu", "kernels_stencil.cu", "kernels_sweep.cu", "kernels_exchange.cu", "geometry.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

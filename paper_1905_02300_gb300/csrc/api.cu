@@ -21,70 +21,17 @@
 #include <vector>
 
 #include "../../include/ys.h"
-#include "geometry.h"
-#include "kernels.cuh"
+#include "ctx.h"
 
 using namespace ys;
 
 namespace {
 
-// kernel classes for timing
-enum KClass {
-  K_EXTRAP = 0, K_FORCE, K_EXCH, K_WALLS, K_RING, K_RES_T, K_RES_U, K_SWEEP_R, K_SWEEP_T, K_SWEEP_P, K_PRES,
-  K_PACK, K_FACTOR, K_NUM
-};
 const char *kClassNames[K_NUM] = {"extrapolate", "forcing",  "exchange", "walls",   "ring",     "resid_T",
                                   "resid_u",     "sweep_r",  "sweep_t",  "sweep_p", "pressure", "pack",
                                   "factorize"};
 
-struct ProfRec {
-  int cls;
-  cudaEvent_t a, b;
-};
-
-// Typed device state of one shell.
-template <typename R>
-struct Fields {
-  State<R> lev[3];           // level n, level n-1, iterate
-  R *A[3];                   // advecting velocity
-  R *fcomb[4];               // forcing at t_n + dt/2
-  R *B, *Cs;                 // work field, Thomas c' (unused by the stored-LU path)
-  R *fac[4][3][3];           // per-step LU factors: fac[loc][dir] = {lo, 1/pivot, c'}
-  R *modes[kMaxModes][4];    // forcing modes
-};
-
 }  // namespace
-
-struct ys_ctx {
-  ys_params prm;
-  GridGeo geo;
-  Layout L;
-  Shell S;
-  cudaStream_t own_stream = nullptr, stream = nullptr;
-  void *dmem = nullptr;
-  size_t dbytes = 0;
-  void *modes_mem[kMaxModes] = {};
-  Fields<double> *f64 = nullptr;
-  Fields<float> *f32 = nullptr;
-  XEntry *xdev = nullptr;
-  XTables X;
-  double *norm = nullptr;     // YS_NFIELDS accumulators
-  double *stage = nullptr;    // host-layout staging (device)
-  double *T_bg = nullptr;     // deviation backgrounds per radial index (mixed form), else null
-  double *p_bg = nullptr;
-  int mode_fn[kMaxModes] = {};
-  int mode_set[kMaxModes] = {};
-  int nmodes_set = 0;
-  double t = 0.0;
-  long steps_done = 0;
-  int level1_set = 0;
-  double norms_host[YS_NFIELDS] = {};
-  int iters_last = 0;
-  long launches = 0;
-  int prof_on = 0;
-  std::vector<ProfRec> prof;
-  size_t prof_used = 0;
-};
 
 namespace {
 

@@ -1,0 +1,826 @@
+// Batched ensembles and the serving loop.
+//
+// A batch advances many independent shells of uneven sizes together: every
+// kernel class of the AC step (Sec. 3.3, Sec. 4) is ONE persistent launch over
+// all member shells.  Each launch walks a work map kept in device memory: per
+// shell, the prefix sum of its block count and its grid width, so a CTA finds
+// the shell and block it executes by binary search.  Time-level rotation is a
+// device kernel, so one step, captured once as a CUDA graph, stays valid while
+// shells join and leave (only the device-resident maps and descriptors change).
+// Per-shell arithmetic and block decomposition do not depend on the other
+// members, so a shell's fields are the same alone and in any mix.
+//
+// The server admits requests by device-memory footprint and free slots,
+// advances every admitted shell one batched step at a time, and retires shells
+// whose step count is reached (continuous batching: admissions and
+// retirements happen at every step boundary).
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "bodies.cuh"
+#include "ctx.h"
+
+using namespace ys;
+
+namespace ys {
+
+template <typename R>
+struct ShellDev {
+  Shell S;
+  State<R> lev[3];   // physical buffers; level n = lev[rot], n-1 = lev[rot+1], iterate = lev[rot+2] (mod 3)
+  R *A[3];
+  R *B;
+  R *fac[4][3][3];
+  double *norm;      // YS_NFIELDS accumulators of this shell
+  XTables X;
+  int rot;
+  int step7;
+};
+
+// work maps: offs[cap + 1] prefix sums of per-shell block counts, gx[cap] grid widths
+struct WorkMap {
+  const int *offs;
+  const int *gx;
+};
+
+enum MapId {
+  M_EXTRAP = 0, M_EX0, M_EX1, M_EX2, M_EX3, M_WALLS, M_RING, M_RC, M_RR, M_RT, M_RP, M_LINE0, M_NUM = M_LINE0 + 12
+};
+
+namespace {
+
+constexpr int kExtrapChunk = 4096;
+constexpr int kMaxCap = 4096;
+
+__device__ __forceinline__ int find_shell(const int *offs, int cap, int w) {
+  int lo = 0, hi = cap;   // offs[lo] <= w < offs[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (offs[mid] <= w)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <typename R>
+__device__ __forceinline__ void roles(const ShellDev<R> &D, State<R> &n, State<R> &nm1, State<R> &it) {
+  int r = D.rot;
+  n = D.lev[r];
+  nm1 = D.lev[(r + 1) % 3];
+  it = D.lev[(r + 2) % 3];
+}
+
+template <typename R>
+__device__ __forceinline__ StepAux<R> aux_of(const ShellDev<R> &D) {
+  StepAux<R> ax;
+  for (int a = 0; a < 3; ++a) ax.A[a] = D.A[a];
+  ax.fT = ax.fr = ax.ft = ax.fp = nullptr;
+  return ax;
+}
+
+#define YS_BATCH_LOOP(map, cap)                               \
+  const int total_w = (map).offs[cap];                       \
+  for (int w = blockIdx.x; w < total_w; w += gridDim.x) {    \
+    const int s = find_shell((map).offs, cap, w);            \
+    const int local = w - (map).offs[s];                     \
+    const int gxs = (map).gx[s];                             \
+    const int bx = local % gxs, by = local / gxs;            \
+    const ShellDev<R> &D = sh[s];                            \
+    State<R> n, nm1, it;                                     \
+    roles(D, n, nm1, it);
+
+template <typename R>
+__global__ void kb_extrapolate(const ShellDev<R> *sh, WorkMap map, int cap) {
+  YS_BATCH_LOOP(map, cap)
+  (void)by;
+  long q0 = (long)bx * kExtrapChunk, q1 = q0 + kExtrapChunk;
+  if (q1 > D.S.L.total) q1 = D.S.L.total;
+  bd::body_extrapolate(q0, q1, it, n, nm1, D.A[0], D.A[1], D.A[2]);
+  }
+}
+
+template <typename R>
+__global__ void kb_factorize(const ShellDev<R> *sh, WorkMap map, int cap, int loc, int dir) {
+  YS_BATCH_LOOP(map, cap)
+  R *const *F = D.fac[loc][dir];
+  bd::body_factorize(D.S, loc, dir, aux_of(D), F[0], F[1], F[2], 3, bx, by);
+  }
+}
+
+template <typename R>
+__global__ void kb_solve(const ShellDev<R> *sh, WorkMap map, int cap, int loc, int dir, int final, int slot) {
+  YS_BATCH_LOOP(map, cap)
+  R *const *F = D.fac[loc][dir];
+  bd::body_solve(D.S, loc, dir, final, F[0], F[1], F[2], D.B, it.f[slot], D.norm, slot, 3, bx, by);
+  }
+}
+
+template <typename R>
+__global__ void kb_resid_T(const ShellDev<R> *sh, WorkMap map, int cap) {
+  YS_BATCH_LOOP(map, cap)
+  bd::body_resid_T(D.S, it, n, aux_of(D), D.B, 3, bx, by);
+  }
+}
+
+template <typename R>
+__global__ void kb_resid_u(const ShellDev<R> *sh, WorkMap map, int cap, int sys, int comp) {
+  YS_BATCH_LOOP(map, cap)
+  if (comp == 0)
+    bd::body_resid_ur(D.S, sys, it, n, aux_of(D), D.B, 3, bx, by);
+  else if (comp == 1)
+    bd::body_resid_ut(D.S, sys, it, n, aux_of(D), D.B, 3, bx, by);
+  else
+    bd::body_resid_up(D.S, sys, it, n, aux_of(D), D.B, 3, bx, by);
+  }
+}
+
+template <typename R>
+__global__ void kb_pressure(const ShellDev<R> *sh, WorkMap map, int cap, int sys) {
+  YS_BATCH_LOOP(map, cap)
+  bd::body_pressure(D.S, sys, it, n, D.norm, 3, bx, by);
+  }
+}
+
+template <typename R>
+__global__ void kb_exchange(const ShellDev<R> *sh, WorkMap map, int cap, int kind) {
+  YS_BATCH_LOOP(map, cap)
+  if (kind == XP && !D.step7) continue;
+  bd::body_exchange(D.S, D.X.e[kind], D.X.n[kind], kind, it, 3, bx, by);
+  }
+}
+
+template <typename R>
+__global__ void kb_walls(const ShellDev<R> *sh, WorkMap map, int cap) {
+  YS_BATCH_LOOP(map, cap)
+  bd::body_walls(D.S, it, 3, bx, by);
+  }
+}
+
+// rotate time levels of every active shell: n-1 <- n, n <- iterate, iterate <- n-1
+template <typename R>
+__global__ void kb_rotate(ShellDev<R> *sh, const int *active, int cap) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < cap && active[s]) sh[s].rot = (sh[s].rot + 2) % 3;
+}
+
+int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
+
+// per-shell block grid (gx, gy) of a map
+void grid_of(const ys_ctx *c, int map, int tpb_line, int &gx, int &gy) {
+  const Layout &L = c->L;
+  gy = 1;
+  if (map == M_EXTRAP) {
+    gx = cdiv(L.total, kExtrapChunk);
+  } else if (map >= M_EX0 && map <= M_EX3) {
+    int kind = map - M_EX0;
+    int ni = (kind == XUR) ? L.Nr - 1 : L.Nr;
+    gx = cdiv((long)c->X.n[kind] * ni, 256);
+    gy = 2;
+  } else if (map == M_WALLS) {
+    gx = cdiv((long)(L.Nt + 2) * (L.Np + 2), 256);
+    gy = 2;
+  } else if (map == M_RING) {
+    gx = cdiv((long)c->X.n[XP] * L.Nr, 256);
+    gy = 2;
+  } else if (map >= M_RC && map <= M_RP) {
+    int loc = map - M_RC;
+    int ni = L.Nr - (loc == LR), nj = L.Nt - (loc == LT), nk = L.Np - (loc == LP);
+    gx = cdiv(nk, 128);
+    gy = 2 * ni * nj;
+  } else {
+    int loc = (map - M_LINE0) / 3, dir = (map - M_LINE0) % 3;
+    int ni = L.Nr - (loc == LR), nj = L.Nt - (loc == LT), nk = L.Np - (loc == LP);
+    if (dir == DR) {
+      gx = cdiv(nk, tpb_line);
+      gy = 2 * nj;
+    } else if (dir == DT) {
+      gx = cdiv(nk, tpb_line);
+      gy = 2 * ni;
+    } else {
+      gx = cdiv(nj, tpb_line);
+      gy = 2 * ni;
+    }
+  }
+}
+
+}  // namespace
+
+}  // namespace ys
+
+// ---------------------------------------------------------------------------
+// batch engine
+
+struct ys_batch {
+  int cap = 0, precision = 0, K = 3, tpb_line = 128;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<ys_ctx *> slot;
+  std::vector<int> rot;           // host mirror of the device rotation counters
+  std::vector<long> steps;        // steps taken in the batch, per slot
+  void *shells = nullptr;         // ShellDev<R>[cap] (device)
+  int *maps = nullptr;            // M_NUM x (2 cap + 1) ints (device)
+  int *active = nullptr;          // cap ints (device)
+  double *norms = nullptr;        // cap x YS_NFIELDS (device)
+  std::vector<int> hmaps;
+  cudaGraphExec_t exec = nullptr;
+  bool dirty = true;              // maps / descriptors need upload
+  long launches = 0;
+};
+
+namespace {
+
+WorkMap map_of(ys_batch *b, int m) {
+  WorkMap w;
+  w.offs = b->maps + (size_t)m * (2 * b->cap + 1);
+  w.gx = w.offs + b->cap + 1;
+  return w;
+}
+
+int grid_size(int tpb) { return 152 * (2048 / tpb > 16 ? 16 : 2048 / tpb); }
+
+template <typename R>
+Fields<R> &FF(ys_ctx *c);
+template <>
+Fields<double> &FF<double>(ys_ctx *c) {
+  return *c->f64;
+}
+template <>
+Fields<float> &FF<float>(ys_ctx *c) {
+  return *c->f32;
+}
+
+template <typename R>
+ShellDev<R> describe(ys_batch *b, int s) {
+  ys_ctx *c = b->slot[s];
+  Fields<R> &D = FF<R>(c);
+  ShellDev<R> d{};
+  d.S = c->S;
+  for (int l = 0; l < 3; ++l) d.lev[l] = D.lev[l];
+  for (int a = 0; a < 3; ++a) d.A[a] = D.A[a];
+  d.B = D.B;
+  std::memcpy(d.fac, D.fac, sizeof(d.fac));
+  d.norm = b->norms + (size_t)s * YS_NFIELDS;
+  d.X = c->X;
+  d.rot = b->rot[s];
+  d.step7 = c->prm.step7;
+  return d;
+}
+
+// upload descriptors, active flags and work maps (between steps only)
+template <typename R>
+int upload(ys_batch *b) {
+  const int cap = b->cap;
+  std::vector<ShellDev<R>> hd(cap);
+  std::vector<int> act(cap, 0);
+  for (int s = 0; s < cap; ++s)
+    if (b->slot[s]) {
+      hd[s] = describe<R>(b, s);
+      act[s] = 1;
+    }
+  b->hmaps.assign((size_t)M_NUM * (2 * cap + 1), 0);
+  for (int m = 0; m < M_NUM; ++m) {
+    int *offs = b->hmaps.data() + (size_t)m * (2 * cap + 1);
+    int *gx = offs + cap + 1;
+    long acc = 0;
+    for (int s = 0; s < cap; ++s) {
+      offs[s] = (int)acc;
+      int gxs = 1, gys = 0;
+      if (b->slot[s]) grid_of(b->slot[s], m, b->tpb_line, gxs, gys);
+      gx[s] = gxs;
+      acc += (long)gxs * gys;
+      if (acc > 0x7fffffffL) return YS_EINVAL;
+    }
+    offs[cap] = (int)acc;
+  }
+  cudaMemcpyAsync(b->shells, hd.data(), sizeof(ShellDev<R>) * cap, cudaMemcpyHostToDevice, b->stream);
+  cudaMemcpyAsync(b->active, act.data(), sizeof(int) * cap, cudaMemcpyHostToDevice, b->stream);
+  cudaMemcpyAsync(b->maps, b->hmaps.data(), sizeof(int) * b->hmaps.size(), cudaMemcpyHostToDevice, b->stream);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return YS_ECUDA;
+  b->dirty = false;
+  return YS_OK;
+}
+
+const int kOrderB[4][3] = {{DR, DT, DP}, {DT, DP, DR}, {DP, DR, DT}, {DR, DT, DP}};
+
+// one AC step of every member shell (additive Schwarz, K iterations)
+template <typename R>
+void enqueue_step(ys_batch *b) {
+  const int cap = b->cap;
+  const ShellDev<R> *sh = (const ShellDev<R> *)b->shells;
+  cudaStream_t st = b->stream;
+  const int g128 = grid_size(128), g256 = grid_size(256), gl = grid_size(b->tpb_line);
+  long nl = 0;
+  kb_extrapolate<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_EXTRAP), cap);
+  ++nl;
+  for (int loc = LC; loc <= LP; ++loc)
+    for (int dir = DR; dir <= DP; ++dir) {
+      kb_factorize<R><<<gl, b->tpb_line, 0, st>>>(sh, map_of(b, M_LINE0 + 3 * loc + dir), cap, loc, dir);
+      ++nl;
+    }
+  auto solve = [&](int loc, int slot) {
+    for (int s = 0; s < 3; ++s) {
+      int dir = kOrderB[loc][s];
+      kb_solve<R><<<gl, b->tpb_line, 0, st>>>(sh, map_of(b, M_LINE0 + 3 * loc + dir), cap, loc, dir, s == 2, slot);
+      ++nl;
+    }
+  };
+  auto exchange = [&]() {
+    for (int kind = XT; kind <= XUP; ++kind) {
+      kb_exchange<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_EX0 + kind), cap, kind);
+      ++nl;
+    }
+    kb_walls<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_WALLS), cap);
+    ++nl;
+  };
+  for (int k = 0; k < b->K; ++k) {
+    cudaMemsetAsync(b->norms, 0, sizeof(double) * YS_NFIELDS * cap, st);
+    exchange();
+    kb_resid_T<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_RC), cap);
+    ++nl;
+    solve(LC, F_T);
+    for (int sys = 1; sys <= 2; ++sys) {
+      int o = (sys == 1) ? 0 : 4;
+      for (int comp = 0; comp < 3; ++comp) {
+        kb_resid_u<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_RR + comp), cap, sys, comp);
+        ++nl;
+        solve(LR + comp, F_U1R + comp + o);
+      }
+      kb_pressure<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_RC), cap, sys);
+      ++nl;
+    }
+    kb_exchange<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_RING), cap, XP);
+    ++nl;
+  }
+  exchange();
+  kb_exchange<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_RING), cap, XP);
+  kb_rotate<R><<<(cap + 127) / 128, 128, 0, st>>>((ShellDev<R> *)b->shells, b->active, cap);
+  nl += 2;
+  b->launches = nl;
+}
+
+template <typename R>
+int capture(ys_batch *b) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  cudaGraph_t g;
+  if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return YS_ECUDA;
+  enqueue_step<R>(b);
+  if (cudaStreamEndCapture(b->stream, &g) != cudaSuccess) return YS_ECUDA;
+  cudaError_t e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  return e == cudaSuccess ? YS_OK : YS_ECUDA;
+}
+
+template <typename R>
+int batch_step(ys_batch *b, int n) {
+  if (b->dirty) {
+    int rc = upload<R>(b);
+    if (rc) return rc;
+  }
+  if (!b->exec) {
+    int rc = capture<R>(b);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < n; ++i)
+    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return YS_ECUDA;
+  for (int s = 0; s < b->cap; ++s)
+    if (b->slot[s]) {
+      b->rot[s] = (b->rot[s] + 2 * n) % 3;
+      b->steps[s] += n;
+    }
+  return YS_OK;
+}
+
+// hand a context back: apply the device rotation to its host-side level order
+template <typename R>
+void give_back(ys_batch *b, int s) {
+  ys_ctx *c = b->slot[s];
+  Fields<R> &D = FF<R>(c);
+  int r = b->rot[s];
+  State<R> l[3] = {D.lev[r], D.lev[(r + 1) % 3], D.lev[(r + 2) % 3]};
+  for (int k = 0; k < 3; ++k) D.lev[k] = l[k];
+  c->t += b->steps[s] * c->prm.dt;
+  c->steps_done += b->steps[s];
+  c->iters_last = b->K;
+  double h[YS_NFIELDS];
+  cudaMemcpy(h, b->norms + (size_t)s * YS_NFIELDS, sizeof(h), cudaMemcpyDeviceToHost);
+  for (int f = 0; f < YS_NFIELDS; ++f) c->norms_host[f] = std::sqrt(h[f]);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ys_batch_create(int capacity, int precision, int n_schwarz, ys_batch **out) {
+  if (!out || capacity < 1 || capacity > kMaxCap || n_schwarz < 1) return YS_EINVAL;
+  if (precision != YS_FP64 && precision != YS_MIXED) return YS_EINVAL;
+  *out = nullptr;
+  ys_batch *b = new (std::nothrow) ys_batch();
+  if (!b) return YS_ENOMEM;
+  b->cap = capacity;
+  b->precision = precision;
+  b->K = n_schwarz;
+  b->slot.assign(capacity, nullptr);
+  b->rot.assign(capacity, 0);
+  b->steps.assign(capacity, 0);
+  cudaGetDevice(&b->dev);
+  size_t shell_bytes = (precision == YS_MIXED ? sizeof(ShellDev<float>) : sizeof(ShellDev<double>)) * capacity;
+  size_t map_bytes = sizeof(int) * (size_t)M_NUM * (2 * capacity + 1);
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&b->shells, shell_bytes) != cudaSuccess || cudaMalloc(&b->maps, map_bytes) != cudaSuccess ||
+      cudaMalloc(&b->active, sizeof(int) * capacity) != cudaSuccess ||
+      cudaMalloc(&b->norms, sizeof(double) * YS_NFIELDS * capacity) != cudaSuccess) {
+    cudaGetLastError();
+    ys_batch_destroy(b);
+    return YS_ENOMEM;
+  }
+  *out = b;
+  return YS_OK;
+}
+
+int ys_batch_add(ys_batch *b, ys_ctx *c, int *slot) {
+  if (!b || !c || !slot) return YS_EINVAL;
+  if ((c->prm.precision == YS_MIXED) != (b->precision == YS_MIXED)) return YS_EINVAL;
+  if (c->prm.schwarz_mode != YS_ADDITIVE || c->nmodes_set > 0) return YS_EINVAL;
+  int s = -1;
+  for (int i = 0; i < b->cap; ++i)
+    if (!b->slot[i]) {
+      s = i;
+      break;
+    }
+  if (s < 0) return YS_EBUSY;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return YS_ECUDA;
+  b->slot[s] = c;
+  b->rot[s] = 0;
+  b->steps[s] = 0;
+  b->dirty = true;
+  *slot = s;
+  return YS_OK;
+}
+
+int ys_batch_remove(ys_batch *b, int s, ys_ctx **out) {
+  if (!b || s < 0 || s >= b->cap || !b->slot[s]) return YS_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return YS_ECUDA;
+  if (b->precision == YS_MIXED)
+    give_back<float>(b, s);
+  else
+    give_back<double>(b, s);
+  if (out) *out = b->slot[s];
+  b->slot[s] = nullptr;
+  b->dirty = true;
+  return YS_OK;
+}
+
+int ys_batch_step(ys_batch *b, int n_steps) {
+  if (!b || n_steps < 0) return YS_EINVAL;
+  int rc = (b->precision == YS_MIXED) ? batch_step<float>(b, n_steps) : batch_step<double>(b, n_steps);
+  if (rc) return rc;
+  return cudaGetLastError() == cudaSuccess ? YS_OK : YS_ECUDA;
+}
+
+int ys_batch_sync(ys_batch *b) {
+  if (!b) return YS_EINVAL;
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? YS_OK : YS_ECUDA;
+}
+
+int ys_batch_norms(ys_batch *b, int s, double *norms) {
+  if (!b || s < 0 || s >= b->cap || !b->slot[s] || !norms) return YS_EINVAL;
+  double h[YS_NFIELDS];
+  if (cudaMemcpyAsync(h, b->norms + (size_t)s * YS_NFIELDS, sizeof(h), cudaMemcpyDeviceToHost, b->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return YS_ECUDA;
+  for (int f = 0; f < YS_NFIELDS; ++f) norms[f] = std::sqrt(h[f]);
+  return YS_OK;
+}
+
+int ys_batch_set_line_threads(ys_batch *b, int tpb) {
+  if (!b || (tpb != 32 && tpb != 64 && tpb != 128 && tpb != 256)) return YS_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return YS_ECUDA;
+  if (tpb != b->tpb_line) {
+    b->tpb_line = tpb;
+    b->dirty = true;
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+  }
+  return YS_OK;
+}
+
+long ys_batch_launches_per_step(ys_batch *b) { return b ? b->launches : -1; }
+
+void *ys_batch_stream(ys_batch *b) { return b ? (void *)b->stream : nullptr; }
+
+int ys_batch_autotune(ys_batch *b, int trial_steps, int *chosen) {
+  if (!b || trial_steps < 1) return YS_EINVAL;
+  const int cand[4] = {32, 64, 128, 256};
+  float best = 1e30f;
+  int best_t = b->tpb_line;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // trial steps advance the member shells like ordinary steps
+  for (int c = 0; c < 4; ++c) {
+    int rc = ys_batch_set_line_threads(b, cand[c]);
+    if (!rc) rc = ys_batch_step(b, 1);   // upload and capture outside the timing
+    if (rc) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc;
+    }
+    cudaEventRecord(e0, b->stream);
+    rc = ys_batch_step(b, trial_steps);
+    cudaEventRecord(e1, b->stream);
+    if (rc || cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc ? rc : YS_ECUDA;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_t = cand[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int rc = ys_batch_set_line_threads(b, best_t);
+  if (chosen) *chosen = best_t;
+  return rc;
+}
+
+int ys_batch_destroy(ys_batch *b) {
+  if (!b) return YS_EINVAL;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  cudaFree(b->shells);
+  cudaFree(b->maps);
+  cudaFree(b->active);
+  cudaFree(b->norms);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return YS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// serving loop
+
+namespace {
+
+struct Request {
+  uint64_t ticket;
+  ys_params prm;
+  std::vector<double> init;     // packed [T | ur | uth | uph | p]
+  std::vector<double> result;   // same layout, valid when DONE
+  int n_steps = 0;
+  int state = 0;                // 0 queued, 1 running, 2 done, 3 failed
+  int error = 0;
+  int slot = -1;
+  long done_steps = 0;
+  ys_ctx *ctx = nullptr;
+  size_t bytes = 0;
+  std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+size_t packed_len(const ys_params &p) {
+  size_t c = 2ul * p.Nr * p.Nth * p.Nph;
+  return 2 * c + 2ul * (p.Nr + 1) * p.Nth * p.Nph + 2ul * p.Nr * (p.Nth + 1) * p.Nph +
+         2ul * p.Nr * p.Nth * (p.Nph + 1);
+}
+
+void unpack_fields(const ys_params &p, const double *buf, const double *f[5]) {
+  size_t c = 2ul * p.Nr * p.Nth * p.Nph;
+  f[0] = buf;
+  f[1] = f[0] + c;
+  f[2] = f[1] + 2ul * (p.Nr + 1) * p.Nth * p.Nph;
+  f[3] = f[2] + 2ul * p.Nr * (p.Nth + 1) * p.Nph;
+  f[4] = f[3] + 2ul * p.Nr * p.Nth * (p.Nph + 1);
+}
+
+}  // namespace
+
+struct ys_server {
+  size_t budget = 0, used = 0;
+  int max_slots = 0, K = 0, precision = YS_MIXED;
+  ys_batch *batch = nullptr;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request *> queue;
+  std::map<uint64_t, Request *> all;
+  std::vector<Request *> running;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  int dev = 0;
+  std::thread worker;
+  long steps_run = 0;
+  double cell_updates = 0.0;
+};
+
+namespace {
+
+constexpr size_t kMaxQueue = 4096;
+
+void server_loop(ys_server *S) {
+  cudaSetDevice(S->dev);
+  for (;;) {
+    std::vector<Request *> admit;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] { return S->stop || !S->queue.empty() || !S->running.empty(); });
+      if (S->stop) return;
+      // admission by free slots and device-memory budget, first come first served
+      while (!S->queue.empty() && (int)(S->running.size() + admit.size()) < S->max_slots) {
+        Request *r = S->queue.front();
+        if (S->used + r->bytes > S->budget) break;
+        S->queue.pop_front();
+        S->used += r->bytes;
+        admit.push_back(r);
+      }
+    }
+    for (Request *r : admit) {
+      const double *f[5];
+      unpack_fields(r->prm, r->init.data(), f);
+      int rc = ys_create_ex(&r->prm, &r->ctx);
+      if (!rc) rc = ys_set_fields(r->ctx, 0, f[0], f[1], f[2], f[3], f[4]);
+      if (!rc) rc = ys_batch_add(S->batch, r->ctx, &r->slot);
+      std::lock_guard<std::mutex> lk(S->mu);
+      if (rc) {
+        if (r->ctx) ys_destroy(r->ctx);
+        r->ctx = nullptr;
+        r->state = 3;
+        r->error = rc;
+        S->used -= r->bytes;
+        r->t_done = std::chrono::steady_clock::now();
+      } else {
+        r->state = 1;
+        S->running.push_back(r);
+      }
+    }
+    std::vector<Request *> run;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      run = S->running;
+    }
+    if (run.empty()) continue;
+    int rc = ys_batch_step(S->batch, 1);
+    if (!rc) rc = ys_batch_sync(S->batch);
+    S->steps_run++;
+    std::vector<Request *> finished;
+    for (Request *r : run) {
+      r->done_steps++;
+      S->cell_updates += 2.0 * r->prm.Nr * r->prm.Nth * r->prm.Nph;
+      double nrm[YS_NFIELDS];
+      bool bad = rc != 0;
+      if (!bad && ys_batch_norms(S->batch, r->slot, nrm) == YS_OK)
+        for (int k = 0; k < YS_NFIELDS; ++k)
+          if (!std::isfinite(nrm[k])) bad = true;
+      if (bad || r->done_steps >= r->n_steps) {
+        ys_ctx *c = nullptr;
+        ys_batch_remove(S->batch, r->slot, &c);
+        int err = bad ? (rc ? rc : YS_EDIVERGED) : 0;
+        if (!bad) {
+          r->result.resize(packed_len(r->prm));
+          const double *f[5];
+          unpack_fields(r->prm, r->result.data(), f);
+          err = ys_get_fields(c, 0, (double *)f[0], (double *)f[1], (double *)f[2], (double *)f[3], (double *)f[4],
+                              nullptr);
+        }
+        ys_destroy(c);
+        r->ctx = nullptr;
+        r->error = err;
+        finished.push_back(r);
+      }
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (Request *r : finished) {
+      r->state = r->error ? 3 : 2;
+      r->t_done = std::chrono::steady_clock::now();
+      r->init.clear();
+      r->init.shrink_to_fit();
+      S->used -= r->bytes;
+      for (size_t i = 0; i < S->running.size(); ++i)
+        if (S->running[i] == r) {
+          S->running.erase(S->running.begin() + i);
+          break;
+        }
+    }
+  }
+}
+
+size_t footprint(const ys_params &p) {
+  // bulk fields (66), FP64 pressures (6), staging and tables; forcing is not
+  // used by served shells
+  size_t elems = 2ul * (p.Nr + 2) * (p.Nth + 2) * (size_t)(((p.Nph + 2) + 7) / 8 * 8) + 64;
+  size_t R = (p.precision == YS_MIXED) ? 4 : 8;
+  return elems * (66 * R + 6 * 8) + packed_len(p) * 8 / 2 + (1u << 20);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ys_server_create(size_t hbm_budget_bytes, int max_slots, ys_server **out) {
+  if (!out || max_slots < 1 || max_slots > kMaxCap || hbm_budget_bytes == 0) return YS_EINVAL;
+  *out = nullptr;
+  ys_server *S = new (std::nothrow) ys_server();
+  if (!S) return YS_ENOMEM;
+  S->budget = hbm_budget_bytes;
+  S->max_slots = max_slots;
+  cudaGetDevice(&S->dev);
+  *out = S;
+  return YS_OK;
+}
+
+int ys_submit(ys_server *S, const ys_params *p, const double *init_fields, int n_steps, int n_schwarz,
+              uint64_t *ticket) {
+  if (!S || !p || !init_fields || n_steps < 1 || n_schwarz < 1 || !ticket) return YS_EINVAL;
+  if (p->schwarz_mode != YS_ADDITIVE || p->schwarz_tol != 0.0) return YS_EINVAL;
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (!S->batch) {
+    // the first request fixes the batch precision and iteration count
+    int rc = ys_batch_create(S->max_slots, p->precision, n_schwarz, &S->batch);
+    if (rc) return rc;
+    S->K = n_schwarz;
+    S->precision = p->precision;
+    S->worker = std::thread(server_loop, S);
+  }
+  if (n_schwarz != S->K || p->precision != S->precision) return YS_EINVAL;
+  if (S->queue.size() >= kMaxQueue) return YS_EBUSY;
+  size_t bytes = footprint(*p);
+  if (bytes > S->budget) return YS_EINVAL;   // can never be admitted
+  Request *r = new (std::nothrow) Request();
+  if (!r) return YS_ENOMEM;
+  r->prm = *p;
+  r->init.assign(init_fields, init_fields + packed_len(*p));
+  r->n_steps = n_steps;
+  r->bytes = bytes;
+  r->ticket = S->next_ticket++;
+  r->t_submit = std::chrono::steady_clock::now();
+  S->queue.push_back(r);
+  S->all[r->ticket] = r;
+  *ticket = r->ticket;
+  lk.unlock();
+  S->cv.notify_one();
+  return YS_OK;
+}
+
+int ys_poll(ys_server *S, uint64_t ticket, int *state, double *out_fields, double *latency_s) {
+  if (!S) return YS_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) return YS_EINVAL;
+  Request *r = it->second;
+  if (state) *state = r->state;
+  if (r->state < 2) return YS_EAGAIN;
+  if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+  if (r->state == 3) return r->error ? r->error : YS_ECUDA;
+  if (out_fields) std::memcpy(out_fields, r->result.data(), r->result.size() * sizeof(double));
+  return YS_OK;
+}
+
+int ys_server_stats(ys_server *S, long *steps_run, double *cell_updates, int *running, int *queued) {
+  if (!S) return YS_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (steps_run) *steps_run = S->steps_run;
+  if (cell_updates) *cell_updates = S->cell_updates;
+  if (running) *running = (int)S->running.size();
+  if (queued) *queued = (int)S->queue.size();
+  return YS_OK;
+}
+
+int ys_server_destroy(ys_server *S) {
+  if (!S) return YS_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  for (Request *r : S->running) {
+    ys_ctx *c = nullptr;
+    ys_batch_remove(S->batch, r->slot, &c);
+    if (c) ys_destroy(c);
+  }
+  if (S->batch) ys_batch_destroy(S->batch);
+  for (auto &kv : S->all) delete kv.second;
+  delete S;
+  return YS_OK;
+}
+
+}  // extern "C"

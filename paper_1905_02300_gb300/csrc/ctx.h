@@ -1,0 +1,67 @@
+// Internal definition of the single-shell context (shared by api.cu and the
+// batch / serving translation unit).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/ys.h"
+#include "geometry.h"
+#include "kernels.cuh"
+
+namespace ys {
+
+// kernel classes for timing
+enum KClass {
+  K_EXTRAP = 0, K_FORCE, K_EXCH, K_WALLS, K_RING, K_RES_T, K_RES_U, K_SWEEP_R, K_SWEEP_T, K_SWEEP_P, K_PRES,
+  K_PACK, K_FACTOR, K_NUM
+};
+
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+// Typed device state of one shell.
+template <typename R>
+struct Fields {
+  State<R> lev[3];           // level n, level n-1, iterate
+  R *A[3];                   // advecting velocity
+  R *fcomb[4];               // forcing at t_n + dt/2
+  R *B, *Cs;                 // work field, Thomas c' (unused by the stored-LU path)
+  R *fac[4][3][3];           // per-step LU factors: fac[loc][dir] = {lo, 1/pivot, c'}
+  R *modes[kMaxModes][4];    // forcing modes
+};
+
+}  // namespace ys
+
+struct ys_ctx {
+  ys_params prm;
+  ys::GridGeo geo;
+  ys::Layout L;
+  ys::Shell S;
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  void *dmem = nullptr;
+  size_t dbytes = 0;
+  void *modes_mem[ys::kMaxModes] = {};
+  ys::Fields<double> *f64 = nullptr;
+  ys::Fields<float> *f32 = nullptr;
+  ys::XEntry *xdev = nullptr;
+  ys::XTables X;
+  double *norm = nullptr;     // YS_NFIELDS accumulators
+  double *stage = nullptr;    // host-layout staging (device)
+  double *T_bg = nullptr;     // deviation backgrounds per radial index (mixed form), else null
+  double *p_bg = nullptr;
+  int mode_fn[ys::kMaxModes] = {};
+  int mode_set[ys::kMaxModes] = {};
+  int nmodes_set = 0;
+  double t = 0.0;
+  long steps_done = 0;
+  int level1_set = 0;
+  double norms_host[YS_NFIELDS] = {};
+  int iters_last = 0;
+  long launches = 0;
+  int prof_on = 0;
+  std::vector<ys::ProfRec> prof;
+  size_t prof_used = 0;
+};

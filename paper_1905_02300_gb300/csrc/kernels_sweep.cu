@@ -13,7 +13,7 @@
 #include <mutex>
 
 #include "../../include/ys.h"
-#include "kernels.cuh"
+#include "bodies.cuh"
 
 namespace ys {
 
@@ -22,174 +22,10 @@ namespace {
 constexpr int TPB = 128;
 
 template <typename R>
-__device__ __forceinline__ double avg4(const R *a, long q1, long q2, long q3, long q4) {
-  return (((double)a[q1] + (double)a[q2]) + (double)a[q3] + (double)a[q4]) * 0.25;
-}
-
-// Advecting velocity (a_r, a_th, a_ph) at a point of location `loc`: own
-// component as stored, others averaged from their nearest stored values.
-template <typename R>
-__device__ __forceinline__ void advecting(const Shell &S, const StepAux<R> &ax, int loc, long q, double &ar,
-                                          double &at, double &ap) {
-  const long SI = S.L.SI, P = S.L.P;
-  const R *A0 = ax.A[0], *A1 = ax.A[1], *A2 = ax.A[2];
-  switch (loc) {
-    case LC:
-      ar = ((double)A0[q] + (double)A0[q + SI]) * 0.5;
-      at = ((double)A1[q] + (double)A1[q + P]) * 0.5;
-      ap = ((double)A2[q] + (double)A2[q + 1]) * 0.5;
-      break;
-    case LR:
-      ar = (double)A0[q];
-      at = avg4(A1, q - SI, q - SI + P, q, q + P);
-      ap = avg4(A2, q - SI, q - SI + 1, q, q + 1);
-      break;
-    case LT:
-      ar = avg4(A0, q - P, q - P + SI, q, q + SI);
-      at = (double)A1[q];
-      ap = avg4(A2, q - P, q - P + 1, q, q + 1);
-      break;
-    default:
-      ar = avg4(A0, q - 1, q - 1 + SI, q, q + SI);
-      at = avg4(A1, q - 1, q - 1 + P, q, q + P);
-      ap = (double)A2[q];
-      break;
-  }
-}
-
-// Coefficients (lo, di, up) of (I - dt/2 Ahat_dir) at point (i, j, k) of `loc`
-// (divisions replaced by FP64 reciprocal metric tables).
-template <typename V, typename R>
-__device__ __forceinline__ void coef(const Shell &S, const StepAux<R> &ax, int loc, int dir, int i, int j, long q,
-                                     V &lo, V &di, V &up) {
-  const V ihr = (V)S.ihr, iht = (V)S.iht, ihp = (V)S.ihp;
-  const V nu = (V)((loc == LC) ? S.kappa : S.nu);
-  double ar_d, at_d, ap_d;
-  advecting(S, ax, loc, q, ar_d, at_d, ap_d);
-  const V ar = (V)ar_d, at = (V)at_d, ap = (V)ap_d;
-  const V ir = (V)((loc == LR) ? S.irf[i] : S.irc[i]);
-  const V is = (V)((loc == LT) ? S.isf[j] : S.isc[j]);
-  const V ir2 = ir * ir;
-  const V rc0 = (V)S.rc[i], rcm = (V)S.rc[i - 1], rf0 = (V)S.rf[i], rfp = (V)S.rf[i + 1], rfm = (V)S.rf[i - 1];
-  const V sc0 = (V)S.sc[j], scm = (V)S.sc[j - 1], sf0 = (V)S.sf[j], sfp = (V)S.sf[j + 1], sfm = (V)S.sf[j - 1];
-  V cm, c0, cp;
-  if (dir == DR) {
-    V cp_d, cm_d;
-    if (loc == LR) {
-      cp_d = rc0 * rc0 * (ir2 * ihr * ihr);
-      cm_d = rcm * rcm * (ir2 * ihr * ihr);
-    } else {
-      cp_d = rfp * rfp * (ir2 * ihr * ihr);
-      cm_d = rf0 * rf0 * (ir2 * ihr * ihr);
-    }
-    cm = nu * cm_d + ar * ((V)0.5 * ihr);
-    c0 = -nu * (cp_d + cm_d);
-    cp = nu * cp_d - ar * ((V)0.5 * ihr);
-    if (loc == LR) {
-      cm = cm - nu * rfm * rfm * (ir2 * ir * ihr);
-      cp = cp + nu * rfp * rfp * (ir2 * ir * ihr);
-      c0 = c0 - nu * (V)2.0 * ir2;
-      const V k = (V)S.i2chi, irm = (V)S.irc[i - 1], irc = (V)S.irc[i];
-      cm = cm + k * rfm * rfm * (irm * irm * ihr * ihr);
-      c0 = c0 - k * (rf0 * rf0 * (irc * irc * ihr * ihr) + rf0 * rf0 * (irm * irm * ihr * ihr));
-      cp = cp + k * rfp * rfp * (irc * irc * ihr * ihr);
-    }
-  } else if (dir == DT) {
-    V cp_d, cm_d;
-    const V iR1sq = (V)S.iR1sq;
-    if (loc == LT) {
-      cp_d = sc0 * (iR1sq * is * iht * iht);
-      cm_d = scm * (iR1sq * is * iht * iht);
-    } else {
-      cp_d = sfp * (iR1sq * is * iht * iht);
-      cm_d = sf0 * (iR1sq * is * iht * iht);
-    }
-    cm = nu * cm_d + at * ((V)0.5 * ir * iht);
-    c0 = -nu * (cp_d + cm_d);
-    cp = nu * cp_d - at * ((V)0.5 * ir * iht);
-    if (loc == LT) {
-      const V c = (V)S.cf[j], s = sf0;
-      const V qq = c * ir2 * is * is * iht;
-      cm = cm - nu * qq * sfm;
-      cp = cp + nu * qq * sfp;
-      c0 = c0 - nu * ir2 * is * is;
-      const V k = (V)S.i2chi, isc0 = (V)S.isc[j], iscm = (V)S.isc[j - 1];
-      cp = cp + k * sfp * (ir2 * isc0 * iht * iht);
-      c0 = c0 - k * (s * (ir2 * isc0 * iht * iht) + s * (ir2 * iscm * iht * iht));
-      cm = cm + k * sfm * (ir2 * iscm * iht * iht);
-    }
-  } else {
-    const V cpm = (V)S.cphi;
-    cm = nu * cpm + ap * ((V)0.5 * ir * is * ihp);
-    c0 = (V)-2.0 * nu * cpm;
-    cp = nu * cpm - ap * ((V)0.5 * ir * is * ihp);
-    if (loc == LP) {
-      c0 = c0 - nu * ir2 * is * is;
-      const V qq = (V)S.i2chi * ir2 * is * is * ihp * ihp;
-      cm = cm + qq;
-      c0 = c0 - (V)2.0 * qq;
-      cp = cp + qq;
-    }
-  }
-  lo = (V)-0.5 * (V)S.dt * cm;
-  di = (V)1.0 - (V)0.5 * (V)S.dt * c0;
-  up = (V)-0.5 * (V)S.dt * cp;
-}
-
-// Line of a (loc, dir) sweep: thread (lane, row) -> patch p, first point
-// (i, j, k), row range [m0, m1) and element stride along the line.  Lanes run
-// along phi for r- and theta-sweeps (coalesced) and along theta for
-// phi-sweeps.
-struct Line {
-  int p, i, j, k, m0, m1;
-  long step;
-  bool valid;
-};
-
-__device__ __forceinline__ Line decode_line(const Layout &L, int loc, int dir, int lane, int row) {
-  const int i0 = (loc == LR) ? 1 : 0, i1 = L.Nr;
-  const int j0 = (loc == LT) ? 1 : 0, j1 = L.Nt;
-  const int k0 = (loc == LP) ? 1 : 0, k1 = L.Np;
-  Line ln;
-  if (dir == DR) {
-    int nj = j1 - j0;
-    ln.k = k0 + lane;
-    ln.j = j0 + row % nj;
-    ln.p = row / nj;
-    ln.i = i0;
-    ln.valid = ln.k < k1;
-    ln.m0 = i0;
-    ln.m1 = i1;
-    ln.step = L.SI;
-  } else if (dir == DT) {
-    int ni = i1 - i0;
-    ln.k = k0 + lane;
-    ln.i = i0 + row % ni;
-    ln.p = row / ni;
-    ln.j = j0;
-    ln.valid = ln.k < k1;
-    ln.m0 = j0;
-    ln.m1 = j1;
-    ln.step = L.P;
-  } else {
-    int ni = i1 - i0;
-    ln.j = j0 + lane;
-    ln.i = i0 + row % ni;
-    ln.p = row / ni;
-    ln.k = k0;
-    ln.valid = ln.j < j1;
-    ln.m0 = k0;
-    ln.m1 = k1;
-    ln.step = 1;
-  }
-  return ln;
-}
-
-template <typename R>
 __global__ void k_sweep(Shell S, int loc, int dir, int final, StepAux<R> ax, R *B, R *Cs, R *dst, double *norm,
                         int slot, int patch_mask) {
   const Layout &L = S.L;
-  const Line ln = decode_line(L, loc, dir, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
+  const bd::Line ln = bd::decode_line(L, loc, dir, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
   const int m0 = ln.m0, m1 = ln.m1, i = ln.i, j = ln.j;
   const long step = ln.step;
   double contrib = 0.0;
@@ -201,7 +37,7 @@ __global__ void k_sweep(Shell S, int loc, int dir, int final, StepAux<R> ax, R *
     for (int m = m0; m < m1; ++m, q += step) {
       int ii = (dir == DR) ? m : i, jj = (dir == DT) ? m : j;
       double lo, di, up;
-      coef<double>(S, ax, loc, dir, ii, jj, q, lo, di, up);
+      bd::coef<double>(S, ax, loc, dir, ii, jj, q, lo, di, up);
       if (m == m0) {
         if (reflect) di -= lo;
         lo = 0.0;
@@ -249,32 +85,7 @@ __global__ void k_sweep(Shell S, int loc, int dir, int final, StepAux<R> ax, R *
 // 1/(di_m - lo_m c'_{m-1}) and c'_m = up_m / pivot_m.
 template <typename R>
 __global__ void k_factorize(Shell S, int loc, int dir, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask) {
-  using V = typename Cmp<R>::type;
-  const Layout &L = S.L;
-  const Line ln = decode_line(L, loc, dir, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
-  if (!ln.valid || !((patch_mask >> ln.p) & 1)) return;
-  const bool reflect = (dir == DR) && (loc != LR);
-  V cprev = (V)0.0;
-  long q = lidx(L, ln.p, ln.i, ln.j, ln.k);
-  for (int m = ln.m0; m < ln.m1; ++m, q += ln.step) {
-    int ii = (dir == DR) ? m : ln.i, jj = (dir == DT) ? m : ln.j;
-    V lo, di, up;
-    coef<V>(S, ax, loc, dir, ii, jj, q, lo, di, up);
-    if (m == ln.m0) {
-      if (reflect) di -= lo;
-      lo = (V)0.0;
-    }
-    if (m == ln.m1 - 1) {
-      if (reflect) di -= up;
-      up = (V)0.0;
-    }
-    V inv = (V)1.0 / (di - lo * cprev);
-    V c = up * inv;
-    Lo[q] = (R)lo;
-    Iv[q] = (R)inv;
-    Cp[q] = (R)c;
-    cprev = c;
-  }
+  bd::body_factorize(S, loc, dir, ax, Lo, Iv, Cp, patch_mask, blockIdx.x, blockIdx.y);
 }
 
 // Thomas solve with a stored factorisation: forward d'_m = (b_m - lo_m d'_{m-1})
@@ -284,39 +95,7 @@ __global__ void k_factorize(Shell S, int loc, int dir, StepAux<R> ax, R *Lo, R *
 template <typename R>
 __global__ void k_solve(Shell S, int loc, int dir, int final, const R *__restrict__ Lo, const R *__restrict__ Iv,
                         const R *__restrict__ Cp, R *B, R *dst, double *norm, int slot, int patch_mask) {
-  using V = typename Cmp<R>::type;
-  const Layout &L = S.L;
-  const Line ln = decode_line(L, loc, dir, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
-  double contrib = 0.0;
-  if (ln.valid && ((patch_mask >> ln.p) & 1)) {
-    const long step = ln.step;
-    long q = lidx(L, ln.p, ln.i, ln.j, ln.k);
-    V d = (V)0.0;
-    for (int m = ln.m0; m < ln.m1; ++m, q += step) {
-      d = ((V)B[q] - (V)Lo[q] * d) * (V)Iv[q];
-      B[q] = (R)d;
-    }
-    q -= step;
-    V x = d;
-    for (int m = ln.m1 - 1;; --m) {
-      if (final) {
-        dst[q] = (R)((V)dst[q] + x);
-        int ii = (dir == DR) ? m : ln.i, jj = (dir == DT) ? m : ln.j;
-        double r = (loc == LR) ? S.rf[ii] : S.rc[ii];
-        double s = (loc == LT) ? S.sf[jj] : S.sc[jj];
-        contrib += r * r * s * S.hr * S.ht * S.hp * (double)x * (double)x;
-      } else {
-        B[q] = (R)x;
-      }
-      if (m == ln.m0) break;
-      q -= step;
-      x = (V)B[q] - (V)Cp[q] * x;
-    }
-  }
-  if (final) {
-    for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, off);
-    if ((threadIdx.x & 31) == 0 && contrib != 0.0) atomicAdd(&norm[slot], contrib);
-  }
+  bd::body_solve(S, loc, dir, final, Lo, Iv, Cp, B, dst, norm, slot, patch_mask, blockIdx.x, blockIdx.y);
 }
 
 dim3 line_grid(const Layout &L, int loc, int dir) {

@@ -561,12 +561,12 @@ def shell_ensemble(seed: int = 4, n: int = 64, nr_max: int = 64, nth_max: int = 
 
 
 def convection_initial(spec: Spec, Pr: float, Ra: float, seed: int = 3, amp: float = 1e-3,
-                       T_in: float = 1.0, T_out: float = 0.0):
+                       T_in: float = 1.0, T_out: float = 0.0, kmax: int = 6):
     """Thermal-convection start (user layout): T = conductive profile + seeded
     perturbation, u = 0, and p in discrete hydrostatic balance with T along
     each radial column, p_{i} - p_{i-1} = h_r Pr Ra (T_{i-1} + T_i)/2, p_0 = 0
     (buoyancy Pr Ra T e_r balanced by the pressure gradient)."""
-    T = conductive_profile(spec, T_in, T_out) + convection_perturbation(spec, seed, amp)
+    T = conductive_profile(spec, T_in, T_out) + convection_perturbation(spec, seed, amp, kmax)
     p = np.zeros_like(T)
     for i in range(1, spec.Nr):
         p[:, i] = p[:, i - 1] + spec.hr * Pr * Ra * 0.5 * (T[:, i - 1] + T[:, i])

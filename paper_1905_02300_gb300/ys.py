@@ -58,6 +58,22 @@ _sig = {
     "ys_factor_solve_static": (C.c_int, [C.POINTER(Params), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p]),
     "ys_strerror": (C.c_char_p, [C.c_int]),
+    "ys_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "ys_batch_add": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
+    "ys_batch_remove": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "ys_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "ys_batch_sync": (C.c_int, [C.c_void_p]),
+    "ys_batch_norms": (C.c_int, [C.c_void_p, C.c_int, _dp]),
+    "ys_batch_set_line_threads": (C.c_int, [C.c_void_p, C.c_int]),
+    "ys_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "ys_batch_launches_per_step": (C.c_long, [C.c_void_p]),
+    "ys_batch_destroy": (C.c_int, [C.c_void_p]),
+    "ys_batch_stream": (C.c_void_p, [C.c_void_p]),
+    "ys_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
+    "ys_submit": (C.c_int, [C.c_void_p, C.POINTER(Params), _dp, C.c_int, C.c_int, C.POINTER(C.c_uint64)]),
+    "ys_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_int), _dp, _dp]),
+    "ys_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_long), _dp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "ys_server_destroy": (C.c_int, [C.c_void_p]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -192,3 +208,130 @@ class Solver:
 
     def device_bytes(self):
         return lib.ys_device_bytes(self.h)
+
+
+class Batch:
+    """Ensemble of shells advanced together (one launch per kernel class,
+    one CUDA graph per step).  Solvers added to a batch are stepped only by it
+    until removed."""
+
+    def __init__(self, capacity, precision=YS_MIXED, n_schwarz=3):
+        h = C.c_void_p()
+        _check(lib.ys_batch_create(capacity, precision, n_schwarz, C.byref(h)), "ys_batch_create")
+        self.h = h
+        self.members = {}
+
+    def add(self, solver):
+        slot = C.c_int()
+        _check(lib.ys_batch_add(self.h, solver.h, C.byref(slot)), "ys_batch_add")
+        self.members[slot.value] = solver
+        return slot.value
+
+    def remove(self, slot):
+        out = C.c_void_p()
+        _check(lib.ys_batch_remove(self.h, slot, C.byref(out)), "ys_batch_remove")
+        return self.members.pop(slot)
+
+    def step(self, n=1):
+        _check(lib.ys_batch_step(self.h, n), "ys_batch_step")
+
+    def sync(self):
+        _check(lib.ys_batch_sync(self.h), "ys_batch_sync")
+
+    def norms(self, slot):
+        a = np.empty(NFIELDS)
+        _check(lib.ys_batch_norms(self.h, slot, _ptr(a)), "ys_batch_norms")
+        return a
+
+    def set_line_threads(self, t):
+        _check(lib.ys_batch_set_line_threads(self.h, t), "ys_batch_set_line_threads")
+
+    def autotune(self, trial_steps=2):
+        ch = C.c_int()
+        _check(lib.ys_batch_autotune(self.h, trial_steps, C.byref(ch)), "ys_batch_autotune")
+        return ch.value
+
+    def launches_per_step(self):
+        return lib.ys_batch_launches_per_step(self.h)
+
+    def stream_handle(self):
+        return lib.ys_batch_stream(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            for slot in list(self.members):
+                self.remove(slot)
+            lib.ys_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pack_fields(f):
+    """[T | ur | uth | uph | p] packed as the serving API expects."""
+    return np.concatenate([np.ascontiguousarray(f[k], dtype=np.float64).ravel()
+                           for k in ("T", "ur", "uth", "uph", "p")])
+
+
+def unpack_fields(buf, Nr, Nth, Nph):
+    shapes = {"T": (2, Nr, Nth, Nph), "ur": (2, Nr + 1, Nth, Nph), "uth": (2, Nr, Nth + 1, Nph),
+              "uph": (2, Nr, Nth, Nph + 1), "p": (2, Nr, Nth, Nph)}
+    out, o = {}, 0
+    for k in ("T", "ur", "uth", "uph", "p"):
+        n = int(np.prod(shapes[k]))
+        out[k] = buf[o:o + n].reshape(shapes[k])
+        o += n
+    return out
+
+
+class Server:
+    """Request loop with continuous batching (ys_server_*)."""
+
+    QUEUED, RUNNING, DONE, FAILED = 0, 1, 2, 3
+
+    def __init__(self, hbm_budget_bytes, max_slots):
+        h = C.c_void_p()
+        _check(lib.ys_server_create(hbm_budget_bytes, max_slots, C.byref(h)), "ys_server_create")
+        self.h = h
+        self.shapes = {}
+
+    def submit(self, fields, n_steps, n_schwarz=3, **params):
+        p = default_params(**params)
+        buf = pack_fields(fields)
+        t = C.c_uint64()
+        _check(lib.ys_submit(self.h, C.byref(p), _ptr(buf), n_steps, n_schwarz, C.byref(t)), "ys_submit")
+        self.shapes[t.value] = (p.Nr, p.Nth, p.Nph)
+        return t.value
+
+    def poll(self, ticket):
+        """(state, fields or None, latency_s or None, error code)"""
+        Nr, Nt, Np = self.shapes[ticket]
+        n = 2 * Nr * Nt * Np * 2 + 2 * (Nr + 1) * Nt * Np + 2 * Nr * (Nt + 1) * Np + 2 * Nr * Nt * (Np + 1)
+        buf = np.empty(n)
+        st, lat = C.c_int(), C.c_double()
+        rc = lib.ys_poll(self.h, C.c_uint64(ticket), C.byref(st), _ptr(buf), C.byref(lat))
+        if rc == YS_EAGAIN:
+            return st.value, None, None, rc
+        if rc != YS_OK:
+            return st.value, None, lat.value, rc
+        return st.value, unpack_fields(buf, Nr, Nt, Np), lat.value, rc
+
+    def stats(self):
+        steps, cu, run, q = C.c_long(), C.c_double(), C.c_int(), C.c_int()
+        _check(lib.ys_server_stats(self.h, C.byref(steps), C.byref(cu), C.byref(run), C.byref(q)), "ys_server_stats")
+        return {"steps": steps.value, "cell_updates": cu.value, "running": run.value, "queued": q.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.ys_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,176 @@
+"""Batched ensembles and serving (continuous batching) on the GPU.
+
+A shell's fields must not depend on what else is in the batch: the per-shell
+arithmetic and block decomposition of the batched kernels are the same alone
+and in any mix, so those checks are bitwise.  Against the single-shell path
+(other kernels, which the compiler may contract into FMAs differently) the
+check is the mixed form's 1e-5 relative tolerance."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1905_02300_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SHELLS = [dict(R1=0.45, Nr=16, Nth=20, Ra=2e3, Pr=1.0), dict(R1=0.55, Nr=20, Nth=16, Ra=1e4, Pr=0.7),
+          dict(R1=0.35, Nr=12, Nth=24, Ra=5e3, Pr=7.0)]
+
+
+def make(ys, sp, precision=None):
+    Nr, Nth = sp["Nr"], sp["Nth"]
+    spec = W.Spec(sp["R1"], 1.0, Nr, Nth, 3 * Nth)
+    hmin = min(spec.hr, sp["R1"] * spec.hth, sp["R1"] * np.sin(spec.th0) * spec.hph)
+    kw = dict(R1=sp["R1"], R2=1.0, Pr=sp["Pr"], Ra=sp["Ra"], Nr=Nr, Nth=Nth, Nph=3 * Nth, dt=0.5 * hmin * hmin,
+              T_inner=1.0, T_outer=0.0, precision=ys.YS_MIXED if precision is None else precision)
+    s = ys.Solver(**kw)
+    spec = W.Spec(kw["R1"], 1.0, Nr, Nth, 3 * Nth)
+    s.set_fields_dict(0, W.convection_initial(spec, sp["Pr"], sp["Ra"], T_in=1.0))
+    return s, kw
+
+
+def fields(s):
+    return s.get_fields(0, aux=True)
+
+
+def same(a, b):
+    return all(np.array_equal(a[k], b[k]) for k in a)
+
+
+def close(a, b, tol=1e-5):
+    for k in a:
+        scale = max(np.abs(b[c]).max() for c in (("ur", "uth", "uph") if k in ("ur", "uth", "uph") else
+                                                  ("ur1", "uth1", "uph1") if k in ("ur1", "uth1", "uph1") else (k,)))
+        if np.abs(a[k] - b[k]).max() > tol * max(scale, 1e-300):
+            return False
+    return True
+
+
+def alone(ys, sp, n):
+    """fields after n steps of the shell alone in a batch"""
+    b = ys.Batch(1)
+    s, _ = make(ys, sp)
+    slot = b.add(s)
+    b.step(n)
+    b.sync()
+    f = fields(b.remove(slot))
+    b.close()
+    return f
+
+
+def test_batch_is_mix_independent_and_matches_single_shell_path(gpu_lib):
+    ys = gpu_lib
+    ref, single = [], []
+    for sp in SHELLS:
+        ref.append(alone(ys, sp, 5))
+        s, _ = make(ys, sp)
+        s.step(5, 3)
+        single.append(fields(s))
+    b = ys.Batch(8)
+    members = [make(ys, sp)[0] for sp in SHELLS]
+    slots = [b.add(m) for m in members]
+    b.step(5)
+    b.sync()
+    for slot, r, sg in zip(slots, ref, single):
+        s = b.remove(slot)
+        assert s.stats()["steps"] == 5
+        f = fields(s)
+        assert same(f, r)
+        assert close(f, sg)
+    assert b.launches_per_step() > 0
+    b.close()
+
+
+def test_shells_join_and_leave_between_steps(gpu_lib):
+    ys = gpu_lib
+    a_ref = alone(ys, SHELLS[0], 6)
+    b_ref = alone(ys, SHELLS[1], 3)
+    bt = ys.Batch(4)
+    a, _ = make(ys, SHELLS[0])
+    sa = bt.add(a)
+    bt.step(3)
+    b, _ = make(ys, SHELLS[1])
+    sb = bt.add(b)
+    bt.step(3)
+    bt.sync()
+    assert same(fields(bt.remove(sa)), a_ref)
+    assert same(fields(bt.remove(sb)), b_ref)  # b ran 3 steps
+    bt.close()
+
+
+def test_autotune_keeps_results(gpu_lib):
+    ys = gpu_lib
+    ref = alone(ys, SHELLS[2], 8)
+    bt = ys.Batch(2)
+    s, _ = make(ys, SHELLS[2])
+    slot = bt.add(s)
+    chosen = bt.autotune(trial_steps=1)      # 4 candidates x (1 + 1) steps = 8 steps
+    assert chosen in (32, 64, 128, 256)
+    bt.sync()
+    assert same(fields(bt.remove(slot)), ref)
+    bt.close()
+
+
+def test_server_continuous_batching(gpu_lib):
+    ys = gpu_lib
+    reqs = [(SHELLS[0], 4), (SHELLS[1], 7), (SHELLS[2], 3), (SHELLS[0], 5), (SHELLS[2], 6)]
+    expect = []
+    for sp, n in reqs:
+        f = alone(ys, sp, n)
+        expect.append({k: f[k] for k in ("T", "ur", "uth", "uph", "p")})
+    # budget for about two shells at a time: the rest wait for memory
+    srv = ys.Server(hbm_budget_bytes=60 << 20, max_slots=8)
+    tickets = []
+    for sp, n in reqs:
+        _, kw = make(ys, sp)
+        spec = W.Spec(kw["R1"], 1.0, kw["Nr"], kw["Nth"], kw["Nph"])
+        tickets.append(srv.submit(W.convection_initial(spec, sp["Pr"], sp["Ra"], T_in=1.0), n, **kw))
+        time.sleep(0.01)
+    peak = 0
+    done = {}
+    t0 = time.time()
+    while len(done) < len(tickets) and time.time() - t0 < 120:
+        peak = max(peak, srv.stats()["running"])
+        for t in tickets:
+            if t in done:
+                continue
+            st, f, lat, rc = srv.poll(t)
+            if st >= 2:
+                done[t] = (st, f, lat, rc)
+        time.sleep(0.002)
+    assert len(done) == len(tickets)
+    for t, e in zip(tickets, expect):
+        st, f, lat, rc = done[t]
+        assert st == ys.Server.DONE and rc == 0 and lat > 0
+        for k in e:
+            assert np.array_equal(f[k], e[k]), k
+    assert 1 <= peak <= 3
+    srv.close()
+
+
+def test_server_failed_request_does_not_poison_others(gpu_lib):
+    ys = gpu_lib
+    srv = ys.Server(hbm_budget_bytes=1 << 30, max_slots=4)
+    _, kw = make(ys, SHELLS[1])
+    good = alone(ys, SHELLS[1], 4)
+    spec = W.Spec(kw["R1"], 1.0, kw["Nr"], kw["Nth"], kw["Nph"])
+    init = W.convection_initial(spec, SHELLS[1]["Pr"], SHELLS[1]["Ra"], T_in=1.0)
+    bad = {k: v.copy() for k, v in init.items()}
+    bad["T"][0, 3, 4, 5] = np.nan
+    tb = srv.submit(bad, 4, **kw)
+    tg = srv.submit(init, 4, **kw)
+    t0 = time.time()
+    res = {}
+    while len(res) < 2 and time.time() - t0 < 60:
+        for t in (tb, tg):
+            if t not in res:
+                st, f, lat, rc = srv.poll(t)
+                if st >= 2:
+                    res[t] = (st, f, rc)
+        time.sleep(0.002)
+    assert res[tb][0] == ys.Server.FAILED and res[tb][2] == ys.YS_EDIVERGED
+    st, f, rc = res[tg]
+    assert st == ys.Server.DONE
+    assert all(np.array_equal(f[k], good[k]) for k in f)
+    srv.close()
