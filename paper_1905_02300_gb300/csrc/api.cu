@@ -152,7 +152,7 @@ void solve_unknown(ys_ctx *c, int loc, int slot, int mask) {
     bool fin = (s == 2);
     R *const *Fc = D.fac[loc][dir];
     LAUNCH(c, kSweepClass[dir], 1,
-           Launch<R>::solve(c->S, loc, dir, fin, Fc[0], Fc[1], Fc[2], D.B, it.f[slot], c->norm, slot, mask,
+           Launch<R>::solve(c->S, loc, dir, fin, Fc[0], Fc[1], Fc[2], D.B, D.Cs, it.f[slot], c->norm, slot, mask,
                             c->stream));
   }
 }
@@ -503,7 +503,8 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   if (user_elems(L, LT) > stage_elems) stage_elems = user_elems(L, LT);
   if (user_elems(L, LP) > stage_elems) stage_elems = user_elems(L, LP);
   size_t off_metric = bulk_bytes + p_bytes;
-  size_t off_x = off_metric + ((met.size() * sizeof(double) + 255) / 256) * 256;
+  size_t off_fmet = off_metric + ((met.size() * sizeof(double) + 255) / 256) * 256;
+  size_t off_x = off_fmet + ((met.size() * sizeof(float) + 255) / 256) * 256;
   size_t off_dev = off_x + ((xcount * sizeof(XEntry) + 255) / 256) * 256;
   size_t dev_bytes = ((4 * (size_t)(p->Nr + 2) * sizeof(double) + 255) / 256) * 256;
   size_t off_norm = off_dev + dev_bytes;
@@ -542,6 +543,9 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
     carve<double>(c, *c->f64, base);
   }
   double *metric = (double *)(base + off_metric);
+  float *fmetric = (float *)(base + off_fmet);
+  std::vector<float> fmet(met.begin(), met.end());   // FP64 tables rounded once to FP32
+  cudaMemcpyAsync(fmetric, fmet.data(), fmet.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
   c->xdev = (XEntry *)(base + off_x);
   double *devtab = (double *)(base + off_dev);
   c->norm = (double *)(base + off_norm);
@@ -588,6 +592,8 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   S.Tc_lap = nullptr;
   S.Tc_dr = nullptr;
   S.step7 = p->step7;
+  shell_fill_fp64(S);
+  for (int k = 0; k < kMetricTables; ++k) S.ftab[k] = fmetric + k * len + pad;
   if (deviation) {
     // device tables: [Tc at centres i = 0..Nr-1 | pc | Tc_lap | Tc_dr], each Nr + 2 long
     const size_t n = p->Nr + 2;
@@ -606,7 +612,7 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
     S.T_in = 0.0;   // the deviation has homogeneous reflection walls
     S.T_out = 0.0;
   }
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {   // also keeps fmet alive until copied
     ys_destroy(c);
     return YS_ECUDA;
   }

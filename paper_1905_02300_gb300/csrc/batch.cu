@@ -37,7 +37,7 @@ struct ShellDev {
   Shell S;
   State<R> lev[3];   // physical buffers; level n = lev[rot], n-1 = lev[rot+1], iterate = lev[rot+2] (mod 3)
   R *A[3];
-  R *B;
+  R *B, *W;          // right-hand side / forward-sweep scratch
   R *fac[4][3][3];
   double *norm;      // YS_NFIELDS accumulators of this shell
   XTables X;
@@ -52,7 +52,9 @@ struct WorkMap {
 };
 
 enum MapId {
-  M_EXTRAP = 0, M_EX0, M_EX1, M_EX2, M_EX3, M_WALLS, M_RING, M_RC, M_RR, M_RT, M_RP, M_LINE0, M_NUM = M_LINE0 + 12
+  M_EXTRAP = 0, M_EX0, M_EX1, M_EX2, M_EX3, M_WALLS, M_RING, M_RC, M_RR, M_RT, M_RP, M_LINE0,
+  M_PHI0 = M_LINE0 + 12,   // shared-memory phi solves, one map per unknown type
+  M_NUM = M_PHI0 + 4
 };
 
 namespace {
@@ -121,7 +123,18 @@ template <typename R>
 __global__ void kb_solve(const ShellDev<R> *sh, WorkMap map, int cap, int loc, int dir, int final, int slot) {
   YS_BATCH_LOOP(map, cap)
   R *const *F = D.fac[loc][dir];
-  bd::body_solve(D.S, loc, dir, final, F[0], F[1], F[2], D.B, it.f[slot], D.norm, slot, 3, bx, by);
+  bd::body_solve(D.S, loc, dir, final, F[0], F[1], F[2], D.B, D.W, it.f[slot], D.norm, slot, 3, bx, by);
+  }
+}
+
+template <typename R>
+__global__ void kb_solve_phi(const ShellDev<R> *sh, WorkMap map, int cap, int loc, int final, int slot) {
+  extern __shared__ __align__(16) unsigned char phi_smem[];
+  YS_BATCH_LOOP(map, cap)
+  (void)by;
+  R *const *F = D.fac[loc][DP];
+  bd::body_solve_phi(D.S, loc, final, F[0], F[1], F[2], D.B, D.W, it.f[slot], D.norm, slot, 3, bx, (R *)phi_smem);
+  __syncwarp();
   }
 }
 
@@ -197,6 +210,8 @@ void grid_of(const ys_ctx *c, int map, int tpb_line, int &gx, int &gy) {
     int ni = L.Nr - (loc == LR), nj = L.Nt - (loc == LT), nk = L.Np - (loc == LP);
     gx = cdiv(nk, 128);
     gy = 2 * ni * nj;
+  } else if (map >= M_PHI0) {
+    gx = bd::phi_ctas(L, map - M_PHI0);
   } else {
     int loc = (map - M_LINE0) / 3, dir = (map - M_LINE0) % 3;
     int ni = L.Nr - (loc == LR), nj = L.Nt - (loc == LT), nk = L.Np - (loc == LP);
@@ -268,6 +283,7 @@ ShellDev<R> describe(ys_batch *b, int s) {
   for (int l = 0; l < 3; ++l) d.lev[l] = D.lev[l];
   for (int a = 0; a < 3; ++a) d.A[a] = D.A[a];
   d.B = D.B;
+  d.W = D.Cs;
   std::memcpy(d.fac, D.fac, sizeof(d.fac));
   d.norm = b->norms + (size_t)s * YS_NFIELDS;
   d.X = c->X;
@@ -327,10 +343,21 @@ void enqueue_step(ys_batch *b) {
       kb_factorize<R><<<gl, b->tpb_line, 0, st>>>(sh, map_of(b, M_LINE0 + 3 * loc + dir), cap, loc, dir);
       ++nl;
     }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(kb_solve_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::phi_smem_bytes<R>());
+    attr = true;
+  }
+  const int gp = 152 * 4;
   auto solve = [&](int loc, int slot) {
     for (int s = 0; s < 3; ++s) {
       int dir = kOrderB[loc][s];
-      kb_solve<R><<<gl, b->tpb_line, 0, st>>>(sh, map_of(b, M_LINE0 + 3 * loc + dir), cap, loc, dir, s == 2, slot);
+      if (dir == DP)
+        kb_solve_phi<R><<<gp, 32 * bd::kPhiWarps, bd::phi_smem_bytes<R>(), st>>>(sh, map_of(b, M_PHI0 + loc), cap,
+                                                                               loc, s == 2, slot);
+      else
+        kb_solve<R><<<gl, b->tpb_line, 0, st>>>(sh, map_of(b, M_LINE0 + 3 * loc + dir), cap, loc, dir, s == 2,
+                                                 slot);
       ++nl;
     }
   };

@@ -57,11 +57,11 @@ template <typename V, typename R>
 __device__ __forceinline__ V divh(const Shell &S, const R *ri, const R *rn, const R *ti, const R *tn, const R *pi,
                                   const R *pn, int i, int j, long q) {
   const Layout &L = S.L;
-  const V ir = (V)S.irc[i], is = (V)S.isc[j];
-  const V rfp = (V)S.rf[i + 1], rf0 = (V)S.rf[i];
-  V d_r = (rfp * rfp * H<V>(ri, rn, q + L.SI) - rf0 * rf0 * H<V>(ri, rn, q)) * (ir * ir * (V)S.ihr);
-  V d_t = ((V)S.sf[j + 1] * H<V>(ti, tn, q + L.P) - (V)S.sf[j] * H<V>(ti, tn, q)) * (ir * is * (V)S.iht);
-  V d_p = (H<V>(pi, pn, q + 1) - H<V>(pi, pn, q)) * (ir * is * (V)S.ihp);
+  const V ir = mt<V>(S, MT_IRC)[i], is = mt<V>(S, MT_ISC)[j];
+  const V rfp = mt<V>(S, MT_RF)[i + 1], rf0 = mt<V>(S, MT_RF)[i];
+  V d_r = (rfp * rfp * H<V>(ri, rn, q + L.SI) - rf0 * rf0 * H<V>(ri, rn, q)) * (ir * ir * cs<V>(S, CS_IHR));
+  V d_t = (mt<V>(S, MT_SF)[j + 1] * H<V>(ti, tn, q + L.P) - mt<V>(S, MT_SF)[j] * H<V>(ti, tn, q)) * (ir * is * cs<V>(S, CS_IHT));
+  V d_p = (H<V>(pi, pn, q + 1) - H<V>(pi, pn, q)) * (ir * is * cs<V>(S, CS_IHP));
   return d_r + d_t + d_p;
 }
 
@@ -74,15 +74,15 @@ __device__ __forceinline__ void body_resid_T(Shell S, State<R> it, State<R> n, S
   if (!decode_point(L, LC, patch_mask, bx, by, p, i, j, k)) return;
   long q = lidx(L, p, i, j, k);
   const R *a = it.f[F_T], *b = n.f[F_T];
-  const V ir = (V)S.irc[i], is = (V)S.isc[j], ir2 = ir * ir;
-  const V ihr = (V)S.ihr, iht = (V)S.iht, ihp = (V)S.ihp;
-  const V rfp = (V)S.rf[i + 1], rf0 = (V)S.rf[i];
+  const V ir = mt<V>(S, MT_IRC)[i], is = mt<V>(S, MT_ISC)[j], ir2 = ir * ir;
+  const V ihr = cs<V>(S, CS_IHR), iht = cs<V>(S, CS_IHT), ihp = cs<V>(S, CS_IHP);
+  const V rfp = mt<V>(S, MT_RF)[i + 1], rf0 = mt<V>(S, MT_RF)[i];
   V X0 = H<V>(a, b, q);
   V Xrp = H<V>(a, b, q + L.SI), Xrm = H<V>(a, b, q - L.SI);
   V Xtp = H<V>(a, b, q + L.P), Xtm = H<V>(a, b, q - L.P);
   V Xpp = H<V>(a, b, q + 1), Xpm = H<V>(a, b, q - 1);
   V Drr = (rfp * rfp * (Xrp - X0) - rf0 * rf0 * (X0 - Xrm)) * (ir2 * ihr * ihr);
-  V Dtt = ((V)S.sf[j + 1] * (Xtp - X0) - (V)S.sf[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
+  V Dtt = (mt<V>(S, MT_SF)[j + 1] * (Xtp - X0) - mt<V>(S, MT_SF)[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
   V Dpp = (Xpp - (V)2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
   V ar = ((V)ax.A[0][q] + (V)ax.A[0][q + L.SI]) * (V)0.5;
   V at = ((V)ax.A[1][q] + (V)ax.A[1][q + L.P]) * (V)0.5;
@@ -90,9 +90,9 @@ __device__ __forceinline__ void body_resid_T(Shell S, State<R> it, State<R> n, S
   V adv = ar * (Xrp - Xrm) * ((V)0.5 * ihr) + at * (Xtp - Xtm) * ((V)0.5 * ir * iht) +
           ap * (Xpp - Xpm) * ((V)0.5 * ir * is * ihp);
   V f = ax.fT ? (V)ax.fT[q] : (V)0.0;
-  V rate = (V)S.kappa * (Drr + Dtt + Dpp) - adv + f;
+  V rate = cs<V>(S, CS_KAPPA) * (Drr + Dtt + Dpp) - adv + f;
   if (S.Tc_lap) rate += (V)(S.kappa * S.Tc_lap[i]) - ar * (V)S.Tc_dr[i];
-  B[q] = (R)((V)S.dt * rate - ((V)a[q] - (V)b[q]));
+  B[q] = (R)(cs<V>(S, CS_DT) * rate - ((V)a[q] - (V)b[q]));
 }
 
 // pressure entering the momentum rows: P_1 = p_1^n, P_2 = p_2^n + (p_1 - p_1^n)/2
@@ -114,16 +114,16 @@ __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, Sta
   const R *xi = it.f[F_U1R + o], *xn = n.f[F_U1R + o];
   const R *yi = it.f[F_U1T + o], *yn = n.f[F_U1T + o];
   const R *zi = it.f[F_U1P + o], *zn = n.f[F_U1P + o];
-  const V ir = (V)S.irf[i], is = (V)S.isc[j], ir2 = ir * ir;
-  const V ihr = (V)S.ihr, iht = (V)S.iht, ihp = (V)S.ihp;
-  const V rc0 = (V)S.rc[i], rcm = (V)S.rc[i - 1], rfp = (V)S.rf[i + 1], rfm = (V)S.rf[i - 1];
+  const V ir = mt<V>(S, MT_IRF)[i], is = mt<V>(S, MT_ISC)[j], ir2 = ir * ir;
+  const V ihr = cs<V>(S, CS_IHR), iht = cs<V>(S, CS_IHT), ihp = cs<V>(S, CS_IHP);
+  const V rc0 = mt<V>(S, MT_RC)[i], rcm = mt<V>(S, MT_RC)[i - 1], rfp = mt<V>(S, MT_RF)[i + 1], rfm = mt<V>(S, MT_RF)[i - 1];
   const long SI = L.SI, P = L.P;
   V X0 = H<V>(xi, xn, q);
   V Xrp = H<V>(xi, xn, q + SI), Xrm = H<V>(xi, xn, q - SI);
   V Xtp = H<V>(xi, xn, q + P), Xtm = H<V>(xi, xn, q - P);
   V Xpp = H<V>(xi, xn, q + 1), Xpm = H<V>(xi, xn, q - 1);
   V Drr = (rc0 * rc0 * (Xrp - X0) - rcm * rcm * (X0 - Xrm)) * (ir2 * ihr * ihr);
-  V Dtt = ((V)S.sf[j + 1] * (Xtp - X0) - (V)S.sf[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
+  V Dtt = (mt<V>(S, MT_SF)[j + 1] * (Xtp - X0) - mt<V>(S, MT_SF)[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
   V Dpp = (Xpp - (V)2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
   V extra = (V)-2.0 * X0 * ir2 + (V)2.0 * ir2 * ir * (rfp * rfp * Xrp - rfm * rfm * Xrm) * ((V)0.5 * ihr);
   V ar = (V)ax.A[0][q];
@@ -137,10 +137,10 @@ __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, Sta
   V Dc = divh<V>(S, xi, xn, yi, yn, zi, zn, i, j, q);
   V Dm = divh<V>(S, xi, xn, yi, yn, zi, zn, i - 1, j, q - SI);
   V gdiv = (Dc - Dm) * ihr;
-  V buoy = (V)S.PrRa * (V)0.5 * (H<V>(it.f[F_T], n.f[F_T], q - SI) + H<V>(it.f[F_T], n.f[F_T], q));
+  V buoy = cs<V>(S, CS_PRRA) * (V)0.5 * (H<V>(it.f[F_T], n.f[F_T], q - SI) + H<V>(it.f[F_T], n.f[F_T], q));
   V f = ax.fr ? (V)ax.fr[q] : (V)0.0;
-  V rate = (V)S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * (V)S.i2chi + buoy + f;
-  B[q] = (R)((V)S.dt * rate - ((V)xi[q] - (V)xn[q]));
+  V rate = cs<V>(S, CS_NU) * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * cs<V>(S, CS_I2CHI) + buoy + f;
+  B[q] = (R)(cs<V>(S, CS_DT) * rate - ((V)xi[q] - (V)xn[q]));
 }
 
 template <typename R>
@@ -154,16 +154,16 @@ __device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, Sta
   const R *wi = it.f[F_U1R + o], *wn = n.f[F_U1R + o];
   const R *xi = it.f[F_U1T + o], *xn = n.f[F_U1T + o];
   const R *zi = it.f[F_U1P + o], *zn = n.f[F_U1P + o];
-  const V ir = (V)S.irc[i], is = (V)S.isf[j], c = (V)S.cf[j], ir2 = ir * ir;
-  const V ihr = (V)S.ihr, iht = (V)S.iht, ihp = (V)S.ihp;
-  const V rfp = (V)S.rf[i + 1], rf0 = (V)S.rf[i];
+  const V ir = mt<V>(S, MT_IRC)[i], is = mt<V>(S, MT_ISF)[j], c = mt<V>(S, MT_CF)[j], ir2 = ir * ir;
+  const V ihr = cs<V>(S, CS_IHR), iht = cs<V>(S, CS_IHT), ihp = cs<V>(S, CS_IHP);
+  const V rfp = mt<V>(S, MT_RF)[i + 1], rf0 = mt<V>(S, MT_RF)[i];
   const long SI = L.SI, P = L.P;
   V X0 = H<V>(xi, xn, q);
   V Xrp = H<V>(xi, xn, q + SI), Xrm = H<V>(xi, xn, q - SI);
   V Xtp = H<V>(xi, xn, q + P), Xtm = H<V>(xi, xn, q - P);
   V Xpp = H<V>(xi, xn, q + 1), Xpm = H<V>(xi, xn, q - 1);
   V Drr = (rfp * rfp * (Xrp - X0) - rf0 * rf0 * (X0 - Xrm)) * (ir2 * ihr * ihr);
-  V Dtt = ((V)S.sc[j] * (Xtp - X0) - (V)S.sc[j - 1] * (X0 - Xtm)) * (ir2 * is * iht * iht);
+  V Dtt = (mt<V>(S, MT_SC)[j] * (Xtp - X0) - mt<V>(S, MT_SC)[j - 1] * (X0 - Xtm)) * (ir2 * is * iht * iht);
   V Dpp = (Xpp - (V)2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
   V W_j = (V)0.5 * (H<V>(wi, wn, q) + H<V>(wi, wn, q + SI));
   V W_jm = (V)0.5 * (H<V>(wi, wn, q - P) + H<V>(wi, wn, q - P + SI));
@@ -172,7 +172,7 @@ __device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, Sta
   V qjm = (rfp * rfp * H<V>(wi, wn, q + SI - P) - rf0 * rf0 * H<V>(wi, wn, q - P)) * ihr;
   V drr2W = (V)0.5 * (qj + qjm);
   V extra = -X0 * ir2 * is * is +
-            (V)2.0 * c * ir2 * is * is * ((V)S.sf[j + 1] * Xtp - (V)S.sf[j - 1] * Xtm) * ((V)0.5 * iht) +
+            (V)2.0 * c * ir2 * is * is * (mt<V>(S, MT_SF)[j + 1] * Xtp - mt<V>(S, MT_SF)[j - 1] * Xtm) * ((V)0.5 * iht) +
             (V)2.0 * ir2 * dW + (V)2.0 * c * ir2 * ir * is * drr2W;
   V ar = avg4<V>(ax.A[0], q - P, q - P + SI, q, q + SI);
   V at = (V)ax.A[1][q];
@@ -186,8 +186,8 @@ __device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, Sta
   V Dm = divh<V>(S, wi, wn, xi, xn, zi, zn, i, j - 1, q - P);
   V gdiv = (Dc - Dm) * (ir * iht);
   V f = ax.ft ? (V)ax.ft[q] : (V)0.0;
-  V rate = (V)S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * (V)S.i2chi + f;
-  B[q] = (R)((V)S.dt * rate - ((V)xi[q] - (V)xn[q]));
+  V rate = cs<V>(S, CS_NU) * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * cs<V>(S, CS_I2CHI) + f;
+  B[q] = (R)(cs<V>(S, CS_DT) * rate - ((V)xi[q] - (V)xn[q]));
 }
 
 template <typename R>
@@ -201,16 +201,16 @@ __device__ __forceinline__ void body_resid_up(Shell S, int sys, State<R> it, Sta
   const R *wi = it.f[F_U1R + o], *wn = n.f[F_U1R + o];
   const R *yi = it.f[F_U1T + o], *yn = n.f[F_U1T + o];
   const R *xi = it.f[F_U1P + o], *xn = n.f[F_U1P + o];
-  const V ir = (V)S.irc[i], is = (V)S.isc[j], c = (V)S.cc[j], ir2 = ir * ir;
-  const V ihr = (V)S.ihr, iht = (V)S.iht, ihp = (V)S.ihp;
-  const V rfp = (V)S.rf[i + 1], rf0 = (V)S.rf[i];
+  const V ir = mt<V>(S, MT_IRC)[i], is = mt<V>(S, MT_ISC)[j], c = mt<V>(S, MT_CC)[j], ir2 = ir * ir;
+  const V ihr = cs<V>(S, CS_IHR), iht = cs<V>(S, CS_IHT), ihp = cs<V>(S, CS_IHP);
+  const V rfp = mt<V>(S, MT_RF)[i + 1], rf0 = mt<V>(S, MT_RF)[i];
   const long SI = L.SI, P = L.P;
   V X0 = H<V>(xi, xn, q);
   V Xrp = H<V>(xi, xn, q + SI), Xrm = H<V>(xi, xn, q - SI);
   V Xtp = H<V>(xi, xn, q + P), Xtm = H<V>(xi, xn, q - P);
   V Xpp = H<V>(xi, xn, q + 1), Xpm = H<V>(xi, xn, q - 1);
   V Drr = (rfp * rfp * (Xrp - X0) - rf0 * rf0 * (X0 - Xrm)) * (ir2 * ihr * ihr);
-  V Dtt = ((V)S.sf[j + 1] * (Xtp - X0) - (V)S.sf[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
+  V Dtt = (mt<V>(S, MT_SF)[j + 1] * (Xtp - X0) - mt<V>(S, MT_SF)[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
   V Dpp = (Xpp - (V)2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
   V W_k = (V)0.5 * (H<V>(wi, wn, q) + H<V>(wi, wn, q + SI));
   V W_km = (V)0.5 * (H<V>(wi, wn, q - 1) + H<V>(wi, wn, q - 1 + SI));
@@ -230,8 +230,8 @@ __device__ __forceinline__ void body_resid_up(Shell S, int sys, State<R> it, Sta
   V Dm = divh<V>(S, wi, wn, yi, yn, xi, xn, i, j, q - 1);
   V gdiv = (Dc - Dm) * (ir * is * ihp);
   V f = ax.fp ? (V)ax.fp[q] : (V)0.0;
-  V rate = (V)S.nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * (V)S.i2chi + f;
-  B[q] = (R)((V)S.dt * rate - ((V)xi[q] - (V)xn[q]));
+  V rate = cs<V>(S, CS_NU) * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * cs<V>(S, CS_I2CHI) + f;
+  B[q] = (R)(cs<V>(S, CS_DT) * rate - ((V)xi[q] - (V)xn[q]));
 }
 
 template <typename R>
@@ -403,16 +403,16 @@ __device__ __forceinline__ void advecting(const Shell &S, const StepAux<R> &ax, 
 template <typename V, typename R>
 __device__ __forceinline__ void coef(const Shell &S, const StepAux<R> &ax, int loc, int dir, int i, int j, long q,
                                      V &lo, V &di, V &up) {
-  const V ihr = (V)S.ihr, iht = (V)S.iht, ihp = (V)S.ihp;
-  const V nu = (V)((loc == LC) ? S.kappa : S.nu);
+  const V ihr = cs<V>(S, CS_IHR), iht = cs<V>(S, CS_IHT), ihp = cs<V>(S, CS_IHP);
+  const V nu = (loc == LC) ? cs<V>(S, CS_KAPPA) : cs<V>(S, CS_NU);
   double ar_d, at_d, ap_d;
   advecting(S, ax, loc, q, ar_d, at_d, ap_d);
   const V ar = (V)ar_d, at = (V)at_d, ap = (V)ap_d;
-  const V ir = (V)((loc == LR) ? S.irf[i] : S.irc[i]);
-  const V is = (V)((loc == LT) ? S.isf[j] : S.isc[j]);
+  const V ir = (loc == LR) ? mt<V>(S, MT_IRF)[i] : mt<V>(S, MT_IRC)[i];
+  const V is = (loc == LT) ? mt<V>(S, MT_ISF)[j] : mt<V>(S, MT_ISC)[j];
   const V ir2 = ir * ir;
-  const V rc0 = (V)S.rc[i], rcm = (V)S.rc[i - 1], rf0 = (V)S.rf[i], rfp = (V)S.rf[i + 1], rfm = (V)S.rf[i - 1];
-  const V sc0 = (V)S.sc[j], scm = (V)S.sc[j - 1], sf0 = (V)S.sf[j], sfp = (V)S.sf[j + 1], sfm = (V)S.sf[j - 1];
+  const V rc0 = mt<V>(S, MT_RC)[i], rcm = mt<V>(S, MT_RC)[i - 1], rf0 = mt<V>(S, MT_RF)[i], rfp = mt<V>(S, MT_RF)[i + 1], rfm = mt<V>(S, MT_RF)[i - 1];
+  const V sc0 = mt<V>(S, MT_SC)[j], scm = mt<V>(S, MT_SC)[j - 1], sf0 = mt<V>(S, MT_SF)[j], sfp = mt<V>(S, MT_SF)[j + 1], sfm = mt<V>(S, MT_SF)[j - 1];
   V cm, c0, cp;
   if (dir == DR) {
     V cp_d, cm_d;
@@ -430,14 +430,14 @@ __device__ __forceinline__ void coef(const Shell &S, const StepAux<R> &ax, int l
       cm = cm - nu * rfm * rfm * (ir2 * ir * ihr);
       cp = cp + nu * rfp * rfp * (ir2 * ir * ihr);
       c0 = c0 - nu * (V)2.0 * ir2;
-      const V k = (V)S.i2chi, irm = (V)S.irc[i - 1], irc = (V)S.irc[i];
+      const V k = cs<V>(S, CS_I2CHI), irm = mt<V>(S, MT_IRC)[i - 1], irc = mt<V>(S, MT_IRC)[i];
       cm = cm + k * rfm * rfm * (irm * irm * ihr * ihr);
       c0 = c0 - k * (rf0 * rf0 * (irc * irc * ihr * ihr) + rf0 * rf0 * (irm * irm * ihr * ihr));
       cp = cp + k * rfp * rfp * (irc * irc * ihr * ihr);
     }
   } else if (dir == DT) {
     V cp_d, cm_d;
-    const V iR1sq = (V)S.iR1sq;
+    const V iR1sq = cs<V>(S, CS_IR1SQ);
     if (loc == LT) {
       cp_d = sc0 * (iR1sq * is * iht * iht);
       cm_d = scm * (iR1sq * is * iht * iht);
@@ -449,32 +449,32 @@ __device__ __forceinline__ void coef(const Shell &S, const StepAux<R> &ax, int l
     c0 = -nu * (cp_d + cm_d);
     cp = nu * cp_d - at * ((V)0.5 * ir * iht);
     if (loc == LT) {
-      const V c = (V)S.cf[j], s = sf0;
+      const V c = mt<V>(S, MT_CF)[j], s = sf0;
       const V qq = c * ir2 * is * is * iht;
       cm = cm - nu * qq * sfm;
       cp = cp + nu * qq * sfp;
       c0 = c0 - nu * ir2 * is * is;
-      const V k = (V)S.i2chi, isc0 = (V)S.isc[j], iscm = (V)S.isc[j - 1];
+      const V k = cs<V>(S, CS_I2CHI), isc0 = mt<V>(S, MT_ISC)[j], iscm = mt<V>(S, MT_ISC)[j - 1];
       cp = cp + k * sfp * (ir2 * isc0 * iht * iht);
       c0 = c0 - k * (s * (ir2 * isc0 * iht * iht) + s * (ir2 * iscm * iht * iht));
       cm = cm + k * sfm * (ir2 * iscm * iht * iht);
     }
   } else {
-    const V cpm = (V)S.cphi;
+    const V cpm = cs<V>(S, CS_CPHI);
     cm = nu * cpm + ap * ((V)0.5 * ir * is * ihp);
     c0 = (V)-2.0 * nu * cpm;
     cp = nu * cpm - ap * ((V)0.5 * ir * is * ihp);
     if (loc == LP) {
       c0 = c0 - nu * ir2 * is * is;
-      const V qq = (V)S.i2chi * ir2 * is * is * ihp * ihp;
+      const V qq = cs<V>(S, CS_I2CHI) * ir2 * is * is * ihp * ihp;
       cm = cm + qq;
       c0 = c0 - (V)2.0 * qq;
       cp = cp + qq;
     }
   }
-  lo = (V)-0.5 * (V)S.dt * cm;
-  di = (V)1.0 - (V)0.5 * (V)S.dt * c0;
-  up = (V)-0.5 * (V)S.dt * cp;
+  lo = (V)-0.5 * cs<V>(S, CS_DT) * cm;
+  di = (V)1.0 - (V)0.5 * cs<V>(S, CS_DT) * c0;
+  up = (V)-0.5 * cs<V>(S, CS_DT) * cp;
 }
 
 // Line of a (loc, dir) sweep: thread (lane, row) -> patch p, first point
@@ -528,71 +528,278 @@ __device__ __forceinline__ Line decode_line(const Layout &L, int loc, int dir, i
 
 
 template <typename R>
-__device__ __forceinline__ void body_factorize(Shell S, int loc, int dir, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask, int bx, int by) {
+__device__ __forceinline__ void body_factorize(Shell S, int loc, int dir, StepAux<R> ax, R *__restrict__ Lo,
+                                               R *__restrict__ Iv, R *__restrict__ Cp, int patch_mask, int bx,
+                                               int by) {
   using V = typename Cmp<R>::type;
+  constexpr int U = 4;   // rows whose coefficients are formed before the recurrence consumes them
   const Layout &L = S.L;
   const Line ln = decode_line(L, loc, dir, bx * blockDim.x + threadIdx.x, by);
   if (!ln.valid || !((patch_mask >> ln.p) & 1)) return;
   const bool reflect = (dir == DR) && (loc != LR);
+  const long step = ln.step;
   V cprev = (V)0.0;
   long q = lidx(L, ln.p, ln.i, ln.j, ln.k);
-  for (int m = ln.m0; m < ln.m1; ++m, q += ln.step) {
-    int ii = (dir == DR) ? m : ln.i, jj = (dir == DT) ? m : ln.j;
-    V lo, di, up;
-    coef<V>(S, ax, loc, dir, ii, jj, q, lo, di, up);
-    if (m == ln.m0) {
-      if (reflect) di -= lo;
-      lo = (V)0.0;
+  for (int m = ln.m0; m < ln.m1; m += U, q += U * step) {
+    V lo[U], di[U], up[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int mm = m + u;
+      if (mm < ln.m1) {
+        int ii = (dir == DR) ? mm : ln.i, jj = (dir == DT) ? mm : ln.j;
+        coef<V>(S, ax, loc, dir, ii, jj, q + u * step, lo[u], di[u], up[u]);
+        if (mm == ln.m0) {
+          if (reflect) di[u] -= lo[u];
+          lo[u] = (V)0.0;
+        }
+        if (mm == ln.m1 - 1) {
+          if (reflect) di[u] -= up[u];
+          up[u] = (V)0.0;
+        }
+      }
     }
-    if (m == ln.m1 - 1) {
-      if (reflect) di -= up;
-      up = (V)0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (m + u < ln.m1) {
+        V inv = (V)1.0 / (di[u] - lo[u] * cprev);
+        V c = up[u] * inv;
+        Lo[q + u * step] = (R)lo[u];
+        Iv[q + u * step] = (R)inv;
+        Cp[q + u * step] = (R)c;
+        cprev = c;
+      }
     }
-    V inv = (V)1.0 / (di - lo * cprev);
-    V c = up * inv;
-    Lo[q] = (R)lo;
-    Iv[q] = (R)inv;
-    Cp[q] = (R)c;
-    cprev = c;
   }
 }
 
+// Thomas solve with a stored factorisation: forward d'_m = (b_m - lo_m d'_{m-1})
+// / pivot_m into the scratch W, back x_m = d'_m - c'_m x_{m+1}.  Rows are
+// handled in register chunks of U: the loads of a chunk are independent of
+// the recurrence and of every store (separate arrays), so they are in flight
+// together.  Non-final factors write x to B (the next factor's right-hand
+// side); the final factor of an unknown adds x to the iterate and accumulates
+// the FP64 midpoint-rule norm of the increment (Sec. 5.1).
 template <typename R>
-__device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final, const R *__restrict__ Lo, const R *__restrict__ Iv,
-                        const R *__restrict__ Cp, R *B, R *dst, double *norm, int slot, int patch_mask, int bx, int by) {
+__device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final, const R *__restrict__ Lo,
+                                           const R *__restrict__ Iv, const R *__restrict__ Cp, R *__restrict__ B,
+                                           R *__restrict__ W, R *__restrict__ dst, double *norm, int slot,
+                                           int patch_mask, int bx, int by) {
   using V = typename Cmp<R>::type;
+  constexpr int U = 8;
   const Layout &L = S.L;
   const Line ln = decode_line(L, loc, dir, bx * blockDim.x + threadIdx.x, by);
   double contrib = 0.0;
   if (ln.valid && ((patch_mask >> ln.p) & 1)) {
     const long step = ln.step;
-    long q = lidx(L, ln.p, ln.i, ln.j, ln.k);
+    const long q0 = lidx(L, ln.p, ln.i, ln.j, ln.k);
+    const int n = ln.m1 - ln.m0;
+    // forward elimination: B -> W
     V d = (V)0.0;
-    for (int m = ln.m0; m < ln.m1; ++m, q += step) {
-      d = ((V)B[q] - (V)Lo[q] * d) * (V)Iv[q];
-      B[q] = (R)d;
-    }
-    q -= step;
-    V x = d;
-    for (int m = ln.m1 - 1;; --m) {
-      if (final) {
-        dst[q] = (R)((V)dst[q] + x);
-        int ii = (dir == DR) ? m : ln.i, jj = (dir == DT) ? m : ln.j;
-        double r = (loc == LR) ? S.rf[ii] : S.rc[ii];
-        double s = (loc == LT) ? S.sf[jj] : S.sc[jj];
-        contrib += r * r * s * S.hr * S.ht * S.hp * (double)x * (double)x;
-      } else {
-        B[q] = (R)x;
+    for (int m = 0; m < n; m += U) {
+      V b[U], lo[U], iv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        long qq = q0 + (long)(m + u) * step;
+        if (m + u < n) {
+          b[u] = (V)B[qq];
+          lo[u] = (V)Lo[qq];
+          iv[u] = (V)Iv[qq];
+        }
       }
-      if (m == ln.m0) break;
-      q -= step;
-      x = (V)B[q] - (V)Cp[q] * x;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (m + u < n) {
+          d = (b[u] - lo[u] * d) * iv[u];
+          W[q0 + (long)(m + u) * step] = (R)d;
+        }
+      }
+    }
+    // back substitution: W -> B or the iterate, last row first
+    V x = d;
+    for (int m = n - 1; m >= 0; m -= U) {
+      V w[U], c[U], o[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        long qq = q0 + (long)(m - u) * step;
+        if (m - u >= 0) {
+          w[u] = (V)W[qq];
+          c[u] = (V)Cp[qq];
+          o[u] = final ? (V)dst[qq] : (V)0.0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        int mm = m - u;
+        if (mm >= 0) {
+          long qq = q0 + (long)mm * step;
+          if (mm < n - 1) x = w[u] - c[u] * x;
+          if (final) {
+            dst[qq] = (R)(o[u] + x);
+            int row = ln.m0 + mm;
+            int ii = (dir == DR) ? row : ln.i, jj = (dir == DT) ? row : ln.j;
+            double r = (loc == LR) ? S.rf[ii] : S.rc[ii];
+            double s = (loc == LT) ? S.sf[jj] : S.sc[jj];
+            contrib += r * r * s * S.hr * S.ht * S.hp * (double)x * (double)x;
+          } else {
+            B[qq] = (R)x;
+          }
+        }
+      }
     }
   }
   if (final) {
     for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, off);
     if ((threadIdx.x & 31) == 0 && contrib != 0.0) atomicAdd(&norm[slot], contrib);
   }
+}
+
+// Line solve along phi (the contiguous index) through shared memory.  Each
+// warp owns 32 adjacent lines (consecutive theta rows at one radius) and
+// walks them in chunks of 32 rows: the chunk's right-hand side and factors
+// are loaded as a [32 lines][32 rows] tile with coalesced row reads, the 32
+// recurrences run from shared memory (rows padded to 33: no bank conflicts),
+// and results leave the same way.  Same arithmetic as body_solve.
+constexpr int kPhiWarps = 4;   // warps (tiles of 32 lines) per CTA
+template <typename R>
+constexpr int phi_smem_bytes() {
+  return kPhiWarps * 3 * 32 * 33 * (int)sizeof(R);
+}
+
+template <typename R>
+__device__ __forceinline__ void body_solve_phi(Shell S, int loc, int final, const R *__restrict__ Lo,
+                                               const R *__restrict__ Iv, const R *__restrict__ Cp,
+                                               R *__restrict__ B, R *__restrict__ W, R *__restrict__ dst,
+                                               double *norm, int slot, int patch_mask, int bx, R *smem) {
+  using V = typename Cmp<R>::type;
+  const Layout &L = S.L;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = (loc == LR) ? 1 : 0, j0 = (loc == LT) ? 1 : 0, k0 = (loc == LP) ? 1 : 0;
+  const int ni = L.Nr - i0, nj = L.Nt - j0, nk = L.Np - k0;
+  const int jt = (nj + 31) / 32;
+  const long tile = (long)bx * kPhiWarps + warp;
+  double contrib = 0.0;
+  if (tile < 2L * ni * jt) {
+    const int jb = (int)(tile % jt) * 32;
+    const long rest = tile / jt;
+    const int i = i0 + (int)(rest % ni), p = (int)(rest / ni);
+    if ((patch_mask >> p) & 1) {
+      R *t0 = smem + warp * 3 * 32 * 33, *t1 = t0 + 32 * 33, *t2 = t1 + 32 * 33;
+      const bool lv = jb + lane < nj;
+      const long rowbase = lidx(L, p, i, j0 + jb, k0);   // line jb, first row
+      const long lstride = L.P;                          // between adjacent lines
+      const int nch = (nk + 31) / 32;
+      V d = (V)0.0;
+      for (int c = 0; c < nch; ++c) {
+        const int kc = c * 32;
+        const bool kv = kc + lane < nk;
+        for (int r0 = 0; r0 < 32; r0 += 8) {   // 8 rows of loads in flight, then to shared memory
+          R a0[8], a1[8], a2[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int rr = r0 + u;
+            if (jb + rr < nj && kv) {
+              long q = rowbase + rr * lstride + kc + lane;
+              a0[u] = B[q];
+              a1[u] = Lo[q];
+              a2[u] = Iv[q];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int rr = r0 + u;
+            if (jb + rr < nj && kv) {
+              t0[rr * 33 + lane] = a0[u];
+              t1[rr * 33 + lane] = a1[u];
+              t2[rr * 33 + lane] = a2[u];
+            }
+          }
+        }
+        __syncwarp();
+        if (lv) {
+          const int kmax = (nk - kc < 32) ? nk - kc : 32;
+          for (int u = 0; u < kmax; ++u) {
+            d = ((V)t0[lane * 33 + u] - (V)t1[lane * 33 + u] * d) * (V)t2[lane * 33 + u];
+            t0[lane * 33 + u] = (R)d;
+          }
+        }
+        __syncwarp();
+#pragma unroll 8
+        for (int rr = 0; rr < 32; ++rr)
+          if (jb + rr < nj && kv) W[rowbase + rr * lstride + kc + lane] = t0[rr * 33 + lane];
+        __syncwarp();
+      }
+      double wline = 0.0;
+      if (final && lv) {
+        int jj = j0 + jb + lane;
+        double r = (loc == LR) ? S.rf[i] : S.rc[i];
+        double sn = (loc == LT) ? S.sf[jj] : S.sc[jj];
+        wline = r * r * sn * S.hr * S.ht * S.hp;
+      }
+      V x = d;
+      for (int c = nch - 1; c >= 0; --c) {
+        const int kc = c * 32;
+        const bool kv = kc + lane < nk;
+        for (int r0 = 0; r0 < 32; r0 += 8) {
+          R a0[8], a1[8], a2[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int rr = r0 + u;
+            if (jb + rr < nj && kv) {
+              long q = rowbase + rr * lstride + kc + lane;
+              a0[u] = W[q];
+              a1[u] = Cp[q];
+              if (final) a2[u] = dst[q];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int rr = r0 + u;
+            if (jb + rr < nj && kv) {
+              t0[rr * 33 + lane] = a0[u];
+              t1[rr * 33 + lane] = a1[u];
+              if (final) t2[rr * 33 + lane] = a2[u];
+            }
+          }
+        }
+        __syncwarp();
+        if (lv) {
+          const int kmax = (nk - kc < 32) ? nk - kc : 32;
+          for (int u = kmax - 1; u >= 0; --u) {
+            if (kc + u < nk - 1) x = (V)t0[lane * 33 + u] - (V)t1[lane * 33 + u] * x;
+            if (final) {
+              t2[lane * 33 + u] = (R)((V)t2[lane * 33 + u] + x);
+              contrib += wline * (double)x * (double)x;
+            } else {
+              t0[lane * 33 + u] = (R)x;
+            }
+          }
+        }
+        __syncwarp();
+#pragma unroll 8
+        for (int rr = 0; rr < 32; ++rr) {
+          if (jb + rr < nj && kv) {
+            long q = rowbase + rr * lstride + kc + lane;
+            if (final)
+              dst[q] = t2[rr * 33 + lane];
+            else
+              B[q] = t0[rr * 33 + lane];
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  if (final) {
+    for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, off);
+    if (lane == 0 && contrib != 0.0) atomicAdd(&norm[slot], contrib);
+  }
+}
+
+// CTAs of kPhiWarps warps needed by body_solve_phi for one shell
+inline int phi_ctas(const Layout &L, int loc) {
+  int ni = L.Nr - (loc == LR ? 1 : 0), nj = L.Nt - (loc == LT ? 1 : 0);
+  long tiles = 2L * ni * ((nj + 31) / 32);
+  return (int)((tiles + kPhiWarps - 1) / kPhiWarps);
 }
 
 }  // namespace bd

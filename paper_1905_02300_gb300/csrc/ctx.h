@@ -28,7 +28,7 @@ struct Fields {
   State<R> lev[3];           // level n, level n-1, iterate
   R *A[3];                   // advecting velocity
   R *fcomb[4];               // forcing at t_n + dt/2
-  R *B, *Cs;                 // work field, Thomas c' (unused by the stored-LU path)
+  R *B, *Cs;                 // right-hand-side work field, forward-sweep scratch of the line solves
   R *fac[4][3][3];           // per-step LU factors: fac[loc][dir] = {lo, 1/pivot, c'}
   R *modes[kMaxModes][4];    // forcing modes
 };

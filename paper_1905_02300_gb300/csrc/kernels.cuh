@@ -67,8 +67,9 @@ struct Launch {
   static void factorize(const Shell &S, int loc, int dir, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask,
                         cudaStream_t st);
   // line solve with a stored factorisation (same conventions as sweep)
+  // W: scratch for the forward sweep (distinct from B and dst)
   static void solve(const Shell &S, int loc, int dir, bool final, const R *Lo, const R *Iv, const R *Cp, R *B,
-                    R *dst, double *norm, int slot, int patch_mask, cudaStream_t st);
+                    R *W, R *dst, double *norm, int slot, int patch_mask, cudaStream_t st);
   static void pressure(const Shell &S, int sys, State<R> it, State<R> n, double *norm, int patch_mask,
                        cudaStream_t st);
   // host layout <-> device layout; bg (FP64 per radial index, may be null) is

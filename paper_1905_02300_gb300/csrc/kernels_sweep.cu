@@ -94,8 +94,8 @@ __global__ void k_factorize(Shell S, int loc, int dir, StepAux<R> ax, R *Lo, R *
 // FP64 midpoint-rule norm of the increment (Sec. 5.1).
 template <typename R>
 __global__ void k_solve(Shell S, int loc, int dir, int final, const R *__restrict__ Lo, const R *__restrict__ Iv,
-                        const R *__restrict__ Cp, R *B, R *dst, double *norm, int slot, int patch_mask) {
-  bd::body_solve(S, loc, dir, final, Lo, Iv, Cp, B, dst, norm, slot, patch_mask, blockIdx.x, blockIdx.y);
+                        const R *__restrict__ Cp, R *B, R *W, R *dst, double *norm, int slot, int patch_mask) {
+  bd::body_solve(S, loc, dir, final, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, blockIdx.x, blockIdx.y);
 }
 
 dim3 line_grid(const Layout &L, int loc, int dir) {
@@ -123,16 +123,33 @@ void Launch<R>::factorize(const Shell &S, int loc, int dir, StepAux<R> ax, R *Lo
 }
 
 template <typename R>
+__global__ void k_solve_phi(Shell S, int loc, int final, const R *__restrict__ Lo, const R *__restrict__ Iv,
+                            const R *__restrict__ Cp, R *B, R *W, R *dst, double *norm, int slot, int patch_mask) {
+  extern __shared__ __align__(16) unsigned char phi_smem[];
+  bd::body_solve_phi(S, loc, final, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, blockIdx.x, (R *)phi_smem);
+}
+
+template <typename R>
 void Launch<R>::solve(const Shell &S, int loc, int dir, bool final, const R *Lo, const R *Iv, const R *Cp, R *B,
-                      R *dst, double *norm, int slot, int patch_mask, cudaStream_t st) {
-  k_solve<R><<<line_grid(S.L, loc, dir), TPB, 0, st>>>(S, loc, dir, final ? 1 : 0, Lo, Iv, Cp, B, dst, norm, slot,
-                                                        patch_mask);
+                      R *W, R *dst, double *norm, int slot, int patch_mask, cudaStream_t st) {
+  if (dir == DP) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_solve_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::phi_smem_bytes<R>());
+      attr = true;
+    }
+    k_solve_phi<R><<<bd::phi_ctas(S.L, loc), 32 * bd::kPhiWarps, bd::phi_smem_bytes<R>(), st>>>(
+        S, loc, final ? 1 : 0, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask);
+    return;
+  }
+  k_solve<R><<<line_grid(S.L, loc, dir), TPB, 0, st>>>(S, loc, dir, final ? 1 : 0, Lo, Iv, Cp, B, W, dst, norm,
+                                                        slot, patch_mask);
 }
 
 #define YS_INST_SWEEP(R)                                                                                          \
   template void Launch<R>::factorize(const Shell &, int, int, StepAux<R>, R *, R *, R *, int, cudaStream_t);       \
-  template void Launch<R>::solve(const Shell &, int, int, bool, const R *, const R *, const R *, R *, R *, double *, \
-                                 int, int, cudaStream_t);
+  template void Launch<R>::solve(const Shell &, int, int, bool, const R *, const R *, const R *, R *, R *, R *,       \
+                                 double *, int, int, cudaStream_t);
 YS_INST_SWEEP(double)
 YS_INST_SWEEP(float)
 template void Launch<double>::sweep(const Shell &, int, int, bool, StepAux<double>, double *, double *, double *,
@@ -312,6 +329,7 @@ extern "C" int ys_factor_solve_static(const ys_params *prm, int loc, const doubl
   S.i2chi = 1.0 / (2.0 * prm->chi);
   S.iR1sq = 1.0 / (prm->R1 * prm->R1);
   S.cphi = 1.0 / (prm->R1 * prm->R1 * S.sin_theta1 * S.sin_theta1 * hp * hp);
+  shell_fill_fp64(S);
   StepAux<double> ax{};
   for (int a = 0; a < 3; ++a) ax.A[a] = Af[a];
   // factor order, first solved first: T r,theta,phi; u_r theta,phi,r;

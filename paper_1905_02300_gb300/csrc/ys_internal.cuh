@@ -27,6 +27,14 @@ __host__ __device__ inline long lidx(const Layout &L, int p, int i, int j, int k
   return p * L.PS + ((long)(i + 1) * L.NJ + (j + 1)) * (long)L.P + k + 8;
 }
 
+struct Shell;
+
+// Number of FP64 metric tables (rc, rf, sc, sf, cc, cf, irc, irf, isc, isf).
+constexpr int kMetricTables = 10;
+enum MetricTable { MT_RC = 0, MT_RF, MT_SC, MT_SF, MT_CC, MT_CF, MT_IRC, MT_IRF, MT_ISC, MT_ISF };
+// scalar constants mirrored in both arithmetic types
+enum ShellConst { CS_IHR = 0, CS_IHT, CS_IHP, CS_I2CHI, CS_IR1SQ, CS_CPHI, CS_DT, CS_NU, CS_KAPPA, CS_PRRA, CS_NUM };
+
 // Everything a kernel needs about one shell (passed by value).
 struct Shell {
   Layout L;
@@ -44,6 +52,13 @@ struct Shell {
   double i2chi;             // 1/(2 chi)
   double iR1sq;             // 1/R1^2 (modified theta operator)
   double cphi;              // 1/(R1^2 sin^2(theta_1) h_phi^2) (modified phi operator)
+  // the same metric tables and constants indexed by MetricTable / ShellConst,
+  // in FP64 and rounded to FP32 (computed in FP64 on the host), so that FP32
+  // stencils need no per-use conversions
+  const double *dtab[kMetricTables];
+  const float *ftab[kMetricTables];
+  double dcs[CS_NUM];
+  float fcs[CS_NUM];
   double T_in, T_out;       // wall temperatures (of the stored temperature)
   // deviation form (mixed precision): the stored temperature is T - T_c with
   // T_c the discrete conductive profile; its rate gets the FP64 source
@@ -52,8 +67,6 @@ struct Shell {
   int step7;
 };
 
-// Number of FP64 metric tables (rc, rf, sc, sf, cc, cf, irc, irf, isc, isf).
-constexpr int kMetricTables = 10;
 
 // Exchange table entry: one target point in the (theta, phi) plane of a patch,
 // with one or two bilinear donor stencils on the other patch and, for
@@ -69,5 +82,42 @@ struct XEntry {
 
 // Table kinds.
 enum XKind { XT = 0, XUR = 1, XUT = 2, XUP = 3, XP = 4, XNUM = 5 };
+
+}  // namespace ys
+
+namespace ys {
+
+// metric table / constant in the arithmetic type V
+template <typename V>
+__host__ __device__ inline const V *mt(const Shell &S, int t);
+template <>
+__host__ __device__ inline const double *mt<double>(const Shell &S, int t) {
+  return S.dtab[t];
+}
+template <>
+__host__ __device__ inline const float *mt<float>(const Shell &S, int t) {
+  return S.ftab[t];
+}
+template <typename V>
+__host__ __device__ inline V cs(const Shell &S, int c);
+template <>
+__host__ __device__ inline double cs<double>(const Shell &S, int c) {
+  return S.dcs[c];
+}
+template <>
+__host__ __device__ inline float cs<float>(const Shell &S, int c) {
+  return S.fcs[c];
+}
+
+// fill dtab / dcs from the named FP64 fields (ftab / fcs are filled by the owner)
+inline void shell_fill_fp64(Shell &S) {
+  const double *t[kMetricTables] = {S.rc, S.rf, S.sc, S.sf, S.cc, S.cf, S.irc, S.irf, S.isc, S.isf};
+  for (int k = 0; k < kMetricTables; ++k) S.dtab[k] = t[k];
+  const double c[CS_NUM] = {S.ihr, S.iht, S.ihp, S.i2chi, S.iR1sq, S.cphi, S.dt, S.nu, S.kappa, S.PrRa};
+  for (int k = 0; k < CS_NUM; ++k) {
+    S.dcs[k] = c[k];
+    S.fcs[k] = (float)c[k];
+  }
+}
 
 }  // namespace ys
