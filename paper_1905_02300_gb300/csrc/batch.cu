@@ -128,6 +128,17 @@ __global__ void kb_solve(const ShellDev<R> *sh, WorkMap map, int cap, int loc, i
 }
 
 template <typename R>
+__global__ void kb_factorize_phi(const ShellDev<R> *sh, WorkMap map, int cap, int loc) {
+  extern __shared__ __align__(16) unsigned char phi_smem[];
+  YS_BATCH_LOOP(map, cap)
+  (void)by;
+  R *const *F = D.fac[loc][DP];
+  bd::body_factorize_phi(D.S, loc, aux_of(D), F[0], F[1], F[2], 3, bx, (R *)phi_smem);
+  __syncwarp();
+  }
+}
+
+template <typename R>
 __global__ void kb_solve_phi(const ShellDev<R> *sh, WorkMap map, int cap, int loc, int final, int slot) {
   extern __shared__ __align__(16) unsigned char phi_smem[];
   YS_BATCH_LOOP(map, cap)
@@ -336,19 +347,24 @@ void enqueue_step(ys_batch *b) {
   cudaStream_t st = b->stream;
   const int g128 = grid_size(128), g256 = grid_size(256), gl = grid_size(b->tpb_line);
   long nl = 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(kb_solve_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::phi_smem_bytes<R>());
+    cudaFuncSetAttribute(kb_factorize_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::phi_smem_bytes<R>());
+    attr = true;
+  }
+  const int gp = 152 * 4;
   kb_extrapolate<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_EXTRAP), cap);
   ++nl;
   for (int loc = LC; loc <= LP; ++loc)
     for (int dir = DR; dir <= DP; ++dir) {
-      kb_factorize<R><<<gl, b->tpb_line, 0, st>>>(sh, map_of(b, M_LINE0 + 3 * loc + dir), cap, loc, dir);
+      if (dir == DP)
+        kb_factorize_phi<R><<<gp, 32 * bd::kPhiWarps, bd::phi_smem_bytes<R>(), st>>>(sh, map_of(b, M_PHI0 + loc), cap,
+                                                                                    loc);
+      else
+        kb_factorize<R><<<gl, b->tpb_line, 0, st>>>(sh, map_of(b, M_LINE0 + 3 * loc + dir), cap, loc, dir);
       ++nl;
     }
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(kb_solve_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::phi_smem_bytes<R>());
-    attr = true;
-  }
-  const int gp = 152 * 4;
   auto solve = [&](int loc, int slot) {
     for (int s = 0; s < 3; ++s) {
       int dir = kOrderB[loc][s];

@@ -802,5 +802,76 @@ inline int phi_ctas(const Layout &L, int loc) {
   return (int)((tiles + kPhiWarps - 1) / kPhiWarps);
 }
 
+// Per-step factorisation of the phi factor through shared memory (same warp
+// tiles as body_solve_phi): coefficients of a [32 lines][32 rows] tile are
+// formed with lanes along phi (coalesced reads of the advecting velocity),
+// the 32 line recurrences run from shared memory, and the factors leave with
+// coalesced row writes.  Same arithmetic as body_factorize.
+template <typename R>
+__device__ __forceinline__ void body_factorize_phi(Shell S, int loc, StepAux<R> ax, R *__restrict__ Lo,
+                                                   R *__restrict__ Iv, R *__restrict__ Cp, int patch_mask, int bx,
+                                                   R *smem) {
+  using V = typename Cmp<R>::type;
+  const Layout &L = S.L;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = (loc == LR) ? 1 : 0, j0 = (loc == LT) ? 1 : 0, k0 = (loc == LP) ? 1 : 0;
+  const int ni = L.Nr - i0, nj = L.Nt - j0, nk = L.Np - k0;
+  const int jt = (nj + 31) / 32;
+  const long tile = (long)bx * kPhiWarps + warp;
+  if (tile >= 2L * ni * jt) return;
+  const int jb = (int)(tile % jt) * 32;
+  const long rest = tile / jt;
+  const int i = i0 + (int)(rest % ni), p = (int)(rest / ni);
+  if (!((patch_mask >> p) & 1)) return;
+  R *t0 = smem + warp * 3 * 32 * 33, *t1 = t0 + 32 * 33, *t2 = t1 + 32 * 33;
+  const long rowbase = lidx(L, p, i, j0 + jb, k0);
+  const long lstride = L.P;
+  const int nch = (nk + 31) / 32;
+  V cprev = (V)0.0;
+  for (int c = 0; c < nch; ++c) {
+    const int kc = c * 32;
+    const int kk = kc + lane;
+    if (kk < nk) {
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr) {
+        if (jb + rr < nj) {
+          V lo, di, up;
+          coef<V>(S, ax, loc, DP, i, j0 + jb + rr, rowbase + rr * lstride + kk, lo, di, up);
+          if (kk == 0) lo = (V)0.0;
+          if (kk == nk - 1) up = (V)0.0;
+          t0[rr * 33 + lane] = (R)lo;
+          t1[rr * 33 + lane] = (R)di;
+          t2[rr * 33 + lane] = (R)up;
+        }
+      }
+    }
+    __syncwarp();
+    if (jb + lane < nj) {
+      const int kmax = (nk - kc < 32) ? nk - kc : 32;
+      for (int u = 0; u < kmax; ++u) {
+        V lo = (V)t0[lane * 33 + u];
+        V inv = (V)1.0 / ((V)t1[lane * 33 + u] - lo * cprev);
+        V cc = (V)t2[lane * 33 + u] * inv;
+        t1[lane * 33 + u] = (R)inv;
+        t2[lane * 33 + u] = (R)cc;
+        cprev = cc;
+      }
+    }
+    __syncwarp();
+    if (kk < nk) {
+#pragma unroll 8
+      for (int rr = 0; rr < 32; ++rr) {
+        if (jb + rr < nj) {
+          long q = rowbase + rr * lstride + kk;
+          Lo[q] = t0[rr * 33 + lane];
+          Iv[q] = t1[rr * 33 + lane];
+          Cp[q] = t2[rr * 33 + lane];
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace bd
 }  // namespace ys

@@ -110,6 +110,19 @@ dim3 line_grid(const Layout &L, int loc, int dir) {
 }  // namespace
 
 template <typename R>
+__global__ void k_factorize_phi(Shell S, int loc, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask) {
+  extern __shared__ __align__(16) unsigned char phi_smem[];
+  bd::body_factorize_phi(S, loc, ax, Lo, Iv, Cp, patch_mask, blockIdx.x, (R *)phi_smem);
+}
+
+template <typename R>
+__global__ void k_solve_phi(Shell S, int loc, int final, const R *__restrict__ Lo, const R *__restrict__ Iv,
+                            const R *__restrict__ Cp, R *B, R *W, R *dst, double *norm, int slot, int patch_mask) {
+  extern __shared__ __align__(16) unsigned char phi_smem[];
+  bd::body_solve_phi(S, loc, final, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, blockIdx.x, (R *)phi_smem);
+}
+
+template <typename R>
 void Launch<R>::sweep(const Shell &S, int loc, int dir, bool final, StepAux<R> ax, R *B, R *Cs, R *dst,
                       double *norm, int slot, int patch_mask, cudaStream_t st) {
   k_sweep<R><<<line_grid(S.L, loc, dir), TPB, 0, st>>>(S, loc, dir, final ? 1 : 0, ax, B, Cs, dst, norm, slot,
@@ -119,14 +132,17 @@ void Launch<R>::sweep(const Shell &S, int loc, int dir, bool final, StepAux<R> a
 template <typename R>
 void Launch<R>::factorize(const Shell &S, int loc, int dir, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask,
                           cudaStream_t st) {
+  if (dir == DP) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_factorize_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::phi_smem_bytes<R>());
+      attr = true;
+    }
+    k_factorize_phi<R><<<bd::phi_ctas(S.L, loc), 32 * bd::kPhiWarps, bd::phi_smem_bytes<R>(), st>>>(S, loc, ax, Lo,
+                                                                                                   Iv, Cp, patch_mask);
+    return;
+  }
   k_factorize<R><<<line_grid(S.L, loc, dir), TPB, 0, st>>>(S, loc, dir, ax, Lo, Iv, Cp, patch_mask);
-}
-
-template <typename R>
-__global__ void k_solve_phi(Shell S, int loc, int final, const R *__restrict__ Lo, const R *__restrict__ Iv,
-                            const R *__restrict__ Cp, R *B, R *W, R *dst, double *norm, int slot, int patch_mask) {
-  extern __shared__ __align__(16) unsigned char phi_smem[];
-  bd::body_solve_phi(S, loc, final, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, blockIdx.x, (R *)phi_smem);
 }
 
 template <typename R>
