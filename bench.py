@@ -44,19 +44,28 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s per AC step"
 UNIT = "cell-updates/s"
 
-# Algorithmic words moved per cell per launch of each kernel class, counting
-# one read of every input array and one write of every output (neighbour
-# reuse on chip; ghosts ~1/N ignored).  Line solves (k_solve, classes sweep_*):
-# rhs + the three stored LU factors + result = 5, a final factor also reads and
-# writes the iterate = 6; averaged over one iteration's launches.  factorize:
-# advecting component in, three factors out = 4.  See the design doc.
+# Algorithmic traffic per cell per launch of each kernel class: (words of the
+# storage type, FP64 words), one read of every input array and one write of
+# every output (neighbour reuse on chip; ghosts ~1/N ignored).
+#   extrapolate (per step): levels n, n-1 in (7 + 7 bulk, 2 + 2 pressures),
+#     iterate out (7 + 2) and the advecting velocity out (3)
+#   resid_T: T at both levels, the advecting velocity (3), forcing in, B out
+#   resid_u (average of 6): its system's 3 components at both levels, the
+#     advecting velocity (3), forcing, B out, T at both levels for u_r; the
+#     pressures entering the row: p1^n for system 1, p2^n, p1, p1^n for 2
+#   line solves (sweep_*): rhs, the three stored factors, result = 5; a final
+#     factor also reads and writes the iterate = 6; averaged over the launches
+#     of one iteration (r: 2 of 7 final, theta: 2 of 7, phi: 3 of 7)
+#   pressure: 6 velocity values in; FP64: p^n, old and new p (system 1),
+#     p2^n, p1, p1^n, old and new p2 (system 2)
+#   factorize: advecting component in, three factors out
 WORDS_PER_CELL = {
-    "extrapolate": 30.0, "resid_T": 7.0, "resid_u": 82.0 / 6, "sweep_r": 37.0 / 7, "sweep_t": 37.0 / 7,
-    "sweep_p": 38.0 / 7, "pressure": 10.0, "factorize": 4.0,
+    "extrapolate": (24.0, 6.0), "resid_T": (7.0, 0.0), "resid_u": (35.0 / 3, 2.0), "sweep_r": (37.0 / 7, 0.0),
+    "sweep_t": (37.0 / 7, 0.0), "sweep_p": (38.0 / 7, 0.0), "pressure": (6.0, 4.0), "factorize": (4.0, 0.0),
 }
-# FP64 operations per cell (hand count of the kernel formulas, FMA = 2) for the
-# ALU-bound FP64 kernels; a division counts as one operation.
-FLOPS_PER_CELL = {"resid_T": 80.0, "resid_u": 200.0, "pressure": 50.0, "factorize": 70.0}
+# FP64 operations per cell (hand count of the kernel formulas, FMA = 2, a
+# division = 1) for the FP64 form, whose kernels are bound by the FP64 pipe.
+FLOPS_PER_CELL = {"resid_T": 42.0, "resid_u": 91.0, "pressure": 21.0, "factorize": 11.0}
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of GB300 (profiling recipe)
 
 
@@ -339,6 +348,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--ref-n", type=int, default=48)
+    ap.add_argument("--ref-steps", type=int, default=8, help="oracle steps of the cpu_baseline sample (~12 s)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
@@ -438,8 +448,7 @@ def main():
     for k, (t_ms, n_l) in prof.items():
         key = "solve" if k.startswith("sweep_") else k
         w = WORDS_PER_CELL.get(k)
-        wb = 8.0 if not mixed else (5.6 if k == "pressure" else 4.0)
-        b = (w * wb * cells * n_l) if w is not None else 0.0
+        b = ((w[0] * (4.0 if mixed else 8.0) + w[1] * 8.0) * cells * n_l) if w is not None else 0.0
         m = merged.setdefault(key, [0.0, 0, 0.0, 0.0])
         m[0] += t_ms
         m[1] += n_l
@@ -462,10 +471,10 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, el = oracle_sample(args.ref_n, K, 1)
+        v, el = oracle_sample(args.ref_n, K, args.ref_steps)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"1 AC step (K={K}) of a {args.ref_n}x{args.ref_n}x{3*args.ref_n}-per-patch shell, "
-                         f"same physics and dt, numpy on 1 host core, {el:.1f} s"}
+               "sample": f"{args.ref_steps} AC steps (K={K}) of a {args.ref_n}x{args.ref_n}x{3*args.ref_n}-per-patch "
+                         f"shell, same physics and dt, numpy on 1 host core, {el:.1f} s"}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,

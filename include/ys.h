@@ -122,6 +122,19 @@ int ys_set_fields_ex(ys_ctx *c, int level, const double *T, const double *ur, co
 int ys_set_forcing(ys_ctx *c, int mode, int time_fn, const double *f_T, const double *f_r,
                    const double *f_th, const double *f_ph);
 
+/* Dirichlet velocity on the walls r = R1 and r = R2 (Sec. 2: the velocity is
+ * prescribed on the boundary; the paper's Landau-jet runs of Sec. 5.1 use
+ * the jet's own wall values), constant in time, in each patch's local basis.
+ * Host arrays (FP64, copied in, caller keeps ownership), wall 0 = R1, 1 = R2:
+ *   ur  [wall][patch][Nth][Nph]      u_r on the wall faces
+ *   uth [wall][patch][Nth + 1][Nph]  u_theta at r = R1, R2 on theta-faces
+ *   uph [wall][patch][Nth][Nph + 1]  u_phi at r = R1, R2 on phi-faces
+ * u_r takes the value on the wall faces; u_theta, u_phi get the reflection
+ * ghosts 2 g - x_0.  A NULL component means no-slip for that component.  The
+ * boundary values of the stored levels are refreshed.
+ * Errors: YS_EINVAL, YS_ENOMEM, YS_ECUDA. */
+int ys_set_wall_velocity(ys_ctx *c, const double *ur, const double *uth, const double *uph);
+
 /* Set the time t_n of level 0. */
 int ys_set_time(ys_ctx *c, double t);
 
@@ -262,8 +275,10 @@ int ys_submit(ys_server *s, const ys_params *p, const double *init_fields, int n
  * *latency_s.  A failed request (e.g. NaN data) returns its error code; other
  * requests are not affected. */
 int ys_poll(ys_server *s, uint64_t ticket, int *state, double *out_fields, double *latency_s);
-/* Batched steps run, cell-updates done, requests running and queued. */
-int ys_server_stats(ys_server *s, long *steps_run, double *cell_updates, int *running, int *queued);
+/* Batched steps run, cell-updates done, requests running and queued now, and
+ * the most requests that were ever running together.  Any pointer may be NULL. */
+int ys_server_stats(ys_server *s, long *steps_run, double *cell_updates, int *running, int *queued,
+                    int *peak_running);
 int ys_server_destroy(ys_server *s);
 
 const char *ys_strerror(int code);

@@ -120,7 +120,7 @@ def _interp(a_donor, st, i_slice):
             + wj * (1 - wk) * A[:, J + 1, K] + wj * wk * A[:, J + 1, K + 1])
 
 
-def exchange_into(tables, target, fields, patches, T_walls=(0.0, 0.0)):
+def exchange_into(tables, target, fields, patches, T_walls=(0.0, 0.0), U_walls=None):
     """Fill the boundary values of the listed target ``patches`` from the other
     patch, for the state dict ``fields`` (padded arrays with keys 'T' and the
     velocity lists 'u1', 'u2').  Donor values are read from a snapshot taken
@@ -145,27 +145,39 @@ def exchange_into(tables, target, fields, patches, T_walls=(0.0, 0.0)):
                 vt = _interp(S[1][d], e["st"], cells)
                 vp = _interp(S[2][d], e["sp"], cells)
                 U[comp][p][cells, e["j"] + 1, e["k"] + 1] = e["rot"][0] * vt + e["rot"][1] * vp
-    wall_ghosts(g, target, patches, T_walls)
+    wall_ghosts(g, target, patches, T_walls, U_walls)
 
 
-def wall_ghosts(g, fields, patches, T_walls=(0.0, 0.0)):
-    """Radial wall data: u_r on the wall faces is the wall value (0); cell-centred
-    quantities get the reflection ghost 2 g - x_0 on their unknown columns."""
+def wall_ghosts(g, fields, patches, T_walls=(0.0, 0.0), U_walls=None):
+    """Radial wall data (Sec. 2, Dirichlet walls): u_r on the wall faces is the
+    wall value; cell-centred quantities in r (T, u_theta, u_phi) get the
+    reflection ghost 2 g - x_0 on their unknown columns, g the wall value.
+    U_walls: None (no-slip) or wall velocities as in Params.wall_u."""
     Nr, Nt, Np = g.Nr, g.Nth, g.Nph
     for p in patches:
         T = fields["T"][p]
         T[0, 1:Nt + 1, 1:Np + 1] = 2.0 * T_walls[0] - T[1, 1:Nt + 1, 1:Np + 1]
         T[Nr + 1, 1:Nt + 1, 1:Np + 1] = 2.0 * T_walls[1] - T[Nr, 1:Nt + 1, 1:Np + 1]
+        if U_walls is None:
+            gr = (0.0, 0.0)
+            gt = (0.0, 0.0)
+            gp = (0.0, 0.0)
+        else:
+            gr = (U_walls["ur"][0][p], U_walls["ur"][1][p])
+            gt = (U_walls["uth"][0][p][1:Nt, :], U_walls["uth"][1][p][1:Nt, :])
+            gp = (U_walls["uph"][0][p][:, 1:Np], U_walls["uph"][1][p][:, 1:Np])
         for key in ("u1", "u2"):
             U = fields[key]
             U[0][p][1, :, :] = 0.0
             U[0][p][Nr + 1, :, :] = 0.0
+            U[0][p][1, 1:Nt + 1, 1:Np + 1] = gr[0]
+            U[0][p][Nr + 1, 1:Nt + 1, 1:Np + 1] = gr[1]
             ut = U[1][p]
-            ut[0, 2:Nt + 1, 1:Np + 1] = -ut[1, 2:Nt + 1, 1:Np + 1]
-            ut[Nr + 1, 2:Nt + 1, 1:Np + 1] = -ut[Nr, 2:Nt + 1, 1:Np + 1]
+            ut[0, 2:Nt + 1, 1:Np + 1] = 2.0 * gt[0] - ut[1, 2:Nt + 1, 1:Np + 1]
+            ut[Nr + 1, 2:Nt + 1, 1:Np + 1] = 2.0 * gt[1] - ut[Nr, 2:Nt + 1, 1:Np + 1]
             up = U[2][p]
-            up[0, 1:Nt + 1, 2:Np + 1] = -up[1, 1:Nt + 1, 2:Np + 1]
-            up[Nr + 1, 1:Nt + 1, 2:Np + 1] = -up[Nr, 1:Nt + 1, 2:Np + 1]
+            up[0, 1:Nt + 1, 2:Np + 1] = 2.0 * gp[0] - up[1, 1:Nt + 1, 2:Np + 1]
+            up[Nr + 1, 1:Nt + 1, 2:Np + 1] = 2.0 * gp[1] - up[Nr, 1:Nt + 1, 2:Np + 1]
 
 
 def pressure_ring(tables, P, patches):

@@ -33,6 +33,7 @@ The l2 norm (Sec. 5.1) is the midpoint rule with weight r^2 sin(theta).
 from __future__ import annotations
 
 from dataclasses import dataclass, field
+from typing import Optional
 
 import numpy as np
 
@@ -62,6 +63,10 @@ class Params:
     T_out: float = 0.0
     step7: bool = True
     kappa: float = 1.0
+    # Dirichlet velocity on the walls r = R1, R2 (steady), in each patch's local
+    # basis: dict 'ur' [2 walls][2 patches][Nth][Nph], 'uth' [..][Nth+1][Nph],
+    # 'uph' [..][Nth][Nph+1]; None = no-slip
+    wall_u: Optional[dict] = None
 
 
 def _time_fn(tid, t):
@@ -135,7 +140,7 @@ class Oracle:
 
     def _refresh(self, L, patches):
         d = L.as_dict()
-        xch.exchange_into(self.tables, d, d, patches, (self.prm.T_in, self.prm.T_out))
+        xch.exchange_into(self.tables, d, d, patches, (self.prm.T_in, self.prm.T_out), self.prm.wall_u)
         if self.prm.step7:
             xch.pressure_ring(self.tables, L.p1, patches)
             xch.pressure_ring(self.tables, L.p2, patches)
@@ -201,7 +206,7 @@ class Oracle:
         for k in range(1, K + 1):
             if prm.schwarz_mode == "additive":
                 d = it.as_dict()
-                xch.exchange_into(self.tables, d, d, (0, 1), (prm.T_in, prm.T_out))
+                xch.exchange_into(self.tables, d, d, (0, 1), (prm.T_in, prm.T_out), prm.wall_u)
                 norms = self._iterate(it, n, A, f, fac, (0, 1))
                 if prm.step7:
                     xch.pressure_ring(self.tables, it.p1, (0, 1))
@@ -210,7 +215,7 @@ class Oracle:
                 norms = np.zeros(len(FIELD_NAMES))
                 for p in (0, 1):
                     d = it.as_dict()
-                    xch.exchange_into(self.tables, d, d, (p,), (prm.T_in, prm.T_out))
+                    xch.exchange_into(self.tables, d, d, (p,), (prm.T_in, prm.T_out), prm.wall_u)
                     norms += self._iterate(it, n, A, f, fac, (p,)) ** 2
                     if prm.step7:
                         xch.pressure_ring(self.tables, it.p1, (p,))

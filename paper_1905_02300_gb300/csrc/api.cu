@@ -168,6 +168,14 @@ void factorize_all(ys_ctx *c, StepAux<R> ax) {
     }
 }
 
+// boundary values of both stored levels from their interiors
+template <typename R>
+void refresh_levels(ys_ctx *c) {
+  Fields<R> &D = F<R>(c);
+  refresh<R>(c, D.lev[0], 3);
+  refresh<R>(c, D.lev[1], 3);
+}
+
 // one defect-correction pass over T, u1, p1, u2, p2 on the masked patches
 template <typename R>
 void iterate(ys_ctx *c, StepAux<R> ax, int mask) {
@@ -181,7 +189,7 @@ void iterate(ys_ctx *c, StepAux<R> ax, int mask) {
       LAUNCH(c, K_RES_U, 1, Launch<R>::resid_u(c->S, sys, comp, it, n, ax, D.B, mask, c->stream));
       solve_unknown<R>(c, LR + comp, F_U1R + comp + o, mask);
     }
-    LAUNCH(c, K_PRES, 1, Launch<R>::pressure(c->S, sys, it, n, c->norm, mask, c->stream));
+    LAUNCH(c, K_PRES, 2, Launch<R>::pressure(c->S, sys, it, n, c->norm, c->stage, mask, c->stream));
   }
 }
 
@@ -439,6 +447,7 @@ int ys_destroy(ys_ctx *c) {
   for (int m = 0; m < kMaxModes; ++m)
     if (c->modes_mem[m]) cudaFree(c->modes_mem[m]);
   if (c->dmem) cudaFree(c->dmem);
+  if (c->dwall) cudaFree(c->dwall);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c->f64;
   delete c->f32;
@@ -502,9 +511,30 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   size_t stage_elems = user_elems(L, LR);
   if (user_elems(L, LT) > stage_elems) stage_elems = user_elems(L, LT);
   if (user_elems(L, LP) > stage_elems) stage_elems = user_elems(L, LP);
+  // residual row-coefficient tables (FP64 and FP32 copies)
+  std::vector<double> rowt[kRowTables];
+  RowPhys ph{p->dt, p->Pr, 1.0, 1.0 / (2.0 * p->chi), p->Pr * p->Ra, deviation ? Tlap.data() : nullptr,
+             deviation ? Tdr.data() : nullptr};
+  make_rowcoef(gs, G, met, pad, len, ph, rowt);
+  std::vector<double> fact;
+  {
+    const double s1 = std::sin(G.th0);
+    FacPhys fp{p->dt, p->Pr, 1.0, 1.0 / (2.0 * p->chi), 1.0 / (p->R1 * p->R1),
+               1.0 / (p->R1 * p->R1 * s1 * s1 * G.hp * G.hp)};
+    make_faccoef(gs, G, met, pad, len, fp, fact);
+  }
+  size_t row_elems = 0, row_off[kRowTables];
+  for (int t = 0; t < kRowTables; ++t) {
+    row_off[t] = row_elems;
+    row_elems += (rowt[t].size() + 31) / 32 * 32;
+  }
+  const size_t fac_off = row_elems;   // the line-operator tables follow the residual tables
+  row_elems += (fact.size() + 31) / 32 * 32;
   size_t off_metric = bulk_bytes + p_bytes;
   size_t off_fmet = off_metric + ((met.size() * sizeof(double) + 255) / 256) * 256;
-  size_t off_x = off_fmet + ((met.size() * sizeof(float) + 255) / 256) * 256;
+  size_t off_rowd = off_fmet + ((2 * met.size() * sizeof(float) + 255) / 256) * 256;
+  size_t off_rowf = off_rowd + ((row_elems * sizeof(double) + 255) / 256) * 256;
+  size_t off_x = off_rowf + ((row_elems * sizeof(float) + 255) / 256) * 256;
   size_t off_dev = off_x + ((xcount * sizeof(XEntry) + 255) / 256) * 256;
   size_t dev_bytes = ((4 * (size_t)(p->Nr + 2) * sizeof(double) + 255) / 256) * 256;
   size_t off_norm = off_dev + dev_bytes;
@@ -544,8 +574,28 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   }
   double *metric = (double *)(base + off_metric);
   float *fmetric = (float *)(base + off_fmet);
-  std::vector<float> fmet(met.begin(), met.end());   // FP64 tables rounded once to FP32
+  // FP64 tables rounded once to FP32, then the FP32 remainders (double-float pairs)
+  std::vector<float> fmet(2 * met.size());
+  for (size_t u = 0; u < met.size(); ++u) {
+    fmet[u] = (float)met[u];
+    fmet[met.size() + u] = (float)(met[u] - (double)fmet[u]);
+  }
   cudaMemcpyAsync(fmetric, fmet.data(), fmet.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  double *rowd = (double *)(base + off_rowd);
+  float *rowf = (float *)(base + off_rowf);
+  std::vector<double> rowh(row_elems, 0.0);
+  std::vector<float> rowhf(row_elems, 0.0f);
+  for (int t = 0; t < kRowTables; ++t)
+    for (size_t u = 0; u < rowt[t].size(); ++u) {
+      rowh[row_off[t] + u] = rowt[t][u];
+      rowhf[row_off[t] + u] = (float)rowt[t][u];
+    }
+  for (size_t u = 0; u < fact.size(); ++u) {
+    rowh[fac_off + u] = fact[u];
+    rowhf[fac_off + u] = (float)fact[u];
+  }
+  cudaMemcpyAsync(rowd, rowh.data(), row_elems * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(rowf, rowhf.data(), row_elems * sizeof(float), cudaMemcpyHostToDevice, c->stream);
   c->xdev = (XEntry *)(base + off_x);
   double *devtab = (double *)(base + off_dev);
   c->norm = (double *)(base + off_norm);
@@ -591,9 +641,19 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   S.T_out = p->T_outer;
   S.Tc_lap = nullptr;
   S.Tc_dr = nullptr;
+  S.wall_ur = S.wall_ut = S.wall_up = nullptr;
   S.step7 = p->step7;
   shell_fill_fp64(S);
-  for (int k = 0; k < kMetricTables; ++k) S.ftab[k] = fmetric + k * len + pad;
+  for (int k = 0; k < kMetricTables; ++k) {
+    S.ftab[k] = fmetric + k * len + pad;
+    S.ltab[k] = fmetric + met.size() + k * len + pad;
+  }
+  for (int t = 0; t < kRowTables; ++t) {
+    S.rowd[t] = rowd + row_off[t];
+    S.rowf[t] = rowf + row_off[t];
+  }
+  S.facd = rowd + fac_off;
+  S.facf = rowf + fac_off;
   if (deviation) {
     // device tables: [Tc at centres i = 0..Nr-1 | pc | Tc_lap | Tc_dr], each Nr + 2 long
     const size_t n = p->Nr + 2;
@@ -612,7 +672,7 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
     S.T_in = 0.0;   // the deviation has homogeneous reflection walls
     S.T_out = 0.0;
   }
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {   // also keeps fmet alive until copied
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {   // also keeps the host tables alive until copied
     ys_destroy(c);
     return YS_ECUDA;
   }
@@ -652,6 +712,40 @@ int ys_set_forcing(ys_ctx *c, int mode, int time_fn_id, const double *f_T, const
   c->mode_fn[mode] = time_fn_id;
   c->mode_set[mode] = 1;
   if (mode + 1 > c->nmodes_set) c->nmodes_set = mode + 1;
+  return YS_OK;
+}
+
+int ys_set_wall_velocity(ys_ctx *c, const double *ur, const double *uth, const double *uph) {
+  if (!c) return YS_EINVAL;
+  const long Nt = c->L.Nt, Np = c->L.Np;
+  const size_t n[3] = {(size_t)(4 * Nt * Np), (size_t)(4 * (Nt + 1) * Np), (size_t)(4 * Nt * (Np + 1))};
+  const double *src[3] = {ur, uth, uph};
+  if (!c->dwall && (ur || uth || uph)) {
+    if (cudaMalloc(&c->dwall, (n[0] + n[1] + n[2]) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      c->dwall = nullptr;
+      return YS_ENOMEM;
+    }
+  }
+  const double **dst[3] = {&c->S.wall_ur, &c->S.wall_ut, &c->S.wall_up};
+  size_t off = 0;
+  for (int m = 0; m < 3; ++m) {
+    if (src[m]) {
+      if (cudaMemcpyAsync(c->dwall + off, src[m], n[m] * sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess)
+        return YS_ECUDA;
+      *dst[m] = c->dwall + off;
+    } else {
+      *dst[m] = nullptr;
+    }
+    off += n[m];
+  }
+  // boundary values of the stored levels follow the new wall data
+  if (c->f32)
+    refresh_levels<float>(c);
+  else
+    refresh_levels<double>(c);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return YS_ECUDA;
   return YS_OK;
 }
 

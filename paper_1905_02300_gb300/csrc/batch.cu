@@ -53,8 +53,8 @@ struct WorkMap {
 
 enum MapId {
   M_EXTRAP = 0, M_EX0, M_EX1, M_EX2, M_EX3, M_WALLS, M_RING, M_RC, M_RR, M_RT, M_RP, M_LINE0,
-  M_PHI0 = M_LINE0 + 12,   // shared-memory phi solves, one map per unknown type
-  M_NUM = M_PHI0 + 4
+  M_PSC0 = M_LINE0 + 12,   // warp-scan phi factorisations and solves (one line per warp), per unknown type
+  M_NUM = M_PSC0 + 4
 };
 
 namespace {
@@ -129,22 +129,23 @@ __global__ void kb_solve(const ShellDev<R> *sh, WorkMap map, int cap, int loc, i
 
 template <typename R>
 __global__ void kb_factorize_phi(const ShellDev<R> *sh, WorkMap map, int cap, int loc) {
-  extern __shared__ __align__(16) unsigned char phi_smem[];
   YS_BATCH_LOOP(map, cap)
   (void)by;
   R *const *F = D.fac[loc][DP];
-  bd::body_factorize_phi(D.S, loc, aux_of(D), F[0], F[1], F[2], 3, bx, (R *)phi_smem);
+  bd::body_factorize_phi_scan(D.S, loc, aux_of(D), F[0], F[1], F[2], 3, bx);
   __syncwarp();
   }
 }
 
 template <typename R>
-__global__ void kb_solve_phi(const ShellDev<R> *sh, WorkMap map, int cap, int loc, int final, int slot) {
+__global__ void kb_solve_phi(const ShellDev<R> *sh, WorkMap map, int cap, int loc, int final, int slot,
+                             int smem_per_warp) {
   extern __shared__ __align__(16) unsigned char phi_smem[];
   YS_BATCH_LOOP(map, cap)
   (void)by;
   R *const *F = D.fac[loc][DP];
-  bd::body_solve_phi(D.S, loc, final, F[0], F[1], F[2], D.B, D.W, it.f[slot], D.norm, slot, 3, bx, (R *)phi_smem);
+  bd::body_solve_phi_scan(D.S, loc, final, F[0], F[1], F[2], D.B, D.W, it.f[slot], D.norm, slot, 3, bx,
+                          (R *)phi_smem, smem_per_warp);
   __syncwarp();
   }
 }
@@ -168,11 +169,21 @@ __global__ void kb_resid_u(const ShellDev<R> *sh, WorkMap map, int cap, int sys,
   }
 }
 
+// Norm shares are summed per thread while the CTA stays on one shell and
+// flushed (one atomic per warp) when its work moves to another shell.
 template <typename R>
 __global__ void kb_pressure(const ShellDev<R> *sh, WorkMap map, int cap, int sys) {
+  typename Cmp<R>::type part = 0;
+  int cur = -1;
   YS_BATCH_LOOP(map, cap)
-  bd::body_pressure(D.S, sys, it, n, D.norm, 3, bx, by);
+  if (s != cur) {
+    if (cur >= 0) bd::norm_flush(part, sh[cur].S.dcs[CS_VOL], &sh[cur].norm[sys == 1 ? 4 : 8]);
+    part = 0;
+    cur = s;
   }
+  part += bd::body_pressure(D.S, sys, it, n, 3, bx, by);
+  }
+  if (cur >= 0) bd::norm_flush(part, sh[cur].S.dcs[CS_VOL], &sh[cur].norm[sys == 1 ? 4 : 8]);
 }
 
 template <typename R>
@@ -221,8 +232,8 @@ void grid_of(const ys_ctx *c, int map, int tpb_line, int &gx, int &gy) {
     int ni = L.Nr - (loc == LR), nj = L.Nt - (loc == LT), nk = L.Np - (loc == LP);
     gx = cdiv(nk, 128);
     gy = 2 * ni * nj;
-  } else if (map >= M_PHI0) {
-    gx = bd::phi_ctas(L, map - M_PHI0);
+  } else if (map >= M_PSC0) {
+    gx = bd::phi_scan_ctas(L, map - M_PSC0);
   } else {
     int loc = (map - M_LINE0) / 3, dir = (map - M_LINE0) % 3;
     int ni = L.Nr - (loc == LR), nj = L.Nt - (loc == LT), nk = L.Np - (loc == LP);
@@ -349,18 +360,25 @@ void enqueue_step(ys_batch *b) {
   long nl = 0;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(kb_solve_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::phi_smem_bytes<R>());
-    cudaFuncSetAttribute(kb_factorize_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::phi_smem_bytes<R>());
+    cudaFuncSetAttribute(kb_solve_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::kScanSmemMax);
     attr = true;
   }
+  // shared-memory positions per warp of the phi solves: the longest line of the
+  // batch that fits; shells with longer lines keep their forward results in W
+  int spw = 0;
+  for (int s = 0; s < cap; ++s) {
+    if (!b->slot[s]) continue;
+    const int pad = bd::scan_pad(b->slot[s]->L.Np);
+    if (pad > spw && (size_t)bd::kScanWarps * pad * sizeof(R) <= (size_t)bd::kScanSmemMax) spw = pad;
+  }
+  const size_t spw_bytes = (size_t)bd::kScanWarps * spw * sizeof(R);
   const int gp = 152 * 4;
   kb_extrapolate<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_EXTRAP), cap);
   ++nl;
   for (int loc = LC; loc <= LP; ++loc)
     for (int dir = DR; dir <= DP; ++dir) {
       if (dir == DP)
-        kb_factorize_phi<R><<<gp, 32 * bd::kPhiWarps, bd::phi_smem_bytes<R>(), st>>>(sh, map_of(b, M_PHI0 + loc), cap,
-                                                                                    loc);
+        kb_factorize_phi<R><<<gp, 32 * bd::kScanWarps, 0, st>>>(sh, map_of(b, M_PSC0 + loc), cap, loc);
       else
         kb_factorize<R><<<gl, b->tpb_line, 0, st>>>(sh, map_of(b, M_LINE0 + 3 * loc + dir), cap, loc, dir);
       ++nl;
@@ -369,8 +387,8 @@ void enqueue_step(ys_batch *b) {
     for (int s = 0; s < 3; ++s) {
       int dir = kOrderB[loc][s];
       if (dir == DP)
-        kb_solve_phi<R><<<gp, 32 * bd::kPhiWarps, bd::phi_smem_bytes<R>(), st>>>(sh, map_of(b, M_PHI0 + loc), cap,
-                                                                               loc, s == 2, slot);
+        kb_solve_phi<R><<<gp, 32 * bd::kScanWarps, spw_bytes, st>>>(sh, map_of(b, M_PSC0 + loc), cap, loc, s == 2,
+                                                                   slot, spw);
       else
         kb_solve<R><<<gl, b->tpb_line, 0, st>>>(sh, map_of(b, M_LINE0 + 3 * loc + dir), cap, loc, dir, s == 2,
                                                  slot);
@@ -673,6 +691,7 @@ struct ys_server {
   std::thread worker;
   long steps_run = 0;
   double cell_updates = 0.0;
+  int peak_running = 0;   // most requests ever resident together
 };
 
 namespace {
@@ -713,6 +732,7 @@ void server_loop(ys_server *S) {
       } else {
         r->state = 1;
         S->running.push_back(r);
+        if ((int)S->running.size() > S->peak_running) S->peak_running = (int)S->running.size();
       }
     }
     std::vector<Request *> run;
@@ -767,11 +787,15 @@ void server_loop(ys_server *S) {
 }
 
 size_t footprint(const ys_params &p) {
-  // bulk fields (66), FP64 pressures (6), staging and tables; forcing is not
-  // used by served shells
+  // bulk fields (66), FP64 pressures (6), residual row tables, staging and
+  // the small tables; forcing is not used by served shells
   size_t elems = 2ul * (p.Nr + 2) * (p.Nth + 2) * (size_t)(((p.Nph + 2) + 7) / 8 * 8) + 64;
   size_t R = (p.precision == YS_MIXED) ? 4 : 8;
-  return elems * (66 * R + 6 * 8) + packed_len(p) * 8 / 2 + (1u << 20);
+  size_t rowrec = 0;   // residual and line-operator row records, FP64 + FP32
+  for (int t = 0; t < kRowTables; ++t) rowrec += row_m(t);
+  rowrec += kFacTables * FC_M;
+  size_t rows = (size_t)(p.Nr + 2) * (p.Nth + 2) * rowrec * 12;
+  return elems * (66 * R + 6 * 8) + rows + packed_len(p) * 8 / 2 + (1u << 20);
 }
 
 }  // namespace
@@ -837,13 +861,15 @@ int ys_poll(ys_server *S, uint64_t ticket, int *state, double *out_fields, doubl
   return YS_OK;
 }
 
-int ys_server_stats(ys_server *S, long *steps_run, double *cell_updates, int *running, int *queued) {
+int ys_server_stats(ys_server *S, long *steps_run, double *cell_updates, int *running, int *queued,
+                    int *peak_running) {
   if (!S) return YS_EINVAL;
   std::lock_guard<std::mutex> lk(S->mu);
   if (steps_run) *steps_run = S->steps_run;
   if (cell_updates) *cell_updates = S->cell_updates;
   if (running) *running = (int)S->running.size();
   if (queued) *queued = (int)S->queue.size();
+  if (peak_running) *peak_running = S->peak_running;
   return YS_OK;
 }
 

@@ -25,6 +25,55 @@ __device__ __forceinline__ V havg4(const R *a, const R *b, long q1, long q2, lon
   return ((H<V>(a, b, q1) + H<V>(a, b, q2)) + H<V>(a, b, q3) + H<V>(a, b, q4)) * (V)0.25;
 }
 
+// Double-float arithmetic: a value carried as the unevaluated sum hi + lo of
+// two FP32 numbers (about 48 significant bits), built from the error-free
+// transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2) and the FMA form of
+// Dekker's TwoProduct (Dekker 1971), each result renormalised by FastTwoSum.
+// On this GPU FP64 instructions (conversions included) issue at 1/64 of the
+// FP32 rate, so FP64-accurate sums of FP32 data are cheaper this way.  The
+// explicit _rn intrinsics keep the compiler from contracting the error terms.
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_fast(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  const FF s = two_sum(x.hi, y.hi);
+  return ff_fast(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+
+__device__ __forceinline__ FF ff_sub(FF x, FF y) { return ff_add(x, FF{-y.hi, -y.lo}); }
+
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return ff_fast(p, e);
+}
+
+__device__ __forceinline__ double ff_double(FF x) { return (double)x.hi + (double)x.lo; }
+
+// metric table entry / shell constant as a double-float pair
+__device__ __forceinline__ FF ff_mt(const Shell &S, int t, int i) { return {S.ftab[t][i], S.ltab[t][i]}; }
+__device__ __forceinline__ FF ff_cs(const Shell &S, int c) { return {S.fcs[c], S.lcs[c]}; }
+
+// exact half-level average 0.5 (a + b) of two FP32 values
+__device__ __forceinline__ FF ff_H(const float *a, const float *b, long q) {
+  const FF s = two_sum(a[q], b[q]);
+  return {0.5f * s.hi, 0.5f * s.lo};
+}
+
 // region of unknowns of a location type, logical half-open ranges
 __device__ __forceinline__ void region(const Layout &L, int loc, int &i0, int &i1, int &j0, int &j1, int &k0,
                                        int &k1) {
@@ -52,47 +101,74 @@ __device__ __forceinline__ bool decode_point(const Layout &L, int loc, int patch
   return k < k1 && ((patch_mask >> p) & 1);
 }
 
-// discrete divergence of the half-level velocity at cell (p, i, j, k)
-template <typename V, typename R>
-__device__ __forceinline__ V divh(const Shell &S, const R *ri, const R *rn, const R *ti, const R *tn, const R *pi,
-                                  const R *pn, int i, int j, long q) {
+// velocity component c (0 r, 1 theta, 2 phi) of system sys, chosen by selects
+// (an index computed at run time would move the State structs to local memory)
+template <typename R>
+__device__ __forceinline__ R *velf(const State<R> &s, int sys, int c) {
+  if (c == 0) return sys == 1 ? s.f[F_U1R] : s.f[F_U2R];
+  if (c == 1) return sys == 1 ? s.f[F_U1T] : s.f[F_U2T];
+  return sys == 1 ? s.f[F_U1P] : s.f[F_U2P];
+}
+
+// Discrete divergence of the half-level FP32 velocity at cell (p, i, j, k)
+// (Sec. 3.3: conservative face differences with the metric at the faces), in
+// double-float arithmetic: FP64-accurate terms at FP32 instruction cost.
+__device__ __forceinline__ FF divh_ff(const Shell &S, const float *ri, const float *rn, const float *ti,
+                                      const float *tn, const float *pi, const float *pn, int i, int j, long q) {
   const Layout &L = S.L;
-  const V ir = mt<V>(S, MT_IRC)[i], is = mt<V>(S, MT_ISC)[j];
-  const V rfp = mt<V>(S, MT_RF)[i + 1], rf0 = mt<V>(S, MT_RF)[i];
-  V d_r = (rfp * rfp * H<V>(ri, rn, q + L.SI) - rf0 * rf0 * H<V>(ri, rn, q)) * (ir * ir * cs<V>(S, CS_IHR));
-  V d_t = (mt<V>(S, MT_SF)[j + 1] * H<V>(ti, tn, q + L.P) - mt<V>(S, MT_SF)[j] * H<V>(ti, tn, q)) * (ir * is * cs<V>(S, CS_IHT));
-  V d_p = (H<V>(pi, pn, q + 1) - H<V>(pi, pn, q)) * (ir * is * cs<V>(S, CS_IHP));
-  return d_r + d_t + d_p;
+  const FF ir = ff_mt(S, MT_IRC, i), is = ff_mt(S, MT_ISC, j);
+  const FF rfp = ff_mt(S, MT_RF, i + 1), rf0 = ff_mt(S, MT_RF, i);
+  FF d_r = ff_sub(ff_mul(ff_mul(rfp, rfp), ff_H(ri, rn, q + L.SI)), ff_mul(ff_mul(rf0, rf0), ff_H(ri, rn, q)));
+  d_r = ff_mul(d_r, ff_mul(ff_mul(ir, ir), ff_cs(S, CS_IHR)));
+  const FF irs = ff_mul(ir, is);
+  FF d_t = ff_sub(ff_mul(ff_mt(S, MT_SF, j + 1), ff_H(ti, tn, q + L.P)), ff_mul(ff_mt(S, MT_SF, j), ff_H(ti, tn, q)));
+  d_t = ff_mul(d_t, ff_mul(irs, ff_cs(S, CS_IHT)));
+  FF d_p = ff_sub(ff_H(pi, pn, q + 1), ff_H(pi, pn, q));
+  d_p = ff_mul(d_p, ff_mul(irs, ff_cs(S, CS_IHP)));
+  return ff_add(ff_add(d_r, d_t), d_p);
 }
 
 
+// sum S = a + b of the two time levels at q (twice the half-level value)
+template <typename V, typename R>
+__device__ __forceinline__ V Sm(const R *a, const R *b, long q) {
+  return (V)a[q] + (V)b[q];
+}
+
+// Residuals -F = dt Rate(psi^{1/2}) - (psi - psi^n) of the defect correction
+// (Sec. 4, Eq. er) on the MAC grid (Sec. 3.2, 3.3).  Each is the discrete
+// operator written as a linear form in the two-level sums S of the stencil
+// values, with the per-row coefficient records of RowTable (all metric
+// factors, spacings, dt and the physical constants folded in), plus the
+// products of the extrapolated advecting velocity with differences of S.
+// The diffusion parts keep the differenced form (S_+ - S_0) - (S_0 - S_-)
+// of the conservative three-point operator.
+
+// temperature at cell centres: kappa Laplacian, advection, forcing, and in
+// the deviation form the conductive-profile source
 template <typename R>
 __device__ __forceinline__ void body_resid_T(Shell S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
   if (!decode_point(L, LC, patch_mask, bx, by, p, i, j, k)) return;
-  long q = lidx(L, p, i, j, k);
+  const long q = lidx(L, p, i, j, k), SI = L.SI, P = L.P;
+  const V *c = rowc<V>(S, RT_T, i, j);
   const R *a = it.f[F_T], *b = n.f[F_T];
-  const V ir = mt<V>(S, MT_IRC)[i], is = mt<V>(S, MT_ISC)[j], ir2 = ir * ir;
-  const V ihr = cs<V>(S, CS_IHR), iht = cs<V>(S, CS_IHT), ihp = cs<V>(S, CS_IHP);
-  const V rfp = mt<V>(S, MT_RF)[i + 1], rf0 = mt<V>(S, MT_RF)[i];
-  V X0 = H<V>(a, b, q);
-  V Xrp = H<V>(a, b, q + L.SI), Xrm = H<V>(a, b, q - L.SI);
-  V Xtp = H<V>(a, b, q + L.P), Xtm = H<V>(a, b, q - L.P);
-  V Xpp = H<V>(a, b, q + 1), Xpm = H<V>(a, b, q - 1);
-  V Drr = (rfp * rfp * (Xrp - X0) - rf0 * rf0 * (X0 - Xrm)) * (ir2 * ihr * ihr);
-  V Dtt = (mt<V>(S, MT_SF)[j + 1] * (Xtp - X0) - mt<V>(S, MT_SF)[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
-  V Dpp = (Xpp - (V)2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
-  V ar = ((V)ax.A[0][q] + (V)ax.A[0][q + L.SI]) * (V)0.5;
-  V at = ((V)ax.A[1][q] + (V)ax.A[1][q + L.P]) * (V)0.5;
-  V ap = ((V)ax.A[2][q] + (V)ax.A[2][q + 1]) * (V)0.5;
-  V adv = ar * (Xrp - Xrm) * ((V)0.5 * ihr) + at * (Xtp - Xtm) * ((V)0.5 * ir * iht) +
-          ap * (Xpp - Xpm) * ((V)0.5 * ir * is * ihp);
-  V f = ax.fT ? (V)ax.fT[q] : (V)0.0;
-  V rate = cs<V>(S, CS_KAPPA) * (Drr + Dtt + Dpp) - adv + f;
-  if (S.Tc_lap) rate += (V)(S.kappa * S.Tc_lap[i]) - ar * (V)S.Tc_dr[i];
-  B[q] = (R)(cs<V>(S, CS_DT) * rate - ((V)a[q] - (V)b[q]));
+  const V S0 = Sm<V>(a, b, q);
+  const V Srp = Sm<V>(a, b, q + SI), Srm = Sm<V>(a, b, q - SI);
+  const V Stp = Sm<V>(a, b, q + P), Stm = Sm<V>(a, b, q - P);
+  const V Spp = Sm<V>(a, b, q + 1), Spm = Sm<V>(a, b, q - 1);
+  const V diff = c[T_RP] * (Srp - S0) - c[T_RM] * (S0 - Srm) + c[T_TP] * (Stp - S0) - c[T_TM] * (S0 - Stm) +
+                 c[T_PP] * (Spp - (V)2.0 * S0 + Spm);
+  const V sAr = (V)ax.A[0][q] + (V)ax.A[0][q + SI];
+  const V sAt = (V)ax.A[1][q] + (V)ax.A[1][q + P];
+  const V sAp = (V)ax.A[2][q] + (V)ax.A[2][q + 1];
+  const V adv = c[T_AR] * sAr * (Srp - Srm) + c[T_AT] * sAt * (Stp - Stm) + c[T_AP] * sAp * (Spp - Spm);
+  V out = diff - adv;
+  if (ax.fT) out += cs<V>(S, CS_DT) * (V)ax.fT[q];
+  if (S.Tc_lap) out += c[T_G0] - sAr * c[T_G1];
+  B[q] = (R)(out - ((V)a[q] - (V)b[q]));
 }
 
 // pressure entering the momentum rows: P_1 = p_1^n, P_2 = p_2^n + (p_1 - p_1^n)/2
@@ -102,170 +178,166 @@ __device__ __forceinline__ double pres(const State<R> &it, const State<R> &n, in
   return n.p[1][q] + 0.5 * (it.p[0][q] - n.p[0][q]);
 }
 
-
+// u_r at r-faces: nu (vector Laplacian), -advection (with the curvature
+// terms), -grad P, grad(div)/(2 chi), buoyancy, forcing
 template <typename R>
 __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
   if (!decode_point(L, LR, patch_mask, bx, by, p, i, j, k)) return;
-  long q = lidx(L, p, i, j, k);
-  int o = (sys == 1) ? 0 : 4;
-  const R *xi = it.f[F_U1R + o], *xn = n.f[F_U1R + o];
-  const R *yi = it.f[F_U1T + o], *yn = n.f[F_U1T + o];
-  const R *zi = it.f[F_U1P + o], *zn = n.f[F_U1P + o];
-  const V ir = mt<V>(S, MT_IRF)[i], is = mt<V>(S, MT_ISC)[j], ir2 = ir * ir;
-  const V ihr = cs<V>(S, CS_IHR), iht = cs<V>(S, CS_IHT), ihp = cs<V>(S, CS_IHP);
-  const V rc0 = mt<V>(S, MT_RC)[i], rcm = mt<V>(S, MT_RC)[i - 1], rfp = mt<V>(S, MT_RF)[i + 1], rfm = mt<V>(S, MT_RF)[i - 1];
-  const long SI = L.SI, P = L.P;
-  V X0 = H<V>(xi, xn, q);
-  V Xrp = H<V>(xi, xn, q + SI), Xrm = H<V>(xi, xn, q - SI);
-  V Xtp = H<V>(xi, xn, q + P), Xtm = H<V>(xi, xn, q - P);
-  V Xpp = H<V>(xi, xn, q + 1), Xpm = H<V>(xi, xn, q - 1);
-  V Drr = (rc0 * rc0 * (Xrp - X0) - rcm * rcm * (X0 - Xrm)) * (ir2 * ihr * ihr);
-  V Dtt = (mt<V>(S, MT_SF)[j + 1] * (Xtp - X0) - mt<V>(S, MT_SF)[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
-  V Dpp = (Xpp - (V)2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
-  V extra = (V)-2.0 * X0 * ir2 + (V)2.0 * ir2 * ir * (rfp * rfp * Xrp - rfm * rfm * Xrm) * ((V)0.5 * ihr);
-  V ar = (V)ax.A[0][q];
-  V at = avg4<V>(ax.A[1], q - SI, q - SI + P, q, q + P);
-  V ap = avg4<V>(ax.A[2], q - SI, q - SI + 1, q, q + 1);
-  V bt = havg4<V>(yi, yn, q - SI, q - SI + P, q, q + P);
-  V bp = havg4<V>(zi, zn, q - SI, q - SI + 1, q, q + 1);
-  V adv = ar * (Xrp - Xrm) * ((V)0.5 * ihr) + at * (Xtp - Xtm) * ((V)0.5 * ir * iht) +
-          ap * (Xpp - Xpm) * ((V)0.5 * ir * is * ihp) - (at * bt + ap * bp) * ir;
-  V gradP = (V)((pres(it, n, sys, q) - pres(it, n, sys, q - SI)) * S.ihr);
-  V Dc = divh<V>(S, xi, xn, yi, yn, zi, zn, i, j, q);
-  V Dm = divh<V>(S, xi, xn, yi, yn, zi, zn, i - 1, j, q - SI);
-  V gdiv = (Dc - Dm) * ihr;
-  V buoy = cs<V>(S, CS_PRRA) * (V)0.5 * (H<V>(it.f[F_T], n.f[F_T], q - SI) + H<V>(it.f[F_T], n.f[F_T], q));
-  V f = ax.fr ? (V)ax.fr[q] : (V)0.0;
-  V rate = cs<V>(S, CS_NU) * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * cs<V>(S, CS_I2CHI) + buoy + f;
-  B[q] = (R)(cs<V>(S, CS_DT) * rate - ((V)xi[q] - (V)xn[q]));
+  const long q = lidx(L, p, i, j, k), SI = L.SI, P = L.P;
+  const V *c = rowc<V>(S, RT_UR, i, j);
+  const R *xi = velf(it, sys, 0), *xn = velf(n, sys, 0);
+  const R *yi = velf(it, sys, 1), *yn = velf(n, sys, 1);
+  const R *zi = velf(it, sys, 2), *zn = velf(n, sys, 2);
+  const V S0 = Sm<V>(xi, xn, q);
+  const V Srp = Sm<V>(xi, xn, q + SI), Srm = Sm<V>(xi, xn, q - SI);
+  const V Stp = Sm<V>(xi, xn, q + P), Stm = Sm<V>(xi, xn, q - P);
+  const V Spp = Sm<V>(xi, xn, q + 1), Spm = Sm<V>(xi, xn, q - 1);
+  // u_theta and u_phi around the face: the two cells sharing it
+  const V y1 = Sm<V>(yi, yn, q + P), y0 = Sm<V>(yi, yn, q), ym1 = Sm<V>(yi, yn, q - SI + P), ym0 = Sm<V>(yi, yn, q - SI);
+  const V z1 = Sm<V>(zi, zn, q + 1), z0 = Sm<V>(zi, zn, q), zm1 = Sm<V>(zi, zn, q - SI + 1), zm0 = Sm<V>(zi, zn, q - SI);
+  const V diff = c[UR_RP] * (Srp - S0) - c[UR_RM] * (S0 - Srm) + c[UR_TP] * (Stp - S0) - c[UR_TM] * (S0 - Stm) +
+                 c[UR_PP] * (Spp - (V)2.0 * S0 + Spm);
+  const V own = c[UR_O1] * Srp + c[UR_O0] * S0 + c[UR_OM] * Srm;
+  const V gd = c[UR_GT1] * y1 + c[UR_GT0] * y0 + c[UR_GTM1] * ym1 + c[UR_GTM0] * ym0 + c[UR_GP1] * (z1 - z0) +
+               c[UR_GPM1] * (zm1 - zm0);
+  const R *A1 = ax.A[1], *A2 = ax.A[2];
+  const V ar = (V)ax.A[0][q];
+  const V sAt = ((V)A1[q - SI] + (V)A1[q - SI + P]) + (V)A1[q] + (V)A1[q + P];
+  const V sAp = ((V)A2[q - SI] + (V)A2[q - SI + 1]) + (V)A2[q] + (V)A2[q + 1];
+  const V adv = c[UR_AR] * ar * (Srp - Srm) + c[UR_AT] * sAt * (Stp - Stm) + c[UR_AP] * sAp * (Spp - Spm);
+  const V curv = c[UR_CV] * (sAt * (((ym0 + ym1) + y0) + y1) + sAp * (((zm0 + zm1) + z0) + z1));
+  const V gradP = (V)(pres(it, n, sys, q) - pres(it, n, sys, q - SI)) * c[UR_GPR];
+  const V buoy = c[UR_BY] * (Sm<V>(it.f[F_T], n.f[F_T], q - SI) + Sm<V>(it.f[F_T], n.f[F_T], q));
+  V out = diff + own + gd - adv + curv - gradP + buoy;
+  if (ax.fr) out += cs<V>(S, CS_DT) * (V)ax.fr[q];
+  B[q] = (R)(out - ((V)xi[q] - (V)xn[q]));
 }
 
+// u_theta at theta-faces
 template <typename R>
 __device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
   if (!decode_point(L, LT, patch_mask, bx, by, p, i, j, k)) return;
-  long q = lidx(L, p, i, j, k);
-  int o = (sys == 1) ? 0 : 4;
-  const R *wi = it.f[F_U1R + o], *wn = n.f[F_U1R + o];
-  const R *xi = it.f[F_U1T + o], *xn = n.f[F_U1T + o];
-  const R *zi = it.f[F_U1P + o], *zn = n.f[F_U1P + o];
-  const V ir = mt<V>(S, MT_IRC)[i], is = mt<V>(S, MT_ISF)[j], c = mt<V>(S, MT_CF)[j], ir2 = ir * ir;
-  const V ihr = cs<V>(S, CS_IHR), iht = cs<V>(S, CS_IHT), ihp = cs<V>(S, CS_IHP);
-  const V rfp = mt<V>(S, MT_RF)[i + 1], rf0 = mt<V>(S, MT_RF)[i];
-  const long SI = L.SI, P = L.P;
-  V X0 = H<V>(xi, xn, q);
-  V Xrp = H<V>(xi, xn, q + SI), Xrm = H<V>(xi, xn, q - SI);
-  V Xtp = H<V>(xi, xn, q + P), Xtm = H<V>(xi, xn, q - P);
-  V Xpp = H<V>(xi, xn, q + 1), Xpm = H<V>(xi, xn, q - 1);
-  V Drr = (rfp * rfp * (Xrp - X0) - rf0 * rf0 * (X0 - Xrm)) * (ir2 * ihr * ihr);
-  V Dtt = (mt<V>(S, MT_SC)[j] * (Xtp - X0) - mt<V>(S, MT_SC)[j - 1] * (X0 - Xtm)) * (ir2 * is * iht * iht);
-  V Dpp = (Xpp - (V)2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
-  V W_j = (V)0.5 * (H<V>(wi, wn, q) + H<V>(wi, wn, q + SI));
-  V W_jm = (V)0.5 * (H<V>(wi, wn, q - P) + H<V>(wi, wn, q - P + SI));
-  V dW = (W_j - W_jm) * iht;
-  V qj = (rfp * rfp * H<V>(wi, wn, q + SI) - rf0 * rf0 * H<V>(wi, wn, q)) * ihr;
-  V qjm = (rfp * rfp * H<V>(wi, wn, q + SI - P) - rf0 * rf0 * H<V>(wi, wn, q - P)) * ihr;
-  V drr2W = (V)0.5 * (qj + qjm);
-  V extra = -X0 * ir2 * is * is +
-            (V)2.0 * c * ir2 * is * is * (mt<V>(S, MT_SF)[j + 1] * Xtp - mt<V>(S, MT_SF)[j - 1] * Xtm) * ((V)0.5 * iht) +
-            (V)2.0 * ir2 * dW + (V)2.0 * c * ir2 * ir * is * drr2W;
-  V ar = avg4<V>(ax.A[0], q - P, q - P + SI, q, q + SI);
-  V at = (V)ax.A[1][q];
-  V ap = avg4<V>(ax.A[2], q - P, q - P + 1, q, q + 1);
-  V br = havg4<V>(wi, wn, q - P, q - P + SI, q, q + SI);
-  V bp = havg4<V>(zi, zn, q - P, q - P + 1, q, q + 1);
-  V adv = ar * (Xrp - Xrm) * ((V)0.5 * ihr) + at * (Xtp - Xtm) * ((V)0.5 * ir * iht) +
-          ap * (Xpp - Xpm) * ((V)0.5 * ir * is * ihp) + (at * br - ap * bp * c * is) * ir;
-  V gradP = (V)((pres(it, n, sys, q) - pres(it, n, sys, q - P)) * (S.irc[i] * S.iht));
-  V Dc = divh<V>(S, wi, wn, xi, xn, zi, zn, i, j, q);
-  V Dm = divh<V>(S, wi, wn, xi, xn, zi, zn, i, j - 1, q - P);
-  V gdiv = (Dc - Dm) * (ir * iht);
-  V f = ax.ft ? (V)ax.ft[q] : (V)0.0;
-  V rate = cs<V>(S, CS_NU) * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * cs<V>(S, CS_I2CHI) + f;
-  B[q] = (R)(cs<V>(S, CS_DT) * rate - ((V)xi[q] - (V)xn[q]));
+  const long q = lidx(L, p, i, j, k), SI = L.SI, P = L.P;
+  const V *c = rowc<V>(S, RT_UT, i, j);
+  const R *wi = velf(it, sys, 0), *wn = velf(n, sys, 0);
+  const R *xi = velf(it, sys, 1), *xn = velf(n, sys, 1);
+  const R *zi = velf(it, sys, 2), *zn = velf(n, sys, 2);
+  const V S0 = Sm<V>(xi, xn, q);
+  const V Srp = Sm<V>(xi, xn, q + SI), Srm = Sm<V>(xi, xn, q - SI);
+  const V Stp = Sm<V>(xi, xn, q + P), Stm = Sm<V>(xi, xn, q - P);
+  const V Spp = Sm<V>(xi, xn, q + 1), Spm = Sm<V>(xi, xn, q - 1);
+  // u_r and u_phi around the face: the two cells sharing it
+  const V w1 = Sm<V>(wi, wn, q + SI), w0 = Sm<V>(wi, wn, q), wm1 = Sm<V>(wi, wn, q + SI - P), wm0 = Sm<V>(wi, wn, q - P);
+  const V z1 = Sm<V>(zi, zn, q + 1), z0 = Sm<V>(zi, zn, q), zm1 = Sm<V>(zi, zn, q - P + 1), zm0 = Sm<V>(zi, zn, q - P);
+  const V diff = c[UT_RP] * (Srp - S0) - c[UT_RM] * (S0 - Srm) + c[UT_TP] * (Stp - S0) - c[UT_TM] * (S0 - Stm) +
+                 c[UT_PP] * (Spp - (V)2.0 * S0 + Spm);
+  const V own = c[UT_OTP] * Stp + c[UT_O0] * S0 + c[UT_OTM] * Stm;
+  const V gd = c[UT_W1] * w1 + c[UT_W0] * w0 + c[UT_WM1] * wm1 + c[UT_WM0] * wm0 + c[UT_GP1] * (z1 - z0) +
+               c[UT_GPM1] * (zm1 - zm0);
+  const R *A0 = ax.A[0], *A2 = ax.A[2];
+  const V sAr = ((V)A0[q - P] + (V)A0[q - P + SI]) + (V)A0[q] + (V)A0[q + SI];
+  const V at = (V)ax.A[1][q];
+  const V sAp = ((V)A2[q - P] + (V)A2[q - P + 1]) + (V)A2[q] + (V)A2[q + 1];
+  const V adv = c[UT_AR] * sAr * (Srp - Srm) + c[UT_AT] * at * (Stp - Stm) + c[UT_AP] * sAp * (Spp - Spm);
+  const V curv = c[UT_CP] * sAp * (((zm0 + zm1) + z0) + z1) - c[UT_CW] * at * (((wm0 + wm1) + w0) + w1);
+  const V gradP = (V)(pres(it, n, sys, q) - pres(it, n, sys, q - P)) * c[UT_GPR];
+  V out = diff + own + gd - adv + curv - gradP;
+  if (ax.ft) out += cs<V>(S, CS_DT) * (V)ax.ft[q];
+  B[q] = (R)(out - ((V)xi[q] - (V)xn[q]));
 }
 
+// u_phi at phi-faces
 template <typename R>
 __device__ __forceinline__ void body_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
   if (!decode_point(L, LP, patch_mask, bx, by, p, i, j, k)) return;
-  long q = lidx(L, p, i, j, k);
-  int o = (sys == 1) ? 0 : 4;
-  const R *wi = it.f[F_U1R + o], *wn = n.f[F_U1R + o];
-  const R *yi = it.f[F_U1T + o], *yn = n.f[F_U1T + o];
-  const R *xi = it.f[F_U1P + o], *xn = n.f[F_U1P + o];
-  const V ir = mt<V>(S, MT_IRC)[i], is = mt<V>(S, MT_ISC)[j], c = mt<V>(S, MT_CC)[j], ir2 = ir * ir;
-  const V ihr = cs<V>(S, CS_IHR), iht = cs<V>(S, CS_IHT), ihp = cs<V>(S, CS_IHP);
-  const V rfp = mt<V>(S, MT_RF)[i + 1], rf0 = mt<V>(S, MT_RF)[i];
-  const long SI = L.SI, P = L.P;
-  V X0 = H<V>(xi, xn, q);
-  V Xrp = H<V>(xi, xn, q + SI), Xrm = H<V>(xi, xn, q - SI);
-  V Xtp = H<V>(xi, xn, q + P), Xtm = H<V>(xi, xn, q - P);
-  V Xpp = H<V>(xi, xn, q + 1), Xpm = H<V>(xi, xn, q - 1);
-  V Drr = (rfp * rfp * (Xrp - X0) - rf0 * rf0 * (X0 - Xrm)) * (ir2 * ihr * ihr);
-  V Dtt = (mt<V>(S, MT_SF)[j + 1] * (Xtp - X0) - mt<V>(S, MT_SF)[j] * (X0 - Xtm)) * (ir2 * is * iht * iht);
-  V Dpp = (Xpp - (V)2.0 * X0 + Xpm) * (ir2 * is * is * ihp * ihp);
-  V W_k = (V)0.5 * (H<V>(wi, wn, q) + H<V>(wi, wn, q + SI));
-  V W_km = (V)0.5 * (H<V>(wi, wn, q - 1) + H<V>(wi, wn, q - 1 + SI));
-  V Y_k = (V)0.5 * (H<V>(yi, yn, q) + H<V>(yi, yn, q + P));
-  V Y_km = (V)0.5 * (H<V>(yi, yn, q - 1) + H<V>(yi, yn, q - 1 + P));
-  V extra = -X0 * ir2 * is * is + (V)2.0 * ir2 * is * (W_k - W_km) * ihp +
-            (V)2.0 * c * ir2 * is * is * (Y_k - Y_km) * ihp;
-  V ar = avg4<V>(ax.A[0], q - 1, q - 1 + SI, q, q + SI);
-  V at = avg4<V>(ax.A[1], q - 1, q - 1 + P, q, q + P);
-  V ap = (V)ax.A[2][q];
-  V br = havg4<V>(wi, wn, q - 1, q - 1 + SI, q, q + SI);
-  V bt = havg4<V>(yi, yn, q - 1, q - 1 + P, q, q + P);
-  V adv = ar * (Xrp - Xrm) * ((V)0.5 * ihr) + at * (Xtp - Xtm) * ((V)0.5 * ir * iht) +
-          ap * (Xpp - Xpm) * ((V)0.5 * ir * is * ihp) + (ap * br + ap * bt * c * is) * ir;
-  V gradP = (V)((pres(it, n, sys, q) - pres(it, n, sys, q - 1)) * (S.irc[i] * S.isc[j] * S.ihp));
-  V Dc = divh<V>(S, wi, wn, yi, yn, xi, xn, i, j, q);
-  V Dm = divh<V>(S, wi, wn, yi, yn, xi, xn, i, j, q - 1);
-  V gdiv = (Dc - Dm) * (ir * is * ihp);
-  V f = ax.fp ? (V)ax.fp[q] : (V)0.0;
-  V rate = cs<V>(S, CS_NU) * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv * cs<V>(S, CS_I2CHI) + f;
-  B[q] = (R)(cs<V>(S, CS_DT) * rate - ((V)xi[q] - (V)xn[q]));
+  const long q = lidx(L, p, i, j, k), SI = L.SI, P = L.P;
+  const V *c = rowc<V>(S, RT_UP, i, j);
+  const R *wi = velf(it, sys, 0), *wn = velf(n, sys, 0);
+  const R *yi = velf(it, sys, 1), *yn = velf(n, sys, 1);
+  const R *xi = velf(it, sys, 2), *xn = velf(n, sys, 2);
+  const V S0 = Sm<V>(xi, xn, q);
+  const V Srp = Sm<V>(xi, xn, q + SI), Srm = Sm<V>(xi, xn, q - SI);
+  const V Stp = Sm<V>(xi, xn, q + P), Stm = Sm<V>(xi, xn, q - P);
+  const V Spp = Sm<V>(xi, xn, q + 1), Spm = Sm<V>(xi, xn, q - 1);
+  // u_r and u_theta around the face: the two cells sharing it
+  const V w1 = Sm<V>(wi, wn, q + SI), w0 = Sm<V>(wi, wn, q), wm1 = Sm<V>(wi, wn, q - 1 + SI), wm0 = Sm<V>(wi, wn, q - 1);
+  const V y1 = Sm<V>(yi, yn, q + P), y0 = Sm<V>(yi, yn, q), ym1 = Sm<V>(yi, yn, q - 1 + P), ym0 = Sm<V>(yi, yn, q - 1);
+  const V diff = c[UP_RP] * (Srp - S0) - c[UP_RM] * (S0 - Srm) + c[UP_TP] * (Stp - S0) - c[UP_TM] * (S0 - Stm) +
+                 c[UP_PP] * (Spp - (V)2.0 * S0 + Spm);
+  const V gd = c[UP_E0] * S0 + c[UP_W1] * w1 + c[UP_W0] * w0 + c[UP_WM1] * wm1 + c[UP_WM0] * wm0 + c[UP_Y1] * y1 +
+               c[UP_Y0] * y0 + c[UP_YM1] * ym1 + c[UP_YM0] * ym0;
+  const R *A0 = ax.A[0], *A1 = ax.A[1];
+  const V sAr = ((V)A0[q - 1] + (V)A0[q - 1 + SI]) + (V)A0[q] + (V)A0[q + SI];
+  const V sAt = ((V)A1[q - 1] + (V)A1[q - 1 + P]) + (V)A1[q] + (V)A1[q + P];
+  const V ap = (V)ax.A[2][q];
+  const V adv = c[UP_AR] * sAr * (Srp - Srm) + c[UP_AT] * sAt * (Stp - Stm) + c[UP_AP] * ap * (Spp - Spm);
+  const V curv = ap * (c[UP_CW] * (((wm0 + wm1) + w0) + w1) + c[UP_CY] * (((ym0 + ym1) + y0) + y1));
+  const V gradP = (V)(pres(it, n, sys, q) - pres(it, n, sys, q - 1)) * c[UP_GPR];
+  V out = diff + gd - adv - curv - gradP;
+  if (ax.fp) out += cs<V>(S, CS_DT) * (V)ax.fp[q];
+  B[q] = (R)(out - ((V)xi[q] - (V)xn[q]));
 }
 
+// Pressure update of one cell (Eq. nst_Mass1 for system 1, Eq. ac2 for system
+// 2).  Returns the cell's share r^2 sin(theta) (p_new - p_old)^2 of the
+// midpoint-rule norm of the pressure increment without the constant cell
+// volume (norm_flush applies it); step-7 ring cells contribute nothing.  The
+// caller accumulates shares over many cells, so that one atomic serves many
+// thousands of cells.
 template <typename R>
-__device__ __forceinline__ void body_pressure(Shell S, int sys, State<R> it, State<R> n, double *norm, int patch_mask, int bx, int by) {
+__device__ __forceinline__ typename Cmp<R>::type body_pressure(Shell S, int sys, State<R> it, State<R> n,
+                                                               int patch_mask, int bx, int by) {
+  using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
-  bool ok = decode_point(L, LC, patch_mask, bx, by, p, i, j, k);
-  double contrib = 0.0;
-  if (ok) {
-    long q = lidx(L, p, i, j, k);
-    int o = (sys == 1) ? 0 : 4;
-    double D = divh<double>(S, it.f[F_U1R + o], n.f[F_U1R + o], it.f[F_U1T + o], n.f[F_U1T + o],
-                            it.f[F_U1P + o], n.f[F_U1P + o], i, j, q);
-    double pnew;
-    double *dst;
-    if (sys == 1) {
-      pnew = n.p[0][q] - D * (2.0 * S.i2chi);
-      dst = it.p[0];
-    } else {
-      pnew = n.p[1][q] + (it.p[0][q] - n.p[0][q]) - D * (2.0 * S.i2chi);
-      dst = it.p[1];
-    }
-    double c = pnew - dst[q];
-    dst[q] = pnew;
-    bool ringcell = (j == 0 || j == L.Nt - 1 || k == 0 || k == L.Np - 1);
-    if (!(S.step7 && ringcell)) {
-      double r = S.rc[i];
-      double w = r * r * S.sc[j] * S.hr * S.ht * S.hp;
-      contrib = w * c * c;
-    }
+  if (!decode_point(L, LC, patch_mask, bx, by, p, i, j, k)) return (V)0.0;
+  const long q = lidx(L, p, i, j, k);
+  double D;
+  if constexpr (sizeof(R) == sizeof(float)) {
+    // FP32 storage: double-float divergence (FP64-accurate, FP32 instructions)
+    D = ff_double(divh_ff(S, velf(it, sys, 0), velf(n, sys, 0), velf(it, sys, 1), velf(n, sys, 1), velf(it, sys, 2),
+                          velf(n, sys, 2), i, j, q));
+    D = D * (2.0 * S.i2chi);
+  } else {
+    // divergence of the half-level velocity times 1/chi from the row record
+    const double *c = rowc<double>(S, RT_DIV, i, j);
+    const R *ri = velf(it, sys, 0), *rn = velf(n, sys, 0), *ti = velf(it, sys, 1), *tn = velf(n, sys, 1);
+    const R *pi = velf(it, sys, 2), *pn = velf(n, sys, 2);
+    D = (c[DV_R1] * Sm<double>(ri, rn, q + L.SI) - c[DV_R0] * Sm<double>(ri, rn, q)) +
+        (c[DV_T1] * Sm<double>(ti, tn, q + L.P) - c[DV_T0] * Sm<double>(ti, tn, q)) +
+        c[DV_P] * (Sm<double>(pi, pn, q + 1) - Sm<double>(pi, pn, q));
   }
-  // warp reduction, one atomic per warp
-  for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, off);
-  if ((threadIdx.x & 31) == 0 && contrib != 0.0) atomicAdd(&norm[sys == 1 ? 4 : 8], contrib);
+  double pnew;
+  double *dst;
+  if (sys == 1) {
+    pnew = n.p[0][q] - D;
+    dst = it.p[0];
+  } else {
+    pnew = n.p[1][q] + (it.p[0][q] - n.p[0][q]) - D;
+    dst = it.p[1];
+  }
+  const V c = (V)(pnew - dst[q]);
+  dst[q] = pnew;
+  const bool ringcell = (j == 0 || j == L.Nt - 1 || k == 0 || k == L.Np - 1);
+  if (S.step7 && ringcell) return (V)0.0;
+  return rowc<V>(S, RT_DIV, i, j)[DV_W] * c * c;
+}
+
+// Warp sum of per-thread norm shares, scaled once and added to *dst by lane 0.
+// Every lane of the warp must call it.
+template <typename V>
+__device__ __forceinline__ void norm_flush(V part, double scale, double *dst) {
+  for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+  if ((threadIdx.x & 31) == 0 && part != (V)0.0) atomicAdd(dst, (double)part * scale);
 }
 
 // elements [q0, q1) of every field, threads striding by blockDim.x
@@ -342,139 +414,87 @@ __device__ __forceinline__ void body_walls(Shell S, State<R> s, int patch_mask, 
   const int Nr = L.Nr, Nt = L.Nt, Np = L.Np;
   long lo = lidx(L, p, -1, j, k), l0 = lidx(L, p, 0, j, k);
   long hi = lidx(L, p, Nr, j, k), h0 = lidx(L, p, Nr - 1, j, k);
-  // u_r on the wall faces i = 0 and i = Nr, the whole plane
-  s.f[F_U1R][l0] = (R)0.0;
-  s.f[F_U2R][l0] = (R)0.0;
-  s.f[F_U1R][hi] = (R)0.0;
-  s.f[F_U2R][hi] = (R)0.0;
-  if (j >= 0 && j < Nt && k >= 0 && k < Np) {
+  // u_r on the wall faces i = 0 and i = Nr: the wall velocity on the unknown
+  // columns (0 = no-slip unless wall data is set), 0 on the ghost columns
+  const bool cc = (j >= 0 && j < Nt && k >= 0 && k < Np);
+  double g0 = 0.0, g1 = 0.0;
+  if (S.wall_ur && cc) {
+    g0 = S.wall_ur[((long)(0 * 2 + p) * Nt + j) * Np + k];
+    g1 = S.wall_ur[((long)(1 * 2 + p) * Nt + j) * Np + k];
+  }
+  s.f[F_U1R][l0] = (R)g0;
+  s.f[F_U2R][l0] = (R)g0;
+  s.f[F_U1R][hi] = (R)g1;
+  s.f[F_U2R][hi] = (R)g1;
+  if (cc) {
     s.f[F_T][lo] = (R)(2.0 * S.T_in - (double)s.f[F_T][l0]);
     s.f[F_T][hi] = (R)(2.0 * S.T_out - (double)s.f[F_T][h0]);
   }
+  // u_theta, u_phi: reflection ghosts 2 g - x_0 about the wall velocity g
   if (j >= 1 && j < Nt && k >= 0 && k < Np) {
+    g0 = g1 = 0.0;
+    if (S.wall_ut) {
+      g0 = S.wall_ut[((long)(0 * 2 + p) * (Nt + 1) + j) * Np + k];
+      g1 = S.wall_ut[((long)(1 * 2 + p) * (Nt + 1) + j) * Np + k];
+    }
     for (int o = 0; o <= 4; o += 4) {
       R *u = s.f[F_U1T + o];
-      u[lo] = (R)(-(double)u[l0]);
-      u[hi] = (R)(-(double)u[h0]);
+      u[lo] = (R)(2.0 * g0 - (double)u[l0]);
+      u[hi] = (R)(2.0 * g1 - (double)u[h0]);
     }
   }
   if (j >= 0 && j < Nt && k >= 1 && k < Np) {
+    g0 = g1 = 0.0;
+    if (S.wall_up) {
+      g0 = S.wall_up[((long)(0 * 2 + p) * Nt + j) * (Np + 1) + k];
+      g1 = S.wall_up[((long)(1 * 2 + p) * Nt + j) * (Np + 1) + k];
+    }
     for (int o = 0; o <= 4; o += 4) {
       R *u = s.f[F_U1P + o];
-      u[lo] = (R)(-(double)u[l0]);
-      u[hi] = (R)(-(double)u[h0]);
+      u[lo] = (R)(2.0 * g0 - (double)u[l0]);
+      u[hi] = (R)(2.0 * g1 - (double)u[h0]);
     }
   }
 }
 
-// Advecting velocity (a_r, a_th, a_ph) at a point of location `loc`: own
-// component as stored, others averaged from their nearest stored values.
-template <typename R>
-__device__ __forceinline__ void advecting(const Shell &S, const StepAux<R> &ax, int loc, long q, double &ar,
-                                          double &at, double &ap) {
+// Component along `dir` of the advecting velocity at a point of location
+// `loc`: the own component as stored, the others averaged from their nearest
+// stored values (in the arithmetic type V).
+template <typename V, typename R>
+__device__ __forceinline__ V advecting(const Shell &S, const StepAux<R> &ax, int loc, int dir, long q) {
   const long SI = S.L.SI, P = S.L.P;
-  const R *A0 = ax.A[0], *A1 = ax.A[1], *A2 = ax.A[2];
-  switch (loc) {
-    case LC:
-      ar = ((double)A0[q] + (double)A0[q + SI]) * 0.5;
-      at = ((double)A1[q] + (double)A1[q + P]) * 0.5;
-      ap = ((double)A2[q] + (double)A2[q + 1]) * 0.5;
-      break;
-    case LR:
-      ar = (double)A0[q];
-      at = avg4<double>(A1, q - SI, q - SI + P, q, q + P);
-      ap = avg4<double>(A2, q - SI, q - SI + 1, q, q + 1);
-      break;
-    case LT:
-      ar = avg4<double>(A0, q - P, q - P + SI, q, q + SI);
-      at = (double)A1[q];
-      ap = avg4<double>(A2, q - P, q - P + 1, q, q + 1);
-      break;
-    default:
-      ar = avg4<double>(A0, q - 1, q - 1 + SI, q, q + SI);
-      at = avg4<double>(A1, q - 1, q - 1 + P, q, q + P);
-      ap = (double)A2[q];
-      break;
+  if (dir == DR) {
+    const R *A0 = ax.A[0];
+    if (loc == LC) return ((V)A0[q] + (V)A0[q + SI]) * (V)0.5;
+    if (loc == LR) return (V)A0[q];
+    if (loc == LT) return avg4<V>(A0, q - P, q - P + SI, q, q + SI);
+    return avg4<V>(A0, q - 1, q - 1 + SI, q, q + SI);
   }
+  if (dir == DT) {
+    const R *A1 = ax.A[1];
+    if (loc == LC) return ((V)A1[q] + (V)A1[q + P]) * (V)0.5;
+    if (loc == LR) return avg4<V>(A1, q - SI, q - SI + P, q, q + P);
+    if (loc == LT) return (V)A1[q];
+    return avg4<V>(A1, q - 1, q - 1 + P, q, q + P);
+  }
+  const R *A2 = ax.A[2];
+  if (loc == LC) return ((V)A2[q] + (V)A2[q + 1]) * (V)0.5;
+  if (loc == LR) return avg4<V>(A2, q - SI, q - SI + 1, q, q + 1);
+  if (loc == LT) return avg4<V>(A2, q - P, q - P + 1, q, q + 1);
+  return (V)A2[q];
 }
 
-// Coefficients (lo, di, up) of (I - dt/2 Ahat_dir) at point (i, j, k) of `loc`
-// (divisions replaced by FP64 reciprocal metric tables).
+// Coefficients (lo, di, up) of (I - dt/2 Ahat_dir) at point (i, j, k) of
+// `loc`: the row's static parts (FacCoef table, formed on the host in FP64)
+// and the advecting velocity at the point.
 template <typename V, typename R>
 __device__ __forceinline__ void coef(const Shell &S, const StepAux<R> &ax, int loc, int dir, int i, int j, long q,
                                      V &lo, V &di, V &up) {
-  const V ihr = cs<V>(S, CS_IHR), iht = cs<V>(S, CS_IHT), ihp = cs<V>(S, CS_IHP);
-  const V nu = (loc == LC) ? cs<V>(S, CS_KAPPA) : cs<V>(S, CS_NU);
-  double ar_d, at_d, ap_d;
-  advecting(S, ax, loc, q, ar_d, at_d, ap_d);
-  const V ar = (V)ar_d, at = (V)at_d, ap = (V)ap_d;
-  const V ir = (loc == LR) ? mt<V>(S, MT_IRF)[i] : mt<V>(S, MT_IRC)[i];
-  const V is = (loc == LT) ? mt<V>(S, MT_ISF)[j] : mt<V>(S, MT_ISC)[j];
-  const V ir2 = ir * ir;
-  const V rc0 = mt<V>(S, MT_RC)[i], rcm = mt<V>(S, MT_RC)[i - 1], rf0 = mt<V>(S, MT_RF)[i], rfp = mt<V>(S, MT_RF)[i + 1], rfm = mt<V>(S, MT_RF)[i - 1];
-  const V sc0 = mt<V>(S, MT_SC)[j], scm = mt<V>(S, MT_SC)[j - 1], sf0 = mt<V>(S, MT_SF)[j], sfp = mt<V>(S, MT_SF)[j + 1], sfm = mt<V>(S, MT_SF)[j - 1];
-  V cm, c0, cp;
-  if (dir == DR) {
-    V cp_d, cm_d;
-    if (loc == LR) {
-      cp_d = rc0 * rc0 * (ir2 * ihr * ihr);
-      cm_d = rcm * rcm * (ir2 * ihr * ihr);
-    } else {
-      cp_d = rfp * rfp * (ir2 * ihr * ihr);
-      cm_d = rf0 * rf0 * (ir2 * ihr * ihr);
-    }
-    cm = nu * cm_d + ar * ((V)0.5 * ihr);
-    c0 = -nu * (cp_d + cm_d);
-    cp = nu * cp_d - ar * ((V)0.5 * ihr);
-    if (loc == LR) {
-      cm = cm - nu * rfm * rfm * (ir2 * ir * ihr);
-      cp = cp + nu * rfp * rfp * (ir2 * ir * ihr);
-      c0 = c0 - nu * (V)2.0 * ir2;
-      const V k = cs<V>(S, CS_I2CHI), irm = mt<V>(S, MT_IRC)[i - 1], irc = mt<V>(S, MT_IRC)[i];
-      cm = cm + k * rfm * rfm * (irm * irm * ihr * ihr);
-      c0 = c0 - k * (rf0 * rf0 * (irc * irc * ihr * ihr) + rf0 * rf0 * (irm * irm * ihr * ihr));
-      cp = cp + k * rfp * rfp * (irc * irc * ihr * ihr);
-    }
-  } else if (dir == DT) {
-    V cp_d, cm_d;
-    const V iR1sq = cs<V>(S, CS_IR1SQ);
-    if (loc == LT) {
-      cp_d = sc0 * (iR1sq * is * iht * iht);
-      cm_d = scm * (iR1sq * is * iht * iht);
-    } else {
-      cp_d = sfp * (iR1sq * is * iht * iht);
-      cm_d = sf0 * (iR1sq * is * iht * iht);
-    }
-    cm = nu * cm_d + at * ((V)0.5 * ir * iht);
-    c0 = -nu * (cp_d + cm_d);
-    cp = nu * cp_d - at * ((V)0.5 * ir * iht);
-    if (loc == LT) {
-      const V c = mt<V>(S, MT_CF)[j], s = sf0;
-      const V qq = c * ir2 * is * is * iht;
-      cm = cm - nu * qq * sfm;
-      cp = cp + nu * qq * sfp;
-      c0 = c0 - nu * ir2 * is * is;
-      const V k = cs<V>(S, CS_I2CHI), isc0 = mt<V>(S, MT_ISC)[j], iscm = mt<V>(S, MT_ISC)[j - 1];
-      cp = cp + k * sfp * (ir2 * isc0 * iht * iht);
-      c0 = c0 - k * (s * (ir2 * isc0 * iht * iht) + s * (ir2 * iscm * iht * iht));
-      cm = cm + k * sfm * (ir2 * iscm * iht * iht);
-    }
-  } else {
-    const V cpm = cs<V>(S, CS_CPHI);
-    cm = nu * cpm + ap * ((V)0.5 * ir * is * ihp);
-    c0 = (V)-2.0 * nu * cpm;
-    cp = nu * cpm - ap * ((V)0.5 * ir * is * ihp);
-    if (loc == LP) {
-      c0 = c0 - nu * ir2 * is * is;
-      const V qq = cs<V>(S, CS_I2CHI) * ir2 * is * is * ihp * ihp;
-      cm = cm + qq;
-      c0 = c0 - (V)2.0 * qq;
-      cp = cp + qq;
-    }
-  }
-  lo = (V)-0.5 * cs<V>(S, CS_DT) * cm;
-  di = (V)1.0 - (V)0.5 * cs<V>(S, CS_DT) * c0;
-  up = (V)-0.5 * cs<V>(S, CS_DT) * cp;
+  const V *c = facc<V>(S, loc, dir, i, j);
+  const V a = advecting<V>(S, ax, loc, dir, q);
+  lo = c[FC_L0] + a * c[FC_LA];
+  di = c[FC_D0];
+  up = c[FC_U0] - a * c[FC_LA];
 }
 
 // Line of a (loc, dir) sweep: thread (lane, row) -> patch p, first point
@@ -614,8 +634,11 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
         }
       }
     }
-    // back substitution: W -> B or the iterate, last row first
+    // back substitution: W -> B or the iterate, last row first; the final
+    // factor sums w x^2 along the line in V, w the metric factor that varies
+    // along it (r^2, sin(theta) or 1), and scales once by the constant rest
     V x = d;
+    V acc = (V)0.0;
     for (int m = n - 1; m >= 0; m -= U) {
       V w[U], c[U], o[U];
 #pragma unroll
@@ -635,16 +658,26 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
           if (mm < n - 1) x = w[u] - c[u] * x;
           if (final) {
             dst[qq] = (R)(o[u] + x);
-            int row = ln.m0 + mm;
-            int ii = (dir == DR) ? row : ln.i, jj = (dir == DT) ? row : ln.j;
-            double r = (loc == LR) ? S.rf[ii] : S.rc[ii];
-            double s = (loc == LT) ? S.sf[jj] : S.sc[jj];
-            contrib += r * r * s * S.hr * S.ht * S.hp * (double)x * (double)x;
+            const int row = ln.m0 + mm;
+            if (dir == DR) {
+              const V t = ((loc == LR) ? mt<V>(S, MT_RF) : mt<V>(S, MT_RC))[row] * x;
+              acc += t * t;
+            } else if (dir == DT) {
+              acc += ((loc == LT) ? mt<V>(S, MT_SF) : mt<V>(S, MT_SC))[row] * x * x;
+            } else {
+              acc += x * x;
+            }
           } else {
             B[qq] = (R)x;
           }
         }
       }
+    }
+    if (final) {
+      const double r = (loc == LR) ? S.rf[ln.i] : S.rc[ln.i];
+      const double sn = (loc == LT) ? S.sf[ln.j] : S.sc[ln.j];
+      const double w = (dir == DR) ? sn : (dir == DT) ? r * r : r * r * sn;
+      contrib = (double)acc * (w * S.dcs[CS_VOL]);
     }
   }
   if (final) {
@@ -653,223 +686,392 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
   }
 }
 
-// Line solve along phi (the contiguous index) through shared memory.  Each
-// warp owns 32 adjacent lines (consecutive theta rows at one radius) and
-// walks them in chunks of 32 rows: the chunk's right-hand side and factors
-// are loaded as a [32 lines][32 rows] tile with coalesced row reads, the 32
-// recurrences run from shared memory (rows padded to 33: no bank conflicts),
-// and results leave the same way.  Same arithmetic as body_solve.
-constexpr int kPhiWarps = 4;   // warps (tiles of 32 lines) per CTA
-template <typename R>
-constexpr int phi_smem_bytes() {
-  return kPhiWarps * 3 * 32 * 33 * (int)sizeof(R);
+// Line solve along phi as a warp scan: one warp per line (the line's values
+// are contiguous in memory).  Lane t owns the segment of EC consecutive
+// positions [c0 + t EC, c0 + (t + 1) EC) of a chunk of 32 EC positions, read
+// and written with 16-byte vector accesses.  The forward recurrence
+// d_m = iv_m (b_m - lo_m d_{m-1}) is the affine map d -> a_m d + f_m
+// (a_m = -iv_m lo_m, f_m = iv_m b_m); each lane composes the maps of its
+// segment, an inclusive Kogge-Stone scan over the lanes (5 shuffle steps)
+// composes the segments, and each lane then replays its segment from its
+// incoming value.  The back substitution x_m = d_m - c'_m x_{m+1} is the
+// same with the scan running downwards.  The forward results d stay in a
+// per-warp shared-memory buffer when the line fits (`wsm`), else in W.
+// Positions outside [k0, Np) map to 0 (the chain restarts at k0 anyway) and
+// are never written.
+constexpr int kScanWarps = 4;           // lines (warps) per CTA
+constexpr int kScanSmemMax = 96 * 1024;   // shared memory a CTA may take for the forward results
+
+template <int EC, typename R, typename V>
+__device__ __forceinline__ void seg_load(const R *__restrict__ p, bool full, int k, int k0, int k1, V *out) {
+  if (full) {
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+      for (int v = 0; v < EC / 4; ++v) {
+        const float4 t = *reinterpret_cast<const float4 *>(p + 4 * v);
+        out[4 * v] = (V)t.x;
+        out[4 * v + 1] = (V)t.y;
+        out[4 * v + 2] = (V)t.z;
+        out[4 * v + 3] = (V)t.w;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < EC / 2; ++v) {
+        const double2 t = *reinterpret_cast<const double2 *>(p + 2 * v);
+        out[2 * v] = (V)t.x;
+        out[2 * v + 1] = (V)t.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < EC; ++e) out[e] = (k + e >= k0 && k + e < k1) ? (V)p[e] : (V)0.0;
+  }
 }
 
+template <int EC, typename R, typename V>
+__device__ __forceinline__ void seg_store(R *__restrict__ p, bool full, int k, int k0, int k1, const V *in) {
+  if (full) {
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+      for (int v = 0; v < EC / 4; ++v)
+        *reinterpret_cast<float4 *>(p + 4 * v) =
+            make_float4((float)in[4 * v], (float)in[4 * v + 1], (float)in[4 * v + 2], (float)in[4 * v + 3]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < EC / 2; ++v)
+        *reinterpret_cast<double2 *>(p + 2 * v) = make_double2((double)in[2 * v], (double)in[2 * v + 1]);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < EC; ++e)
+      if (k + e >= k0 && k + e < k1) p[e] = (R)in[e];
+  }
+}
+
+template <int EC, typename R>
+__device__ __forceinline__ void solve_line_scan(int k0, int k1, int final, const R *__restrict__ Lo,
+                                                const R *__restrict__ Iv, const R *__restrict__ Cp,
+                                                R *__restrict__ B, R *__restrict__ wbuf, R *__restrict__ dst,
+                                                typename Cmp<R>::type &acc) {
+  using V = typename Cmp<R>::type;
+  const int lane = threadIdx.x & 31;
+  constexpr int CH = 32 * EC;
+  const int nch = (k1 + CH - 1) / CH;
+  // forward elimination into wbuf
+  V dcarry = (V)0.0;
+  for (int c = 0; c < nch; ++c) {
+    const int k = c * CH + lane * EC;
+    const bool full = (k >= k0 && k + EC <= k1);
+    V a[EC], f[EC];
+    {
+      V b[EC], lo[EC], iv[EC];
+      seg_load<EC>(B + k, full, k, k0, k1, b);
+      seg_load<EC>(Lo + k, full, k, k0, k1, lo);
+      seg_load<EC>(Iv + k, full, k, k0, k1, iv);
+#pragma unroll
+      for (int e = 0; e < EC; ++e) {
+        a[e] = -iv[e] * lo[e];
+        f[e] = iv[e] * b[e];
+      }
+    }
+    V A = (V)1.0, F = (V)0.0;
+#pragma unroll
+    for (int e = 0; e < EC; ++e) {
+      A = a[e] * A;
+      F = a[e] * F + f[e];
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const V Ao = __shfl_up_sync(0xffffffffu, A, off), Fo = __shfl_up_sync(0xffffffffu, F, off);
+      if (lane >= off) {
+        F = A * Fo + F;
+        A = A * Ao;
+      }
+    }
+    V Ae = __shfl_up_sync(0xffffffffu, A, 1), Fe = __shfl_up_sync(0xffffffffu, F, 1);
+    if (lane == 0) {
+      Ae = (V)1.0;
+      Fe = (V)0.0;
+    }
+    V d = Ae * dcarry + Fe;
+    V out[EC];
+#pragma unroll
+    for (int e = 0; e < EC; ++e) {
+      d = a[e] * d + f[e];
+      out[e] = d;
+    }
+    seg_store<EC>(wbuf + k, full, k, k0, k1, out);
+    dcarry = __shfl_sync(0xffffffffu, A * dcarry + F, 31);
+  }
+  __syncwarp();
+  // back substitution from the last chunk down
+  V xcarry = (V)0.0;
+  for (int c = nch - 1; c >= 0; --c) {
+    const int k = c * CH + lane * EC;
+    const bool full = (k >= k0 && k + EC <= k1);
+    V g[EC], w[EC];
+    {
+      V cp[EC];
+      seg_load<EC>(Cp + k, full, k, k0, k1, cp);
+      seg_load<EC>(wbuf + k, full, k, k0, k1, w);
+#pragma unroll
+      for (int e = 0; e < EC; ++e) g[e] = -cp[e];
+    }
+    V G = (V)1.0, X = (V)0.0;
+#pragma unroll
+    for (int e = EC - 1; e >= 0; --e) {
+      G = g[e] * G;
+      X = g[e] * X + w[e];
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const V Go = __shfl_down_sync(0xffffffffu, G, off), Xo = __shfl_down_sync(0xffffffffu, X, off);
+      if (lane + off < 32) {
+        X = G * Xo + X;
+        G = G * Go;
+      }
+    }
+    V Ge = __shfl_down_sync(0xffffffffu, G, 1), Xe = __shfl_down_sync(0xffffffffu, X, 1);
+    if (lane == 31) {
+      Ge = (V)1.0;
+      Xe = (V)0.0;
+    }
+    V x = Ge * xcarry + Xe;
+    V out[EC];
+#pragma unroll
+    for (int e = EC - 1; e >= 0; --e) {
+      x = g[e] * x + w[e];
+      out[e] = x;
+    }
+    if (final) {
+      V o[EC];
+      seg_load<EC>(dst + k, full, k, k0, k1, o);
+#pragma unroll
+      for (int e = 0; e < EC; ++e) {
+        if (k + e >= k0 && k + e < k1) acc += out[e] * out[e];
+        o[e] = o[e] + out[e];
+      }
+      seg_store<EC>(dst + k, full, k, k0, k1, o);
+    } else {
+      seg_store<EC>(B + k, full, k, k0, k1, out);
+    }
+    xcarry = __shfl_sync(0xffffffffu, G * xcarry + X, 0);
+  }
+}
+
+// positions per lane of a phi line of Np positions (one chunk up to 384,
+// longer lines in chunks of 384)
+inline __host__ __device__ int scan_ec(int Np) {
+  const int e = (Np + 31) / 32;
+  return e <= 4 ? 4 : e <= 8 ? 8 : 12;
+}
+// shared-memory positions per warp for the forward results of a line
+inline __host__ __device__ int scan_pad(int Np) {
+  const int ch = 32 * scan_ec(Np);
+  return (Np + ch - 1) / ch * ch;
+}
+// lines of a location type and the CTAs of body_solve_phi_scan for one shell
+inline int phi_scan_ctas(const Layout &L, int loc) {
+  const long lines = 2L * (L.Nr - (loc == LR ? 1 : 0)) * (L.Nt - (loc == LT ? 1 : 0));
+  return (int)((lines + kScanWarps - 1) / kScanWarps);
+}
+
+// one phi line per warp; `smem_per_warp` positions of shared memory per warp
+// (0 or too few: the forward results go through W)
 template <typename R>
-__device__ __forceinline__ void body_solve_phi(Shell S, int loc, int final, const R *__restrict__ Lo,
-                                               const R *__restrict__ Iv, const R *__restrict__ Cp,
-                                               R *__restrict__ B, R *__restrict__ W, R *__restrict__ dst,
-                                               double *norm, int slot, int patch_mask, int bx, R *smem) {
+__device__ __forceinline__ void body_solve_phi_scan(Shell S, int loc, int final, const R *__restrict__ Lo,
+                                                    const R *__restrict__ Iv, const R *__restrict__ Cp,
+                                                    R *__restrict__ B, R *__restrict__ W, R *__restrict__ dst,
+                                                    double *norm, int slot, int patch_mask, int bx, R *smem,
+                                                    int smem_per_warp) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   const int i0 = (loc == LR) ? 1 : 0, j0 = (loc == LT) ? 1 : 0, k0 = (loc == LP) ? 1 : 0;
-  const int ni = L.Nr - i0, nj = L.Nt - j0, nk = L.Np - k0;
-  const int jt = (nj + 31) / 32;
-  const long tile = (long)bx * kPhiWarps + warp;
-  double contrib = 0.0;
-  if (tile < 2L * ni * jt) {
-    const int jb = (int)(tile % jt) * 32;
-    const long rest = tile / jt;
+  const int ni = L.Nr - i0, nj = L.Nt - j0;
+  const long line = (long)bx * kScanWarps + warp;
+  V acc = (V)0.0;
+  double scale = 0.0;
+  if (line < 2L * ni * nj) {
+    const int j = j0 + (int)(line % nj);
+    const long rest = line / nj;
     const int i = i0 + (int)(rest % ni), p = (int)(rest / ni);
     if ((patch_mask >> p) & 1) {
-      R *t0 = smem + warp * 3 * 32 * 33, *t1 = t0 + 32 * 33, *t2 = t1 + 32 * 33;
-      const bool lv = jb + lane < nj;
-      const long rowbase = lidx(L, p, i, j0 + jb, k0);   // line jb, first row
-      const long lstride = L.P;                          // between adjacent lines
-      const int nch = (nk + 31) / 32;
-      V d = (V)0.0;
-      for (int c = 0; c < nch; ++c) {
-        const int kc = c * 32;
-        const bool kv = kc + lane < nk;
-        for (int r0 = 0; r0 < 32; r0 += 8) {   // 8 rows of loads in flight, then to shared memory
-          R a0[8], a1[8], a2[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int rr = r0 + u;
-            if (jb + rr < nj && kv) {
-              long q = rowbase + rr * lstride + kc + lane;
-              a0[u] = B[q];
-              a1[u] = Lo[q];
-              a2[u] = Iv[q];
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int rr = r0 + u;
-            if (jb + rr < nj && kv) {
-              t0[rr * 33 + lane] = a0[u];
-              t1[rr * 33 + lane] = a1[u];
-              t2[rr * 33 + lane] = a2[u];
-            }
-          }
-        }
-        __syncwarp();
-        if (lv) {
-          const int kmax = (nk - kc < 32) ? nk - kc : 32;
-          for (int u = 0; u < kmax; ++u) {
-            d = ((V)t0[lane * 33 + u] - (V)t1[lane * 33 + u] * d) * (V)t2[lane * 33 + u];
-            t0[lane * 33 + u] = (R)d;
-          }
-        }
-        __syncwarp();
-#pragma unroll 8
-        for (int rr = 0; rr < 32; ++rr)
-          if (jb + rr < nj && kv) W[rowbase + rr * lstride + kc + lane] = t0[rr * 33 + lane];
-        __syncwarp();
+      const long q = lidx(L, p, i, j, 0);
+      R *wbuf = (scan_pad(L.Np) <= smem_per_warp) ? smem + (long)warp * smem_per_warp : W + q;
+      switch (scan_ec(L.Np)) {
+        case 4:
+          solve_line_scan<4>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc);
+          break;
+        case 8:
+          solve_line_scan<8>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc);
+          break;
+        default:
+          solve_line_scan<12>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc);
+          break;
       }
-      double wline = 0.0;
-      if (final && lv) {
-        int jj = j0 + jb + lane;
-        double r = (loc == LR) ? S.rf[i] : S.rc[i];
-        double sn = (loc == LT) ? S.sf[jj] : S.sc[jj];
-        wline = r * r * sn * S.hr * S.ht * S.hp;
-      }
-      V x = d;
-      for (int c = nch - 1; c >= 0; --c) {
-        const int kc = c * 32;
-        const bool kv = kc + lane < nk;
-        for (int r0 = 0; r0 < 32; r0 += 8) {
-          R a0[8], a1[8], a2[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int rr = r0 + u;
-            if (jb + rr < nj && kv) {
-              long q = rowbase + rr * lstride + kc + lane;
-              a0[u] = W[q];
-              a1[u] = Cp[q];
-              if (final) a2[u] = dst[q];
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int rr = r0 + u;
-            if (jb + rr < nj && kv) {
-              t0[rr * 33 + lane] = a0[u];
-              t1[rr * 33 + lane] = a1[u];
-              if (final) t2[rr * 33 + lane] = a2[u];
-            }
-          }
-        }
-        __syncwarp();
-        if (lv) {
-          const int kmax = (nk - kc < 32) ? nk - kc : 32;
-          for (int u = kmax - 1; u >= 0; --u) {
-            if (kc + u < nk - 1) x = (V)t0[lane * 33 + u] - (V)t1[lane * 33 + u] * x;
-            if (final) {
-              t2[lane * 33 + u] = (R)((V)t2[lane * 33 + u] + x);
-              contrib += wline * (double)x * (double)x;
-            } else {
-              t0[lane * 33 + u] = (R)x;
-            }
-          }
-        }
-        __syncwarp();
-#pragma unroll 8
-        for (int rr = 0; rr < 32; ++rr) {
-          if (jb + rr < nj && kv) {
-            long q = rowbase + rr * lstride + kc + lane;
-            if (final)
-              dst[q] = t2[rr * 33 + lane];
-            else
-              B[q] = t0[rr * 33 + lane];
-          }
-        }
-        __syncwarp();
+      if (final) {
+        const double r = (loc == LR) ? S.rf[i] : S.rc[i];
+        const double sn = (loc == LT) ? S.sf[j] : S.sc[j];
+        scale = r * r * sn * S.dcs[CS_VOL];
       }
     }
   }
-  if (final) {
-    for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, off);
-    if (lane == 0 && contrib != 0.0) atomicAdd(&norm[slot], contrib);
+  if (final) norm_flush(acc, scale, &norm[slot]);
+}
+
+
+
+// Per-step factorisation of a phi line operator as a warp scan (one warp per
+// line, lane t owning the same EC-position segment as in body_solve_phi_scan).
+// The pivot recurrence c'_m = up_m / (di_m - lo_m c'_{m-1}) is the Moebius
+// map of the matrix M_m = [[0, up_m], [-lo_m, di_m]] acting on (N, D) with
+// c' = N / D, so segments compose as 2x2 matrix products; each lane composes
+// its segment, an inclusive Kogge-Stone scan over the lanes composes the
+// segments (matrices rescaled by exact powers of two to stay in range), and
+// each lane replays its segment from the incoming c' with the exact divisions
+// of the sequential elimination.  lo = 0 at the first unknown restarts the
+// chain.  Outputs as body_factorize: Lo, Iv = 1 / pivot, Cp = c'.
+template <typename V>
+__device__ __forceinline__ V pow2_recip(V s);
+template <>
+__device__ __forceinline__ float pow2_recip<float>(float s) {
+  int e = (__float_as_int(s) >> 23) & 0xff;
+  e = e < 253 ? e : 253;
+  return __int_as_float((254 - e) << 23);   // 2^(127 - e) ~ 1 / s, exact scaling
+}
+template <>
+__device__ __forceinline__ double pow2_recip<double>(double s) {
+  int e = (__double2hiint(s) >> 20) & 0x7ff;
+  e = e < 2045 ? e : 2045;
+  return __hiloint2double((2046 - e) << 20, 0);   // 2^(1023 - e)
+}
+
+template <typename V>
+__device__ __forceinline__ void mat_rescale(V &a, V &b, V &c, V &d) {
+  const V m = fmax(fmax(fabs(a), fabs(b)), fmax(fabs(c), fabs(d)));
+  if (m > (V)0.0) {
+    const V f = pow2_recip(m);
+    a *= f;
+    b *= f;
+    c *= f;
+    d *= f;
   }
 }
 
-// CTAs of kPhiWarps warps needed by body_solve_phi for one shell
-inline int phi_ctas(const Layout &L, int loc) {
-  int ni = L.Nr - (loc == LR ? 1 : 0), nj = L.Nt - (loc == LT ? 1 : 0);
-  long tiles = 2L * ni * ((nj + 31) / 32);
-  return (int)((tiles + kPhiWarps - 1) / kPhiWarps);
+template <int EC, typename R>
+__device__ __forceinline__ void factor_line_scan(const Shell &S, const StepAux<R> &ax, int loc, int i, int j,
+                                                 long q, int k0, int k1, R *__restrict__ Lo, R *__restrict__ Iv,
+                                                 R *__restrict__ Cp) {
+  using V = typename Cmp<R>::type;
+  const int lane = threadIdx.x & 31;
+  constexpr int CH = 32 * EC;
+  const int nch = (k1 + CH - 1) / CH;
+  const V *fc = facc<V>(S, loc, DP, i, j);
+  const V L0 = fc[FC_L0], D0 = fc[FC_D0], U0 = fc[FC_U0], LA = fc[FC_LA];
+  V ccarry = (V)0.0;
+  for (int c = 0; c < nch; ++c) {
+    const int k = c * CH + lane * EC;
+    const bool full = (k >= k0 && k + EC <= k1);
+    // the row (i, j) is fixed along a phi line: lo = L0 + a La, di = D0,
+    // up = U0 - a La (as coef), only the advecting velocity a varies
+    V a[EC];
+#pragma unroll
+    for (int e = 0; e < EC; ++e) {
+      const int kk = k + e;
+      a[e] = (kk >= k0 && kk < k1) ? advecting<V>(S, ax, loc, DP, q + kk) : (V)0.0;
+    }
+    auto lo_of = [&](int e) -> V {
+      const int kk = k + e;
+      return (kk > k0 && kk < k1) ? L0 + a[e] * LA : (V)0.0;
+    };
+    auto up_of = [&](int e) -> V {
+      const int kk = k + e;
+      return (kk >= k0 && kk < k1 - 1) ? U0 - a[e] * LA : (V)0.0;
+    };
+    auto di_of = [&](int e) -> V {
+      const int kk = k + e;
+      return (kk >= k0 && kk < k1) ? D0 : (V)1.0;
+    };
+    // segment composite M_last ... M_first
+    V A = (V)1.0, B = (V)0.0, C = (V)0.0, D = (V)1.0;
+#pragma unroll
+    for (int e = 0; e < EC; ++e) {
+      const V lo = lo_of(e), di = di_of(e), up = up_of(e);
+      const V nA = up * C, nB = up * D;
+      const V nC = di * C - lo * A, nD = di * D - lo * B;
+      A = nA;
+      B = nB;
+      C = nC;
+      D = nD;
+      if ((e & 3) == 3) mat_rescale(A, B, C, D);
+    }
+    mat_rescale(A, B, C, D);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const V Ao = __shfl_up_sync(0xffffffffu, A, off), Bo = __shfl_up_sync(0xffffffffu, B, off);
+      const V Co = __shfl_up_sync(0xffffffffu, C, off), Do = __shfl_up_sync(0xffffffffu, D, off);
+      if (lane >= off) {
+        const V nA = A * Ao + B * Co, nB = A * Bo + B * Do;
+        const V nC = C * Ao + D * Co, nD = C * Bo + D * Do;
+        A = nA;
+        B = nB;
+        C = nC;
+        D = nD;
+        mat_rescale(A, B, C, D);
+      }
+    }
+    V Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+    V Ce = __shfl_up_sync(0xffffffffu, C, 1), De = __shfl_up_sync(0xffffffffu, D, 1);
+    if (lane == 0) {
+      Ae = (V)1.0;
+      Be = (V)0.0;
+      Ce = (V)0.0;
+      De = (V)1.0;
+    }
+    V cc = (Ae * ccarry + Be) / (Ce * ccarry + De);
+    V oi[EC], oc[EC];
+#pragma unroll
+    for (int e = 0; e < EC; ++e) {
+      const V inv = (V)1.0 / (di_of(e) - lo_of(e) * cc);
+      cc = up_of(e) * inv;
+      oi[e] = inv;
+      oc[e] = cc;
+    }
+#pragma unroll
+    for (int e = 0; e < EC; ++e) a[e] = lo_of(e);
+    seg_store<EC>(Lo + q + k, full, k, k0, k1, a);
+    seg_store<EC>(Iv + q + k, full, k, k0, k1, oi);
+    seg_store<EC>(Cp + q + k, full, k, k0, k1, oc);
+    ccarry = __shfl_sync(0xffffffffu, cc, 31);
+  }
 }
 
-// Per-step factorisation of the phi factor through shared memory (same warp
-// tiles as body_solve_phi): coefficients of a [32 lines][32 rows] tile are
-// formed with lanes along phi (coalesced reads of the advecting velocity),
-// the 32 line recurrences run from shared memory, and the factors leave with
-// coalesced row writes.  Same arithmetic as body_factorize.
 template <typename R>
-__device__ __forceinline__ void body_factorize_phi(Shell S, int loc, StepAux<R> ax, R *__restrict__ Lo,
-                                                   R *__restrict__ Iv, R *__restrict__ Cp, int patch_mask, int bx,
-                                                   R *smem) {
-  using V = typename Cmp<R>::type;
+__device__ __forceinline__ void body_factorize_phi_scan(Shell S, int loc, StepAux<R> ax, R *__restrict__ Lo,
+                                                        R *__restrict__ Iv, R *__restrict__ Cp, int patch_mask,
+                                                        int bx) {
   const Layout &L = S.L;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   const int i0 = (loc == LR) ? 1 : 0, j0 = (loc == LT) ? 1 : 0, k0 = (loc == LP) ? 1 : 0;
-  const int ni = L.Nr - i0, nj = L.Nt - j0, nk = L.Np - k0;
-  const int jt = (nj + 31) / 32;
-  const long tile = (long)bx * kPhiWarps + warp;
-  if (tile >= 2L * ni * jt) return;
-  const int jb = (int)(tile % jt) * 32;
-  const long rest = tile / jt;
+  const int ni = L.Nr - i0, nj = L.Nt - j0;
+  const long line = (long)bx * kScanWarps + warp;
+  if (line >= 2L * ni * nj) return;
+  const int j = j0 + (int)(line % nj);
+  const long rest = line / nj;
   const int i = i0 + (int)(rest % ni), p = (int)(rest / ni);
   if (!((patch_mask >> p) & 1)) return;
-  R *t0 = smem + warp * 3 * 32 * 33, *t1 = t0 + 32 * 33, *t2 = t1 + 32 * 33;
-  const long rowbase = lidx(L, p, i, j0 + jb, k0);
-  const long lstride = L.P;
-  const int nch = (nk + 31) / 32;
-  V cprev = (V)0.0;
-  for (int c = 0; c < nch; ++c) {
-    const int kc = c * 32;
-    const int kk = kc + lane;
-    if (kk < nk) {
-#pragma unroll 4
-      for (int rr = 0; rr < 32; ++rr) {
-        if (jb + rr < nj) {
-          V lo, di, up;
-          coef<V>(S, ax, loc, DP, i, j0 + jb + rr, rowbase + rr * lstride + kk, lo, di, up);
-          if (kk == 0) lo = (V)0.0;
-          if (kk == nk - 1) up = (V)0.0;
-          t0[rr * 33 + lane] = (R)lo;
-          t1[rr * 33 + lane] = (R)di;
-          t2[rr * 33 + lane] = (R)up;
-        }
-      }
-    }
-    __syncwarp();
-    if (jb + lane < nj) {
-      const int kmax = (nk - kc < 32) ? nk - kc : 32;
-      for (int u = 0; u < kmax; ++u) {
-        V lo = (V)t0[lane * 33 + u];
-        V inv = (V)1.0 / ((V)t1[lane * 33 + u] - lo * cprev);
-        V cc = (V)t2[lane * 33 + u] * inv;
-        t1[lane * 33 + u] = (R)inv;
-        t2[lane * 33 + u] = (R)cc;
-        cprev = cc;
-      }
-    }
-    __syncwarp();
-    if (kk < nk) {
-#pragma unroll 8
-      for (int rr = 0; rr < 32; ++rr) {
-        if (jb + rr < nj) {
-          long q = rowbase + rr * lstride + kk;
-          Lo[q] = t0[rr * 33 + lane];
-          Iv[q] = t1[rr * 33 + lane];
-          Cp[q] = t2[rr * 33 + lane];
-        }
-      }
-    }
-    __syncwarp();
+  const long q = lidx(L, p, i, j, 0);
+  switch (scan_ec(L.Np)) {
+    case 4:
+      factor_line_scan<4>(S, ax, loc, i, j, q, k0, L.Np, Lo, Iv, Cp);
+      break;
+    case 8:
+      factor_line_scan<8>(S, ax, loc, i, j, q, k0, L.Np, Lo, Iv, Cp);
+      break;
+    default:
+      factor_line_scan<12>(S, ax, loc, i, j, q, k0, L.Np, Lo, Iv, Cp);
+      break;
   }
 }
 

@@ -49,7 +49,8 @@ struct ys_ctx {
   ys::XEntry *xdev = nullptr;
   ys::XTables X;
   double *norm = nullptr;     // YS_NFIELDS accumulators
-  double *stage = nullptr;    // host-layout staging (device)
+  double *stage = nullptr;    // host-layout staging (device); per-block norm shares of k_pressure during a step
+  double *dwall = nullptr;    // Dirichlet wall velocity (device, ys_set_wall_velocity), or null
   double *T_bg = nullptr;     // deviation backgrounds per radial index (mixed form), else null
   double *p_bg = nullptr;
   int mode_fn[ys::kMaxModes] = {};

@@ -48,6 +48,247 @@ void make_metric(const GridSpec &g, const GridGeo &G, std::vector<double> &tab, 
   }
 }
 
+void make_rowcoef(const GridSpec &g, const GridGeo &G, const std::vector<double> &met, int pad, int len,
+                  const RowPhys &ph, std::vector<double> tab[kRowTables]) {
+  // metric lookups by logical index (tables of make_metric)
+  auto T = [&](int t, int i) { return met[(size_t)t * len + i + pad]; };
+  auto rc = [&](int i) { return T(0, i); };
+  auto rf = [&](int i) { return T(1, i); };
+  auto sc = [&](int j) { return T(2, j); };
+  auto sf = [&](int j) { return T(3, j); };
+  auto cc = [&](int j) { return T(4, j); };
+  auto cf = [&](int j) { return T(5, j); };
+  auto irc = [&](int i) { return T(6, i); };
+  auto irf = [&](int i) { return T(7, i); };
+  auto isc = [&](int j) { return T(8, j); };
+  auto isf = [&](int j) { return T(9, j); };
+  const double ihr = 1.0 / G.hr, iht = 1.0 / G.ht, ihp = 1.0 / G.hp;
+  const double dt = ph.dt, nu = ph.nu, ka = ph.kappa, i2chi = ph.i2chi;
+  const int NJ = g.Nth + 2;
+  const size_t rows = (size_t)(g.Nr + 2) * NJ;
+  for (int t = 0; t < kRowTables; ++t) tab[t].assign(rows * row_m(t), 0.0);
+  auto rec = [&](int t, int i, int j) { return &tab[t][((size_t)(i + 1) * NJ + (j + 1)) * row_m(t)]; };
+
+  // temperature at cell centres (i, j): kappa Laplacian, advection by the
+  // 2-point face averages of the advecting velocity (the kernel forms their
+  // sums), and the deviation-form source
+  for (int i = 0; i < g.Nr; ++i)
+    for (int j = 0; j < g.Nth; ++j) {
+      double *c = rec(RT_T, i, j);
+      const double ir = irc(i), is = isc(j), ir2 = ir * ir;
+      c[T_RP] = 0.5 * dt * ka * rf(i + 1) * rf(i + 1) * ir2 * ihr * ihr;
+      c[T_RM] = 0.5 * dt * ka * rf(i) * rf(i) * ir2 * ihr * ihr;
+      c[T_TP] = 0.5 * dt * ka * sf(j + 1) * ir2 * is * iht * iht;
+      c[T_TM] = 0.5 * dt * ka * sf(j) * ir2 * is * iht * iht;
+      c[T_PP] = 0.5 * dt * ka * ir2 * is * is * ihp * ihp;
+      c[T_AR] = 0.125 * dt * ihr;
+      c[T_AT] = 0.125 * dt * ir * iht;
+      c[T_AP] = 0.125 * dt * ir * is * ihp;
+      c[T_G0] = ph.Tc_lap ? dt * ka * ph.Tc_lap[i] : 0.0;
+      c[T_G1] = ph.Tc_dr ? 0.5 * dt * ph.Tc_dr[i] : 0.0;
+    }
+
+  // u_r at r-face i (1 .. Nr-1), cell row j
+  for (int i = 1; i < g.Nr; ++i)
+    for (int j = 0; j < g.Nth; ++j) {
+      double *c = rec(RT_UR, i, j);
+      const double ir = irf(i), is = isc(j), ir2 = ir * ir;
+      const double rfp = rf(i + 1), rf0 = rf(i), rfm = rf(i - 1);
+      const double icc = irc(i), icm = irc(i - 1);   // the two cells sharing face i
+      c[UR_RP] = 0.5 * dt * nu * rc(i) * rc(i) * ir2 * ihr * ihr;
+      c[UR_RM] = 0.5 * dt * nu * rc(i - 1) * rc(i - 1) * ir2 * ihr * ihr;
+      c[UR_TP] = 0.5 * dt * nu * sf(j + 1) * ir2 * is * iht * iht;
+      c[UR_TM] = 0.5 * dt * nu * sf(j) * ir2 * is * iht * iht;
+      c[UR_PP] = 0.5 * dt * nu * ir2 * is * is * ihp * ihp;
+      // own values outside the Laplacian: the curvature term of the vector
+      // Laplacian and the r-part of grad(div) across the two cells
+      const double G = 0.5 * dt * ihr * i2chi;
+      c[UR_O1] = 0.5 * dt * nu * ir2 * ir * ihr * rfp * rfp + G * rfp * rfp * icc * icc * ihr;
+      c[UR_O0] = -dt * nu * ir2 - G * rf0 * rf0 * (icc * icc + icm * icm) * ihr;
+      c[UR_OM] = -0.5 * dt * nu * ir2 * ir * ihr * rfm * rfm + G * rfm * rfm * icm * icm * ihr;
+      // u_theta at (q + P, q, q - SI + P, q - SI): theta-part of grad(div)
+      c[UR_GT1] = G * sf(j + 1) * icc * is * iht;
+      c[UR_GT0] = -G * sf(j) * icc * is * iht;
+      c[UR_GTM1] = -G * sf(j + 1) * icm * is * iht;
+      c[UR_GTM0] = G * sf(j) * icm * is * iht;
+      // u_phi differences (q + 1) - q and (q - SI + 1) - (q - SI)
+      c[UR_GP1] = G * icc * is * ihp;
+      c[UR_GPM1] = -G * icm * is * ihp;
+      c[UR_AR] = 0.25 * dt * ihr;
+      c[UR_AT] = 0.0625 * dt * ir * iht;
+      c[UR_AP] = 0.0625 * dt * ir * is * ihp;
+      c[UR_CV] = dt * ir / 32.0;
+      c[UR_GPR] = dt * ihr;
+      c[UR_BY] = 0.25 * dt * ph.PrRa;
+    }
+
+  // u_theta at cell row i, theta-face j (1 .. Nth-1)
+  for (int i = 0; i < g.Nr; ++i)
+    for (int j = 1; j < g.Nth; ++j) {
+      double *c = rec(RT_UT, i, j);
+      const double ir = irc(i), is = isf(j), cs = cf(j), ir2 = ir * ir;
+      const double rfp = rf(i + 1), rf0 = rf(i);
+      const double isj = isc(j), ism = isc(j - 1);   // the two cells sharing face j
+      c[UT_RP] = 0.5 * dt * nu * rfp * rfp * ir2 * ihr * ihr;
+      c[UT_RM] = 0.5 * dt * nu * rf0 * rf0 * ir2 * ihr * ihr;
+      c[UT_TP] = 0.5 * dt * nu * sc(j) * ir2 * is * iht * iht;
+      c[UT_TM] = 0.5 * dt * nu * sc(j - 1) * ir2 * is * iht * iht;
+      c[UT_PP] = 0.5 * dt * nu * ir2 * is * is * ihp * ihp;
+      const double G = 0.5 * dt * i2chi * ir * iht;
+      const double E = 0.5 * dt * nu * cs * ir2 * is * is * iht;
+      c[UT_OTP] = E * sf(j + 1) + G * sf(j + 1) * ir * isj * iht;
+      c[UT_O0] = -0.5 * dt * nu * ir2 * is * is - G * sf(j) * ir * (isj + ism) * iht;
+      c[UT_OTM] = -E * sf(j - 1) + G * sf(j - 1) * ir * ism * iht;
+      // u_r at (q + SI, q, q + SI - P, q - P): vector-Laplacian coupling and
+      // r-part of grad(div)
+      const double a = 0.5 * dt * nu * ir2 * iht, b = 0.5 * dt * nu * cs * ir2 * ir * is * ihr;
+      c[UT_W1] = a + b * rfp * rfp + G * rfp * rfp * ir * ir * ihr;
+      c[UT_W0] = a - b * rf0 * rf0 - G * rf0 * rf0 * ir * ir * ihr;
+      c[UT_WM1] = -a + b * rfp * rfp - G * rfp * rfp * ir * ir * ihr;
+      c[UT_WM0] = -a - b * rf0 * rf0 + G * rf0 * rf0 * ir * ir * ihr;
+      c[UT_GP1] = G * ir * isj * ihp;
+      c[UT_GPM1] = -G * ir * ism * ihp;
+      c[UT_AR] = 0.0625 * dt * ihr;
+      c[UT_AT] = 0.25 * dt * ir * iht;
+      c[UT_AP] = 0.0625 * dt * ir * is * ihp;
+      c[UT_CW] = 0.125 * dt * ir;
+      c[UT_CP] = dt * ir * cs * is / 32.0;
+      c[UT_GPR] = dt * irc(i) * iht;
+    }
+
+  // u_phi at cell row (i, j), phi-faces
+  for (int i = 0; i < g.Nr; ++i)
+    for (int j = 0; j < g.Nth; ++j) {
+      double *c = rec(RT_UP, i, j);
+      const double ir = irc(i), is = isc(j), cs = cc(j), ir2 = ir * ir;
+      const double rfp = rf(i + 1), rf0 = rf(i);
+      c[UP_RP] = 0.5 * dt * nu * rfp * rfp * ir2 * ihr * ihr;
+      c[UP_RM] = 0.5 * dt * nu * rf0 * rf0 * ir2 * ihr * ihr;
+      c[UP_TP] = 0.5 * dt * nu * sf(j + 1) * ir2 * is * iht * iht;
+      c[UP_TM] = 0.5 * dt * nu * sf(j) * ir2 * is * iht * iht;
+      // the phi-part of grad(div) has the stencil of the phi-diffusion
+      c[UP_PP] = 0.5 * dt * (nu + i2chi) * ir2 * is * is * ihp * ihp;
+      c[UP_E0] = -0.5 * dt * nu * ir2 * is * is;
+      const double G = 0.5 * dt * i2chi * ir * is * ihp;
+      const double a = 0.5 * dt * nu * ir2 * is * ihp, b = 0.5 * dt * nu * cs * ir2 * is * is * ihp;
+      // u_r at (q + SI, q, q - 1 + SI, q - 1)
+      c[UP_W1] = a + G * rfp * rfp * ir2 * ihr;
+      c[UP_W0] = a - G * rf0 * rf0 * ir2 * ihr;
+      c[UP_WM1] = -a - G * rfp * rfp * ir2 * ihr;
+      c[UP_WM0] = -a + G * rf0 * rf0 * ir2 * ihr;
+      // u_theta at (q + P, q, q - 1 + P, q - 1)
+      c[UP_Y1] = b + G * sf(j + 1) * ir * is * iht;
+      c[UP_Y0] = b - G * sf(j) * ir * is * iht;
+      c[UP_YM1] = -b - G * sf(j + 1) * ir * is * iht;
+      c[UP_YM0] = -b + G * sf(j) * ir * is * iht;
+      c[UP_AR] = 0.0625 * dt * ihr;
+      c[UP_AT] = 0.0625 * dt * ir * iht;
+      c[UP_AP] = 0.25 * dt * ir * is * ihp;
+      c[UP_CW] = 0.125 * dt * ir;
+      c[UP_CY] = 0.125 * dt * ir * cs * is;
+      c[UP_GPR] = dt * ir * is * ihp;
+    }
+
+  // divergence of the half-level velocity times 1/chi at cell (i, j), and the
+  // weight r^2 sin(theta) of the pressure-increment norm
+  for (int i = 0; i < g.Nr; ++i)
+    for (int j = 0; j < g.Nth; ++j) {
+      double *c = rec(RT_DIV, i, j);
+      const double ir = irc(i), is = isc(j);
+      c[DV_R1] = i2chi * rf(i + 1) * rf(i + 1) * ir * ir * ihr;
+      c[DV_R0] = i2chi * rf(i) * rf(i) * ir * ir * ihr;
+      c[DV_T1] = i2chi * sf(j + 1) * ir * is * iht;
+      c[DV_T0] = i2chi * sf(j) * ir * is * iht;
+      c[DV_P] = i2chi * ir * is * ihp;
+      c[DV_W] = rc(i) * rc(i) * sc(j);
+    }
+}
+
+void make_faccoef(const GridSpec &g, const GridGeo &G, const std::vector<double> &met, int pad, int len,
+                  const FacPhys &ph, std::vector<double> &tab) {
+  auto T = [&](int t, int i) { return met[(size_t)t * len + i + pad]; };
+  auto rc = [&](int i) { return T(0, i); };
+  auto rf = [&](int i) { return T(1, i); };
+  auto sc = [&](int j) { return T(2, j); };
+  auto sf = [&](int j) { return T(3, j); };
+  auto cf = [&](int j) { return T(5, j); };
+  auto irc = [&](int i) { return T(6, i); };
+  auto irf = [&](int i) { return T(7, i); };
+  auto isc = [&](int j) { return T(8, j); };
+  auto isf = [&](int j) { return T(9, j); };
+  const double ihr = 1.0 / G.hr, iht = 1.0 / G.ht, ihp = 1.0 / G.hp;
+  const int NJ = g.Nth + 2;
+  const size_t rows = (size_t)(g.Nr + 2) * NJ;
+  tab.assign((size_t)kFacTables * rows * FC_M, 0.0);
+  for (int loc = LC; loc <= LP; ++loc)
+    for (int dir = DR; dir <= DP; ++dir)
+      for (int i = (loc == LR) ? 1 : 0; i < g.Nr; ++i)
+        for (int j = (loc == LT) ? 1 : 0; j < g.Nth; ++j) {
+          // (I - dt/2 Ahat_dir): the diffusion along dir (modified operators
+          // with R1 and theta_1 for theta and phi), the own-direction extras
+          // of the vector Laplacian and of grad(div)/(2 chi), and the
+          // advection a d/dx_dir whose coefficient is ka
+          const double nu = (loc == LC) ? ph.kappa : ph.nu;
+          const double ir = (loc == LR) ? irf(i) : irc(i);
+          const double is = (loc == LT) ? isf(j) : isc(j);
+          const double ir2 = ir * ir;
+          double cm, c0, cp, ka;
+          if (dir == DR) {
+            const double cp_d = (loc == LR) ? rc(i) * rc(i) * (ir2 * ihr * ihr) : rf(i + 1) * rf(i + 1) * (ir2 * ihr * ihr);
+            const double cm_d = (loc == LR) ? rc(i - 1) * rc(i - 1) * (ir2 * ihr * ihr) : rf(i) * rf(i) * (ir2 * ihr * ihr);
+            cm = nu * cm_d;
+            c0 = -nu * (cp_d + cm_d);
+            cp = nu * cp_d;
+            ka = 0.5 * ihr;
+            if (loc == LR) {
+              const double rfm = rf(i - 1), rf0 = rf(i), rfp = rf(i + 1), irm = irc(i - 1), ic = irc(i);
+              cm -= nu * rfm * rfm * (ir2 * ir * ihr);
+              cp += nu * rfp * rfp * (ir2 * ir * ihr);
+              c0 -= nu * 2.0 * ir2;
+              cm += ph.i2chi * rfm * rfm * (irm * irm * ihr * ihr);
+              c0 -= ph.i2chi * (rf0 * rf0 * (ic * ic * ihr * ihr) + rf0 * rf0 * (irm * irm * ihr * ihr));
+              cp += ph.i2chi * rfp * rfp * (ic * ic * ihr * ihr);
+            }
+          } else if (dir == DT) {
+            const double cp_d = (loc == LT) ? sc(j) * (ph.iR1sq * is * iht * iht) : sf(j + 1) * (ph.iR1sq * is * iht * iht);
+            const double cm_d = (loc == LT) ? sc(j - 1) * (ph.iR1sq * is * iht * iht) : sf(j) * (ph.iR1sq * is * iht * iht);
+            cm = nu * cm_d;
+            c0 = -nu * (cp_d + cm_d);
+            cp = nu * cp_d;
+            ka = 0.5 * ir * iht;
+            if (loc == LT) {
+              const double qq = cf(j) * ir2 * is * is * iht;
+              cm -= nu * qq * sf(j - 1);
+              cp += nu * qq * sf(j + 1);
+              c0 -= nu * ir2 * is * is;
+              const double isc0 = isc(j), iscm = isc(j - 1);
+              cp += ph.i2chi * sf(j + 1) * (ir2 * isc0 * iht * iht);
+              c0 -= ph.i2chi * (sf(j) * (ir2 * isc0 * iht * iht) + sf(j) * (ir2 * iscm * iht * iht));
+              cm += ph.i2chi * sf(j - 1) * (ir2 * iscm * iht * iht);
+            }
+          } else {
+            cm = nu * ph.cphi;
+            c0 = -2.0 * nu * ph.cphi;
+            cp = nu * ph.cphi;
+            ka = 0.5 * ir * is * ihp;
+            if (loc == LP) {
+              c0 -= nu * ir2 * is * is;
+              const double qq = ph.i2chi * ir2 * is * is * ihp * ihp;
+              cm += qq;
+              c0 -= 2.0 * qq;
+              cp += qq;
+            }
+          }
+          double *c = &tab[((size_t)(3 * loc + dir) * rows + (size_t)(i + 1) * NJ + (j + 1)) * FC_M];
+          c[FC_L0] = -0.5 * ph.dt * cm;
+          c[FC_D0] = 1.0 - 0.5 * ph.dt * c0;
+          c[FC_U0] = -0.5 * ph.dt * cp;
+          c[FC_LA] = -0.5 * ph.dt * ka;
+        }
+  (void)rc;
+  (void)sc;
+}
+
 namespace {
 
 struct V3 {

@@ -70,8 +70,10 @@ struct Launch {
   // W: scratch for the forward sweep (distinct from B and dst)
   static void solve(const Shell &S, int loc, int dir, bool final, const R *Lo, const R *Iv, const R *Cp, R *B,
                     R *W, R *dst, double *norm, int slot, int patch_mask, cudaStream_t st);
-  static void pressure(const Shell &S, int sys, State<R> it, State<R> n, double *norm, int patch_mask,
-                       cudaStream_t st);
+  // pressure update of system sys; part: scratch of one FP64 per cell block
+  // (partial norms, summed into norm[4] or norm[8] by a second kernel)
+  static void pressure(const Shell &S, int sys, State<R> it, State<R> n, double *norm, double *part,
+                       int patch_mask, cudaStream_t st);
   // host layout <-> device layout; bg (FP64 per radial index, may be null) is
   // subtracted on the way in and added on the way out
   static void unpack(const Layout &L, int loc, const double *src, R *dst, const double *bg, cudaStream_t st);

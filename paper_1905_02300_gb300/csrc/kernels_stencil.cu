@@ -26,15 +26,23 @@ __global__ void k_extrapolate(long total, State<R> it, State<R> n, State<R> nm1,
     bd::body_extrapolate(c * chunk, (c + 1) * chunk < total ? (c + 1) * chunk : total, it, n, nm1, A0, A1, A2);
 }
 
+// sum over modes of tau_m(t) F_m, accumulated in the arithmetic type
 template <typename R>
 __global__ void k_combine(long total, Modes<R> M, R *o0, R *o1, R *o2, R *o3) {
+  using V = typename Cmp<R>::type;
   long q = blockIdx.x * (long)blockDim.x + threadIdx.x;
   long stride = (long)gridDim.x * blockDim.x;
   R *out[4] = {o0, o1, o2, o3};
+  V tau[kMaxModes];
+#pragma unroll
+  for (int m = 0; m < kMaxModes; ++m) tau[m] = (m < M.n) ? (V)M.tau[m] : (V)0.0;
   for (; q < total; q += stride) {
+#pragma unroll
     for (int c = 0; c < 4; ++c) {
-      double acc = 0.0;
-      for (int m = 0; m < M.n; ++m) acc = acc + M.tau[m] * (double)M.F[m][c][q];
+      V acc = (V)0.0;
+#pragma unroll
+      for (int m = 0; m < kMaxModes; ++m)
+        if (m < M.n) acc = acc + tau[m] * (V)M.F[m][c][q];
       out[c][q] = (R)acc;
     }
   }
@@ -64,10 +72,50 @@ __global__ void k_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R>
 }
 
 // ----------------------------------------------------------------- pressure
-// FP64 divergence and FP64 pressure accumulation in both forms.
+// FP64-accurate divergence and FP64 pressure accumulation in both forms.  One
+// CTA per pres_rows<R>() consecutive cell rows: with FP32 storage the kernel
+// is latency-bound and takes one row per CTA (the most CTAs in flight); in
+// FP64 it is bound by the FP64 pipe and four rows per CTA amortise the norm
+// reduction.  Each thread sums its cells' norm shares, the CTA reduces them
+// once and writes part[block] without atomics, and k_sum_parts adds the
+// shares up.
 template <typename R>
-__global__ void k_pressure(Shell S, int sys, State<R> it, State<R> n, double *norm, int patch_mask) {
-  bd::body_pressure(S, sys, it, n, norm, patch_mask, blockIdx.x, blockIdx.y);
+constexpr int pres_rows() {
+  return sizeof(R) == sizeof(float) ? 1 : 4;
+}
+template <typename R>
+__global__ void k_pressure(Shell S, int sys, State<R> it, State<R> n, double *part, int rows, int patch_mask) {
+  using V = typename Cmp<R>::type;
+  __shared__ V ws[TPB];
+  V v = (V)0.0;
+  for (int t = 0; t < pres_rows<R>(); ++t) {
+    const int by = blockIdx.y * pres_rows<R>() + t;
+    if (by < rows) v += bd::body_pressure(S, sys, it, n, patch_mask, blockIdx.x, by);
+  }
+  ws[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    V w = ws[threadIdx.x];
+    for (int u = threadIdx.x + 32; u < TPB; u += 32) w += ws[u];
+    for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(0xffffffffu, w, off);
+    if (threadIdx.x == 0) part[(long)blockIdx.y * gridDim.x + blockIdx.x] = (double)w;
+  }
+}
+
+// dst += scale * sum(part[0, n)): CTAs take interleaved slices, one atomic each
+constexpr int kSumCtas = 64;
+__global__ void k_sum_parts(const double *part, long n, double scale, double *dst) {
+  __shared__ double ws[8];
+  double t = 0.0;
+  for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) t += part[u];
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+    if (s != 0.0) atomicAdd(dst, s * scale);
+  }
 }
 
 // ----------------------------------------------------------------- packing
@@ -156,8 +204,12 @@ void Launch<R>::resid_u(const Shell &S, int sys, int comp, State<R> it, State<R>
 }
 
 template <typename R>
-void Launch<R>::pressure(const Shell &S, int sys, State<R> it, State<R> n, double *norm, int pm, cudaStream_t st) {
-  k_pressure<R><<<point_grid(S.L, LC), TPB, 0, st>>>(S, sys, it, n, norm, pm);
+void Launch<R>::pressure(const Shell &S, int sys, State<R> it, State<R> n, double *norm, double *part, int pm,
+                         cudaStream_t st) {
+  const dim3 g = point_grid(S.L, LC);
+  const dim3 gp(g.x, (g.y + pres_rows<R>() - 1) / pres_rows<R>());
+  k_pressure<R><<<gp, TPB, 0, st>>>(S, sys, it, n, part, (int)g.y, pm);
+  k_sum_parts<<<kSumCtas, 256, 0, st>>>(part, (long)gp.x * gp.y, S.dcs[CS_VOL], &norm[sys == 1 ? 4 : 8]);
 }
 
 template <typename R>
@@ -184,7 +236,7 @@ void pack_p(const Layout &L, const double *src, double *dst, const double *bg, c
   template void Launch<R>::resid_T(const Shell &, State<R>, State<R>, StepAux<R>, R *, int, cudaStream_t);        \
   template void Launch<R>::resid_u(const Shell &, int, int, State<R>, State<R>, StepAux<R>, R *, int,             \
                                    cudaStream_t);                                                                  \
-  template void Launch<R>::pressure(const Shell &, int, State<R>, State<R>, double *, int, cudaStream_t);         \
+  template void Launch<R>::pressure(const Shell &, int, State<R>, State<R>, double *, double *, int, cudaStream_t); \
   template void Launch<R>::unpack(const Layout &, int, const double *, R *, const double *, cudaStream_t);        \
   template void Launch<R>::pack(const Layout &, int, const R *, double *, const double *, cudaStream_t);
 YS_INST_STENCIL(double)

@@ -2,13 +2,19 @@
 // (I - dt/2 Ahat_d) (Sec. 3.2 modified operators, Eq. Convect_Douglas,
 // Eq. r_comp / theta_comp / phi_comp; Thomas algorithm, Sec. 4).
 //
-// One thread owns one grid line.  For sweeps along r and theta the lines of a
-// warp are neighbours along phi (the fastest index), so every load and store
-// of the recurrence is coalesced.  The forward elimination keeps the modified
-// super-diagonal c' in a scratch field Cs and overwrites the right-hand side
-// with d'; back substitution overwrites d' with the solution, or, for the last
-// factor of an unknown, adds it to the iterate and accumulates the FP64
-// midpoint-rule norm of the increment (Sec. 5.1).
+// Every step first factorises each line operator once (lower diagonal,
+// reciprocal pivots, modified super-diagonal c'), and every Schwarz iteration
+// then solves with the stored factors.  Lines along r and theta: one thread
+// per line, the lines of a warp neighbours along phi (the fastest index), so
+// every load and store of the recurrences is coalesced.  Lines along phi
+// (contiguous in memory): factorisation and solves as warp scans (one warp
+// per line, see body_factorize_phi_scan and body_solve_phi_scan).  The
+// last factor of an unknown adds its solution to the iterate and accumulates
+// the midpoint-rule norm of the increment (Sec. 5.1).
+//
+// k_sweep is the allocation-free variant (ys_factor_solve_static): one pass
+// that forms the coefficients, eliminates and substitutes without stored
+// factors.
 #include <cmath>
 #include <mutex>
 
@@ -20,6 +26,87 @@ namespace ys {
 namespace {
 
 constexpr int TPB = 128;
+
+// Coefficients (lo, di, up) of (I - dt/2 Ahat_dir) at point (i, j, k) of `loc`
+// formed from the metric tables alone: the allocation-free entry point keeps
+// no precomputed line-operator tables.  Same operator as the host tables of
+// make_faccoef (diffusion with the modified theta / phi operators, the
+// own-direction extras of the vector Laplacian and grad(div)/(2 chi), and the
+// advection along dir).
+template <typename V, typename R>
+__device__ __forceinline__ void coef_metric(const Shell &S, const StepAux<R> &ax, int loc, int dir, int i, int j, long q,
+                                     V &lo, V &di, V &up) {
+  const V ihr = cs<V>(S, CS_IHR), iht = cs<V>(S, CS_IHT), ihp = cs<V>(S, CS_IHP);
+  const V nu = (loc == LC) ? cs<V>(S, CS_KAPPA) : cs<V>(S, CS_NU);
+  const V adv = bd::advecting<V>(S, ax, loc, dir, q);
+  const V ir = (loc == LR) ? mt<V>(S, MT_IRF)[i] : mt<V>(S, MT_IRC)[i];
+  const V is = (loc == LT) ? mt<V>(S, MT_ISF)[j] : mt<V>(S, MT_ISC)[j];
+  const V ir2 = ir * ir;
+  const V rc0 = mt<V>(S, MT_RC)[i], rcm = mt<V>(S, MT_RC)[i - 1], rf0 = mt<V>(S, MT_RF)[i], rfp = mt<V>(S, MT_RF)[i + 1], rfm = mt<V>(S, MT_RF)[i - 1];
+  const V sc0 = mt<V>(S, MT_SC)[j], scm = mt<V>(S, MT_SC)[j - 1], sf0 = mt<V>(S, MT_SF)[j], sfp = mt<V>(S, MT_SF)[j + 1], sfm = mt<V>(S, MT_SF)[j - 1];
+  V cm, c0, cp;
+  if (dir == DR) {
+    V cp_d, cm_d;
+    if (loc == LR) {
+      cp_d = rc0 * rc0 * (ir2 * ihr * ihr);
+      cm_d = rcm * rcm * (ir2 * ihr * ihr);
+    } else {
+      cp_d = rfp * rfp * (ir2 * ihr * ihr);
+      cm_d = rf0 * rf0 * (ir2 * ihr * ihr);
+    }
+    cm = nu * cm_d + adv * ((V)0.5 * ihr);
+    c0 = -nu * (cp_d + cm_d);
+    cp = nu * cp_d - adv * ((V)0.5 * ihr);
+    if (loc == LR) {
+      cm = cm - nu * rfm * rfm * (ir2 * ir * ihr);
+      cp = cp + nu * rfp * rfp * (ir2 * ir * ihr);
+      c0 = c0 - nu * (V)2.0 * ir2;
+      const V k = cs<V>(S, CS_I2CHI), irm = mt<V>(S, MT_IRC)[i - 1], irc = mt<V>(S, MT_IRC)[i];
+      cm = cm + k * rfm * rfm * (irm * irm * ihr * ihr);
+      c0 = c0 - k * (rf0 * rf0 * (irc * irc * ihr * ihr) + rf0 * rf0 * (irm * irm * ihr * ihr));
+      cp = cp + k * rfp * rfp * (irc * irc * ihr * ihr);
+    }
+  } else if (dir == DT) {
+    V cp_d, cm_d;
+    const V iR1sq = cs<V>(S, CS_IR1SQ);
+    if (loc == LT) {
+      cp_d = sc0 * (iR1sq * is * iht * iht);
+      cm_d = scm * (iR1sq * is * iht * iht);
+    } else {
+      cp_d = sfp * (iR1sq * is * iht * iht);
+      cm_d = sf0 * (iR1sq * is * iht * iht);
+    }
+    cm = nu * cm_d + adv * ((V)0.5 * ir * iht);
+    c0 = -nu * (cp_d + cm_d);
+    cp = nu * cp_d - adv * ((V)0.5 * ir * iht);
+    if (loc == LT) {
+      const V c = mt<V>(S, MT_CF)[j], s = sf0;
+      const V qq = c * ir2 * is * is * iht;
+      cm = cm - nu * qq * sfm;
+      cp = cp + nu * qq * sfp;
+      c0 = c0 - nu * ir2 * is * is;
+      const V k = cs<V>(S, CS_I2CHI), isc0 = mt<V>(S, MT_ISC)[j], iscm = mt<V>(S, MT_ISC)[j - 1];
+      cp = cp + k * sfp * (ir2 * isc0 * iht * iht);
+      c0 = c0 - k * (s * (ir2 * isc0 * iht * iht) + s * (ir2 * iscm * iht * iht));
+      cm = cm + k * sfm * (ir2 * iscm * iht * iht);
+    }
+  } else {
+    const V cpm = cs<V>(S, CS_CPHI);
+    cm = nu * cpm + adv * ((V)0.5 * ir * is * ihp);
+    c0 = (V)-2.0 * nu * cpm;
+    cp = nu * cpm - adv * ((V)0.5 * ir * is * ihp);
+    if (loc == LP) {
+      c0 = c0 - nu * ir2 * is * is;
+      const V qq = cs<V>(S, CS_I2CHI) * ir2 * is * is * ihp * ihp;
+      cm = cm + qq;
+      c0 = c0 - (V)2.0 * qq;
+      cp = cp + qq;
+    }
+  }
+  lo = (V)-0.5 * cs<V>(S, CS_DT) * cm;
+  di = (V)1.0 - (V)0.5 * cs<V>(S, CS_DT) * c0;
+  up = (V)-0.5 * cs<V>(S, CS_DT) * cp;
+}
 
 template <typename R>
 __global__ void k_sweep(Shell S, int loc, int dir, int final, StepAux<R> ax, R *B, R *Cs, R *dst, double *norm,
@@ -37,7 +124,7 @@ __global__ void k_sweep(Shell S, int loc, int dir, int final, StepAux<R> ax, R *
     for (int m = m0; m < m1; ++m, q += step) {
       int ii = (dir == DR) ? m : i, jj = (dir == DT) ? m : j;
       double lo, di, up;
-      bd::coef<double>(S, ax, loc, dir, ii, jj, q, lo, di, up);
+      coef_metric<double>(S, ax, loc, dir, ii, jj, q, lo, di, up);
       if (m == m0) {
         if (reflect) di -= lo;
         lo = 0.0;
@@ -111,15 +198,16 @@ dim3 line_grid(const Layout &L, int loc, int dir) {
 
 template <typename R>
 __global__ void k_factorize_phi(Shell S, int loc, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask) {
-  extern __shared__ __align__(16) unsigned char phi_smem[];
-  bd::body_factorize_phi(S, loc, ax, Lo, Iv, Cp, patch_mask, blockIdx.x, (R *)phi_smem);
+  bd::body_factorize_phi_scan(S, loc, ax, Lo, Iv, Cp, patch_mask, blockIdx.x);
 }
 
 template <typename R>
 __global__ void k_solve_phi(Shell S, int loc, int final, const R *__restrict__ Lo, const R *__restrict__ Iv,
-                            const R *__restrict__ Cp, R *B, R *W, R *dst, double *norm, int slot, int patch_mask) {
+                            const R *__restrict__ Cp, R *B, R *W, R *dst, double *norm, int slot, int patch_mask,
+                            int smem_per_warp) {
   extern __shared__ __align__(16) unsigned char phi_smem[];
-  bd::body_solve_phi(S, loc, final, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, blockIdx.x, (R *)phi_smem);
+  bd::body_solve_phi_scan(S, loc, final, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, blockIdx.x, (R *)phi_smem,
+                          smem_per_warp);
 }
 
 template <typename R>
@@ -133,13 +221,8 @@ template <typename R>
 void Launch<R>::factorize(const Shell &S, int loc, int dir, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask,
                           cudaStream_t st) {
   if (dir == DP) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_factorize_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::phi_smem_bytes<R>());
-      attr = true;
-    }
-    k_factorize_phi<R><<<bd::phi_ctas(S.L, loc), 32 * bd::kPhiWarps, bd::phi_smem_bytes<R>(), st>>>(S, loc, ax, Lo,
-                                                                                                   Iv, Cp, patch_mask);
+    k_factorize_phi<R><<<bd::phi_scan_ctas(S.L, loc), 32 * bd::kScanWarps, 0, st>>>(S, loc, ax, Lo, Iv, Cp,
+                                                                                   patch_mask);
     return;
   }
   k_factorize<R><<<line_grid(S.L, loc, dir), TPB, 0, st>>>(S, loc, dir, ax, Lo, Iv, Cp, patch_mask);
@@ -149,13 +232,17 @@ template <typename R>
 void Launch<R>::solve(const Shell &S, int loc, int dir, bool final, const R *Lo, const R *Iv, const R *Cp, R *B,
                       R *W, R *dst, double *norm, int slot, int patch_mask, cudaStream_t st) {
   if (dir == DP) {
+    // forward results of each warp's line in shared memory when they fit
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(k_solve_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::phi_smem_bytes<R>());
+      cudaFuncSetAttribute(k_solve_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::kScanSmemMax);
       attr = true;
     }
-    k_solve_phi<R><<<bd::phi_ctas(S.L, loc), 32 * bd::kPhiWarps, bd::phi_smem_bytes<R>(), st>>>(
-        S, loc, final ? 1 : 0, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask);
+    const int pad = bd::scan_pad(S.L.Np);
+    const size_t bytes = (size_t)bd::kScanWarps * pad * sizeof(R);
+    const bool fits = bytes <= (size_t)bd::kScanSmemMax;
+    k_solve_phi<R><<<bd::phi_scan_ctas(S.L, loc), 32 * bd::kScanWarps, fits ? bytes : 0, st>>>(
+        S, loc, final ? 1 : 0, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, fits ? pad : 0);
     return;
   }
   k_solve<R><<<line_grid(S.L, loc, dir), TPB, 0, st>>>(S, loc, dir, final ? 1 : 0, Lo, Iv, Cp, B, W, dst, norm,

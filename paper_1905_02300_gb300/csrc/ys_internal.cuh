@@ -33,7 +33,43 @@ struct Shell;
 constexpr int kMetricTables = 10;
 enum MetricTable { MT_RC = 0, MT_RF, MT_SC, MT_SF, MT_CC, MT_CF, MT_IRC, MT_IRF, MT_ISC, MT_ISF };
 // scalar constants mirrored in both arithmetic types
-enum ShellConst { CS_IHR = 0, CS_IHT, CS_IHP, CS_I2CHI, CS_IR1SQ, CS_CPHI, CS_DT, CS_NU, CS_KAPPA, CS_PRRA, CS_NUM };
+// (CS_VOL = h_r h_theta h_phi, the coordinate cell volume of the midpoint-rule norms)
+enum ShellConst { CS_IHR = 0, CS_IHT, CS_IHP, CS_I2CHI, CS_IR1SQ, CS_CPHI, CS_DT, CS_NU, CS_KAPPA, CS_PRRA, CS_VOL, CS_NUM };
+
+// Row-coefficient tables of the explicit residuals.  On the MAC grid every
+// metric factor of the residual stencils depends on the row (i, j) only, so
+// the products of metric factors, spacings, dt, nu, kappa and 1/(2 chi) that
+// multiply each stencil value are formed once per row on the host in FP64
+// (geometry.cpp) and kept in FP64 and FP32.  The stencils take sums
+// S = psi + psi^n of the two time levels (the half-level value is S / 2; the
+// 1/2 is folded into the coefficients).  One record of *_M values per row,
+// record index (i + 1) * (Nth + 2) + (j + 1).
+enum RowTable { RT_T = 0, RT_UR, RT_UT, RT_UP, RT_DIV, kRowTables };
+// temperature (cell centres)
+enum RowT { T_RP = 0, T_RM, T_TP, T_TM, T_PP, T_AR, T_AT, T_AP, T_G0, T_G1, T_M };
+// u_r (r-faces)
+enum RowUR { UR_RP = 0, UR_RM, UR_TP, UR_TM, UR_PP, UR_O1, UR_O0, UR_OM, UR_GT1, UR_GT0, UR_GTM1, UR_GTM0,
+             UR_GP1, UR_GPM1, UR_AR, UR_AT, UR_AP, UR_CV, UR_GPR, UR_BY, UR_M };
+// u_theta (theta-faces)
+enum RowUT { UT_RP = 0, UT_RM, UT_TP, UT_TM, UT_PP, UT_OTP, UT_O0, UT_OTM, UT_W1, UT_W0, UT_WM1, UT_WM0,
+             UT_GP1, UT_GPM1, UT_AR, UT_AT, UT_AP, UT_CW, UT_CP, UT_GPR, UT_M };
+// u_phi (phi-faces)
+enum RowUP { UP_RP = 0, UP_RM, UP_TP, UP_TM, UP_PP, UP_E0, UP_W1, UP_W0, UP_WM1, UP_WM0, UP_Y1, UP_Y0,
+             UP_YM1, UP_YM0, UP_AR, UP_AT, UP_AP, UP_CW, UP_CY, UP_GPR, UP_M };
+// divergence times 1/chi for the pressure update, and the norm weight r^2 sin(theta)
+enum RowDiv { DV_R1 = 0, DV_R0, DV_T1, DV_T0, DV_P, DV_W, DV_M };
+// values per record of table t
+__host__ __device__ constexpr int row_m(int t) {
+  return t == RT_T ? T_M : t == RT_UR ? UR_M : t == RT_UT ? UT_M : t == RT_UP ? UP_M : DV_M;
+}
+
+// Static parts of the line-operator coefficients: the rows of
+// (I - dt/2 Ahat_dir) at a point of location loc are lo = L0 + a La,
+// di = D0, up = U0 - a La, with a the advecting velocity along dir at the
+// point; L0, D0, U0, La depend on the row (i, j) only.  Table
+// t = 3 loc + dir, record index (i + 1) (Nth + 2) + (j + 1).
+enum FacCoef { FC_L0 = 0, FC_D0, FC_U0, FC_LA, FC_M };
+constexpr int kFacTables = 12;
 
 // Everything a kernel needs about one shell (passed by value).
 struct Shell {
@@ -59,11 +95,24 @@ struct Shell {
   const float *ftab[kMetricTables];
   double dcs[CS_NUM];
   float fcs[CS_NUM];
+  // FP32 remainders x - (double)ftab[x] of the tables and constants: with
+  // ftab / fcs they carry each FP64 value as a double-float pair
+  const float *ltab[kMetricTables];
+  float lcs[CS_NUM];
+  // row-coefficient tables (RowTable), FP64 and the same values rounded to FP32
+  const double *rowd[kRowTables];
+  const float *rowf[kRowTables];
+  // line-operator coefficient tables (FacCoef), [kFacTables][rows][FC_M]
+  const double *facd;
+  const float *facf;
   double T_in, T_out;       // wall temperatures (of the stored temperature)
   // deviation form (mixed precision): the stored temperature is T - T_c with
   // T_c the discrete conductive profile; its rate gets the FP64 source
   // Tc_lap[i] - a_r Tc_dr[i] (null in the FP64 form)
   const double *Tc_lap, *Tc_dr;
+  // Dirichlet wall velocity (FP64, user layout [wall][patch][j][k] per
+  // component, as ys_set_wall_velocity); null = no-slip
+  const double *wall_ur, *wall_ut, *wall_up;
   int step7;
 };
 
@@ -98,6 +147,30 @@ template <>
 __host__ __device__ inline const float *mt<float>(const Shell &S, int t) {
   return S.ftab[t];
 }
+// row-coefficient record of row (i, j) in table t, in the arithmetic type V
+template <typename V>
+__host__ __device__ inline const V *rowc(const Shell &S, int t, int i, int j);
+template <>
+__host__ __device__ inline const double *rowc<double>(const Shell &S, int t, int i, int j) {
+  return S.rowd[t] + ((long)(i + 1) * (S.L.Nt + 2) + (j + 1)) * row_m(t);
+}
+template <>
+__host__ __device__ inline const float *rowc<float>(const Shell &S, int t, int i, int j) {
+  return S.rowf[t] + ((long)(i + 1) * (S.L.Nt + 2) + (j + 1)) * row_m(t);
+}
+// static line-operator coefficients of row (i, j) for (loc, dir), in the arithmetic type V
+template <typename V>
+__host__ __device__ inline const V *facc(const Shell &S, int loc, int dir, int i, int j);
+template <>
+__host__ __device__ inline const double *facc<double>(const Shell &S, int loc, int dir, int i, int j) {
+  const long rows = (long)(S.L.Nr + 2) * (S.L.Nt + 2);
+  return S.facd + ((3 * loc + dir) * rows + (long)(i + 1) * (S.L.Nt + 2) + (j + 1)) * FC_M;
+}
+template <>
+__host__ __device__ inline const float *facc<float>(const Shell &S, int loc, int dir, int i, int j) {
+  const long rows = (long)(S.L.Nr + 2) * (S.L.Nt + 2);
+  return S.facf + ((3 * loc + dir) * rows + (long)(i + 1) * (S.L.Nt + 2) + (j + 1)) * FC_M;
+}
 template <typename V>
 __host__ __device__ inline V cs(const Shell &S, int c);
 template <>
@@ -109,14 +182,16 @@ __host__ __device__ inline float cs<float>(const Shell &S, int c) {
   return S.fcs[c];
 }
 
-// fill dtab / dcs from the named FP64 fields (ftab / fcs are filled by the owner)
+// fill dtab / dcs / fcs / lcs from the named FP64 fields (ftab / ltab are filled by the owner)
 inline void shell_fill_fp64(Shell &S) {
   const double *t[kMetricTables] = {S.rc, S.rf, S.sc, S.sf, S.cc, S.cf, S.irc, S.irf, S.isc, S.isf};
   for (int k = 0; k < kMetricTables; ++k) S.dtab[k] = t[k];
-  const double c[CS_NUM] = {S.ihr, S.iht, S.ihp, S.i2chi, S.iR1sq, S.cphi, S.dt, S.nu, S.kappa, S.PrRa};
+  const double c[CS_NUM] = {S.ihr, S.iht, S.ihp, S.i2chi, S.iR1sq, S.cphi, S.dt, S.nu, S.kappa, S.PrRa,
+                            S.hr * S.ht * S.hp};
   for (int k = 0; k < CS_NUM; ++k) {
     S.dcs[k] = c[k];
     S.fcs[k] = (float)c[k];
+    S.lcs[k] = (float)(c[k] - (double)S.fcs[k]);
   }
 }
 

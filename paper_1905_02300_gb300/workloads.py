@@ -364,7 +364,59 @@ class SymmetricShell(Exact):
         return U, P, Th
 
 
-EXACT = {c.name: c for c in (TrigShell, CurlShell, RadialHeat, SymmetricShell)}
+class LandauJet(Exact):
+    """Landau's round jet (the steady solution used in Sec. 5.1), axisymmetric
+    about the global z-axis, with nu = Pr and jet parameter A > 1: stream
+    function psi = 2 nu r sin^2(theta) / (A - cos theta), so
+      u_r = (2 nu / r) ((A^2 - 1) / (A - cos theta)^2 - 1),
+      u_theta = -(2 nu / r) sin(theta) / (A - cos theta),
+      p = 4 nu^2 (A cos theta - 1) / (r^2 (A - cos theta)^2),  T = 0.
+    Steady (time factor 1); needs the wall velocity of the formula (wall_velocity)."""
+
+    name = "landau"
+    time_fn = 0
+    A = 2.0
+
+    def fields(self, x, y, z, F):
+        nu, A = self.Pr, self.A
+        r = F.sqrt(x * x + y * y + z * z)
+        c = z / r
+        w = A - c
+        ur = (2.0 * nu) / r * ((A * A - 1.0) / (w * w) - 1.0)
+        # u_theta e_theta = -(2 nu / (r (A - c))) (z x / r^2, z y / r^2, -(x^2 + y^2) / r^2)
+        g = (-2.0 * nu) / (r * w) / (r * r)
+        U = [ur * x / r + g * (z * x), ur * y / r + g * (z * y), ur * z / r - g * (x * x + y * y)]
+        P = (4.0 * nu * nu) * (A * c - 1.0) / (r * r * w * w)
+        Th = x * 0.0
+        return U, P, Th
+
+
+EXACT = {c.name: c for c in (TrigShell, CurlShell, RadialHeat, SymmetricShell, LandauJet)}
+
+
+def wall_velocity(ex: Exact, spec: Spec, t: float = 0.0):
+    """Velocity of ``ex`` on the walls r = R1 and r = R2 in each patch's local
+    basis, at every face point of the wall planes: dict 'ur' [2 walls][2
+    patches][Nth][Nph], 'uth' [..][Nth+1][Nph], 'uph' [..][Nth][Nph+1]."""
+    c = ex.tfac(t)
+    out = {}
+    for key, loc, comp in (("ur", "c", 0), ("uth", "t", 1), ("uph", "p", 2)):
+        _, th, ph = spec.coords(loc)
+        th2, ph2 = th[0, 0], ph[0, 0]
+        er, et, ep = local_basis(th2, ph2)
+        walls = []
+        for R in (spec.R1, spec.R2):
+            xl = R * np.sin(th2) * np.cos(ph2)
+            yl = R * np.sin(th2) * np.sin(ph2)
+            zl = R * np.cos(th2) + 0.0 * ph2
+            x, y, z = np.stack([xl, -xl]), np.stack([yl, zl]), np.stack([zl, yl])
+            U, _, _ = ex.fields(x, y, z, np)
+            U = [np.broadcast_to(u, x.shape) for u in U]
+            lx, ly, lz = np.stack([U[0][0], -U[0][1]]), np.stack([U[1][0], U[2][1]]), np.stack([U[2][0], U[1][1]])
+            e = (er, et, ep)[comp]
+            walls.append((lx * e[0] + ly * e[1] + lz * e[2]) * c)
+        out[key] = np.stack(walls)
+    return out
 
 
 class JetNS:

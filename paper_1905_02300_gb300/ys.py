@@ -44,6 +44,7 @@ _sig = {
     "ys_set_fields_dev": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
     "ys_set_forcing": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, _dp, _dp, _dp]),
+    "ys_set_wall_velocity": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
     "ys_set_time": (C.c_int, [C.c_void_p, C.c_double]),
     "ys_step": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "ys_get_fields": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]),
@@ -72,7 +73,8 @@ _sig = {
     "ys_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
     "ys_submit": (C.c_int, [C.c_void_p, C.POINTER(Params), _dp, C.c_int, C.c_int, C.POINTER(C.c_uint64)]),
     "ys_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_int), _dp, _dp]),
-    "ys_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_long), _dp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "ys_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_long), _dp, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int)]),
     "ys_server_destroy": (C.c_int, [C.c_void_p]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -153,6 +155,22 @@ class Solver:
     def set_forcing(self, mode, time_fn, fT, fr, fth, fph):
         arrs = [self._arr("T", fT), self._arr("ur", fr), self._arr("uth", fth), self._arr("uph", fph)]
         _check(lib.ys_set_forcing(self.h, mode, time_fn, *[_ptr(a) for a in arrs]), "ys_set_forcing")
+
+    def set_wall_velocity(self, walls):
+        """Dirichlet wall velocity: dict 'ur' [2][2][Nth][Nph], 'uth'
+        [2][2][Nth+1][Nph], 'uph' [2][2][Nth][Nph+1] (wall, patch, j, k);
+        a missing key means no-slip for that component."""
+        Nt, Np = self.params.Nth, self.params.Nph
+        shapes = {"ur": (2, 2, Nt, Np), "uth": (2, 2, Nt + 1, Np), "uph": (2, 2, Nt, Np + 1)}
+        arrs = []
+        for k in ("ur", "uth", "uph"):
+            a = walls.get(k)
+            if a is not None:
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                if a.shape != shapes[k]:
+                    raise ValueError(f"{k}: shape {a.shape}, expected {shapes[k]}")
+            arrs.append(a)
+        _check(lib.ys_set_wall_velocity(self.h, *[_ptr(a) for a in arrs]), "ys_set_wall_velocity")
 
     def set_time(self, t):
         _check(lib.ys_set_time(self.h, t), "ys_set_time")
@@ -321,9 +339,11 @@ class Server:
         return st.value, unpack_fields(buf, Nr, Nt, Np), lat.value, rc
 
     def stats(self):
-        steps, cu, run, q = C.c_long(), C.c_double(), C.c_int(), C.c_int()
-        _check(lib.ys_server_stats(self.h, C.byref(steps), C.byref(cu), C.byref(run), C.byref(q)), "ys_server_stats")
-        return {"steps": steps.value, "cell_updates": cu.value, "running": run.value, "queued": q.value}
+        steps, cu, run, q, pk = C.c_long(), C.c_double(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib.ys_server_stats(self.h, C.byref(steps), C.byref(cu), C.byref(run), C.byref(q), C.byref(pk)),
+               "ys_server_stats")
+        return {"steps": steps.value, "cell_updates": cu.value, "running": run.value, "queued": q.value,
+                "peak_running": pk.value}
 
     def close(self):
         if getattr(self, "h", None):

@@ -127,11 +127,9 @@ def test_server_continuous_batching(gpu_lib):
         spec = W.Spec(kw["R1"], 1.0, kw["Nr"], kw["Nth"], kw["Nph"])
         tickets.append(srv.submit(W.convection_initial(spec, sp["Pr"], sp["Ra"], T_in=1.0), n, **kw))
         time.sleep(0.01)
-    peak = 0
     done = {}
     t0 = time.time()
     while len(done) < len(tickets) and time.time() - t0 < 120:
-        peak = max(peak, srv.stats()["running"])
         for t in tickets:
             if t in done:
                 continue
@@ -145,7 +143,9 @@ def test_server_continuous_batching(gpu_lib):
         assert st == ys.Server.DONE and rc == 0 and lat > 0
         for k in e:
             assert np.array_equal(f[k], e[k]), k
-    assert 1 <= peak <= 3
+    # the server's own record: the budget never let more than ~2 run together
+    peak = srv.stats()["peak_running"]
+    assert 1 <= peak <= 3, peak
     srv.close()
 
 

@@ -532,3 +532,75 @@ def test_multiplicative_and_additive_reach_the_same_step():
     for k in a:
         assert np.abs(a[k] - m[k]).max() < 1e-8 * max(1.0, np.abs(a[k]).max()), k
     assert om.iters_done <= oa.iters_done
+
+
+# ------------------------------------------------------------------ Landau jet
+def _landau(N, dt, nsteps, tol=1e-9, maxit=20):
+    """Oracle run of Landau's jet (Sec. 5.1) from the exact steady state, with
+    the exact wall velocity, no forcing and no buoyancy."""
+    spec = W.Spec(0.5, 1.0, N, N, 3 * N)
+    ex = W.LandauJet(0.5, 1.0, 1.0, 0.0)
+    f = W.sample_fields(ex, spec, 0.0)
+    prm = Params(R1=0.5, R2=1.0, Pr=1.0, Ra=0.0, dt=dt, Nr=N, Nth=N, Nph=3 * N, schwarz_tol=tol,
+                 wall_u=W.wall_velocity(ex, spec))
+    o = Oracle(prm)
+    for lvl in (0, 1):
+        o.set_fields(lvl, f["T"], f["ur"], f["uth"], f["uph"], f["p"])
+    o.step(nsteps, maxit)
+    return o, spec, f
+
+
+def _div_l2(spec, f):
+    """l2 norm of the discrete divergence (Sec. 3.3: conservative face
+    differences with r^2 and sin(theta) at the faces) of user-layout velocity."""
+    r, th, _ = spec.coords("c")
+    rf = spec.R1 + np.arange(spec.Nr + 1) * spec.hr
+    sf = np.sin(spec.th0 + np.arange(spec.Nth + 1) * spec.hth)
+    ur, ut, up = f["ur"], f["uth"], f["uph"]
+    s = np.sin(th)[0]
+    d = ((rf[1:, None, None] ** 2 * ur[:, 1:] - rf[:-1, None, None] ** 2 * ur[:, :-1]) / (r[0] ** 2 * spec.hr)
+         + (sf[None, 1:, None] * ut[:, :, 1:] - sf[None, :-1, None] * ut[:, :, :-1]) / (r[0] * s * spec.hth)
+         + (up[..., 1:] - up[..., :-1]) / (r[0] * s * spec.hph))
+    return _l2(spec, "c", d)
+
+
+def test_landau_jet_is_a_steady_navier_stokes_solution():
+    """The Landau jet fields (stream function 2 nu r sin^2 / (A - cos), pressure
+    4 nu^2 (A cos - 1) / (r^2 (A - cos)^2)) solve the steady, unforced
+    Navier-Stokes equations: the continuous rate nu lap u - (u.grad)u - grad p
+    (AD in Cartesian coordinates) and div u vanish at every MAC point."""
+    spec = W.Spec(0.5, 1.0, 12, 12, 36)
+    ex = W.LandauJet(0.5, 1.0, 1.0, 0.0)
+    for loc, comp in (("r", 0), ("t", 1), ("p", 2)):
+        rt = W.exact_rates(ex, spec, loc, 0.0, 1.0, 0.0, 1.0)
+        terms = (rt["vlap"][comp], rt["adv"][comp], rt["gradp"][comp])
+        scale = max(np.abs(t).max() for t in terms)
+        res = terms[0] - terms[1] - terms[2]
+        assert np.abs(res).max() <= 1e-11 * scale, (loc, np.abs(res).max(), scale)
+        assert np.abs(rt["div"]).max() <= 1e-11 * scale
+
+
+def test_landau_jet_space_convergence_second_order():
+    """Sec. 5.1: second order in space on Landau's jet with Dirichlet wall
+    velocity from the formula (both patches carry the axisymmetric jet in
+    rotated local bases), Schwarz converged to a tolerance."""
+    errs = []
+    for N in (12, 20):
+        o, spec, f = _landau(N, 1e-4, 10)
+        g = o.get_fields(0)
+        errs.append({k: _l2(spec, LOCS[k], g[k] - f[k]) for k in ("ur", "uth", "uph", "p")})
+    for k in errs[0]:
+        order = math.log(errs[0][k] / errs[1][k]) / math.log(20 / 12)
+        assert order > 1.8, (k, errs, order)
+
+
+def test_landau_jet_divergence_is_second_order():
+    """The discrete divergence of the Landau run stays at the O(h^2) level of
+    the sampled exact field (its decay to zero needs the Step-4 mass-flux
+    correction of the Algorithm, which corrects the spurious flux of the
+    non-conservative overlap interpolation)."""
+    divs = []
+    for N in (12, 20):
+        o, spec, _ = _landau(N, 2e-4, 20, tol=0.0, maxit=3)
+        divs.append(_div_l2(spec, o.get_fields(0)))
+    assert math.log(divs[0] / divs[1]) / math.log(20 / 12) > 1.7, divs
