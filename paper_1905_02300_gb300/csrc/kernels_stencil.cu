@@ -80,7 +80,7 @@ __global__ void k_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R>
 // once and writes part[block] without atomics, and k_sum_parts adds the
 // shares up.
 template <typename R>
-constexpr int pres_rows() {
+__host__ __device__ constexpr int pres_rows() {
   return sizeof(R) == sizeof(float) ? 1 : 4;
 }
 template <typename R>
