@@ -552,7 +552,8 @@ __device__ __forceinline__ void body_factorize(Shell S, int loc, int dir, StepAu
                                                R *__restrict__ Iv, R *__restrict__ Cp, int patch_mask, int bx,
                                                int by) {
   using V = typename Cmp<R>::type;
-  constexpr int U = 4;   // rows whose coefficients are formed before the recurrence consumes them
+  // rows whose coefficients are formed (loads in flight) before the recurrence consumes them
+  constexpr int U = sizeof(R) == sizeof(float) ? 8 : 4;
   const Layout &L = S.L;
   const Line ln = decode_line(L, loc, dir, bx * blockDim.x + threadIdx.x, by);
   if (!ln.valid || !((patch_mask >> ln.p) & 1)) return;
