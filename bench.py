@@ -67,6 +67,31 @@ WORDS_PER_CELL = {
 # division = 1) for the FP64 form, whose kernels are bound by the FP64 pipe.
 FLOPS_PER_CELL = {"resid_T": 42.0, "resid_u": 91.0, "pressure": 21.0, "factorize": 11.0}
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of GB300 (profiling recipe)
+# DRAM bytes (read + write) per point of the top kernel class from one ncu
+# capture of its u_r launch on a smaller shell whose launch already exceeds L2
+# (traffic scales with the points processed); the bench reports it scaled to
+# one full launch.  Valid for the kernel code the capture was taken of.
+TRAFFIC_PER_POINT = {
+    (False, "resid_u"): (183.0e6 / (2 * 64 * 63 * 192), "profiles/k_resid_ur_fp64_64x64x192_full.md"),
+    (True, "resid_u"): (519.6e6 / (2 * 112 * 111 * 336), "profiles/k_resid_ur_mixed_112x112x336_full.md"),
+}
+
+
+def max_over_ranks(value, dist, device):
+    """Largest `value` over the ranks of the process group (all_reduce MAX); the
+    value itself without one.  The job's time is the slowest rank's."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, cells, steps, seconds):
+    """Whole-job cell-updates/s: every rank advances its own shell (replicas,
+    weak scaling), the job takes the slowest rank's time."""
+    return world * cells * steps / seconds
 
 
 def env_rank():
@@ -409,12 +434,8 @@ def main():
     prof = s.profile_read()
     s.profile(False)
     clk = clocks.stop()
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * cells * args.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = job_throughput(world, cells, args.steps, ms_max / 1e3)
 
     # end to end through the C ABI with pinned host buffers
     pinned = {}
@@ -438,8 +459,8 @@ def main():
             raise ys.YSError(rc, "ys_get_fields")
         if it > 0:
             t_e2e.append(time.perf_counter() - t0)
-    e2e_s = statistics.median(t_e2e)
-    e2e_val = world * cells / e2e_s
+    e2e_s = max_over_ranks(statistics.median(t_e2e), dist, "cuda")
+    e2e_val = job_throughput(world, cells, 1, e2e_s)
 
     # roofline of the dominant kernel: the three line-solve classes are one
     # kernel (k_solve)
@@ -468,6 +489,11 @@ def main():
                 "traffic": None, "kernel": top, "peak_source": src}
     roof["kernel_share"] = t_ms / sum(v[0] for v in prof.values())
     roof["launches"] = n_l
+    tp = TRAFFIC_PER_POINT.get((mixed, top))
+    if tp is not None:
+        roof["traffic"] = tp[0] * cells
+        roof["traffic_source"] = tp[1] + " (scaled from the capture's points to this launch)"
+        roof["algorithmic_bytes_per_launch"] = tot_bytes / n_l
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

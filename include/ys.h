@@ -85,10 +85,18 @@ typedef struct {
   int step7;            /* 1 = interpolate the pressure ring from the other
                            patch after each pressure update (Algorithm step 7,
                            default); 0 = off */
+  int step4;            /* 1 = mass-flux correction of the interpolated boundary
+                           velocity after every exchange (Algorithm step 4: the
+                           minimiser of its functional J, which the paper finds
+                           by conjugate gradients and which has the closed form
+                           v = u - alpha (w.u + c) / (1 + alpha w.w) w); 0 = off
+                           (default, as for the paper's results) */
+  double step4_eps;     /* epsilon << 1 of J (default 1e-8) */
+  double step4_tol;     /* correct only when |net boundary flux| >= tol (default 1e-13) */
 } ys_params;
 
 /* Fill *p with defaults (all sizes zero, chi = 1, overlap = 2, FP64,
- * additive, tol 0, walls 0, step7 on). */
+ * additive, tol 0, walls 0, step7 on, step4 off with eps 1e-8, tol 1e-13). */
 void ys_default_params(ys_params *p);
 
 /* Create a context for one shell with default parameters.  Validates the
@@ -230,7 +238,9 @@ typedef struct ys_batch ys_batch;
 /* capacity: 1..4096 slots; precision YS_FP64 or YS_MIXED; n_schwarz >= 1. */
 int ys_batch_create(int capacity, int precision, int n_schwarz, ys_batch **out);
 /* Add a context; *slot receives its slot.  YS_EBUSY when full, YS_EINVAL on a
- * precision / mode / forcing mismatch.  The caller keeps ownership. */
+ * precision mismatch, multiplicative Schwarz, forcing modes or step4 (batched
+ * shells run additive Schwarz without Algorithm step 4).  The caller keeps
+ * ownership. */
 int ys_batch_add(ys_batch *b, ys_ctx *c, int *slot);
 /* Remove the shell in `slot`; its context (time, step count, levels) is
  * brought up to date and returned in *c for ys_get_fields or ys_step. */

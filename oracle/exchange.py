@@ -30,6 +30,8 @@ this and raises if the grid is too coarse for it.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 from .grid import C, PH, R, TH, M, e_phi, e_theta, sph_to_unit, unit_to_sph
@@ -120,7 +122,68 @@ def _interp(a_donor, st, i_slice):
             + wj * (1 - wk) * A[:, J + 1, K] + wj * wk * A[:, J + 1, K + 1])
 
 
-def exchange_into(tables, target, fields, patches, T_walls=(0.0, 0.0), U_walls=None):
+def boundary_flux_weights(g):
+    """Outward normal times face area of every boundary velocity value of a
+    patch, from the discrete Gauss theorem of the divergence (Sec. 3.3: the
+    sum over cells of div * r^2 sin(theta) h_r h_th h_ph telescopes to these
+    face terms): theta-edge faces r_c sin(theta_f) h_r h_ph, phi-edge faces
+    r_c h_r h_th, wall faces r_f^2 sin(theta_c) h_th h_ph.  Returns
+    (wt0, wt1, wp0, wp1, wr0, wr1) shaped like the faces' value blocks
+    (Nr x Nph, Nr x Nph, Nr x Nth, Nr x Nth, Nth x Nph, Nth x Nph)."""
+    Nr, Nt, Np = g.Nr, g.Nth, g.Nph
+    rc = g.r_c(np.arange(Nr))[:, None]
+    sc = np.sin(g.th_c(np.arange(Nt)))
+    ones_p = np.ones((1, Np))
+    wt = lambda j: rc * math.sin(g.th_f(j)) * g.hr * g.hph * ones_p
+    wp = rc * g.hr * g.hth * np.ones((1, Nt))
+    wr = lambda i: g.r_f(i) ** 2 * sc[:, None] * g.hth * g.hph * ones_p
+    return (-wt(0), wt(Nt), -wp, wp, -wr(0), wr(Nr))
+
+
+def mass_flux_correction(g, U, p, eps, tol, maxit=50):
+    """Algorithm step 4: if the net flux of patch p's boundary velocity
+    through its boundary is at least tol, replace the interpolated normal
+    components v on the theta and phi edges by the minimiser of
+      J(v) = |v - u_bd|^2 / 2 + (flux_edges(v) + flux_walls(u_bd))^2 / (2 eps |dOmega|^2)
+    found by the conjugate gradient method (the Hessian is I + alpha w w^T,
+    alpha = 1 / (eps |dOmega|^2), w the edge weights).  U: padded velocity
+    components [u_r, u_theta, u_phi] of both patches."""
+    Nr, Nt, Np = g.Nr, g.Nth, g.Nph
+    wt0, wt1, wp0, wp1, wr0, wr1 = boundary_flux_weights(g)
+    ur, ut, up = U[0][p], U[1][p], U[2][p]
+    cells_r = slice(1, Nr + 1)
+    blocks = [(ut, (cells_r, 1, slice(1, Np + 1)), wt0), (ut, (cells_r, Nt + 1, slice(1, Np + 1)), wt1),
+              (up, (cells_r, slice(1, Nt + 1), 1), wp0), (up, (cells_r, slice(1, Nt + 1), Np + 1), wp1)]
+    u = np.concatenate([a[ix].ravel() for a, ix, _ in blocks])
+    w = np.concatenate([wb.ravel() for _, _, wb in blocks])
+    c = np.sum(wr0 * ur[1, 1:Nt + 1, 1:Np + 1]) + np.sum(wr1 * ur[Nr + 1, 1:Nt + 1, 1:Np + 1])
+    if abs(np.dot(w, u) + c) < tol:
+        return
+    area = np.sum(np.abs(w)) + np.sum(np.abs(wr0)) + np.sum(np.abs(wr1))
+    alpha = 1.0 / (eps * area * area)
+    H = lambda x: x + alpha * w * np.dot(w, x)
+    b = u - alpha * c * w
+    x = u.copy()
+    r = b - H(x)
+    d = r.copy()
+    rr = np.dot(r, r)
+    for _ in range(maxit):
+        if math.sqrt(rr) <= 1e-15 * math.sqrt(np.dot(b, b)):
+            break
+        Hd = H(d)
+        a = rr / np.dot(d, Hd)
+        x += a * d
+        r -= a * Hd
+        rr_new = np.dot(r, r)
+        d = r + (rr_new / rr) * d
+        rr = rr_new
+    o = 0
+    for a, ix, wb in blocks:
+        a[ix] = x[o:o + wb.size].reshape(wb.shape)
+        o += wb.size
+
+
+def exchange_into(tables, target, fields, patches, T_walls=(0.0, 0.0), U_walls=None, step4=None):
     """Fill the boundary values of the listed target ``patches`` from the other
     patch, for the state dict ``fields`` (padded arrays with keys 'T' and the
     velocity lists 'u1', 'u2').  Donor values are read from a snapshot taken
@@ -146,6 +209,10 @@ def exchange_into(tables, target, fields, patches, T_walls=(0.0, 0.0), U_walls=N
                 vp = _interp(S[2][d], e["sp"], cells)
                 U[comp][p][cells, e["j"] + 1, e["k"] + 1] = e["rot"][0] * vt + e["rot"][1] * vp
     wall_ghosts(g, target, patches, T_walls, U_walls)
+    if step4 is not None:   # (eps, tol): Algorithm step 4 on both systems' boundary velocity
+        for p in patches:
+            for key in ("u1", "u2"):
+                mass_flux_correction(g, target[key], p, step4[0], step4[1])
 
 
 def wall_ghosts(g, fields, patches, T_walls=(0.0, 0.0), U_walls=None):

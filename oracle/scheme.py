@@ -67,6 +67,11 @@ class Params:
     # basis: dict 'ur' [2 walls][2 patches][Nth][Nph], 'uth' [..][Nth+1][Nph],
     # 'uph' [..][Nth][Nph+1]; None = no-slip
     wall_u: Optional[dict] = None
+    # Algorithm step 4 (mass-flux correction of the interpolated boundary
+    # velocity); the paper skips it for its results, so it is off by default
+    step4: bool = False
+    step4_eps: float = 1e-8
+    step4_tol: float = 1e-13
 
 
 def _time_fn(tid, t):
@@ -140,7 +145,8 @@ class Oracle:
 
     def _refresh(self, L, patches):
         d = L.as_dict()
-        xch.exchange_into(self.tables, d, d, patches, (self.prm.T_in, self.prm.T_out), self.prm.wall_u)
+        xch.exchange_into(self.tables, d, d, patches, (self.prm.T_in, self.prm.T_out), self.prm.wall_u,
+                          self._step4())
         if self.prm.step7:
             xch.pressure_ring(self.tables, L.p1, patches)
             xch.pressure_ring(self.tables, L.p2, patches)
@@ -183,6 +189,9 @@ class Oracle:
         for _ in range(n_steps):
             self._one_step(n_schwarz)
 
+    def _step4(self):
+        return (self.prm.step4_eps, self.prm.step4_tol) if self.prm.step4 else None
+
     def _factors(self, A):
         prm, g = self.prm, self.g
         fac = {}
@@ -206,7 +215,7 @@ class Oracle:
         for k in range(1, K + 1):
             if prm.schwarz_mode == "additive":
                 d = it.as_dict()
-                xch.exchange_into(self.tables, d, d, (0, 1), (prm.T_in, prm.T_out), prm.wall_u)
+                xch.exchange_into(self.tables, d, d, (0, 1), (prm.T_in, prm.T_out), prm.wall_u, self._step4())
                 norms = self._iterate(it, n, A, f, fac, (0, 1))
                 if prm.step7:
                     xch.pressure_ring(self.tables, it.p1, (0, 1))
@@ -215,7 +224,7 @@ class Oracle:
                 norms = np.zeros(len(FIELD_NAMES))
                 for p in (0, 1):
                     d = it.as_dict()
-                    xch.exchange_into(self.tables, d, d, (p,), (prm.T_in, prm.T_out), prm.wall_u)
+                    xch.exchange_into(self.tables, d, d, (p,), (prm.T_in, prm.T_out), prm.wall_u, self._step4())
                     norms += self._iterate(it, n, A, f, fac, (p,)) ** 2
                     if prm.step7:
                         xch.pressure_ring(self.tables, it.p1, (p,))

@@ -83,6 +83,7 @@ int validate(const ys_params *p) {
   if (p->precision != YS_FP64 && p->precision != YS_MIXED) return YS_EINVAL;
   if (p->schwarz_mode != YS_ADDITIVE && p->schwarz_mode != YS_MULTIPLICATIVE) return YS_EINVAL;
   if (!(p->Pr > 0.0) || !(p->Ra >= 0.0) || !(p->schwarz_tol >= 0.0)) return YS_EINVAL;
+  if (p->step4 && (!(p->step4_eps > 0.0) || !(p->step4_tol >= 0.0))) return YS_EINVAL;
   return YS_OK;
 }
 
@@ -129,9 +130,18 @@ int copy_out_p(ys_ctx *c, const double *src, double *dst) {
 // exchange + walls (+ pressure ring) of a whole state: boundary values as
 // functions of the interior
 template <typename R>
-void refresh(ys_ctx *c, State<R> s, int mask) {
+void exchange_walls(ys_ctx *c, State<R> s, int mask) {
   LAUNCH(c, K_EXCH, 4, Launch<R>::exchange(c->S, c->X, s, mask, c->stream));
   LAUNCH(c, K_WALLS, 1, Launch<R>::walls(c->S, s, mask, c->stream));
+  if (c->prm.step4)
+    LAUNCH(c, K_EXCH, 2,
+           Launch<R>::mass_flux(c->S, s, mask, c->norm + 16, c->s4_alpha, c->s4_wsq, c->s4_cwall[0],
+                                c->s4_cwall[1], c->prm.step4_tol, c->stream));
+}
+
+template <typename R>
+void refresh(ys_ctx *c, State<R> s, int mask) {
+  exchange_walls<R>(c, s, mask);
   if (c->prm.step7) LAUNCH(c, K_RING, 1, Launch<R>::ring(c->S, c->X, s, mask, c->stream));
 }
 
@@ -234,15 +244,13 @@ int step_t(ys_ctx *c, int n_steps, int n_schwarz) {
     for (int k = 1; k <= n_schwarz; ++k) {
       cudaMemsetAsync(c->norm, 0, YS_NFIELDS * sizeof(double), c->stream);
       if (prm.schwarz_mode == YS_ADDITIVE) {
-        LAUNCH(c, K_EXCH, 4, Launch<R>::exchange(c->S, c->X, it, 3, c->stream));
-        LAUNCH(c, K_WALLS, 1, Launch<R>::walls(c->S, it, 3, c->stream));
+        exchange_walls<R>(c, it, 3);
         iterate<R>(c, ax, 3);
         if (prm.step7) LAUNCH(c, K_RING, 1, Launch<R>::ring(c->S, c->X, it, 3, c->stream));
       } else {
         for (int p = 0; p < 2; ++p) {
           int m = 1 << p;
-          LAUNCH(c, K_EXCH, 4, Launch<R>::exchange(c->S, c->X, it, m, c->stream));
-          LAUNCH(c, K_WALLS, 1, Launch<R>::walls(c->S, it, m, c->stream));
+          exchange_walls<R>(c, it, m);
           iterate<R>(c, ax, m);
           if (prm.step7) LAUNCH(c, K_RING, 1, Launch<R>::ring(c->S, c->X, it, m, c->stream));
         }
@@ -364,6 +372,9 @@ int set_forcing_t(ys_ctx *c, int mode, const double *f_T, const double *f_r, con
   return cuda_ok(cudaStreamSynchronize(c->stream));
 }
 
+// FP64 fields: p1, p2 of the three levels
+constexpr size_t kPresFields = 6;
+
 // carve the typed state out of one device allocation starting at `base`
 template <typename R>
 char *carve(ys_ctx *c, Fields<R> &D, char *base) {
@@ -388,7 +399,7 @@ char *carve(ys_ctx *c, Fields<R> &D, char *base) {
   double *pp = (double *)next;
   for (int l = 0; l < 3; ++l)
     for (int q = 0; q < 2; ++q) D.lev[l].p[q] = pp + (2 * l + q) * T;
-  return next + ((6 * T * sizeof(double) + 255) / 256) * 256;
+  return next + ((kPresFields * T * sizeof(double) + 255) / 256) * 256;
 }
 
 // number of bulk fields of one shell (3 x 7 levels, 3 a, 4 forcing, B, Cs, 36 factors)
@@ -407,6 +418,9 @@ void ys_default_params(ys_params *p) {
   p->schwarz_mode = YS_ADDITIVE;
   p->schwarz_tol = 0.0;
   p->step7 = 1;
+  p->step4 = 0;
+  p->step4_eps = 1e-8;
+  p->step4_tol = 1e-13;
 }
 
 const char *ys_strerror(int code) {
@@ -505,7 +519,7 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   }
   size_t Rsz = mixed ? sizeof(float) : sizeof(double);
   size_t bulk_bytes = ((kBulkFields * L.total * Rsz + 255) / 256) * 256;
-  size_t p_bytes = ((6 * L.total * sizeof(double) + 255) / 256) * 256;
+  size_t p_bytes = ((kPresFields * L.total * sizeof(double) + 255) / 256) * 256;
   size_t xcount = 0;
   for (int k = 0; k < XNUM; ++k) xcount += xt[k].size();
   size_t stage_elems = user_elems(L, LR);
@@ -608,6 +622,26 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
     c->X.e[k] = c->xdev + xo;
     c->X.n[k] = (int)xt[k].size();
     xo += xt[k].size();
+  }
+  if (p->step4) {
+    // Algorithm step 4: edge flux weights (outward normal x face area) of one
+    // patch, their squares' sum and the whole boundary's area
+    double wsq = 0.0, area = 0.0;
+    for (int i = 0; i < p->Nr; ++i) {
+      const double rc = p->R1 + (i + 0.5) * G.hr;
+      for (int side = 0; side < 2; ++side) {
+        const double wt = rc * std::sin(G.th0 + (side ? p->Nth : 0) * G.ht) * G.hr * G.hp;
+        const double wp = rc * G.hr * G.ht;
+        wsq += p->Nph * wt * wt + p->Nth * wp * wp;
+        area += p->Nph * wt + p->Nth * wp;
+      }
+    }
+    for (int j = 0; j < p->Nth; ++j) {
+      const double sc = std::sin(G.th0 + (j + 0.5) * G.ht);
+      area += p->Nph * (p->R1 * p->R1 + p->R2 * p->R2) * sc * G.ht * G.hp;
+    }
+    c->s4_wsq = wsq;
+    c->s4_alpha = 1.0 / (p->step4_eps * area * area);
   }
   Shell &S = c->S;
   S.L = L;
@@ -739,6 +773,18 @@ int ys_set_wall_velocity(ys_ctx *c, const double *ur, const double *uth, const d
       *dst[m] = nullptr;
     }
     off += n[m];
+  }
+  // Algorithm step 4: wall flux of each patch, sum of (outward) r_f^2 sin(theta_c) h_th h_ph u_r
+  c->s4_cwall[0] = c->s4_cwall[1] = 0.0;
+  if (ur) {
+    const double R[2] = {c->prm.R1, c->prm.R2};
+    for (int w = 0; w < 2; ++w)
+      for (int p = 0; p < 2; ++p)
+        for (long j = 0; j < Nt; ++j) {
+          const double a = (w ? 1.0 : -1.0) * R[w] * R[w] * std::sin(c->geo.th0 + (j + 0.5) * c->geo.ht) *
+                           c->geo.ht * c->geo.hp;
+          for (long k = 0; k < Np; ++k) c->s4_cwall[p] += a * ur[((w * 2 + p) * Nt + j) * Np + k];
+        }
   }
   // boundary values of the stored levels follow the new wall data
   if (c->f32)

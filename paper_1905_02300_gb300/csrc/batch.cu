@@ -377,7 +377,7 @@ void enqueue_step(ys_batch *b) {
   ++nl;
   for (int loc = LC; loc <= LP; ++loc)
     for (int dir = DR; dir <= DP; ++dir) {
-      if (dir == DP)
+      if (dir == DP && bd::use_phi_scan<R>())
         kb_factorize_phi<R><<<gp, 32 * bd::kScanWarps, 0, st>>>(sh, map_of(b, M_PSC0 + loc), cap, loc);
       else
         kb_factorize<R><<<gl, b->tpb_line, 0, st>>>(sh, map_of(b, M_LINE0 + 3 * loc + dir), cap, loc, dir);
@@ -514,7 +514,7 @@ int ys_batch_create(int capacity, int precision, int n_schwarz, ys_batch **out) 
 int ys_batch_add(ys_batch *b, ys_ctx *c, int *slot) {
   if (!b || !c || !slot) return YS_EINVAL;
   if ((c->prm.precision == YS_MIXED) != (b->precision == YS_MIXED)) return YS_EINVAL;
-  if (c->prm.schwarz_mode != YS_ADDITIVE || c->nmodes_set > 0) return YS_EINVAL;
+  if (c->prm.schwarz_mode != YS_ADDITIVE || c->nmodes_set > 0 || c->prm.step4) return YS_EINVAL;
   int s = -1;
   for (int i = 0; i < b->cap; ++i)
     if (!b->slot[i]) {

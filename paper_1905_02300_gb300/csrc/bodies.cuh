@@ -304,9 +304,10 @@ __device__ __forceinline__ typename Cmp<R>::type body_pressure(Shell S, int sys,
   double D;
   if constexpr (sizeof(R) == sizeof(float)) {
     // FP32 storage: double-float divergence (FP64-accurate, FP32 instructions)
-    D = ff_double(divh_ff(S, velf(it, sys, 0), velf(n, sys, 0), velf(it, sys, 1), velf(n, sys, 1), velf(it, sys, 2),
-                          velf(n, sys, 2), i, j, q));
-    D = D * (2.0 * S.i2chi);
+    // (divergence / chi) with the factor 2 (2 chi)^-1 applied in double-float
+    const FF kc = ff_mul(ff_cs(S, CS_I2CHI), FF{2.0f, 0.0f});
+    D = ff_double(ff_mul(kc, divh_ff(S, velf(it, sys, 0), velf(n, sys, 0), velf(it, sys, 1), velf(n, sys, 1),
+                                     velf(it, sys, 2), velf(n, sys, 2), i, j, q)));
   } else {
     // divergence of the half-level velocity times 1/chi from the row record
     const double *c = rowc<double>(S, RT_DIV, i, j);
@@ -700,6 +701,15 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
 // per-warp shared-memory buffer when the line fits (`wsm`), else in W.
 // Positions outside [k0, Np) map to 0 (the chain restarts at k0 anyway) and
 // are never written.
+// The factorisation scan carries several times the arithmetic of the
+// sequential elimination (2x2 matrix products): it pays off where memory
+// latency is the bound (FP32 storage), not where the FP64 pipe is (measured:
+// FP64 phi factorisation 59.9 ms per 10 steps as a scan, 50.0 sequential;
+// the solve scan stays ahead in both forms, 54.1 vs 69.9 ms in FP64).
+template <typename R>
+__host__ __device__ constexpr bool use_phi_scan() {
+  return sizeof(R) == sizeof(float);
+}
 constexpr int kScanWarps = 4;           // lines (warps) per CTA
 constexpr int kScanSmemMax = 96 * 1024;   // shared memory a CTA may take for the forward results
 

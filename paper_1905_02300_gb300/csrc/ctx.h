@@ -51,6 +51,9 @@ struct ys_ctx {
   double *norm = nullptr;     // YS_NFIELDS accumulators
   double *stage = nullptr;    // host-layout staging (device); per-block norm shares of k_pressure during a step
   double *dwall = nullptr;    // Dirichlet wall velocity (device, ys_set_wall_velocity), or null
+  // Algorithm step 4: alpha = 1 / (eps |dOmega|^2), w.w of the edge flux
+  // weights, and the wall flux c of each patch (from the wall velocity)
+  double s4_alpha = 0.0, s4_wsq = 0.0, s4_cwall[2] = {0.0, 0.0};
   double *T_bg = nullptr;     // deviation backgrounds per radial index (mixed form), else null
   double *p_bg = nullptr;
   int mode_fn[ys::kMaxModes] = {};

@@ -72,6 +72,9 @@ struct Launch {
                     R *W, R *dst, double *norm, int slot, int patch_mask, cudaStream_t st);
   // pressure update of system sys; part: scratch of one FP64 per cell block
   // (partial norms, summed into norm[4] or norm[8] by a second kernel)
+  // Algorithm step 4 on the edge velocity of both systems (acc: 4 FP64 scratch)
+  static void mass_flux(const Shell &S, State<R> s, int patch_mask, double *acc, double alpha, double wsq,
+                        double cw0, double cw1, double tol, cudaStream_t st);
   static void pressure(const Shell &S, int sys, State<R> it, State<R> n, double *norm, double *part,
                        int patch_mask, cudaStream_t st);
   // host layout <-> device layout; bg (FP64 per radial index, may be null) is

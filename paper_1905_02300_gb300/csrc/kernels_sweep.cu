@@ -7,8 +7,10 @@
 // then solves with the stored factors.  Lines along r and theta: one thread
 // per line, the lines of a warp neighbours along phi (the fastest index), so
 // every load and store of the recurrences is coalesced.  Lines along phi
-// (contiguous in memory): factorisation and solves as warp scans (one warp
-// per line, see body_factorize_phi_scan and body_solve_phi_scan).  The
+// (contiguous in memory): solves as warp scans (one warp per line, see
+// body_solve_phi_scan); factorisation as a warp scan with FP32 storage
+// (body_factorize_phi_scan) and, in FP64, where the FP64 pipe is the bound,
+// one thread per line as along r and theta (lanes along theta).  The
 // last factor of an unknown adds its solution to the iterate and accumulates
 // the midpoint-rule norm of the increment (Sec. 5.1).
 //
@@ -220,7 +222,7 @@ void Launch<R>::sweep(const Shell &S, int loc, int dir, bool final, StepAux<R> a
 template <typename R>
 void Launch<R>::factorize(const Shell &S, int loc, int dir, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask,
                           cudaStream_t st) {
-  if (dir == DP) {
+  if (dir == DP && bd::use_phi_scan<R>()) {
     k_factorize_phi<R><<<bd::phi_scan_ctas(S.L, loc), 32 * bd::kScanWarps, 0, st>>>(S, loc, ax, Lo, Iv, Cp,
                                                                                    patch_mask);
     return;

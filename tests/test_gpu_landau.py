@@ -92,3 +92,41 @@ def test_landau_space_convergence_second_order(gpu_lib):
     for k in errs[0]:
         order = math.log(errs[0][k] / errs[1][k]) / math.log(2.0)
         assert order > 1.8, (k, errs, order)
+
+
+def test_step4_parity_and_zero_boundary_flux(gpu_lib):
+    """Algorithm step 4 on both sides (oracle: conjugate gradients on J; CUDA:
+    its closed-form minimiser): FP64 parity after 10 steps, and the stored
+    level's boundary velocity carries no net flux through either patch's
+    boundary (discrete Gauss weights)."""
+    ys = gpu_lib
+    N, dt = 12, 1e-4
+    spec = W.Spec(0.5, 1.0, N, N, 3 * N)
+    ex = W.LandauJet(0.5, 1.0, 1.0, 0.0)
+    f = W.sample_fields(ex, spec, 0.0)
+    walls = W.wall_velocity(ex, spec)
+    o = Oracle(Params(R1=0.5, R2=1.0, Pr=1.0, Ra=0.0, dt=dt, Nr=N, Nth=N, Nph=3 * N, wall_u=walls, step4=True))
+    s = ys.Solver(R1=0.5, R2=1.0, Pr=1.0, Ra=0.0, dt=dt, Nr=N, Nth=N, Nph=3 * N, step4=1)
+    s.set_wall_velocity(walls)
+    for lvl in (0, 1):
+        o.set_fields(lvl, f["T"], f["ur"], f["uth"], f["uph"], f["p"])
+        s.set_fields_dict(lvl, f)
+    o.step(10, 3)
+    s.step(10, 3)
+    e = rel_errs(s, o)
+    assert max(e.values()) <= 1e-11, e
+    g = s.get_fields(0)
+    r = 0.5 + (np.arange(N) + 0.5) * spec.hr
+    thf = spec.th0 + np.arange(N + 1) * spec.hth
+    thc = spec.th0 + (np.arange(N) + 0.5) * spec.hth
+    for p in (0, 1):
+        terms = [-r[:, None] * math.sin(thf[0]) * spec.hr * spec.hph * g["uth"][p, :, 0, :],
+                 r[:, None] * math.sin(thf[N]) * spec.hr * spec.hph * g["uth"][p, :, N, :],
+                 -r[:, None] * spec.hr * spec.hth * g["uph"][p, :, :, 0],
+                 r[:, None] * spec.hr * spec.hth * g["uph"][p, :, :, 3 * N],
+                 -0.25 * np.sin(thc)[:, None] * spec.hth * spec.hph * g["ur"][p, 0],
+                 1.0 * np.sin(thc)[:, None] * spec.hth * spec.hph * g["ur"][p, N]]
+        flux = sum(np.sum(t) for t in terms)
+        scale = sum(np.sum(np.abs(t)) for t in terms[:4])
+        # eps = 1e-8 shrinks the flux by 1 + |w|^2 / (eps |dOmega|^2) (~2e3 here)
+        assert abs(flux) <= 1e-6 * scale, (p, flux, scale)
