@@ -93,10 +93,17 @@ typedef struct {
                            (default, as for the paper's results) */
   double step4_eps;     /* epsilon << 1 of J (default 1e-8) */
   double step4_tol;     /* correct only when |net boundary flux| >= tol (default 1e-13) */
+  /* temperature wall conditions a T + b dT/dn = T_inner (r = R1) and
+     = T_outer (r = R2), n the outward normal (Sec. 1: Dirichlet, Neumann or
+     Robin walls); a, b >= 0, a + b > 0; default a = 1, b = 0 (Dirichlet).  The
+     mixed form keeps its conductive-profile deviation variables only for
+     Dirichlet walls. */
+  double Tbc_inner_a, Tbc_inner_b, Tbc_outer_a, Tbc_outer_b;
 } ys_params;
 
 /* Fill *p with defaults (all sizes zero, chi = 1, overlap = 2, FP64,
- * additive, tol 0, walls 0, step7 on, step4 off with eps 1e-8, tol 1e-13). */
+ * additive, tol 0, walls 0 (Dirichlet), step7 on, step4 off with eps 1e-8,
+ * tol 1e-13). */
 void ys_default_params(ys_params *p);
 
 /* Create a context for one shell with default parameters.  Validates the
@@ -200,8 +207,9 @@ size_t ys_device_bytes(ys_ctx *c);
  * the three 1-D factors (I - dt/2 Ahat_d) of one unknown in its stated order
  * (the correction solve of Eq. er: T r, theta, phi; u_r theta, phi, r;
  * u_theta phi, r, theta; u_phi r, theta, phi), for one shell described by
- * *prm (R1, R2, Pr as viscosity, dt, chi, overlap, Nr, Nth, Nph; other fields
- * ignored).  loc selects the unknown: 0 = T, 1 = u_r, 2 = u_theta, 3 = u_phi.
+ * *prm (R1, R2, Pr as viscosity, dt, chi, overlap, Nr, Nth, Nph, and the
+ * temperature wall conditions Tbc_* whose ghosts set the T factor's wall rows;
+ * other fields ignored).  loc selects the unknown: 0 = T, 1 = u_r, 2 = u_theta, 3 = u_phi.
  * All pointers are caller-owned DEVICE memory in the field layouts above:
  * A_r, A_th, A_ph the advecting velocity on r-, theta- and phi-faces; rhs and
  * x in the layout of the unknown (boundary entries of rhs are ignored, those

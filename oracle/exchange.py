@@ -183,7 +183,8 @@ def mass_flux_correction(g, U, p, eps, tol, maxit=50):
         o += wb.size
 
 
-def exchange_into(tables, target, fields, patches, T_walls=(0.0, 0.0), U_walls=None, step4=None):
+def exchange_into(tables, target, fields, patches, T_walls=(0.0, 0.0), U_walls=None, step4=None,
+                  T_robin=((1.0, 0.0), (1.0, 0.0))):
     """Fill the boundary values of the listed target ``patches`` from the other
     patch, for the state dict ``fields`` (padded arrays with keys 'T' and the
     velocity lists 'u1', 'u2').  Donor values are read from a snapshot taken
@@ -208,23 +209,35 @@ def exchange_into(tables, target, fields, patches, T_walls=(0.0, 0.0), U_walls=N
                 vt = _interp(S[1][d], e["st"], cells)
                 vp = _interp(S[2][d], e["sp"], cells)
                 U[comp][p][cells, e["j"] + 1, e["k"] + 1] = e["rot"][0] * vt + e["rot"][1] * vp
-    wall_ghosts(g, target, patches, T_walls, U_walls)
+    wall_ghosts(g, target, patches, T_walls, U_walls, T_robin)
     if step4 is not None:   # (eps, tol): Algorithm step 4 on both systems' boundary velocity
         for p in patches:
             for key in ("u1", "u2"):
                 mass_flux_correction(g, target[key], p, step4[0], step4[1])
 
 
-def wall_ghosts(g, fields, patches, T_walls=(0.0, 0.0), U_walls=None):
-    """Radial wall data (Sec. 2, Dirichlet walls): u_r on the wall faces is the
-    wall value; cell-centred quantities in r (T, u_theta, u_phi) get the
-    reflection ghost 2 g - x_0 on their unknown columns, g the wall value.
+def robin_ghost(a, b, hr):
+    """Ghost x_g = gamma x_0 + delta of a cell-centred quantity for the wall
+    condition a x + b dx/dn = g (Sec. 1: Dirichlet, Neumann or Robin walls),
+    with x = (x_g + x_0)/2 and dx/dn = (x_g - x_0)/h_r on the wall: returns
+    (gamma, delta per unit g).  Dirichlet (1, 0): (-1, 2)."""
+    den = 0.5 * a + b / hr
+    return -(0.5 * a - b / hr) / den, 1.0 / den
+
+
+def wall_ghosts(g, fields, patches, T_walls=(0.0, 0.0), U_walls=None, T_robin=((1.0, 0.0), (1.0, 0.0))):
+    """Radial wall data (Sec. 2): u_r on the wall faces is the wall value;
+    u_theta, u_phi get the reflection ghost 2 g - x_0 about the wall velocity g;
+    T gets the ghost of its wall condition a T + b dT/dn = T_wall (T_robin
+    gives (a, b) per wall; (1, 0) = Dirichlet: 2 T_wall - T_0).
     U_walls: None (no-slip) or wall velocities as in Params.wall_u."""
     Nr, Nt, Np = g.Nr, g.Nth, g.Nph
+    gi, di_ = robin_ghost(T_robin[0][0], T_robin[0][1], g.hr)
+    go, do_ = robin_ghost(T_robin[1][0], T_robin[1][1], g.hr)
     for p in patches:
         T = fields["T"][p]
-        T[0, 1:Nt + 1, 1:Np + 1] = 2.0 * T_walls[0] - T[1, 1:Nt + 1, 1:Np + 1]
-        T[Nr + 1, 1:Nt + 1, 1:Np + 1] = 2.0 * T_walls[1] - T[Nr, 1:Nt + 1, 1:Np + 1]
+        T[0, 1:Nt + 1, 1:Np + 1] = gi * T[1, 1:Nt + 1, 1:Np + 1] + di_ * T_walls[0]
+        T[Nr + 1, 1:Nt + 1, 1:Np + 1] = go * T[Nr, 1:Nt + 1, 1:Np + 1] + do_ * T_walls[1]
         if U_walls is None:
             gr = (0.0, 0.0)
             gt = (0.0, 0.0)

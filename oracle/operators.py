@@ -236,10 +236,11 @@ ORDER = {C: "rtp", R: "tpr", TH: "prt", PH: "rtp"}
 REFLECT_R = {C: True, R: False, TH: True, PH: True}
 
 
-def factor(g, loc, d, A, dt, nu, chi):
+def factor(g, loc, d, A, dt, nu, chi, gamma=(-1.0, -1.0)):
     """Tridiagonal coefficients (lo, di, up) of (I - dt/2 Ahat_d) at the
     unknowns of ``loc`` along direction ``d`` in 'r', 't', 'p', with the
-    homogeneous boundary rows of the correction already folded in.
+    homogeneous boundary rows of the correction already folded in (gamma:
+    ghost factors of T at the two walls, see exchange.robin_ghost).
 
     Ahat_d (Sec. 3.2 modified operators; Eq. r_comp, theta_comp, phi_comp):
       diffusion: true D_rr along r; (R1^2 s)^-1 d_th(s d_th) along theta;
@@ -319,9 +320,11 @@ def factor(g, loc, d, A, dt, nu, chi):
     last[ax] = -1
     first, last = tuple(first), tuple(last)
     if d == "r" and REFLECT_R[loc]:
-        # correction ghost = -(first/last unknown): fold into the diagonal
-        di[first] -= lo[first]
-        di[last] -= up[last]
+        # correction ghost = gamma (first/last unknown) (homogeneous wall
+        # condition; gamma = -1 for Dirichlet): fold into the diagonal
+        g0, g1 = gamma if loc == C else (-1.0, -1.0)
+        di[first] += g0 * lo[first]
+        di[last] += g1 * up[last]
     lo[first] = 0.0
     up[last] = 0.0
     return lo, di, up

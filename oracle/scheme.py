@@ -61,6 +61,10 @@ class Params:
     schwarz_tol: float = 0.0
     T_in: float = 0.0
     T_out: float = 0.0
+    # temperature wall condition a T + b dT/dn = T_in / T_out per wall (Sec. 1:
+    # Dirichlet (1, 0), Neumann (0, 1) or Robin)
+    Tbc_in: tuple = (1.0, 0.0)
+    Tbc_out: tuple = (1.0, 0.0)
     step7: bool = True
     kappa: float = 1.0
     # Dirichlet velocity on the walls r = R1, R2 (steady), in each patch's local
@@ -146,7 +150,7 @@ class Oracle:
     def _refresh(self, L, patches):
         d = L.as_dict()
         xch.exchange_into(self.tables, d, d, patches, (self.prm.T_in, self.prm.T_out), self.prm.wall_u,
-                          self._step4())
+                          self._step4(), (self.prm.Tbc_in, self.prm.Tbc_out))
         if self.prm.step7:
             xch.pressure_ring(self.tables, L.p1, patches)
             xch.pressure_ring(self.tables, L.p2, patches)
@@ -197,7 +201,8 @@ class Oracle:
         fac = {}
         for loc in (C, R, TH, PH):
             nu = prm.kappa if loc == C else prm.Pr
-            fac[loc] = {d: ops.factor(g, loc, d, A, prm.dt, nu, prm.chi) for d in "rtp"}
+            gam = (xch.robin_ghost(*prm.Tbc_in, g.hr)[0], xch.robin_ghost(*prm.Tbc_out, g.hr)[0])
+            fac[loc] = {d: ops.factor(g, loc, d, A, prm.dt, nu, prm.chi, gam) for d in "rtp"}
         return fac
 
     def _one_step(self, K):
@@ -215,7 +220,8 @@ class Oracle:
         for k in range(1, K + 1):
             if prm.schwarz_mode == "additive":
                 d = it.as_dict()
-                xch.exchange_into(self.tables, d, d, (0, 1), (prm.T_in, prm.T_out), prm.wall_u, self._step4())
+                xch.exchange_into(self.tables, d, d, (0, 1), (prm.T_in, prm.T_out), prm.wall_u, self._step4(),
+                                  (prm.Tbc_in, prm.Tbc_out))
                 norms = self._iterate(it, n, A, f, fac, (0, 1))
                 if prm.step7:
                     xch.pressure_ring(self.tables, it.p1, (0, 1))
@@ -224,7 +230,8 @@ class Oracle:
                 norms = np.zeros(len(FIELD_NAMES))
                 for p in (0, 1):
                     d = it.as_dict()
-                    xch.exchange_into(self.tables, d, d, (p,), (prm.T_in, prm.T_out), prm.wall_u, self._step4())
+                    xch.exchange_into(self.tables, d, d, (p,), (prm.T_in, prm.T_out), prm.wall_u, self._step4(),
+                                      (prm.Tbc_in, prm.Tbc_out))
                     norms += self._iterate(it, n, A, f, fac, (p,)) ** 2
                     if prm.step7:
                         xch.pressure_ring(self.tables, it.p1, (p,))

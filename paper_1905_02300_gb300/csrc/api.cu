@@ -84,6 +84,9 @@ int validate(const ys_params *p) {
   if (p->schwarz_mode != YS_ADDITIVE && p->schwarz_mode != YS_MULTIPLICATIVE) return YS_EINVAL;
   if (!(p->Pr > 0.0) || !(p->Ra >= 0.0) || !(p->schwarz_tol >= 0.0)) return YS_EINVAL;
   if (p->step4 && (!(p->step4_eps > 0.0) || !(p->step4_tol >= 0.0))) return YS_EINVAL;
+  const double tb[4] = {p->Tbc_inner_a, p->Tbc_inner_b, p->Tbc_outer_a, p->Tbc_outer_b};
+  for (int w = 0; w < 2; ++w)
+    if (!(tb[2 * w] >= 0.0) || !(tb[2 * w + 1] >= 0.0) || !(tb[2 * w] + tb[2 * w + 1] > 0.0)) return YS_EINVAL;
   return YS_OK;
 }
 
@@ -421,6 +424,10 @@ void ys_default_params(ys_params *p) {
   p->step4 = 0;
   p->step4_eps = 1e-8;
   p->step4_tol = 1e-13;
+  p->Tbc_inner_a = 1.0;
+  p->Tbc_inner_b = 0.0;
+  p->Tbc_outer_a = 1.0;
+  p->Tbc_outer_b = 0.0;
 }
 
 const char *ys_strerror(int code) {
@@ -503,7 +510,8 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   make_metric(gs, G, met, pad, len);
   // deviation backgrounds of the mixed form (per radial index)
   std::vector<double> Tc(p->Nr + 2), Tlap(p->Nr, 0.0), Tdr(p->Nr, 0.0), pc(p->Nr, 0.0);
-  const bool deviation = mixed && (p->T_inner != 0.0 || p->T_outer != 0.0);
+  const bool dirichlet_T = (p->Tbc_inner_b == 0.0 && p->Tbc_outer_b == 0.0);
+  const bool deviation = mixed && dirichlet_T && (p->T_inner != 0.0 || p->T_outer != 0.0);
   if (deviation) {
     double Ac = (p->T_inner - p->T_outer) / (1.0 / p->R1 - 1.0 / p->R2);
     double Bc = p->T_inner - Ac / p->R1;
@@ -673,6 +681,10 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   S.cphi = 1.0 / (p->R1 * p->R1 * S.sin_theta1 * S.sin_theta1 * G.hp * G.hp);
   S.T_in = p->T_inner;
   S.T_out = p->T_outer;
+  {
+    const double a[2] = {p->Tbc_inner_a, p->Tbc_outer_a}, b[2] = {p->Tbc_inner_b, p->Tbc_outer_b};
+    shell_set_T_walls(S, a, b, G.hr);
+  }
   S.Tc_lap = nullptr;
   S.Tc_dr = nullptr;
   S.wall_ur = S.wall_ut = S.wall_up = nullptr;

@@ -428,8 +428,8 @@ __device__ __forceinline__ void body_walls(Shell S, State<R> s, int patch_mask, 
   s.f[F_U1R][hi] = (R)g1;
   s.f[F_U2R][hi] = (R)g1;
   if (cc) {
-    s.f[F_T][lo] = (R)(2.0 * S.T_in - (double)s.f[F_T][l0]);
-    s.f[F_T][hi] = (R)(2.0 * S.T_out - (double)s.f[F_T][h0]);
+    s.f[F_T][lo] = (R)(S.Tgam[0] * (double)s.f[F_T][l0] + S.Tdel[0] * S.T_in);
+    s.f[F_T][hi] = (R)(S.Tgam[1] * (double)s.f[F_T][h0] + S.Tdel[1] * S.T_out);
   }
   // u_theta, u_phi: reflection ghosts 2 g - x_0 about the wall velocity g
   if (j >= 1 && j < Nt && k >= 0 && k < Np) {
@@ -558,7 +558,10 @@ __device__ __forceinline__ void body_factorize(Shell S, int loc, int dir, StepAu
   const Layout &L = S.L;
   const Line ln = decode_line(L, loc, dir, bx * blockDim.x + threadIdx.x, by);
   if (!ln.valid || !((patch_mask >> ln.p) & 1)) return;
+  // cell-centred quantities in r: correction ghost = gamma x (reflection -1;
+  // the temperature's wall condition gives its own gamma)
   const bool reflect = (dir == DR) && (loc != LR);
+  const V gam0 = (loc == LC) ? (V)S.Tgam[0] : (V)-1.0, gam1 = (loc == LC) ? (V)S.Tgam[1] : (V)-1.0;
   const long step = ln.step;
   V cprev = (V)0.0;
   long q = lidx(L, ln.p, ln.i, ln.j, ln.k);
@@ -571,11 +574,11 @@ __device__ __forceinline__ void body_factorize(Shell S, int loc, int dir, StepAu
         int ii = (dir == DR) ? mm : ln.i, jj = (dir == DT) ? mm : ln.j;
         coef<V>(S, ax, loc, dir, ii, jj, q + u * step, lo[u], di[u], up[u]);
         if (mm == ln.m0) {
-          if (reflect) di[u] -= lo[u];
+          if (reflect) di[u] += gam0 * lo[u];
           lo[u] = (V)0.0;
         }
         if (mm == ln.m1 - 1) {
-          if (reflect) di[u] -= up[u];
+          if (reflect) di[u] += gam1 * up[u];
           up[u] = (V)0.0;
         }
       }

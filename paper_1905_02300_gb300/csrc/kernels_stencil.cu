@@ -55,19 +55,29 @@ __global__ void k_resid_T(Shell S, State<R> it, State<R> n, StepAux<R> ax, R *B,
 }
 
 // ----------------------------------------------------------------- residual u
+// The FP32 residuals are memory-latency bound: 32 registers let 16 CTAs (full
+// occupancy) hide the latency; FP64 ones are bound by the FP64 pipe and keep
+// the register budget they had without a bound (10 CTAs of 128 threads).
+template <typename R>
+struct ResidOcc {
+  static constexpr int kMinCtas = sizeof(R) == sizeof(float) ? 16 : 10;
+};
 
 template <typename R>
-__global__ void k_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
+__global__ void __launch_bounds__(TPB, ResidOcc<R>::kMinCtas)
+    k_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
   bd::body_resid_ur(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
 }
 
 template <typename R>
-__global__ void k_resid_ut(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
+__global__ void __launch_bounds__(TPB, ResidOcc<R>::kMinCtas)
+    k_resid_ut(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
   bd::body_resid_ut(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
 }
 
 template <typename R>
-__global__ void k_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
+__global__ void __launch_bounds__(TPB, ResidOcc<R>::kMinCtas)
+    k_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
   bd::body_resid_up(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
 }
 

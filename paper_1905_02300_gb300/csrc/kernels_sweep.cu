@@ -128,11 +128,11 @@ __global__ void k_sweep(Shell S, int loc, int dir, int final, StepAux<R> ax, R *
       double lo, di, up;
       coef_metric<double>(S, ax, loc, dir, ii, jj, q, lo, di, up);
       if (m == m0) {
-        if (reflect) di -= lo;
+        if (reflect) di += ((loc == LC) ? S.Tgam[0] : -1.0) * lo;
         lo = 0.0;
       }
       if (m == m1 - 1) {
-        if (reflect) di -= up;
+        if (reflect) di += ((loc == LC) ? S.Tgam[1] : -1.0) * up;
         up = 0.0;
       }
       double den = di - lo * cprev;
@@ -355,6 +355,9 @@ extern "C" int ys_factor_solve_static(const ys_params *prm, int loc, const doubl
   if (prm->Nr < 8 || prm->Nth < 8 || prm->Nph < 8 || prm->overlap < 1) return YS_EINVAL;
   if (prm->Nr > kStaticMaxN || prm->Nth > kStaticMaxN || prm->Nph > kStaticMaxN) return YS_EINVAL;
   if (prm->Nth <= 2 * prm->overlap + 4) return YS_EINVAL;
+  const double tb[4] = {prm->Tbc_inner_a, prm->Tbc_inner_b, prm->Tbc_outer_a, prm->Tbc_outer_b};
+  for (int w = 0; w < 2; ++w)
+    if (!(tb[2 * w] >= 0.0) || !(tb[2 * w + 1] >= 0.0) || !(tb[2 * w] + tb[2 * w + 1] > 0.0)) return YS_EINVAL;
   Layout L;
   L.Nr = prm->Nr;
   L.Nt = prm->Nth;
@@ -434,6 +437,11 @@ extern "C" int ys_factor_solve_static(const ys_params *prm, int loc, const doubl
   S.i2chi = 1.0 / (2.0 * prm->chi);
   S.iR1sq = 1.0 / (prm->R1 * prm->R1);
   S.cphi = 1.0 / (prm->R1 * prm->R1 * S.sin_theta1 * S.sin_theta1 * hp * hp);
+  {
+    // the temperature factor's wall rows follow the wall condition in prm
+    const double a[2] = {prm->Tbc_inner_a, prm->Tbc_outer_a}, b[2] = {prm->Tbc_inner_b, prm->Tbc_outer_b};
+    shell_set_T_walls(S, a, b, hr);
+  }
   shell_fill_fp64(S);
   StepAux<double> ax{};
   for (int a = 0; a < 3; ++a) ax.A[a] = Af[a];

@@ -106,6 +106,9 @@ struct Shell {
   const double *facd;
   const float *facf;
   double T_in, T_out;       // wall temperatures (of the stored temperature)
+  // temperature ghost beyond wall w: gamma[w] T_0 + delta[w] T_wall (the wall
+  // condition a T + b dT/dn = T_wall; Dirichlet: -1, 2)
+  double Tgam[2], Tdel[2];
   // deviation form (mixed precision): the stored temperature is T - T_c with
   // T_c the discrete conductive profile; its rate gets the FP64 source
   // Tc_lap[i] - a_r Tc_dr[i] (null in the FP64 form)
@@ -180,6 +183,18 @@ __host__ __device__ inline double cs<double>(const Shell &S, int c) {
 template <>
 __host__ __device__ inline float cs<float>(const Shell &S, int c) {
   return S.fcs[c];
+}
+
+// Ghost of the temperature wall condition a T + b dT/dn = T_w (inner: w = 0,
+// outer: w = 1) with T = (T_g + T_0)/2 and dT/dn = (T_g - T_0)/h_r on the wall:
+// T_g = Tgam[w] T_0 + Tdel[w] T_w.  a = 1, b = 0 is the Dirichlet reflection
+// T_g = 2 T_w - T_0.
+inline void shell_set_T_walls(Shell &S, const double a[2], const double b[2], double hr) {
+  for (int w = 0; w < 2; ++w) {
+    const double den = 0.5 * a[w] + b[w] / hr;
+    S.Tgam[w] = -(0.5 * a[w] - b[w] / hr) / den;
+    S.Tdel[w] = 1.0 / den;
+  }
 }
 
 // fill dtab / dcs / fcs / lcs from the named FP64 fields (ftab / ltab are filled by the owner)

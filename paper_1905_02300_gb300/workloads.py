@@ -337,6 +337,45 @@ class RadialHeat(Exact):
         return math.exp(-((math.pi / L) ** 2) * t)
 
 
+class RadialHeatRobin(Exact):
+    """Closed-form heat solution with T = 0 at r = R1 and the homogeneous Robin
+    condition a T + b dT/dn = 0 at r = R2 (n = e_r there; b = 1, a = 0 is
+    Neumann): T = sin(k (r - R1)) / r exp(-k^2 t), lap(g(r)/r) = g''/r, with k
+    the smallest positive root of
+      a R2 sin(k L) + b (k R2 cos(k L) - sin(k L)) = 0,  L = R2 - R1
+    (R2^2 times the condition: dT/dr = (k r cos - sin) / r^2 at r = R2).
+    u = 0, p = 0, Ra = 0: no forcing."""
+
+    name = "radial_heat_robin"
+    a, b = 0.0, 1.0
+
+    def __init__(self, R1, R2, Pr, Ra, a=0.0, b=1.0):
+        super().__init__(R1, R2, Pr, Ra)
+        self.a, self.b = a, b
+        L = R2 - R1
+        f = lambda k: a * R2 * math.sin(k * L) + b * (k * R2 * math.cos(k * L) - math.sin(k * L))
+        # bracket the first sign change above k = 0+ and bisect
+        lo, step = 1e-6, 1e-3
+        while f(lo) * f(lo + step) > 0:
+            lo += step
+        hi = lo + step
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if f(lo) * f(mid) <= 0:
+                hi = mid
+            else:
+                lo = mid
+        self.k = 0.5 * (lo + hi)
+
+    def fields(self, x, y, z, F):
+        r = F.sqrt(x * x + y * y + z * z)
+        zero = r * 0.0
+        return [zero, zero, zero], zero, F.sin((r - self.R1) * self.k) / r
+
+    def tfac(self, t):
+        return math.exp(-(self.k ** 2) * t)
+
+
 class SymmetricShell(Exact):
     """Data invariant under M(x, y, z) = (-x, z, y): a scalar f(MX) = f(X) and
     a vector v(MX) = M v(X).  Used for Yin/Yang congruence.
@@ -391,7 +430,7 @@ class LandauJet(Exact):
         return U, P, Th
 
 
-EXACT = {c.name: c for c in (TrigShell, CurlShell, RadialHeat, SymmetricShell, LandauJet)}
+EXACT = {c.name: c for c in (TrigShell, CurlShell, RadialHeat, RadialHeatRobin, SymmetricShell, LandauJet)}
 
 
 def wall_velocity(ex: Exact, spec: Spec, t: float = 0.0):

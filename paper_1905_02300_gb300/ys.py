@@ -31,7 +31,8 @@ class Params(C.Structure):
                 ("chi", C.c_double), ("overlap", C.c_int), ("precision", C.c_int),
                 ("schwarz_mode", C.c_int), ("schwarz_tol", C.c_double), ("T_inner", C.c_double),
                 ("T_outer", C.c_double), ("step7", C.c_int), ("step4", C.c_int), ("step4_eps", C.c_double),
-                ("step4_tol", C.c_double)]
+                ("step4_tol", C.c_double), ("Tbc_inner_a", C.c_double), ("Tbc_inner_b", C.c_double),
+                ("Tbc_outer_a", C.c_double), ("Tbc_outer_b", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)

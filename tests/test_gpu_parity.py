@@ -203,3 +203,30 @@ def test_full_size_space_convergence(gpu_lib):
     for k in errs[0]:
         for a, b in ((0, 1), (1, 2)):
             assert math.log2(errs[a][k] / errs[b][k]) > 1.7, (k, errs)
+
+
+@pytest.mark.parametrize("ab", [(0.0, 1.0), (1.0, 0.5)])
+def test_neumann_and_robin_temperature_walls(gpu_lib, ab):
+    """Temperature wall condition a T + b dT/dn = 0 at R2 (Neumann, Robin):
+    FP64 parity with the oracle after 10 steps of the closed-form heat
+    solution, and the mixed form within 1e-5."""
+    ys = gpu_lib
+    a, b = ab
+    N, dt = 12, 1e-3
+    spec = W.Spec(0.5, 1.0, N, N, 3 * N)
+    ex = W.RadialHeatRobin(0.5, 1.0, 1.0, 0.0, a=a, b=b)
+    f0, fm = W.sample_fields(ex, spec, 0.0), W.sample_fields(ex, spec, -dt)
+    o = Oracle(Params(R1=0.5, R2=1.0, Pr=1.0, Ra=0.0, dt=dt, Nr=N, Nth=N, Nph=3 * N, Tbc_out=(a, b)))
+    o.set_fields(0, f0["T"], f0["ur"], f0["uth"], f0["uph"], f0["p"])
+    o.set_fields(1, fm["T"], fm["ur"], fm["uth"], fm["uph"], fm["p"])
+    o.step(10, 3)
+    for prec, tol in ((ys.YS_FP64, 1e-11), (ys.YS_MIXED, 1e-5)):
+        s = ys.Solver(R1=0.5, R2=1.0, Pr=1.0, Ra=0.0, dt=dt, Nr=N, Nth=N, Nph=3 * N, precision=prec,
+                      Tbc_outer_a=a, Tbc_outer_b=b)
+        s.set_fields_dict(0, f0)
+        s.set_fields_dict(1, fm)
+        s.step(10, 3)
+        g = s.get_fields(0)["T"]
+        r = o.get_fields(0)["T"]
+        err = np.abs(g - r).max() / np.abs(r).max()
+        assert err <= tol, (prec, err)

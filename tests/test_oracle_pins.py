@@ -672,3 +672,33 @@ def test_step4_zeroes_the_boundary_mass_flux():
         u1, _, _ = parts(p)
         assert np.abs(u1 - closed).max() <= 1e-10 * np.abs(u0).max()
         assert abs(np.dot(w, u1) + c) <= 1e-6 * np.sum(np.abs(w * u0))
+
+
+@pytest.mark.parametrize("ab", [(0.0, 1.0), (1.0, 0.5)])
+def test_radial_heat_neumann_and_robin_walls_second_order(ab):
+    """Sec. 1 (Neumann and Robin walls): T = sin(k (r - R1))/r exp(-k^2 t) with
+    T = 0 at R1 and a T + b dT/dn = 0 at R2 (k the first root of the wall
+    condition) converges at second order in space and time together."""
+    a, b = ab
+    errs = []
+    for N, dt in ((12, 2e-3), (24, 5e-4)):
+        spec = W.Spec(0.5, 1.0, N, N, 3 * N)
+        ex = W.RadialHeatRobin(0.5, 1.0, 1.0, 0.0, a=a, b=b)
+        o = Oracle(Params(R1=0.5, R2=1.0, Pr=1.0, Ra=0.0, dt=dt, Nr=N, Nth=N, Nph=3 * N, Tbc_out=(a, b),
+                          schwarz_tol=1e-8))
+        f0, fm = W.sample_fields(ex, spec, 0.0), W.sample_fields(ex, spec, -dt)
+        o.set_fields(0, f0["T"], f0["ur"], f0["uth"], f0["uph"], f0["p"])
+        o.set_fields(1, fm["T"], fm["ur"], fm["uth"], fm["uph"], fm["p"])
+        o.step(int(round(0.008 / dt)), 20)
+        errs.append(_l2(spec, "c", o.get_fields(0)["T"] - W.sample_fields(ex, spec, o.t)["T"]))
+    assert math.log(errs[0] / errs[1]) / math.log(2.0) > 1.8, errs
+
+
+def test_robin_ghost_reduces_to_dirichlet_and_neumann():
+    """The wall-condition ghost: Dirichlet (1, 0) gives 2 g - x0, Neumann (0, 1)
+    gives x0 + h g (dT/dn = g)."""
+    h = 0.03
+    gam, dl = xch.robin_ghost(1.0, 0.0, h)
+    assert gam == -1.0 and dl == 2.0
+    gam, dl = xch.robin_ghost(0.0, 1.0, h)
+    assert gam == pytest.approx(1.0) and dl == pytest.approx(h)
