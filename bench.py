@@ -48,11 +48,14 @@ UNIT = "cell-updates/s"
 # storage type, FP64 words), one read of every input array and one write of
 # every output (neighbour reuse on chip; ghosts ~1/N ignored).
 #   extrapolate (per step): levels n, n-1 in (7 + 7 bulk, 2 + 2 pressures),
-#     iterate out (7 + 2) and the advecting velocity out (3)
-#   resid_T: T at both levels, the advecting velocity (3), forcing in, B out
+#     iterate out (7 + 2) and the advecting velocity out (3); then the sums
+#     of the advecting velocity around each location: a in (3), 9 sums out
+#   resid_T: T at both levels, 3 sums of the advecting velocity, forcing in,
+#     B out
 #   resid_u (average of 6): its system's 3 components at both levels, the
-#     advecting velocity (3), forcing, B out, T at both levels for u_r; the
-#     pressures entering the row: p1^n for system 1, p2^n, p1, p1^n for 2
+#     own advecting component and 2 sums of the others, forcing, B out, T at
+#     both levels for u_r; the pressures entering the row: p1^n for system 1,
+#     p2^n, p1, p1^n for 2
 #   line solves (sweep_*): rhs, the three stored factors, result = 5; a final
 #     factor also reads and writes the iterate = 6; averaged over the launches
 #     of one iteration (r: 2 of 7 final, theta: 2 of 7, phi: 3 of 7)
@@ -60,20 +63,21 @@ UNIT = "cell-updates/s"
 #     p2^n, p1, p1^n, old and new p2 (system 2)
 #   factorize: advecting component in, three factors out
 WORDS_PER_CELL = {
-    "extrapolate": (24.0, 6.0), "resid_T": (7.0, 0.0), "resid_u": (35.0 / 3, 2.0), "sweep_r": (37.0 / 7, 0.0),
+    "extrapolate": (36.0, 6.0), "resid_T": (7.0, 0.0), "resid_u": (35.0 / 3, 2.0), "sweep_r": (37.0 / 7, 0.0),
     "sweep_t": (37.0 / 7, 0.0), "sweep_p": (38.0 / 7, 0.0), "pressure": (6.0, 4.0), "factorize": (4.0, 0.0),
 }
 # FP64 operations per cell (hand count of the kernel formulas, FMA = 2, a
 # division = 1) for the FP64 form, whose kernels are bound by the FP64 pipe.
-FLOPS_PER_CELL = {"resid_T": 42.0, "resid_u": 91.0, "pressure": 21.0, "factorize": 11.0}
+# The sums of the advecting velocity are formed once per step (extrapolate
+# class) and not counted again here.
+FLOPS_PER_CELL = {"resid_T": 39.0, "resid_u": 85.0, "pressure": 21.0, "factorize": 9.0}
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of GB300 (profiling recipe)
 # DRAM bytes (read + write) per point of the top kernel class from one ncu
 # capture of its u_r launch on a smaller shell whose launch already exceeds L2
 # (traffic scales with the points processed); the bench reports it scaled to
 # one full launch.  Valid for the kernel code the capture was taken of.
 TRAFFIC_PER_POINT = {
-    (False, "resid_u"): (183.0e6 / (2 * 64 * 63 * 192), "profiles/k_resid_ur_fp64_64x64x192_full.md"),
-    (True, "resid_u"): (519.6e6 / (2 * 112 * 111 * 336), "profiles/k_resid_ur_mixed_112x112x336_full.md"),
+    (True, "resid_u"): (518.75e6 / (2 * 112 * 111 * 336), "profiles/k_resid_ur_mixed_112x112x336_full.md"),
 }
 
 

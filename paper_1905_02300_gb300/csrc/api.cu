@@ -224,8 +224,11 @@ int step_t(ys_ctx *c, int n_steps, int n_schwarz) {
   for (int st = 0; st < n_steps; ++st) {
     State<R> n = D.lev[0], nm1 = D.lev[1], it = D.lev[2];
     LAUNCH(c, K_EXTRAP, 1, Launch<R>::extrapolate(c->L, it, n, nm1, D.A, c->stream));
-    StepAux<R> ax;
+    LAUNCH(c, K_EXTRAP, 1, Launch<R>::adv_sums(c->L, D.A, D.As, c->stream));
+    StepAux<R> ax{};
     for (int a = 0; a < 3; ++a) ax.A[a] = D.A[a];
+    for (int loc = 0; loc < 4; ++loc)
+      for (int dir = 0; dir < 3; ++dir) ax.As[loc][dir] = D.As[loc][dir];
     ax.fT = ax.fr = ax.ft = ax.fp = nullptr;
     if (c->nmodes_set > 0) {
       // pointers and time weights of the modes at t_n + dt/2, passed by value
@@ -396,6 +399,8 @@ char *carve(ys_ctx *c, Fields<R> &D, char *base) {
   for (int loc = 0; loc < 4; ++loc)
     for (int dir = 0; dir < 3; ++dir)
       for (int a = 0; a < 3; ++a) D.fac[loc][dir][a] = f + (fi++) * T;
+  for (int loc = 0; loc < 4; ++loc)
+    for (int dir = 0; dir < 3; ++dir) D.As[loc][dir] = (loc == dir + 1) ? nullptr : f + (fi++) * T;
   for (int m = 0; m < kMaxModes; ++m)
     for (int a = 0; a < 4; ++a) D.modes[m][a] = nullptr;
   char *next = base + ((fi * T * sizeof(R) + 255) / 256) * 256;
@@ -405,8 +410,8 @@ char *carve(ys_ctx *c, Fields<R> &D, char *base) {
   return next + ((kPresFields * T * sizeof(double) + 255) / 256) * 256;
 }
 
-// number of bulk fields of one shell (3 x 7 levels, 3 a, 4 forcing, B, Cs, 36 factors)
-constexpr size_t kBulkFields = 3 * 7 + 3 + 4 + 2 + 36;
+// number of bulk fields of one shell (3 x 7 levels, 3 a, 4 forcing, B, Cs, 36 factors, 9 sums of a)
+constexpr size_t kBulkFields = 3 * 7 + 3 + 4 + 2 + 36 + 9;
 
 }  // namespace
 

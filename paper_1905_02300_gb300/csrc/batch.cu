@@ -84,7 +84,7 @@ __device__ __forceinline__ void roles(const ShellDev<R> &D, State<R> &n, State<R
 
 template <typename R>
 __device__ __forceinline__ StepAux<R> aux_of(const ShellDev<R> &D) {
-  StepAux<R> ax;
+  StepAux<R> ax{};  // no sum tables: the bodies form the sums of a themselves
   for (int a = 0; a < 3; ++a) ax.A[a] = D.A[a];
   ax.fT = ax.fr = ax.ft = ax.fp = nullptr;
   return ax;

@@ -144,9 +144,124 @@ __device__ __forceinline__ V Sm(const R *a, const R *b, long q) {
 // The diffusion parts keep the differenced form (S_+ - S_0) - (S_0 - S_-)
 // of the conservative three-point operator.
 
+// Lane vectors: a residual thread computes NV consecutive points along phi.
+// NV = 1 is one point per thread (any k); NV > 1 (FP32 storage, NV = 4)
+// starts at a k that is a multiple of NV, so that every row's group is one
+// 16-byte vector (rows start 32-byte aligned: k = 0 sits 8 elements into a
+// row whose pitch is a multiple of 8), and masks the lanes outside the
+// region.  Lanes outside the region still load: a group never reaches more
+// than NV + 3 elements past the last point of a row, which stays inside the
+// row's padding, the next row's leading pad, or the patch box's tail slack.
+template <int NV>
+__device__ __forceinline__ int decode_group(const Layout &L, int loc, int patch_mask, int bx, int by, int &p, int &i,
+                                            int &j, int &k) {
+  int i0, i1, j0, j1, k0, k1;
+  region(L, loc, i0, i1, j0, j1, k0, k1);
+  int nj = j1 - j0, ni = i1 - i0;
+  int row = by;
+  j = j0 + row % nj;
+  row /= nj;
+  i = i0 + row % ni;
+  p = row / ni;
+  if (!((patch_mask >> p) & 1)) return 0;
+  if constexpr (NV == 1) {
+    k = k0 + bx * blockDim.x + threadIdx.x;
+    return k < k1 ? 1 : 0;
+  } else {
+    k = NV * (bx * blockDim.x + threadIdx.x);
+    int m = 0;
+#pragma unroll
+    for (int l = 0; l < NV; ++l)
+      if (k + l >= k0 && k + l < k1) m |= 1 << l;
+    return m;
+  }
+}
+
+// o[l] = p[l]: one scalar (NV = 1) or 16-byte vector loads
+template <int NV, typename R, typename V>
+__device__ __forceinline__ void vld(const R *__restrict__ p, V (&o)[NV]) {
+  if constexpr (NV == 1) {
+    o[0] = (V)p[0];
+  } else if constexpr (sizeof(R) == 4 && NV == 2) {
+    const float2 t = *reinterpret_cast<const float2 *>(p);
+    o[0] = (V)t.x;
+    o[1] = (V)t.y;
+  } else if constexpr (sizeof(R) == 4) {
+    static_assert(NV % 4 == 0, "FP32 lane vectors are float2 or whole float4");
+#pragma unroll
+    for (int v = 0; v < NV / 4; ++v) {
+      const float4 t = *reinterpret_cast<const float4 *>(p + 4 * v);
+      o[4 * v] = (V)t.x;
+      o[4 * v + 1] = (V)t.y;
+      o[4 * v + 2] = (V)t.z;
+      o[4 * v + 3] = (V)t.w;
+    }
+  } else {
+    static_assert(NV % 2 == 0, "FP64 lane vectors are whole double2");
+#pragma unroll
+    for (int v = 0; v < NV / 2; ++v) {
+      const double2 t = *reinterpret_cast<const double2 *>(p + 2 * v);
+      o[2 * v] = (V)t.x;
+      o[2 * v + 1] = (V)t.y;
+    }
+  }
+}
+
+// o[l] = a[q + l] + b[q + l]: the two-level sums S of the stencil
+template <int NV, typename R, typename V>
+__device__ __forceinline__ void vsm(const R *__restrict__ a, const R *__restrict__ b, long q, V (&o)[NV]) {
+  V x[NV], y[NV];
+  vld<NV>(a + q, x);
+  vld<NV>(b + q, y);
+#pragma unroll
+  for (int l = 0; l < NV; ++l) o[l] = x[l] + y[l];
+}
+
+// values one position up (o[l] = value at l + 1) from the group c and the
+// value e at position NV
+template <int NV, typename V>
+__device__ __forceinline__ void vup(const V (&c)[NV], V e, V (&o)[NV]) {
+#pragma unroll
+  for (int l = 0; l + 1 < NV; ++l) o[l] = c[l + 1];
+  o[NV - 1] = e;
+}
+
+// values one position down (o[l] = value at l - 1) from the group c and the
+// value e at position -1
+template <int NV, typename V>
+__device__ __forceinline__ void vdn(const V (&c)[NV], V e, V (&o)[NV]) {
+#pragma unroll
+  for (int l = NV - 1; l > 0; --l) o[l] = c[l - 1];
+  o[0] = e;
+}
+
+// store the lanes set in `lanes` (one vector store when all are)
+template <int NV, typename R, typename V>
+__device__ __forceinline__ void vst(R *__restrict__ p, const V (&v)[NV], int lanes) {
+  if constexpr (NV == 1) {
+    p[0] = (R)v[0];
+  } else {
+    static_assert(sizeof(R) == 4 && (NV == 2 || NV == 4), "vector stores are FP32 float2 or float4");
+    if (lanes == (1 << NV) - 1) {
+      if constexpr (NV == 2)
+        *reinterpret_cast<float2 *>(p) = make_float2((float)v[0], (float)v[1]);
+      else
+        *reinterpret_cast<float4 *>(p) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+    } else {
+#pragma unroll
+      for (int l = 0; l < NV; ++l)
+        if ((lanes >> l) & 1) p[l] = (R)v[l];
+    }
+  }
+}
+
+// kTab (the single-shell launches): the sums of the advecting velocity come
+// from the per-step tables StepAux::As; otherwise (batched shells) the body
+// forms them.  Both add the same values in the same order.
+
 // temperature at cell centres: kappa Laplacian, advection, forcing, and in
 // the deviation form the conductive-profile source
-template <typename R>
+template <typename R, bool kTab = false>
 __device__ __forceinline__ void body_resid_T(Shell S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
@@ -161,9 +276,9 @@ __device__ __forceinline__ void body_resid_T(Shell S, State<R> it, State<R> n, S
   const V Spp = Sm<V>(a, b, q + 1), Spm = Sm<V>(a, b, q - 1);
   const V diff = c[T_RP] * (Srp - S0) - c[T_RM] * (S0 - Srm) + c[T_TP] * (Stp - S0) - c[T_TM] * (S0 - Stm) +
                  c[T_PP] * (Spp - (V)2.0 * S0 + Spm);
-  const V sAr = (V)ax.A[0][q] + (V)ax.A[0][q + SI];
-  const V sAt = (V)ax.A[1][q] + (V)ax.A[1][q + P];
-  const V sAp = (V)ax.A[2][q] + (V)ax.A[2][q + 1];
+  const V sAr = kTab ? (V)ax.As[LC][DR][q] : (V)ax.A[0][q] + (V)ax.A[0][q + SI];
+  const V sAt = kTab ? (V)ax.As[LC][DT][q] : (V)ax.A[1][q] + (V)ax.A[1][q + P];
+  const V sAp = kTab ? (V)ax.As[LC][DP][q] : (V)ax.A[2][q] + (V)ax.A[2][q + 1];
   const V adv = c[T_AR] * sAr * (Srp - Srm) + c[T_AT] * sAt * (Stp - Stm) + c[T_AP] * sAp * (Spp - Spm);
   V out = diff - adv;
   if (ax.fT) out += cs<V>(S, CS_DT) * (V)ax.fT[q];
@@ -180,7 +295,7 @@ __device__ __forceinline__ double pres(const State<R> &it, const State<R> &n, in
 
 // u_r at r-faces: nu (vector Laplacian), -advection (with the curvature
 // terms), -grad P, grad(div)/(2 chi), buoyancy, forcing
-template <typename R>
+template <typename R, bool kTab = false>
 __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
@@ -205,8 +320,8 @@ __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, Sta
                c[UR_GPM1] * (zm1 - zm0);
   const R *A1 = ax.A[1], *A2 = ax.A[2];
   const V ar = (V)ax.A[0][q];
-  const V sAt = ((V)A1[q - SI] + (V)A1[q - SI + P]) + (V)A1[q] + (V)A1[q + P];
-  const V sAp = ((V)A2[q - SI] + (V)A2[q - SI + 1]) + (V)A2[q] + (V)A2[q + 1];
+  const V sAt = kTab ? (V)ax.As[LR][DT][q] : ((V)A1[q - SI] + (V)A1[q - SI + P]) + (V)A1[q] + (V)A1[q + P];
+  const V sAp = kTab ? (V)ax.As[LR][DP][q] : ((V)A2[q - SI] + (V)A2[q - SI + 1]) + (V)A2[q] + (V)A2[q + 1];
   const V adv = c[UR_AR] * ar * (Srp - Srm) + c[UR_AT] * sAt * (Stp - Stm) + c[UR_AP] * sAp * (Spp - Spm);
   const V curv = c[UR_CV] * (sAt * (((ym0 + ym1) + y0) + y1) + sAp * (((zm0 + zm1) + z0) + z1));
   const V gradP = (V)(pres(it, n, sys, q) - pres(it, n, sys, q - SI)) * c[UR_GPR];
@@ -217,7 +332,7 @@ __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, Sta
 }
 
 // u_theta at theta-faces
-template <typename R>
+template <typename R, bool kTab = false>
 __device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
@@ -241,9 +356,9 @@ __device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, Sta
   const V gd = c[UT_W1] * w1 + c[UT_W0] * w0 + c[UT_WM1] * wm1 + c[UT_WM0] * wm0 + c[UT_GP1] * (z1 - z0) +
                c[UT_GPM1] * (zm1 - zm0);
   const R *A0 = ax.A[0], *A2 = ax.A[2];
-  const V sAr = ((V)A0[q - P] + (V)A0[q - P + SI]) + (V)A0[q] + (V)A0[q + SI];
+  const V sAr = kTab ? (V)ax.As[LT][DR][q] : ((V)A0[q - P] + (V)A0[q - P + SI]) + (V)A0[q] + (V)A0[q + SI];
   const V at = (V)ax.A[1][q];
-  const V sAp = ((V)A2[q - P] + (V)A2[q - P + 1]) + (V)A2[q] + (V)A2[q + 1];
+  const V sAp = kTab ? (V)ax.As[LT][DP][q] : ((V)A2[q - P] + (V)A2[q - P + 1]) + (V)A2[q] + (V)A2[q + 1];
   const V adv = c[UT_AR] * sAr * (Srp - Srm) + c[UT_AT] * at * (Stp - Stm) + c[UT_AP] * sAp * (Spp - Spm);
   const V curv = c[UT_CP] * sAp * (((zm0 + zm1) + z0) + z1) - c[UT_CW] * at * (((wm0 + wm1) + w0) + w1);
   const V gradP = (V)(pres(it, n, sys, q) - pres(it, n, sys, q - P)) * c[UT_GPR];
@@ -253,7 +368,7 @@ __device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, Sta
 }
 
 // u_phi at phi-faces
-template <typename R>
+template <typename R, bool kTab = false>
 __device__ __forceinline__ void body_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
@@ -276,8 +391,8 @@ __device__ __forceinline__ void body_resid_up(Shell S, int sys, State<R> it, Sta
   const V gd = c[UP_E0] * S0 + c[UP_W1] * w1 + c[UP_W0] * w0 + c[UP_WM1] * wm1 + c[UP_WM0] * wm0 + c[UP_Y1] * y1 +
                c[UP_Y0] * y0 + c[UP_YM1] * ym1 + c[UP_YM0] * ym0;
   const R *A0 = ax.A[0], *A1 = ax.A[1];
-  const V sAr = ((V)A0[q - 1] + (V)A0[q - 1 + SI]) + (V)A0[q] + (V)A0[q + SI];
-  const V sAt = ((V)A1[q - 1] + (V)A1[q - 1 + P]) + (V)A1[q] + (V)A1[q + P];
+  const V sAr = kTab ? (V)ax.As[LP][DR][q] : ((V)A0[q - 1] + (V)A0[q - 1 + SI]) + (V)A0[q] + (V)A0[q + SI];
+  const V sAt = kTab ? (V)ax.As[LP][DT][q] : ((V)A1[q - 1] + (V)A1[q - 1 + P]) + (V)A1[q] + (V)A1[q + P];
   const V ap = (V)ax.A[2][q];
   const V adv = c[UP_AR] * sAr * (Srp - Srm) + c[UP_AT] * sAt * (Stp - Stm) + c[UP_AP] * ap * (Spp - Spm);
   const V curv = ap * (c[UP_CW] * (((wm0 + wm1) + w0) + w1) + c[UP_CY] * (((ym0 + ym1) + y0) + y1));
@@ -285,6 +400,264 @@ __device__ __forceinline__ void body_resid_up(Shell S, int sys, State<R> it, Sta
   V out = diff + gd - adv - curv - gradP;
   if (ax.fp) out += cs<V>(S, CS_DT) * (V)ax.fp[q];
   B[q] = (R)(out - ((V)xi[q] - (V)xn[q]));
+}
+
+// The same residuals with NV consecutive points along phi per thread (FP32
+// storage): identical arithmetic per point, the stencil values gathered with
+// vector loads of the aligned group plus one scalar at each end where a
+// stencil reaches past it, and the sums of the advecting velocity read from
+// the per-step tables StepAux::As (required here).
+
+// temperature (body_resid_T)
+template <typename R, int NV>
+__device__ __forceinline__ void body_resid_T_vec(Shell S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask,
+                                             int bx, int by) {
+  using V = typename Cmp<R>::type;
+  const Layout &L = S.L;
+  int p, i, j, k;
+  const int lanes = decode_group<NV>(L, LC, patch_mask, bx, by, p, i, j, k);
+  if (!lanes) return;
+  const long q = lidx(L, p, i, j, k), SI = L.SI, P = L.P;
+  const V *c = rowc<V>(S, RT_T, i, j);
+  const R *a = it.f[F_T], *b = n.f[F_T];
+  V ta[NV], tb[NV], S0[NV], Srp[NV], Srm[NV], Stp[NV], Stm[NV], Spp[NV], Spm[NV];
+  vld<NV>(a + q, ta);
+  vld<NV>(b + q, tb);
+#pragma unroll
+  for (int l = 0; l < NV; ++l) S0[l] = ta[l] + tb[l];
+  vsm<NV>(a, b, q + SI, Srp);
+  vsm<NV>(a, b, q - SI, Srm);
+  vsm<NV>(a, b, q + P, Stp);
+  vsm<NV>(a, b, q - P, Stm);
+  vup<NV>(S0, Sm<V>(a, b, q + NV), Spp);
+  vdn<NV>(S0, Sm<V>(a, b, q - 1), Spm);
+  V sAr[NV], sAt[NV], sAp[NV], f[NV];
+  vld<NV>(ax.As[LC][DR] + q, sAr);
+  vld<NV>(ax.As[LC][DT] + q, sAt);
+  vld<NV>(ax.As[LC][DP] + q, sAp);
+  if (ax.fT) vld<NV>(ax.fT + q, f);
+  V o[NV];
+#pragma unroll
+  for (int l = 0; l < NV; ++l) {
+    const V diff = c[T_RP] * (Srp[l] - S0[l]) - c[T_RM] * (S0[l] - Srm[l]) + c[T_TP] * (Stp[l] - S0[l]) -
+                   c[T_TM] * (S0[l] - Stm[l]) + c[T_PP] * (Spp[l] - (V)2.0 * S0[l] + Spm[l]);
+    const V adv = c[T_AR] * sAr[l] * (Srp[l] - Srm[l]) + c[T_AT] * sAt[l] * (Stp[l] - Stm[l]) +
+                  c[T_AP] * sAp[l] * (Spp[l] - Spm[l]);
+    V out = diff - adv;
+    if (ax.fT) out += cs<V>(S, CS_DT) * f[l];
+    if (S.Tc_lap) out += c[T_G0] - sAr[l] * c[T_G1];
+    o[l] = out - (ta[l] - tb[l]);
+  }
+  vst<NV>(B + q, o, lanes);
+}
+
+// the same for the NV points of a group
+template <int NV, typename R>
+__device__ __forceinline__ void vpres(const State<R> &it, const State<R> &n, int sys, long q, double (&o)[NV]) {
+  if (sys == 1) {
+    vld<NV>(n.p[0] + q, o);
+    return;
+  }
+  double a[NV], b[NV], c[NV];
+  vld<NV>(n.p[1] + q, a);
+  vld<NV>(it.p[0] + q, b);
+  vld<NV>(n.p[0] + q, c);
+#pragma unroll
+  for (int l = 0; l < NV; ++l) o[l] = a[l] + 0.5 * (b[l] - c[l]);
+}
+
+// u_r (body_resid_ur)
+template <typename R, int NV>
+__device__ __forceinline__ void body_resid_ur_vec(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B,
+                                              int patch_mask, int bx, int by) {
+  using V = typename Cmp<R>::type;
+  const Layout &L = S.L;
+  int p, i, j, k;
+  const int lanes = decode_group<NV>(L, LR, patch_mask, bx, by, p, i, j, k);
+  if (!lanes) return;
+  const long q = lidx(L, p, i, j, k), SI = L.SI, P = L.P;
+  const V *c = rowc<V>(S, RT_UR, i, j);
+  const R *xi = velf(it, sys, 0), *xn = velf(n, sys, 0);
+  const R *yi = velf(it, sys, 1), *yn = velf(n, sys, 1);
+  const R *zi = velf(it, sys, 2), *zn = velf(n, sys, 2);
+  V xa[NV], xb[NV], S0[NV], Srp[NV], Srm[NV], Stp[NV], Stm[NV], Spp[NV], Spm[NV];
+  vld<NV>(xi + q, xa);
+  vld<NV>(xn + q, xb);
+#pragma unroll
+  for (int l = 0; l < NV; ++l) S0[l] = xa[l] + xb[l];
+  vsm<NV>(xi, xn, q + SI, Srp);
+  vsm<NV>(xi, xn, q - SI, Srm);
+  vsm<NV>(xi, xn, q + P, Stp);
+  vsm<NV>(xi, xn, q - P, Stm);
+  vup<NV>(S0, Sm<V>(xi, xn, q + NV), Spp);
+  vdn<NV>(S0, Sm<V>(xi, xn, q - 1), Spm);
+  // u_theta and u_phi around the face: the two cells sharing it
+  V y1[NV], y0[NV], ym1[NV], ym0[NV], z1[NV], z0[NV], zm1[NV], zm0[NV];
+  vsm<NV>(yi, yn, q + P, y1);
+  vsm<NV>(yi, yn, q, y0);
+  vsm<NV>(yi, yn, q - SI + P, ym1);
+  vsm<NV>(yi, yn, q - SI, ym0);
+  vsm<NV>(zi, zn, q, z0);
+  vup<NV>(z0, Sm<V>(zi, zn, q + NV), z1);
+  vsm<NV>(zi, zn, q - SI, zm0);
+  vup<NV>(zm0, Sm<V>(zi, zn, q - SI + NV), zm1);
+  V ar[NV], sAt[NV], sAp[NV];
+  vld<NV>(ax.A[0] + q, ar);
+  vld<NV>(ax.As[LR][DT] + q, sAt);
+  vld<NV>(ax.As[LR][DP] + q, sAp);
+  double P0[NV], Pm[NV];
+  vpres<NV>(it, n, sys, q, P0);
+  vpres<NV>(it, n, sys, q - SI, Pm);
+  V tm[NV], t0[NV], f[NV];
+  vsm<NV>(it.f[F_T], n.f[F_T], q - SI, tm);
+  vsm<NV>(it.f[F_T], n.f[F_T], q, t0);
+  if (ax.fr) vld<NV>(ax.fr + q, f);
+  V o[NV];
+#pragma unroll
+  for (int l = 0; l < NV; ++l) {
+    const V diff = c[UR_RP] * (Srp[l] - S0[l]) - c[UR_RM] * (S0[l] - Srm[l]) + c[UR_TP] * (Stp[l] - S0[l]) -
+                   c[UR_TM] * (S0[l] - Stm[l]) + c[UR_PP] * (Spp[l] - (V)2.0 * S0[l] + Spm[l]);
+    const V own = c[UR_O1] * Srp[l] + c[UR_O0] * S0[l] + c[UR_OM] * Srm[l];
+    const V gd = c[UR_GT1] * y1[l] + c[UR_GT0] * y0[l] + c[UR_GTM1] * ym1[l] + c[UR_GTM0] * ym0[l] +
+                 c[UR_GP1] * (z1[l] - z0[l]) + c[UR_GPM1] * (zm1[l] - zm0[l]);
+    const V adv = c[UR_AR] * ar[l] * (Srp[l] - Srm[l]) + c[UR_AT] * sAt[l] * (Stp[l] - Stm[l]) +
+                  c[UR_AP] * sAp[l] * (Spp[l] - Spm[l]);
+    const V curv = c[UR_CV] * (sAt[l] * (((ym0[l] + ym1[l]) + y0[l]) + y1[l]) +
+                               sAp[l] * (((zm0[l] + zm1[l]) + z0[l]) + z1[l]));
+    const V gradP = (V)(P0[l] - Pm[l]) * c[UR_GPR];
+    const V buoy = c[UR_BY] * (tm[l] + t0[l]);
+    V out = diff + own + gd - adv + curv - gradP + buoy;
+    if (ax.fr) out += cs<V>(S, CS_DT) * f[l];
+    o[l] = out - (xa[l] - xb[l]);
+  }
+  vst<NV>(B + q, o, lanes);
+}
+
+// u_theta (body_resid_ut)
+template <typename R, int NV>
+__device__ __forceinline__ void body_resid_ut_vec(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B,
+                                              int patch_mask, int bx, int by) {
+  using V = typename Cmp<R>::type;
+  const Layout &L = S.L;
+  int p, i, j, k;
+  const int lanes = decode_group<NV>(L, LT, patch_mask, bx, by, p, i, j, k);
+  if (!lanes) return;
+  const long q = lidx(L, p, i, j, k), SI = L.SI, P = L.P;
+  const V *c = rowc<V>(S, RT_UT, i, j);
+  const R *wi = velf(it, sys, 0), *wn = velf(n, sys, 0);
+  const R *xi = velf(it, sys, 1), *xn = velf(n, sys, 1);
+  const R *zi = velf(it, sys, 2), *zn = velf(n, sys, 2);
+  V xa[NV], xb[NV], S0[NV], Srp[NV], Srm[NV], Stp[NV], Stm[NV], Spp[NV], Spm[NV];
+  vld<NV>(xi + q, xa);
+  vld<NV>(xn + q, xb);
+#pragma unroll
+  for (int l = 0; l < NV; ++l) S0[l] = xa[l] + xb[l];
+  vsm<NV>(xi, xn, q + SI, Srp);
+  vsm<NV>(xi, xn, q - SI, Srm);
+  vsm<NV>(xi, xn, q + P, Stp);
+  vsm<NV>(xi, xn, q - P, Stm);
+  vup<NV>(S0, Sm<V>(xi, xn, q + NV), Spp);
+  vdn<NV>(S0, Sm<V>(xi, xn, q - 1), Spm);
+  // u_r and u_phi around the face: the two cells sharing it
+  V w1[NV], w0[NV], wm1[NV], wm0[NV], z1[NV], z0[NV], zm1[NV], zm0[NV];
+  vsm<NV>(wi, wn, q + SI, w1);
+  vsm<NV>(wi, wn, q, w0);
+  vsm<NV>(wi, wn, q + SI - P, wm1);
+  vsm<NV>(wi, wn, q - P, wm0);
+  vsm<NV>(zi, zn, q, z0);
+  vup<NV>(z0, Sm<V>(zi, zn, q + NV), z1);
+  vsm<NV>(zi, zn, q - P, zm0);
+  vup<NV>(zm0, Sm<V>(zi, zn, q - P + NV), zm1);
+  V sAr[NV], at[NV], sAp[NV];
+  vld<NV>(ax.As[LT][DR] + q, sAr);
+  vld<NV>(ax.A[1] + q, at);
+  vld<NV>(ax.As[LT][DP] + q, sAp);
+  double P0[NV], Pm[NV];
+  vpres<NV>(it, n, sys, q, P0);
+  vpres<NV>(it, n, sys, q - P, Pm);
+  V f[NV];
+  if (ax.ft) vld<NV>(ax.ft + q, f);
+  V o[NV];
+#pragma unroll
+  for (int l = 0; l < NV; ++l) {
+    const V diff = c[UT_RP] * (Srp[l] - S0[l]) - c[UT_RM] * (S0[l] - Srm[l]) + c[UT_TP] * (Stp[l] - S0[l]) -
+                   c[UT_TM] * (S0[l] - Stm[l]) + c[UT_PP] * (Spp[l] - (V)2.0 * S0[l] + Spm[l]);
+    const V own = c[UT_OTP] * Stp[l] + c[UT_O0] * S0[l] + c[UT_OTM] * Stm[l];
+    const V gd = c[UT_W1] * w1[l] + c[UT_W0] * w0[l] + c[UT_WM1] * wm1[l] + c[UT_WM0] * wm0[l] +
+                 c[UT_GP1] * (z1[l] - z0[l]) + c[UT_GPM1] * (zm1[l] - zm0[l]);
+    const V adv = c[UT_AR] * sAr[l] * (Srp[l] - Srm[l]) + c[UT_AT] * at[l] * (Stp[l] - Stm[l]) +
+                  c[UT_AP] * sAp[l] * (Spp[l] - Spm[l]);
+    const V curv = c[UT_CP] * sAp[l] * (((zm0[l] + zm1[l]) + z0[l]) + z1[l]) -
+                   c[UT_CW] * at[l] * (((wm0[l] + wm1[l]) + w0[l]) + w1[l]);
+    const V gradP = (V)(P0[l] - Pm[l]) * c[UT_GPR];
+    V out = diff + own + gd - adv + curv - gradP;
+    if (ax.ft) out += cs<V>(S, CS_DT) * f[l];
+    o[l] = out - (xa[l] - xb[l]);
+  }
+  vst<NV>(B + q, o, lanes);
+}
+
+// u_phi (body_resid_up)
+template <typename R, int NV>
+__device__ __forceinline__ void body_resid_up_vec(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B,
+                                              int patch_mask, int bx, int by) {
+  using V = typename Cmp<R>::type;
+  const Layout &L = S.L;
+  int p, i, j, k;
+  const int lanes = decode_group<NV>(L, LP, patch_mask, bx, by, p, i, j, k);
+  if (!lanes) return;
+  const long q = lidx(L, p, i, j, k), SI = L.SI, P = L.P;
+  const V *c = rowc<V>(S, RT_UP, i, j);
+  const R *wi = velf(it, sys, 0), *wn = velf(n, sys, 0);
+  const R *yi = velf(it, sys, 1), *yn = velf(n, sys, 1);
+  const R *xi = velf(it, sys, 2), *xn = velf(n, sys, 2);
+  V xa[NV], xb[NV], S0[NV], Srp[NV], Srm[NV], Stp[NV], Stm[NV], Spp[NV], Spm[NV];
+  vld<NV>(xi + q, xa);
+  vld<NV>(xn + q, xb);
+#pragma unroll
+  for (int l = 0; l < NV; ++l) S0[l] = xa[l] + xb[l];
+  vsm<NV>(xi, xn, q + SI, Srp);
+  vsm<NV>(xi, xn, q - SI, Srm);
+  vsm<NV>(xi, xn, q + P, Stp);
+  vsm<NV>(xi, xn, q - P, Stm);
+  vup<NV>(S0, Sm<V>(xi, xn, q + NV), Spp);
+  vdn<NV>(S0, Sm<V>(xi, xn, q - 1), Spm);
+  // u_r and u_theta around the face: the two cells sharing it
+  V w1[NV], w0[NV], wm1[NV], wm0[NV], y1[NV], y0[NV], ym1[NV], ym0[NV];
+  vsm<NV>(wi, wn, q + SI, w1);
+  vsm<NV>(wi, wn, q, w0);
+  vdn<NV>(w1, Sm<V>(wi, wn, q - 1 + SI), wm1);
+  vdn<NV>(w0, Sm<V>(wi, wn, q - 1), wm0);
+  vsm<NV>(yi, yn, q + P, y1);
+  vsm<NV>(yi, yn, q, y0);
+  vdn<NV>(y1, Sm<V>(yi, yn, q - 1 + P), ym1);
+  vdn<NV>(y0, Sm<V>(yi, yn, q - 1), ym0);
+  V sAr[NV], sAt[NV], ap[NV];
+  vld<NV>(ax.As[LP][DR] + q, sAr);
+  vld<NV>(ax.As[LP][DT] + q, sAt);
+  vld<NV>(ax.A[2] + q, ap);
+  double P0[NV], Pm[NV];
+  vpres<NV>(it, n, sys, q, P0);
+  vdn<NV>(P0, pres(it, n, sys, q - 1), Pm);
+  V f[NV];
+  if (ax.fp) vld<NV>(ax.fp + q, f);
+  V o[NV];
+#pragma unroll
+  for (int l = 0; l < NV; ++l) {
+    const V diff = c[UP_RP] * (Srp[l] - S0[l]) - c[UP_RM] * (S0[l] - Srm[l]) + c[UP_TP] * (Stp[l] - S0[l]) -
+                   c[UP_TM] * (S0[l] - Stm[l]) + c[UP_PP] * (Spp[l] - (V)2.0 * S0[l] + Spm[l]);
+    const V gd = c[UP_E0] * S0[l] + c[UP_W1] * w1[l] + c[UP_W0] * w0[l] + c[UP_WM1] * wm1[l] + c[UP_WM0] * wm0[l] +
+                 c[UP_Y1] * y1[l] + c[UP_Y0] * y0[l] + c[UP_YM1] * ym1[l] + c[UP_YM0] * ym0[l];
+    const V adv = c[UP_AR] * sAr[l] * (Srp[l] - Srm[l]) + c[UP_AT] * sAt[l] * (Stp[l] - Stm[l]) +
+                  c[UP_AP] * ap[l] * (Spp[l] - Spm[l]);
+    const V curv = ap[l] * (c[UP_CW] * (((wm0[l] + wm1[l]) + w0[l]) + w1[l]) +
+                            c[UP_CY] * (((ym0[l] + ym1[l]) + y0[l]) + y1[l]));
+    const V gradP = (V)(P0[l] - Pm[l]) * c[UP_GPR];
+    V out = diff + gd - adv - curv - gradP;
+    if (ax.fp) out += cs<V>(S, CS_DT) * f[l];
+    o[l] = out - (xa[l] - xb[l]);
+  }
+  vst<NV>(B + q, o, lanes);
 }
 
 // Pressure update of one cell (Eq. nst_Mass1 for system 1, Eq. ac2 for system
@@ -463,6 +836,8 @@ __device__ __forceinline__ void body_walls(Shell S, State<R> s, int patch_mask, 
 // stored values (in the arithmetic type V).
 template <typename V, typename R>
 __device__ __forceinline__ V advecting(const Shell &S, const StepAux<R> &ax, int loc, int dir, long q) {
+  // the per-step sum (the same values added in the same order) times 1/2 or 1/4
+  if (const R *t = ax.As[loc][dir]) return (V)t[q] * ((loc == LC) ? (V)0.5 : (V)0.25);
   const long SI = S.L.SI, P = S.L.P;
   if (dir == DR) {
     const R *A0 = ax.A[0];

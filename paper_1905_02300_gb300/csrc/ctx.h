@@ -30,6 +30,7 @@ struct Fields {
   R *fcomb[4];               // forcing at t_n + dt/2
   R *B, *Cs;                 // right-hand-side work field, forward-sweep scratch of the line solves
   R *fac[4][3][3];           // per-step LU factors: fac[loc][dir] = {lo, 1/pivot, c'}
+  R *As[4][3];               // per-step sums of the advecting velocity (StepAux::As)
   R *modes[kMaxModes][4];    // forcing modes
 };
 

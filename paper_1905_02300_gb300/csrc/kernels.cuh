@@ -27,6 +27,13 @@ template <typename R>
 struct StepAux {
   const R *A[3];   // a = 1.5 u2^n - 0.5 u2^{n-1} at r-, theta-, phi-faces
   const R *fT, *fr, *ft, *fp;   // forcing at t_n + dt/2 (nullptr = none)
+  // As[loc][dir]: per-step sums of the advecting component `dir` over its
+  // nearest stored values around the points of `loc` (2 values at cell
+  // centres, 4 at the other faces), summed in the order the stencils use;
+  // nullptr for a face's own component, and all nullptr where a launch
+  // forms the sums itself (batched shells, the allocation-free solve).  The
+  // FP32-storage residual kernels k_resid_* require them.
+  const R *As[4][3];
 };
 
 // Separable forcing modes, passed by value: out_c = sum_m tau[m] F[m][c].
@@ -48,6 +55,8 @@ struct Launch {
   // extrapolation: it = 2 n - nm1 (all slots), A = 1.5 n.u2 - 0.5 nm1.u2
   static void extrapolate(const Layout &L, State<R> it, State<R> n, State<R> nm1, R *A[3],
                           cudaStream_t st);
+  // the per-step sums of the advecting velocity (StepAux::As) from A
+  static void adv_sums(const Layout &L, R *const A[3], R *const As[4][3], cudaStream_t st);
   // forcing f = sum_m tau_m F_m for the four forcing fields
   static void combine_forcing(long total, Modes<R> modes, R *out[4], cudaStream_t st);
   // Schwarz exchange into the listed patches (mask bit p) of state s

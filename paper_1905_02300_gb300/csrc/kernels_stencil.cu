@@ -26,6 +26,30 @@ __global__ void k_extrapolate(long total, State<R> it, State<R> n, State<R> nm1,
     bd::body_extrapolate(c * chunk, (c + 1) * chunk < total ? (c + 1) * chunk : total, it, n, nm1, A0, A1, A2);
 }
 
+// Per-step sums of the advecting velocity around every point location
+// (StepAux::As): at cell centres the two faces of each component, at a face
+// the four nearest stored values of each other component, added in the
+// order the stencils and the line factors use, so that the tables hold the
+// same values those kernels formed themselves.  Every element q in
+// [SI, total - SI) is written (the regions of all locations lie inside it).
+template <typename R>
+__global__ void k_adv_sums(long lo, long hi, long SI, long P, const R *__restrict__ A0, const R *__restrict__ A1,
+                           const R *__restrict__ A2, R *cr, R *ct, R *cp, R *rt, R *rp, R *tr, R *tp, R *pr, R *pt) {
+  using V = typename Cmp<R>::type;
+  for (long q = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; q < hi; q += (long)gridDim.x * blockDim.x) {
+    const V a0 = (V)A0[q], a1 = (V)A1[q], a2 = (V)A2[q];
+    cr[q] = (R)(a0 + (V)A0[q + SI]);
+    ct[q] = (R)(a1 + (V)A1[q + P]);
+    cp[q] = (R)(a2 + (V)A2[q + 1]);
+    rt[q] = (R)((((V)A1[q - SI] + (V)A1[q - SI + P]) + a1) + (V)A1[q + P]);
+    rp[q] = (R)((((V)A2[q - SI] + (V)A2[q - SI + 1]) + a2) + (V)A2[q + 1]);
+    tr[q] = (R)((((V)A0[q - P] + (V)A0[q - P + SI]) + a0) + (V)A0[q + SI]);
+    tp[q] = (R)((((V)A2[q - P] + (V)A2[q - P + 1]) + a2) + (V)A2[q + 1]);
+    pr[q] = (R)((((V)A0[q - 1] + (V)A0[q - 1 + SI]) + a0) + (V)A0[q + SI]);
+    pt[q] = (R)((((V)A1[q - 1] + (V)A1[q - 1 + P]) + a1) + (V)A1[q + P]);
+  }
+}
+
 // sum over modes of tau_m(t) F_m, accumulated in the arithmetic type
 template <typename R>
 __global__ void k_combine(long total, Modes<R> M, R *o0, R *o1, R *o2, R *o3) {
@@ -48,37 +72,60 @@ __global__ void k_combine(long total, Modes<R> M, R *o0, R *o1, R *o2, R *o3) {
   }
 }
 
-// ----------------------------------------------------------------- residual T
-template <typename R>
-__global__ void k_resid_T(Shell S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
-  bd::body_resid_T(S, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
-}
+// ----------------------------------------------------------------- residuals
 
-// ----------------------------------------------------------------- residual u
-// The FP32 residuals are memory-latency bound: 32 registers let 16 CTAs (full
-// occupancy) hide the latency; FP64 ones are bound by the FP64 pipe and keep
-// the register budget they had without a bound (10 CTAs of 128 threads).
+// Points per thread along phi of a residual launch.  FP32 storage is bound by
+// memory latency: several points per thread (the *_vec bodies, vector loads)
+// put more bytes in flight per thread.  FP64 storage is bound by the FP64
+// pipe and computes one point per thread with 10 CTAs of 128 threads per SM
+// for the velocity rows (the register budget they take without a bound).
+template <typename R>
+__host__ __device__ constexpr int resid_nv() {
+  return sizeof(R) == sizeof(float) ? 4 : 1;
+}
+constexpr int kResidVecTpb = 256;  // most threads per CTA of a vector launch
 template <typename R>
 struct ResidOcc {
-  static constexpr int kMinCtas = sizeof(R) == sizeof(float) ? 16 : 10;
+  static constexpr int kTpb = resid_nv<R>() == 1 ? TPB : kResidVecTpb;
+  static constexpr int kMinCtas = resid_nv<R>() == 1 ? 10 : 2;  // vector: at most 128 registers
+  static constexpr int kTpbT = resid_nv<R>() == 1 ? 1024 : kResidVecTpb;  // 1024: no tighter bound than the default
 };
 
 template <typename R>
-__global__ void __launch_bounds__(TPB, ResidOcc<R>::kMinCtas)
+__global__ void __launch_bounds__(ResidOcc<R>::kTpbT)
+    k_resid_T(Shell S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
+  if constexpr (resid_nv<R>() == 1)
+    bd::body_resid_T<R, true>(S, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
+  else
+    bd::body_resid_T_vec<R, resid_nv<R>()>(S, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
+}
+
+// ----------------------------------------------------------------- residual u
+template <typename R>
+__global__ void __launch_bounds__(ResidOcc<R>::kTpb, ResidOcc<R>::kMinCtas)
     k_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
-  bd::body_resid_ur(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
+  if constexpr (resid_nv<R>() == 1)
+    bd::body_resid_ur<R, true>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
+  else
+    bd::body_resid_ur_vec<R, resid_nv<R>()>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
 }
 
 template <typename R>
-__global__ void __launch_bounds__(TPB, ResidOcc<R>::kMinCtas)
+__global__ void __launch_bounds__(ResidOcc<R>::kTpb, ResidOcc<R>::kMinCtas)
     k_resid_ut(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
-  bd::body_resid_ut(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
+  if constexpr (resid_nv<R>() == 1)
+    bd::body_resid_ut<R, true>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
+  else
+    bd::body_resid_ut_vec<R, resid_nv<R>()>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
 }
 
 template <typename R>
-__global__ void __launch_bounds__(TPB, ResidOcc<R>::kMinCtas)
+__global__ void __launch_bounds__(ResidOcc<R>::kTpb, ResidOcc<R>::kMinCtas)
     k_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
-  bd::body_resid_up(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
+  if constexpr (resid_nv<R>() == 1)
+    bd::body_resid_up<R, true>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
+  else
+    bd::body_resid_up_vec<R, resid_nv<R>()>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
 }
 
 // ----------------------------------------------------------------- pressure
@@ -178,6 +225,23 @@ dim3 point_grid(const Layout &L, int loc) {
   return dim3((nk + TPB - 1) / TPB, 2 * ni * nj);
 }
 
+// grid and CTA size of a residual launch over the points of `loc`, nv points
+// per thread: one CTA row per (patch, i, j) row, groups of nv along k from
+// k = 0 (aligned) covering [k0, Np)
+struct ResidLaunch {
+  dim3 grid;
+  int tpb;
+};
+ResidLaunch resid_launch(const Layout &L, int loc, int nv) {
+  if (nv == 1) return {point_grid(L, loc), TPB};
+  const int ni = L.Nr - (loc == LR ? 1 : 0);
+  const int nj = L.Nt - (loc == LT ? 1 : 0);
+  const int groups = (L.Np + nv - 1) / nv;
+  int tpb = (groups + 31) / 32 * 32;
+  if (tpb > kResidVecTpb) tpb = kResidVecTpb;
+  return {dim3((groups + tpb - 1) / tpb, 2 * ni * nj), tpb};
+}
+
 int flat_blocks(long n) {
   long b = (n + 255) / 256;
   return (int)(b < 152L * 16 ? b : 152L * 16);
@@ -193,24 +257,33 @@ void Launch<R>::extrapolate(const Layout &L, State<R> it, State<R> n, State<R> n
 }
 
 template <typename R>
+void Launch<R>::adv_sums(const Layout &L, R *const A[3], R *const As[4][3], cudaStream_t st) {
+  k_adv_sums<R><<<flat_blocks(L.total), 256, 0, st>>>(L.SI, L.total - L.SI, L.SI, L.P, A[0], A[1], A[2], As[LC][DR],
+                                                       As[LC][DT], As[LC][DP], As[LR][DT], As[LR][DP], As[LT][DR],
+                                                       As[LT][DP], As[LP][DR], As[LP][DT]);
+}
+
+template <typename R>
 void Launch<R>::combine_forcing(long total, Modes<R> modes, R *out[4], cudaStream_t st) {
   k_combine<R><<<flat_blocks(total), 256, 0, st>>>(total, modes, out[0], out[1], out[2], out[3]);
 }
 
 template <typename R>
 void Launch<R>::resid_T(const Shell &S, State<R> it, State<R> n, StepAux<R> ax, R *B, int pm, cudaStream_t st) {
-  k_resid_T<R><<<point_grid(S.L, LC), TPB, 0, st>>>(S, it, n, ax, B, pm);
+  const ResidLaunch g = resid_launch(S.L, LC, resid_nv<R>());
+  k_resid_T<R><<<g.grid, g.tpb, 0, st>>>(S, it, n, ax, B, pm);
 }
 
 template <typename R>
 void Launch<R>::resid_u(const Shell &S, int sys, int comp, State<R> it, State<R> n, StepAux<R> ax, R *B, int pm,
                         cudaStream_t st) {
+  const ResidLaunch g = resid_launch(S.L, LR + comp, resid_nv<R>());
   if (comp == 0)
-    k_resid_ur<R><<<point_grid(S.L, LR), TPB, 0, st>>>(S, sys, it, n, ax, B, pm);
+    k_resid_ur<R><<<g.grid, g.tpb, 0, st>>>(S, sys, it, n, ax, B, pm);
   else if (comp == 1)
-    k_resid_ut<R><<<point_grid(S.L, LT), TPB, 0, st>>>(S, sys, it, n, ax, B, pm);
+    k_resid_ut<R><<<g.grid, g.tpb, 0, st>>>(S, sys, it, n, ax, B, pm);
   else
-    k_resid_up<R><<<point_grid(S.L, LP), TPB, 0, st>>>(S, sys, it, n, ax, B, pm);
+    k_resid_up<R><<<g.grid, g.tpb, 0, st>>>(S, sys, it, n, ax, B, pm);
 }
 
 template <typename R>
@@ -243,6 +316,7 @@ void pack_p(const Layout &L, const double *src, double *dst, const double *bg, c
 #define YS_INST_STENCIL(R)                                                                                         \
   template void Launch<R>::extrapolate(const Layout &, State<R>, State<R>, State<R>, R *[3], cudaStream_t);       \
   template void Launch<R>::combine_forcing(long, Modes<R>, R *[4], cudaStream_t);                                  \
+  template void Launch<R>::adv_sums(const Layout &, R *const[3], R *const[4][3], cudaStream_t);                   \
   template void Launch<R>::resid_T(const Shell &, State<R>, State<R>, StepAux<R>, R *, int, cudaStream_t);        \
   template void Launch<R>::resid_u(const Shell &, int, int, State<R>, State<R>, StepAux<R>, R *, int,             \
                                    cudaStream_t);                                                                  \
