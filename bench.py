@@ -77,6 +77,7 @@ FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of GB300 (profiling recipe)
 # (traffic scales with the points processed); the bench reports it scaled to
 # one full launch.  Valid for the kernel code the capture was taken of.
 TRAFFIC_PER_POINT = {
+    (False, "resid_u"): (183.26e6 / (2 * 64 * 63 * 192), "profiles/k_resid_ur_fp64_64x64x192_full.md"),
     (True, "resid_u"): (518.75e6 / (2 * 112 * 111 * 336), "profiles/k_resid_ur_mixed_112x112x336_full.md"),
 }
 

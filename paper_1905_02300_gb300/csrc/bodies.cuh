@@ -993,19 +993,26 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
     const long step = ln.step;
     const long q0 = lidx(L, ln.p, ln.i, ln.j, ln.k);
     const int n = ln.m1 - ln.m0;
-    // forward elimination: B -> W
+    // forward elimination: B -> W; the loads of the next chunk are issued
+    // before the current chunk is eliminated, so that they are in flight
+    // during its dependent arithmetic and stores
     V d = (V)0.0;
-    for (int m = 0; m < n; m += U) {
-      V b[U], lo[U], iv[U];
+    V b[U], lo[U], iv[U];
+    auto load_fwd = [&](int m, V (&bb)[U], V (&ll)[U], V (&ii)[U]) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        long qq = q0 + (long)(m + u) * step;
+        const long qq = q0 + (long)(m + u) * step;
         if (m + u < n) {
-          b[u] = (V)B[qq];
-          lo[u] = (V)Lo[qq];
-          iv[u] = (V)Iv[qq];
+          bb[u] = (V)B[qq];
+          ll[u] = (V)Lo[qq];
+          ii[u] = (V)Iv[qq];
         }
       }
+    };
+    load_fwd(0, b, lo, iv);
+    for (int m = 0; m < n; m += U) {
+      V nb[U], nlo[U], niv[U];
+      if (m + U < n) load_fwd(m + U, nb, nlo, niv);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (m + u < n) {
@@ -1013,23 +1020,34 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
           W[q0 + (long)(m + u) * step] = (R)d;
         }
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        b[u] = nb[u];
+        lo[u] = nlo[u];
+        iv[u] = niv[u];
+      }
     }
     // back substitution: W -> B or the iterate, last row first; the final
     // factor sums w x^2 along the line in V, w the metric factor that varies
     // along it (r^2, sin(theta) or 1), and scales once by the constant rest
     V x = d;
     V acc = (V)0.0;
-    for (int m = n - 1; m >= 0; m -= U) {
-      V w[U], c[U], o[U];
+    V w[U], c[U], o[U];
+    auto load_bwd = [&](int m, V (&ww)[U], V (&cc)[U], V (&oo)[U]) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        long qq = q0 + (long)(m - u) * step;
+        const long qq = q0 + (long)(m - u) * step;
         if (m - u >= 0) {
-          w[u] = (V)W[qq];
-          c[u] = (V)Cp[qq];
-          o[u] = final ? (V)dst[qq] : (V)0.0;
+          ww[u] = (V)W[qq];
+          cc[u] = (V)Cp[qq];
+          oo[u] = final ? (V)dst[qq] : (V)0.0;
         }
       }
+    };
+    load_bwd(n - 1, w, c, o);
+    for (int m = n - 1; m >= 0; m -= U) {
+      V nw[U], nc[U], no[U];
+      if (m - U >= 0) load_bwd(m - U, nw, nc, no);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         int mm = m - u;
@@ -1051,6 +1069,12 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
             B[qq] = (R)x;
           }
         }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        w[u] = nw[u];
+        c[u] = nc[u];
+        o[u] = no[u];
       }
     }
     if (final) {

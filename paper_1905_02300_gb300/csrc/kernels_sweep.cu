@@ -453,5 +453,3 @@ extern "C" int ys_factor_solve_static(const ys_params *prm, int loc, const doubl
   k_static_pack<<<256, 256, 0, st>>>(L, loc, B, x);
   return cudaGetLastError() == cudaSuccess ? YS_OK : YS_ECUDA;
 }
-
-
