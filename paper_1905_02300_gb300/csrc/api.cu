@@ -94,40 +94,46 @@ size_t user_elems(const Layout &L, int loc) {
   return 2ul * (L.Nr + (loc == LR)) * (L.Nt + (loc == LT)) * (L.Np + (loc == LP));
 }
 
+// user array -> staging buffer -> padded field(s): one host-to-device copy,
+// unpacked into dst and, when dst2 is given, into dst2 as well (the two
+// velocity systems and the two pressures start from the same values)
 template <typename R>
-int copy_in(ys_ctx *c, int loc, const double *src, R *dst, const double *bg, bool device_src) {
+int copy_in(ys_ctx *c, int loc, const double *src, R *dst, const double *bg, bool device_src, R *dst2 = nullptr) {
   size_t n = user_elems(c->L, loc);
   cudaError_t e = cudaMemcpyAsync(c->stage, src, n * sizeof(double),
                                   device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return YS_ECUDA;
   LAUNCH(c, K_PACK, 1, Launch<R>::unpack(c->L, loc, c->stage, dst, bg, c->stream));
+  if (dst2) LAUNCH(c, K_PACK, 1, Launch<R>::unpack(c->L, loc, c->stage, dst2, bg, c->stream));
   return YS_OK;
 }
 
-int copy_in_p(ys_ctx *c, const double *src, double *dst, bool device_src) {
+int copy_in_p(ys_ctx *c, const double *src, double *dst, bool device_src, double *dst2 = nullptr) {
   size_t n = user_elems(c->L, LC);
   cudaError_t e = cudaMemcpyAsync(c->stage, src, n * sizeof(double),
                                   device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return YS_ECUDA;
   LAUNCH(c, K_PACK, 1, unpack_p(c->L, c->stage, dst, c->p_bg, c->stream));
+  if (dst2) LAUNCH(c, K_PACK, 1, unpack_p(c->L, c->stage, dst2, c->p_bg, c->stream));
   return YS_OK;
 }
 
+// padded field -> staging buffer -> user array; queued on the context's
+// stream (the staging buffer is reused in stream order), the caller
+// synchronises once after the last field
 template <typename R>
 int copy_out(ys_ctx *c, int loc, const R *src, double *dst, const double *bg) {
   size_t n = user_elems(c->L, loc);
   LAUNCH(c, K_PACK, 1, Launch<R>::pack(c->L, loc, src, c->stage, bg, c->stream));
   cudaError_t e = cudaMemcpyAsync(dst, c->stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-  if (e != cudaSuccess) return YS_ECUDA;
-  return cuda_ok(cudaStreamSynchronize(c->stream));
+  return e == cudaSuccess ? YS_OK : YS_ECUDA;
 }
 
 int copy_out_p(ys_ctx *c, const double *src, double *dst) {
   size_t n = user_elems(c->L, LC);
   LAUNCH(c, K_PACK, 1, pack_p(c->L, src, c->stage, c->p_bg, c->stream));
   cudaError_t e = cudaMemcpyAsync(dst, c->stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-  if (e != cudaSuccess) return YS_ECUDA;
-  return cuda_ok(cudaStreamSynchronize(c->stream));
+  return e == cudaSuccess ? YS_OK : YS_ECUDA;
 }
 
 // exchange + walls (+ pressure ring) of a whole state: boundary values as
@@ -305,11 +311,9 @@ int set_fields_t(ys_ctx *c, int level, const double *T, const double *ur, const 
   int rc = 0;
   rc |= copy_in<R>(c, LC, T, s.f[F_T], c->T_bg, dev);
   const double *u[3] = {ur, uth, uph};
-  for (int m = 0; m < 3; ++m) {
-    rc |= copy_in<R>(c, LR + m, u[m], s.f[F_U2R + m], nullptr, dev);
-    if (!aux) rc |= copy_in<R>(c, LR + m, u[m], s.f[F_U1R + m], nullptr, dev);
-  }
-  rc |= copy_in_p(c, p, s.p[1], dev);
+  for (int m = 0; m < 3; ++m)
+    rc |= copy_in<R>(c, LR + m, u[m], s.f[F_U2R + m], nullptr, dev, aux ? nullptr : s.f[F_U1R + m]);
+  rc |= copy_in_p(c, p, s.p[1], dev, aux ? nullptr : s.p[0]);
   if (aux) {
     size_t o = 0;
     for (int m = 0; m < 3; ++m) {
@@ -317,8 +321,6 @@ int set_fields_t(ys_ctx *c, int level, const double *T, const double *ur, const 
       o += user_elems(L, LR + m);
     }
     rc |= copy_in_p(c, aux + o, s.p[0], dev);
-  } else {
-    rc |= copy_in_p(c, p, s.p[0], dev);
   }
   if (rc) return YS_ECUDA;
   refresh<R>(c, s, 3);
@@ -351,7 +353,8 @@ int get_fields_t(ys_ctx *c, int level, double *T, double *ur, double *uth, doubl
     }
     rc |= copy_out_p(c, s.p[0], aux + o);
   }
-  return rc ? YS_ECUDA : YS_OK;
+  if (rc) return YS_ECUDA;
+  return cuda_ok(cudaStreamSynchronize(c->stream));
 }
 
 template <typename R>

@@ -834,10 +834,15 @@ __device__ __forceinline__ void body_walls(Shell S, State<R> s, int patch_mask, 
 // Component along `dir` of the advecting velocity at a point of location
 // `loc`: the own component as stored, the others averaged from their nearest
 // stored values (in the arithmetic type V).
-template <typename V, typename R>
+// kTab: the other components come from the per-step sums StepAux::As (the
+// same values added in the same order, times 1/2 or 1/4); without it (the
+// batched launches, whose StepAux is built at run time, where indexing its
+// table array would put it in local memory) they are averaged here.
+template <typename V, bool kTab = false, typename R>
 __device__ __forceinline__ V advecting(const Shell &S, const StepAux<R> &ax, int loc, int dir, long q) {
-  // the per-step sum (the same values added in the same order) times 1/2 or 1/4
-  if (const R *t = ax.As[loc][dir]) return (V)t[q] * ((loc == LC) ? (V)0.5 : (V)0.25);
+  if constexpr (kTab) {
+    if (loc != dir + 1) return (V)ax.As[loc][dir][q] * ((loc == LC) ? (V)0.5 : (V)0.25);
+  }
   const long SI = S.L.SI, P = S.L.P;
   if (dir == DR) {
     const R *A0 = ax.A[0];
@@ -863,11 +868,11 @@ __device__ __forceinline__ V advecting(const Shell &S, const StepAux<R> &ax, int
 // Coefficients (lo, di, up) of (I - dt/2 Ahat_dir) at point (i, j, k) of
 // `loc`: the row's static parts (FacCoef table, formed on the host in FP64)
 // and the advecting velocity at the point.
-template <typename V, typename R>
+template <typename V, bool kTab = false, typename R>
 __device__ __forceinline__ void coef(const Shell &S, const StepAux<R> &ax, int loc, int dir, int i, int j, long q,
                                      V &lo, V &di, V &up) {
   const V *c = facc<V>(S, loc, dir, i, j);
-  const V a = advecting<V>(S, ax, loc, dir, q);
+  const V a = advecting<V, kTab>(S, ax, loc, dir, q);
   lo = c[FC_L0] + a * c[FC_LA];
   di = c[FC_D0];
   up = c[FC_U0] - a * c[FC_LA];
@@ -923,7 +928,37 @@ __device__ __forceinline__ Line decode_line(const Layout &L, int loc, int dir, i
 }
 
 
-template <typename R>
+// Coefficients (lo, di, up) of the rows [m, m + U) of a line, with the wall
+// rows closed (reflection ghosts folded into the diagonal, the outside
+// coupling zeroed).
+template <int U, bool kTab, typename V, typename R>
+__device__ __forceinline__ void factor_coefs(const Shell &S, const StepAux<R> &ax, const Line &ln, int loc, int dir,
+                                             bool reflect, V gam0, V gam1, long step, int m, long qm, V (&lo)[U],
+                                             V (&di)[U], V (&up)[U]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int mm = m + u;
+    if (mm < ln.m1) {
+      const int ii = (dir == DR) ? mm : ln.i, jj = (dir == DT) ? mm : ln.j;
+      coef<V, kTab>(S, ax, loc, dir, ii, jj, qm + u * step, lo[u], di[u], up[u]);
+      if (mm == ln.m0) {
+        if (reflect) di[u] += gam0 * lo[u];
+        lo[u] = (V)0.0;
+      }
+      if (mm == ln.m1 - 1) {
+        if (reflect) di[u] += gam1 * up[u];
+        up[u] = (V)0.0;
+      }
+    }
+  }
+}
+
+// kTab (the single-shell launches): the advecting velocity comes from the
+// per-step sums; the batched launches average it themselves.  (Forming the
+// next chunk's coefficients before the current chunk's recurrence, as the
+// solves prefetch, made the factorisations slower: 42 -> 48 ms FP64,
+// 12 -> 19 ms mixed per 10 steps at 128x128x384.)
+template <typename R, bool kTab = false>
 __device__ __forceinline__ void body_factorize(Shell S, int loc, int dir, StepAux<R> ax, R *__restrict__ Lo,
                                                R *__restrict__ Iv, R *__restrict__ Cp, int patch_mask, int bx,
                                                int by) {
@@ -942,22 +977,7 @@ __device__ __forceinline__ void body_factorize(Shell S, int loc, int dir, StepAu
   long q = lidx(L, ln.p, ln.i, ln.j, ln.k);
   for (int m = ln.m0; m < ln.m1; m += U, q += U * step) {
     V lo[U], di[U], up[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      int mm = m + u;
-      if (mm < ln.m1) {
-        int ii = (dir == DR) ? mm : ln.i, jj = (dir == DT) ? mm : ln.j;
-        coef<V>(S, ax, loc, dir, ii, jj, q + u * step, lo[u], di[u], up[u]);
-        if (mm == ln.m0) {
-          if (reflect) di[u] += gam0 * lo[u];
-          lo[u] = (V)0.0;
-        }
-        if (mm == ln.m1 - 1) {
-          if (reflect) di[u] += gam1 * up[u];
-          up[u] = (V)0.0;
-        }
-      }
-    }
+    factor_coefs<U, kTab>(S, ax, ln, loc, dir, reflect, gam0, gam1, step, m, q, lo, di, up);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (m + u < ln.m1) {
@@ -972,6 +992,39 @@ __device__ __forceinline__ void body_factorize(Shell S, int loc, int dir, StepAu
   }
 }
 
+// Loads of one chunk of a line solve: forward rows [m, m + U) of b, lo and
+// 1/pivot; backward rows m, m - 1, ..., m - U + 1 of d', c' and (final
+// factor) the iterate.  Issued for the next chunk before the current one is
+// processed.
+template <int U, typename R, typename V>
+__device__ __forceinline__ void solve_load_fwd(const R *__restrict__ B, const R *__restrict__ Lo,
+                                               const R *__restrict__ Iv, long q0, long step, int n, int m,
+                                               V (&b)[U], V (&lo)[U], V (&iv)[U]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const long qq = q0 + (long)(m + u) * step;
+    if (m + u < n) {
+      b[u] = (V)B[qq];
+      lo[u] = (V)Lo[qq];
+      iv[u] = (V)Iv[qq];
+    }
+  }
+}
+template <int U, typename R, typename V>
+__device__ __forceinline__ void solve_load_bwd(const R *__restrict__ W, const R *__restrict__ Cp,
+                                               const R *__restrict__ dst, int final, long q0, long step, int m,
+                                               V (&w)[U], V (&c)[U], V (&o)[U]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const long qq = q0 + (long)(m - u) * step;
+    if (m - u >= 0) {
+      w[u] = (V)W[qq];
+      c[u] = (V)Cp[qq];
+      o[u] = final ? (V)dst[qq] : (V)0.0;
+    }
+  }
+}
+
 // Thomas solve with a stored factorisation: forward d'_m = (b_m - lo_m d'_{m-1})
 // / pivot_m into the scratch W, back x_m = d'_m - c'_m x_{m+1}.  Rows are
 // handled in register chunks of U: the loads of a chunk are independent of
@@ -979,7 +1032,7 @@ __device__ __forceinline__ void body_factorize(Shell S, int loc, int dir, StepAu
 // together.  Non-final factors write x to B (the next factor's right-hand
 // side); the final factor of an unknown adds x to the iterate and accumulates
 // the FP64 midpoint-rule norm of the increment (Sec. 5.1).
-template <typename R>
+template <typename R, bool kPf = false>
 __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final, const R *__restrict__ Lo,
                                            const R *__restrict__ Iv, const R *__restrict__ Cp, R *__restrict__ B,
                                            R *__restrict__ W, R *__restrict__ dst, double *norm, int slot,
@@ -993,26 +1046,20 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
     const long step = ln.step;
     const long q0 = lidx(L, ln.p, ln.i, ln.j, ln.k);
     const int n = ln.m1 - ln.m0;
-    // forward elimination: B -> W; the loads of the next chunk are issued
-    // before the current chunk is eliminated, so that they are in flight
-    // during its dependent arithmetic and stores
+    // forward elimination: B -> W; with kPf the loads of the next chunk are
+    // issued before the current chunk is eliminated, so that they are in
+    // flight during its dependent arithmetic and stores (the single-shell
+    // launches; the batched ones, short of registers, load chunk by chunk)
     V d = (V)0.0;
     V b[U], lo[U], iv[U];
-    auto load_fwd = [&](int m, V (&bb)[U], V (&ll)[U], V (&ii)[U]) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const long qq = q0 + (long)(m + u) * step;
-        if (m + u < n) {
-          bb[u] = (V)B[qq];
-          ll[u] = (V)Lo[qq];
-          ii[u] = (V)Iv[qq];
-        }
-      }
-    };
-    load_fwd(0, b, lo, iv);
+    if constexpr (kPf) solve_load_fwd<U>(B, Lo, Iv, q0, step, n, 0, b, lo, iv);
     for (int m = 0; m < n; m += U) {
       V nb[U], nlo[U], niv[U];
-      if (m + U < n) load_fwd(m + U, nb, nlo, niv);
+      if constexpr (kPf) {
+        if (m + U < n) solve_load_fwd<U>(B, Lo, Iv, q0, step, n, m + U, nb, nlo, niv);
+      } else {
+        solve_load_fwd<U>(B, Lo, Iv, q0, step, n, m, b, lo, iv);
+      }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (m + u < n) {
@@ -1020,11 +1067,13 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
           W[q0 + (long)(m + u) * step] = (R)d;
         }
       }
+      if constexpr (kPf) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        b[u] = nb[u];
-        lo[u] = nlo[u];
-        iv[u] = niv[u];
+        for (int u = 0; u < U; ++u) {
+          b[u] = nb[u];
+          lo[u] = nlo[u];
+          iv[u] = niv[u];
+        }
       }
     }
     // back substitution: W -> B or the iterate, last row first; the final
@@ -1033,21 +1082,14 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
     V x = d;
     V acc = (V)0.0;
     V w[U], c[U], o[U];
-    auto load_bwd = [&](int m, V (&ww)[U], V (&cc)[U], V (&oo)[U]) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const long qq = q0 + (long)(m - u) * step;
-        if (m - u >= 0) {
-          ww[u] = (V)W[qq];
-          cc[u] = (V)Cp[qq];
-          oo[u] = final ? (V)dst[qq] : (V)0.0;
-        }
-      }
-    };
-    load_bwd(n - 1, w, c, o);
+    if constexpr (kPf) solve_load_bwd<U>(W, Cp, dst, final, q0, step, n - 1, w, c, o);
     for (int m = n - 1; m >= 0; m -= U) {
       V nw[U], nc[U], no[U];
-      if (m - U >= 0) load_bwd(m - U, nw, nc, no);
+      if constexpr (kPf) {
+        if (m - U >= 0) solve_load_bwd<U>(W, Cp, dst, final, q0, step, m - U, nw, nc, no);
+      } else {
+        solve_load_bwd<U>(W, Cp, dst, final, q0, step, m, w, c, o);
+      }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         int mm = m - u;
@@ -1070,11 +1112,13 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
           }
         }
       }
+      if constexpr (kPf) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        w[u] = nw[u];
-        c[u] = nc[u];
-        o[u] = no[u];
+        for (int u = 0; u < U; ++u) {
+          w[u] = nw[u];
+          c[u] = nc[u];
+          o[u] = no[u];
+        }
       }
     }
     if (final) {
@@ -1372,7 +1416,7 @@ __device__ __forceinline__ void mat_rescale(V &a, V &b, V &c, V &d) {
   }
 }
 
-template <int EC, typename R>
+template <int EC, bool kTab, typename R>
 __device__ __forceinline__ void factor_line_scan(const Shell &S, const StepAux<R> &ax, int loc, int i, int j,
                                                  long q, int k0, int k1, R *__restrict__ Lo, R *__restrict__ Iv,
                                                  R *__restrict__ Cp) {
@@ -1392,7 +1436,7 @@ __device__ __forceinline__ void factor_line_scan(const Shell &S, const StepAux<R
 #pragma unroll
     for (int e = 0; e < EC; ++e) {
       const int kk = k + e;
-      a[e] = (kk >= k0 && kk < k1) ? advecting<V>(S, ax, loc, DP, q + kk) : (V)0.0;
+      a[e] = (kk >= k0 && kk < k1) ? advecting<V, kTab>(S, ax, loc, DP, q + kk) : (V)0.0;
     }
     auto lo_of = [&](int e) -> V {
       const int kk = k + e;
@@ -1460,7 +1504,7 @@ __device__ __forceinline__ void factor_line_scan(const Shell &S, const StepAux<R
   }
 }
 
-template <typename R>
+template <typename R, bool kTab = false>
 __device__ __forceinline__ void body_factorize_phi_scan(Shell S, int loc, StepAux<R> ax, R *__restrict__ Lo,
                                                         R *__restrict__ Iv, R *__restrict__ Cp, int patch_mask,
                                                         int bx) {
@@ -1477,13 +1521,13 @@ __device__ __forceinline__ void body_factorize_phi_scan(Shell S, int loc, StepAu
   const long q = lidx(L, p, i, j, 0);
   switch (scan_ec(L.Np)) {
     case 4:
-      factor_line_scan<4>(S, ax, loc, i, j, q, k0, L.Np, Lo, Iv, Cp);
+      factor_line_scan<4, kTab>(S, ax, loc, i, j, q, k0, L.Np, Lo, Iv, Cp);
       break;
     case 8:
-      factor_line_scan<8>(S, ax, loc, i, j, q, k0, L.Np, Lo, Iv, Cp);
+      factor_line_scan<8, kTab>(S, ax, loc, i, j, q, k0, L.Np, Lo, Iv, Cp);
       break;
     default:
-      factor_line_scan<12>(S, ax, loc, i, j, q, k0, L.Np, Lo, Iv, Cp);
+      factor_line_scan<12, kTab>(S, ax, loc, i, j, q, k0, L.Np, Lo, Iv, Cp);
       break;
   }
 }

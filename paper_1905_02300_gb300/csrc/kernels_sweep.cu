@@ -174,7 +174,7 @@ __global__ void k_sweep(Shell S, int loc, int dir, int final, StepAux<R> ax, R *
 // 1/(di_m - lo_m c'_{m-1}) and c'_m = up_m / pivot_m.
 template <typename R>
 __global__ void k_factorize(Shell S, int loc, int dir, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask) {
-  bd::body_factorize(S, loc, dir, ax, Lo, Iv, Cp, patch_mask, blockIdx.x, blockIdx.y);
+  bd::body_factorize<R, true>(S, loc, dir, ax, Lo, Iv, Cp, patch_mask, blockIdx.x, blockIdx.y);
 }
 
 // Thomas solve with a stored factorisation: forward d'_m = (b_m - lo_m d'_{m-1})
@@ -184,7 +184,7 @@ __global__ void k_factorize(Shell S, int loc, int dir, StepAux<R> ax, R *Lo, R *
 template <typename R>
 __global__ void k_solve(Shell S, int loc, int dir, int final, const R *__restrict__ Lo, const R *__restrict__ Iv,
                         const R *__restrict__ Cp, R *B, R *W, R *dst, double *norm, int slot, int patch_mask) {
-  bd::body_solve(S, loc, dir, final, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, blockIdx.x, blockIdx.y);
+  bd::body_solve<R, true>(S, loc, dir, final, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, blockIdx.x, blockIdx.y);
 }
 
 dim3 line_grid(const Layout &L, int loc, int dir) {
@@ -200,7 +200,7 @@ dim3 line_grid(const Layout &L, int loc, int dir) {
 
 template <typename R>
 __global__ void k_factorize_phi(Shell S, int loc, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask) {
-  bd::body_factorize_phi_scan(S, loc, ax, Lo, Iv, Cp, patch_mask, blockIdx.x);
+  bd::body_factorize_phi_scan<R, true>(S, loc, ax, Lo, Iv, Cp, patch_mask, blockIdx.x);
 }
 
 template <typename R>
