@@ -54,7 +54,8 @@ struct WorkMap {
 enum MapId {
   M_EXTRAP = 0, M_EX0, M_EX1, M_EX2, M_EX3, M_WALLS, M_RING, M_RC, M_RR, M_RT, M_RP, M_LINE0,
   M_PSC0 = M_LINE0 + 12,   // warp-scan phi factorisations and solves (one line per warp), per unknown type
-  M_NUM = M_PSC0 + 4
+  M_VEC0 = M_PSC0 + 4,     // FP32 residuals, 4 phi-points per thread over flat groups, per unknown type
+  M_NUM = M_VEC0 + 4
 };
 
 namespace {
@@ -157,6 +158,30 @@ __global__ void kb_resid_T(const ShellDev<R> *sh, WorkMap map, int cap) {
   }
 }
 
+// FP32 storage: the residuals with 4 phi-points per thread (16-byte loads)
+// over each shell's groups taken as one flat range; the sums of the advecting
+// velocity are formed in the body (no per-step tables in a batch).
+constexpr int kVecNV = 4;
+template <typename R>
+__global__ void __launch_bounds__(128, 4) kb_resid_T_vec(const ShellDev<R> *sh, WorkMap map, int cap) {
+  YS_BATCH_LOOP(map, cap)
+  bd::body_resid_T_vec<R, kVecNV, false, true>(D.S, it, n, aux_of(D), D.B, 3, bx, by);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128, 4)
+    kb_resid_u_vec(const ShellDev<R> *sh, WorkMap map, int cap, int sys, int comp) {
+  YS_BATCH_LOOP(map, cap)
+  if (comp == 0)
+    bd::body_resid_ur_vec<R, kVecNV, false, true>(D.S, sys, it, n, aux_of(D), D.B, 3, bx, by);
+  else if (comp == 1)
+    bd::body_resid_ut_vec<R, kVecNV, false, true>(D.S, sys, it, n, aux_of(D), D.B, 3, bx, by);
+  else
+    bd::body_resid_up_vec<R, kVecNV, false, true>(D.S, sys, it, n, aux_of(D), D.B, 3, bx, by);
+  }
+}
+
 template <typename R>
 __global__ void kb_resid_u(const ShellDev<R> *sh, WorkMap map, int cap, int sys, int comp) {
   YS_BATCH_LOOP(map, cap)
@@ -232,6 +257,10 @@ void grid_of(const ys_ctx *c, int map, int tpb_line, int &gx, int &gy) {
     int ni = L.Nr - (loc == LR), nj = L.Nt - (loc == LT), nk = L.Np - (loc == LP);
     gx = cdiv(nk, 128);
     gy = 2 * ni * nj;
+  } else if (map >= M_VEC0) {
+    int loc = map - M_VEC0;
+    int ni = L.Nr - (loc == LR), nj = L.Nt - (loc == LT);
+    gx = cdiv((long)2 * ni * nj * cdiv(L.Np, kVecNV), 128);
   } else if (map >= M_PSC0) {
     gx = bd::phi_scan_ctas(L, map - M_PSC0);
   } else {
@@ -406,13 +435,19 @@ void enqueue_step(ys_batch *b) {
   for (int k = 0; k < b->K; ++k) {
     cudaMemsetAsync(b->norms, 0, sizeof(double) * YS_NFIELDS * cap, st);
     exchange();
-    kb_resid_T<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_RC), cap);
+    if constexpr (sizeof(R) == sizeof(float))
+      kb_resid_T_vec<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_VEC0 + LC), cap);
+    else
+      kb_resid_T<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_RC), cap);
     ++nl;
     solve(LC, F_T);
     for (int sys = 1; sys <= 2; ++sys) {
       int o = (sys == 1) ? 0 : 4;
       for (int comp = 0; comp < 3; ++comp) {
-        kb_resid_u<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_RR + comp), cap, sys, comp);
+        if constexpr (sizeof(R) == sizeof(float))
+          kb_resid_u_vec<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_VEC0 + LR + comp), cap, sys, comp);
+        else
+          kb_resid_u<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_RR + comp), cap, sys, comp);
         ++nl;
         solve(LR + comp, F_U1R + comp + o);
       }

@@ -152,23 +152,34 @@ __device__ __forceinline__ V Sm(const R *a, const R *b, long q) {
 // region.  Lanes outside the region still load: a group never reaches more
 // than NV + 3 elements past the last point of a row, which stays inside the
 // row's padding, the next row's leading pad, or the patch box's tail slack.
-template <int NV>
+//
+// kFlat (the batched launches): bx is a flat block index over the shell's
+// groups, rows one after another (ceil(Np / NV) groups a row), so that short
+// rows do not leave most of a CTA idle; by is unused.
+template <int NV, bool kFlat = false>
 __device__ __forceinline__ int decode_group(const Layout &L, int loc, int patch_mask, int bx, int by, int &p, int &i,
                                             int &j, int &k) {
   int i0, i1, j0, j1, k0, k1;
   region(L, loc, i0, i1, j0, j1, k0, k1);
   int nj = j1 - j0, ni = i1 - i0;
   int row = by;
+  int grp = bx * blockDim.x + threadIdx.x;
+  if constexpr (kFlat) {
+    const int gpr = (L.Np + NV - 1) / NV;
+    row = grp / gpr;
+    grp -= row * gpr;
+    if (row >= 2 * ni * nj) return 0;
+  }
   j = j0 + row % nj;
   row /= nj;
   i = i0 + row % ni;
   p = row / ni;
   if (!((patch_mask >> p) & 1)) return 0;
   if constexpr (NV == 1) {
-    k = k0 + bx * blockDim.x + threadIdx.x;
+    k = k0 + grp;
     return k < k1 ? 1 : 0;
   } else {
-    k = NV * (bx * blockDim.x + threadIdx.x);
+    k = NV * grp;
     int m = 0;
 #pragma unroll
     for (int l = 0; l < NV; ++l)
@@ -233,6 +244,15 @@ __device__ __forceinline__ void vdn(const V (&c)[NV], V e, V (&o)[NV]) {
 #pragma unroll
   for (int l = NV - 1; l > 0; --l) o[l] = c[l - 1];
   o[0] = e;
+}
+
+// o = ((a + b) + c) + d: a 4-point sum of the advecting velocity, in the
+// order the tables of StepAux::As use
+template <int NV, typename V>
+__device__ __forceinline__ void vsum4(const V (&a)[NV], const V (&b)[NV], const V (&c)[NV], const V (&d)[NV],
+                                      V (&o)[NV]) {
+#pragma unroll
+  for (int l = 0; l < NV; ++l) o[l] = ((a[l] + b[l]) + c[l]) + d[l];
 }
 
 // store the lanes set in `lanes` (one vector store when all are)
@@ -313,20 +333,33 @@ __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, Sta
   // u_theta and u_phi around the face: the two cells sharing it
   const V y1 = Sm<V>(yi, yn, q + P), y0 = Sm<V>(yi, yn, q), ym1 = Sm<V>(yi, yn, q - SI + P), ym0 = Sm<V>(yi, yn, q - SI);
   const V z1 = Sm<V>(zi, zn, q + 1), z0 = Sm<V>(zi, zn, q), zm1 = Sm<V>(zi, zn, q - SI + 1), zm0 = Sm<V>(zi, zn, q - SI);
-  const V diff = c[UR_RP] * (Srp - S0) - c[UR_RM] * (S0 - Srm) + c[UR_TP] * (Stp - S0) - c[UR_TM] * (S0 - Stm) +
-                 c[UR_PP] * (Spp - (V)2.0 * S0 + Spm);
-  const V own = c[UR_O1] * Srp + c[UR_O0] * S0 + c[UR_OM] * Srm;
-  const V gd = c[UR_GT1] * y1 + c[UR_GT0] * y0 + c[UR_GTM1] * ym1 + c[UR_GTM0] * ym0 + c[UR_GP1] * (z1 - z0) +
-               c[UR_GPM1] * (zm1 - zm0);
   const R *A1 = ax.A[1], *A2 = ax.A[2];
   const V ar = (V)ax.A[0][q];
   const V sAt = kTab ? (V)ax.As[LR][DT][q] : ((V)A1[q - SI] + (V)A1[q - SI + P]) + (V)A1[q] + (V)A1[q + P];
   const V sAp = kTab ? (V)ax.As[LR][DP][q] : ((V)A2[q - SI] + (V)A2[q - SI + 1]) + (V)A2[q] + (V)A2[q + 1];
-  const V adv = c[UR_AR] * ar * (Srp - Srm) + c[UR_AT] * sAt * (Stp - Stm) + c[UR_AP] * sAp * (Spp - Spm);
-  const V curv = c[UR_CV] * (sAt * (((ym0 + ym1) + y0) + y1) + sAp * (((zm0 + zm1) + z0) + z1));
-  const V gradP = (V)(pres(it, n, sys, q) - pres(it, n, sys, q - SI)) * c[UR_GPR];
-  const V buoy = c[UR_BY] * (Sm<V>(it.f[F_T], n.f[F_T], q - SI) + Sm<V>(it.f[F_T], n.f[F_T], q));
-  V out = diff + own + gd - adv + curv - gradP + buoy;
+  // every term multiply-added into one accumulator (diffusion, own-component
+  // couplings, grad-div couplings, -advection, curvature, -grad P, buoyancy)
+  V out = c[UR_RP] * (Srp - S0);
+  out -= c[UR_RM] * (S0 - Srm);
+  out += c[UR_TP] * (Stp - S0);
+  out -= c[UR_TM] * (S0 - Stm);
+  out += c[UR_PP] * (Spp - (V)2.0 * S0 + Spm);
+  out += c[UR_O1] * Srp;
+  out += c[UR_O0] * S0;
+  out += c[UR_OM] * Srm;
+  out += c[UR_GT1] * y1;
+  out += c[UR_GT0] * y0;
+  out += c[UR_GTM1] * ym1;
+  out += c[UR_GTM0] * ym0;
+  out += c[UR_GP1] * (z1 - z0);
+  out += c[UR_GPM1] * (zm1 - zm0);
+  out -= (c[UR_AR] * ar) * (Srp - Srm);
+  out -= (c[UR_AT] * sAt) * (Stp - Stm);
+  out -= (c[UR_AP] * sAp) * (Spp - Spm);
+  out += (c[UR_CV] * sAt) * (((ym0 + ym1) + y0) + y1);
+  out += (c[UR_CV] * sAp) * (((zm0 + zm1) + z0) + z1);
+  out -= c[UR_GPR] * (V)(pres(it, n, sys, q) - pres(it, n, sys, q - SI));
+  out += c[UR_BY] * (Sm<V>(it.f[F_T], n.f[F_T], q - SI) + Sm<V>(it.f[F_T], n.f[F_T], q));
   if (ax.fr) out += cs<V>(S, CS_DT) * (V)ax.fr[q];
   B[q] = (R)(out - ((V)xi[q] - (V)xn[q]));
 }
@@ -350,19 +383,31 @@ __device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, Sta
   // u_r and u_phi around the face: the two cells sharing it
   const V w1 = Sm<V>(wi, wn, q + SI), w0 = Sm<V>(wi, wn, q), wm1 = Sm<V>(wi, wn, q + SI - P), wm0 = Sm<V>(wi, wn, q - P);
   const V z1 = Sm<V>(zi, zn, q + 1), z0 = Sm<V>(zi, zn, q), zm1 = Sm<V>(zi, zn, q - P + 1), zm0 = Sm<V>(zi, zn, q - P);
-  const V diff = c[UT_RP] * (Srp - S0) - c[UT_RM] * (S0 - Srm) + c[UT_TP] * (Stp - S0) - c[UT_TM] * (S0 - Stm) +
-                 c[UT_PP] * (Spp - (V)2.0 * S0 + Spm);
-  const V own = c[UT_OTP] * Stp + c[UT_O0] * S0 + c[UT_OTM] * Stm;
-  const V gd = c[UT_W1] * w1 + c[UT_W0] * w0 + c[UT_WM1] * wm1 + c[UT_WM0] * wm0 + c[UT_GP1] * (z1 - z0) +
-               c[UT_GPM1] * (zm1 - zm0);
   const R *A0 = ax.A[0], *A2 = ax.A[2];
   const V sAr = kTab ? (V)ax.As[LT][DR][q] : ((V)A0[q - P] + (V)A0[q - P + SI]) + (V)A0[q] + (V)A0[q + SI];
   const V at = (V)ax.A[1][q];
   const V sAp = kTab ? (V)ax.As[LT][DP][q] : ((V)A2[q - P] + (V)A2[q - P + 1]) + (V)A2[q] + (V)A2[q + 1];
-  const V adv = c[UT_AR] * sAr * (Srp - Srm) + c[UT_AT] * at * (Stp - Stm) + c[UT_AP] * sAp * (Spp - Spm);
-  const V curv = c[UT_CP] * sAp * (((zm0 + zm1) + z0) + z1) - c[UT_CW] * at * (((wm0 + wm1) + w0) + w1);
-  const V gradP = (V)(pres(it, n, sys, q) - pres(it, n, sys, q - P)) * c[UT_GPR];
-  V out = diff + own + gd - adv + curv - gradP;
+  // every term multiply-added into one accumulator
+  V out = c[UT_RP] * (Srp - S0);
+  out -= c[UT_RM] * (S0 - Srm);
+  out += c[UT_TP] * (Stp - S0);
+  out -= c[UT_TM] * (S0 - Stm);
+  out += c[UT_PP] * (Spp - (V)2.0 * S0 + Spm);
+  out += c[UT_OTP] * Stp;
+  out += c[UT_O0] * S0;
+  out += c[UT_OTM] * Stm;
+  out += c[UT_W1] * w1;
+  out += c[UT_W0] * w0;
+  out += c[UT_WM1] * wm1;
+  out += c[UT_WM0] * wm0;
+  out += c[UT_GP1] * (z1 - z0);
+  out += c[UT_GPM1] * (zm1 - zm0);
+  out -= (c[UT_AR] * sAr) * (Srp - Srm);
+  out -= (c[UT_AT] * at) * (Stp - Stm);
+  out -= (c[UT_AP] * sAp) * (Spp - Spm);
+  out += (c[UT_CP] * sAp) * (((zm0 + zm1) + z0) + z1);
+  out -= (c[UT_CW] * at) * (((wm0 + wm1) + w0) + w1);
+  out -= c[UT_GPR] * (V)(pres(it, n, sys, q) - pres(it, n, sys, q - P));
   if (ax.ft) out += cs<V>(S, CS_DT) * (V)ax.ft[q];
   B[q] = (R)(out - ((V)xi[q] - (V)xn[q]));
 }
@@ -386,18 +431,31 @@ __device__ __forceinline__ void body_resid_up(Shell S, int sys, State<R> it, Sta
   // u_r and u_theta around the face: the two cells sharing it
   const V w1 = Sm<V>(wi, wn, q + SI), w0 = Sm<V>(wi, wn, q), wm1 = Sm<V>(wi, wn, q - 1 + SI), wm0 = Sm<V>(wi, wn, q - 1);
   const V y1 = Sm<V>(yi, yn, q + P), y0 = Sm<V>(yi, yn, q), ym1 = Sm<V>(yi, yn, q - 1 + P), ym0 = Sm<V>(yi, yn, q - 1);
-  const V diff = c[UP_RP] * (Srp - S0) - c[UP_RM] * (S0 - Srm) + c[UP_TP] * (Stp - S0) - c[UP_TM] * (S0 - Stm) +
-                 c[UP_PP] * (Spp - (V)2.0 * S0 + Spm);
-  const V gd = c[UP_E0] * S0 + c[UP_W1] * w1 + c[UP_W0] * w0 + c[UP_WM1] * wm1 + c[UP_WM0] * wm0 + c[UP_Y1] * y1 +
-               c[UP_Y0] * y0 + c[UP_YM1] * ym1 + c[UP_YM0] * ym0;
   const R *A0 = ax.A[0], *A1 = ax.A[1];
   const V sAr = kTab ? (V)ax.As[LP][DR][q] : ((V)A0[q - 1] + (V)A0[q - 1 + SI]) + (V)A0[q] + (V)A0[q + SI];
   const V sAt = kTab ? (V)ax.As[LP][DT][q] : ((V)A1[q - 1] + (V)A1[q - 1 + P]) + (V)A1[q] + (V)A1[q + P];
   const V ap = (V)ax.A[2][q];
-  const V adv = c[UP_AR] * sAr * (Srp - Srm) + c[UP_AT] * sAt * (Stp - Stm) + c[UP_AP] * ap * (Spp - Spm);
-  const V curv = ap * (c[UP_CW] * (((wm0 + wm1) + w0) + w1) + c[UP_CY] * (((ym0 + ym1) + y0) + y1));
-  const V gradP = (V)(pres(it, n, sys, q) - pres(it, n, sys, q - 1)) * c[UP_GPR];
-  V out = diff + gd - adv - curv - gradP;
+  // every term multiply-added into one accumulator
+  V out = c[UP_RP] * (Srp - S0);
+  out -= c[UP_RM] * (S0 - Srm);
+  out += c[UP_TP] * (Stp - S0);
+  out -= c[UP_TM] * (S0 - Stm);
+  out += c[UP_PP] * (Spp - (V)2.0 * S0 + Spm);
+  out += c[UP_E0] * S0;
+  out += c[UP_W1] * w1;
+  out += c[UP_W0] * w0;
+  out += c[UP_WM1] * wm1;
+  out += c[UP_WM0] * wm0;
+  out += c[UP_Y1] * y1;
+  out += c[UP_Y0] * y0;
+  out += c[UP_YM1] * ym1;
+  out += c[UP_YM0] * ym0;
+  out -= (c[UP_AR] * sAr) * (Srp - Srm);
+  out -= (c[UP_AT] * sAt) * (Stp - Stm);
+  out -= (c[UP_AP] * ap) * (Spp - Spm);
+  out -= (c[UP_CW] * ap) * (((wm0 + wm1) + w0) + w1);
+  out -= (c[UP_CY] * ap) * (((ym0 + ym1) + y0) + y1);
+  out -= c[UP_GPR] * (V)(pres(it, n, sys, q) - pres(it, n, sys, q - 1));
   if (ax.fp) out += cs<V>(S, CS_DT) * (V)ax.fp[q];
   B[q] = (R)(out - ((V)xi[q] - (V)xn[q]));
 }
@@ -405,17 +463,18 @@ __device__ __forceinline__ void body_resid_up(Shell S, int sys, State<R> it, Sta
 // The same residuals with NV consecutive points along phi per thread (FP32
 // storage): identical arithmetic per point, the stencil values gathered with
 // vector loads of the aligned group plus one scalar at each end where a
-// stencil reaches past it, and the sums of the advecting velocity read from
-// the per-step tables StepAux::As (required here).
+// stencil reaches past it.  kTab (the single-shell launches): the sums of the
+// advecting velocity come from the per-step tables StepAux::As; otherwise
+// (the batched launches) they are formed here, in the tables' order.
 
 // temperature (body_resid_T)
-template <typename R, int NV>
+template <typename R, int NV, bool kTab = true, bool kFlat = false>
 __device__ __forceinline__ void body_resid_T_vec(Shell S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask,
                                              int bx, int by) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
-  const int lanes = decode_group<NV>(L, LC, patch_mask, bx, by, p, i, j, k);
+  const int lanes = decode_group<NV, kFlat>(L, LC, patch_mask, bx, by, p, i, j, k);
   if (!lanes) return;
   const long q = lidx(L, p, i, j, k), SI = L.SI, P = L.P;
   const V *c = rowc<V>(S, RT_T, i, j);
@@ -432,9 +491,25 @@ __device__ __forceinline__ void body_resid_T_vec(Shell S, State<R> it, State<R> 
   vup<NV>(S0, Sm<V>(a, b, q + NV), Spp);
   vdn<NV>(S0, Sm<V>(a, b, q - 1), Spm);
   V sAr[NV], sAt[NV], sAp[NV], f[NV];
-  vld<NV>(ax.As[LC][DR] + q, sAr);
-  vld<NV>(ax.As[LC][DT] + q, sAt);
-  vld<NV>(ax.As[LC][DP] + q, sAp);
+  if constexpr (kTab) {
+    vld<NV>(ax.As[LC][DR] + q, sAr);
+    vld<NV>(ax.As[LC][DT] + q, sAt);
+    vld<NV>(ax.As[LC][DP] + q, sAp);
+  } else {
+    V a[NV], b[NV];
+    vld<NV>(ax.A[0] + q, a);
+    vld<NV>(ax.A[0] + q + SI, b);
+#pragma unroll
+    for (int l = 0; l < NV; ++l) sAr[l] = a[l] + b[l];
+    vld<NV>(ax.A[1] + q, a);
+    vld<NV>(ax.A[1] + q + P, b);
+#pragma unroll
+    for (int l = 0; l < NV; ++l) sAt[l] = a[l] + b[l];
+    vld<NV>(ax.A[2] + q, a);
+    vup<NV>(a, (V)ax.A[2][q + NV], b);
+#pragma unroll
+    for (int l = 0; l < NV; ++l) sAp[l] = a[l] + b[l];
+  }
   if (ax.fT) vld<NV>(ax.fT + q, f);
   V o[NV];
 #pragma unroll
@@ -467,13 +542,13 @@ __device__ __forceinline__ void vpres(const State<R> &it, const State<R> &n, int
 }
 
 // u_r (body_resid_ur)
-template <typename R, int NV>
+template <typename R, int NV, bool kTab = true, bool kFlat = false>
 __device__ __forceinline__ void body_resid_ur_vec(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B,
                                               int patch_mask, int bx, int by) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
-  const int lanes = decode_group<NV>(L, LR, patch_mask, bx, by, p, i, j, k);
+  const int lanes = decode_group<NV, kFlat>(L, LR, patch_mask, bx, by, p, i, j, k);
   if (!lanes) return;
   const long q = lidx(L, p, i, j, k), SI = L.SI, P = L.P;
   const V *c = rowc<V>(S, RT_UR, i, j);
@@ -503,8 +578,23 @@ __device__ __forceinline__ void body_resid_ur_vec(Shell S, int sys, State<R> it,
   vup<NV>(zm0, Sm<V>(zi, zn, q - SI + NV), zm1);
   V ar[NV], sAt[NV], sAp[NV];
   vld<NV>(ax.A[0] + q, ar);
-  vld<NV>(ax.As[LR][DT] + q, sAt);
-  vld<NV>(ax.As[LR][DP] + q, sAp);
+  if constexpr (kTab) {
+    vld<NV>(ax.As[LR][DT] + q, sAt);
+    vld<NV>(ax.As[LR][DP] + q, sAp);
+  } else {
+    const R *A1 = ax.A[1], *A2 = ax.A[2];
+    V a[NV], b[NV], c2[NV], d[NV];
+    vld<NV>(A1 + q - SI, a);
+    vld<NV>(A1 + q - SI + P, b);
+    vld<NV>(A1 + q, c2);
+    vld<NV>(A1 + q + P, d);
+    vsum4<NV>(a, b, c2, d, sAt);
+    vld<NV>(A2 + q - SI, a);
+    vup<NV>(a, (V)A2[q - SI + NV], b);
+    vld<NV>(A2 + q, c2);
+    vup<NV>(c2, (V)A2[q + NV], d);
+    vsum4<NV>(a, b, c2, d, sAp);
+  }
   double P0[NV], Pm[NV];
   vpres<NV>(it, n, sys, q, P0);
   vpres<NV>(it, n, sys, q - SI, Pm);
@@ -515,18 +605,27 @@ __device__ __forceinline__ void body_resid_ur_vec(Shell S, int sys, State<R> it,
   V o[NV];
 #pragma unroll
   for (int l = 0; l < NV; ++l) {
-    const V diff = c[UR_RP] * (Srp[l] - S0[l]) - c[UR_RM] * (S0[l] - Srm[l]) + c[UR_TP] * (Stp[l] - S0[l]) -
-                   c[UR_TM] * (S0[l] - Stm[l]) + c[UR_PP] * (Spp[l] - (V)2.0 * S0[l] + Spm[l]);
-    const V own = c[UR_O1] * Srp[l] + c[UR_O0] * S0[l] + c[UR_OM] * Srm[l];
-    const V gd = c[UR_GT1] * y1[l] + c[UR_GT0] * y0[l] + c[UR_GTM1] * ym1[l] + c[UR_GTM0] * ym0[l] +
-                 c[UR_GP1] * (z1[l] - z0[l]) + c[UR_GPM1] * (zm1[l] - zm0[l]);
-    const V adv = c[UR_AR] * ar[l] * (Srp[l] - Srm[l]) + c[UR_AT] * sAt[l] * (Stp[l] - Stm[l]) +
-                  c[UR_AP] * sAp[l] * (Spp[l] - Spm[l]);
-    const V curv = c[UR_CV] * (sAt[l] * (((ym0[l] + ym1[l]) + y0[l]) + y1[l]) +
-                               sAp[l] * (((zm0[l] + zm1[l]) + z0[l]) + z1[l]));
-    const V gradP = (V)(P0[l] - Pm[l]) * c[UR_GPR];
-    const V buoy = c[UR_BY] * (tm[l] + t0[l]);
-    V out = diff + own + gd - adv + curv - gradP + buoy;
+    V out = c[UR_RP] * (Srp[l] - S0[l]);
+    out -= c[UR_RM] * (S0[l] - Srm[l]);
+    out += c[UR_TP] * (Stp[l] - S0[l]);
+    out -= c[UR_TM] * (S0[l] - Stm[l]);
+    out += c[UR_PP] * (Spp[l] - (V)2.0 * S0[l] + Spm[l]);
+    out += c[UR_O1] * Srp[l];
+    out += c[UR_O0] * S0[l];
+    out += c[UR_OM] * Srm[l];
+    out += c[UR_GT1] * y1[l];
+    out += c[UR_GT0] * y0[l];
+    out += c[UR_GTM1] * ym1[l];
+    out += c[UR_GTM0] * ym0[l];
+    out += c[UR_GP1] * (z1[l] - z0[l]);
+    out += c[UR_GPM1] * (zm1[l] - zm0[l]);
+    out -= (c[UR_AR] * ar[l]) * (Srp[l] - Srm[l]);
+    out -= (c[UR_AT] * sAt[l]) * (Stp[l] - Stm[l]);
+    out -= (c[UR_AP] * sAp[l]) * (Spp[l] - Spm[l]);
+    out += (c[UR_CV] * sAt[l]) * (((ym0[l] + ym1[l]) + y0[l]) + y1[l]);
+    out += (c[UR_CV] * sAp[l]) * (((zm0[l] + zm1[l]) + z0[l]) + z1[l]);
+    out -= c[UR_GPR] * (V)(P0[l] - Pm[l]);
+    out += c[UR_BY] * (tm[l] + t0[l]);
     if (ax.fr) out += cs<V>(S, CS_DT) * f[l];
     o[l] = out - (xa[l] - xb[l]);
   }
@@ -534,13 +633,13 @@ __device__ __forceinline__ void body_resid_ur_vec(Shell S, int sys, State<R> it,
 }
 
 // u_theta (body_resid_ut)
-template <typename R, int NV>
+template <typename R, int NV, bool kTab = true, bool kFlat = false>
 __device__ __forceinline__ void body_resid_ut_vec(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B,
                                               int patch_mask, int bx, int by) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
-  const int lanes = decode_group<NV>(L, LT, patch_mask, bx, by, p, i, j, k);
+  const int lanes = decode_group<NV, kFlat>(L, LT, patch_mask, bx, by, p, i, j, k);
   if (!lanes) return;
   const long q = lidx(L, p, i, j, k), SI = L.SI, P = L.P;
   const V *c = rowc<V>(S, RT_UT, i, j);
@@ -569,9 +668,24 @@ __device__ __forceinline__ void body_resid_ut_vec(Shell S, int sys, State<R> it,
   vsm<NV>(zi, zn, q - P, zm0);
   vup<NV>(zm0, Sm<V>(zi, zn, q - P + NV), zm1);
   V sAr[NV], at[NV], sAp[NV];
-  vld<NV>(ax.As[LT][DR] + q, sAr);
   vld<NV>(ax.A[1] + q, at);
-  vld<NV>(ax.As[LT][DP] + q, sAp);
+  if constexpr (kTab) {
+    vld<NV>(ax.As[LT][DR] + q, sAr);
+    vld<NV>(ax.As[LT][DP] + q, sAp);
+  } else {
+    const R *A0 = ax.A[0], *A2 = ax.A[2];
+    V a[NV], b[NV], c2[NV], d[NV];
+    vld<NV>(A0 + q - P, a);
+    vld<NV>(A0 + q - P + SI, b);
+    vld<NV>(A0 + q, c2);
+    vld<NV>(A0 + q + SI, d);
+    vsum4<NV>(a, b, c2, d, sAr);
+    vld<NV>(A2 + q - P, a);
+    vup<NV>(a, (V)A2[q - P + NV], b);
+    vld<NV>(A2 + q, c2);
+    vup<NV>(c2, (V)A2[q + NV], d);
+    vsum4<NV>(a, b, c2, d, sAp);
+  }
   double P0[NV], Pm[NV];
   vpres<NV>(it, n, sys, q, P0);
   vpres<NV>(it, n, sys, q - P, Pm);
@@ -580,17 +694,26 @@ __device__ __forceinline__ void body_resid_ut_vec(Shell S, int sys, State<R> it,
   V o[NV];
 #pragma unroll
   for (int l = 0; l < NV; ++l) {
-    const V diff = c[UT_RP] * (Srp[l] - S0[l]) - c[UT_RM] * (S0[l] - Srm[l]) + c[UT_TP] * (Stp[l] - S0[l]) -
-                   c[UT_TM] * (S0[l] - Stm[l]) + c[UT_PP] * (Spp[l] - (V)2.0 * S0[l] + Spm[l]);
-    const V own = c[UT_OTP] * Stp[l] + c[UT_O0] * S0[l] + c[UT_OTM] * Stm[l];
-    const V gd = c[UT_W1] * w1[l] + c[UT_W0] * w0[l] + c[UT_WM1] * wm1[l] + c[UT_WM0] * wm0[l] +
-                 c[UT_GP1] * (z1[l] - z0[l]) + c[UT_GPM1] * (zm1[l] - zm0[l]);
-    const V adv = c[UT_AR] * sAr[l] * (Srp[l] - Srm[l]) + c[UT_AT] * at[l] * (Stp[l] - Stm[l]) +
-                  c[UT_AP] * sAp[l] * (Spp[l] - Spm[l]);
-    const V curv = c[UT_CP] * sAp[l] * (((zm0[l] + zm1[l]) + z0[l]) + z1[l]) -
-                   c[UT_CW] * at[l] * (((wm0[l] + wm1[l]) + w0[l]) + w1[l]);
-    const V gradP = (V)(P0[l] - Pm[l]) * c[UT_GPR];
-    V out = diff + own + gd - adv + curv - gradP;
+    V out = c[UT_RP] * (Srp[l] - S0[l]);
+    out -= c[UT_RM] * (S0[l] - Srm[l]);
+    out += c[UT_TP] * (Stp[l] - S0[l]);
+    out -= c[UT_TM] * (S0[l] - Stm[l]);
+    out += c[UT_PP] * (Spp[l] - (V)2.0 * S0[l] + Spm[l]);
+    out += c[UT_OTP] * Stp[l];
+    out += c[UT_O0] * S0[l];
+    out += c[UT_OTM] * Stm[l];
+    out += c[UT_W1] * w1[l];
+    out += c[UT_W0] * w0[l];
+    out += c[UT_WM1] * wm1[l];
+    out += c[UT_WM0] * wm0[l];
+    out += c[UT_GP1] * (z1[l] - z0[l]);
+    out += c[UT_GPM1] * (zm1[l] - zm0[l]);
+    out -= (c[UT_AR] * sAr[l]) * (Srp[l] - Srm[l]);
+    out -= (c[UT_AT] * at[l]) * (Stp[l] - Stm[l]);
+    out -= (c[UT_AP] * sAp[l]) * (Spp[l] - Spm[l]);
+    out += (c[UT_CP] * sAp[l]) * (((zm0[l] + zm1[l]) + z0[l]) + z1[l]);
+    out -= (c[UT_CW] * at[l]) * (((wm0[l] + wm1[l]) + w0[l]) + w1[l]);
+    out -= c[UT_GPR] * (V)(P0[l] - Pm[l]);
     if (ax.ft) out += cs<V>(S, CS_DT) * f[l];
     o[l] = out - (xa[l] - xb[l]);
   }
@@ -598,13 +721,13 @@ __device__ __forceinline__ void body_resid_ut_vec(Shell S, int sys, State<R> it,
 }
 
 // u_phi (body_resid_up)
-template <typename R, int NV>
+template <typename R, int NV, bool kTab = true, bool kFlat = false>
 __device__ __forceinline__ void body_resid_up_vec(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B,
                                               int patch_mask, int bx, int by) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
-  const int lanes = decode_group<NV>(L, LP, patch_mask, bx, by, p, i, j, k);
+  const int lanes = decode_group<NV, kFlat>(L, LP, patch_mask, bx, by, p, i, j, k);
   if (!lanes) return;
   const long q = lidx(L, p, i, j, k), SI = L.SI, P = L.P;
   const V *c = rowc<V>(S, RT_UP, i, j);
@@ -633,9 +756,24 @@ __device__ __forceinline__ void body_resid_up_vec(Shell S, int sys, State<R> it,
   vdn<NV>(y1, Sm<V>(yi, yn, q - 1 + P), ym1);
   vdn<NV>(y0, Sm<V>(yi, yn, q - 1), ym0);
   V sAr[NV], sAt[NV], ap[NV];
-  vld<NV>(ax.As[LP][DR] + q, sAr);
-  vld<NV>(ax.As[LP][DT] + q, sAt);
   vld<NV>(ax.A[2] + q, ap);
+  if constexpr (kTab) {
+    vld<NV>(ax.As[LP][DR] + q, sAr);
+    vld<NV>(ax.As[LP][DT] + q, sAt);
+  } else {
+    const R *A0 = ax.A[0], *A1 = ax.A[1];
+    V a[NV], b[NV], c2[NV], d[NV];
+    vld<NV>(A0 + q, c2);
+    vld<NV>(A0 + q + SI, d);
+    vdn<NV>(c2, (V)A0[q - 1], a);
+    vdn<NV>(d, (V)A0[q - 1 + SI], b);
+    vsum4<NV>(a, b, c2, d, sAr);
+    vld<NV>(A1 + q, c2);
+    vld<NV>(A1 + q + P, d);
+    vdn<NV>(c2, (V)A1[q - 1], a);
+    vdn<NV>(d, (V)A1[q - 1 + P], b);
+    vsum4<NV>(a, b, c2, d, sAt);
+  }
   double P0[NV], Pm[NV];
   vpres<NV>(it, n, sys, q, P0);
   vdn<NV>(P0, pres(it, n, sys, q - 1), Pm);
@@ -644,16 +782,26 @@ __device__ __forceinline__ void body_resid_up_vec(Shell S, int sys, State<R> it,
   V o[NV];
 #pragma unroll
   for (int l = 0; l < NV; ++l) {
-    const V diff = c[UP_RP] * (Srp[l] - S0[l]) - c[UP_RM] * (S0[l] - Srm[l]) + c[UP_TP] * (Stp[l] - S0[l]) -
-                   c[UP_TM] * (S0[l] - Stm[l]) + c[UP_PP] * (Spp[l] - (V)2.0 * S0[l] + Spm[l]);
-    const V gd = c[UP_E0] * S0[l] + c[UP_W1] * w1[l] + c[UP_W0] * w0[l] + c[UP_WM1] * wm1[l] + c[UP_WM0] * wm0[l] +
-                 c[UP_Y1] * y1[l] + c[UP_Y0] * y0[l] + c[UP_YM1] * ym1[l] + c[UP_YM0] * ym0[l];
-    const V adv = c[UP_AR] * sAr[l] * (Srp[l] - Srm[l]) + c[UP_AT] * sAt[l] * (Stp[l] - Stm[l]) +
-                  c[UP_AP] * ap[l] * (Spp[l] - Spm[l]);
-    const V curv = ap[l] * (c[UP_CW] * (((wm0[l] + wm1[l]) + w0[l]) + w1[l]) +
-                            c[UP_CY] * (((ym0[l] + ym1[l]) + y0[l]) + y1[l]));
-    const V gradP = (V)(P0[l] - Pm[l]) * c[UP_GPR];
-    V out = diff + gd - adv - curv - gradP;
+    V out = c[UP_RP] * (Srp[l] - S0[l]);
+    out -= c[UP_RM] * (S0[l] - Srm[l]);
+    out += c[UP_TP] * (Stp[l] - S0[l]);
+    out -= c[UP_TM] * (S0[l] - Stm[l]);
+    out += c[UP_PP] * (Spp[l] - (V)2.0 * S0[l] + Spm[l]);
+    out += c[UP_E0] * S0[l];
+    out += c[UP_W1] * w1[l];
+    out += c[UP_W0] * w0[l];
+    out += c[UP_WM1] * wm1[l];
+    out += c[UP_WM0] * wm0[l];
+    out += c[UP_Y1] * y1[l];
+    out += c[UP_Y0] * y0[l];
+    out += c[UP_YM1] * ym1[l];
+    out += c[UP_YM0] * ym0[l];
+    out -= (c[UP_AR] * sAr[l]) * (Srp[l] - Srm[l]);
+    out -= (c[UP_AT] * sAt[l]) * (Stp[l] - Stm[l]);
+    out -= (c[UP_AP] * ap[l]) * (Spp[l] - Spm[l]);
+    out -= (c[UP_CW] * ap[l]) * (((wm0[l] + wm1[l]) + w0[l]) + w1[l]);
+    out -= (c[UP_CY] * ap[l]) * (((ym0[l] + ym1[l]) + y0[l]) + y1[l]);
+    out -= c[UP_GPR] * (V)(P0[l] - Pm[l]);
     if (ax.fp) out += cs<V>(S, CS_DT) * f[l];
     o[l] = out - (xa[l] - xb[l]);
   }
