@@ -125,17 +125,19 @@ def _interp(a_donor, st, i_slice):
 def boundary_flux_weights(g):
     """Outward normal times face area of every boundary velocity value of a
     patch, from the discrete Gauss theorem of the divergence (Sec. 3.3: the
-    sum over cells of div * r^2 sin(theta) h_r h_th h_ph telescopes to these
-    face terms): theta-edge faces r_c sin(theta_f) h_r h_ph, phi-edge faces
-    r_c h_r h_th, wall faces r_f^2 sin(theta_c) h_th h_ph.  Returns
+    sum over cells of div * r^2 sin(theta) h_c h_th h_ph telescopes to these
+    face terms): theta-edge faces r_c sin(theta_f) h_c h_ph, phi-edge faces
+    r_c h_c h_th, wall faces r_f^2 sin(theta_c) h_th h_ph (h_c the radial cell
+    width, grid.py).  Returns
     (wt0, wt1, wp0, wp1, wr0, wr1) shaped like the faces' value blocks
     (Nr x Nph, Nr x Nph, Nr x Nth, Nr x Nth, Nth x Nph, Nth x Nph)."""
     Nr, Nt, Np = g.Nr, g.Nth, g.Nph
     rc = g.r_c(np.arange(Nr))[:, None]
+    hc = g.h_c(np.arange(Nr))[:, None]
     sc = np.sin(g.th_c(np.arange(Nt)))
     ones_p = np.ones((1, Np))
-    wt = lambda j: rc * math.sin(g.th_f(j)) * g.hr * g.hph * ones_p
-    wp = rc * g.hr * g.hth * np.ones((1, Nt))
+    wt = lambda j: rc * math.sin(g.th_f(j)) * hc * g.hph * ones_p
+    wp = rc * hc * g.hth * np.ones((1, Nt))
     wr = lambda i: g.r_f(i) ** 2 * sc[:, None] * g.hth * g.hph * ones_p
     return (-wt(0), wt(Nt), -wp, wp, -wr(0), wr(Nr))
 
@@ -216,13 +218,14 @@ def exchange_into(tables, target, fields, patches, T_walls=(0.0, 0.0), U_walls=N
                 mass_flux_correction(g, target[key], p, step4[0], step4[1])
 
 
-def robin_ghost(a, b, hr):
+def robin_ghost(a, b, h):
     """Ghost x_g = gamma x_0 + delta of a cell-centred quantity for the wall
     condition a x + b dx/dn = g (Sec. 1: Dirichlet, Neumann or Robin walls),
-    with x = (x_g + x_0)/2 and dx/dn = (x_g - x_0)/h_r on the wall: returns
-    (gamma, delta per unit g).  Dirichlet (1, 0): (-1, 2)."""
-    den = 0.5 * a + b / hr
-    return -(0.5 * a - b / hr) / den, 1.0 / den
+    with x = (x_g + x_0)/2 and dx/dn = (x_g - x_0)/h on the wall, h the
+    distance of the ghost centre from the first one (h_f of the wall face):
+    returns (gamma, delta per unit g).  Dirichlet (1, 0): (-1, 2)."""
+    den = 0.5 * a + b / h
+    return -(0.5 * a - b / h) / den, 1.0 / den
 
 
 def wall_ghosts(g, fields, patches, T_walls=(0.0, 0.0), U_walls=None, T_robin=((1.0, 0.0), (1.0, 0.0))):
@@ -232,8 +235,8 @@ def wall_ghosts(g, fields, patches, T_walls=(0.0, 0.0), U_walls=None, T_robin=((
     gives (a, b) per wall; (1, 0) = Dirichlet: 2 T_wall - T_0).
     U_walls: None (no-slip) or wall velocities as in Params.wall_u."""
     Nr, Nt, Np = g.Nr, g.Nth, g.Nph
-    gi, di_ = robin_ghost(T_robin[0][0], T_robin[0][1], g.hr)
-    go, do_ = robin_ghost(T_robin[1][0], T_robin[1][1], g.hr)
+    gi, di_ = robin_ghost(T_robin[0][0], T_robin[0][1], float(g.h_f(0)))
+    go, do_ = robin_ghost(T_robin[1][0], T_robin[1][1], float(g.h_f(Nr)))
     for p in patches:
         T = fields["T"][p]
         T[0, 1:Nt + 1, 1:Np + 1] = gi * T[1, 1:Nt + 1, 1:Np + 1] + di_ * T_walls[0]

@@ -12,7 +12,19 @@ phi in [-3pi/4 - d, 3pi/4 + d] with one overlap angle d = overlap * h_theta,
 h_theta = (pi/2) / (N_theta - 2 overlap), h_phi = (3pi/2 + 2d) / N_phi.
 
 MAC placement (Sec. 4): T and p at cell centres, u_r on r-faces, u_theta on
-theta-faces, u_phi on phi-faces, uniform spacing in each direction.
+theta-faces, u_phi on phi-faces, uniform spacing in theta and phi.
+
+Radial grid (Sec. 4 allows a non-uniform grid; its tests use uniform ones):
+uniform by default, else given by the radii of all 2 Nr + 1 half points
+r_half[m] (faces at even m, centres at odd m; r_half[0] = R1,
+r_half[2 Nr] = R2).  The reading taken for "centred differences on a
+non-uniform grid" is the stretched-coordinate one: a half-cell difference
+divides by the distance between its two points, h_c(i) = r_f(i+1) - r_f(i) at
+centre i and h_f(i) = r_c(i) - r_c(i-1) at face i; a whole-cell centred
+difference divides by 2 h of its point; averages of radial neighbours stay
+arithmetic means.  Ghost half points are the mirror images of the interior
+ones about the walls, so that h_f(0) = 2 (r_c(0) - R1).  On a uniform grid
+every h is h_r.
 
 Storage: every field of one patch is an array indexed by logical
 (i, j, k) in [-1, Nr] x [-1, Nth] x [-1, Nph], stored with offset +1, so a
@@ -32,7 +44,7 @@ M = np.array([[-1.0, 0.0, 0.0], [0.0, 0.0, 1.0], [0.0, 1.0, 0.0]])
 
 
 class Grid:
-    def __init__(self, R1, R2, Nr, Nth, Nph, overlap=2):
+    def __init__(self, R1, R2, Nr, Nth, Nph, overlap=2, r_half=None):
         if not (R1 > 0 and R2 > R1):
             raise ValueError("need 0 < R1 < R2")
         if Nth <= 2 * overlap:
@@ -40,7 +52,20 @@ class Grid:
         self.R1, self.R2 = float(R1), float(R2)
         self.Nr, self.Nth, self.Nph = int(Nr), int(Nth), int(Nph)
         self.overlap = int(overlap)
-        self.hr = (self.R2 - self.R1) / self.Nr
+        self.hr = (self.R2 - self.R1) / self.Nr     # the uniform grid's radial spacing
+        self.uniform_r = r_half is None
+        if r_half is not None:
+            rh = np.array(r_half, dtype=np.float64)
+            if rh.shape != (2 * self.Nr + 1,) or not np.all(np.diff(rh) > 0):
+                raise ValueError("r_half: 2 Nr + 1 strictly increasing radii")
+            tol = 1e-12 * (self.R2 - self.R1)
+            if abs(rh[0] - self.R1) > tol or abs(rh[-1] - self.R2) > tol:
+                raise ValueError("r_half must start at R1 and end at R2")
+            rh[0], rh[-1] = self.R1, self.R2
+            # 4 ghost half points beyond each wall, mirrored about it
+            lo = 2.0 * self.R1 - rh[4:0:-1]
+            hi = 2.0 * self.R2 - rh[-2:-6:-1]
+            self._rh = np.concatenate([lo, rh, hi])    # half point m at index m + 4
         self.hth = (math.pi / 2) / (self.Nth - 2 * self.overlap)
         self.delta = self.overlap * self.hth
         self.hph = (1.5 * math.pi + 2 * self.delta) / self.Nph
@@ -54,10 +79,25 @@ class Grid:
 
     # 1-D coordinates, indexed by logical index (array of logical indices in)
     def r_c(self, i):
-        return self.R1 + (np.asarray(i, dtype=np.float64) + 0.5) * self.hr
+        if self.uniform_r:
+            return self.R1 + (np.asarray(i, dtype=np.float64) + 0.5) * self.hr
+        return self._rh[2 * np.asarray(i) + 1 + 4]
 
     def r_f(self, i):
-        return self.R1 + np.asarray(i, dtype=np.float64) * self.hr
+        if self.uniform_r:
+            return self.R1 + np.asarray(i, dtype=np.float64) * self.hr
+        return self._rh[2 * np.asarray(i) + 4]
+
+    # radial spacings: h_c at centre i (cell width), h_f at face i (centre distance)
+    def h_c(self, i):
+        if self.uniform_r:
+            return np.full(np.shape(i), self.hr)
+        return self.r_f(np.asarray(i) + 1) - self.r_f(i)
+
+    def h_f(self, i):
+        if self.uniform_r:
+            return np.full(np.shape(i), self.hr)
+        return self.r_c(i) - self.r_c(np.asarray(i) - 1)
 
     def th_c(self, j):
         return self.th0 + (np.asarray(j, dtype=np.float64) + 0.5) * self.hth
@@ -101,9 +141,13 @@ class Grid:
         return (slice(None), slice(1, 1 + ni), slice(1, 1 + nj), slice(1, 1 + nk))
 
     def weight(self, loc):
-        """Midpoint-rule weight r^2 sin(theta) h_r h_th h_ph at the unknowns of ``loc``."""
+        """Midpoint-rule weight r^2 sin(theta) h h_th h_ph at the unknowns of
+        ``loc``, h the radial spacing of the point (h_f at r-faces, h_c else)."""
         r, th = self.coords(loc)
-        return r * r * np.sin(th) * self.hr * self.hth * self.hph
+        i0, i1 = self.region(loc)[:2]
+        ii = np.arange(i0, i1)
+        h = (self.h_f(ii) if loc == R else self.h_c(ii))[None, :, None, None]
+        return r * r * np.sin(th) * h * self.hth * self.hph
 
 
 def view(a, reg, di=0, dj=0, dk=0):

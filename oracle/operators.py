@@ -22,9 +22,13 @@ which reduce to the printed nonlinear terms when a = b = u.
 
 Discretisation rules (second-order centred differences on the MAC grid, Sec. 4):
   * diffusion is conservative 3-point with the metric at the half points,
-    e.g. D_rr x_m = r_m^-2 [r_{m+1/2}^2 (x_{m+1}-x_m) - r_{m-1/2}^2 (x_m-x_{m-1})]/h_r^2;
+    e.g. D_rr x_m = r_m^-2 [r_{m+1/2}^2 (x_{m+1}-x_m)/h_{m+1/2}
+                            - r_{m-1/2}^2 (x_m-x_{m-1})/h_{m-1/2}] / h_m;
   * a first derivative of a quantity stored half a cell away is a 2-point
-    difference, otherwise a centred 2h difference;
+    difference over the distance of the two points, otherwise a centred
+    difference over 2 h of the point;
+  * radial spacings are local (grid.py: h_c at centres, h_f at faces; both
+    h_r on a uniform grid);
   * a quantity needed off its own location is the arithmetic mean of its 2 or
     4 nearest stored values (products are formed after averaging each factor);
   * metric factors are evaluated exactly at the point of the row.
@@ -43,6 +47,16 @@ def _rc(g, reg, d=0):
 
 def _rf(g, reg, d=0):
     return g.r_f(np.arange(reg[0] + d, reg[1] + d))[None, :, None, None]
+
+
+def _hc(g, reg, d=0):
+    """Radial cell widths h_c at centre indices reg[0] + d .. reg[1] + d."""
+    return g.h_c(np.arange(reg[0] + d, reg[1] + d))[None, :, None, None]
+
+
+def _hf(g, reg, d=0):
+    """Radial centre distances h_f at face indices reg[0] + d .. reg[1] + d."""
+    return g.h_f(np.arange(reg[0] + d, reg[1] + d))[None, :, None, None]
 
 
 def _sc(g, reg, d=0):
@@ -106,7 +120,7 @@ def divergence(g, U):
     reg = g.region(C)
     r, s = _rc(g, reg), _sc(g, reg)
     Ur, Ut, Up = U
-    d_r = (_rf(g, reg, 1) ** 2 * view(Ur, reg, 1, 0, 0) - _rf(g, reg) ** 2 * view(Ur, reg)) / (r * r * g.hr)
+    d_r = (_rf(g, reg, 1) ** 2 * view(Ur, reg, 1, 0, 0) - _rf(g, reg) ** 2 * view(Ur, reg)) / (r * r * _hc(g, reg))
     d_t = (_sf(g, reg, 1) * view(Ut, reg, 0, 1, 0) - _sf(g, reg) * view(Ut, reg)) / (r * s * g.hth)
     d_p = (view(Up, reg, 0, 0, 1) - view(Up, reg)) / (r * s * g.hph)
     return d_r + d_t + d_p
@@ -123,16 +137,17 @@ def rate_T(g, X, A, f, kappa=1.0):
     """Rate of the temperature equation, kappa lap X - a.grad X + f, at centres."""
     reg = g.region(C)
     r, s = _rc(g, reg), _sc(g, reg)
-    hr, ht, hp = g.hr, g.hth, g.hph
+    ht, hp = g.hth, g.hph
     X0 = view(X, reg)
     Xr_p, Xr_m = view(X, reg, 1, 0, 0), view(X, reg, -1, 0, 0)
     Xt_p, Xt_m = view(X, reg, 0, 1, 0), view(X, reg, 0, -1, 0)
     Xp_p, Xp_m = view(X, reg, 0, 0, 1), view(X, reg, 0, 0, -1)
-    Drr = (_rf(g, reg, 1) ** 2 * (Xr_p - X0) - _rf(g, reg) ** 2 * (X0 - Xr_m)) / (r * r * hr * hr)
+    hc = _hc(g, reg)
+    Drr = (_rf(g, reg, 1) ** 2 * (Xr_p - X0) / _hf(g, reg, 1) - _rf(g, reg) ** 2 * (X0 - Xr_m) / _hf(g, reg)) / (r * r * hc)
     Dtt = (_sf(g, reg, 1) * (Xt_p - X0) - _sf(g, reg) * (X0 - Xt_m)) / (r * r * s * ht * ht)
     Dpp = (Xp_p - 2.0 * X0 + Xp_m) / (r * r * s * s * hp * hp)
     ar, at, ap = advecting(g, C, A)
-    adv = (ar * (Xr_p - Xr_m) / (2 * hr) + at * (Xt_p - Xt_m) / (2 * r * ht)
+    adv = (ar * (Xr_p - Xr_m) / (2 * hc) + at * (Xt_p - Xt_m) / (2 * r * ht)
            + ap * (Xp_p - Xp_m) / (2 * r * s * hp))
     return kappa * (Drr + Dtt + Dpp) - adv + f
 
@@ -143,24 +158,25 @@ def rate_ur(g, U, A, P, D, Tb, f, nu, chi, PrRa):
     (padded), Tb: half-level temperature (padded)."""
     reg = g.region(R)
     r, s = _rf(g, reg), _sc(g, reg)
-    hr, ht, hp = g.hr, g.hth, g.hph
+    ht, hp = g.hth, g.hph
     X = U[0]
     X0 = view(X, reg)
     Xr_p, Xr_m = view(X, reg, 1, 0, 0), view(X, reg, -1, 0, 0)
     Xt_p, Xt_m = view(X, reg, 0, 1, 0), view(X, reg, 0, -1, 0)
     Xp_p, Xp_m = view(X, reg, 0, 0, 1), view(X, reg, 0, 0, -1)
-    Drr = (_rc(g, reg) ** 2 * (Xr_p - X0) - _rc(g, reg, -1) ** 2 * (X0 - Xr_m)) / (r * r * hr * hr)
+    hf = _hf(g, reg)
+    Drr = (_rc(g, reg) ** 2 * (Xr_p - X0) / _hc(g, reg) - _rc(g, reg, -1) ** 2 * (X0 - Xr_m) / _hc(g, reg, -1)) / (r * r * hf)
     Dtt = (_sf(g, reg, 1) * (Xt_p - X0) - _sf(g, reg) * (X0 - Xt_m)) / (r * r * s * ht * ht)
     Dpp = (Xp_p - 2.0 * X0 + Xp_m) / (r * r * s * s * hp * hp)
     extra = (-2.0 * X0 / (r * r)
-             + 2.0 / r ** 3 * (_rf(g, reg, 1) ** 2 * Xr_p - _rf(g, reg, -1) ** 2 * Xr_m) / (2 * hr))
+             + 2.0 / r ** 3 * (_rf(g, reg, 1) ** 2 * Xr_p - _rf(g, reg, -1) ** 2 * Xr_m) / (2 * hf))
     ar, at, ap = advecting(g, R, A)
     bt = _avg(U[1], reg, NB[(R, TH)])
     bp = _avg(U[2], reg, NB[(R, PH)])
-    adv = (ar * (Xr_p - Xr_m) / (2 * hr) + at * (Xt_p - Xt_m) / (2 * r * ht)
+    adv = (ar * (Xr_p - Xr_m) / (2 * hf) + at * (Xt_p - Xt_m) / (2 * r * ht)
            + ap * (Xp_p - Xp_m) / (2 * r * s * hp) - (at * bt + ap * bp) / r)
-    gradP = (view(P, reg) - view(P, reg, -1, 0, 0)) / hr
-    gdiv = (view(D, reg) - view(D, reg, -1, 0, 0)) / hr
+    gradP = (view(P, reg) - view(P, reg, -1, 0, 0)) / hf
+    gdiv = (view(D, reg) - view(D, reg, -1, 0, 0)) / hf
     buoy = PrRa * 0.5 * (view(Tb, reg, -1, 0, 0) + view(Tb, reg))
     return nu * (Drr + Dtt + Dpp + extra) - adv - gradP + gdiv / (2 * chi) + buoy + f
 
@@ -169,13 +185,14 @@ def rate_ut(g, U, A, P, D, f, nu, chi):
     """Rate of the u_theta equation at interior theta-faces."""
     reg = g.region(TH)
     r, s, c = _rc(g, reg), _sf(g, reg), _cf(g, reg)
-    hr, ht, hp = g.hr, g.hth, g.hph
+    ht, hp = g.hth, g.hph
     X, W = U[1], U[0]
     X0 = view(X, reg)
     Xr_p, Xr_m = view(X, reg, 1, 0, 0), view(X, reg, -1, 0, 0)
     Xt_p, Xt_m = view(X, reg, 0, 1, 0), view(X, reg, 0, -1, 0)
     Xp_p, Xp_m = view(X, reg, 0, 0, 1), view(X, reg, 0, 0, -1)
-    Drr = (_rf(g, reg, 1) ** 2 * (Xr_p - X0) - _rf(g, reg) ** 2 * (X0 - Xr_m)) / (r * r * hr * hr)
+    hc = _hc(g, reg)
+    Drr = (_rf(g, reg, 1) ** 2 * (Xr_p - X0) / _hf(g, reg, 1) - _rf(g, reg) ** 2 * (X0 - Xr_m) / _hf(g, reg)) / (r * r * hc)
     Dtt = (_sc(g, reg) * (Xt_p - X0) - _sc(g, reg, -1) * (X0 - Xt_m)) / (r * r * s * ht * ht)
     Dpp = (Xp_p - 2.0 * X0 + Xp_m) / (r * r * s * s * hp * hp)
     # u_r averaged to the r-centre, on theta-cells j and j-1
@@ -183,8 +200,8 @@ def rate_ut(g, U, A, P, D, f, nu, chi):
     W_jm = 0.5 * (view(W, reg, 0, -1, 0) + view(W, reg, 1, -1, 0))
     dW_dth = (W_j - W_jm) / ht
     # d_r(r^2 u_r) at the r-centre on theta-cells j and j-1, averaged to the face
-    q_j = (_rf(g, reg, 1) ** 2 * view(W, reg, 1, 0, 0) - _rf(g, reg) ** 2 * view(W, reg)) / hr
-    q_jm = (_rf(g, reg, 1) ** 2 * view(W, reg, 1, -1, 0) - _rf(g, reg) ** 2 * view(W, reg, 0, -1, 0)) / hr
+    q_j = (_rf(g, reg, 1) ** 2 * view(W, reg, 1, 0, 0) - _rf(g, reg) ** 2 * view(W, reg)) / hc
+    q_jm = (_rf(g, reg, 1) ** 2 * view(W, reg, 1, -1, 0) - _rf(g, reg) ** 2 * view(W, reg, 0, -1, 0)) / hc
     dr_r2W = 0.5 * (q_j + q_jm)
     extra = (-X0 / (r * r * s * s)
              + 2.0 * c / (r * r * s * s) * (_sf(g, reg, 1) * Xt_p - _sf(g, reg, -1) * Xt_m) / (2 * ht)
@@ -192,7 +209,7 @@ def rate_ut(g, U, A, P, D, f, nu, chi):
     ar, at, ap = advecting(g, TH, A)
     br = _avg(W, reg, NB[(TH, R)])
     bp = _avg(U[2], reg, NB[(TH, PH)])
-    adv = (ar * (Xr_p - Xr_m) / (2 * hr) + at * (Xt_p - Xt_m) / (2 * r * ht)
+    adv = (ar * (Xr_p - Xr_m) / (2 * hc) + at * (Xt_p - Xt_m) / (2 * r * ht)
            + ap * (Xp_p - Xp_m) / (2 * r * s * hp) + (at * br - ap * bp * c / s) / r)
     gradP = (view(P, reg) - view(P, reg, 0, -1, 0)) / (r * ht)
     gdiv = (view(D, reg) - view(D, reg, 0, -1, 0)) / (r * ht)
@@ -203,13 +220,14 @@ def rate_up(g, U, A, P, D, f, nu, chi):
     """Rate of the u_phi equation at interior phi-faces."""
     reg = g.region(PH)
     r, s, c = _rc(g, reg), _sc(g, reg), _cc(g, reg)
-    hr, ht, hp = g.hr, g.hth, g.hph
+    ht, hp = g.hth, g.hph
     X, W, Y = U[2], U[0], U[1]
     X0 = view(X, reg)
     Xr_p, Xr_m = view(X, reg, 1, 0, 0), view(X, reg, -1, 0, 0)
     Xt_p, Xt_m = view(X, reg, 0, 1, 0), view(X, reg, 0, -1, 0)
     Xp_p, Xp_m = view(X, reg, 0, 0, 1), view(X, reg, 0, 0, -1)
-    Drr = (_rf(g, reg, 1) ** 2 * (Xr_p - X0) - _rf(g, reg) ** 2 * (X0 - Xr_m)) / (r * r * hr * hr)
+    hc = _hc(g, reg)
+    Drr = (_rf(g, reg, 1) ** 2 * (Xr_p - X0) / _hf(g, reg, 1) - _rf(g, reg) ** 2 * (X0 - Xr_m) / _hf(g, reg)) / (r * r * hc)
     Dtt = (_sf(g, reg, 1) * (Xt_p - X0) - _sf(g, reg) * (X0 - Xt_m)) / (r * r * s * ht * ht)
     Dpp = (Xp_p - 2.0 * X0 + Xp_m) / (r * r * s * s * hp * hp)
     W_k = 0.5 * (view(W, reg) + view(W, reg, 1, 0, 0))
@@ -221,7 +239,7 @@ def rate_up(g, U, A, P, D, f, nu, chi):
     ar, at, ap = advecting(g, PH, A)
     br = _avg(W, reg, NB[(PH, R)])
     bt = _avg(Y, reg, NB[(PH, TH)])
-    adv = (ar * (Xr_p - Xr_m) / (2 * hr) + at * (Xt_p - Xt_m) / (2 * r * ht)
+    adv = (ar * (Xr_p - Xr_m) / (2 * hc) + at * (Xt_p - Xt_m) / (2 * r * ht)
            + ap * (Xp_p - Xp_m) / (2 * r * s * hp) + (ap * br + ap * bt * c / s) / r)
     gradP = (view(P, reg) - view(P, reg, 0, 0, -1)) / (r * s * hp)
     gdiv = (view(D, reg) - view(D, reg, 0, 0, -1)) / (r * s * hp)
@@ -251,31 +269,34 @@ def factor(g, loc, d, A, dt, nu, chi, gamma=(-1.0, -1.0)):
         u_th along t: nu(-1/(r^2 s^2) + 2c/(r^2 s^2) d_th(s .)) + (2chi)^-1 r^-1 d_th((r s)^-1 d_th(s .))
         u_ph along p: -nu/(r^2 s^2) + (2chi)^-1 (r s)^-2 d_phph."""
     reg = g.region(loc)
-    hr, ht, hp = g.hr, g.hth, g.hph
+    ht, hp = g.hth, g.hph
     R1 = g.R1
     ar, at, ap = advecting(g, loc, A)
     r = _rf(g, reg) if loc == R else _rc(g, reg)
     s = _sf(g, reg) if loc == TH else _sc(g, reg)
     zero = 0.0
     if d == "r":
+        # local spacings: h of the row's point, and of the half points on either side
         if loc == R:
-            cp_d = _rc(g, reg) ** 2 / (r * r * hr * hr)
-            cm_d = _rc(g, reg, -1) ** 2 / (r * r * hr * hr)
+            h, hp_, hm_ = _hf(g, reg), _hc(g, reg), _hc(g, reg, -1)
+            cp_d = _rc(g, reg) ** 2 / (r * r * h * hp_)
+            cm_d = _rc(g, reg, -1) ** 2 / (r * r * h * hm_)
         else:
-            cp_d = _rf(g, reg, 1) ** 2 / (r * r * hr * hr)
-            cm_d = _rf(g, reg) ** 2 / (r * r * hr * hr)
-        cm = nu * cm_d + ar / (2 * hr)
+            h, hp_, hm_ = _hc(g, reg), _hf(g, reg, 1), _hf(g, reg)
+            cp_d = _rf(g, reg, 1) ** 2 / (r * r * h * hp_)
+            cm_d = _rf(g, reg) ** 2 / (r * r * h * hm_)
+        cm = nu * cm_d + ar / (2 * h)
         c0 = -nu * (cp_d + cm_d) + zero * ar
-        cp = nu * cp_d - ar / (2 * hr)
+        cp = nu * cp_d - ar / (2 * h)
         if loc == R:
-            cm = cm - nu * 2.0 * _rf(g, reg, -1) ** 2 / (r ** 3 * 2 * hr)
-            cp = cp + nu * 2.0 * _rf(g, reg, 1) ** 2 / (r ** 3 * 2 * hr)
+            cm = cm - nu * 2.0 * _rf(g, reg, -1) ** 2 / (r ** 3 * 2 * h)
+            cp = cp + nu * 2.0 * _rf(g, reg, 1) ** 2 / (r ** 3 * 2 * h)
             c0 = c0 - nu * 2.0 / (r * r)
             k = 1.0 / (2 * chi)
-            cm = cm + k * _rf(g, reg, -1) ** 2 / (_rc(g, reg, -1) ** 2 * hr * hr)
-            c0 = c0 - k * (_rf(g, reg) ** 2 / (_rc(g, reg) ** 2 * hr * hr)
-                           + _rf(g, reg) ** 2 / (_rc(g, reg, -1) ** 2 * hr * hr))
-            cp = cp + k * _rf(g, reg, 1) ** 2 / (_rc(g, reg) ** 2 * hr * hr)
+            cm = cm + k * _rf(g, reg, -1) ** 2 / (_rc(g, reg, -1) ** 2 * hm_ * h)
+            c0 = c0 - k * (_rf(g, reg) ** 2 / (_rc(g, reg) ** 2 * hp_ * h)
+                           + _rf(g, reg) ** 2 / (_rc(g, reg, -1) ** 2 * hm_ * h))
+            cp = cp + k * _rf(g, reg, 1) ** 2 / (_rc(g, reg) ** 2 * hp_ * h)
     elif d == "t":
         if loc == TH:
             cp_d = _sc(g, reg) / (R1 * R1 * s * ht * ht)

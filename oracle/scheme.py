@@ -76,6 +76,9 @@ class Params:
     step4: bool = False
     step4_eps: float = 1e-8
     step4_tol: float = 1e-13
+    # radii of the 2 Nr + 1 radial half points (faces at even, centres at odd
+    # positions; grid.py); None = uniform radial grid
+    r_half: Optional[tuple] = None
 
 
 def _time_fn(tid, t):
@@ -103,7 +106,7 @@ class Level:
 class Oracle:
     def __init__(self, prm: Params, exchange=True):
         self.prm = prm
-        self.g = Grid(prm.R1, prm.R2, prm.Nr, prm.Nth, prm.Nph, prm.overlap)
+        self.g = Grid(prm.R1, prm.R2, prm.Nr, prm.Nth, prm.Nph, prm.overlap, prm.r_half)
         # exchange=False: a single-patch problem with frozen boundary values
         self.tables = xch.ExchangeTables(self.g) if exchange else None
         g = self.g
@@ -201,7 +204,8 @@ class Oracle:
         fac = {}
         for loc in (C, R, TH, PH):
             nu = prm.kappa if loc == C else prm.Pr
-            gam = (xch.robin_ghost(*prm.Tbc_in, g.hr)[0], xch.robin_ghost(*prm.Tbc_out, g.hr)[0])
+            gam = (xch.robin_ghost(*prm.Tbc_in, float(g.h_f(0)))[0],
+                   xch.robin_ghost(*prm.Tbc_out, float(g.h_f(g.Nr)))[0])
             fac[loc] = {d: ops.factor(g, loc, d, A, prm.dt, nu, prm.chi, gam) for d in "rtp"}
         return fac
 

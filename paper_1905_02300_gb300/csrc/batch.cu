@@ -194,21 +194,47 @@ __global__ void kb_resid_u(const ShellDev<R> *sh, WorkMap map, int cap, int sys,
   }
 }
 
-// Norm shares are summed per thread while the CTA stays on one shell and
-// flushed (one atomic per warp) when its work moves to another shell.
+// Pressure updates; each block's norm shares are reduced in the CTA and
+// written to parts[w] (w the block's index in the map, so a shell's blocks are
+// the contiguous range offs[s] .. offs[s+1]); kb_norm_sum adds them up per
+// shell.  No atomics here: a CTA's successive blocks belong to different
+// shells, and per-shell atomics from every CTA piled up on a few addresses.
+constexpr int kPresTpb = 128;
 template <typename R>
-__global__ void kb_pressure(const ShellDev<R> *sh, WorkMap map, int cap, int sys) {
-  typename Cmp<R>::type part = 0;
-  int cur = -1;
+__global__ void __launch_bounds__(kPresTpb) kb_pressure(const ShellDev<R> *sh, WorkMap map, int cap, int sys,
+                                                        double *parts) {
+  using V = typename Cmp<R>::type;
+  __shared__ V ws[kPresTpb];
   YS_BATCH_LOOP(map, cap)
-  if (s != cur) {
-    if (cur >= 0) bd::norm_flush(part, sh[cur].S.dcs[CS_VOL], &sh[cur].norm[sys == 1 ? 4 : 8]);
-    part = 0;
-    cur = s;
+  ws[threadIdx.x] = bd::body_pressure(D.S, sys, it, n, 3, bx, by);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    V v = ws[threadIdx.x];
+    for (int u = threadIdx.x + 32; u < kPresTpb; u += 32) v += ws[u];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (threadIdx.x == 0) parts[w] = (double)v;
   }
-  part += bd::body_pressure(D.S, sys, it, n, 3, bx, by);
+  __syncthreads();
   }
-  if (cur >= 0) bd::norm_flush(part, sh[cur].S.dcs[CS_VOL], &sh[cur].norm[sys == 1 ? 4 : 8]);
+}
+
+// norm[s][slot] += CS_VOL(s) * sum of parts over shell s's blocks: one CTA a shell
+template <typename R>
+__global__ void kb_norm_sum(const ShellDev<R> *sh, WorkMap map, int cap, int slot, const double *parts) {
+  __shared__ double ws[8];
+  const int s = blockIdx.x;
+  if (s >= cap) return;
+  const int w0 = map.offs[s], w1 = map.offs[s + 1];
+  double t = 0.0;
+  for (int w = w0 + threadIdx.x; w < w1; w += blockDim.x) t += parts[w];
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0 && w1 > w0) {
+    double v = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v += ws[k];
+    if (v != 0.0) atomicAdd(&sh[s].norm[slot], v * sh[s].S.dcs[CS_VOL]);
+  }
 }
 
 template <typename R>
@@ -297,6 +323,8 @@ struct ys_batch {
   int *maps = nullptr;            // M_NUM x (2 cap + 1) ints (device)
   int *active = nullptr;          // cap ints (device)
   double *norms = nullptr;        // cap x YS_NFIELDS (device)
+  double *parts = nullptr;        // per-block pressure norm shares (device), parts_n doubles
+  long parts_n = 0;
   std::vector<int> hmaps;
   cudaGraphExec_t exec = nullptr;
   bool dirty = true;              // maps / descriptors need upload
@@ -368,6 +396,25 @@ int upload(ys_batch *b) {
       if (acc > 0x7fffffffL) return YS_EINVAL;
     }
     offs[cap] = (int)acc;
+  }
+  // per-block pressure norm shares: grow the buffer to the pressure map's
+  // blocks; the captured graph holds the old pointer, so drop it
+  const long need = b->hmaps[(size_t)M_RC * (2 * cap + 1) + cap];
+  if (need > b->parts_n) {
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    cudaFree(b->parts);
+    b->parts = nullptr;
+    b->parts_n = 0;
+    if (cudaMalloc(&b->parts, sizeof(double) * (size_t)need) != cudaSuccess) {
+      cudaGetLastError();
+      b->parts = nullptr;
+      return YS_ENOMEM;
+    }
+    b->parts_n = need;
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
   }
   cudaMemcpyAsync(b->shells, hd.data(), sizeof(ShellDev<R>) * cap, cudaMemcpyHostToDevice, b->stream);
   cudaMemcpyAsync(b->active, act.data(), sizeof(int) * cap, cudaMemcpyHostToDevice, b->stream);
@@ -451,8 +498,9 @@ void enqueue_step(ys_batch *b) {
         ++nl;
         solve(LR + comp, F_U1R + comp + o);
       }
-      kb_pressure<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_RC), cap, sys);
-      ++nl;
+      kb_pressure<R><<<g128, kPresTpb, 0, st>>>(sh, map_of(b, M_RC), cap, sys, b->parts);
+      kb_norm_sum<R><<<cap, 256, 0, st>>>(sh, map_of(b, M_RC), cap, sys == 1 ? 4 : 8, b->parts);
+      nl += 2;
     }
     kb_exchange<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_RING), cap, XP);
     ++nl;
@@ -667,6 +715,7 @@ int ys_batch_destroy(ys_batch *b) {
   cudaFree(b->maps);
   cudaFree(b->active);
   cudaFree(b->norms);
+  cudaFree(b->parts);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return YS_OK;
