@@ -33,6 +33,7 @@ import math
 import os
 from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
+from typing import Optional
 
 import numpy as np
 
@@ -67,6 +68,9 @@ class Spec:
     Nth: int
     Nph: int
     overlap: int = 2
+    # radii of the 2 Nr + 1 radial half points (faces at even, centres at odd
+    # positions); None = uniform radial grid
+    r_half: Optional[tuple] = None
 
     @property
     def hr(self):
@@ -105,10 +109,24 @@ class Spec:
         ri = np.arange(Nr + 1 if loc == "r" else Nr, dtype=np.float64)
         tj = np.arange(Nt + 1 if loc == "t" else Nt, dtype=np.float64)
         pk = np.arange(Np + 1 if loc == "p" else Np, dtype=np.float64)
-        r = self.R1 + (ri + (0.0 if loc == "r" else 0.5)) * self.hr
+        if self.r_half is None:
+            r = self.R1 + (ri + (0.0 if loc == "r" else 0.5)) * self.hr
+        else:
+            r = np.asarray(self.r_half, dtype=np.float64)[2 * ri.astype(int) + (0 if loc == "r" else 1)]
         th = self.th0 + (tj + (0.0 if loc == "t" else 0.5)) * self.hth
         ph = self.ph0 + (pk + (0.0 if loc == "p" else 0.5)) * self.hph
         return r[None, :, None, None], th[None, None, :, None], ph[None, None, None, :]
+
+
+def stretched_radii(R1, R2, Nr, beta):
+    """Radii of the 2 Nr + 1 half points of a smoothly stretched radial grid:
+    r(xi) = R1 + (R2 - R1) (xi - beta sin(2 pi xi) / (2 pi)) at xi = m / (2 Nr),
+    cells finer near both walls (spacing ratio (1 - beta) / (1 + beta) between
+    the walls and mid-shell), 0 <= beta < 1."""
+    xi = np.arange(2 * Nr + 1) / (2.0 * Nr)
+    r = R1 + (R2 - R1) * (xi - beta * np.sin(2.0 * math.pi * xi) / (2.0 * math.pi))
+    r[0], r[-1] = R1, R2
+    return tuple(r.tolist())
 
 
 def local_basis(th, ph):

@@ -200,9 +200,10 @@ class GradCurlShell(W.Exact):
         return [U[m] + g_[m] for m in range(3)], P, Th
 
 
-def _operator_errors(N):
-    g = Grid(0.5, 1.0, N, N, 3 * N)
-    spec = W.Spec(0.5, 1.0, N, N, 3 * N)
+def _operator_errors(N, beta=None):
+    rh = None if beta is None else W.stretched_radii(0.5, 1.0, N, beta)
+    g = Grid(0.5, 1.0, N, N, 3 * N, r_half=rh)
+    spec = W.Spec(0.5, 1.0, N, N, 3 * N, r_half=rh)
     ex = GradCurlShell(0.5, 1.0, 1.0, 1.0)
     aex = W.TrigShell(0.5, 1.0, 1.0, 1.0)
     t = 0.3
@@ -246,11 +247,49 @@ def test_discrete_operators_converge_to_continuous_at_second_order():
         assert ratio > 3.3, (k, e1[k], e2[k], ratio)
 
 
+def test_stretched_radial_grid_operators_converge_at_second_order():
+    """Sec. 4 (centred differences on a non-uniform grid): on a smoothly
+    stretched radial grid (cells 3x finer at the walls than mid-shell) every
+    discrete operator still converges to its continuous value at second order."""
+    e1, e2 = _operator_errors(12, 0.5), _operator_errors(24, 0.5)
+    for k in e1:
+        ratio = e1[k] / max(e2[k], 1e-300)
+        assert ratio > 3.3, (k, e1[k], e2[k], ratio)
+
+
+def test_uniform_half_points_give_the_uniform_operators():
+    """A radial grid given by the half points of the uniform grid is the
+    uniform grid: the same rates and line factors to rounding."""
+    N = 8
+    rh = tuple((0.5 + 0.5 * np.arange(2 * N + 1) / (2 * N)).tolist())
+    g0, g1 = Grid(0.5, 1.0, N, 12, 36), Grid(0.5, 1.0, N, 12, 36, r_half=rh)
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=g0.shape)
+    U = [rng.normal(size=g0.shape) for _ in range(3)]
+    A = [rng.normal(size=g0.shape) for _ in range(3)]
+    P, D, Tb = (rng.normal(size=g0.shape) for _ in range(3))
+    zc = np.zeros(view(g0.zeros(), g0.region(C)).shape)
+    for g in (g0, g1):
+        g.out = [ops.rate_T(g, X, A, zc), ops.divergence(g, U),
+                 ops.rate_ur(g, U, A, P, D, Tb, 0.0, 0.7, 1.3, 2.0), ops.rate_ut(g, U, A, P, D, 0.0, 0.7, 1.3),
+                 ops.rate_up(g, U, A, P, D, 0.0, 0.7, 1.3)]
+        g.out += [np.stack(ops.factor(g, loc, "r", A, 0.01, 0.7, 1.3)) for loc in (C, R, TH, PH)]
+        g.out.append(g.weight(R))
+        g.out.append(g.weight(C))
+    for a, b in zip(g0.out, g1.out):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
 def test_factors_hold_the_one_direction_terms_of_the_rates():
     """(I - dt/2 Ahat_d) y = y - dt/2 (d-part of the rate) for data varying
     along d only; theta/phi diffusion carries the modified metric
     r^2/R1^2 and r^2 sin^2(theta)/(R1^2 sin^2 theta_1) (Sec. 3.2)."""
-    g = Grid(0.5, 1.0, 8, 12, 36)
+    for beta in (None, 0.5):
+        _factor_rate_consistency(None if beta is None else W.stretched_radii(0.5, 1.0, 8, beta))
+
+
+def _factor_rate_consistency(rh):
+    g = Grid(0.5, 1.0, 8, 12, 36, r_half=rh)
     dt = 0.02
     rng = np.random.default_rng(5)
     ii, jj, kk = np.arange(-1, g.Nr + 1), np.arange(-1, g.Nth + 1), np.arange(-1, g.Nph + 1)
@@ -435,10 +474,12 @@ def test_heat_first_iterate_stable_for_large_dt():
 
 
 # ------------------------------------------------------------------ convergence
-def _run(kind, N, dt, nsteps, tol=1e-9, maxit=40, mode="additive", R1=0.5, R2=1.0, Pr=1.0, Ra=1e3):
-    prm = Params(R1=R1, R2=R2, Pr=Pr, Ra=Ra, dt=dt, Nr=N, Nth=N, Nph=3 * N, schwarz_tol=tol, schwarz_mode=mode)
+def _run(kind, N, dt, nsteps, tol=1e-9, maxit=40, mode="additive", R1=0.5, R2=1.0, Pr=1.0, Ra=1e3, beta=None):
+    rh = None if beta is None else W.stretched_radii(R1, R2, N, beta)
+    prm = Params(R1=R1, R2=R2, Pr=Pr, Ra=Ra, dt=dt, Nr=N, Nth=N, Nph=3 * N, schwarz_tol=tol, schwarz_mode=mode,
+                 r_half=rh)
     o = Oracle(prm)
-    spec = W.Spec(R1, R2, N, N, 3 * N)
+    spec = W.Spec(R1, R2, N, N, 3 * N, r_half=rh)
     ex = W.EXACT[kind](R1, R2, Pr, Ra)
     f0, fm = W.sample_fields(ex, spec, 0.0), W.sample_fields(ex, spec, -dt)
     o.set_fields(0, f0["T"], f0["ur"], f0["uth"], f0["uph"], f0["p"])
@@ -478,6 +519,30 @@ def test_space_convergence_second_order(kind):
             continue            # the exact u_r is zero for this solution
         order = math.log(errs[0][k] / errs[1][k]) / math.log(20 / 12)
         assert order > 1.7, (k, errs, order)
+
+
+def test_stretched_radial_grid_space_convergence_second_order():
+    """The whole scheme on a smoothly stretched radial grid (cells 3x finer at
+    the walls than mid-shell): second order in space on the manufactured
+    solution, as on the uniform grid."""
+    errs = []
+    for N in (12, 20):
+        o, spec, ex = _run("trig", N, 5e-4, 4, beta=0.5)
+        errs.append(_errors(o, spec, ex))
+    for k in errs[0]:
+        if k == "ur":
+            continue            # the exact u_r is zero for this solution
+        order = math.log(errs[0][k] / errs[1][k]) / math.log(20 / 12)
+        assert order > 1.7, (k, errs, order)
+
+
+def test_stretched_radial_heat_closed_form_second_order():
+    """The radial heat closed form on the stretched grid: second order."""
+    errs = []
+    for N, dt in ((12, 2e-3), (24, 5e-4)):
+        o, spec, ex = _run("radial_heat", N, dt, int(round(0.008 / dt)), Pr=1.0, Ra=0.0, beta=0.5)
+        errs.append(_errors(o, spec, ex)["T"])
+    assert math.log(errs[0] / errs[1]) / math.log(2.0) > 1.7, errs
 
 
 def test_radial_heat_closed_form_second_order():
