@@ -99,6 +99,17 @@ typedef struct {
      mixed form keeps its conductive-profile deviation variables only for
      Dirichlet walls. */
   double Tbc_inner_a, Tbc_inner_b, Tbc_outer_a, Tbc_outer_b;
+  /* non-uniform radial grid (Sec. 4: centred differences on a non-uniform
+     grid): NULL = uniform (default), else 2 Nr + 1 strictly increasing radii of
+     the radial half points, faces at even and cell centres at odd positions,
+     r_half[0] = R1 and r_half[2 Nr] = R2 (to 1e-12 (R2 - R1)).  A half-cell
+     difference divides by the distance of its two points, a whole-cell
+     centred difference by twice the local spacing (the cell width at a
+     centre, the centre distance at a face); averages of radial neighbours stay
+     arithmetic means (the stretched-coordinate form, second order for smooth
+     stretchings).  ys_create_ex copies the array; ys_submit and
+     ys_factor_solve_static take uniform grids only (YS_EINVAL otherwise). */
+  const double *r_half;
 } ys_params;
 
 /* Fill *p with defaults (all sizes zero, chi = 1, overlap = 2, FP64,
@@ -215,7 +226,7 @@ size_t ys_device_bytes(ys_ctx *c);
  * x in the layout of the unknown (boundary entries of rhs are ignored, those
  * of x are set to 0).  Work is queued on `stream` (a cudaStream_t, NULL = the
  * legacy default stream).
- * Scratch: one static device array of 5 * 2^18 + 10 * 264 doubles (about
+ * Scratch: one static device array of 5 * 2^18 + 14 * 264 doubles (about
  * 10.5 MB) that every GPU which loads the library holds until the process
  * exits.  Grids are limited to Nr, Nth, Nph <= 256 and at most 2^18 padded
  * elements per field (e.g. 32 x 32 x 96 per patch fits, 48 x 48 x 144 does
@@ -281,10 +292,11 @@ int ys_batch_destroy(ys_batch *b);
 typedef struct ys_server ys_server;
 
 int ys_server_create(size_t hbm_budget_bytes, int max_slots, ys_server **out);
-/* Queue a simulation: parameters (additive Schwarz, schwarz_tol 0), initial
- * fields packed as [T | ur | uth | uph | p] in the field layouts above
- * (copied), number of steps.  *ticket identifies it.  YS_EBUSY when the queue
- * is full; YS_EINVAL if it can never fit the budget. */
+/* Queue a simulation: parameters (additive Schwarz, schwarz_tol 0, uniform
+ * radial grid: r_half NULL), initial fields packed as [T | ur | uth | uph | p]
+ * in the field layouts above (copied), number of steps.  *ticket identifies
+ * it.  YS_EBUSY when the queue is full; YS_EINVAL if it can never fit the
+ * budget or the parameters are outside these limits. */
 int ys_submit(ys_server *s, const ys_params *p, const double *init_fields, int n_steps, int n_schwarz,
               uint64_t *ticket);
 /* State of a request: *state = 0 queued, 1 running, 2 done, 3 failed.  Returns

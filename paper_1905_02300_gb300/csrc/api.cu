@@ -489,7 +489,7 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   *out = nullptr;
   int rc = validate(p);
   if (rc) return rc;
-  GridSpec gs{p->R1, p->R2, p->Nr, p->Nth, p->Nph, p->overlap};
+  GridSpec gs{p->R1, p->R2, p->Nr, p->Nth, p->Nph, p->overlap, p->r_half};
   GridGeo G;
   if (make_grid(gs, G)) return YS_EINVAL;
   std::vector<XEntry> xt[XNUM];
@@ -501,6 +501,8 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   if (!c) return YS_ENOMEM;
   c->prm = *p;
   c->geo = G;
+  // the context owns its radial half points (the caller's array may go away)
+  c->prm.r_half = c->geo.rh.empty() ? nullptr : c->geo.rh.data() + kGhostHalf;
   const bool mixed = (p->precision == YS_MIXED);
   Layout &L = c->L;
   L.Nr = p->Nr;
@@ -523,14 +525,17 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   if (deviation) {
     double Ac = (p->T_inner - p->T_outer) / (1.0 / p->R1 - 1.0 / p->R2);
     double Bc = p->T_inner - Ac / p->R1;
-    for (int i = 0; i < p->Nr; ++i) Tc[i + 1] = Ac / (p->R1 + (i + 0.5) * G.hr) + Bc;
+    for (int i = 0; i < p->Nr; ++i) Tc[i + 1] = Ac / G.rc(i) + Bc;
     Tc[0] = 2.0 * p->T_inner - Tc[1];             // reflection ghosts, as for T
     Tc[p->Nr + 1] = 2.0 * p->T_outer - Tc[p->Nr];
+    // the discrete operators of the residuals applied to T_c (local radial
+    // spacings), and the hydrostatic pressure of its buoyancy
     for (int i = 0; i < p->Nr; ++i) {
-      double rc = p->R1 + (i + 0.5) * G.hr, rfp = p->R1 + (i + 1) * G.hr, rf0 = p->R1 + i * G.hr;
-      Tlap[i] = (rfp * rfp * (Tc[i + 2] - Tc[i + 1]) - rf0 * rf0 * (Tc[i + 1] - Tc[i])) / (rc * rc * G.hr * G.hr);
-      Tdr[i] = (Tc[i + 2] - Tc[i]) / (2.0 * G.hr);
-      if (i > 0) pc[i] = pc[i - 1] + G.hr * p->Pr * p->Ra * 0.5 * (Tc[i] + Tc[i + 1]);
+      double rc = G.rc(i), rfp = G.rf(i + 1), rf0 = G.rf(i);
+      Tlap[i] = (rfp * rfp * (Tc[i + 2] - Tc[i + 1]) / G.hf(i + 1) - rf0 * rf0 * (Tc[i + 1] - Tc[i]) / G.hf(i)) /
+                (rc * rc * G.hc(i));
+      Tdr[i] = (Tc[i + 2] - Tc[i]) / (2.0 * G.hc(i));
+      if (i > 0) pc[i] = pc[i - 1] + G.hf(i) * p->Pr * p->Ra * 0.5 * (Tc[i] + Tc[i + 1]);
     }
   }
   size_t Rsz = mixed ? sizeof(float) : sizeof(double);
@@ -644,10 +649,10 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
     // patch, their squares' sum and the whole boundary's area
     double wsq = 0.0, area = 0.0;
     for (int i = 0; i < p->Nr; ++i) {
-      const double rc = p->R1 + (i + 0.5) * G.hr;
+      const double rc = G.rc(i), hc = G.hc(i);
       for (int side = 0; side < 2; ++side) {
-        const double wt = rc * std::sin(G.th0 + (side ? p->Nth : 0) * G.ht) * G.hr * G.hp;
-        const double wp = rc * G.hr * G.ht;
+        const double wt = rc * std::sin(G.th0 + (side ? p->Nth : 0) * G.ht) * hc * G.hp;
+        const double wp = rc * hc * G.ht;
         wsq += p->Nph * wt * wt + p->Nth * wp * wp;
         area += p->Nph * wt + p->Nth * wp;
       }
@@ -681,6 +686,10 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   S.irf = metric + 7 * len + pad;
   S.isc = metric + 8 * len + pad;
   S.isf = metric + 9 * len + pad;
+  S.hc = metric + 10 * len + pad;
+  S.ihc = metric + 11 * len + pad;
+  S.nrc = metric + 12 * len + pad;
+  S.nrf = metric + 13 * len + pad;
   S.ihr = 1.0 / G.hr;
   S.iht = 1.0 / G.ht;
   S.ihp = 1.0 / G.hp;
@@ -691,7 +700,7 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   S.T_out = p->T_outer;
   {
     const double a[2] = {p->Tbc_inner_a, p->Tbc_outer_a}, b[2] = {p->Tbc_inner_b, p->Tbc_outer_b};
-    shell_set_T_walls(S, a, b, G.hr);
+    shell_set_T_walls(S, a, b, G.hf(0), G.hf(p->Nr));
   }
   S.Tc_lap = nullptr;
   S.Tc_dr = nullptr;

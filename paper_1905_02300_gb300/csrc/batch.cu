@@ -902,6 +902,7 @@ int ys_submit(ys_server *S, const ys_params *p, const double *init_fields, int n
               uint64_t *ticket) {
   if (!S || !p || !init_fields || n_steps < 1 || n_schwarz < 1 || !ticket) return YS_EINVAL;
   if (p->schwarz_mode != YS_ADDITIVE || p->schwarz_tol != 0.0) return YS_EINVAL;
+  if (p->r_half) return YS_EINVAL;   // queued requests keep no copy of the radii: uniform grids only
   std::unique_lock<std::mutex> lk(S->mu);
   if (!S->batch) {
     // the first request fixes the batch precision and iteration count

@@ -119,7 +119,7 @@ __device__ __forceinline__ FF divh_ff(const Shell &S, const float *ri, const flo
   const FF ir = ff_mt(S, MT_IRC, i), is = ff_mt(S, MT_ISC, j);
   const FF rfp = ff_mt(S, MT_RF, i + 1), rf0 = ff_mt(S, MT_RF, i);
   FF d_r = ff_sub(ff_mul(ff_mul(rfp, rfp), ff_H(ri, rn, q + L.SI)), ff_mul(ff_mul(rf0, rf0), ff_H(ri, rn, q)));
-  d_r = ff_mul(d_r, ff_mul(ff_mul(ir, ir), ff_cs(S, CS_IHR)));
+  d_r = ff_mul(d_r, ff_mul(ff_mul(ir, ir), ff_mt(S, MT_IHC, i)));
   const FF irs = ff_mul(ir, is);
   FF d_t = ff_sub(ff_mul(ff_mt(S, MT_SF, j + 1), ff_H(ti, tn, q + L.P)), ff_mul(ff_mt(S, MT_SF, j), ff_H(ti, tn, q)));
   d_t = ff_mul(d_t, ff_mul(irs, ff_cs(S, CS_IHT)));
@@ -1248,7 +1248,7 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
             dst[qq] = (R)(o[u] + x);
             const int row = ln.m0 + mm;
             if (dir == DR) {
-              const V t = ((loc == LR) ? mt<V>(S, MT_RF) : mt<V>(S, MT_RC))[row] * x;
+              const V t = ((loc == LR) ? mt<V>(S, MT_NRF) : mt<V>(S, MT_NRC))[row] * x;
               acc += t * t;
             } else if (dir == DT) {
               acc += ((loc == LT) ? mt<V>(S, MT_SF) : mt<V>(S, MT_SC))[row] * x * x;
@@ -1270,7 +1270,8 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
       }
     }
     if (final) {
-      const double r = (loc == LR) ? S.rf[ln.i] : S.rc[ln.i];
+      // r sqrt(h / h_r): the radial part of the point's midpoint-rule weight
+      const double r = (loc == LR) ? S.nrf[ln.i] : S.nrc[ln.i];
       const double sn = (loc == LT) ? S.sf[ln.j] : S.sc[ln.j];
       const double w = (dir == DR) ? sn : (dir == DT) ? r * r : r * r * sn;
       contrib = (double)acc * (w * S.dcs[CS_VOL]);
@@ -1516,7 +1517,7 @@ __device__ __forceinline__ void body_solve_phi_scan(Shell S, int loc, int final,
           break;
       }
       if (final) {
-        const double r = (loc == LR) ? S.rf[i] : S.rc[i];
+        const double r = (loc == LR) ? S.nrf[i] : S.nrc[i];   // r sqrt(h / h_r)
         const double sn = (loc == LT) ? S.sf[j] : S.sc[j];
         scale = r * r * sn * S.dcs[CS_VOL];
       }

@@ -10,10 +10,40 @@ namespace ys {
 
 static const double kPi = 3.14159265358979323846;
 
+double GridGeo::rhalf(int m) const {
+  const int lo = -kGhostHalf, hi = 2 * Nr + kGhostHalf;
+  if (m < lo) return rh[0] - (lo - m) * (rh[1] - rh[0]);
+  if (m > hi) return rh.back() + (m - hi) * (rh.back() - rh[rh.size() - 2]);
+  return rh[m + kGhostHalf];
+}
+double GridGeo::rc(int i) const { return rh.empty() ? R1 + (i + 0.5) * hr : rhalf(2 * i + 1); }
+double GridGeo::rf(int i) const { return rh.empty() ? R1 + i * hr : rhalf(2 * i); }
+double GridGeo::hc(int i) const { return rh.empty() ? hr : rf(i + 1) - rf(i); }
+double GridGeo::hf(int i) const { return rh.empty() ? hr : rc(i) - rc(i - 1); }
+
 int make_grid(const GridSpec &g, GridGeo &out) {
   if (!(g.R1 > 0.0) || !(g.R2 > g.R1)) return 1;
   if (g.overlap < 1 || g.Nth <= 2 * g.overlap + 4) return 1;
   out.hr = (g.R2 - g.R1) / g.Nr;
+  out.R1 = g.R1;
+  out.Nr = g.Nr;
+  out.rh.clear();
+  if (g.r_half) {
+    // 2 Nr + 1 strictly increasing radii from R1 to R2; ghosts mirrored about the walls
+    const int n = 2 * g.Nr + 1;
+    const double tol = 1e-12 * (g.R2 - g.R1);
+    for (int m = 0; m < n; ++m)
+      if (!std::isfinite(g.r_half[m]) || (m > 0 && !(g.r_half[m] > g.r_half[m - 1]))) return 1;
+    if (std::fabs(g.r_half[0] - g.R1) > tol || std::fabs(g.r_half[n - 1] - g.R2) > tol) return 1;
+    out.rh.assign(n + 2 * kGhostHalf, 0.0);
+    for (int m = 0; m < n; ++m) out.rh[m + kGhostHalf] = g.r_half[m];
+    out.rh[kGhostHalf] = g.R1;
+    out.rh[kGhostHalf + n - 1] = g.R2;
+    for (int k = 1; k <= kGhostHalf; ++k) {
+      out.rh[kGhostHalf - k] = 2.0 * g.R1 - out.rh[kGhostHalf + k];
+      out.rh[kGhostHalf + n - 1 + k] = 2.0 * g.R2 - out.rh[kGhostHalf + n - 1 - k];
+    }
+  }
   out.ht = (kPi / 2) / (g.Nth - 2 * g.overlap);
   out.delta = g.overlap * out.ht;
   out.hp = (1.5 * kPi + 2 * out.delta) / g.Nph;
@@ -33,7 +63,7 @@ void make_metric(const GridSpec &g, const GridGeo &G, std::vector<double> &tab, 
   auto inv = [](double v) { return v != 0.0 ? 1.0 / v : 0.0; };
   for (int t = 0; t < n; ++t) {
     int i = t - pad;
-    double rc = g.R1 + (i + 0.5) * G.hr, rf = g.R1 + i * G.hr;
+    double rc = G.rc(i), rf = G.rf(i);
     double thc = G.th0 + (i + 0.5) * G.ht, thf = G.th0 + i * G.ht;
     tab[0 * n + t] = rc;
     tab[1 * n + t] = rf;
@@ -45,6 +75,12 @@ void make_metric(const GridSpec &g, const GridGeo &G, std::vector<double> &tab, 
     tab[7 * n + t] = inv(rf);
     tab[8 * n + t] = inv(std::sin(thc));
     tab[9 * n + t] = inv(std::sin(thf));
+    // radial spacing of cell i, its reciprocal, and the radial norm factors
+    // r sqrt(h / h_r) of centres and faces (r on a uniform grid)
+    tab[10 * n + t] = G.hc(i);
+    tab[11 * n + t] = inv(G.hc(i));
+    tab[12 * n + t] = rc * std::sqrt(G.hc(i) / G.hr);
+    tab[13 * n + t] = rf * std::sqrt(G.hf(i) / G.hr);
   }
 }
 
@@ -62,7 +98,11 @@ void make_rowcoef(const GridSpec &g, const GridGeo &G, const std::vector<double>
   auto irf = [&](int i) { return T(7, i); };
   auto isc = [&](int j) { return T(8, j); };
   auto isf = [&](int j) { return T(9, j); };
-  const double ihr = 1.0 / G.hr, iht = 1.0 / G.ht, ihp = 1.0 / G.hp;
+  const double iht = 1.0 / G.ht, ihp = 1.0 / G.hp;
+  // reciprocal radial spacings: of cell i (centre), and between the centres
+  // on either side of face i (both 1/h_r on a uniform radial grid)
+  auto ihc = [&](int i) { return 1.0 / G.hc(i); };
+  auto ihf = [&](int i) { return 1.0 / G.hf(i); };
   const double dt = ph.dt, nu = ph.nu, ka = ph.kappa, i2chi = ph.i2chi;
   const int NJ = g.Nth + 2;
   const size_t rows = (size_t)(g.Nr + 2) * NJ;
@@ -76,12 +116,12 @@ void make_rowcoef(const GridSpec &g, const GridGeo &G, const std::vector<double>
     for (int j = 0; j < g.Nth; ++j) {
       double *c = rec(RT_T, i, j);
       const double ir = irc(i), is = isc(j), ir2 = ir * ir;
-      c[T_RP] = 0.5 * dt * ka * rf(i + 1) * rf(i + 1) * ir2 * ihr * ihr;
-      c[T_RM] = 0.5 * dt * ka * rf(i) * rf(i) * ir2 * ihr * ihr;
+      c[T_RP] = 0.5 * dt * ka * rf(i + 1) * rf(i + 1) * ir2 * ihc(i) * ihf(i + 1);
+      c[T_RM] = 0.5 * dt * ka * rf(i) * rf(i) * ir2 * ihc(i) * ihf(i);
       c[T_TP] = 0.5 * dt * ka * sf(j + 1) * ir2 * is * iht * iht;
       c[T_TM] = 0.5 * dt * ka * sf(j) * ir2 * is * iht * iht;
       c[T_PP] = 0.5 * dt * ka * ir2 * is * is * ihp * ihp;
-      c[T_AR] = 0.125 * dt * ihr;
+      c[T_AR] = 0.125 * dt * ihc(i);
       c[T_AT] = 0.125 * dt * ir * iht;
       c[T_AP] = 0.125 * dt * ir * is * ihp;
       c[T_G0] = ph.Tc_lap ? dt * ka * ph.Tc_lap[i] : 0.0;
@@ -95,17 +135,17 @@ void make_rowcoef(const GridSpec &g, const GridGeo &G, const std::vector<double>
       const double ir = irf(i), is = isc(j), ir2 = ir * ir;
       const double rfp = rf(i + 1), rf0 = rf(i), rfm = rf(i - 1);
       const double icc = irc(i), icm = irc(i - 1);   // the two cells sharing face i
-      c[UR_RP] = 0.5 * dt * nu * rc(i) * rc(i) * ir2 * ihr * ihr;
-      c[UR_RM] = 0.5 * dt * nu * rc(i - 1) * rc(i - 1) * ir2 * ihr * ihr;
+      c[UR_RP] = 0.5 * dt * nu * rc(i) * rc(i) * ir2 * ihf(i) * ihc(i);
+      c[UR_RM] = 0.5 * dt * nu * rc(i - 1) * rc(i - 1) * ir2 * ihf(i) * ihc(i - 1);
       c[UR_TP] = 0.5 * dt * nu * sf(j + 1) * ir2 * is * iht * iht;
       c[UR_TM] = 0.5 * dt * nu * sf(j) * ir2 * is * iht * iht;
       c[UR_PP] = 0.5 * dt * nu * ir2 * is * is * ihp * ihp;
       // own values outside the Laplacian: the curvature term of the vector
       // Laplacian and the r-part of grad(div) across the two cells
-      const double G = 0.5 * dt * ihr * i2chi;
-      c[UR_O1] = 0.5 * dt * nu * ir2 * ir * ihr * rfp * rfp + G * rfp * rfp * icc * icc * ihr;
-      c[UR_O0] = -dt * nu * ir2 - G * rf0 * rf0 * (icc * icc + icm * icm) * ihr;
-      c[UR_OM] = -0.5 * dt * nu * ir2 * ir * ihr * rfm * rfm + G * rfm * rfm * icm * icm * ihr;
+      const double G = 0.5 * dt * ihf(i) * i2chi;
+      c[UR_O1] = 0.5 * dt * nu * ir2 * ir * ihf(i) * rfp * rfp + G * rfp * rfp * icc * icc * ihc(i);
+      c[UR_O0] = -dt * nu * ir2 - G * rf0 * rf0 * (icc * icc * ihc(i) + icm * icm * ihc(i - 1));
+      c[UR_OM] = -0.5 * dt * nu * ir2 * ir * ihf(i) * rfm * rfm + G * rfm * rfm * icm * icm * ihc(i - 1);
       // u_theta at (q + P, q, q - SI + P, q - SI): theta-part of grad(div)
       c[UR_GT1] = G * sf(j + 1) * icc * is * iht;
       c[UR_GT0] = -G * sf(j) * icc * is * iht;
@@ -114,11 +154,11 @@ void make_rowcoef(const GridSpec &g, const GridGeo &G, const std::vector<double>
       // u_phi differences (q + 1) - q and (q - SI + 1) - (q - SI)
       c[UR_GP1] = G * icc * is * ihp;
       c[UR_GPM1] = -G * icm * is * ihp;
-      c[UR_AR] = 0.25 * dt * ihr;
+      c[UR_AR] = 0.25 * dt * ihf(i);
       c[UR_AT] = 0.0625 * dt * ir * iht;
       c[UR_AP] = 0.0625 * dt * ir * is * ihp;
       c[UR_CV] = dt * ir / 32.0;
-      c[UR_GPR] = dt * ihr;
+      c[UR_GPR] = dt * ihf(i);
       c[UR_BY] = 0.25 * dt * ph.PrRa;
     }
 
@@ -129,8 +169,8 @@ void make_rowcoef(const GridSpec &g, const GridGeo &G, const std::vector<double>
       const double ir = irc(i), is = isf(j), cs = cf(j), ir2 = ir * ir;
       const double rfp = rf(i + 1), rf0 = rf(i);
       const double isj = isc(j), ism = isc(j - 1);   // the two cells sharing face j
-      c[UT_RP] = 0.5 * dt * nu * rfp * rfp * ir2 * ihr * ihr;
-      c[UT_RM] = 0.5 * dt * nu * rf0 * rf0 * ir2 * ihr * ihr;
+      c[UT_RP] = 0.5 * dt * nu * rfp * rfp * ir2 * ihc(i) * ihf(i + 1);
+      c[UT_RM] = 0.5 * dt * nu * rf0 * rf0 * ir2 * ihc(i) * ihf(i);
       c[UT_TP] = 0.5 * dt * nu * sc(j) * ir2 * is * iht * iht;
       c[UT_TM] = 0.5 * dt * nu * sc(j - 1) * ir2 * is * iht * iht;
       c[UT_PP] = 0.5 * dt * nu * ir2 * is * is * ihp * ihp;
@@ -141,14 +181,14 @@ void make_rowcoef(const GridSpec &g, const GridGeo &G, const std::vector<double>
       c[UT_OTM] = -E * sf(j - 1) + G * sf(j - 1) * ir * ism * iht;
       // u_r at (q + SI, q, q + SI - P, q - P): vector-Laplacian coupling and
       // r-part of grad(div)
-      const double a = 0.5 * dt * nu * ir2 * iht, b = 0.5 * dt * nu * cs * ir2 * ir * is * ihr;
-      c[UT_W1] = a + b * rfp * rfp + G * rfp * rfp * ir * ir * ihr;
-      c[UT_W0] = a - b * rf0 * rf0 - G * rf0 * rf0 * ir * ir * ihr;
-      c[UT_WM1] = -a + b * rfp * rfp - G * rfp * rfp * ir * ir * ihr;
-      c[UT_WM0] = -a - b * rf0 * rf0 + G * rf0 * rf0 * ir * ir * ihr;
+      const double a = 0.5 * dt * nu * ir2 * iht, b = 0.5 * dt * nu * cs * ir2 * ir * is * ihc(i);
+      c[UT_W1] = a + b * rfp * rfp + G * rfp * rfp * ir * ir * ihc(i);
+      c[UT_W0] = a - b * rf0 * rf0 - G * rf0 * rf0 * ir * ir * ihc(i);
+      c[UT_WM1] = -a + b * rfp * rfp - G * rfp * rfp * ir * ir * ihc(i);
+      c[UT_WM0] = -a - b * rf0 * rf0 + G * rf0 * rf0 * ir * ir * ihc(i);
       c[UT_GP1] = G * ir * isj * ihp;
       c[UT_GPM1] = -G * ir * ism * ihp;
-      c[UT_AR] = 0.0625 * dt * ihr;
+      c[UT_AR] = 0.0625 * dt * ihc(i);
       c[UT_AT] = 0.25 * dt * ir * iht;
       c[UT_AP] = 0.0625 * dt * ir * is * ihp;
       c[UT_CW] = 0.125 * dt * ir;
@@ -162,8 +202,8 @@ void make_rowcoef(const GridSpec &g, const GridGeo &G, const std::vector<double>
       double *c = rec(RT_UP, i, j);
       const double ir = irc(i), is = isc(j), cs = cc(j), ir2 = ir * ir;
       const double rfp = rf(i + 1), rf0 = rf(i);
-      c[UP_RP] = 0.5 * dt * nu * rfp * rfp * ir2 * ihr * ihr;
-      c[UP_RM] = 0.5 * dt * nu * rf0 * rf0 * ir2 * ihr * ihr;
+      c[UP_RP] = 0.5 * dt * nu * rfp * rfp * ir2 * ihc(i) * ihf(i + 1);
+      c[UP_RM] = 0.5 * dt * nu * rf0 * rf0 * ir2 * ihc(i) * ihf(i);
       c[UP_TP] = 0.5 * dt * nu * sf(j + 1) * ir2 * is * iht * iht;
       c[UP_TM] = 0.5 * dt * nu * sf(j) * ir2 * is * iht * iht;
       // the phi-part of grad(div) has the stencil of the phi-diffusion
@@ -172,16 +212,16 @@ void make_rowcoef(const GridSpec &g, const GridGeo &G, const std::vector<double>
       const double G = 0.5 * dt * i2chi * ir * is * ihp;
       const double a = 0.5 * dt * nu * ir2 * is * ihp, b = 0.5 * dt * nu * cs * ir2 * is * is * ihp;
       // u_r at (q + SI, q, q - 1 + SI, q - 1)
-      c[UP_W1] = a + G * rfp * rfp * ir2 * ihr;
-      c[UP_W0] = a - G * rf0 * rf0 * ir2 * ihr;
-      c[UP_WM1] = -a - G * rfp * rfp * ir2 * ihr;
-      c[UP_WM0] = -a + G * rf0 * rf0 * ir2 * ihr;
+      c[UP_W1] = a + G * rfp * rfp * ir2 * ihc(i);
+      c[UP_W0] = a - G * rf0 * rf0 * ir2 * ihc(i);
+      c[UP_WM1] = -a - G * rfp * rfp * ir2 * ihc(i);
+      c[UP_WM0] = -a + G * rf0 * rf0 * ir2 * ihc(i);
       // u_theta at (q + P, q, q - 1 + P, q - 1)
       c[UP_Y1] = b + G * sf(j + 1) * ir * is * iht;
       c[UP_Y0] = b - G * sf(j) * ir * is * iht;
       c[UP_YM1] = -b - G * sf(j + 1) * ir * is * iht;
       c[UP_YM0] = -b + G * sf(j) * ir * is * iht;
-      c[UP_AR] = 0.0625 * dt * ihr;
+      c[UP_AR] = 0.0625 * dt * ihc(i);
       c[UP_AT] = 0.0625 * dt * ir * iht;
       c[UP_AP] = 0.25 * dt * ir * is * ihp;
       c[UP_CW] = 0.125 * dt * ir;
@@ -195,12 +235,12 @@ void make_rowcoef(const GridSpec &g, const GridGeo &G, const std::vector<double>
     for (int j = 0; j < g.Nth; ++j) {
       double *c = rec(RT_DIV, i, j);
       const double ir = irc(i), is = isc(j);
-      c[DV_R1] = i2chi * rf(i + 1) * rf(i + 1) * ir * ir * ihr;
-      c[DV_R0] = i2chi * rf(i) * rf(i) * ir * ir * ihr;
+      c[DV_R1] = i2chi * rf(i + 1) * rf(i + 1) * ir * ir * ihc(i);
+      c[DV_R0] = i2chi * rf(i) * rf(i) * ir * ir * ihc(i);
       c[DV_T1] = i2chi * sf(j + 1) * ir * is * iht;
       c[DV_T0] = i2chi * sf(j) * ir * is * iht;
       c[DV_P] = i2chi * ir * is * ihp;
-      c[DV_W] = rc(i) * rc(i) * sc(j);
+      c[DV_W] = rc(i) * rc(i) * sc(j) * (G.hc(i) / G.hr);   // r^2 sin(theta) h / h_r
     }
 }
 
@@ -216,7 +256,9 @@ void make_faccoef(const GridSpec &g, const GridGeo &G, const std::vector<double>
   auto irf = [&](int i) { return T(7, i); };
   auto isc = [&](int j) { return T(8, j); };
   auto isf = [&](int j) { return T(9, j); };
-  const double ihr = 1.0 / G.hr, iht = 1.0 / G.ht, ihp = 1.0 / G.hp;
+  const double iht = 1.0 / G.ht, ihp = 1.0 / G.hp;
+  auto ihc = [&](int i) { return 1.0 / G.hc(i); };   // as in make_rowcoef
+  auto ihf = [&](int i) { return 1.0 / G.hf(i); };
   const int NJ = g.Nth + 2;
   const size_t rows = (size_t)(g.Nr + 2) * NJ;
   tab.assign((size_t)kFacTables * rows * FC_M, 0.0);
@@ -234,20 +276,23 @@ void make_faccoef(const GridSpec &g, const GridGeo &G, const std::vector<double>
           const double ir2 = ir * ir;
           double cm, c0, cp, ka;
           if (dir == DR) {
-            const double cp_d = (loc == LR) ? rc(i) * rc(i) * (ir2 * ihr * ihr) : rf(i + 1) * rf(i + 1) * (ir2 * ihr * ihr);
-            const double cm_d = (loc == LR) ? rc(i - 1) * rc(i - 1) * (ir2 * ihr * ihr) : rf(i) * rf(i) * (ir2 * ihr * ihr);
+            // h of the row's point and of the half points on either side
+            const double ih = (loc == LR) ? ihf(i) : ihc(i);
+            const double ihp_ = (loc == LR) ? ihc(i) : ihf(i + 1), ihm_ = (loc == LR) ? ihc(i - 1) : ihf(i);
+            const double cp_d = (loc == LR) ? rc(i) * rc(i) * (ir2 * ih * ihp_) : rf(i + 1) * rf(i + 1) * (ir2 * ih * ihp_);
+            const double cm_d = (loc == LR) ? rc(i - 1) * rc(i - 1) * (ir2 * ih * ihm_) : rf(i) * rf(i) * (ir2 * ih * ihm_);
             cm = nu * cm_d;
             c0 = -nu * (cp_d + cm_d);
             cp = nu * cp_d;
-            ka = 0.5 * ihr;
+            ka = 0.5 * ih;
             if (loc == LR) {
               const double rfm = rf(i - 1), rf0 = rf(i), rfp = rf(i + 1), irm = irc(i - 1), ic = irc(i);
-              cm -= nu * rfm * rfm * (ir2 * ir * ihr);
-              cp += nu * rfp * rfp * (ir2 * ir * ihr);
+              cm -= nu * rfm * rfm * (ir2 * ir * ih);
+              cp += nu * rfp * rfp * (ir2 * ir * ih);
               c0 -= nu * 2.0 * ir2;
-              cm += ph.i2chi * rfm * rfm * (irm * irm * ihr * ihr);
-              c0 -= ph.i2chi * (rf0 * rf0 * (ic * ic * ihr * ihr) + rf0 * rf0 * (irm * irm * ihr * ihr));
-              cp += ph.i2chi * rfp * rfp * (ic * ic * ihr * ihr);
+              cm += ph.i2chi * rfm * rfm * (irm * irm * ihm_ * ih);
+              c0 -= ph.i2chi * (rf0 * rf0 * (ic * ic * ihp_ * ih) + rf0 * rf0 * (irm * irm * ihm_ * ih));
+              cp += ph.i2chi * rfp * rfp * (ic * ic * ihp_ * ih);
             }
           } else if (dir == DT) {
             const double cp_d = (loc == LT) ? sc(j) * (ph.iR1sq * is * iht * iht) : sf(j + 1) * (ph.iR1sq * is * iht * iht);

@@ -9,10 +9,25 @@ namespace ys {
 struct GridSpec {
   double R1, R2;
   int Nr, Nth, Nph, overlap;
+  const double *r_half;   // 2 Nr + 1 radial half-point radii (faces even, centres odd), or null (uniform)
 };
 
+// Grid spacings and the radial positions.  hr is the uniform grid's radial
+// spacing (R2 - R1) / Nr, the reference of the norms' cell volume.  A
+// non-uniform radial grid keeps its half points in rh with kGhostHalf ghost
+// half points on either side, mirrored about the walls; positions beyond
+// them (used only by table padding) are extended linearly.
+constexpr int kGhostHalf = 4;
 struct GridGeo {
   double hr, ht, hp, delta, th0, ph0;
+  double R1 = 0.0;
+  int Nr = 0;
+  std::vector<double> rh;   // empty: uniform
+  double rhalf(int m) const;
+  double rc(int i) const;   // centre of radial cell i
+  double rf(int i) const;   // radial face i
+  double hc(int i) const;   // width of radial cell i, rf(i + 1) - rf(i)
+  double hf(int i) const;   // distance of the centres on either side of face i, rc(i) - rc(i - 1)
 };
 
 // 0 on success, 1 if the parameters do not define a valid patch

@@ -31,8 +31,8 @@ __global__ void k_walls(Shell S, State<R> s, int patch_mask) {
 // Algorithm step 4 (mass-flux correction).  Edge faces of a patch: theta
 // faces j = 0, Nth for every (i, k) and phi faces k = 0, Nph for every (i, j);
 // flux weight w = outward normal x face area from the discrete Gauss theorem
-// of the divergence: r_c sin(theta_f) h_r h_phi (theta faces), r_c h_r h_theta
-// (phi faces).  Thread e of the y = patch plane handles one edge face.
+// of the divergence: r_c sin(theta_f) h_c h_phi (theta faces), r_c h_c h_theta
+// (phi faces), h_c the radial cell width.  Thread e of the y = patch plane handles one edge face.
 __device__ __forceinline__ bool edge_face(const Shell &S, int p, long e, long &q, bool &theta, double &w) {
   const Layout &L = S.L;
   const long nt = 2L * L.Nr * L.Np, np = 2L * L.Nr * L.Nt;
@@ -42,7 +42,7 @@ __device__ __forceinline__ bool edge_face(const Shell &S, int p, long e, long &q
     const int i = (int)(rem / L.Np), k = (int)(rem % L.Np), j = side ? L.Nt : 0;
     q = lidx(L, p, i, j, k);
     theta = true;
-    w = (side ? 1.0 : -1.0) * S.rc[i] * S.sf[j] * S.hr * S.hp;
+    w = (side ? 1.0 : -1.0) * S.rc[i] * S.sf[j] * S.hc[i] * S.hp;
     return true;
   }
   e -= nt;
@@ -52,7 +52,7 @@ __device__ __forceinline__ bool edge_face(const Shell &S, int p, long e, long &q
   const int i = (int)(rem / L.Nt), j = (int)(rem % L.Nt), k = side ? L.Np : 0;
   q = lidx(L, p, i, j, k);
   theta = false;
-  w = (side ? 1.0 : -1.0) * S.rc[i] * S.hr * S.ht;
+  w = (side ? 1.0 : -1.0) * S.rc[i] * S.hc[i] * S.ht;
   return true;
 }
 

@@ -355,6 +355,7 @@ extern "C" int ys_factor_solve_static(const ys_params *prm, int loc, const doubl
   if (prm->Nr < 8 || prm->Nth < 8 || prm->Nph < 8 || prm->overlap < 1) return YS_EINVAL;
   if (prm->Nr > kStaticMaxN || prm->Nth > kStaticMaxN || prm->Nph > kStaticMaxN) return YS_EINVAL;
   if (prm->Nth <= 2 * prm->overlap + 4) return YS_EINVAL;
+  if (prm->r_half) return YS_EINVAL;  // uniform radial grids only
   const double tb[4] = {prm->Tbc_inner_a, prm->Tbc_inner_b, prm->Tbc_outer_a, prm->Tbc_outer_b};
   for (int w = 0; w < 2; ++w)
     if (!(tb[2 * w] >= 0.0) || !(tb[2 * w + 1] >= 0.0) || !(tb[2 * w] + tb[2 * w + 1] > 0.0)) return YS_EINVAL;
@@ -402,6 +403,11 @@ extern "C" int ys_factor_solve_static(const ys_params *prm, int loc, const doubl
     mh[7 * kStaticMetricLen + t] = rf != 0.0 ? 1.0 / rf : 0.0;
     mh[8 * kStaticMetricLen + t] = sc != 0.0 ? 1.0 / sc : 0.0;
     mh[9 * kStaticMetricLen + t] = sf != 0.0 ? 1.0 / sf : 0.0;
+    // uniform radial grid: cell width h_r, norm factors r
+    mh[10 * kStaticMetricLen + t] = hr;
+    mh[11 * kStaticMetricLen + t] = 1.0 / hr;
+    mh[12 * kStaticMetricLen + t] = rc;
+    mh[13 * kStaticMetricLen + t] = rf;
   }
   // every call shares the scratch: clear the working fields left by the last call
   if (cudaMemsetAsync(base, 0, 4 * kStaticFieldElems * sizeof(double), st) != cudaSuccess) return YS_ECUDA;
@@ -431,6 +437,10 @@ extern "C" int ys_factor_solve_static(const ys_params *prm, int loc, const doubl
   S.irf = met + 7 * kStaticMetricLen + pad;
   S.isc = met + 8 * kStaticMetricLen + pad;
   S.isf = met + 9 * kStaticMetricLen + pad;
+  S.hc = met + 10 * kStaticMetricLen + pad;
+  S.ihc = met + 11 * kStaticMetricLen + pad;
+  S.nrc = met + 12 * kStaticMetricLen + pad;
+  S.nrf = met + 13 * kStaticMetricLen + pad;
   S.ihr = 1.0 / hr;
   S.iht = 1.0 / ht;
   S.ihp = 1.0 / hp;
@@ -440,7 +450,7 @@ extern "C" int ys_factor_solve_static(const ys_params *prm, int loc, const doubl
   {
     // the temperature factor's wall rows follow the wall condition in prm
     const double a[2] = {prm->Tbc_inner_a, prm->Tbc_outer_a}, b[2] = {prm->Tbc_inner_b, prm->Tbc_outer_b};
-    shell_set_T_walls(S, a, b, hr);
+    shell_set_T_walls(S, a, b, hr, hr);
   }
   shell_fill_fp64(S);
   StepAux<double> ax{};

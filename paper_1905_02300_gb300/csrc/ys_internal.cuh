@@ -29,11 +29,18 @@ __host__ __device__ inline long lidx(const Layout &L, int p, int i, int j, int k
 
 struct Shell;
 
-// Number of FP64 metric tables (rc, rf, sc, sf, cc, cf, irc, irf, isc, isf).
-constexpr int kMetricTables = 10;
-enum MetricTable { MT_RC = 0, MT_RF, MT_SC, MT_SF, MT_CC, MT_CF, MT_IRC, MT_IRF, MT_ISC, MT_ISF };
+// Number of FP64 metric tables (rc, rf, sc, sf, cc, cf, irc, irf, isc, isf;
+// then the radial cell width hc, its reciprocal, and the radial norm factors
+// nrc = rc sqrt(hc / h_r), nrf = rf sqrt(hf / h_r) of centres and faces, which
+// equal rc, rf on a uniform radial grid).
+constexpr int kMetricTables = 14;
+enum MetricTable {
+  MT_RC = 0, MT_RF, MT_SC, MT_SF, MT_CC, MT_CF, MT_IRC, MT_IRF, MT_ISC, MT_ISF, MT_HC, MT_IHC, MT_NRC, MT_NRF
+};
 // scalar constants mirrored in both arithmetic types
-// (CS_VOL = h_r h_theta h_phi, the coordinate cell volume of the midpoint-rule norms)
+// (CS_VOL = h_r h_theta h_phi, the coordinate cell volume of the midpoint-rule
+// norms on a uniform radial grid; a non-uniform one carries the ratio h / h_r
+// of each point in its norm factors nrc, nrf)
 enum ShellConst { CS_IHR = 0, CS_IHT, CS_IHP, CS_I2CHI, CS_IR1SQ, CS_CPHI, CS_DT, CS_NU, CS_KAPPA, CS_PRRA, CS_VOL, CS_NUM };
 
 // Row-coefficient tables of the explicit residuals.  On the MAC grid every
@@ -84,6 +91,8 @@ struct Shell {
   const double *cc, *cf;    // cos(theta) at centres / faces
   const double *irc, *irf;  // 1/r at centres / faces
   const double *isc, *isf;  // 1/sin(theta) at centres / faces
+  const double *hc, *ihc;   // radial cell width and its reciprocal per cell
+  const double *nrc, *nrf;  // radial norm factors r sqrt(h / h_r) of centres / faces
   double ihr, iht, ihp;     // 1/h_r, 1/h_theta, 1/h_phi
   double i2chi;             // 1/(2 chi)
   double iR1sq;             // 1/R1^2 (modified theta operator)
@@ -186,20 +195,23 @@ __host__ __device__ inline float cs<float>(const Shell &S, int c) {
 }
 
 // Ghost of the temperature wall condition a T + b dT/dn = T_w (inner: w = 0,
-// outer: w = 1) with T = (T_g + T_0)/2 and dT/dn = (T_g - T_0)/h_r on the wall:
+// outer: w = 1) with T = (T_g + T_0)/2 and dT/dn = (T_g - T_0)/h on the wall,
+// h the distance of the ghost centre from the first one (h_in, h_out):
 // T_g = Tgam[w] T_0 + Tdel[w] T_w.  a = 1, b = 0 is the Dirichlet reflection
 // T_g = 2 T_w - T_0.
-inline void shell_set_T_walls(Shell &S, const double a[2], const double b[2], double hr) {
+inline void shell_set_T_walls(Shell &S, const double a[2], const double b[2], double h_in, double h_out) {
+  const double h[2] = {h_in, h_out};
   for (int w = 0; w < 2; ++w) {
-    const double den = 0.5 * a[w] + b[w] / hr;
-    S.Tgam[w] = -(0.5 * a[w] - b[w] / hr) / den;
+    const double den = 0.5 * a[w] + b[w] / h[w];
+    S.Tgam[w] = -(0.5 * a[w] - b[w] / h[w]) / den;
     S.Tdel[w] = 1.0 / den;
   }
 }
 
 // fill dtab / dcs / fcs / lcs from the named FP64 fields (ftab / ltab are filled by the owner)
 inline void shell_fill_fp64(Shell &S) {
-  const double *t[kMetricTables] = {S.rc, S.rf, S.sc, S.sf, S.cc, S.cf, S.irc, S.irf, S.isc, S.isf};
+  const double *t[kMetricTables] = {S.rc, S.rf, S.sc, S.sf, S.cc, S.cf, S.irc, S.irf, S.isc, S.isf,
+                                    S.hc, S.ihc, S.nrc, S.nrf};
   for (int k = 0; k < kMetricTables; ++k) S.dtab[k] = t[k];
   const double c[CS_NUM] = {S.ihr, S.iht, S.ihp, S.i2chi, S.iR1sq, S.cphi, S.dt, S.nu, S.kappa, S.PrRa,
                             S.hr * S.ht * S.hp};

@@ -32,7 +32,7 @@ class Params(C.Structure):
                 ("schwarz_mode", C.c_int), ("schwarz_tol", C.c_double), ("T_inner", C.c_double),
                 ("T_outer", C.c_double), ("step7", C.c_int), ("step4", C.c_int), ("step4_eps", C.c_double),
                 ("step4_tol", C.c_double), ("Tbc_inner_a", C.c_double), ("Tbc_inner_b", C.c_double),
-                ("Tbc_outer_a", C.c_double), ("Tbc_outer_b", C.c_double)]
+                ("Tbc_outer_a", C.c_double), ("Tbc_outer_b", C.c_double), ("r_half", C.POINTER(C.c_double))]
 
 
 _dp = C.POINTER(C.c_double)
@@ -103,11 +103,22 @@ def _ptr(a):
 
 
 def default_params(**kw) -> Params:
+    """ys_params with the library defaults and the given fields.  r_half (a
+    sequence of 2 Nr + 1 radii) is kept alive on the returned struct
+    (attribute _r_half) for as long as the struct is."""
     p = Params()
     lib.ys_default_params(C.byref(p))
     for k, v in kw.items():
         if not hasattr(p, k):
             raise KeyError(k)
+        if k == "r_half":
+            if v is None:
+                p.r_half = None
+                continue
+            arr = np.ascontiguousarray(v, dtype=np.float64)
+            p._r_half = arr
+            p.r_half = arr.ctypes.data_as(_dp)
+            continue
         setattr(p, k, v)
     return p
 
@@ -116,6 +127,9 @@ class Solver:
     """One shell on the GPU (owns a ys_ctx)."""
 
     def __init__(self, **params):
+        rh = params.get("r_half")
+        if rh is not None and len(rh) != 2 * int(params.get("Nr", 0)) + 1:
+            raise ValueError("r_half: 2 Nr + 1 radii expected")
         self.params = default_params(**params)
         h = C.c_void_p()
         _check(lib.ys_create_ex(C.byref(self.params), C.byref(h)), "ys_create_ex")

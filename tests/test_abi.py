@@ -46,3 +46,21 @@ def test_strerror_and_defaults():
     assert ys.lib.ys_strerror(ys.YS_EDIVERGED) == b"diverged (NaN/Inf)"
     p = ys.default_params()
     assert p.chi == 1.0 and p.overlap == 2 and p.step7 == 1 and p.precision == ys.YS_FP64
+
+
+def test_invalid_radial_half_points_rejected_without_gpu():
+    """Non-uniform radial grids: radii that do not increase, or do not start at
+    R1 / end at R2, are rejected before any device work (YS_EINVAL); a wrong
+    count is caught by the binding."""
+    import numpy as np
+    from paper_1905_02300_gb300 import ys, workloads as W
+    kw = dict(R1=0.5, R2=1.0, Pr=1.0, Ra=1e3, dt=1e-3, Nr=16, Nth=16, Nph=48)
+    good = np.array(W.stretched_radii(0.5, 1.0, 16, 0.5))
+    bad = [good[::-1].copy(), good + 0.01, np.concatenate([good[:5], good[5:6], good[5:-1]])]
+    for b in bad:
+        with pytest.raises(ys.YSError) as e:
+            ys.Solver(**kw, r_half=b)
+        assert e.value.code == ys.YS_EINVAL
+    with pytest.raises(ValueError):
+        ys.Solver(**kw, r_half=good[:-1])
+

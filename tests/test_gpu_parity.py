@@ -19,8 +19,9 @@ FIELDS = ("T", "ur", "uth", "uph", "p", "ur1", "uth1", "uph1", "p1")
 
 
 def make_pair(ys, kind="trig", R1=0.5, R2=1.0, Pr=1.0, Ra=1e3, Nr=16, Nth=16, Nph=48, dt=1e-3,
-              mode="additive", tol=0.0, step7=True, T_in=0.0, T_out=0.0, with_gpu=True, with_oracle=True):
-    spec = W.Spec(R1, R2, Nr, Nth, Nph)
+              mode="additive", tol=0.0, step7=True, T_in=0.0, T_out=0.0, with_gpu=True, with_oracle=True,
+              r_half=None, precision=None):
+    spec = W.Spec(R1, R2, Nr, Nth, Nph, r_half=r_half)
     ex = W.EXACT[kind](R1, R2, Pr, Ra)
     f0, fm = W.sample_fields(ex, spec, 0.0), W.sample_fields(ex, spec, -dt)
     if T_in or T_out:
@@ -31,15 +32,16 @@ def make_pair(ys, kind="trig", R1=0.5, R2=1.0, Pr=1.0, Ra=1e3, Nr=16, Nth=16, Np
     o = s = None
     if with_oracle:
         o = Oracle(Params(R1=R1, R2=R2, Pr=Pr, Ra=Ra, dt=dt, Nr=Nr, Nth=Nth, Nph=Nph, schwarz_mode=mode,
-                          schwarz_tol=tol, step7=step7, T_in=T_in, T_out=T_out))
+                          schwarz_tol=tol, step7=step7, T_in=T_in, T_out=T_out, r_half=r_half))
         o.set_fields(0, f0["T"], f0["ur"], f0["uth"], f0["uph"], f0["p"])
         o.set_fields(1, fm["T"], fm["ur"], fm["uth"], fm["uph"], fm["p"])
         for tid, F in modes:
             o.set_forcing(tid, F["T"], F["ur"], F["uth"], F["uph"])
     if with_gpu:
+        kw = {} if precision is None else {"precision": precision}
         s = ys.Solver(R1=R1, R2=R2, Pr=Pr, Ra=Ra, dt=dt, Nr=Nr, Nth=Nth, Nph=Nph,
                       schwarz_mode=ys.YS_MULTIPLICATIVE if mode == "multiplicative" else ys.YS_ADDITIVE,
-                      schwarz_tol=tol, step7=1 if step7 else 0, T_inner=T_in, T_outer=T_out)
+                      schwarz_tol=tol, step7=1 if step7 else 0, T_inner=T_in, T_outer=T_out, r_half=r_half, **kw)
         s.set_fields_dict(0, f0)
         s.set_fields_dict(1, fm)
         for m, (tid, F) in enumerate(modes):
@@ -230,3 +232,59 @@ def test_neumann_and_robin_temperature_walls(gpu_lib, ab):
         r = o.get_fields(0)["T"]
         err = np.abs(g - r).max() / np.abs(r).max()
         assert err <= tol, (prec, err)
+
+
+def test_stretched_radial_grid_parity(gpu_lib):
+    """Sec. 4 non-uniform radial grid (cells 3x finer at the walls than
+    mid-shell): FP64 within 1e-11 of the oracle after 10 steps, both time
+    levels and the Schwarz increment norms; the mixed form within 1e-5, also
+    with inhomogeneous wall temperatures (deviation variables built on the
+    stretched grid)."""
+    ys = gpu_lib
+    rh = W.stretched_radii(0.5, 1.0, 16, 0.5)
+    o, s, _, _ = make_pair(ys, r_half=rh)
+    o.step(10, 3)
+    s.step(10, 3)
+    assert_parity(s, o, 1e-11)
+    assert_parity(s, o, 1e-11, level=1)
+    gn, _ = s.norms()
+    assert np.allclose(gn, o.last_norms, rtol=1e-9, atol=1e-300)
+    # mixed form: the measure of tests/test_gpu_mixed.py (a velocity component
+    # against the velocity vector's largest value: the exact u_r is zero here)
+    vel = {"ur": ("ur", "uth", "uph"), "uth": ("ur", "uth", "uph"), "uph": ("ur", "uth", "uph"),
+           "ur1": ("ur1", "uth1", "uph1"), "uth1": ("ur1", "uth1", "uph1"), "uph1": ("ur1", "uth1", "uph1")}
+    for T_in in (0.0, 1.0):
+        o, s, _, _ = make_pair(ys, r_half=rh, T_in=T_in, precision=ys.YS_MIXED)
+        o.step(10, 3)
+        s.step(10, 3)
+        g, r = s.get_fields(0, aux=True), o.get_fields(0, aux=True)
+        e = {k: np.abs(g[k] - r[k]).max() / max(np.abs(r[c]).max() for c in vel.get(k, (k,))) for k in FIELDS}
+        assert max(e.values()) <= 1e-5, (T_in, e)
+
+
+def test_stretched_radial_grid_ragged_and_robin(gpu_lib):
+    """Stretched radial grid on odd sizes with a ragged phi tail, and with a
+    Robin temperature wall (its ghost uses the wall's own centre distance)."""
+    ys = gpu_lib
+    rh = W.stretched_radii(0.5, 1.0, 9, 0.4)
+    o, s, _, _ = make_pair(ys, kind="curl", Nr=9, Nth=21, Nph=151, dt=2e-3, Ra=50.0, r_half=rh)
+    o.step(3, 2)
+    s.step(3, 2)
+    assert_parity(s, o, 1e-12)
+    N, dt = 12, 1e-3
+    rh = W.stretched_radii(0.5, 1.0, N, 0.5)
+    spec = W.Spec(0.5, 1.0, N, N, 3 * N, r_half=rh)
+    ex = W.RadialHeatRobin(0.5, 1.0, 1.0, 0.0, a=1.0, b=0.5)
+    f0, fm = W.sample_fields(ex, spec, 0.0), W.sample_fields(ex, spec, -dt)
+    o = Oracle(Params(R1=0.5, R2=1.0, Pr=1.0, Ra=0.0, dt=dt, Nr=N, Nth=N, Nph=3 * N, Tbc_out=(1.0, 0.5), r_half=rh))
+    o.set_fields(0, f0["T"], f0["ur"], f0["uth"], f0["uph"], f0["p"])
+    o.set_fields(1, fm["T"], fm["ur"], fm["uth"], fm["uph"], fm["p"])
+    o.step(10, 3)
+    s = ys.Solver(R1=0.5, R2=1.0, Pr=1.0, Ra=0.0, dt=dt, Nr=N, Nth=N, Nph=3 * N, Tbc_outer_a=1.0,
+                  Tbc_outer_b=0.5, r_half=rh)
+    s.set_fields_dict(0, f0)
+    s.set_fields_dict(1, fm)
+    s.step(10, 3)
+    g, r = s.get_fields(0)["T"], o.get_fields(0)["T"]
+    assert np.abs(g - r).max() <= 1e-11 * np.abs(r).max()
+
