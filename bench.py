@@ -157,7 +157,7 @@ def workload(n, dt=5e-4, K=3):
 
 def inputs(kw):
     from paper_1905_02300_gb300 import workloads as W
-    spec = W.Spec(kw["R1"], kw["R2"], kw["Nr"], kw["Nth"], kw["Nph"])
+    spec = W.Spec(kw["R1"], kw["R2"], kw["Nr"], kw["Nth"], kw["Nph"], r_half=kw.get("r_half"))
     ex = W.TrigShell(kw["R1"], kw["R2"], kw["Pr"], kw["Ra"])
     return (W.sample_fields(ex, spec, 0.0), W.sample_fields(ex, spec, -kw["dt"]), W.forcing_modes(ex, spec))
 
@@ -384,6 +384,8 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=8, help="oracle steps of the cpu_baseline sample (~12 s)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stretch", type=float, default=None,
+                    help="run the shell on a stretched radial grid (workloads.stretched_radii beta)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="shell", choices=["shell", "ensemble", "serving"])
     ap.add_argument("--requests", type=int, default=32)
@@ -409,6 +411,9 @@ def main():
     from paper_1905_02300_gb300 import ys
 
     kw, K = workload(args.n)
+    if args.stretch is not None:
+        from paper_1905_02300_gb300 import workloads as W
+        kw["r_half"] = W.stretched_radii(kw["R1"], kw["R2"], kw["Nr"], args.stretch)
     f0, fm, modes = inputs(kw)
     mixed = args.precision == "mixed"
     s = ys.Solver(**kw, precision=ys.YS_MIXED if mixed else ys.YS_FP64)
@@ -517,7 +522,9 @@ def main():
                 "config": {"workload": f"yin-yang shell {args.n}x{args.n}x{3*args.n} MAC cells per patch, "
                                        f"R1=0.5 R2=1 Pr=1 Ra=1e3 dt=5e-4, K={K} Schwarz iterations, "
                                        f"{'mixed FP32/FP64' if mixed else 'FP64'}, "
-                                       f"manufactured-solution forcing",
+                                       f"manufactured-solution forcing"
+                                       + (f", stretched radial grid (beta {args.stretch})"
+                                          if args.stretch is not None else ""),
                            "cells_per_shell": cells, "l2": "inputs larger than L2 (state ~%.1f GB)"
                            % (s.device_bytes() / 1e9), "parallelism": f"replicas x{world}"},
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
