@@ -20,12 +20,14 @@ SHELLS = [dict(R1=0.45, Nr=16, Nth=20, Ra=2e3, Pr=1.0), dict(R1=0.55, Nr=20, Nth
 
 def make(ys, sp, precision=None):
     Nr, Nth = sp["Nr"], sp["Nth"]
+    rh = W.stretched_radii(sp["R1"], 1.0, Nr, sp["stretch"]) if "stretch" in sp else None
     spec = W.Spec(sp["R1"], 1.0, Nr, Nth, 3 * Nth)
-    hmin = min(spec.hr, sp["R1"] * spec.hth, sp["R1"] * np.sin(spec.th0) * spec.hph)
+    hr = spec.hr if rh is None else float(np.min(np.diff(np.asarray(rh)[::2])))
+    hmin = min(hr, sp["R1"] * spec.hth, sp["R1"] * np.sin(spec.th0) * spec.hph)
     kw = dict(R1=sp["R1"], R2=1.0, Pr=sp["Pr"], Ra=sp["Ra"], Nr=Nr, Nth=Nth, Nph=3 * Nth, dt=0.5 * hmin * hmin,
-              T_inner=1.0, T_outer=0.0, precision=ys.YS_MIXED if precision is None else precision)
+              T_inner=1.0, T_outer=0.0, precision=ys.YS_MIXED if precision is None else precision, r_half=rh)
     s = ys.Solver(**kw)
-    spec = W.Spec(kw["R1"], 1.0, Nr, Nth, 3 * Nth)
+    spec = W.Spec(kw["R1"], 1.0, Nr, Nth, 3 * Nth, r_half=rh)
     s.set_fields_dict(0, W.convection_initial(spec, sp["Pr"], sp["Ra"], T_in=1.0))
     return s, kw
 
@@ -79,6 +81,26 @@ def test_batch_is_mix_independent_and_matches_single_shell_path(gpu_lib):
         assert same(f, r)
         assert close(f, sg)
     assert b.launches_per_step() > 0
+    b.close()
+
+
+def test_stretched_radial_grid_shell_in_a_batch(gpu_lib):
+    """A shell on a stretched radial grid batches with uniform ones: its
+    fields are the same alone and in the mix (bitwise) and within 1e-5 of the
+    single-shell path (its coefficient tables travel with it)."""
+    ys = gpu_lib
+    mix = [dict(R1=0.45, Nr=16, Nth=20, Ra=2e3, Pr=1.0, stretch=0.5), SHELLS[1]]
+    ref = alone(ys, mix[0], 5)
+    s, _ = make(ys, mix[0])
+    s.step(5, 3)
+    single = fields(s)
+    b = ys.Batch(4)
+    slots = [b.add(make(ys, sp)[0]) for sp in mix]
+    b.step(5)
+    b.sync()
+    f = fields(b.remove(slots[0]))
+    assert same(f, ref)
+    assert close(f, single)
     b.close()
 
 
