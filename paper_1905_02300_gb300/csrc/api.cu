@@ -94,36 +94,66 @@ size_t user_elems(const Layout &L, int loc) {
   return 2ul * (L.Nr + (loc == LR)) * (L.Nt + (loc == LT)) * (L.Np + (loc == LP));
 }
 
-// user array -> staging buffer -> padded field(s): one host-to-device copy,
-// unpacked into dst and, when dst2 is given, into dst2 as well (the two
-// velocity systems and the two pressures start from the same values)
+// Device address of a user host buffer that kernels may access directly:
+// page-locked (pinned or registered) host memory mapped into the device's
+// address space; null for pageable memory (which goes through the staging
+// buffer).  Over the CPU-GPU link such a buffer is read or written by the
+// (un)pack kernel itself, in one pass instead of a copy plus a kernel.
+const void *mapped_host(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
+// source of an unpack: device memory as is, mapped host memory directly, else
+// a host-to-device copy into the staging buffer
+int unpack_source(ys_ctx *c, const double *src, size_t n, bool device_src, const double **from) {
+  if (device_src) {
+    *from = src;
+    return YS_OK;
+  }
+  if (const void *m = mapped_host(src)) {
+    *from = (const double *)m;
+    return YS_OK;
+  }
+  if (cudaMemcpyAsync(c->stage, src, n * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    return YS_ECUDA;
+  *from = c->stage;
+  return YS_OK;
+}
+
+// user array -> padded field(s), unpacked into dst and, when dst2 is given,
+// into dst2 from the same read (the two velocity systems and the two
+// pressures start from the same values)
 template <typename R>
 int copy_in(ys_ctx *c, int loc, const double *src, R *dst, const double *bg, bool device_src, R *dst2 = nullptr) {
-  size_t n = user_elems(c->L, loc);
-  cudaError_t e = cudaMemcpyAsync(c->stage, src, n * sizeof(double),
-                                  device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
-  if (e != cudaSuccess) return YS_ECUDA;
-  LAUNCH(c, K_PACK, 1, Launch<R>::unpack(c->L, loc, c->stage, dst, bg, c->stream));
-  if (dst2) LAUNCH(c, K_PACK, 1, Launch<R>::unpack(c->L, loc, c->stage, dst2, bg, c->stream));
+  const double *from = nullptr;
+  if (int rc = unpack_source(c, src, user_elems(c->L, loc), device_src, &from)) return rc;
+  LAUNCH(c, K_PACK, 1, Launch<R>::unpack(c->L, loc, from, dst, bg, c->stream, dst2));
   return YS_OK;
 }
 
 int copy_in_p(ys_ctx *c, const double *src, double *dst, bool device_src, double *dst2 = nullptr) {
-  size_t n = user_elems(c->L, LC);
-  cudaError_t e = cudaMemcpyAsync(c->stage, src, n * sizeof(double),
-                                  device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
-  if (e != cudaSuccess) return YS_ECUDA;
-  LAUNCH(c, K_PACK, 1, unpack_p(c->L, c->stage, dst, c->p_bg, c->stream));
-  if (dst2) LAUNCH(c, K_PACK, 1, unpack_p(c->L, c->stage, dst2, c->p_bg, c->stream));
+  const double *from = nullptr;
+  if (int rc = unpack_source(c, src, user_elems(c->L, LC), device_src, &from)) return rc;
+  LAUNCH(c, K_PACK, 1, unpack_p(c->L, from, dst, c->p_bg, c->stream, dst2));
   return YS_OK;
 }
 
-// padded field -> staging buffer -> user array; queued on the context's
-// stream (the staging buffer is reused in stream order), the caller
+// padded field -> user array: packed straight into mapped host memory, else
+// through the staging buffer and a device-to-host copy; queued on the
+// context's stream (the staging buffer is reused in stream order), the caller
 // synchronises once after the last field
 template <typename R>
 int copy_out(ys_ctx *c, int loc, const R *src, double *dst, const double *bg) {
   size_t n = user_elems(c->L, loc);
+  if (void *m = const_cast<void *>(mapped_host(dst))) {
+    LAUNCH(c, K_PACK, 1, Launch<R>::pack(c->L, loc, src, (double *)m, bg, c->stream));
+    return YS_OK;
+  }
   LAUNCH(c, K_PACK, 1, Launch<R>::pack(c->L, loc, src, c->stage, bg, c->stream));
   cudaError_t e = cudaMemcpyAsync(dst, c->stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   return e == cudaSuccess ? YS_OK : YS_ECUDA;
@@ -131,6 +161,10 @@ int copy_out(ys_ctx *c, int loc, const R *src, double *dst, const double *bg) {
 
 int copy_out_p(ys_ctx *c, const double *src, double *dst) {
   size_t n = user_elems(c->L, LC);
+  if (void *m = const_cast<void *>(mapped_host(dst))) {
+    LAUNCH(c, K_PACK, 1, pack_p(c->L, src, (double *)m, c->p_bg, c->stream));
+    return YS_OK;
+  }
   LAUNCH(c, K_PACK, 1, pack_p(c->L, src, c->stage, c->p_bg, c->stream));
   cudaError_t e = cudaMemcpyAsync(dst, c->stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   return e == cudaSuccess ? YS_OK : YS_ECUDA;

@@ -88,12 +88,16 @@ struct Launch {
                        int patch_mask, cudaStream_t st);
   // host layout <-> device layout; bg (FP64 per radial index, may be null) is
   // subtracted on the way in and added on the way out
-  static void unpack(const Layout &L, int loc, const double *src, R *dst, const double *bg, cudaStream_t st);
+  // user layout (device or mapped pinned host memory) -> padded field dst and,
+  // when given, dst2 (src read once)
+  static void unpack(const Layout &L, int loc, const double *src, R *dst, const double *bg, cudaStream_t st,
+                     R *dst2 = nullptr);
   static void pack(const Layout &L, int loc, const R *src, double *dst, const double *bg, cudaStream_t st);
 };
 
 // FP64 pressure fields: host layout <-> device layout
-void unpack_p(const Layout &L, const double *src, double *dst, const double *bg, cudaStream_t st);
+void unpack_p(const Layout &L, const double *src, double *dst, const double *bg, cudaStream_t st,
+              double *dst2 = nullptr);
 void pack_p(const Layout &L, const double *src, double *dst, const double *bg, cudaStream_t st);
 
 }  // namespace ys

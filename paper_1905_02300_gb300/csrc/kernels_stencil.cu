@@ -182,8 +182,10 @@ __device__ __forceinline__ void user_extent(const Layout &L, int loc, int &ni, i
   nk = L.Np + (loc == LP ? 1 : 0);
 }
 
+// user layout -> padded field(s); src may be device memory or mapped pinned
+// host memory (read once, written to dst and, when given, dst2)
 template <typename R>
-__global__ void k_unpack(Layout L, int loc, const double *src, R *dst, const double *bg) {
+__global__ void k_unpack(Layout L, int loc, const double *src, R *dst, const double *bg, R *dst2) {
   int ni, nj, nk;
   user_extent(L, loc, ni, nj, nk);
   long n = 2L * ni * nj * nk;
@@ -196,7 +198,9 @@ __global__ void k_unpack(Layout L, int loc, const double *src, R *dst, const dou
     int p = (int)(t / ni);
     double v = src[u];
     if (bg) v -= bg[i];
-    dst[lidx(L, p, i, j, k)] = (R)v;
+    const long q = lidx(L, p, i, j, k);
+    dst[q] = (R)v;
+    if (dst2) dst2[q] = (R)v;
   }
 }
 
@@ -296,8 +300,9 @@ void Launch<R>::pressure(const Shell &S, int sys, State<R> it, State<R> n, doubl
 }
 
 template <typename R>
-void Launch<R>::unpack(const Layout &L, int loc, const double *src, R *dst, const double *bg, cudaStream_t st) {
-  k_unpack<R><<<flat_blocks(user_max(L)), 256, 0, st>>>(L, loc, src, dst, bg);
+void Launch<R>::unpack(const Layout &L, int loc, const double *src, R *dst, const double *bg, cudaStream_t st,
+                       R *dst2) {
+  k_unpack<R><<<flat_blocks(user_max(L)), 256, 0, st>>>(L, loc, src, dst, bg, dst2);
 }
 
 template <typename R>
@@ -305,8 +310,8 @@ void Launch<R>::pack(const Layout &L, int loc, const R *src, double *dst, const 
   k_pack<R><<<flat_blocks(user_max(L)), 256, 0, st>>>(L, loc, src, dst, bg);
 }
 
-void unpack_p(const Layout &L, const double *src, double *dst, const double *bg, cudaStream_t st) {
-  k_unpack<double><<<flat_blocks(user_max(L)), 256, 0, st>>>(L, LC, src, dst, bg);
+void unpack_p(const Layout &L, const double *src, double *dst, const double *bg, cudaStream_t st, double *dst2) {
+  k_unpack<double><<<flat_blocks(user_max(L)), 256, 0, st>>>(L, LC, src, dst, bg, dst2);
 }
 
 void pack_p(const Layout &L, const double *src, double *dst, const double *bg, cudaStream_t st) {
@@ -321,7 +326,7 @@ void pack_p(const Layout &L, const double *src, double *dst, const double *bg, c
   template void Launch<R>::resid_u(const Shell &, int, int, State<R>, State<R>, StepAux<R>, R *, int,             \
                                    cudaStream_t);                                                                  \
   template void Launch<R>::pressure(const Shell &, int, State<R>, State<R>, double *, double *, int, cudaStream_t); \
-  template void Launch<R>::unpack(const Layout &, int, const double *, R *, const double *, cudaStream_t);        \
+  template void Launch<R>::unpack(const Layout &, int, const double *, R *, const double *, cudaStream_t, R *);   \
   template void Launch<R>::pack(const Layout &, int, const R *, double *, const double *, cudaStream_t);
 YS_INST_STENCIL(double)
 YS_INST_STENCIL(float)

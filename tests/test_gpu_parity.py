@@ -288,3 +288,29 @@ def test_stretched_radial_grid_ragged_and_robin(gpu_lib):
     g, r = s.get_fields(0)["T"], o.get_fields(0)["T"]
     assert np.abs(g - r).max() <= 1e-11 * np.abs(r).max()
 
+
+
+def test_pinned_and_pageable_host_buffers_agree(gpu_lib):
+    """set/get through page-locked host buffers (read and written by the
+    (un)pack kernels over the CPU-GPU link) and through pageable ones (staged
+    copies) give the same state and the same fields, bit for bit."""
+    import torch
+    ys = gpu_lib
+    o, s1, spec, ex = make_pair(ys, with_oracle=False)
+    _, s2, _, _ = make_pair(ys, with_oracle=False)
+    f0 = W.sample_fields(ex, spec, 0.0)
+    pinned = {}
+    for k, a in f0.items():
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        pinned[k] = t.numpy()
+    s2.set_fields(0, *[pinned[k] for k in ("T", "ur", "uth", "uph", "p")])
+    s1.set_fields(0, *[f0[k] for k in ("T", "ur", "uth", "uph", "p")])
+    s1.step(2, 2)
+    s2.step(2, 2)
+    out = {k: torch.empty(a.shape, dtype=torch.float64, pin_memory=True).numpy() for k, a in f0.items()}
+    rc = ys.lib.ys_get_fields(s2.h, 0, *[ys._ptr(out[k]) for k in ("T", "ur", "uth", "uph", "p")], None)
+    assert rc == ys.YS_OK
+    g1 = s1.get_fields(0)
+    for k in ("T", "ur", "uth", "uph", "p"):
+        assert np.array_equal(g1[k], out[k]), k
