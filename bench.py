@@ -77,8 +77,8 @@ FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of GB300 (profiling recipe)
 # (traffic scales with the points processed); the bench reports it scaled to
 # one full launch.  Valid for the kernel code the capture was taken of.
 TRAFFIC_PER_POINT = {
-    (False, "resid_u"): (183.26e6 / (2 * 64 * 63 * 192), "profiles/k_resid_ur_fp64_64x64x192_full.md"),
-    (True, "resid_u"): (518.75e6 / (2 * 112 * 111 * 336), "profiles/k_resid_ur_mixed_112x112x336_full.md"),
+    (False, "resid_u"): (183.14e6 / (2 * 64 * 63 * 192), "profiles/k_resid_ur_fp64_64x64x192_full.md"),
+    (True, "resid_u"): (518.40e6 / (2 * 112 * 111 * 336), "profiles/k_resid_ur_mixed_112x112x336_full.md"),
     # mean of the captured r, theta and phi solves of T (non-final, non-final, final)
     (True, "solve"): ((185.524e6 + 182.543e6 + 190.098e6) / (3 * 2 * 112 * 112 * 336),
                       "profiles/line_kernels_mixed_112x112x336_full.md"),
