@@ -354,10 +354,9 @@ __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, Sta
   out += c[UR_GP1] * (z1 - z0);
   out += c[UR_GPM1] * (zm1 - zm0);
   out -= (c[UR_AR] * ar) * (Srp - Srm);
-  out -= (c[UR_AT] * sAt) * (Stp - Stm);
-  out -= (c[UR_AP] * sAp) * (Spp - Spm);
-  out += (c[UR_CV] * sAt) * (((ym0 + ym1) + y0) + y1);
-  out += (c[UR_CV] * sAp) * (((zm0 + zm1) + z0) + z1);
+  // advection along theta / phi and the curvature term of the same advecting component
+  out += sAt * (c[UR_CV] * (((ym0 + ym1) + y0) + y1) - c[UR_AT] * (Stp - Stm));
+  out += sAp * (c[UR_CV] * (((zm0 + zm1) + z0) + z1) - c[UR_AP] * (Spp - Spm));
   out -= c[UR_GPR] * (V)(pres(it, n, sys, q) - pres(it, n, sys, q - SI));
   out += c[UR_BY] * (Sm<V>(it.f[F_T], n.f[F_T], q - SI) + Sm<V>(it.f[F_T], n.f[F_T], q));
   if (ax.fr) out += cs<V>(S, CS_DT) * (V)ax.fr[q];
@@ -403,10 +402,9 @@ __device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, Sta
   out += c[UT_GP1] * (z1 - z0);
   out += c[UT_GPM1] * (zm1 - zm0);
   out -= (c[UT_AR] * sAr) * (Srp - Srm);
-  out -= (c[UT_AT] * at) * (Stp - Stm);
-  out -= (c[UT_AP] * sAp) * (Spp - Spm);
-  out += (c[UT_CP] * sAp) * (((zm0 + zm1) + z0) + z1);
-  out -= (c[UT_CW] * at) * (((wm0 + wm1) + w0) + w1);
+  // advection along theta / phi and the curvature term of the same advecting component
+  out -= at * (c[UT_AT] * (Stp - Stm) + c[UT_CW] * (((wm0 + wm1) + w0) + w1));
+  out += sAp * (c[UT_CP] * (((zm0 + zm1) + z0) + z1) - c[UT_AP] * (Spp - Spm));
   out -= c[UT_GPR] * (V)(pres(it, n, sys, q) - pres(it, n, sys, q - P));
   if (ax.ft) out += cs<V>(S, CS_DT) * (V)ax.ft[q];
   B[q] = (R)(out - ((V)xi[q] - (V)xn[q]));
@@ -452,9 +450,9 @@ __device__ __forceinline__ void body_resid_up(Shell S, int sys, State<R> it, Sta
   out += c[UP_YM0] * ym0;
   out -= (c[UP_AR] * sAr) * (Srp - Srm);
   out -= (c[UP_AT] * sAt) * (Stp - Stm);
-  out -= (c[UP_AP] * ap) * (Spp - Spm);
-  out -= (c[UP_CW] * ap) * (((wm0 + wm1) + w0) + w1);
-  out -= (c[UP_CY] * ap) * (((ym0 + ym1) + y0) + y1);
+  // advection along phi and the curvature terms, all with the advecting a_phi
+  out -= ap * (c[UP_AP] * (Spp - Spm) + c[UP_CW] * (((wm0 + wm1) + w0) + w1) +
+               c[UP_CY] * (((ym0 + ym1) + y0) + y1));
   out -= c[UP_GPR] * (V)(pres(it, n, sys, q) - pres(it, n, sys, q - 1));
   if (ax.fp) out += cs<V>(S, CS_DT) * (V)ax.fp[q];
   B[q] = (R)(out - ((V)xi[q] - (V)xn[q]));
@@ -620,10 +618,8 @@ __device__ __forceinline__ void body_resid_ur_vec(Shell S, int sys, State<R> it,
     out += c[UR_GP1] * (z1[l] - z0[l]);
     out += c[UR_GPM1] * (zm1[l] - zm0[l]);
     out -= (c[UR_AR] * ar[l]) * (Srp[l] - Srm[l]);
-    out -= (c[UR_AT] * sAt[l]) * (Stp[l] - Stm[l]);
-    out -= (c[UR_AP] * sAp[l]) * (Spp[l] - Spm[l]);
-    out += (c[UR_CV] * sAt[l]) * (((ym0[l] + ym1[l]) + y0[l]) + y1[l]);
-    out += (c[UR_CV] * sAp[l]) * (((zm0[l] + zm1[l]) + z0[l]) + z1[l]);
+    out += sAt[l] * (c[UR_CV] * (((ym0[l] + ym1[l]) + y0[l]) + y1[l]) - c[UR_AT] * (Stp[l] - Stm[l]));
+    out += sAp[l] * (c[UR_CV] * (((zm0[l] + zm1[l]) + z0[l]) + z1[l]) - c[UR_AP] * (Spp[l] - Spm[l]));
     out -= c[UR_GPR] * (V)(P0[l] - Pm[l]);
     out += c[UR_BY] * (tm[l] + t0[l]);
     if (ax.fr) out += cs<V>(S, CS_DT) * f[l];
@@ -709,10 +705,8 @@ __device__ __forceinline__ void body_resid_ut_vec(Shell S, int sys, State<R> it,
     out += c[UT_GP1] * (z1[l] - z0[l]);
     out += c[UT_GPM1] * (zm1[l] - zm0[l]);
     out -= (c[UT_AR] * sAr[l]) * (Srp[l] - Srm[l]);
-    out -= (c[UT_AT] * at[l]) * (Stp[l] - Stm[l]);
-    out -= (c[UT_AP] * sAp[l]) * (Spp[l] - Spm[l]);
-    out += (c[UT_CP] * sAp[l]) * (((zm0[l] + zm1[l]) + z0[l]) + z1[l]);
-    out -= (c[UT_CW] * at[l]) * (((wm0[l] + wm1[l]) + w0[l]) + w1[l]);
+    out -= at[l] * (c[UT_AT] * (Stp[l] - Stm[l]) + c[UT_CW] * (((wm0[l] + wm1[l]) + w0[l]) + w1[l]));
+    out += sAp[l] * (c[UT_CP] * (((zm0[l] + zm1[l]) + z0[l]) + z1[l]) - c[UT_AP] * (Spp[l] - Spm[l]));
     out -= c[UT_GPR] * (V)(P0[l] - Pm[l]);
     if (ax.ft) out += cs<V>(S, CS_DT) * f[l];
     o[l] = out - (xa[l] - xb[l]);
@@ -798,9 +792,8 @@ __device__ __forceinline__ void body_resid_up_vec(Shell S, int sys, State<R> it,
     out += c[UP_YM0] * ym0[l];
     out -= (c[UP_AR] * sAr[l]) * (Srp[l] - Srm[l]);
     out -= (c[UP_AT] * sAt[l]) * (Stp[l] - Stm[l]);
-    out -= (c[UP_AP] * ap[l]) * (Spp[l] - Spm[l]);
-    out -= (c[UP_CW] * ap[l]) * (((wm0[l] + wm1[l]) + w0[l]) + w1[l]);
-    out -= (c[UP_CY] * ap[l]) * (((ym0[l] + ym1[l]) + y0[l]) + y1[l]);
+    out -= ap[l] * (c[UP_AP] * (Spp[l] - Spm[l]) + c[UP_CW] * (((wm0[l] + wm1[l]) + w0[l]) + w1[l]) +
+                    c[UP_CY] * (((ym0[l] + ym1[l]) + y0[l]) + y1[l]));
     out -= c[UP_GPR] * (V)(P0[l] - Pm[l]);
     if (ax.fp) out += cs<V>(S, CS_DT) * f[l];
     o[l] = out - (xa[l] - xb[l]);
