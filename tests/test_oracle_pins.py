@@ -767,3 +767,36 @@ def test_robin_ghost_reduces_to_dirichlet_and_neumann():
     assert gam == -1.0 and dl == 2.0
     gam, dl = xch.robin_ghost(0.0, 1.0, h)
     assert gam == pytest.approx(1.0) and dl == pytest.approx(h)
+
+
+def test_printed_landau_grid_sizes_fix_the_patch_extents():
+    """Sec. 2's patch extents are garbled; the reading taken (theta in
+    [pi/4 - d, 3pi/4 + d], phi in [-3pi/4 - d, 3pi/4 + d], d the overlap angle)
+    reproduces the grid sizes Sec. 5.1 prints for its Landau runs (R1 = 1,
+    R2 = 2, d = 0.1) to every printed digit with whole cell counts (36, 104,
+    136); the extents without the overlap, or with it on one side only, give
+    no whole counts.  The oracle's grid has these extents."""
+    import os
+    vals = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "landau_grid_sizes.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, *v = line.split()
+            vals[k] = [float(x) for x in v]
+    R1, R2, d = vals["R1"][0], vals["R2"][0], vals["overlap"][0]
+    h_r, h_t, h_p = vals["h"]
+    ext = {"r": R2 - R1, "t": math.pi / 2 + 2 * d, "p": 1.5 * math.pi + 2 * d}
+    counts = {}
+    for key, h in (("r", h_r), ("t", h_t), ("p", h_p)):
+        n = round(ext[key] / h)
+        assert abs(ext[key] / n - h) <= 5e-5 * h, (key, n, ext[key] / n, h)
+        counts[key] = n
+    assert counts == {"r": 36, "t": 104, "p": 136}
+    # alternative readings of the theta extent give no whole count
+    for alt in (math.pi / 2, math.pi / 2 + d):
+        n = round(alt / h_t)
+        assert abs(alt / n - h_t) > 5e-5 * h_t
+    # the oracle's grid: theta and phi extents are pi/2 + 2 delta and 3 pi/2 + 2 delta
+    g = Grid(1.0, 2.0, 36, 104, 136, overlap=6)
+    assert abs(g.Nth * g.hth - (math.pi / 2 + 2 * g.delta)) < 1e-13
+    assert abs(g.Nph * g.hph - (1.5 * math.pi + 2 * g.delta)) < 1e-13
+    assert abs(g.th0 - (math.pi / 4 - g.delta)) < 1e-15 and abs(g.ph0 + 0.75 * math.pi + g.delta) < 1e-15
