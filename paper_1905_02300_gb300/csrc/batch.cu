@@ -434,11 +434,8 @@ void enqueue_step(ys_batch *b) {
   cudaStream_t st = b->stream;
   const int g128 = grid_size(128), g256 = grid_size(256), gl = grid_size(b->tpb_line);
   long nl = 0;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(kb_solve_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::kScanSmemMax);
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  smem_attr_once(attr_done, kb_solve_phi<R>, bd::kScanSmemMax);
   // shared-memory positions per warp of the phi solves: the longest line of the
   // batch that fits; shells with longer lines keep their forward results in W
   int spw = 0;

@@ -2,6 +2,8 @@
 #pragma once
 #include "ys_internal.cuh"
 
+#include <atomic>
+
 namespace ys {
 
 // Field slots of one time level / iterate.
@@ -21,6 +23,23 @@ template <typename R>
 struct Cmp {
   using type = R;
 };
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` once per device: a
+// bit per device in `done` (the call site's own flag word), set after the
+// attribute took, so that concurrent first calls merely repeat it.
+template <typename K>
+inline void smem_attr_once(std::atomic<unsigned long long> &done, K kernel, int bytes) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return;
+  }
+  const unsigned long long bit = 1ull << dev;
+  if (done.load(std::memory_order_acquire) & bit) return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
+    done.fetch_or(bit, std::memory_order_acq_rel);
+}
 
 // Advecting velocity and forcing pointers of one step.
 template <typename R>

@@ -235,11 +235,8 @@ void Launch<R>::solve(const Shell &S, int loc, int dir, bool final, const R *Lo,
                       R *W, R *dst, double *norm, int slot, int patch_mask, cudaStream_t st) {
   if (dir == DP) {
     // forward results of each warp's line in shared memory when they fit
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_solve_phi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd::kScanSmemMax);
-      attr = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};
+    smem_attr_once(attr_done, k_solve_phi<R>, bd::kScanSmemMax);
     const int pad = bd::scan_pad(S.L.Np);
     const size_t bytes = (size_t)bd::kScanWarps * pad * sizeof(R);
     const bool fits = bytes <= (size_t)bd::kScanSmemMax;
