@@ -539,7 +539,7 @@ def test_stretched_radial_grid_space_convergence_second_order():
 def test_stretched_radial_heat_closed_form_second_order():
     """The radial heat closed form on the stretched grid: second order."""
     errs = []
-    for N, dt in ((12, 2e-3), (24, 5e-4)):
+    for N, dt in ((10, 2e-3), (20, 5e-4)):
         o, spec, ex = _run("radial_heat", N, dt, int(round(0.008 / dt)), Pr=1.0, Ra=0.0, beta=0.5)
         errs.append(_errors(o, spec, ex)["T"])
     assert math.log(errs[0] / errs[1]) / math.log(2.0) > 1.7, errs
@@ -800,3 +800,22 @@ def test_printed_landau_grid_sizes_fix_the_patch_extents():
     assert abs(g.Nth * g.hth - (math.pi / 2 + 2 * g.delta)) < 1e-13
     assert abs(g.Nph * g.hph - (1.5 * math.pi + 2 * g.delta)) < 1e-13
     assert abs(g.th0 - (math.pi / 4 - g.delta)) < 1e-15 and abs(g.ph0 + 0.75 * math.pi + g.delta) < 1e-15
+
+
+def test_stretched_radial_grid_robin_wall_second_order():
+    """A Robin temperature wall (a, b) = (1, 0.5) at R2 on the stretched radial
+    grid: its ghost uses the wall's own centre distance h_f, and the closed-form
+    heat solution still converges at second order."""
+    errs = []
+    for N, dt in ((10, 2e-3), (20, 5e-4)):
+        rh = W.stretched_radii(0.5, 1.0, N, 0.5)
+        spec = W.Spec(0.5, 1.0, N, N, 3 * N, r_half=rh)
+        ex = W.RadialHeatRobin(0.5, 1.0, 1.0, 0.0, a=1.0, b=0.5)
+        o = Oracle(Params(R1=0.5, R2=1.0, Pr=1.0, Ra=0.0, dt=dt, Nr=N, Nth=N, Nph=3 * N, Tbc_out=(1.0, 0.5),
+                          schwarz_tol=1e-8, r_half=rh))
+        f0, fm = W.sample_fields(ex, spec, 0.0), W.sample_fields(ex, spec, -dt)
+        o.set_fields(0, f0["T"], f0["ur"], f0["uth"], f0["uph"], f0["p"])
+        o.set_fields(1, fm["T"], fm["ur"], fm["uth"], fm["uph"], fm["p"])
+        o.step(int(round(0.008 / dt)), 20)
+        errs.append(_l2(spec, "c", o.get_fields(0)["T"] - W.sample_fields(ex, spec, o.t)["T"]))
+    assert math.log(errs[0] / errs[1]) / math.log(2.0) > 1.8, errs
