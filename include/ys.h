@@ -132,7 +132,9 @@ int ys_create_ex(const ys_params *p, ys_ctx **out);
  * Eq. ac2), or, if aux != NULL, takes u1 and p1 from aux packed as
  * [ur1 | uth1 | uph1 | p1] in the same layouts.  Then recomputes every
  * boundary value of that level.  Setting level 0 while level 1 was never set
- * also sets level 1 to the same state (psi^{-1} := psi^0).
+ * also sets level 1 to the same state (psi^{-1} := psi^0).  Page-locked
+ * (pinned) host buffers are read by the device directly over the CPU-GPU
+ * link; pageable ones go through one staging copy.
  * Synchronous.  Errors: YS_EINVAL (bad level / NULL field), YS_ECUDA. */
 int ys_set_fields(ys_ctx *c, int level, const double *T, const double *ur, const double *uth,
                   const double *uph, const double *p);
@@ -168,14 +170,19 @@ int ys_set_time(ys_ctx *c, double t);
  * splitting-error-reduction iterations (Sec. 4, Eq. er).  Per iteration:
  * exchange boundary values, defect-correct T, then u1 (r, theta, phi), p1,
  * u2 (r, theta, phi), p2, each correction through three line sweeps.
- * Returns YS_EDIVERGED (state restored to the last good step) if a norm
- * becomes NaN/Inf.  Asynchronous on the context's stream unless
- * schwarz_tol > 0 (then it synchronises once per iteration). */
+ * The work is queued on the context's stream; the call returns once the last
+ * step's increment norms have been read back (with schwarz_tol > 0 it also
+ * waits for the norms after every iteration).  Returns YS_EDIVERGED if one
+ * of those norms is NaN or Inf (a divergence in an earlier step propagates to
+ * it); the state then holds the diverged values and the caller restarts
+ * from its own copy (ys_get_fields / ys_set_fields restart exactly). */
 int ys_step(ys_ctx *c, int n_steps, int n_schwarz);
 
 /* Copy time level `level` to host buffers (u2 and p2, the second-order
  * solution); any pointer may be NULL to skip that field.  aux != NULL
- * receives [ur1 | uth1 | uph1 | p1].  Synchronous. */
+ * receives [ur1 | uth1 | uph1 | p1].  Page-locked host buffers are written
+ * by the device directly, pageable ones through one staging copy.
+ * Synchronous.  Errors: YS_EINVAL (bad level), YS_ECUDA. */
 int ys_get_fields(ys_ctx *c, int level, double *T, double *ur, double *uth, double *uph,
                   double *p, double *aux);
 
