@@ -28,9 +28,10 @@
  *
  * Geometry: each patch covers theta in [pi/4 - d, 3pi/4 + d],
  * phi in [-3pi/4 - d, 3pi/4 + d] of its own frame with d = overlap * h_theta,
- * h_theta = (pi/2)/(Nth - 2 overlap), h_phi = (3pi/2 + 2d)/Nph, uniform
- * h_r = (R2 - R1)/Nr.  The Yang frame is the Yin frame composed with
- * M(x, y, z) = (-x, z, y) (Sec. 2).
+ * h_theta = (pi/2)/(Nth - 2 overlap), h_phi = (3pi/2 + 2d)/Nph; radially
+ * uniform h_r = (R2 - R1)/Nr by default, or the half points of
+ * ys_params.r_half (a non-uniform radial grid).  The Yang frame is the Yin
+ * frame composed with M(x, y, z) = (-x, z, y) (Sec. 2).
  *
  * Threading: a context is not thread-safe; distinct contexts may be used
  * from distinct threads.
@@ -50,7 +51,7 @@ extern "C" {
 #define YS_EINVAL 1     /* invalid argument or grid too coarse for the exchange */
 #define YS_ENOMEM 2     /* device or host allocation failed */
 #define YS_ECUDA 3      /* CUDA error (no device, launch failure, ...) */
-#define YS_EDIVERGED 4  /* NaN/Inf or Schwarz blow-up; state left at the last good step */
+#define YS_EDIVERGED 4  /* NaN/Inf increment norms: the state holds the diverged values */
 #define YS_ETIMEOUT 5   /* a bounded device wait gave up */
 #define YS_EAGAIN 6     /* result not ready yet */
 #define YS_EBUSY 7      /* admission refused: queue full */
@@ -253,7 +254,7 @@ int ys_destroy(ys_ctx *c);
 /* ------------------------------------------------------------------------
  * Batched ensembles.  A batch advances many independent shells (contexts
  * created with ys_create_ex and filled with ys_set_fields, uneven sizes,
- * Ra, Pr allowed) together: every kernel class of the AC step is one launch
+ * Ra, Pr and radial grids allowed) together: every kernel class of the AC step is one launch
  * over all member shells, and a whole step is replayed from one captured CUDA
  * graph that stays valid while shells join and leave.  Members must share the
  * batch's precision, use additive Schwarz and have no forcing modes; all run
