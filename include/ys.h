@@ -251,6 +251,20 @@ int ys_factor_solve_static(const ys_params *prm, int loc, const double *A_r, con
 
 int ys_destroy(ys_ctx *c);
 
+/* Diagnostic, host only (builds the tables without touching a device): the
+ * FP64 coefficients of the 1-D line operators (I - dt/2 Ahat_d) (Sec. 3.2,
+ * Sec. 4; T, u_r, u_theta, u_phi along r, theta, phi) that the
+ * factorisations use for the shell *p.  The row of the operator at a point
+ * whose advecting velocity component along d is a is
+ * (L0 + a LA, D0, U0 - a LA) on (x_{m-1}, x_m, x_{m+1}), before the wall and
+ * line-end rows are closed.  Layout: out[((3 loc + d) (Nr + 2) + i + 1)
+ * (Nth + 2) + j + 1][4] = {L0, D0, U0, LA} with loc 0..3 = T, u_r, u_theta,
+ * u_phi and d 0..2 = r, theta, phi; entries of points that are not unknowns
+ * are zero.  *count receives the number of doubles (12 (Nr + 2) (Nth + 2) 4);
+ * out = NULL only queries it.  Errors: YS_EINVAL (bad parameters, cap too
+ * small, NULL count). */
+int ys_line_coefficients(const ys_params *p, double *out, size_t cap, size_t *count);
+
 /* ------------------------------------------------------------------------
  * Batched ensembles.  A batch advances many independent shells (contexts
  * created with ys_create_ex and filled with ys_set_fields, uneven sizes,

@@ -518,6 +518,28 @@ int ys_destroy(ys_ctx *c) {
   return YS_OK;
 }
 
+int ys_line_coefficients(const ys_params *p, double *out, size_t cap, size_t *count) {
+  if (!count) return YS_EINVAL;
+  int rc = validate(p);
+  if (rc) return rc;
+  GridSpec gs{p->R1, p->R2, p->Nr, p->Nth, p->Nph, p->overlap, p->r_half};
+  GridGeo G;
+  if (make_grid(gs, G)) return YS_EINVAL;
+  const size_t n = (size_t)kFacTables * (p->Nr + 2) * (p->Nth + 2) * FC_M;
+  *count = n;
+  if (!out) return YS_OK;
+  if (cap < n) return YS_EINVAL;
+  std::vector<double> met, fact;
+  int pad, len;
+  make_metric(gs, G, met, pad, len);
+  const double s1 = std::sin(G.th0);
+  FacPhys fp{p->dt, p->Pr, 1.0, 1.0 / (2.0 * p->chi), 1.0 / (p->R1 * p->R1),
+             1.0 / (p->R1 * p->R1 * s1 * s1 * G.hp * G.hp)};
+  make_faccoef(gs, G, met, pad, len, fp, fact);
+  std::memcpy(out, fact.data(), n * sizeof(double));
+  return YS_OK;
+}
+
 int ys_create_ex(const ys_params *p, ys_ctx **out) {
   if (!out) return YS_EINVAL;
   *out = nullptr;
