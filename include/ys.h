@@ -265,6 +265,28 @@ int ys_destroy(ys_ctx *c);
  * small, NULL count). */
 int ys_line_coefficients(const ys_params *p, double *out, size_t cap, size_t *count);
 
+/* Diagnostic, host only: the FP64 row-coefficient records of the explicit
+ * residuals (Sec. 3.3) of the FP64 form for the shell *p.  Every metric factor
+ * of a residual stencil depends on the row (i, j) only; a record holds, for
+ * one row, the products of metric factors, spacings, dt and the physical
+ * constants that multiply the stencil values, written for the two-level sums
+ * S = x + x^n (so that the half-level value is S/2).  table: 0 temperature,
+ * 1 u_r, 2 u_theta, 3 u_phi, 4 divergence.  Record orders:
+ *   0: (S_i+1 - S_i), (S_i - S_i-1), same along theta, S_k+1 - 2 S_k + S_k-1
+ *      (diffusion: RP, RM, TP, TM, PP, the minus sign of RM, TM applied by
+ *      the stencil), a_r (S_i+1 - S_i-1), a_th (..), a_ph (..) with a the
+ *      2-point sums of the advecting velocity (AR, AT, AP), the two
+ *      deviation-form sources (zero here);
+ *   4: S_r(i+1), S_r(i), S_th(j+1), S_th(j), S_ph(k+1) - S_ph(k) (R1, R0, T1,
+ *      T0, P: the divergence of the half-level velocity over chi as
+ *      R1 S_r(i+1) - R0 S_r(i) + T1 S_th(j+1) - T0 S_th(j) + P (..)), then the
+ *      norm weight r^2 sin(theta) h / h_r of the cell;
+ *   1-3: the velocity rows (orders of their kernels, not a stable interface).
+ * Layout out[(i + 1) (Nth + 2) + j + 1][*record]; rows of points that are not
+ * unknowns are zero.  *count receives the number of doubles; out = NULL only
+ * queries.  Errors: YS_EINVAL. */
+int ys_residual_coefficients(const ys_params *p, int table, double *out, size_t cap, size_t *count, int *record);
+
 /* ------------------------------------------------------------------------
  * Batched ensembles.  A batch advances many independent shells (contexts
  * created with ys_create_ex and filled with ys_set_fields, uneven sizes,

@@ -540,6 +540,27 @@ int ys_line_coefficients(const ys_params *p, double *out, size_t cap, size_t *co
   return YS_OK;
 }
 
+int ys_residual_coefficients(const ys_params *p, int table, double *out, size_t cap, size_t *count, int *record) {
+  if (!count || !record || table < 0 || table >= kRowTables) return YS_EINVAL;
+  int rc = validate(p);
+  if (rc) return rc;
+  GridSpec gs{p->R1, p->R2, p->Nr, p->Nth, p->Nph, p->overlap, p->r_half};
+  GridGeo G;
+  if (make_grid(gs, G)) return YS_EINVAL;
+  *record = row_m(table);
+  const size_t n = (size_t)(p->Nr + 2) * (p->Nth + 2) * row_m(table);
+  *count = n;
+  if (!out) return YS_OK;
+  if (cap < n) return YS_EINVAL;
+  std::vector<double> met, rowt[kRowTables];
+  int pad, len;
+  make_metric(gs, G, met, pad, len);
+  RowPhys ph{p->dt, p->Pr, 1.0, 1.0 / (2.0 * p->chi), p->Pr * p->Ra, nullptr, nullptr};
+  make_rowcoef(gs, G, met, pad, len, ph, rowt);
+  std::memcpy(out, rowt[table].data(), n * sizeof(double));
+  return YS_OK;
+}
+
 int ys_create_ex(const ys_params *p, ys_ctx **out) {
   if (!out) return YS_EINVAL;
   *out = nullptr;
