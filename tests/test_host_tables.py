@@ -116,3 +116,86 @@ def test_host_residual_records_match_the_oracle_operators(beta):
     assert np.abs(D - ref).max() <= 1e-12 * np.abs(ref).max()
     w = g.weight(C) / (g.hr * g.hth * g.hph)
     assert np.abs(np.broadcast_to(d[..., 5], w.shape) - w).max() <= 1e-13 * np.abs(w).max()
+
+
+@pytest.mark.parametrize("beta", [None, 0.5])
+def test_host_velocity_records_match_the_oracle_rates(beta):
+    """The u_r, u_theta, u_phi records applied as the residual kernels apply
+    them (two-level sums S of the three components, the 4-point sums of the
+    advecting velocity, the pressure entering the row and, for u_r, the
+    temperature sum) give dt times the oracle's rates (vector Laplacian,
+    advection with curvature terms, -grad P, grad div / (2 chi), buoyancy) at
+    every unknown, on a uniform and a stretched radial grid."""
+    from oracle.grid import view
+    from paper_1905_02300_gb300 import ys
+    Nr, Nt, Np, dt, Pr, Ra, chi = 8, 12, 36, 0.02, 0.7, 3.0, 1.3
+    rh = None if beta is None else W.stretched_radii(0.5, 1.0, Nr, beta)
+    kw = dict(R1=0.5, R2=1.0, Pr=Pr, Ra=Ra, dt=dt, Nr=Nr, Nth=Nt, Nph=Np, chi=chi, r_half=rh)
+    g = Grid(0.5, 1.0, Nr, Nt, Np, r_half=rh)
+    rng = np.random.default_rng(11)
+    Sr, St, Sp, ST, P = (rng.normal(size=g.shape) for _ in range(5))
+    A = [rng.uniform(-2.0, 2.0, size=g.shape) for _ in range(3)]
+    U = [0.5 * Sr, 0.5 * St, 0.5 * Sp]
+    D = ops.padded(g, ops.divergence(g, U))
+
+    def records(table, loc):
+        i0, i1, j0, j1, _, _ = g.region(loc)
+        c = residual_table(ys, kw, table)[i0 + 1:i1 + 1, j0 + 1:j1 + 1][None, :, :, None, :]
+        return lambda m: c[..., m]
+
+    def diff(c, v, X):
+        S0 = v(X)
+        return (c(0) * (v(X, 1) - S0) - c(1) * (S0 - v(X, -1)) + c(2) * (v(X, 0, 1) - S0)
+                - c(3) * (S0 - v(X, 0, -1)) + c(4) * (v(X, 0, 0, 1) - 2 * S0 + v(X, 0, 0, -1)))
+
+    def sum4(a):
+        return ((a[0] + a[1]) + a[2]) + a[3]
+
+    checks = []
+    # u_r at r-faces: own S_r, S_th and S_ph around the face, T sums
+    v = lambda a, di=0, dj=0, dk=0: view(a, g.region(R), di, dj, dk)
+    c = records(1, R)
+    y1, y0, ym1, ym0 = v(St, 0, 1), v(St), v(St, -1, 1), v(St, -1)
+    z1, z0, zm1, zm0 = v(Sp, 0, 0, 1), v(Sp), v(Sp, -1, 0, 1), v(Sp, -1)
+    sAt = sum4([v(A[1], -1), v(A[1], -1, 1), v(A[1]), v(A[1], 0, 1)])
+    sAp = sum4([v(A[2], -1), v(A[2], -1, 0, 1), v(A[2]), v(A[2], 0, 0, 1)])
+    out = (diff(c, v, Sr) + c(5) * v(Sr, 1) + c(6) * v(Sr) + c(7) * v(Sr, -1)
+           + c(8) * y1 + c(9) * y0 + c(10) * ym1 + c(11) * ym0 + c(12) * (z1 - z0) + c(13) * (zm1 - zm0)
+           - c(14) * v(A[0]) * (v(Sr, 1) - v(Sr, -1))
+           + sAt * (c(17) * sum4([ym0, ym1, y0, y1]) - c(15) * (v(Sr, 0, 1) - v(Sr, 0, -1)))
+           + sAp * (c(17) * sum4([zm0, zm1, z0, z1]) - c(16) * (v(Sr, 0, 0, 1) - v(Sr, 0, 0, -1)))
+           - c(18) * (v(P) - v(P, -1)) + c(19) * (v(ST, -1) + v(ST)))
+    checks.append(("ur", out, dt * ops.rate_ur(g, U, A, P, D, 0.5 * ST, 0.0, Pr, chi, Pr * Ra)))
+    # u_theta at theta-faces: own S_th, S_r and S_ph around the face
+    v = lambda a, di=0, dj=0, dk=0: view(a, g.region(TH), di, dj, dk)
+    c = records(2, TH)
+    w1, w0, wm1, wm0 = v(Sr, 1), v(Sr), v(Sr, 1, -1), v(Sr, 0, -1)
+    z1, z0, zm1, zm0 = v(Sp, 0, 0, 1), v(Sp), v(Sp, 0, -1, 1), v(Sp, 0, -1)
+    sAr = sum4([v(A[0], 0, -1), v(A[0], 1, -1), v(A[0]), v(A[0], 1)])
+    sAp = sum4([v(A[2], 0, -1), v(A[2], 0, -1, 1), v(A[2]), v(A[2], 0, 0, 1)])
+    at = v(A[1])
+    out = (diff(c, v, St) + c(5) * v(St, 0, 1) + c(6) * v(St) + c(7) * v(St, 0, -1)
+           + c(8) * w1 + c(9) * w0 + c(10) * wm1 + c(11) * wm0 + c(12) * (z1 - z0) + c(13) * (zm1 - zm0)
+           - c(14) * sAr * (v(St, 1) - v(St, -1))
+           - at * (c(15) * (v(St, 0, 1) - v(St, 0, -1)) + c(17) * sum4([wm0, wm1, w0, w1]))
+           + sAp * (c(18) * sum4([zm0, zm1, z0, z1]) - c(16) * (v(St, 0, 0, 1) - v(St, 0, 0, -1)))
+           - c(19) * (v(P) - v(P, 0, -1)))
+    checks.append(("ut", out, dt * ops.rate_ut(g, U, A, P, D, 0.0, Pr, chi)))
+    # u_phi at phi-faces: own S_ph, S_r and S_th around the face
+    v = lambda a, di=0, dj=0, dk=0: view(a, g.region(PH), di, dj, dk)
+    c = records(3, PH)
+    w1, w0, wm1, wm0 = v(Sr, 1), v(Sr), v(Sr, 1, 0, -1), v(Sr, 0, 0, -1)
+    y1, y0, ym1, ym0 = v(St, 0, 1), v(St), v(St, 0, 1, -1), v(St, 0, 0, -1)
+    sAr = sum4([v(A[0], 0, 0, -1), v(A[0], 1, 0, -1), v(A[0]), v(A[0], 1)])
+    sAt = sum4([v(A[1], 0, 0, -1), v(A[1], 0, 1, -1), v(A[1]), v(A[1], 0, 1)])
+    ap = v(A[2])
+    out = (diff(c, v, Sp) + c(5) * v(Sp) + c(6) * w1 + c(7) * w0 + c(8) * wm1 + c(9) * wm0
+           + c(10) * y1 + c(11) * y0 + c(12) * ym1 + c(13) * ym0
+           - c(14) * sAr * (v(Sp, 1) - v(Sp, -1)) - c(15) * sAt * (v(Sp, 0, 1) - v(Sp, 0, -1))
+           - ap * (c(16) * (v(Sp, 0, 0, 1) - v(Sp, 0, 0, -1)) + c(17) * sum4([wm0, wm1, w0, w1])
+                   + c(18) * sum4([ym0, ym1, y0, y1]))
+           - c(19) * (v(P) - v(P, 0, 0, -1)))
+    checks.append(("up", out, dt * ops.rate_up(g, U, A, P, D, 0.0, Pr, chi)))
+    for name, got, ref in checks:
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= 1e-12, (name, err)
