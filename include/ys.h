@@ -287,6 +287,23 @@ int ys_line_coefficients(const ys_params *p, double *out, size_t cap, size_t *co
  * queries.  Errors: YS_EINVAL. */
 int ys_residual_coefficients(const ys_params *p, int table, double *out, size_t cap, size_t *count, int *record);
 
+/* Diagnostic, host only: the Yin <-> Yang exchange table of one kind (Sec. 4,
+ * Algorithm steps 1, 3 and 7) that the library builds for the shell *p and
+ * uses on both patches.  kind: 0 temperature (theta-ghost rows and
+ * phi-ghost columns, every radial cell), 1 u_r (the same points, interior
+ * radial faces), 2 u_theta (edge faces j = 0, Nth and phi-ghosts), 3 u_phi
+ * (edge faces k = 0, Nph and theta-ghosts), 4 the pressure ring (outermost
+ * interior cells).  Each target point is one record of 12 doubles:
+ * (tj, tk, j0a, k0a, wja, wka, j0b, k0b, wjb, wkb, ra, rb): the target's
+ * logical (j, k); donor stencil A, the tensor bilinear stencil on the other
+ * patch at the same radial index with base (j0a, k0a) and weights (wja, wka)
+ * along theta and phi, of T, u_r or p (kinds 0, 1, 4) or of u_theta (2, 3);
+ * stencil B, of u_phi (kinds 2, 3; zero otherwise); the target value is
+ * ra A + rb B (ra = 1, rb = 0 for scalars).  *count receives the number of
+ * doubles (12 per point); out = NULL only queries.  Errors: YS_EINVAL (bad
+ * parameters, grid too coarse for the donor stencils, cap too small). */
+int ys_exchange_table(const ys_params *p, int kind, double *out, size_t cap, size_t *count);
+
 /* ------------------------------------------------------------------------
  * Batched ensembles.  A batch advances many independent shells (contexts
  * created with ys_create_ex and filled with ys_set_fields, uneven sizes,

@@ -561,6 +561,29 @@ int ys_residual_coefficients(const ys_params *p, int table, double *out, size_t 
   return YS_OK;
 }
 
+int ys_exchange_table(const ys_params *p, int kind, double *out, size_t cap, size_t *count) {
+  if (!count || kind < 0 || kind >= XNUM) return YS_EINVAL;
+  int rc = validate(p);
+  if (rc) return rc;
+  GridSpec gs{p->R1, p->R2, p->Nr, p->Nth, p->Nph, p->overlap, p->r_half};
+  GridGeo G;
+  if (make_grid(gs, G)) return YS_EINVAL;
+  std::vector<XEntry> xt[XNUM];
+  if (make_exchange(gs, G, xt)) return YS_EINVAL;
+  const std::vector<XEntry> &T = xt[kind];
+  const size_t n = T.size() * 12;
+  *count = n;
+  if (!out) return YS_OK;
+  if (cap < n) return YS_EINVAL;
+  for (size_t e = 0; e < T.size(); ++e) {
+    const XEntry &x = T[e];
+    const double rec[12] = {(double)x.tj, (double)x.tk, (double)x.j0a, (double)x.k0a, x.wja, x.wka,
+                            (double)x.j0b, (double)x.k0b, x.wjb, x.wkb, x.ra, x.rb};
+    std::memcpy(out + 12 * e, rec, sizeof rec);
+  }
+  return YS_OK;
+}
+
 int ys_create_ex(const ys_params *p, ys_ctx **out) {
   if (!out) return YS_EINVAL;
   *out = nullptr;

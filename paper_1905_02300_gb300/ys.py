@@ -63,6 +63,7 @@ _sig = {
     "ys_line_coefficients": (C.c_int, [C.POINTER(Params), C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "ys_residual_coefficients": (C.c_int, [C.POINTER(Params), C.c_int, C.c_void_p, C.c_size_t,
                                            C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
+    "ys_exchange_table": (C.c_int, [C.POINTER(Params), C.c_int, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "ys_strerror": (C.c_char_p, [C.c_int]),
     "ys_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
     "ys_batch_add": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),

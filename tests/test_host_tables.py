@@ -199,3 +199,77 @@ def test_host_velocity_records_match_the_oracle_rates(beta):
     for name, got, ref in checks:
         err = np.abs(got - ref).max() / np.abs(ref).max()
         assert err <= 1e-12, (name, err)
+
+
+XKINDS = ("T", "ur", "uth", "uph", "p")
+
+
+def exchange_table(ys, kw, kind):
+    p = ys.default_params(**kw)
+    n = ctypes.c_size_t(0)
+    rc = ys.lib.ys_exchange_table(ctypes.byref(p), kind, None, 0, ctypes.byref(n))
+    if rc != ys.YS_OK:
+        return rc, None
+    out = np.zeros(n.value)
+    assert ys.lib.ys_exchange_table(ctypes.byref(p), kind, out.ctypes.data, n.value, ctypes.byref(n)) == ys.YS_OK
+    return rc, out.reshape(-1, 12)
+
+
+def same_stencil(got, ref, name):
+    """Bilinear stencils (j0, k0, wj, wk) agree: the donor coordinates
+    j0 + wj and k0 + wk, which fix the interpolated value, to rounding; the
+    bases exactly, except where a coordinate falls on a grid line to rounding,
+    where base j0 with weight 1 and base j0 + 1 with weight 0 are the same
+    stencil (the floor of the two sides may break that tie either way)."""
+    for a in (0, 1):
+        b, w = got[:, a], got[:, 2 + a]
+        rb, rw = ref[a], ref[2 + a]
+        assert np.abs((b + w) - (rb + rw)).max() <= 1e-12, name
+        tie = b != rb
+        assert np.all(np.abs(b - rb)[tie] == 1), name
+        assert np.all(np.minimum(np.abs(w[tie]), np.abs(1 - w[tie])) <= 1e-12), name
+        assert tie.sum() <= 2, (name, int(tie.sum()))
+
+
+@pytest.mark.parametrize("dims", [(8, 12, 36, 2), (8, 17, 41, 2), (9, 20, 60, 3), (8, 9, 27, 1)])
+def test_host_exchange_tables_match_the_oracle(dims):
+    """Target points, donor stencil bases (exact), bilinear weights and the
+    2x2 rotation rows of the host-built Yin <-> Yang tables equal the oracle's
+    ExchangeTables (Sec. 4), kind by kind, in the oracle's point order; the
+    rotation rows are unit vectors (the target's tangent basis vector lies in
+    the plane of the donor's mapped tangent basis at the same point)."""
+    from oracle.exchange import ExchangeTables
+    from paper_1905_02300_gb300 import ys
+    Nr, Nt, Np, ov = dims
+    kw = dict(R1=0.5, R2=1.0, Pr=1.0, Ra=0.0, dt=1e-3, Nr=Nr, Nth=Nt, Nph=Np, overlap=ov)
+    ref = ExchangeTables(Grid(0.5, 1.0, Nr, Nt, Np, overlap=ov)).tab
+    for kind, name in enumerate(XKINDS):
+        rc, t = exchange_table(ys, kw, kind)
+        assert rc == ys.YS_OK, (name, rc)
+        e = ref[name]
+        assert t.shape[0] == len(e["j"]), name
+        np.testing.assert_array_equal(t[:, 0], e["j"])
+        np.testing.assert_array_equal(t[:, 1], e["k"])
+        sa, sb = (e["s"], None) if "s" in e else (e["st"], e["sp"])
+        same_stencil(t[:, 2:6], sa, name)
+        if sb is None:
+            assert np.all(t[:, 6:10] == 0) and np.all(t[:, 10] == 1) and np.all(t[:, 11] == 0), name
+        else:
+            same_stencil(t[:, 6:10], sb, name)
+            assert np.abs(t[:, 10] - e["rot"][0]).max() <= 1e-13, name
+            assert np.abs(t[:, 11] - e["rot"][1]).max() <= 1e-13, name
+            assert np.abs(np.hypot(t[:, 10], t[:, 11]) - 1.0).max() <= 1e-13, name
+        assert np.all((t[:, 4:6] >= 0) & (t[:, 4:6] < 1)), name
+
+
+def test_exchange_table_argument_checks():
+    from paper_1905_02300_gb300 import ys
+    kw = dict(R1=0.5, R2=1.0, Pr=1.0, Ra=0.0, dt=1e-3, Nr=8, Nth=12, Nph=36)
+    p = ys.default_params(**kw)
+    n = ctypes.c_size_t(0)
+    assert ys.lib.ys_exchange_table(ctypes.byref(p), 0, None, 0, None) == ys.YS_EINVAL
+    assert ys.lib.ys_exchange_table(ctypes.byref(p), 5, None, 0, ctypes.byref(n)) == ys.YS_EINVAL
+    assert ys.lib.ys_exchange_table(ctypes.byref(p), -1, None, 0, ctypes.byref(n)) == ys.YS_EINVAL
+    assert ys.lib.ys_exchange_table(ctypes.byref(p), 4, None, 0, ctypes.byref(n)) == ys.YS_OK
+    small = np.zeros(12)
+    assert ys.lib.ys_exchange_table(ctypes.byref(p), 4, small.ctypes.data, 12, ctypes.byref(n)) == ys.YS_EINVAL
