@@ -216,6 +216,11 @@ long ys_launch_count(ys_ctx *c);
 
 /* Bytes of device memory held by the context. */
 size_t ys_device_bytes(ys_ctx *c);
+/* Host only (no GPU): the bytes of device memory ys_create_ex allocates for
+ * *p, which ys_device_bytes of the new context reports until forcing modes
+ * or a wall velocity are added; the serving queue admits requests by this
+ * figure.  0 for parameters ys_create_ex rejects. */
+size_t ys_shell_device_bytes(const ys_params *p);
 
 /* Allocation-free preconditioner solve (the paper has no counterpart; this is
  * a library convenience).  Some callers cannot call cudaMalloc: code running

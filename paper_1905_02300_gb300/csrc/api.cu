@@ -450,6 +450,58 @@ char *carve(ys_ctx *c, Fields<R> &D, char *base) {
 // number of bulk fields of one shell (3 x 7 levels, 3 a, 4 forcing, B, Cs, 36 factors, 9 sums of a)
 constexpr size_t kBulkFields = 3 * 7 + 3 + 4 + 2 + 36 + 9;
 
+// padded field layout of a shell (both patches)
+void set_layout(const ys_params *p, Layout &L) {
+  L.Nr = p->Nr;
+  L.Nt = p->Nth;
+  L.Np = p->Nph;
+  L.NJ = p->Nth + 2;
+  L.P = ((p->Nph + 2) + 7) / 8 * 8;
+  L.SI = (long)L.NJ * L.P;
+  long box = (long)(p->Nr + 2) * L.SI + 16;
+  L.PS = (box + 31) / 32 * 32;
+  L.total = 2 * L.PS;
+}
+
+// Byte offsets of the parts of a shell's one device allocation, in order: bulk
+// fields, FP64 pressures, metric tables (FP64, FP32 pairs), row tables (FP64,
+// FP32; the line-operator tables follow the residual tables), exchange
+// entries, the deviation profiles, norms, staging.  ys_create_ex allocates
+// `total` bytes; the serving queue admits shells by the same figure.
+struct ShellPlan {
+  size_t row_off[kRowTables], fac_off, row_elems;
+  size_t off_metric, off_fmet, off_rowd, off_rowf, off_x, off_dev, off_norm, off_stage, total;
+};
+
+ShellPlan plan_shell(const Layout &L, bool mixed, size_t met_n, const size_t (&row_n)[kRowTables], size_t fact_n,
+                     size_t xcount) {
+  ShellPlan s{};
+  const size_t Rsz = mixed ? sizeof(float) : sizeof(double);
+  const size_t bulk_bytes = ((kBulkFields * L.total * Rsz + 255) / 256) * 256;
+  const size_t p_bytes = ((kPresFields * L.total * sizeof(double) + 255) / 256) * 256;
+  size_t stage_elems = user_elems(L, LR);
+  if (user_elems(L, LT) > stage_elems) stage_elems = user_elems(L, LT);
+  if (user_elems(L, LP) > stage_elems) stage_elems = user_elems(L, LP);
+  s.row_elems = 0;
+  for (int t = 0; t < kRowTables; ++t) {
+    s.row_off[t] = s.row_elems;
+    s.row_elems += (row_n[t] + 31) / 32 * 32;
+  }
+  s.fac_off = s.row_elems;
+  s.row_elems += (fact_n + 31) / 32 * 32;
+  s.off_metric = bulk_bytes + p_bytes;
+  s.off_fmet = s.off_metric + ((met_n * sizeof(double) + 255) / 256) * 256;
+  s.off_rowd = s.off_fmet + ((2 * met_n * sizeof(float) + 255) / 256) * 256;
+  s.off_rowf = s.off_rowd + ((s.row_elems * sizeof(double) + 255) / 256) * 256;
+  s.off_x = s.off_rowf + ((s.row_elems * sizeof(float) + 255) / 256) * 256;
+  s.off_dev = s.off_x + ((xcount * sizeof(XEntry) + 255) / 256) * 256;
+  const size_t dev_bytes = ((4 * (size_t)(L.Nr + 2) * sizeof(double) + 255) / 256) * 256;
+  s.off_norm = s.off_dev + dev_bytes;
+  s.off_stage = s.off_norm + 256;
+  s.total = s.off_stage + stage_elems * sizeof(double);
+  return s;
+}
+
 }  // namespace
 
 extern "C" {
@@ -584,6 +636,31 @@ int ys_exchange_table(const ys_params *p, int kind, double *out, size_t cap, siz
   return YS_OK;
 }
 
+size_t ys_shell_device_bytes(const ys_params *p) {
+  if (validate(p)) return 0;
+  GridSpec gs{p->R1, p->R2, p->Nr, p->Nth, p->Nph, p->overlap, p->r_half};
+  GridGeo G;
+  if (make_grid(gs, G)) return 0;
+  std::vector<XEntry> xt[XNUM];
+  if (make_exchange(gs, G, xt)) return 0;
+  size_t xcount = 0;
+  for (int k = 0; k < XNUM; ++k) xcount += xt[k].size();
+  std::vector<double> met, rowt[kRowTables], fact;
+  int pad, len;
+  make_metric(gs, G, met, pad, len);
+  RowPhys ph{p->dt, p->Pr, 1.0, 1.0 / (2.0 * p->chi), p->Pr * p->Ra, nullptr, nullptr};
+  make_rowcoef(gs, G, met, pad, len, ph, rowt);
+  const double s1 = std::sin(G.th0);
+  FacPhys fp{p->dt, p->Pr, 1.0, 1.0 / (2.0 * p->chi), 1.0 / (p->R1 * p->R1),
+             1.0 / (p->R1 * p->R1 * s1 * s1 * G.hp * G.hp)};
+  make_faccoef(gs, G, met, pad, len, fp, fact);
+  size_t row_n[kRowTables];
+  for (int t = 0; t < kRowTables; ++t) row_n[t] = rowt[t].size();
+  Layout L;
+  set_layout(p, L);
+  return plan_shell(L, p->precision == YS_MIXED, met.size(), row_n, fact.size(), xcount).total;
+}
+
 int ys_create_ex(const ys_params *p, ys_ctx **out) {
   if (!out) return YS_EINVAL;
   *out = nullptr;
@@ -605,15 +682,7 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
   c->prm.r_half = c->geo.rh.empty() ? nullptr : c->geo.rh.data() + kGhostHalf;
   const bool mixed = (p->precision == YS_MIXED);
   Layout &L = c->L;
-  L.Nr = p->Nr;
-  L.Nt = p->Nth;
-  L.Np = p->Nph;
-  L.NJ = p->Nth + 2;
-  L.P = ((p->Nph + 2) + 7) / 8 * 8;
-  L.SI = (long)L.NJ * L.P;
-  long box = (long)(p->Nr + 2) * L.SI + 16;
-  L.PS = (box + 31) / 32 * 32;
-  L.total = 2 * L.PS;
+  set_layout(p, L);
 
   std::vector<double> met;
   int pad, len;
@@ -638,14 +707,8 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
       if (i > 0) pc[i] = pc[i - 1] + G.hf(i) * p->Pr * p->Ra * 0.5 * (Tc[i] + Tc[i + 1]);
     }
   }
-  size_t Rsz = mixed ? sizeof(float) : sizeof(double);
-  size_t bulk_bytes = ((kBulkFields * L.total * Rsz + 255) / 256) * 256;
-  size_t p_bytes = ((kPresFields * L.total * sizeof(double) + 255) / 256) * 256;
   size_t xcount = 0;
   for (int k = 0; k < XNUM; ++k) xcount += xt[k].size();
-  size_t stage_elems = user_elems(L, LR);
-  if (user_elems(L, LT) > stage_elems) stage_elems = user_elems(L, LT);
-  if (user_elems(L, LP) > stage_elems) stage_elems = user_elems(L, LP);
   // residual row-coefficient tables (FP64 and FP32 copies)
   std::vector<double> rowt[kRowTables];
   RowPhys ph{p->dt, p->Pr, 1.0, 1.0 / (2.0 * p->chi), p->Pr * p->Ra, deviation ? Tlap.data() : nullptr,
@@ -658,23 +721,14 @@ int ys_create_ex(const ys_params *p, ys_ctx **out) {
                1.0 / (p->R1 * p->R1 * s1 * s1 * G.hp * G.hp)};
     make_faccoef(gs, G, met, pad, len, fp, fact);
   }
-  size_t row_elems = 0, row_off[kRowTables];
-  for (int t = 0; t < kRowTables; ++t) {
-    row_off[t] = row_elems;
-    row_elems += (rowt[t].size() + 31) / 32 * 32;
-  }
-  const size_t fac_off = row_elems;   // the line-operator tables follow the residual tables
-  row_elems += (fact.size() + 31) / 32 * 32;
-  size_t off_metric = bulk_bytes + p_bytes;
-  size_t off_fmet = off_metric + ((met.size() * sizeof(double) + 255) / 256) * 256;
-  size_t off_rowd = off_fmet + ((2 * met.size() * sizeof(float) + 255) / 256) * 256;
-  size_t off_rowf = off_rowd + ((row_elems * sizeof(double) + 255) / 256) * 256;
-  size_t off_x = off_rowf + ((row_elems * sizeof(float) + 255) / 256) * 256;
-  size_t off_dev = off_x + ((xcount * sizeof(XEntry) + 255) / 256) * 256;
-  size_t dev_bytes = ((4 * (size_t)(p->Nr + 2) * sizeof(double) + 255) / 256) * 256;
-  size_t off_norm = off_dev + dev_bytes;
-  size_t off_stage = off_norm + 256;
-  size_t total = off_stage + stage_elems * sizeof(double);
+  size_t row_n[kRowTables];
+  for (int t = 0; t < kRowTables; ++t) row_n[t] = rowt[t].size();
+  const ShellPlan plan = plan_shell(L, mixed, met.size(), row_n, fact.size(), xcount);
+  const size_t *row_off = plan.row_off;
+  const size_t fac_off = plan.fac_off, row_elems = plan.row_elems;
+  const size_t off_metric = plan.off_metric, off_fmet = plan.off_fmet, off_rowd = plan.off_rowd;
+  const size_t off_rowf = plan.off_rowf, off_x = plan.off_x, off_dev = plan.off_dev;
+  const size_t off_norm = plan.off_norm, off_stage = plan.off_stage, total = plan.total;
 
   if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
     ys_destroy(c);

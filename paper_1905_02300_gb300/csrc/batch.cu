@@ -868,15 +868,11 @@ void server_loop(ys_server *S) {
 }
 
 size_t footprint(const ys_params &p) {
-  // bulk fields (66), FP64 pressures (6), residual row tables, staging and
-  // the small tables; forcing is not used by served shells
-  size_t elems = 2ul * (p.Nr + 2) * (p.Nth + 2) * (size_t)(((p.Nph + 2) + 7) / 8 * 8) + 64;
-  size_t R = (p.precision == YS_MIXED) ? 4 : 8;
-  size_t rowrec = 0;   // residual and line-operator row records, FP64 + FP32
-  for (int t = 0; t < kRowTables; ++t) rowrec += row_m(t);
-  rowrec += kFacTables * FC_M;
-  size_t rows = (size_t)(p.Nr + 2) * (p.Nth + 2) * rowrec * 12;
-  return elems * (66 * R + 6 * 8) + rows + packed_len(p) * 8 / 2 + (1u << 20);
+  // the shell's own device allocation (exactly what ys_create_ex takes) plus
+  // a margin for its share of the batch's member buffers (maps, norms,
+  // pressure parts); served shells use no forcing modes; 0: invalid
+  const size_t b = ys_shell_device_bytes(&p);
+  return b ? b + (1u << 20) : 0;
 }
 
 }  // namespace
@@ -900,6 +896,8 @@ int ys_submit(ys_server *S, const ys_params *p, const double *init_fields, int n
   if (!S || !p || !init_fields || n_steps < 1 || n_schwarz < 1 || !ticket) return YS_EINVAL;
   if (p->schwarz_mode != YS_ADDITIVE || p->schwarz_tol != 0.0) return YS_EINVAL;
   if (p->r_half) return YS_EINVAL;   // queued requests keep no copy of the radii: uniform grids only
+  const size_t bytes = footprint(*p);
+  if (!bytes || bytes > S->budget) return YS_EINVAL;   // invalid, or can never be admitted
   std::unique_lock<std::mutex> lk(S->mu);
   if (!S->batch) {
     // the first request fixes the batch precision and iteration count
@@ -911,8 +909,6 @@ int ys_submit(ys_server *S, const ys_params *p, const double *init_fields, int n
   }
   if (n_schwarz != S->K || p->precision != S->precision) return YS_EINVAL;
   if (S->queue.size() >= kMaxQueue) return YS_EBUSY;
-  size_t bytes = footprint(*p);
-  if (bytes > S->budget) return YS_EINVAL;   // can never be admitted
   Request *r = new (std::nothrow) Request();
   if (!r) return YS_ENOMEM;
   r->prm = *p;

@@ -57,6 +57,7 @@ _sig = {
     "ys_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_char_p), _dp, C.POINTER(C.c_long), C.c_int]),
     "ys_launch_count": (C.c_long, [C.c_void_p]),
     "ys_device_bytes": (C.c_size_t, [C.c_void_p]),
+    "ys_shell_device_bytes": (C.c_size_t, [C.POINTER(Params)]),
     "ys_destroy": (C.c_int, [C.c_void_p]),
     "ys_factor_solve_static": (C.c_int, [C.POINTER(Params), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p]),

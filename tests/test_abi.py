@@ -64,3 +64,83 @@ def test_invalid_radial_half_points_rejected_without_gpu():
     with pytest.raises(ValueError):
         ys.Solver(**kw, r_half=good[:-1])
 
+
+
+def _layout_bytes(Nr, Nt, Np, mixed, rec_counts, line_count, x_count):
+    """Bytes of one shell's device allocation from the field layout of
+    include/ys.h: 75 bulk fields (3 levels x 7 unknowns, 3 advecting
+    velocities, 4 forcing combinations, 2 work fields, 36 line-factor fields,
+    9 per-step sums of the advecting velocity) of the precision's size, 6 FP64
+    pressures, the 14 metric tables of max(Nr, Nth) + 6 entries (FP64 and
+    FP32 pairs), the row tables (FP64 and FP32, each padded to 32 entries),
+    the exchange entries (72 bytes each: 6 ints, 6 doubles), 4 deviation profiles of Nr + 2
+    values, the norms and the staging buffer of the largest face-centred
+    field; each part rounded up to 256 bytes."""
+    r256 = lambda b: (b + 255) // 256 * 256
+    P = ((Np + 2) + 7) // 8 * 8
+    total = 2 * (((Nr + 2) * (Nt + 2) * P + 16 + 31) // 32 * 32)
+    R = 4 if mixed else 8
+    met = 14 * (max(Nr, Nt) + 6)
+    rows = sum((n + 31) // 32 * 32 for n in rec_counts) + (line_count + 31) // 32 * 32
+    stage = 2 * max((Nr + 1) * Nt * Np, Nr * (Nt + 1) * Np, Nr * Nt * (Np + 1))
+    return (r256(75 * total * R) + r256(6 * total * 8) + r256(met * 8) + r256(2 * met * 4) + r256(rows * 8)
+            + r256(rows * 4) + r256(x_count * 72) + r256(4 * (Nr + 2) * 8) + 256 + stage * 8)
+
+
+@pytest.mark.parametrize("dims", [(8, 12, 36), (16, 16, 48), (13, 17, 51), (128, 128, 384)])
+@pytest.mark.parametrize("mixed", [False, True])
+def test_shell_device_bytes_match_the_layout(dims, mixed):
+    """ys_shell_device_bytes (what ys_create_ex allocates and the serving queue
+    admits by) counts every part of the documented layout; a stretched radial
+    grid takes the same memory; invalid parameters give 0."""
+    import numpy as np
+    from paper_1905_02300_gb300 import ys, workloads as W
+    Nr, Nt, Np = dims
+    kw = dict(R1=0.5, R2=1.0, Pr=1.0, Ra=1e3, dt=1e-3, Nr=Nr, Nth=Nt, Nph=Np,
+              precision=ys.YS_MIXED if mixed else ys.YS_FP64)
+    p = ys.default_params(**kw)
+    n, rec = ctypes.c_size_t(0), ctypes.c_int(0)
+    recs = []
+    for t in range(5):
+        assert ys.lib.ys_residual_coefficients(ctypes.byref(p), t, None, 0, ctypes.byref(n), ctypes.byref(rec)) == 0
+        recs.append(n.value)
+    assert ys.lib.ys_line_coefficients(ctypes.byref(p), None, 0, ctypes.byref(n)) == 0
+    line = n.value
+    xc = 0
+    for k in range(5):
+        assert ys.lib.ys_exchange_table(ctypes.byref(p), k, None, 0, ctypes.byref(n)) == 0
+        xc += n.value // 12
+    got = ys.lib.ys_shell_device_bytes(ctypes.byref(p))
+    assert got == _layout_bytes(Nr, Nt, Np, mixed, recs, line, xc)
+    ps = ys.default_params(**kw, r_half=np.array(W.stretched_radii(0.5, 1.0, Nr, 0.5)))
+    assert ys.lib.ys_shell_device_bytes(ctypes.byref(ps)) == got
+    bad = ys.default_params(**dict(kw, Nr=4))
+    assert ys.lib.ys_shell_device_bytes(ctypes.byref(bad)) == 0
+    assert ys.lib.ys_shell_device_bytes(None) == 0
+
+
+def test_server_rejects_unfit_and_invalid_requests_at_submit():
+    """The serving queue refuses, before any device work, a request whose
+    shell can never fit its memory budget and one with invalid parameters
+    (YS_EINVAL), and one with a non-uniform radial grid."""
+    import numpy as np
+    from paper_1905_02300_gb300 import ys, workloads as W
+    kw = dict(R1=0.5, R2=1.0, Pr=1.0, Ra=1e3, dt=1e-3, Nr=16, Nth=16, Nph=48)
+    p = ys.default_params(**kw)
+    need = ys.lib.ys_shell_device_bytes(ctypes.byref(p))
+    h = ctypes.c_void_p()
+    assert ys.lib.ys_server_create(need // 2, 4, ctypes.byref(h)) == ys.YS_OK
+    try:
+        init = np.zeros(2 * 16 * 16 * 48 * 5 + 2 * (16 * 48 + 16 * 16 * 2))
+        t = ctypes.c_uint64()
+        ptr = init.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        assert ys.lib.ys_submit(h, ctypes.byref(p), ptr, 3, 2, ctypes.byref(t)) == ys.YS_EINVAL
+        bad = ys.default_params(**dict(kw, Nr=4))
+        assert ys.lib.ys_submit(h, ctypes.byref(bad), ptr, 3, 2, ctypes.byref(t)) == ys.YS_EINVAL
+        st = ys.default_params(**kw, r_half=np.array(W.stretched_radii(0.5, 1.0, 16, 0.5)))
+        assert ys.lib.ys_submit(h, ctypes.byref(st), ptr, 3, 2, ctypes.byref(t)) == ys.YS_EINVAL
+        running, queued = ctypes.c_int(-1), ctypes.c_int(-1)
+        assert ys.lib.ys_server_stats(h, None, None, ctypes.byref(running), ctypes.byref(queued), None) == ys.YS_OK
+        assert running.value == 0 and queued.value == 0
+    finally:
+        assert ys.lib.ys_server_destroy(h) == ys.YS_OK

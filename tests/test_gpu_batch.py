@@ -196,3 +196,17 @@ def test_server_failed_request_does_not_poison_others(gpu_lib):
     assert st == ys.Server.DONE
     assert all(np.array_equal(f[k], good[k]) for k in f)
     srv.close()
+
+
+def test_served_footprint_is_the_context_allocation(gpu_lib):
+    """The figure the serving queue admits by (ys_shell_device_bytes, host
+    only) is the device memory a created context holds, for the shells of
+    these tests in both precisions and on a stretched radial grid."""
+    import ctypes
+    ys = gpu_lib
+    for sp in SHELLS + [dict(SHELLS[0], stretch=0.5)]:
+        for prec in (ys.YS_FP64, ys.YS_MIXED):
+            s, kw = make(ys, sp, prec)
+            p = ys.default_params(**kw)
+            assert s.device_bytes() == ys.lib.ys_shell_device_bytes(ctypes.byref(p)), (sp, prec)
+            s.close()
