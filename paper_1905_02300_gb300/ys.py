@@ -341,6 +341,10 @@ class Server:
     def submit(self, fields, n_steps, n_schwarz=3, **params):
         p = default_params(**params)
         buf = pack_fields(fields)
+        Nr, Nt, Np = p.Nr, p.Nth, p.Nph
+        need = 2 * Nr * Nt * Np * 2 + 2 * (Nr + 1) * Nt * Np + 2 * Nr * (Nt + 1) * Np + 2 * Nr * Nt * (Np + 1)
+        if buf.size != need:
+            raise YSError(YS_EINVAL, "ys_submit: fields of %d values, the shell needs %d" % (buf.size, need))
         t = C.c_uint64()
         _check(lib.ys_submit(self.h, C.byref(p), _ptr(buf), n_steps, n_schwarz, C.byref(t)), "ys_submit")
         self.shapes[t.value] = (p.Nr, p.Nth, p.Nph)

@@ -131,7 +131,7 @@ def test_server_rejects_unfit_and_invalid_requests_at_submit():
     h = ctypes.c_void_p()
     assert ys.lib.ys_server_create(need // 2, 4, ctypes.byref(h)) == ys.YS_OK
     try:
-        init = np.zeros(2 * 16 * 16 * 48 * 5 + 2 * (16 * 48 + 16 * 16 * 2))
+        init = np.zeros(2 * 16 * 16 * 48 * 5 + 2 * (16 * 48 + 16 * 48 + 16 * 16))   # packed [T|ur|uth|uph|p]
         t = ctypes.c_uint64()
         ptr = init.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         assert ys.lib.ys_submit(h, ctypes.byref(p), ptr, 3, 2, ctypes.byref(t)) == ys.YS_EINVAL
@@ -144,3 +144,23 @@ def test_server_rejects_unfit_and_invalid_requests_at_submit():
         assert running.value == 0 and queued.value == 0
     finally:
         assert ys.lib.ys_server_destroy(h) == ys.YS_OK
+
+
+def test_server_binding_checks_the_packed_field_length():
+    """The binding refuses fields whose packed length is not the shell's (the
+    library would read past the caller's buffer); with the right length, a
+    shell larger than the budget is refused by the library."""
+    import numpy as np
+    from paper_1905_02300_gb300 import ys
+    Nr, Nt, Np = 8, 12, 36
+    kw = dict(R1=0.5, R2=1.0, Pr=1.0, Ra=0.0, dt=1e-3, Nr=Nr, Nth=Nt, Nph=Np)
+    f = {"T": np.zeros((2, Nr, Nt, Np)), "ur": np.zeros((2, Nr + 1, Nt, Np)), "uth": np.zeros((2, Nr, Nt + 1, Np)),
+         "uph": np.zeros((2, Nr, Nt, Np + 1)), "p": np.zeros((2, Nr, Nt, Np))}
+    for budget, fields in ((1 << 30, dict(f, p=np.zeros((2, Nr, Nt, Np - 1)))), (1 << 10, f)):
+        srv = ys.Server(hbm_budget_bytes=budget, max_slots=2)
+        try:
+            with pytest.raises(ys.YSError) as e:
+                srv.submit(fields, 2, **kw)
+            assert e.value.code == ys.YS_EINVAL
+        finally:
+            srv.close()
