@@ -360,7 +360,7 @@ def run_reference(args):
         oracle_sample(n, K, 1)
     v, el = oracle_sample(n, K, args.steps)
     cores = 1
-    sample = f"{args.steps} AC steps of a {n}x{n}x{3*n}-per-patch shell (same physics, dt, K={K}) on 1 host core"
+    sample = f"{args.steps} AC step{'s' if args.steps != 1 else ''} of a {n}x{n}x{3*n}-per-patch shell (same physics, dt, K={K}) on 1 host core"
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

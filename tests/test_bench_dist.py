@@ -1,6 +1,8 @@
-"""The N > 1 host logic of bench.py (replicas, one process per GPU) on CPU:
+"""The host logic of bench.py on CPU: for N > 1 (replicas, one process per GPU)
 two gloo ranks agree on the slowest rank's time and on the whole-job
-throughput, and the reference arm does its work on rank 0 only."""
+throughput, and the reference arm does its work on rank 0 only; the
+reference arm's JSON line keeps the contract; the GPU arm fails loudly
+without a device."""
 import os
 import socket
 import sys
@@ -58,3 +60,36 @@ def test_reference_arm_runs_on_rank_0_only(monkeypatch):
 
     assert bench.run_reference(Args) == 0
     assert not called
+
+
+def test_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference (the oracle on the host cores, a bounded
+    sample) prints exactly one JSON line with the contract's keys, the
+    cpu_baseline describing the run and an e2e entry with no device copies."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--ref-n", "12"], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_gpu_arm_fails_loudly_without_a_device():
+    """Without a CUDA device the product arm exits non-zero: there is no CPU
+    fallback to measure."""
+    import subprocess
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "1", "--warmup", "3"], cwd=ROOT,
+                         capture_output=True, text=True, timeout=300)
+    assert out.returncode != 0
+    assert not out.stdout.strip()
