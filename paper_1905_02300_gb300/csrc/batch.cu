@@ -824,11 +824,11 @@ void server_loop(ys_server *S) {
     if (run.empty()) continue;
     int rc = ys_batch_step(S->batch, 1);
     if (!rc) rc = ys_batch_sync(S->batch);
-    S->steps_run++;
+    double step_cells = 0.0;   // counters are published under the lock below (ys_server_stats reads them)
     std::vector<Request *> finished;
     for (Request *r : run) {
       r->done_steps++;
-      S->cell_updates += 2.0 * r->prm.Nr * r->prm.Nth * r->prm.Nph;
+      step_cells += 2.0 * r->prm.Nr * r->prm.Nth * r->prm.Nph;
       double nrm[YS_NFIELDS];
       bool bad = rc != 0;
       if (!bad && ys_batch_norms(S->batch, r->slot, nrm) == YS_OK)
@@ -852,6 +852,8 @@ void server_loop(ys_server *S) {
       }
     }
     std::lock_guard<std::mutex> lk(S->mu);
+    S->steps_run++;
+    S->cell_updates += step_cells;
     for (Request *r : finished) {
       r->state = r->error ? 3 : 2;
       r->t_done = std::chrono::steady_clock::now();
