@@ -943,6 +943,7 @@ int ys_set_wall_velocity(ys_ctx *c, const double *ur, const double *uth, const d
       c->dwall = nullptr;
       return YS_ENOMEM;
     }
+    c->dbytes += (n[0] + n[1] + n[2]) * sizeof(double);
   }
   const double **dst[3] = {&c->S.wall_ur, &c->S.wall_ut, &c->S.wall_up};
   size_t off = 0;
