@@ -101,6 +101,39 @@ def test_scalar_interpolation_exact_for_bilinear_functions():
         assert np.abs(got - f(tt, pp)[None]).max() < 1e-13
 
 
+def test_pressure_ring_exact_for_bilinear_functions_and_blind_to_the_donor_ring():
+    """Algorithm step 7: the ring of outermost interior pressure cells is
+    refilled from the other patch.  A pressure bilinear in the donor's local
+    (theta, phi) is reproduced exactly at each ring cell's own position
+    (mapped into the donor frame); the donor stencils stay off the donor's
+    own ring, so garbage there does not reach the result, and both patches
+    can be refilled at once; cells off the ring are left alone."""
+    g = Grid(0.5, 1.0, 3, 16, 48)
+    tables = xch.ExchangeTables(g)
+    f = lambda th, ph: -0.3 + 0.8 * th + 0.5 * ph - 0.6 * th * ph
+    jj, kk = np.arange(-1, g.Nth + 1), np.arange(-1, g.Nph + 1)
+    TH_, PH_ = np.meshgrid(g.th_c(jj), g.ph_c(kk), indexing="ij")
+    P = g.zeros()
+    P[:] = f(TH_, PH_)[None, None]
+    e = tables.tab["p"]
+    ring = np.zeros((g.Nth + 2, g.Nph + 2), bool)
+    ring[e["j"] + 1, e["k"] + 1] = True
+    assert ring.sum() == 2 * g.Nph + 2 * g.Nth - 4
+    rng = np.random.default_rng(3)
+    for p in (0, 1):       # garbage on every ring cell and in the ghosts of both patches
+        P[p][:, ring] = rng.uniform(-1e3, 1e3, size=P[p][:, ring].shape)
+        P[p][:, 0, :] = P[p][:, -1, :] = P[p][:, :, 0] = P[p][:, :, -1] = np.nan
+    inner = P[:, 1:g.Nr + 1].copy()
+    xch.pressure_ring(tables, P, (0, 1))
+    for p in (0, 1):
+        tt, pp = _donor_angles_of_targets(g, p, C, e["j"], e["k"])
+        got = P[p][1:g.Nr + 1, e["j"] + 1, e["k"] + 1]
+        assert np.abs(got - f(tt, pp)[None]).max() < 1e-13
+        off = ~ring
+        off[0, :] = off[-1, :] = off[:, 0] = off[:, -1] = False
+        np.testing.assert_array_equal(P[p][1:g.Nr + 1][:, off], inner[p][:, off])
+
+
 def test_constant_scalar_exact_and_vector_field_second_order():
     errs = []
     for N in (16, 32):
