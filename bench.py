@@ -180,7 +180,7 @@ def oracle_sample(n, K, steps):
 
 
 def ensemble_shells(seed, n, nr_max, nth_max, ys, precision):
-    """Seeded uneven shells (config c4 distribution): convection start with a
+    """Seeded uneven shells (workloads.shell_ensemble): convection start with a
     hot inner wall, dt = 0.5 h_min^2 per shell, h_min the smallest of h_r,
     R1 h_theta and R1 sin(theta_1) h_phi (inside the fixed-iteration stability
     limit dt < chi h^2)."""
@@ -196,7 +196,7 @@ def ensemble_shells(seed, n, nr_max, nth_max, ys, precision):
 
 
 def run_ensemble(args):
-    """Config c4: 64 uneven shells in one batch (one launch per kernel class,
+    """Ensemble workload: 64 uneven shells in one batch (one launch per kernel class,
     one CUDA graph per step, autotuned lines per block), mixed precision,
     against the plain single-shell FP64 path running the same shells one at a
     time."""
@@ -264,8 +264,8 @@ def run_ensemble(args):
 
 
 def run_serving(args):
-    """Config c5, scaled: Poisson arrivals of shell simulations from the c4
-    distribution (Nr <= 64, Nth <= 96), N ~ U{20..80} steps, at 0.8 of the
+    """Serving workload: Poisson arrivals of shell simulations from the uneven-
+    shell ensemble distribution (Nr <= 64, Nth <= 96), N ~ U{20..80} steps, at 0.8 of the
     measured batched capacity; p50/p99 time to completion and aggregate
     cell-updates/s against the same trace served FIFO one at a time by the
     plain FP64 path (replayed with each request's measured FP64 run time)."""
@@ -343,7 +343,7 @@ def run_serving(args):
                                 "p99_s": float(np.percentile(fifo_lat, 99)),
                                 "aggregate_cell_updates_per_s": float(sum(work) / max(free_at, arrivals[-1]))},
             "data": "synthetic", "dtype": "f32+f64",
-            "config": {"workload": f"{R} Poisson-arriving shells (c4 distribution, seed 5), N in [20, 80] steps, "
+            "config": {"workload": f"{R} Poisson-arriving shells (uneven-shell ensemble distribution, seed 5), N in [20, 80] steps, "
                                    f"K=3, mixed FP32/FP64, continuous batching"},
             "server_steps": stats["steps"]}
     print(json.dumps(line), flush=True)
