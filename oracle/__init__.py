@@ -17,8 +17,8 @@ Modules:
   scheme    -- the AC step with Schwarz iterations and splitting-error
                reduction (Sec. 3.3, Sec. 4, Eq. er)
 
-Parity status: the exact values at a finite number of Schwarz iterations are
-pinned only through the pieces (operators against continuous operators, line
+Parity status: scheme.Oracle.step at a finite number of Schwarz iterations is
+"parity unpinned" as a whole: its exact values are pinned only through the pieces (operators against continuous operators, line
 solves against dense LU, fixed point against a dense solve, convergence orders
 against manufactured and closed-form solutions, Yin/Yang congruence).
 """
