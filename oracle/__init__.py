@@ -18,7 +18,8 @@ Modules:
                reduction (Sec. 3.3, Sec. 4, Eq. er)
 
 Parity status: scheme.Oracle.step at a finite number of Schwarz iterations is
-"parity unpinned" as a whole: its exact values are pinned only through the pieces (operators against continuous operators, line
-solves against dense LU, fixed point against a dense solve, convergence orders
-against manufactured and closed-form solutions, Yin/Yang congruence).
+"parity unpinned" as a whole: its exact values are pinned only through the
+pieces (operators against continuous operators, line solves against dense LU,
+fixed point against a dense solve, convergence orders against manufactured and
+closed-form solutions, Yin/Yang congruence).
 """
