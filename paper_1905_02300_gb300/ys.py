@@ -125,6 +125,9 @@ def default_params(**kw) -> Params:
             p.r_half = arr.ctypes.data_as(_dp)
             continue
         setattr(p, k, v)
+    rh = getattr(p, "_r_half", None)
+    if rh is not None and rh.shape != (2 * p.Nr + 1,):
+        raise ValueError("r_half: 2 Nr + 1 radii expected")   # the library reads exactly that many
     return p
 
 
@@ -132,9 +135,6 @@ class Solver:
     """One shell on the GPU (owns a ys_ctx)."""
 
     def __init__(self, **params):
-        rh = params.get("r_half")
-        if rh is not None and len(rh) != 2 * int(params.get("Nr", 0)) + 1:
-            raise ValueError("r_half: 2 Nr + 1 radii expected")
         self.params = default_params(**params)
         h = C.c_void_p()
         _check(lib.ys_create_ex(C.byref(self.params), C.byref(h)), "ys_create_ex")

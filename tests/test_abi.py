@@ -63,6 +63,8 @@ def test_invalid_radial_half_points_rejected_without_gpu():
         assert e.value.code == ys.YS_EINVAL
     with pytest.raises(ValueError):
         ys.Solver(**kw, r_half=good[:-1])
+    with pytest.raises(ValueError):    # every path to the library, not only the Solver
+        ys.default_params(**kw, r_half=np.concatenate([good, good[-1:] + 0.1]))
 
 
 
