@@ -290,6 +290,28 @@ def test_stretched_radial_grid_ragged_and_robin(gpu_lib):
 
 
 
+def test_device_pointer_fields_agree_with_host_buffers(gpu_lib):
+    """ys_set_fields_dev (fields already on the device, e.g. torch tensors)
+    fills the same state as the host-buffer path: the fields after two
+    steps are equal bit for bit."""
+    import torch
+    ys = gpu_lib
+    o, s1, spec, ex = make_pair(ys, with_oracle=False)
+    _, s2, _, _ = make_pair(ys, with_oracle=False)
+    f0 = W.sample_fields(ex, spec, 0.0)
+    keys = ("T", "ur", "uth", "uph", "p")
+    dev = {k: torch.from_numpy(np.ascontiguousarray(f0[k], dtype=np.float64)).to("cuda:0") for k in keys}
+    torch.cuda.synchronize()
+    rc = ys.lib.ys_set_fields_dev(s2.h, 0, *[dev[k].data_ptr() for k in keys], None)
+    assert rc == ys.YS_OK
+    s1.set_fields(0, *[f0[k] for k in keys])
+    s1.step(2, 2)
+    s2.step(2, 2)
+    g1, g2 = s1.get_fields(0), s2.get_fields(0)
+    for k in keys:
+        assert np.array_equal(g1[k], g2[k]), k
+
+
 def test_pinned_and_pageable_host_buffers_agree(gpu_lib):
     """set/get through page-locked host buffers (read and written by the
     (un)pack kernels over the CPU-GPU link) and through pageable ones (staged
