@@ -312,6 +312,29 @@ def test_device_pointer_fields_agree_with_host_buffers(gpu_lib):
         assert np.array_equal(g1[k], g2[k]), k
 
 
+def test_caller_stream_gives_the_same_fields(gpu_lib):
+    """Running a context on a caller-provided stream (ys_set_stream, e.g. a
+    torch stream) changes where the work is queued, not what it computes:
+    the fields after three steps are equal bit for bit, and the context's own
+    stream can be taken back."""
+    import torch
+    ys = gpu_lib
+    _, s1, _, _ = make_pair(ys, with_oracle=False)
+    _, s2, _, _ = make_pair(ys, with_oracle=False)
+    stream = torch.cuda.Stream()
+    s2.set_stream(stream.cuda_stream)
+    s1.step(3, 2)
+    s2.step(3, 2)
+    g1, g2 = s1.get_fields(0), s2.get_fields(0)
+    s2.set_stream(0)
+    s2.step(1, 2)
+    s1.step(1, 2)
+    h1, h2 = s1.get_fields(0), s2.get_fields(0)
+    for k in ("T", "ur", "uth", "uph", "p"):
+        assert np.array_equal(g1[k], g2[k]), k
+        assert np.array_equal(h1[k], h2[k]), k
+
+
 def test_pinned_and_pageable_host_buffers_agree(gpu_lib):
     """set/get through page-locked host buffers (read and written by the
     (un)pack kernels over the CPU-GPU link) and through pageable ones (staged
