@@ -1,5 +1,7 @@
-"""The C-ABI library loads and exports every function include/ys.h declares;
-argument validation works without a GPU (no compute calls here)."""
+"""The C-ABI library loads and exports every function include/ys.h declares (a
+plain C program can include the header and link it); argument validation, the
+host-only entries and the serving queue's admission checks work without a GPU
+(no compute calls here)."""
 import ctypes
 import os
 import re
@@ -166,3 +168,53 @@ def test_server_binding_checks_the_packed_field_length():
             assert e.value.code == ys.YS_EINVAL
         finally:
             srv.close()
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "ys.h"
+
+int main(void) {
+  ys_params p;
+  size_t n = 0, bytes;
+  ys_default_params(&p);
+  p.R1 = 0.5; p.R2 = 1.0; p.Pr = 1.0; p.Ra = 1e3; p.dt = 1e-3;
+  p.Nr = 8; p.Nth = 12; p.Nph = 36;
+  bytes = ys_shell_device_bytes(&p);
+  if (bytes == 0) return 2;
+  if (ys_exchange_table(&p, 4, NULL, 0, &n) != YS_OK || n == 0 || n % 12 != 0) return 3;
+  p.dt = 0.0;
+  if (ys_shell_device_bytes(&p) != 0) return 4;
+  if (strlen(ys_strerror(YS_EINVAL)) == 0) return 5;
+  printf("%zu %zu\n", bytes, n / 12);
+  return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_the_library_links_from_c(tmp_path):
+    """A C99 program includes include/ys.h, links libys.so and calls host-only
+    entries through the C ABI (no Python, no GPU): the header is plain C and
+    the exported names are unmangled."""
+    import shutil
+    import subprocess
+    from paper_1905_02300_gb300 import build
+    from paper_1905_02300_gb300 import ys
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib = build.build()
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(lib)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), lib,
+                        "-Wl,-rpath," + libdir, "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    bytes_, npts = map(int, r.stdout.split())
+    p = ys.default_params(R1=0.5, R2=1.0, Pr=1.0, Ra=1e3, dt=1e-3, Nr=8, Nth=12, Nph=36)
+    assert bytes_ == ys.lib.ys_shell_device_bytes(ctypes.byref(p))
+    assert npts == 2 * 36 + 2 * 12 - 4     # the pressure ring of a 12 x 36 patch
