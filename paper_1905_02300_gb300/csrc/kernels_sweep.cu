@@ -339,6 +339,35 @@ __global__ void k_static_pack(Layout L, int loc, const double *src, double *dst)
   }
 }
 
+// The 14 metric tables of a uniform radial grid (r and 1/r at centres and
+// faces, sin, cos and 1/sin at theta centres and faces, the radial cell
+// width and its reciprocal, the norm factors r), each kStaticMetricLen long
+// with `pad` entries before index 0, formed on the device so that a call
+// queues no host-to-device copy.
+__global__ void k_static_metric(double *met, double R1, double hr, double th0, double ht, int pad) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < kStaticMetricLen; t += gridDim.x * blockDim.x) {
+    const int i = t - pad;
+    const double rc = R1 + (i + 0.5) * hr, rf = R1 + i * hr;
+    const double sc = sin(th0 + (i + 0.5) * ht), sf = sin(th0 + i * ht);
+    const double v[kMetricTables] = {rc,
+                                     rf,
+                                     sc,
+                                     sf,
+                                     cos(th0 + (i + 0.5) * ht),
+                                     cos(th0 + i * ht),
+                                     rc != 0.0 ? 1.0 / rc : 0.0,
+                                     rf != 0.0 ? 1.0 / rf : 0.0,
+                                     sc != 0.0 ? 1.0 / sc : 0.0,
+                                     sf != 0.0 ? 1.0 / sf : 0.0,
+                                     hr,
+                                     1.0 / hr,
+                                     rc,
+                                     rf};
+#pragma unroll
+    for (int k = 0; k < kMetricTables; ++k) met[k * kStaticMetricLen + t] = v[k];
+  }
+}
+
 }  // namespace
 
 }  // namespace ys
@@ -383,32 +412,17 @@ extern "C" int ys_factor_solve_static(const ys_params *prm, int loc, const doubl
   double *Cs = base + 4 * kStaticFieldElems;
   double *met = base + 5 * kStaticFieldElems;
 
-  // metric tables r_c, r_f, sin/cos at theta centres and faces (pad 2), on the stack
+  // Every call shares the scratch.  The padded copies of the advecting
+  // velocity and of the right-hand side are cleared over this grid's extent
+  // (the unpacks write the unknowns only; the rest of the box must read 0,
+  // not the last call's values); c' is written before it is read.  The
+  // metric tables are formed on the device: the call queues memsets and
+  // kernels only, no copy from host memory.
   const int pad = 2;
-  double mh[kMetricTables * kStaticMetricLen];
-  for (int t = 0; t < kStaticMetricLen; ++t) {
-    int i = t - pad;
-    double rc = prm->R1 + (i + 0.5) * hr, rf = prm->R1 + i * hr;
-    double sc = std::sin(th0 + (i + 0.5) * ht), sf = std::sin(th0 + i * ht);
-    mh[0 * kStaticMetricLen + t] = rc;
-    mh[1 * kStaticMetricLen + t] = rf;
-    mh[2 * kStaticMetricLen + t] = sc;
-    mh[3 * kStaticMetricLen + t] = sf;
-    mh[4 * kStaticMetricLen + t] = std::cos(th0 + (i + 0.5) * ht);
-    mh[5 * kStaticMetricLen + t] = std::cos(th0 + i * ht);
-    mh[6 * kStaticMetricLen + t] = rc != 0.0 ? 1.0 / rc : 0.0;
-    mh[7 * kStaticMetricLen + t] = rf != 0.0 ? 1.0 / rf : 0.0;
-    mh[8 * kStaticMetricLen + t] = sc != 0.0 ? 1.0 / sc : 0.0;
-    mh[9 * kStaticMetricLen + t] = sf != 0.0 ? 1.0 / sf : 0.0;
-    // uniform radial grid: cell width h_r, norm factors r
-    mh[10 * kStaticMetricLen + t] = hr;
-    mh[11 * kStaticMetricLen + t] = 1.0 / hr;
-    mh[12 * kStaticMetricLen + t] = rc;
-    mh[13 * kStaticMetricLen + t] = rf;
-  }
-  // every call shares the scratch: clear the working fields left by the last call
-  if (cudaMemsetAsync(base, 0, 4 * kStaticFieldElems * sizeof(double), st) != cudaSuccess) return YS_ECUDA;
-  if (cudaMemcpyAsync(met, mh, sizeof(mh), cudaMemcpyHostToDevice, st) != cudaSuccess) return YS_ECUDA;
+  for (int f = 0; f < 4; ++f)
+    if (cudaMemsetAsync(base + f * kStaticFieldElems, 0, L.total * sizeof(double), st) != cudaSuccess)
+      return YS_ECUDA;
+  k_static_metric<<<2, 256, 0, st>>>(met, prm->R1, hr, th0, ht, pad);
   const double *Ain[3] = {A_r, A_th, A_ph};
   for (int a = 0; a < 3; ++a) k_static_unpack<<<256, 256, 0, st>>>(L, LR + a, Ain[a], Af[a]);
   k_static_unpack<<<256, 256, 0, st>>>(L, loc, rhs, B);
@@ -458,5 +472,7 @@ extern "C" int ys_factor_solve_static(const ys_params *prm, int loc, const doubl
   for (int s = 0; s < 3; ++s)
     Launch<double>::sweep(S, loc, order[loc][s], false, ax, B, Cs, nullptr, nullptr, 0, 3, st);
   k_static_pack<<<256, 256, 0, st>>>(L, loc, B, x);
+  // a launch error of this call, or an error that earlier work left pending
+  // in the caller's CUDA context, is returned as YS_ECUDA (and cleared)
   return cudaGetLastError() == cudaSuccess ? YS_OK : YS_ECUDA;
 }
