@@ -51,10 +51,12 @@ extern "C" {
 #define YS_EINVAL 1     /* invalid argument or grid too coarse for the exchange */
 #define YS_ENOMEM 2     /* device or host allocation failed */
 #define YS_ECUDA 3      /* CUDA error (no device, launch failure, ...) */
-#define YS_EDIVERGED 4  /* NaN/Inf increment norms: the state holds the diverged values */
-#define YS_ETIMEOUT 5   /* a bounded device wait gave up */
+#define YS_EDIVERGED 4  /* NaN/Inf increment norms, or Schwarz increments that grew more than
+                           10^3-fold in one iteration: the state holds the diverged values */
+#define YS_ETIMEOUT 5   /* a served request passed its deadline */
 #define YS_EAGAIN 6     /* result not ready yet */
 #define YS_EBUSY 7      /* admission refused: queue full */
+#define YS_ECANCELED 8  /* a served request was cancelled */
 
 /* precision */
 #define YS_FP64 0       /* every field and operation in FP64 */
@@ -174,9 +176,14 @@ int ys_set_time(ys_ctx *c, double t);
  * The work is queued on the context's stream; the call returns once the last
  * step's increment norms have been read back (with schwarz_tol > 0 it also
  * waits for the norms after every iteration).  Returns YS_EDIVERGED if one
- * of those norms is NaN or Inf (a divergence in an earlier step propagates to
- * it); the state then holds the diverged values and the caller restarts
- * from its own copy (ys_get_fields / ys_set_fields restart exactly). */
+ * of those norms is NaN or Inf, or if in any iteration of this call an
+ * increment norm was not finite or, from the third iteration of a step on,
+ * the largest one exceeded 10^3 times the previous iteration's (a
+ * device-side watch after every iteration: a working defect correction
+ * contracts from its second iteration on, so growth by three orders of
+ * magnitude in one iteration means it diverges); the state then holds the
+ * diverged values and the caller restarts from its own copy (ys_get_fields /
+ * ys_set_fields restart exactly). */
 int ys_step(ys_ctx *c, int n_steps, int n_schwarz);
 
 /* Copy time level `level` to host buffers (u2 and p2, the second-order
@@ -213,6 +220,12 @@ int ys_set_fields_dev(ys_ctx *c, int level, const double *T, const double *ur, c
 int ys_profile_enable(ys_ctx *c, int on);
 int ys_profile_read(ys_ctx *c, const char **names, double *ms, long *launches, int cap);
 long ys_launch_count(ys_ctx *c);
+/* Diagnostic: the dense FP64 rate of the current device in TFLOP/s (2 flops
+ * per FMA), measured by a kernel of independent FMA chains on every SM, timed
+ * with CUDA events (synchronous; allocates 8 bytes).  The roofline
+ * denominator of the FP64 form's kernels, which are bound by the FP64 pipe.
+ * Errors: YS_EINVAL, YS_ENOMEM, YS_ECUDA. */
+int ys_measure_fp64_rate(double *tflops);
 
 /* Bytes of device memory held by the context. */
 size_t ys_device_bytes(ys_ctx *c);
@@ -227,10 +240,11 @@ size_t ys_shell_device_bytes(const ys_params *p);
  * inside a host-side memory budget enforced by another allocator, callbacks
  * that must not trigger the driver's allocator or its implicit
  * synchronisation, and embedders that forbid device allocations after start-up.
- * This entry point allocates nothing: it applies x = P^-1 rhs, the product of
- * the three 1-D factors (I - dt/2 Ahat_d) of one unknown in its stated order
- * (the correction solve of Eq. er: T r, theta, phi; u_r theta, phi, r;
- * u_theta phi, r, theta; u_phi r, theta, phi), for one shell described by
+ * This entry point allocates nothing: it applies x = P^-1 rhs, where P is the
+ * product of the three 1-D line operators (I - dt/2 Ahat_d) of one unknown,
+ * solved one direction after the other in this order: T along r, theta,
+ * phi; u_r along theta, phi, r; u_theta along phi, r, theta; u_phi along r,
+ * theta, phi.  It is meant for one shell described by
  * *prm (R1, R2, Pr as viscosity, dt, chi, overlap, Nr, Nth, Nph, and the
  * temperature wall conditions Tbc_* whose ghosts set the T factor's wall rows;
  * other fields ignored).  loc selects the unknown: 0 = T, 1 = u_r, 2 = u_theta, 3 = u_phi.
@@ -246,11 +260,15 @@ size_t ys_shell_device_bytes(const ys_params *p);
  * not); larger grids, bad sizes or NULL pointers return YS_EINVAL before any
  * work is queued.  The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current, so make the first
- * call on a device before any stream capture.  Every call shares the one
- * array and overwrites the previous call's contents (the working fields are
- * cleared at the start of each call): calls that overlap on the GPU (other
- * streams, other host threads) race and must be serialised by the caller.
- * Errors: YS_EINVAL, YS_ECUDA. */
+ * call on a device before any stream capture.  A call queues only memsets and
+ * kernels on `stream` (the metric tables are formed on the device) and does
+ * not wait for them.  Every call shares the one array and overwrites the
+ * previous call's contents (the working fields are cleared at the start of
+ * each call): calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.
+ * Errors: YS_EINVAL; YS_ECUDA for a failed launch of this call, and also when
+ * earlier work left an error pending in the calling thread's CUDA context
+ * (the pending error is cleared). */
 int ys_factor_solve_static(const ys_params *prm, int loc, const double *A_r, const double *A_th,
                            const double *A_ph, const double *rhs, double *x, void *stream);
 
@@ -333,7 +351,11 @@ int ys_batch_remove(ys_batch *b, int slot, ys_ctx **c);
 /* Advance every member n_steps steps (asynchronous on the batch's stream). */
 int ys_batch_step(ys_batch *b, int n_steps);
 int ys_batch_sync(ys_batch *b);
-/* l2 increment norms (YS_NFIELDS) of the member's last iteration. */
+/* l2 increment norms (YS_NFIELDS) of the member's last iteration.  Returns
+ * YS_EDIVERGED (norms still written) when one is not finite, or when, in a
+ * step since the member joined the batch, its largest increment norm grew
+ * more than 10^3-fold from one iteration to the next after the second (the
+ * same watch as ys_step). */
 int ys_batch_norms(ys_batch *b, int slot, double *norms);
 /* Threads per block of the line-solve launches (lines per block): 32, 64,
  * 128 (default) or 256. */
@@ -343,6 +365,15 @@ int ys_batch_set_line_threads(ys_batch *b, int threads);
 int ys_batch_autotune(ys_batch *b, int trial_steps, int *chosen);
 /* kernel launches in one batched step (independent of the member count) */
 long ys_batch_launches_per_step(ys_batch *b);
+/* Kernel-class timing of batched steps: with profiling on, ys_batch_step
+ * launches each step's kernels directly on the batch's stream (the same
+ * kernels, arguments and order as the captured graph) with a CUDA event
+ * pair around every launch; ys_batch_profile_read fills up to `cap` names /
+ * total milliseconds / launch counts and returns the number of classes
+ * (synchronous; a negative error code on failure).  Enabling or disabling
+ * clears the tallies. */
+int ys_batch_profile_enable(ys_batch *b, int on);
+int ys_batch_profile_read(ys_batch *b, const char **names, double *ms, long *launches, int cap);
 /* the cudaStream_t the batch runs on (for event timing by the caller) */
 void *ys_batch_stream(ys_batch *b);
 int ys_batch_destroy(ys_batch *b);
@@ -365,6 +396,20 @@ int ys_server_create(size_t hbm_budget_bytes, int max_slots, ys_server **out);
  * budget or the parameters are outside these limits. */
 int ys_submit(ys_server *s, const ys_params *p, const double *init_fields, int n_steps, int n_schwarz,
               uint64_t *ticket);
+/* ys_submit with a deadline: a request not done deadline_s seconds after its
+ * submission fails with YS_ETIMEOUT (checked at every batched step boundary,
+ * while it waits in the queue and while it runs; its batch mates are not
+ * affected).  deadline_s = 0: no deadline; < 0 or NaN: YS_EINVAL. */
+int ys_submit_ex(ys_server *s, const ys_params *p, const double *init_fields, int n_steps, int n_schwarz,
+                 double deadline_s, uint64_t *ticket);
+/* Cancel a request: a queued one fails with YS_ECANCELED at once, a running
+ * one at the next batched step boundary (its device state is released there;
+ * its batch mates are not affected).  YS_EINVAL for an unknown ticket or one
+ * that has already finished. */
+int ys_cancel(ys_server *s, uint64_t ticket);
+/* Most requests the queue holds while they wait for admission (1..4096,
+ * default 4096); ys_submit beyond it returns YS_EBUSY. */
+int ys_server_set_queue_limit(ys_server *s, int max_queued);
 /* State of a request: *state = 0 queued, 1 running, 2 done, 3 failed.  Returns
  * YS_EAGAIN until it is done; when done, copies level 0 packed like the input
  * to out_fields (if not NULL) and the time from submission to completion to

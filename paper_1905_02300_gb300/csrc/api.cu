@@ -29,7 +29,7 @@ namespace {
 
 const char *kClassNames[K_NUM] = {"extrapolate", "forcing",  "exchange", "walls",   "ring",     "resid_T",
                                   "resid_u",     "sweep_r",  "sweep_t",  "sweep_p", "pressure", "pack",
-                                  "factorize"};
+                                  "factorize",   "watch"};
 
 }  // namespace
 
@@ -74,6 +74,26 @@ void prof_end(ys_ctx *c, int nk) {
     expr;                          \
     prof_end(ctx, nk);             \
   } while (0)
+
+// FP64 rate probe (ys_measure_fp64_rate): kRateChains independent FMA
+// chains per thread, so that each warp always has a ready FP64 instruction;
+// the conditional store keeps the chains live.
+constexpr int kRateChains = 8, kRateThreads = 256, kRateBlocksPerSM = 8;
+__global__ void __launch_bounds__(kRateThreads) k_fp64_rate(double *sink, double seed, int iters) {
+  double a[kRateChains];
+#pragma unroll
+  for (int c = 0; c < kRateChains; ++c) a[c] = seed + 1e-3 * (threadIdx.x + c);
+  const double b = 0.999999999, d = 1e-9;
+#pragma unroll 4
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < kRateChains; ++c) a[c] = fma(a[c], b, d);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < kRateChains; ++c) s += a[c];
+  if (s == -1.0) *sink = s;
+}
 
 int validate(const ys_params *p) {
   if (!p) return YS_EINVAL;
@@ -261,6 +281,8 @@ template <typename R>
 int step_t(ys_ctx *c, int n_steps, int n_schwarz) {
   const ys_params &prm = c->prm;
   Fields<R> &D = F<R>(c);
+  // the divergence watch reports on this call's iterations only
+  cudaMemsetAsync(c->norm + kWatchFlag, 0, sizeof(double), c->stream);
   for (int st = 0; st < n_steps; ++st) {
     State<R> n = D.lev[0], nm1 = D.lev[1], it = D.lev[2];
     LAUNCH(c, K_EXTRAP, 1, Launch<R>::extrapolate(c->L, it, n, nm1, D.A, c->stream));
@@ -302,6 +324,7 @@ int step_t(ys_ctx *c, int n_steps, int n_schwarz) {
         }
       }
       c->iters_last = k;
+      LAUNCH(c, K_WATCH, 1, norm_watch(c->norm, k, c->stream));
       if (prm.schwarz_tol > 0.0) {
         double h[YS_NFIELDS];
         if (cudaMemcpyAsync(h, c->norm, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -322,11 +345,11 @@ int step_t(ys_ctx *c, int n_steps, int n_schwarz) {
   }
   if (cudaGetLastError() != cudaSuccess) return YS_ECUDA;
   if (n_steps > 0) {
-    double h[YS_NFIELDS];
+    double h[kWatchFlag + 1];
     if (cudaMemcpyAsync(h, c->norm, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)
       return YS_ECUDA;
-    bool bad = false;
+    bool bad = h[kWatchFlag] != 0.0;
     for (int f = 0; f < YS_NFIELDS; ++f) {
       c->norms_host[f] = std::sqrt(h[f]);
       if (!std::isfinite(c->norms_host[f])) bad = true;
@@ -530,10 +553,11 @@ const char *ys_strerror(int code) {
     case YS_EINVAL: return "invalid argument";
     case YS_ENOMEM: return "out of memory";
     case YS_ECUDA: return "CUDA error";
-    case YS_EDIVERGED: return "diverged (NaN/Inf)";
-    case YS_ETIMEOUT: return "timeout";
+    case YS_EDIVERGED: return "diverged (NaN/Inf or Schwarz blow-up)";
+    case YS_ETIMEOUT: return "deadline passed";
     case YS_EAGAIN: return "not ready";
     case YS_EBUSY: return "busy";
+    case YS_ECANCELED: return "cancelled";
   }
   return "unknown error";
 }
@@ -1053,6 +1077,38 @@ int ys_profile_read(ys_ctx *c, const char **names, double *ms, long *launches, i
 }
 
 long ys_launch_count(ys_ctx *c) { return c ? c->launches : -1; }
+
+int ys_measure_fp64_rate(double *tflops) {
+  if (!tflops) return YS_EINVAL;
+  *tflops = 0.0;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess)
+    return YS_ECUDA;
+  double *sink = nullptr;
+  if (cudaMalloc(&sink, sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return YS_ENOMEM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = sms * kRateBlocksPerSM, iters = 8192;
+  float ms = 0.f;
+  k_fp64_rate<<<blocks, kRateThreads>>>(sink, 1.0, iters / 8);   // warm-up
+  cudaEventRecord(e0);
+  k_fp64_rate<<<blocks, kRateThreads>>>(sink, 1.0, iters);
+  cudaEventRecord(e1);
+  const bool ok = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+                  cudaGetLastError() == cudaSuccess;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (!ok || !(ms > 0.f)) return YS_ECUDA;
+  const double flops = 2.0 * kRateChains * (double)iters * blocks * kRateThreads;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  return YS_OK;
+}
 
 size_t ys_device_bytes(ys_ctx *c) { return c ? c->dbytes : 0; }
 

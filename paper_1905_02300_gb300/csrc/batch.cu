@@ -307,6 +307,27 @@ void grid_of(const ys_ctx *c, int map, int tpb_line, int &gx, int &gy) {
 
 }  // namespace
 
+// Divergence watch of every member after Schwarz iteration k (1-based) of a
+// step (the single-shell norm_watch per slot): watch[2 s] holds the largest
+// squared increment norm of the member's previous iteration, watch[2 s + 1]
+// its sticky flag, set by a non-finite norm or, for k >= 3, by a norm above
+// kWatchGrowth times the previous iteration's.  Empty slots have zero norms
+// and never set it.
+__global__ void kb_norm_watch(const double *norms, double *watch, int cap, int k) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= cap) return;
+  double cur = 0.0;
+  bool bad = false;
+  for (int f = 0; f < YS_NFIELDS; ++f) {
+    const double v = norms[(size_t)s * YS_NFIELDS + f];
+    if (!(v <= 1.79e308)) bad = true;
+    else cur = fmax(cur, v);
+  }
+  if (k >= 3 && cur > kWatchGrowth * kWatchGrowth * watch[2 * s]) bad = true;
+  if (bad) watch[2 * s + 1] = 1.0;
+  watch[2 * s] = cur;
+}
+
 }  // namespace ys
 
 // ---------------------------------------------------------------------------
@@ -323,12 +344,22 @@ struct ys_batch {
   int *maps = nullptr;            // M_NUM x (2 cap + 1) ints (device)
   int *active = nullptr;          // cap ints (device)
   double *norms = nullptr;        // cap x YS_NFIELDS (device)
+  double *watch = nullptr;        // cap x 2: divergence watch per member (device; kb_norm_watch)
   double *parts = nullptr;        // per-block pressure norm shares (device), parts_n doubles
   long parts_n = 0;
   std::vector<int> hmaps;
   cudaGraphExec_t exec = nullptr;
   bool dirty = true;              // maps / descriptors need upload
   long launches = 0;
+  // kernel-class timing (ys_batch_profile_*): profiled steps are launched
+  // eagerly with an event pair around each launch instead of replaying the graph
+  struct Prof {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<Prof> prof;
+  size_t prof_used = 0;
 };
 
 namespace {
@@ -426,6 +457,35 @@ int upload(ys_batch *b) {
 
 const int kOrderB[4][3] = {{DR, DT, DP}, {DT, DP, DR}, {DP, DR, DT}, {DR, DT, DP}};
 
+// kernel classes of a batched step (timing names)
+enum BClass {
+  B_EXTRAP = 0, B_FACTOR, B_EXCH, B_WALLS, B_RING, B_RES_T, B_RES_U, B_SWEEP_R, B_SWEEP_T, B_SWEEP_P, B_PRES,
+  B_WATCH, B_ROTATE, B_NUM
+};
+const char *kBClassNames[B_NUM] = {"extrapolate", "factorize", "exchange", "walls",    "ring",  "resid_T", "resid_u",
+                                   "sweep_r",     "sweep_t",   "sweep_p",  "pressure", "watch", "rotate"};
+
+// event pair around one launch of a profiled (eager) step
+struct BMark {
+  ys_batch *b;
+  BMark(ys_batch *bb, int cls) : b(bb) {
+    if (!b->prof_on) return;
+    if (b->prof_used == b->prof.size()) {
+      ys_batch::Prof r{cls, nullptr, nullptr};
+      cudaEventCreate(&r.a);
+      cudaEventCreate(&r.b);
+      b->prof.push_back(r);
+    }
+    b->prof[b->prof_used].cls = cls;
+    cudaEventRecord(b->prof[b->prof_used].a, b->stream);
+  }
+  ~BMark() {
+    if (!b->prof_on) return;
+    cudaEventRecord(b->prof[b->prof_used].b, b->stream);
+    b->prof_used++;
+  }
+};
+
 // one AC step of every member shell (additive Schwarz, K iterations)
 template <typename R>
 void enqueue_step(ys_batch *b) {
@@ -446,10 +506,14 @@ void enqueue_step(ys_batch *b) {
   }
   const size_t spw_bytes = (size_t)bd::kScanWarps * spw * sizeof(R);
   const int gp = 152 * 4;
-  kb_extrapolate<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_EXTRAP), cap);
+  {
+    BMark m(b, B_EXTRAP);
+    kb_extrapolate<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_EXTRAP), cap);
+  }
   ++nl;
   for (int loc = LC; loc <= LP; ++loc)
     for (int dir = DR; dir <= DP; ++dir) {
+      BMark m(b, B_FACTOR);
       if (dir == DP && bd::use_phi_scan<R>())
         kb_factorize_phi<R><<<gp, 32 * bd::kScanWarps, 0, st>>>(sh, map_of(b, M_PSC0 + loc), cap, loc);
       else
@@ -459,6 +523,7 @@ void enqueue_step(ys_batch *b) {
   auto solve = [&](int loc, int slot) {
     for (int s = 0; s < 3; ++s) {
       int dir = kOrderB[loc][s];
+      BMark m(b, dir == DR ? B_SWEEP_R : dir == DT ? B_SWEEP_T : B_SWEEP_P);
       if (dir == DP)
         kb_solve_phi<R><<<gp, 32 * bd::kScanWarps, spw_bytes, st>>>(sh, map_of(b, M_PSC0 + loc), cap, loc, s == 2,
                                                                    slot, spw);
@@ -470,41 +535,67 @@ void enqueue_step(ys_batch *b) {
   };
   auto exchange = [&]() {
     for (int kind = XT; kind <= XUP; ++kind) {
+      BMark m(b, B_EXCH);
       kb_exchange<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_EX0 + kind), cap, kind);
       ++nl;
     }
-    kb_walls<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_WALLS), cap);
+    {
+      BMark m(b, B_WALLS);
+      kb_walls<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_WALLS), cap);
+    }
     ++nl;
   };
   for (int k = 0; k < b->K; ++k) {
     cudaMemsetAsync(b->norms, 0, sizeof(double) * YS_NFIELDS * cap, st);
     exchange();
-    if constexpr (sizeof(R) == sizeof(float))
-      kb_resid_T_vec<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_VEC0 + LC), cap);
-    else
-      kb_resid_T<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_RC), cap);
+    {
+      BMark m(b, B_RES_T);
+      if constexpr (sizeof(R) == sizeof(float))
+        kb_resid_T_vec<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_VEC0 + LC), cap);
+      else
+        kb_resid_T<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_RC), cap);
+    }
     ++nl;
     solve(LC, F_T);
     for (int sys = 1; sys <= 2; ++sys) {
       int o = (sys == 1) ? 0 : 4;
       for (int comp = 0; comp < 3; ++comp) {
-        if constexpr (sizeof(R) == sizeof(float))
-          kb_resid_u_vec<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_VEC0 + LR + comp), cap, sys, comp);
-        else
-          kb_resid_u<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_RR + comp), cap, sys, comp);
+        {
+          BMark m(b, B_RES_U);
+          if constexpr (sizeof(R) == sizeof(float))
+            kb_resid_u_vec<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_VEC0 + LR + comp), cap, sys, comp);
+          else
+            kb_resid_u<R><<<g128, 128, 0, st>>>(sh, map_of(b, M_RR + comp), cap, sys, comp);
+        }
         ++nl;
         solve(LR + comp, F_U1R + comp + o);
       }
-      kb_pressure<R><<<g128, kPresTpb, 0, st>>>(sh, map_of(b, M_RC), cap, sys, b->parts);
-      kb_norm_sum<R><<<cap, 256, 0, st>>>(sh, map_of(b, M_RC), cap, sys == 1 ? 4 : 8, b->parts);
+      {
+        BMark m(b, B_PRES);
+        kb_pressure<R><<<g128, kPresTpb, 0, st>>>(sh, map_of(b, M_RC), cap, sys, b->parts);
+        kb_norm_sum<R><<<cap, 256, 0, st>>>(sh, map_of(b, M_RC), cap, sys == 1 ? 4 : 8, b->parts);
+      }
       nl += 2;
     }
-    kb_exchange<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_RING), cap, XP);
-    ++nl;
+    {
+      BMark m(b, B_RING);
+      kb_exchange<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_RING), cap, XP);
+    }
+    {
+      BMark m(b, B_WATCH);
+      kb_norm_watch<<<(cap + 127) / 128, 128, 0, st>>>(b->norms, b->watch, cap, k + 1);
+    }
+    nl += 2;
   }
   exchange();
-  kb_exchange<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_RING), cap, XP);
-  kb_rotate<R><<<(cap + 127) / 128, 128, 0, st>>>((ShellDev<R> *)b->shells, b->active, cap);
+  {
+    BMark m(b, B_RING);
+    kb_exchange<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_RING), cap, XP);
+  }
+  {
+    BMark m(b, B_ROTATE);
+    kb_rotate<R><<<(cap + 127) / 128, 128, 0, st>>>((ShellDev<R> *)b->shells, b->active, cap);
+  }
   nl += 2;
   b->launches = nl;
 }
@@ -530,12 +621,17 @@ int batch_step(ys_batch *b, int n) {
     int rc = upload<R>(b);
     if (rc) return rc;
   }
-  if (!b->exec) {
-    int rc = capture<R>(b);
-    if (rc) return rc;
+  if (b->prof_on) {
+    // profiled steps: the same launches, eagerly, with events around each
+    for (int i = 0; i < n; ++i) enqueue_step<R>(b);
+  } else {
+    if (!b->exec) {
+      int rc = capture<R>(b);
+      if (rc) return rc;
+    }
+    for (int i = 0; i < n; ++i)
+      if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return YS_ECUDA;
   }
-  for (int i = 0; i < n; ++i)
-    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return YS_ECUDA;
   for (int s = 0; s < b->cap; ++s)
     if (b->slot[s]) {
       b->rot[s] = (b->rot[s] + 2 * n) % 3;
@@ -582,7 +678,9 @@ int ys_batch_create(int capacity, int precision, int n_schwarz, ys_batch **out) 
   if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&b->shells, shell_bytes) != cudaSuccess || cudaMalloc(&b->maps, map_bytes) != cudaSuccess ||
       cudaMalloc(&b->active, sizeof(int) * capacity) != cudaSuccess ||
-      cudaMalloc(&b->norms, sizeof(double) * YS_NFIELDS * capacity) != cudaSuccess) {
+      cudaMalloc(&b->norms, sizeof(double) * YS_NFIELDS * capacity) != cudaSuccess ||
+      cudaMalloc(&b->watch, sizeof(double) * 2 * capacity) != cudaSuccess ||
+      cudaMemsetAsync(b->watch, 0, sizeof(double) * 2 * capacity, b->stream) != cudaSuccess) {
     cudaGetLastError();
     ys_batch_destroy(b);
     return YS_ENOMEM;
@@ -603,6 +701,9 @@ int ys_batch_add(ys_batch *b, ys_ctx *c, int *slot) {
     }
   if (s < 0) return YS_EBUSY;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return YS_ECUDA;
+  // a new member starts with a clear divergence watch (ordered after the
+  // batch's queued steps, before its next one)
+  if (cudaMemsetAsync(b->watch + 2 * s, 0, 2 * sizeof(double), b->stream) != cudaSuccess) return YS_ECUDA;
   b->slot[s] = c;
   b->rot[s] = 0;
   b->steps[s] = 0;
@@ -638,13 +739,45 @@ int ys_batch_sync(ys_batch *b) {
 
 int ys_batch_norms(ys_batch *b, int s, double *norms) {
   if (!b || s < 0 || s >= b->cap || !b->slot[s] || !norms) return YS_EINVAL;
-  double h[YS_NFIELDS];
+  double h[YS_NFIELDS], w[2];
   if (cudaMemcpyAsync(h, b->norms + (size_t)s * YS_NFIELDS, sizeof(h), cudaMemcpyDeviceToHost, b->stream) !=
           cudaSuccess ||
+      cudaMemcpyAsync(w, b->watch + 2 * s, sizeof(w), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return YS_ECUDA;
-  for (int f = 0; f < YS_NFIELDS; ++f) norms[f] = std::sqrt(h[f]);
+  bool bad = w[1] != 0.0;
+  for (int f = 0; f < YS_NFIELDS; ++f) {
+    norms[f] = std::sqrt(h[f]);
+    if (!std::isfinite(norms[f])) bad = true;
+  }
+  return bad ? YS_EDIVERGED : YS_OK;
+}
+
+int ys_batch_profile_enable(ys_batch *b, int on) {
+  if (!b) return YS_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return YS_ECUDA;
+  b->prof_on = on != 0;
+  b->prof_used = 0;
   return YS_OK;
+}
+
+int ys_batch_profile_read(ys_batch *b, const char **names, double *ms, long *launches, int cap) {
+  if (!b) return -YS_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return -YS_ECUDA;
+  double tot[B_NUM] = {};
+  long cnt[B_NUM] = {};
+  for (size_t r = 0; r < b->prof_used; ++r) {
+    float m = 0.f;
+    cudaEventElapsedTime(&m, b->prof[r].a, b->prof[r].b);
+    tot[b->prof[r].cls] += m;
+    cnt[b->prof[r].cls] += 1;
+  }
+  for (int k = 0; k < B_NUM && k < cap; ++k) {
+    if (names) names[k] = kBClassNames[k];
+    if (ms) ms[k] = tot[k];
+    if (launches) launches[k] = cnt[k];
+  }
+  return B_NUM;
 }
 
 int ys_batch_set_line_threads(ys_batch *b, int tpb) {
@@ -708,10 +841,15 @@ int ys_batch_destroy(ys_batch *b) {
   if (!b) return YS_EINVAL;
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto &r : b->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
   cudaFree(b->shells);
   cudaFree(b->maps);
   cudaFree(b->active);
   cudaFree(b->norms);
+  cudaFree(b->watch);
   cudaFree(b->parts);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -737,7 +875,13 @@ struct Request {
   long done_steps = 0;
   ys_ctx *ctx = nullptr;
   size_t bytes = 0;
+  double deadline_s = 0.0;      // 0: none
+  bool cancel = false;          // set under the server mutex by ys_cancel
   std::chrono::steady_clock::time_point t_submit, t_done;
+
+  bool expired(std::chrono::steady_clock::time_point now) const {
+    return deadline_s > 0.0 && std::chrono::duration<double>(now - t_submit).count() > deadline_s;
+  }
 };
 
 size_t packed_len(const ys_params &p) {
@@ -768,6 +912,7 @@ struct ys_server {
   std::vector<Request *> running;
   uint64_t next_ticket = 1;
   bool stop = false;
+  size_t max_queue = 4096;
   int dev = 0;
   std::thread worker;
   long steps_run = 0;
@@ -787,6 +932,20 @@ void server_loop(ys_server *S) {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv.wait(lk, [&] { return S->stop || !S->queue.empty() || !S->running.empty(); });
       if (S->stop) return;
+      // queued requests past their deadline fail without running
+      const auto now = std::chrono::steady_clock::now();
+      for (auto it = S->queue.begin(); it != S->queue.end();) {
+        if ((*it)->expired(now)) {
+          (*it)->state = 3;
+          (*it)->error = YS_ETIMEOUT;
+          (*it)->t_done = now;
+          (*it)->init.clear();
+          (*it)->init.shrink_to_fit();
+          it = S->queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
       // admission by free slots and device-memory budget, first come first served
       while (!S->queue.empty() && (int)(S->running.size() + admit.size()) < S->max_slots) {
         Request *r = S->queue.front();
@@ -824,20 +983,38 @@ void server_loop(ys_server *S) {
     if (run.empty()) continue;
     int rc = ys_batch_step(S->batch, 1);
     if (!rc) rc = ys_batch_sync(S->batch);
+    // requests cancelled, or past their deadline, leave at this step boundary
+    std::vector<int> stop_code(run.size(), 0);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      const auto now = std::chrono::steady_clock::now();
+      for (size_t i = 0; i < run.size(); ++i)
+        stop_code[i] = run[i]->cancel ? YS_ECANCELED : run[i]->expired(now) ? YS_ETIMEOUT : 0;
+    }
     double step_cells = 0.0;   // counters are published under the lock below (ys_server_stats reads them)
     std::vector<Request *> finished;
-    for (Request *r : run) {
+    for (size_t i = 0; i < run.size(); ++i) {
+      Request *r = run[i];
       r->done_steps++;
       step_cells += 2.0 * r->prm.Nr * r->prm.Nth * r->prm.Nph;
+      if (stop_code[i]) {
+        ys_ctx *c = nullptr;
+        ys_batch_remove(S->batch, r->slot, &c);
+        ys_destroy(c);
+        r->ctx = nullptr;
+        r->error = stop_code[i];
+        finished.push_back(r);
+        continue;
+      }
       double nrm[YS_NFIELDS];
       bool bad = rc != 0;
-      if (!bad && ys_batch_norms(S->batch, r->slot, nrm) == YS_OK)
-        for (int k = 0; k < YS_NFIELDS; ++k)
-          if (!std::isfinite(nrm[k])) bad = true;
+      // non-finite norms or a tripped divergence watch fail this request alone
+      const int nrc = bad ? YS_OK : ys_batch_norms(S->batch, r->slot, nrm);
+      if (nrc != YS_OK) bad = true;
       if (bad || r->done_steps >= r->n_steps) {
         ys_ctx *c = nullptr;
         ys_batch_remove(S->batch, r->slot, &c);
-        int err = bad ? (rc ? rc : YS_EDIVERGED) : 0;
+        int err = bad ? (rc ? rc : nrc) : 0;
         if (!bad) {
           r->result.resize(packed_len(r->prm));
           const double *f[5];
@@ -895,7 +1072,13 @@ int ys_server_create(size_t hbm_budget_bytes, int max_slots, ys_server **out) {
 
 int ys_submit(ys_server *S, const ys_params *p, const double *init_fields, int n_steps, int n_schwarz,
               uint64_t *ticket) {
+  return ys_submit_ex(S, p, init_fields, n_steps, n_schwarz, 0.0, ticket);
+}
+
+int ys_submit_ex(ys_server *S, const ys_params *p, const double *init_fields, int n_steps, int n_schwarz,
+                 double deadline_s, uint64_t *ticket) {
   if (!S || !p || !init_fields || n_steps < 1 || n_schwarz < 1 || !ticket) return YS_EINVAL;
+  if (!(deadline_s >= 0.0)) return YS_EINVAL;
   if (p->schwarz_mode != YS_ADDITIVE || p->schwarz_tol != 0.0) return YS_EINVAL;
   if (p->r_half) return YS_EINVAL;   // queued requests keep no copy of the radii: uniform grids only
   const size_t bytes = footprint(*p);
@@ -910,13 +1093,14 @@ int ys_submit(ys_server *S, const ys_params *p, const double *init_fields, int n
     S->worker = std::thread(server_loop, S);
   }
   if (n_schwarz != S->K || p->precision != S->precision) return YS_EINVAL;
-  if (S->queue.size() >= kMaxQueue) return YS_EBUSY;
+  if (S->queue.size() >= S->max_queue) return YS_EBUSY;
   Request *r = new (std::nothrow) Request();
   if (!r) return YS_ENOMEM;
   r->prm = *p;
   r->init.assign(init_fields, init_fields + packed_len(*p));
   r->n_steps = n_steps;
   r->bytes = bytes;
+  r->deadline_s = deadline_s;
   r->ticket = S->next_ticket++;
   r->t_submit = std::chrono::steady_clock::now();
   S->queue.push_back(r);
@@ -938,6 +1122,37 @@ int ys_poll(ys_server *S, uint64_t ticket, int *state, double *out_fields, doubl
   if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
   if (r->state == 3) return r->error ? r->error : YS_ECUDA;
   if (out_fields) std::memcpy(out_fields, r->result.data(), r->result.size() * sizeof(double));
+  return YS_OK;
+}
+
+int ys_cancel(ys_server *S, uint64_t ticket) {
+  if (!S) return YS_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) return YS_EINVAL;
+  Request *r = it->second;
+  if (r->state >= 2) return YS_EINVAL;
+  if (r->state == 0) {
+    for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
+      if (*q == r) {
+        S->queue.erase(q);
+        r->state = 3;
+        r->error = YS_ECANCELED;
+        r->t_done = std::chrono::steady_clock::now();
+        r->init.clear();
+        r->init.shrink_to_fit();
+        return YS_OK;
+      }
+  }
+  // admitted (or being admitted): the worker retires it at the next step boundary
+  r->cancel = true;
+  return YS_OK;
+}
+
+int ys_server_set_queue_limit(ys_server *S, int max_queued) {
+  if (!S || max_queued < 1 || max_queued > (int)kMaxQueue) return YS_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->max_queue = (size_t)max_queued;
   return YS_OK;
 }
 

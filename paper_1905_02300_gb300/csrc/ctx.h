@@ -14,7 +14,7 @@ namespace ys {
 // kernel classes for timing
 enum KClass {
   K_EXTRAP = 0, K_FORCE, K_EXCH, K_WALLS, K_RING, K_RES_T, K_RES_U, K_SWEEP_R, K_SWEEP_T, K_SWEEP_P, K_PRES,
-  K_PACK, K_FACTOR, K_NUM
+  K_PACK, K_FACTOR, K_WATCH, K_NUM
 };
 
 struct ProfRec {

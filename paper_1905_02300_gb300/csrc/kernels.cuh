@@ -118,5 +118,10 @@ struct Launch {
 void unpack_p(const Layout &L, const double *src, double *dst, const double *bg, cudaStream_t st,
               double *dst2 = nullptr);
 void pack_p(const Layout &L, const double *src, double *dst, const double *bg, cudaStream_t st);
+// After Schwarz iteration k (1-based) of a step: set norm[kWatchFlag] when
+// the iteration's squared increment norms norm[0..NF) are not finite or, for
+// k >= 3, the largest exceeds kWatchGrowth^2 times norm[kWatchPrev], the
+// previous iteration's; then store it there.
+void norm_watch(double *norm, int k, cudaStream_t st);
 
 }  // namespace ys

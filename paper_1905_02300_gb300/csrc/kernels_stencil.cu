@@ -318,6 +318,28 @@ void pack_p(const Layout &L, const double *src, double *dst, const double *bg, c
   k_pack<double><<<flat_blocks(user_max(L)), 256, 0, st>>>(L, LC, src, dst, bg);
 }
 
+// One iteration's divergence test (one thread): norm[0..NF) hold the squared
+// increment norms of iteration k (1-based) of the step just finished
+// (non-negative sums); `prev` holds the largest of iteration k - 1, `flag`
+// the sticky flag.
+__global__ void k_norm_watch(const double *norm, double *prev, double *flag, int k) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double cur = 0.0;
+  bool bad = false;
+  for (int f = 0; f < NF; ++f) {
+    const double v = norm[f];
+    if (!(v <= 1.79e308)) bad = true;   // NaN or +Inf
+    else cur = fmax(cur, v);
+  }
+  if (k >= 3 && cur > kWatchGrowth * kWatchGrowth * *prev) bad = true;
+  if (bad) *flag = 1.0;
+  *prev = cur;
+}
+
+void norm_watch(double *norm, int k, cudaStream_t st) {
+  k_norm_watch<<<1, 32, 0, st>>>(norm, norm + kWatchPrev, norm + kWatchFlag, k);
+}
+
 #define YS_INST_STENCIL(R)                                                                                         \
   template void Launch<R>::extrapolate(const Layout &, State<R>, State<R>, State<R>, R *[3], cudaStream_t);       \
   template void Launch<R>::combine_forcing(long, Modes<R>, R *[4], cudaStream_t);                                  \

@@ -14,7 +14,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libys.so")
 
-YS_OK, YS_EINVAL, YS_ENOMEM, YS_ECUDA, YS_EDIVERGED, YS_ETIMEOUT, YS_EAGAIN, YS_EBUSY = range(8)
+YS_OK, YS_EINVAL, YS_ENOMEM, YS_ECUDA, YS_EDIVERGED, YS_ETIMEOUT, YS_EAGAIN, YS_EBUSY, YS_ECANCELED = range(9)
 YS_FP64, YS_MIXED = 0, 1
 YS_ADDITIVE, YS_MULTIPLICATIVE = 0, 1
 NFIELDS = 9
@@ -56,6 +56,7 @@ _sig = {
     "ys_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "ys_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_char_p), _dp, C.POINTER(C.c_long), C.c_int]),
     "ys_launch_count": (C.c_long, [C.c_void_p]),
+    "ys_measure_fp64_rate": (C.c_int, [_dp]),
     "ys_device_bytes": (C.c_size_t, [C.c_void_p]),
     "ys_shell_device_bytes": (C.c_size_t, [C.POINTER(Params)]),
     "ys_destroy": (C.c_int, [C.c_void_p]),
@@ -77,8 +78,14 @@ _sig = {
     "ys_batch_launches_per_step": (C.c_long, [C.c_void_p]),
     "ys_batch_destroy": (C.c_int, [C.c_void_p]),
     "ys_batch_stream": (C.c_void_p, [C.c_void_p]),
+    "ys_batch_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "ys_batch_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_char_p), _dp, C.POINTER(C.c_long), C.c_int]),
     "ys_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
     "ys_submit": (C.c_int, [C.c_void_p, C.POINTER(Params), _dp, C.c_int, C.c_int, C.POINTER(C.c_uint64)]),
+    "ys_submit_ex": (C.c_int, [C.c_void_p, C.POINTER(Params), _dp, C.c_int, C.c_int, C.c_double,
+                               C.POINTER(C.c_uint64)]),
+    "ys_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "ys_server_set_queue_limit": (C.c_int, [C.c_void_p, C.c_int]),
     "ys_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_int), _dp, _dp]),
     "ys_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_long), _dp, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_int)]),
@@ -88,6 +95,13 @@ for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
     _f.restype = _res
     _f.argtypes = _args
+
+
+def measure_fp64_rate():
+    """Dense FP64 FMA rate of the current device, TFLOP/s (ys_measure_fp64_rate)."""
+    v = C.c_double()
+    _check(lib.ys_measure_fp64_rate(C.byref(v)), "ys_measure_fp64_rate")
+    return v.value
 
 
 class YSError(RuntimeError):
@@ -296,6 +310,20 @@ class Batch:
     def stream_handle(self):
         return lib.ys_batch_stream(self.h)
 
+    def profile(self, on=True):
+        _check(lib.ys_batch_profile_enable(self.h, 1 if on else 0), "ys_batch_profile_enable")
+
+    def profile_read(self):
+        """{kernel class: (total ms, launches)} of the profiled steps."""
+        cap = 32
+        names = (C.c_char_p * cap)()
+        ms = np.zeros(cap)
+        cnt = (C.c_long * cap)()
+        n = lib.ys_batch_profile_read(self.h, names, _ptr(ms), cnt, cap)
+        if n < 0:
+            raise YSError(-n, "ys_batch_profile_read")
+        return {names[i].decode(): (float(ms[i]), int(cnt[i])) for i in range(n)}
+
     def close(self):
         if getattr(self, "h", None):
             for slot in list(self.members):
@@ -332,13 +360,18 @@ class Server:
 
     QUEUED, RUNNING, DONE, FAILED = 0, 1, 2, 3
 
-    def __init__(self, hbm_budget_bytes, max_slots):
+    def __init__(self, hbm_budget_bytes, max_slots, max_queue=None):
         h = C.c_void_p()
         _check(lib.ys_server_create(hbm_budget_bytes, max_slots, C.byref(h)), "ys_server_create")
         self.h = h
         self.shapes = {}
+        if max_queue is not None:
+            _check(lib.ys_server_set_queue_limit(self.h, max_queue), "ys_server_set_queue_limit")
 
-    def submit(self, fields, n_steps, n_schwarz=3, **params):
+    def cancel(self, ticket):
+        _check(lib.ys_cancel(self.h, C.c_uint64(ticket)), "ys_cancel")
+
+    def submit(self, fields, n_steps, n_schwarz=3, deadline_s=0.0, **params):
         p = default_params(**params)
         buf = pack_fields(fields)
         Nr, Nt, Np = p.Nr, p.Nth, p.Nph
@@ -346,7 +379,8 @@ class Server:
         if buf.size != need:
             raise YSError(YS_EINVAL, "ys_submit: fields of %d values, the shell needs %d" % (buf.size, need))
         t = C.c_uint64()
-        _check(lib.ys_submit(self.h, C.byref(p), _ptr(buf), n_steps, n_schwarz, C.byref(t)), "ys_submit")
+        _check(lib.ys_submit_ex(self.h, C.byref(p), _ptr(buf), n_steps, n_schwarz, deadline_s, C.byref(t)),
+               "ys_submit_ex")
         self.shapes[t.value] = (p.Nr, p.Nth, p.Nph)
         return t.value
 

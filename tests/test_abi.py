@@ -45,7 +45,9 @@ def test_argument_validation_without_gpu():
 
 def test_strerror_and_defaults():
     from paper_1905_02300_gb300 import ys
-    assert ys.lib.ys_strerror(ys.YS_EDIVERGED) == b"diverged (NaN/Inf)"
+    assert ys.lib.ys_strerror(ys.YS_EDIVERGED) == b"diverged (NaN/Inf or Schwarz blow-up)"
+    assert ys.lib.ys_strerror(ys.YS_ETIMEOUT) == b"deadline passed"
+    assert ys.lib.ys_strerror(ys.YS_ECANCELED) == b"cancelled"
     p = ys.default_params()
     assert p.chi == 1.0 and p.overlap == 2 and p.step7 == 1 and p.precision == ys.YS_FP64
 
@@ -146,6 +148,31 @@ def test_server_rejects_unfit_and_invalid_requests_at_submit():
         running, queued = ctypes.c_int(-1), ctypes.c_int(-1)
         assert ys.lib.ys_server_stats(h, None, None, ctypes.byref(running), ctypes.byref(queued), None) == ys.YS_OK
         assert running.value == 0 and queued.value == 0
+    finally:
+        assert ys.lib.ys_server_destroy(h) == ys.YS_OK
+
+
+def test_server_deadline_cancel_and_queue_limit_arguments_without_gpu():
+    """Host-side checks of the serving controls, before any device work: a
+    negative or NaN deadline is refused at submit, cancelling an unknown
+    ticket is refused, and the queue limit must lie in 1..4096 (YS_EINVAL)."""
+    import math
+    import numpy as np
+    from paper_1905_02300_gb300 import ys
+    kw = dict(R1=0.5, R2=1.0, Pr=1.0, Ra=1e3, dt=1e-3, Nr=16, Nth=16, Nph=48)
+    p = ys.default_params(**kw)
+    h = ctypes.c_void_p()
+    assert ys.lib.ys_server_create(1 << 30, 4, ctypes.byref(h)) == ys.YS_OK
+    try:
+        init = np.zeros(2 * 16 * 16 * 48 * 5 + 2 * (16 * 48 + 16 * 48 + 16 * 16))
+        ptr = init.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        t = ctypes.c_uint64()
+        for d in (-1.0, math.nan):
+            assert ys.lib.ys_submit_ex(h, ctypes.byref(p), ptr, 3, 2, d, ctypes.byref(t)) == ys.YS_EINVAL
+        assert ys.lib.ys_cancel(h, ctypes.c_uint64(12345)) == ys.YS_EINVAL
+        for q in (0, -3, 4097):
+            assert ys.lib.ys_server_set_queue_limit(h, q) == ys.YS_EINVAL
+        assert ys.lib.ys_server_set_queue_limit(h, 2) == ys.YS_OK
     finally:
         assert ys.lib.ys_server_destroy(h) == ys.YS_OK
 

@@ -210,3 +210,217 @@ def test_served_footprint_is_the_context_allocation(gpu_lib):
             p = ys.default_params(**kw)
             assert s.device_bytes() == ys.lib.ys_shell_device_bytes(ctypes.byref(p)), (sp, prec)
             s.close()
+
+
+# uneven FP64 shells held to the oracle: phi lines longer than one scan chunk
+# of 384, a stretched radial grid, a hot inner wall, a larger ragged shell
+ORACLE_SHELLS = [dict(R1=0.45, Nr=8, Nth=12, Nph=400, Pr=1.0, Ra=50.0),
+                 dict(R1=0.5, Nr=12, Nth=16, Nph=48, Pr=0.7, Ra=200.0, stretch=0.5),
+                 dict(R1=0.4, Nr=10, Nth=14, Nph=42, Pr=7.0, Ra=1e3, T_in=1.0),
+                 dict(R1=0.55, Nr=17, Nth=20, Nph=61, Pr=1.0, Ra=1e4)]
+DT_ORACLE = 1e-4
+
+
+def _oracle_case(sp, levels=2):
+    """(solver parameters, level fields, oracle after set-up): the curl
+    solution at t = 0 and t = -dt without forcing (batched shells take no
+    forcing modes), plus the conductive profile when the inner wall is hot."""
+    from oracle.scheme import Oracle, Params
+    rh = W.stretched_radii(sp["R1"], 1.0, sp["Nr"], sp["stretch"]) if "stretch" in sp else None
+    spec = W.Spec(sp["R1"], 1.0, sp["Nr"], sp["Nth"], sp["Nph"], r_half=rh)
+    ex = W.CurlShell(sp["R1"], 1.0, sp["Pr"], sp["Ra"])
+    T_in = sp.get("T_in", 0.0)
+    lv = [W.sample_fields(ex, spec, -m * DT_ORACLE) for m in range(levels)]
+    if T_in:
+        Tc = W.conductive_profile(spec, T_in, 0.0)
+        for f in lv:
+            f["T"] = f["T"] + Tc
+    kw = dict(R1=sp["R1"], R2=1.0, Pr=sp["Pr"], Ra=sp["Ra"], Nr=sp["Nr"], Nth=sp["Nth"], Nph=sp["Nph"],
+              dt=DT_ORACLE, T_inner=T_in, T_outer=0.0, r_half=rh)
+    o = Oracle(Params(R1=sp["R1"], R2=1.0, Pr=sp["Pr"], Ra=sp["Ra"], dt=DT_ORACLE, Nr=sp["Nr"], Nth=sp["Nth"],
+                      Nph=sp["Nph"], T_in=T_in, T_out=0.0, r_half=rh))
+    for m, f in enumerate(lv):
+        o.set_fields(m, f["T"], f["ur"], f["uth"], f["uph"], f["p"])
+    return kw, lv, o
+
+
+def _parity(got, ref):
+    return {k: float(np.abs(got[k] - ref[k]).max() / max(np.abs(ref[k]).max(), 1e-300)) for k in ref}
+
+
+def test_fp64_batch_of_uneven_shells_matches_the_oracle(gpu_lib):
+    """An FP64 batch of four uneven shells (one launch per kernel class over
+    all of them, the batched kernels of the ensemble path) against the
+    oracle, shell by shell, at the FP64 parity bound 1e-11 after 4 steps of 3
+    Schwarz iterations."""
+    ys = gpu_lib
+    b = ys.Batch(4, precision=ys.YS_FP64, n_schwarz=3)
+    cases, slots = [], []
+    for sp in ORACLE_SHELLS:
+        kw, lv, o = _oracle_case(sp)
+        s = ys.Solver(**kw, precision=ys.YS_FP64)
+        for m, f in enumerate(lv):
+            s.set_fields_dict(m, f)
+        slots.append(b.add(s))
+        o.step(4, 3)
+        cases.append(o)
+    b.step(4)
+    b.sync()
+    for sp, slot, o in zip(ORACLE_SHELLS, slots, cases):
+        s = b.remove(slot)
+        assert s.stats()["steps"] == 4
+        e = _parity(s.get_fields(0, aux=True), o.get_fields(0, aux=True))
+        assert max(e.values()) <= 1e-11, (sp, e)
+    b.close()
+
+
+def test_served_fp64_request_matches_the_oracle(gpu_lib):
+    """One request served in FP64 (continuous-batching server, fields packed
+    through ys_submit / ys_poll, one time level given) against the oracle."""
+    ys = gpu_lib
+    sp = ORACLE_SHELLS[2]
+    kw, lv, o = _oracle_case(sp, levels=1)
+    o.step(5, 3)
+    srv = ys.Server(hbm_budget_bytes=1 << 30, max_slots=2)
+    t = srv.submit(lv[0], 5, precision=ys.YS_FP64, **kw)
+    t0 = time.time()
+    while time.time() - t0 < 60:
+        st, f, lat, rc = srv.poll(t)
+        if st >= 2:
+            break
+        time.sleep(0.002)
+    srv.close()
+    assert st == ys.Server.DONE and rc == 0, (st, rc)
+    ref = o.get_fields(0)
+    e = _parity(f, ref)
+    assert max(e.values()) <= 1e-11, e
+
+
+def test_batch_member_that_blows_up_is_flagged_alone(gpu_lib):
+    """In an FP64 batch with 3 Schwarz iterations a member whose iteration
+    diverges (the blow-up state of the single-shell watch test) is reported by
+    ys_batch_norms as YS_EDIVERGED, while its batch mate reports OK and ends
+    bitwise where it ends alone."""
+    import ctypes
+    from tests.test_gpu_parity import blow_up_state
+    ys = gpu_lib
+    kw, lv0, lv1, aux = blow_up_state()
+
+    def good():
+        kwg, lv, _ = _oracle_case(ORACLE_SHELLS[2])
+        s = ys.Solver(**kwg, precision=ys.YS_FP64)
+        for m, f in enumerate(lv):
+            s.set_fields_dict(m, f)
+        return s
+
+    b1 = ys.Batch(1, precision=ys.YS_FP64, n_schwarz=3)
+    slot = b1.add(good())
+    b1.step(2)
+    b1.sync()
+    ref = fields(b1.remove(slot))
+    b1.close()
+
+    b = ys.Batch(2, precision=ys.YS_FP64, n_schwarz=3)
+    bad = ys.Solver(**kw)
+    bad.set_fields_dict(0, lv0, aux)
+    bad.set_fields_dict(1, lv1, aux)
+    sb = b.add(bad)
+    sg = b.add(good())
+    b.step(1)
+    b.sync()
+    nrm = np.empty(ys.NFIELDS)
+    ptr = nrm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert ys.lib.ys_batch_norms(b.h, sb, ptr) == ys.YS_EDIVERGED
+    assert np.isfinite(nrm).all(), nrm
+    assert ys.lib.ys_batch_norms(b.h, sg, ptr) == ys.YS_OK
+    b.remove(sb)
+    b.step(1)
+    b.sync()
+    assert same(fields(b.remove(sg)), ref)
+    b.close()
+
+
+def _wait(srv, t, states, limit=60.0):
+    t0 = time.time()
+    while time.time() - t0 < limit:
+        r = srv.poll(t)
+        if r[0] in states:
+            return r
+        time.sleep(0.002)
+    raise AssertionError(f"request {t} not in {states} after {limit} s")
+
+
+def _served(ys, sp):
+    _, kw = make(ys, sp)
+    spec = W.Spec(kw["R1"], 1.0, kw["Nr"], kw["Nth"], kw["Nph"])
+    return W.convection_initial(spec, sp["Pr"], sp["Ra"], T_in=1.0), kw
+
+
+def test_server_deadline_fails_the_late_request_alone(gpu_lib):
+    """A request that cannot finish before its deadline fails with
+    YS_ETIMEOUT at a step boundary past it; the request served beside it
+    completes, bitwise as alone."""
+    ys = gpu_lib
+    expect = alone(ys, SHELLS[1], 4)
+    srv = ys.Server(hbm_budget_bytes=1 << 30, max_slots=4)
+    f_long, kw_long = _served(ys, SHELLS[2])
+    f_ok, kw_ok = _served(ys, SHELLS[1])
+    t_long = srv.submit(f_long, 10 ** 6, deadline_s=0.5, **kw_long)
+    t_ok = srv.submit(f_ok, 4, **kw_ok)
+    st, f, lat, rc = _wait(srv, t_ok, (ys.Server.DONE, ys.Server.FAILED))
+    assert st == ys.Server.DONE and rc == ys.YS_OK
+    assert all(np.array_equal(f[k], expect[k]) for k in f)
+    st, _, lat, rc = _wait(srv, t_long, (ys.Server.DONE, ys.Server.FAILED))
+    assert st == ys.Server.FAILED and rc == ys.YS_ETIMEOUT and 0.5 <= lat < 30.0, (st, rc, lat)
+    srv.close()
+
+
+def test_server_cancels_queued_and_running_requests_alone(gpu_lib):
+    """With one slot: a queued request cancelled fails at once with
+    YS_ECANCELED, the running one at its next step boundary; the request
+    queued behind them is then admitted and completes bitwise as alone;
+    cancelling a finished request is refused."""
+    ys = gpu_lib
+    expect = alone(ys, SHELLS[1], 4)
+    srv = ys.Server(hbm_budget_bytes=1 << 30, max_slots=1)
+    f_long, kw_long = _served(ys, SHELLS[2])
+    f_ok, kw_ok = _served(ys, SHELLS[1])
+    t1 = srv.submit(f_long, 10 ** 6, **kw_long)
+    _wait(srv, t1, (ys.Server.RUNNING,))
+    t2 = srv.submit(f_long, 10 ** 6, **kw_long)
+    assert srv.poll(t2)[0] == ys.Server.QUEUED
+    srv.cancel(t2)
+    st, _, _, rc = srv.poll(t2)
+    assert st == ys.Server.FAILED and rc == ys.YS_ECANCELED
+    t3 = srv.submit(f_ok, 4, **kw_ok)
+    srv.cancel(t1)
+    st, _, _, rc = _wait(srv, t1, (ys.Server.DONE, ys.Server.FAILED))
+    assert st == ys.Server.FAILED and rc == ys.YS_ECANCELED
+    st, f, _, rc = _wait(srv, t3, (ys.Server.DONE, ys.Server.FAILED))
+    assert st == ys.Server.DONE and rc == ys.YS_OK
+    assert all(np.array_equal(f[k], expect[k]) for k in f)
+    with pytest.raises(ys.YSError) as e:
+        srv.cancel(t3)
+    assert e.value.code == ys.YS_EINVAL
+    srv.close()
+
+
+def test_server_queue_limit_refuses_with_busy(gpu_lib):
+    """A full queue refuses a new request with YS_EBUSY at submit; once a
+    queued request leaves (cancelled) the next submit is accepted."""
+    ys = gpu_lib
+    srv = ys.Server(hbm_budget_bytes=1 << 30, max_slots=1, max_queue=2)
+    f_long, kw_long = _served(ys, SHELLS[2])
+    t1 = srv.submit(f_long, 10 ** 6, **kw_long)
+    _wait(srv, t1, (ys.Server.RUNNING,))
+    q = [srv.submit(f_long, 10 ** 6, **kw_long) for _ in range(2)]
+    with pytest.raises(ys.YSError) as e:
+        srv.submit(f_long, 10 ** 6, **kw_long)
+    assert e.value.code == ys.YS_EBUSY
+    srv.cancel(q[0])
+    q.append(srv.submit(f_long, 10 ** 6, **kw_long))
+    for t in [t1] + q[1:]:
+        srv.cancel(t)
+    for t in [t1] + q[1:]:
+        assert _wait(srv, t, (ys.Server.FAILED,))[3] == ys.YS_ECANCELED
+    srv.close()

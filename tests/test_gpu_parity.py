@@ -359,3 +359,98 @@ def test_pinned_and_pageable_host_buffers_agree(gpu_lib):
     g1 = s1.get_fields(0)
     for k in ("T", "ur", "uth", "uph", "p"):
         assert np.array_equal(g1[k], out[k]), k
+
+
+@pytest.mark.parametrize("Nph", [300, 400, 576])
+def test_long_phi_lines_take_the_wide_and_multi_chunk_scans(gpu_lib, Nph):
+    """phi lines of 300, 400 and 576 positions on a thin 8 x 12 shell: the
+    warp-scan line solves give each lane 12 consecutive positions, as on the
+    128 x 128 x 384 shell; 300 fits one chunk of 384 with a ragged end, 400
+    and 576 take a full chunk of 384 and then a ragged one (16 and 192
+    positions), the path of lines longer than 384.  FP64 against the oracle
+    at the 1e-11 parity bound after 3 steps of 3 iterations.
+
+    The mixed form: T and velocity within 1e-5 of the oracle.  Its pressures
+    are bounded by the storage itself: a velocity stored in FP32 carries a
+    relative rounding of 6e-8, whose discrete divergence, ~6e-8 |u| / (chi h),
+    enters the pressure update at every step, and the phi cells here are 40
+    times narrower than the theta cells.  The test measures that floor on
+    the same grid: the FP64 path started from the initial fields rounded to
+    FP32 once.  The mixed pressures must stay within 10 times its distance to
+    the oracle (and the stated 1e-5 where the floor allows)."""
+    from tests.test_gpu_mixed import rel_errs as mixed_errs
+    ys = gpu_lib
+    kw = dict(kind="curl", Nr=8, Nth=12, Nph=Nph, dt=1e-4, Ra=50.0)
+    o, s, _, _ = make_pair(ys, **kw)
+    _, sm, _, _ = make_pair(ys, **kw, with_oracle=False, precision=ys.YS_MIXED)
+    o.step(3, 3)
+    s.step(3, 3)
+    sm.step(3, 3)
+    ref = o.get_fields(0, aux=True)
+    e = assert_parity(s, o, 1e-11)
+    em = mixed_errs(sm.get_fields(0, aux=True), ref)
+    # the FP32 storage floor of the pressure on this grid
+    spec = W.Spec(0.5, 1.0, 8, 12, Nph)
+    ex = W.CurlShell(0.5, 1.0, 1.0, 50.0)
+    s32 = gpu_lib.Solver(R1=0.5, R2=1.0, Pr=1.0, Ra=50.0, dt=1e-4, Nr=8, Nth=12, Nph=Nph)
+    for lvl, t in ((0, 0.0), (1, -1e-4)):
+        f = W.sample_fields(ex, spec, t)
+        s32.set_fields_dict(lvl, {k: v.astype(np.float32).astype(np.float64) for k, v in f.items()})
+    for m, (tid, F) in enumerate(W.forcing_modes(ex, spec)):
+        s32.set_forcing(m, tid, F["T"], F["ur"], F["uth"], F["uph"])
+    s32.step(3, 3)
+    floor = mixed_errs(s32.get_fields(0, aux=True), ref)
+    print(Nph, e, em, floor)
+    assert max(v for k, v in em.items() if k not in ("p", "p1")) <= 1e-5, em
+    for k in ("p", "p1"):
+        assert em[k] <= max(1e-5, 10.0 * floor[k]), (k, em[k], floor[k])
+
+
+def blow_up_state(c=1e6):
+    """Inconsistent time levels, a failure made on the host: the second-order
+    velocity of level n-1 is twice that of level n, which is c times the curl
+    solution, while the first-order system, T and p are at rest.  The
+    extrapolated iterate is then c u, and the advecting velocity
+    1.5 u^n - 0.5 u^{n-1} = c u / 2 is so large that the line operators lose
+    diagonal dominance: the defect correction diverges within the step."""
+    spec = W.Spec(0.5, 1.0, 16, 16, 48)
+    f = W.sample_fields(W.CurlShell(0.5, 1.0, 1.0, 10.0), spec, 0.0)
+    z = {k: np.zeros_like(v) for k, v in f.items()}
+    aux = (z["ur"], z["uth"], z["uph"], z["p"])
+    lv0 = dict(z, ur=c * f["ur"], uth=c * f["uth"], uph=c * f["uph"])
+    lv1 = dict(z, ur=2 * c * f["ur"], uth=2 * c * f["uth"], uph=2 * c * f["uph"])
+    return dict(R1=0.5, R2=1.0, Pr=1.0, Ra=10.0, dt=1e-3, Nr=16, Nth=16, Nph=48), lv0, lv1, aux
+
+
+def test_schwarz_blow_up_is_reported_while_the_norms_are_finite(gpu_lib):
+    """The divergence watch: on the blow-up state the oracle's largest
+    increment norm grows more than 1e3-fold from the second iteration to the
+    third, all finite.  ys_step with 2 iterations (nothing to compare: the
+    watch starts at the third) returns OK, with 3 it returns YS_EDIVERGED
+    although every norm it read back is finite (the NaN test alone would not
+    trip)."""
+    ys = gpu_lib
+    kw, lv0, lv1, aux = blow_up_state()
+    o = Oracle(Params(**kw))
+    o.set_fields(0, lv0["T"], lv0["ur"], lv0["uth"], lv0["uph"], lv0["p"], aux=aux)
+    o.set_fields(1, lv1["T"], lv1["ur"], lv1["uth"], lv1["uph"], lv1["p"], aux=aux)
+    rec = []
+    iterate = o._iterate
+
+    def watched(*a, **k):
+        r = iterate(*a, **k)
+        rec.append(float(np.max(r)))
+        return r
+
+    o._iterate = watched
+    o.step(1, 3)
+    assert np.isfinite(rec).all() and rec[2] > 1e3 * rec[1], rec
+    for K, expect in ((2, ys.YS_OK), (3, ys.YS_EDIVERGED)):
+        s = ys.Solver(**kw)
+        s.set_fields_dict(0, lv0, aux)
+        s.set_fields_dict(1, lv1, aux)
+        rc = ys.lib.ys_step(s.h, 1, K)
+        assert rc == expect, (K, rc)
+        nrm, it = s.norms()
+        assert it == K and np.isfinite(nrm).all(), nrm
+        s.close()
