@@ -166,6 +166,21 @@ int ys_set_forcing(ys_ctx *c, int mode, int time_fn, const double *f_T, const do
  * Errors: YS_EINVAL, YS_ENOMEM, YS_ECUDA. */
 int ys_set_wall_velocity(ys_ctx *c, const double *ur, const double *uth, const double *uph);
 
+/* Time-dependent Dirichlet wall data tau(t) W, tau one of the forcing time
+ * functions (time_fn as in ys_set_forcing), for solutions with non-zero,
+ * time-varying walls such as the manufactured solution of Sec. 5.1.  T:
+ * [wall][patch][Nth][Nph] wall temperature at the cell-centre angles, added
+ * to T_inner / T_outer (for the wall condition a T + b dT/dn of Tbc_*);
+ * ur, uth, uph: wall velocity in the layouts of ys_set_wall_velocity, added
+ * to the steady wall velocity.  Each state's boundary values take tau at
+ * that state's time: t_n + dt for the iterate of a step, the level's own
+ * time for the stored levels.  Any pointer may be NULL (that part is zero);
+ * a later call replaces the data.  The boundary values of the stored levels
+ * are refreshed.  A context with such data cannot join a batch (YS_EINVAL
+ * from ys_batch_add).  Errors: YS_EINVAL, YS_ENOMEM, YS_ECUDA. */
+int ys_set_wall_data(ys_ctx *c, int time_fn, const double *T, const double *ur, const double *uth,
+                     const double *uph);
+
 /* Set the time t_n of level 0. */
 int ys_set_time(ys_ctx *c, double t);
 

@@ -232,15 +232,21 @@ def wall_ghosts(g, fields, patches, T_walls=(0.0, 0.0), U_walls=None, T_robin=((
     """Radial wall data (Sec. 2): u_r on the wall faces is the wall value;
     u_theta, u_phi get the reflection ghost 2 g - x_0 about the wall velocity g;
     T gets the ghost of its wall condition a T + b dT/dn = T_wall (T_robin
-    gives (a, b) per wall; (1, 0) = Dirichlet: 2 T_wall - T_0).
+    gives (a, b) per wall; (1, 0) = Dirichlet: 2 T_wall - T_0); T_walls[w]
+    is a constant or per point, [2 patches][Nth][Nph].
     U_walls: None (no-slip) or wall velocities as in Params.wall_u."""
     Nr, Nt, Np = g.Nr, g.Nth, g.Nph
     gi, di_ = robin_ghost(T_robin[0][0], T_robin[0][1], float(g.h_f(0)))
     go, do_ = robin_ghost(T_robin[1][0], T_robin[1][1], float(g.h_f(Nr)))
+
+    def wall_T(w, p):   # a constant, or per point [2 patches][Nth][Nph]
+        a = np.asarray(T_walls[w], dtype=np.float64)
+        return a[p] if a.ndim == 3 else a
+
     for p in patches:
         T = fields["T"][p]
-        T[0, 1:Nt + 1, 1:Np + 1] = gi * T[1, 1:Nt + 1, 1:Np + 1] + di_ * T_walls[0]
-        T[Nr + 1, 1:Nt + 1, 1:Np + 1] = go * T[Nr, 1:Nt + 1, 1:Np + 1] + do_ * T_walls[1]
+        T[0, 1:Nt + 1, 1:Np + 1] = gi * T[1, 1:Nt + 1, 1:Np + 1] + di_ * wall_T(0, p)
+        T[Nr + 1, 1:Nt + 1, 1:Np + 1] = go * T[Nr, 1:Nt + 1, 1:Np + 1] + do_ * wall_T(1, p)
         if U_walls is None:
             gr = (0.0, 0.0)
             gt = (0.0, 0.0)

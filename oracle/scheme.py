@@ -79,6 +79,11 @@ class Params:
     # radii of the 2 Nr + 1 radial half points (faces at even, centres at odd
     # positions; grid.py); None = uniform radial grid
     r_half: Optional[tuple] = None
+    # time-dependent Dirichlet wall data tau(t) W (the manufactured solution
+    # of Sec. 5.1 has non-zero, time-dependent walls): (time function id,
+    # dict with any of 'T' [2 walls][2 patches][Nth][Nph] added to T_in /
+    # T_out, and 'ur', 'uth', 'uph' as in wall_u, added to it); None = none
+    wall_mode: Optional[tuple] = None
 
 
 def _time_fn(tid, t):
@@ -144,16 +149,39 @@ class Oracle:
         else:
             L.u1 = [self._to_padded(R, aux[0]), self._to_padded(TH, aux[1]), self._to_padded(PH, aux[2])]
             L.p1 = self._to_padded(C, aux[3])
-        self._refresh(L, (0, 1))
+        self._refresh(L, (0, 1), self.t - level * self.prm.dt)
         if level == 0 and not self.level1_set:
             self.lev[1] = L.copy()
         if level == 1:
             self.level1_set = True
 
-    def _refresh(self, L, patches):
+    def _walls(self, t):
+        """Wall data at time t: (T_walls, U_walls) for the exchange; the
+        constant wall temperatures and steady wall velocity plus the
+        time-dependent mode tau(t) W."""
+        prm = self.prm
+        T_walls, U_walls = (prm.T_in, prm.T_out), prm.wall_u
+        if prm.wall_mode is not None:
+            tid, W = prm.wall_mode
+            c = _time_fn(tid, t)
+            if W.get("T") is not None:
+                T_walls = tuple(T_walls[w] + c * np.asarray(W["T"][w]) for w in range(2))
+            if any(W.get(k) is not None for k in ("ur", "uth", "uph")):
+                base = U_walls
+                U_walls = {}
+                for k, n in (("ur", (self.g.Nth, self.g.Nph)), ("uth", (self.g.Nth + 1, self.g.Nph)),
+                             ("uph", (self.g.Nth, self.g.Nph + 1))):
+                    a = np.zeros((2, 2) + n) if base is None or base.get(k) is None else np.asarray(base[k])
+                    if W.get(k) is not None:
+                        a = a + c * np.asarray(W[k])
+                    U_walls[k] = a
+        return T_walls, U_walls
+
+    def _refresh(self, L, patches, t):
         d = L.as_dict()
-        xch.exchange_into(self.tables, d, d, patches, (self.prm.T_in, self.prm.T_out), self.prm.wall_u,
-                          self._step4(), (self.prm.Tbc_in, self.prm.Tbc_out))
+        T_walls, U_walls = self._walls(t)
+        xch.exchange_into(self.tables, d, d, patches, T_walls, U_walls, self._step4(),
+                          (self.prm.Tbc_in, self.prm.Tbc_out))
         if self.prm.step7:
             xch.pressure_ring(self.tables, L.p1, patches)
             xch.pressure_ring(self.tables, L.p2, patches)
@@ -220,11 +248,12 @@ class Oracle:
                    2.0 * n.p1 - nm1.p1, 2.0 * n.p2 - nm1.p2)
         f = self.forcing(self.t + 0.5 * dt)
         fac = self._factors(A)
+        T_walls, U_walls = self._walls(self.t + dt)     # the new level's wall data
         self.iters_done = 0
         for k in range(1, K + 1):
             if prm.schwarz_mode == "additive":
                 d = it.as_dict()
-                xch.exchange_into(self.tables, d, d, (0, 1), (prm.T_in, prm.T_out), prm.wall_u, self._step4(),
+                xch.exchange_into(self.tables, d, d, (0, 1), T_walls, U_walls, self._step4(),
                                   (prm.Tbc_in, prm.Tbc_out))
                 norms = self._iterate(it, n, A, f, fac, (0, 1))
                 if prm.step7:
@@ -234,7 +263,7 @@ class Oracle:
                 norms = np.zeros(len(FIELD_NAMES))
                 for p in (0, 1):
                     d = it.as_dict()
-                    xch.exchange_into(self.tables, d, d, (p,), (prm.T_in, prm.T_out), prm.wall_u, self._step4(),
+                    xch.exchange_into(self.tables, d, d, (p,), T_walls, U_walls, self._step4(),
                                       (prm.Tbc_in, prm.Tbc_out))
                     norms += self._iterate(it, n, A, f, fac, (p,)) ** 2
                     if prm.step7:
@@ -247,7 +276,7 @@ class Oracle:
             self.iters_done = k
             if prm.schwarz_tol > 0 and norms.max() < prm.schwarz_tol:
                 break
-        self._refresh(it, (0, 1))
+        self._refresh(it, (0, 1), self.t + dt)
         self.lev = [it, n]
         self.t += dt
         self.steps_done += 1

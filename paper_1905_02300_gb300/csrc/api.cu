@@ -190,21 +190,36 @@ int copy_out_p(ys_ctx *c, const double *src, double *dst) {
   return e == cudaSuccess ? YS_OK : YS_ECUDA;
 }
 
+// time function id of separable forcing and wall modes
+double time_fn(int id, double t) {
+  switch (id) {
+    case 0: return 1.0;
+    case 1: return std::cos(t);
+    case 2: return std::sin(t);
+    case 3: return std::cos(t) * std::cos(t);
+    case 4: return std::sin(t) * std::cos(t);
+  }
+  return 0.0;
+}
+
 // exchange + walls (+ pressure ring) of a whole state: boundary values as
-// functions of the interior
+// functions of the interior; t: the time of the state (time-dependent wall data)
 template <typename R>
-void exchange_walls(ys_ctx *c, State<R> s, int mask) {
+void exchange_walls(ys_ctx *c, State<R> s, int mask, double t) {
+  WallData wt = c->wall_t;
+  wt.tau = time_fn(c->wall_tfn, t);
   LAUNCH(c, K_EXCH, 4, Launch<R>::exchange(c->S, c->X, s, mask, c->stream));
-  LAUNCH(c, K_WALLS, 1, Launch<R>::walls(c->S, s, mask, c->stream));
+  LAUNCH(c, K_WALLS, 1, Launch<R>::walls(c->S, wt, s, mask, c->stream));
   if (c->prm.step4)
     LAUNCH(c, K_EXCH, 2,
-           Launch<R>::mass_flux(c->S, s, mask, c->norm + 16, c->s4_alpha, c->s4_wsq, c->s4_cwall[0],
-                                c->s4_cwall[1], c->prm.step4_tol, c->stream));
+           Launch<R>::mass_flux(c->S, s, mask, c->norm + 16, c->s4_alpha, c->s4_wsq,
+                                c->s4_cwall[0] + wt.tau * c->s4_cwall_t[0],
+                                c->s4_cwall[1] + wt.tau * c->s4_cwall_t[1], c->prm.step4_tol, c->stream));
 }
 
 template <typename R>
-void refresh(ys_ctx *c, State<R> s, int mask) {
-  exchange_walls<R>(c, s, mask);
+void refresh(ys_ctx *c, State<R> s, int mask, double t) {
+  exchange_walls<R>(c, s, mask, t);
   if (c->prm.step7) LAUNCH(c, K_RING, 1, Launch<R>::ring(c->S, c->X, s, mask, c->stream));
 }
 
@@ -245,8 +260,8 @@ void factorize_all(ys_ctx *c, StepAux<R> ax) {
 template <typename R>
 void refresh_levels(ys_ctx *c) {
   Fields<R> &D = F<R>(c);
-  refresh<R>(c, D.lev[0], 3);
-  refresh<R>(c, D.lev[1], 3);
+  refresh<R>(c, D.lev[0], 3, c->t);
+  refresh<R>(c, D.lev[1], 3, c->t - c->prm.dt);
 }
 
 // one defect-correction pass over T, u1, p1, u2, p2 on the masked patches
@@ -266,16 +281,6 @@ void iterate(ys_ctx *c, StepAux<R> ax, int mask) {
   }
 }
 
-double time_fn(int id, double t) {
-  switch (id) {
-    case 0: return 1.0;
-    case 1: return std::cos(t);
-    case 2: return std::sin(t);
-    case 3: return std::cos(t) * std::cos(t);
-    case 4: return std::sin(t) * std::cos(t);
-  }
-  return 0.0;
-}
 
 template <typename R>
 int step_t(ys_ctx *c, int n_steps, int n_schwarz) {
@@ -312,13 +317,13 @@ int step_t(ys_ctx *c, int n_steps, int n_schwarz) {
     for (int k = 1; k <= n_schwarz; ++k) {
       cudaMemsetAsync(c->norm, 0, YS_NFIELDS * sizeof(double), c->stream);
       if (prm.schwarz_mode == YS_ADDITIVE) {
-        exchange_walls<R>(c, it, 3);
+        exchange_walls<R>(c, it, 3, c->t + prm.dt);
         iterate<R>(c, ax, 3);
         if (prm.step7) LAUNCH(c, K_RING, 1, Launch<R>::ring(c->S, c->X, it, 3, c->stream));
       } else {
         for (int p = 0; p < 2; ++p) {
           int m = 1 << p;
-          exchange_walls<R>(c, it, m);
+          exchange_walls<R>(c, it, m, c->t + prm.dt);
           iterate<R>(c, ax, m);
           if (prm.step7) LAUNCH(c, K_RING, 1, Launch<R>::ring(c->S, c->X, it, m, c->stream));
         }
@@ -335,7 +340,7 @@ int step_t(ys_ctx *c, int n_steps, int n_schwarz) {
         if (mx < prm.schwarz_tol) break;
       }
     }
-    refresh<R>(c, it, 3);
+    refresh<R>(c, it, 3, c->t + prm.dt);
     // rotate time levels: n-1 <- n, n <- iterate, iterate <- old n-1
     D.lev[0] = it;
     D.lev[1] = n;
@@ -380,7 +385,7 @@ int set_fields_t(ys_ctx *c, int level, const double *T, const double *ur, const 
     rc |= copy_in_p(c, aux + o, s.p[0], dev);
   }
   if (rc) return YS_ECUDA;
-  refresh<R>(c, s, 3);
+  refresh<R>(c, s, 3, c->t - level * c->prm.dt);
   if (level == 0 && !c->level1_set) {
     const int bulk[7] = {F_T, F_U1R, F_U1T, F_U1P, F_U2R, F_U2T, F_U2P};
     for (int b = 0; b < 7; ++b)
@@ -587,6 +592,7 @@ int ys_destroy(ys_ctx *c) {
     if (c->modes_mem[m]) cudaFree(c->modes_mem[m]);
   if (c->dmem) cudaFree(c->dmem);
   if (c->dwall) cudaFree(c->dwall);
+  if (c->dwall_t) cudaFree(c->dwall_t);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c->f64;
   delete c->f32;
@@ -992,6 +998,56 @@ int ys_set_wall_velocity(ys_ctx *c, const double *ur, const double *uth, const d
           const double a = (w ? 1.0 : -1.0) * R[w] * R[w] * std::sin(c->geo.th0 + (j + 0.5) * c->geo.ht) *
                            c->geo.ht * c->geo.hp;
           for (long k = 0; k < Np; ++k) c->s4_cwall[p] += a * ur[((w * 2 + p) * Nt + j) * Np + k];
+        }
+  }
+  // boundary values of the stored levels follow the new wall data
+  if (c->f32)
+    refresh_levels<float>(c);
+  else
+    refresh_levels<double>(c);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return YS_ECUDA;
+  return YS_OK;
+}
+
+int ys_set_wall_data(ys_ctx *c, int time_fn_id, const double *T, const double *ur, const double *uth,
+                     const double *uph) {
+  if (!c || time_fn_id < 0 || time_fn_id > 4) return YS_EINVAL;
+  const long Nt = c->L.Nt, Np = c->L.Np;
+  const size_t n[4] = {(size_t)(4 * Nt * Np), (size_t)(4 * Nt * Np), (size_t)(4 * (Nt + 1) * Np),
+                       (size_t)(4 * Nt * (Np + 1))};
+  const double *src[4] = {T, ur, uth, uph};
+  if (!c->dwall_t && (T || ur || uth || uph)) {
+    if (cudaMalloc(&c->dwall_t, (n[0] + n[1] + n[2] + n[3]) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      c->dwall_t = nullptr;
+      return YS_ENOMEM;
+    }
+    c->dbytes += (n[0] + n[1] + n[2] + n[3]) * sizeof(double);
+  }
+  const double **dst[4] = {&c->wall_t.T, &c->wall_t.ur, &c->wall_t.ut, &c->wall_t.up};
+  size_t off = 0;
+  for (int m = 0; m < 4; ++m) {
+    if (src[m]) {
+      if (cudaMemcpyAsync(c->dwall_t + off, src[m], n[m] * sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess)
+        return YS_ECUDA;
+      *dst[m] = c->dwall_t + off;
+    } else {
+      *dst[m] = nullptr;
+    }
+    off += n[m];
+  }
+  c->wall_tfn = time_fn_id;
+  // Algorithm step 4: wall flux of the time-dependent u_r per unit tau
+  c->s4_cwall_t[0] = c->s4_cwall_t[1] = 0.0;
+  if (ur) {
+    const double R[2] = {c->prm.R1, c->prm.R2};
+    for (int w = 0; w < 2; ++w)
+      for (int p = 0; p < 2; ++p)
+        for (long j = 0; j < Nt; ++j) {
+          const double a = (w ? 1.0 : -1.0) * R[w] * R[w] * std::sin(c->geo.th0 + (j + 0.5) * c->geo.ht) *
+                           c->geo.ht * c->geo.hp;
+          for (long k = 0; k < Np; ++k) c->s4_cwall_t[p] += a * ur[((w * 2 + p) * Nt + j) * Np + k];
         }
   }
   // boundary values of the stored levels follow the new wall data

@@ -248,7 +248,7 @@ __global__ void kb_exchange(const ShellDev<R> *sh, WorkMap map, int cap, int kin
 template <typename R>
 __global__ void kb_walls(const ShellDev<R> *sh, WorkMap map, int cap) {
   YS_BATCH_LOOP(map, cap)
-  bd::body_walls(D.S, it, 3, bx, by);
+  bd::body_walls(D.S, WallData{}, it, 3, bx, by);
   }
 }
 
@@ -693,6 +693,7 @@ int ys_batch_add(ys_batch *b, ys_ctx *c, int *slot) {
   if (!b || !c || !slot) return YS_EINVAL;
   if ((c->prm.precision == YS_MIXED) != (b->precision == YS_MIXED)) return YS_EINVAL;
   if (c->prm.schwarz_mode != YS_ADDITIVE || c->nmodes_set > 0 || c->prm.step4) return YS_EINVAL;
+  if (c->wall_t.T || c->wall_t.ur || c->wall_t.ut || c->wall_t.up) return YS_EINVAL;
   int s = -1;
   for (int i = 0; i < b->cap; ++i)
     if (!b->slot[i]) {

@@ -917,7 +917,7 @@ __device__ __forceinline__ void body_exchange(Shell S, const XEntry *__restrict_
 }
 
 template <typename R>
-__device__ __forceinline__ void body_walls(Shell S, State<R> s, int patch_mask, int bx, int by) {
+__device__ __forceinline__ void body_walls(Shell S, WallData wt, State<R> s, int patch_mask, int bx, int by) {
   const Layout &L = S.L;
   int p = by;
   if (!((patch_mask >> p) & 1)) return;
@@ -933,24 +933,39 @@ __device__ __forceinline__ void body_walls(Shell S, State<R> s, int patch_mask, 
   // columns (0 = no-slip unless wall data is set), 0 on the ghost columns
   const bool cc = (j >= 0 && j < Nt && k >= 0 && k < Np);
   double g0 = 0.0, g1 = 0.0;
+  const long qc0 = ((long)(0 * 2 + p) * Nt + j) * Np + k, qc1 = ((long)(1 * 2 + p) * Nt + j) * Np + k;
   if (S.wall_ur && cc) {
-    g0 = S.wall_ur[((long)(0 * 2 + p) * Nt + j) * Np + k];
-    g1 = S.wall_ur[((long)(1 * 2 + p) * Nt + j) * Np + k];
+    g0 = S.wall_ur[qc0];
+    g1 = S.wall_ur[qc1];
+  }
+  if (wt.ur && cc) {
+    g0 += wt.tau * wt.ur[qc0];
+    g1 += wt.tau * wt.ur[qc1];
   }
   s.f[F_U1R][l0] = (R)g0;
   s.f[F_U2R][l0] = (R)g0;
   s.f[F_U1R][hi] = (R)g1;
   s.f[F_U2R][hi] = (R)g1;
   if (cc) {
-    s.f[F_T][lo] = (R)(S.Tgam[0] * (double)s.f[F_T][l0] + S.Tdel[0] * S.T_in);
-    s.f[F_T][hi] = (R)(S.Tgam[1] * (double)s.f[F_T][h0] + S.Tdel[1] * S.T_out);
+    double T0 = S.T_in, T1 = S.T_out;
+    if (wt.T) {
+      T0 += wt.tau * wt.T[qc0];
+      T1 += wt.tau * wt.T[qc1];
+    }
+    s.f[F_T][lo] = (R)(S.Tgam[0] * (double)s.f[F_T][l0] + S.Tdel[0] * T0);
+    s.f[F_T][hi] = (R)(S.Tgam[1] * (double)s.f[F_T][h0] + S.Tdel[1] * T1);
   }
   // u_theta, u_phi: reflection ghosts 2 g - x_0 about the wall velocity g
   if (j >= 1 && j < Nt && k >= 0 && k < Np) {
     g0 = g1 = 0.0;
+    const long q0 = ((long)(0 * 2 + p) * (Nt + 1) + j) * Np + k, q1 = ((long)(1 * 2 + p) * (Nt + 1) + j) * Np + k;
     if (S.wall_ut) {
-      g0 = S.wall_ut[((long)(0 * 2 + p) * (Nt + 1) + j) * Np + k];
-      g1 = S.wall_ut[((long)(1 * 2 + p) * (Nt + 1) + j) * Np + k];
+      g0 = S.wall_ut[q0];
+      g1 = S.wall_ut[q1];
+    }
+    if (wt.ut) {
+      g0 += wt.tau * wt.ut[q0];
+      g1 += wt.tau * wt.ut[q1];
     }
     for (int o = 0; o <= 4; o += 4) {
       R *u = s.f[F_U1T + o];
@@ -960,9 +975,14 @@ __device__ __forceinline__ void body_walls(Shell S, State<R> s, int patch_mask, 
   }
   if (j >= 0 && j < Nt && k >= 1 && k < Np) {
     g0 = g1 = 0.0;
+    const long q0 = ((long)(0 * 2 + p) * Nt + j) * (Np + 1) + k, q1 = ((long)(1 * 2 + p) * Nt + j) * (Np + 1) + k;
     if (S.wall_up) {
-      g0 = S.wall_up[((long)(0 * 2 + p) * Nt + j) * (Np + 1) + k];
-      g1 = S.wall_up[((long)(1 * 2 + p) * Nt + j) * (Np + 1) + k];
+      g0 = S.wall_up[q0];
+      g1 = S.wall_up[q1];
+    }
+    if (wt.up) {
+      g0 += wt.tau * wt.up[q0];
+      g1 += wt.tau * wt.up[q1];
     }
     for (int o = 0; o <= 4; o += 4) {
       R *u = s.f[F_U1P + o];

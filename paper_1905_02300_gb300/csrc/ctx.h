@@ -52,6 +52,10 @@ struct ys_ctx {
   double *norm = nullptr;     // YS_NFIELDS accumulators
   double *stage = nullptr;    // host-layout staging (device); per-block norm shares of k_pressure during a step
   double *dwall = nullptr;    // Dirichlet wall velocity (device, ys_set_wall_velocity), or null
+  double *dwall_t = nullptr;  // time-dependent wall data (device, ys_set_wall_data), or null
+  ys::WallData wall_t = {};   // its parts (pointers into dwall_t)
+  int wall_tfn = 0;           // its time function
+  double s4_cwall_t[2] = {0.0, 0.0};   // wall flux of the time-dependent wall velocity per unit tau
   // Algorithm step 4: alpha = 1 / (eps |dOmega|^2), w.w of the edge flux
   // weights, and the wall flux c of each patch (from the wall velocity)
   double s4_alpha = 0.0, s4_wsq = 0.0, s4_cwall[2] = {0.0, 0.0};

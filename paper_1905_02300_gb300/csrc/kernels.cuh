@@ -80,7 +80,7 @@ struct Launch {
   static void combine_forcing(long total, Modes<R> modes, R *out[4], cudaStream_t st);
   // Schwarz exchange into the listed patches (mask bit p) of state s
   static void exchange(const Shell &S, const XTables &X, State<R> s, int patch_mask, cudaStream_t st);
-  static void walls(const Shell &S, State<R> s, int patch_mask, cudaStream_t st);
+  static void walls(const Shell &S, const WallData &wt, State<R> s, int patch_mask, cudaStream_t st);
   static void ring(const Shell &S, const XTables &X, State<R> s, int patch_mask, cudaStream_t st);
   // residual -F into B
   static void resid_T(const Shell &S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask,

@@ -24,8 +24,8 @@ __global__ void k_exchange(Shell S, const XEntry *__restrict__ e, int n, int kin
 
 // radial wall data: threads over the padded (j, k) plane, blockIdx.y = patch
 template <typename R>
-__global__ void k_walls(Shell S, State<R> s, int patch_mask) {
-  bd::body_walls(S, s, patch_mask, blockIdx.x, blockIdx.y);
+__global__ void k_walls(Shell S, WallData wt, State<R> s, int patch_mask) {
+  bd::body_walls(S, wt, s, patch_mask, blockIdx.x, blockIdx.y);
 }
 
 // Algorithm step 4 (mass-flux correction).  Edge faces of a patch: theta
@@ -122,9 +122,9 @@ void Launch<R>::exchange(const Shell &S, const XTables &X, State<R> s, int pm, c
 }
 
 template <typename R>
-void Launch<R>::walls(const Shell &S, State<R> s, int pm, cudaStream_t st) {
+void Launch<R>::walls(const Shell &S, const WallData &wt, State<R> s, int pm, cudaStream_t st) {
   long plane = (long)(S.L.Nt + 2) * (S.L.Np + 2);
-  k_walls<R><<<dim3((unsigned)((plane + 255) / 256), 2), 256, 0, st>>>(S, s, pm);
+  k_walls<R><<<dim3((unsigned)((plane + 255) / 256), 2), 256, 0, st>>>(S, wt, s, pm);
 }
 
 template <typename R>
@@ -135,7 +135,7 @@ void Launch<R>::ring(const Shell &S, const XTables &X, State<R> s, int pm, cudaS
 
 #define YS_INST_EXCHANGE(R)                                                                 \
   template void Launch<R>::exchange(const Shell &, const XTables &, State<R>, int, cudaStream_t); \
-  template void Launch<R>::walls(const Shell &, State<R>, int, cudaStream_t);                   \
+  template void Launch<R>::walls(const Shell &, const WallData &, State<R>, int, cudaStream_t);                   \
   template void Launch<R>::ring(const Shell &, const XTables &, State<R>, int, cudaStream_t);       \
   template void Launch<R>::mass_flux(const Shell &, State<R>, int, double *, double, double, double, double, \
                                      double, cudaStream_t);

@@ -139,6 +139,16 @@ struct Shell {
   int step7;
 };
 
+// Time-dependent wall data tau(t) W (ys_set_wall_data), passed to the wall
+// kernel beside the shell: wall temperature [wall][patch][j][k] at the
+// cell-centre angles, added to T_in / T_out, and wall velocity in the layouts
+// of Shell::wall_*, added to the steady one; tau at the time of the state
+// whose boundary values the launch fills.  Null pointers: no such part.
+struct WallData {
+  const double *T, *ur, *ut, *up;
+  double tau;
+};
+
 
 // Exchange table entry: one target point in the (theta, phi) plane of a patch,
 // with one or two bilinear donor stencils on the other patch and, for

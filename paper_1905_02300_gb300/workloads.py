@@ -448,7 +448,41 @@ class LandauJet(Exact):
         return U, P, Th
 
 
-EXACT = {c.name: c for c in (TrigShell, CurlShell, RadialHeat, RadialHeatRobin, SymmetricShell, LandauJet)}
+class PaperShell(Exact):
+    """The manufactured solution of Sec. 5.1, given in Cartesian form:
+      u = cos t (2 x^2 y z, -x y^2 z, -x y z^2),  p = cos t x y z,
+      T = 2 cos t x^2 y z,
+    divergence-free (4xyz - 2xyz - 2xyz = 0), with time-dependent,
+    non-zero velocity and temperature on both walls (the paper runs it with
+    R1 = 1, R2 = 2, Ra = Pr = 1): it needs the wall data of wall_velocity and
+    wall_temperature, which follow cos t."""
+
+    name = "paper"
+
+    def fields(self, x, y, z, F):
+        U = [2.0 * x * x * y * z, -x * y * y * z, -x * y * z * z]
+        return U, x * y * z, 2.0 * x * x * y * z
+
+
+EXACT = {c.name: c for c in (TrigShell, CurlShell, RadialHeat, RadialHeatRobin, SymmetricShell, LandauJet,
+                             PaperShell)}
+
+
+def wall_temperature(ex: Exact, spec: Spec, t: float = 0.0):
+    """Temperature of ``ex`` on the walls r = R1 and r = R2 at the cell-centre
+    angles of each patch: array [2 walls][2 patches][Nth][Nph]."""
+    c = ex.tfac(t)
+    _, th, ph = spec.coords("c")
+    th2, ph2 = th[0, 0], ph[0, 0]
+    walls = []
+    for R in (spec.R1, spec.R2):
+        xl = R * np.sin(th2) * np.cos(ph2)
+        yl = R * np.sin(th2) * np.sin(ph2)
+        zl = R * np.cos(th2) + 0.0 * ph2
+        x, y, z = np.stack([xl, -xl]), np.stack([yl, zl]), np.stack([zl, yl])
+        _, _, Th = ex.fields(x, y, z, np)
+        walls.append(np.broadcast_to(Th, x.shape) * c)
+    return np.stack(walls)
 
 
 def wall_velocity(ex: Exact, spec: Spec, t: float = 0.0):
@@ -641,15 +675,38 @@ def convection_perturbation(spec: Spec, seed: int = 3, amp: float = 1e-3, kmax: 
     gth = np.arccos(np.clip(z / rr, -1.0, 1.0))
     gph = np.arctan2(y, x)
     L = spec.R2 - spec.R1
-    rad = [np.sin((k + 1) * math.pi * (rr - spec.R1) / L) for k in range(kmax)]
-    sth = [np.sin((l + 1) * gth) for l in range(kmax)]
-    cph = [np.cos(m * gph) for m in range(kmax + 1)]
-    pert = np.zeros(spec.shape("c"))
-    for k in range(kmax):
-        for l in range(kmax):
-            tl = rad[k] * sth[l]
-            for m in range(kmax + 1):
-                pert += coef[k, l, m] * tl * cph[m]
+    # the triple sum contracted point by point: sum_k rad_k sum_l sth_l
+    # (sum_m c_klm cph_m), in chunks of points (bounded memory)
+    rr, gth, gph = (np.broadcast_to(a, spec.shape("c")).ravel() for a in (rr, gth, gph))
+    pert = np.empty(rr.size)
+    cmat = coef.reshape(kmax * kmax, kmax + 1).T
+    def multiples(x, n, sine):
+        """Rows sin(j x), j = 1..n (sine) or cos(j x), j = 0..n, by the
+        recurrence f_{j+1} = 2 cos(x) f_j - f_{j-1}."""
+        c1 = np.cos(x)
+        out = np.empty((n if sine else n + 1, x.size))
+        if sine:
+            out[0] = np.sin(x)
+            prev = np.zeros_like(x)
+        else:
+            out[0] = 1.0
+            out[1] = c1
+            prev = out[0]
+        for j in range(1, out.shape[0]):
+            if not sine and j == 1:
+                continue
+            out[j] = 2.0 * c1 * out[j - 1] - prev
+            prev = out[j - 1]
+        return out
+
+    for a in range(0, rr.size, 1 << 20):
+        sl = slice(a, a + (1 << 20))
+        rad = multiples((rr[sl] - spec.R1) * (math.pi / L), kmax, True)      # (k, p)
+        sth = multiples(gth[sl], kmax, True)                                 # (l, p)
+        cph = multiples(gph[sl], kmax, False)                                # (m, p)
+        A = (cmat.T @ cph).reshape(kmax, kmax, -1)                           # (k, l, p)
+        pert[sl] = np.sum(rad * np.einsum("klp,lp->kp", A, sth), axis=0)
+    pert = pert.reshape(spec.shape("c"))
     return pert * (amp / np.abs(pert).max())
 
 

@@ -48,6 +48,7 @@ _sig = {
     "ys_set_forcing": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, _dp, _dp, _dp]),
     "ys_set_wall_velocity": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
     "ys_set_time": (C.c_int, [C.c_void_p, C.c_double]),
+    "ys_set_wall_data": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp]),
     "ys_step": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "ys_get_fields": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]),
     "ys_get_stats": (C.c_int, [C.c_void_p, _dp, _dp, C.POINTER(C.c_long)]),
@@ -206,6 +207,21 @@ class Solver:
                     raise ValueError(f"{k}: shape {a.shape}, expected {shapes[k]}")
             arrs.append(a)
         _check(lib.ys_set_wall_velocity(self.h, *[_ptr(a) for a in arrs]), "ys_set_wall_velocity")
+
+    def set_wall_data(self, time_fn, walls):
+        """Time-dependent wall data tau(t) W: dict with any of 'T'
+        [2][2][Nth][Nph] and 'ur', 'uth', 'uph' as in set_wall_velocity."""
+        Nt, Np = self.params.Nth, self.params.Nph
+        shapes = {"T": (2, 2, Nt, Np), "ur": (2, 2, Nt, Np), "uth": (2, 2, Nt + 1, Np), "uph": (2, 2, Nt, Np + 1)}
+        arrs = []
+        for k in ("T", "ur", "uth", "uph"):
+            a = walls.get(k)
+            if a is not None:
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                if a.shape != shapes[k]:
+                    raise ValueError(f"{k}: shape {a.shape}, expected {shapes[k]}")
+            arrs.append(a)
+        _check(lib.ys_set_wall_data(self.h, time_fn, *[_ptr(a) for a in arrs]), "ys_set_wall_data")
 
     def set_time(self, t):
         _check(lib.ys_set_time(self.h, t), "ys_set_time")
@@ -384,18 +400,19 @@ class Server:
         self.shapes[t.value] = (p.Nr, p.Nth, p.Nph)
         return t.value
 
-    def poll(self, ticket):
-        """(state, fields or None, latency_s or None, error code)"""
+    def poll(self, ticket, fields=True):
+        """(state, fields or None, latency_s or None, error code); with
+        fields=False the result is not copied out."""
         Nr, Nt, Np = self.shapes[ticket]
         n = 2 * Nr * Nt * Np * 2 + 2 * (Nr + 1) * Nt * Np + 2 * Nr * (Nt + 1) * Np + 2 * Nr * Nt * (Np + 1)
-        buf = np.empty(n)
+        buf = np.empty(n) if fields else None
         st, lat = C.c_int(), C.c_double()
         rc = lib.ys_poll(self.h, C.c_uint64(ticket), C.byref(st), _ptr(buf), C.byref(lat))
         if rc == YS_EAGAIN:
             return st.value, None, None, rc
         if rc != YS_OK:
             return st.value, None, lat.value, rc
-        return st.value, unpack_fields(buf, Nr, Nt, Np), lat.value, rc
+        return st.value, unpack_fields(buf, Nr, Nt, Np) if fields else None, lat.value, rc
 
     def stats(self):
         steps, cu, run, q, pk = C.c_long(), C.c_double(), C.c_int(), C.c_int(), C.c_int()
