@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark: cell-updates/s per artificial-compressibility time step.
 
-Workload (default): one Yin-Yang shell, 128x128x384 MAC cells per patch,
+Workload (headline): one Yin-Yang shell, 128x128x384 MAC cells per patch,
 R1=0.5, R2=1, Pr=1, Ra=1e3, dt=5e-4, 3 Schwarz / splitting-error-reduction
 iterations per step, FP64, forced by the trigonometric manufactured solution
 with homogeneous walls (synthetic data, seeded, no dataset).  A cell-update is
@@ -10,7 +10,7 @@ iterations included: value = 2 Nr Nth Nph * steps / time.
 
 Timing: W untimed warm-up steps, then exactly K steps bracketed by
 barrier + synchronize, timed with CUDA events on the solver's stream; the
-state (~5 GB) is larger than L2, so no flush is needed.  N > 1: one
+state (~10 GB) is larger than L2, so no flush is needed.  N > 1: one
 independent shell per GPU (replicas; no collective on the data path), value =
 total cell-updates / max over ranks.
 
@@ -19,6 +19,18 @@ buffers: upload both time levels, one step, download level 0, per step),
 per-kernel times from CUDA events, roofline of the dominant kernel class,
 SM clocks sampled during the timed region, and the FP64 oracle timed on the
 host cores on a bounded sample (cpu_baseline).
+
+By default (one GPU) the same JSON line also carries, as objects:
+  mixed     the same shell in the mixed FP32/FP64 form (device and e2e
+            rates, roofline, the line solves' fraction of HBM bandwidth);
+  ensemble  64 seeded uneven shells in one batch (one launch per kernel
+            class, a CUDA graph per step), 100 timed steps, per-class
+            roofline, against the plain FP64 path one shell at a time;
+  serving   200 Poisson-arriving requests (Nr <= 128, Nth <= 192,
+            N in [50, 500] steps) under continuous batching at 0.8 of the
+            batched capacity: p50/p99 time to completion, aggregate
+            cell-updates/s, against FIFO plain FP64 service.
+--workload shell|ensemble|serving runs one of them alone.
 
 --impl reference runs the oracle (a plain CPU program; there is no other
 implementation of the paper's method) on a bounded sample of the same
@@ -71,7 +83,7 @@ WORDS_PER_CELL = {
 # The sums of the advecting velocity are formed once per step (extrapolate
 # class) and not counted again here.
 FLOPS_PER_CELL = {"resid_T": 39.0, "resid_u": 83.0, "pressure": 21.0, "factorize": 9.0}
-FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of GB300 (profiling recipe)
+FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of GB300 (context; the bench measures its own)
 # DRAM bytes (read + write) per point of the top kernel class from one ncu
 # capture of its u_r launch on a smaller shell whose launch already exceeds L2
 # (traffic scales with the points processed); the bench reports it scaled to
@@ -181,173 +193,242 @@ def oracle_sample(n, K, steps):
 
 def ensemble_shells(seed, n, nr_max, nth_max, ys, precision):
     """Seeded uneven shells (workloads.shell_ensemble): convection start with a
-    hot inner wall, dt = 0.5 h_min^2 per shell, h_min the smallest of h_r,
-    R1 h_theta and R1 sin(theta_1) h_phi (inside the fixed-iteration stability
-    limit dt < chi h^2)."""
+    hot inner wall and the perturbation of wave numbers k, l, m <= 6,
+    dt = 0.5 h_min^2 min(1, sqrt(1e3 / Ra)) per shell, h_min the smallest of
+    h_r, R1 h_theta and R1 sin(theta_1) h_phi: inside the fixed-iteration
+    stability limit dt < chi h^2, and short enough at high Ra that a run of
+    a few hundred steps stays in the growth phase of the convection (its
+    growth rate rises like sqrt(Ra); the saturated flow at Ra ~ 1e6 would
+    need an advective CFL limit near 1e-6, and with 0.5 h_min^2 alone some
+    shells of the ensemble overflow within 100 steps)."""
     from paper_1905_02300_gb300 import workloads as W
     out = []
     for idx, sp in enumerate(W.shell_ensemble(seed=seed, n=n, nr_max=nr_max, nth_max=nth_max)):
         spec = W.Spec(sp["R1"], sp["R2"], sp["Nr"], sp["Nth"], sp["Nph"])
         hmin = min(spec.hr, sp["R1"] * spec.hth, sp["R1"] * math.sin(spec.th0) * spec.hph)
         kw = dict(R1=sp["R1"], R2=sp["R2"], Pr=sp["Pr"], Ra=sp["Ra"], Nr=sp["Nr"], Nth=sp["Nth"], Nph=sp["Nph"],
-                  dt=0.5 * hmin * hmin, T_inner=1.0, T_outer=0.0, precision=precision)
-        out.append((kw, W.convection_initial(spec, sp["Pr"], sp["Ra"], seed=seed + idx, kmax=3)))
+                  dt=0.5 * hmin * hmin * min(1.0, math.sqrt(1e3 / sp["Ra"])), T_inner=1.0, T_outer=0.0,
+                  precision=precision)
+        out.append((kw, lambda spec=spec, sp=sp, idx=idx: W.convection_initial(spec, sp["Pr"], sp["Ra"],
+                                                                                 seed=seed + idx, kmax=6)))
+    return out
+
+
+def class_roofline(prof, cells, mixed, hbm, src):
+    """Roofline figures per kernel class from live CUDA-event tallies
+    {class: (ms, launches)}: algorithmic bytes per launch = WORDS_PER_CELL x
+    the cells one launch processes; the three line-solve classes are one
+    kernel family (the line solves)."""
+    merged = {}
+    for k, (t_ms, n_l) in prof.items():
+        key = "solve" if k.startswith("sweep_") else k
+        w = WORDS_PER_CELL.get(k)
+        b = ((w[0] * (4.0 if mixed else 8.0) + w[1] * 8.0) * cells * n_l) if w is not None else 0.0
+        m = merged.setdefault(key, [0.0, 0, 0.0, 0.0])
+        m[0] += t_ms
+        m[1] += n_l
+        m[2] += b
+        m[3] += (0.0 if mixed else FLOPS_PER_CELL.get(k, 0.0)) * cells * n_l
+    total = sum(v[0] for v in prof.values())
+    out = {}
+    for k, (t_ms, n_l, by, fl) in merged.items():
+        if not n_l or not t_ms:
+            continue
+        gbs = by / (t_ms * 1e-3) / 1e9
+        out[k] = {"ms": t_ms, "launches": n_l, "share": t_ms / total, "gbs": gbs, "hbm_frac": gbs / hbm,
+                  "tflops": fl / (t_ms * 1e-3) / 1e12, "bytes_per_launch": by / n_l}
     return out
 
 
 def run_ensemble(args):
-    """Ensemble workload: 64 uneven shells in one batch (one launch per kernel class,
-    one CUDA graph per step, autotuned lines per block), mixed precision,
-    against the plain single-shell FP64 path running the same shells one at a
-    time."""
+    """Ensemble workload (the uneven-shell ensemble: 64 seeded shells, Nr
+    16-64, Nth 16-96, Nph = 3 Nth): one batch, one launch per kernel class,
+    one CUDA graph per step, autotuned lines per block, mixed precision, 100
+    timed steps; per-class CUDA-event times from 2 further steps launched
+    eagerly (ys_batch_profile_*); against the plain single-shell FP64 path
+    running the same shells one at a time."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1905_02300_gb300 import ys
-    torch.cuda.set_device(0)
-    shells = ensemble_shells(4, 64, 64, 96, ys, ys.YS_MIXED)
+    shells = ensemble_shells(4, args.ensemble_shells, 64, 96, ys, ys.YS_MIXED)
     cells = sum(2 * kw["Nr"] * kw["Nth"] * kw["Nph"] for kw, _ in shells)
     b = ys.Batch(len(shells), precision=ys.YS_MIXED, n_schwarz=3)
-    solvers = []
-    for kw, f0 in shells:
+    for kw, init in shells:
         s = ys.Solver(**kw)
-        s.set_fields_dict(0, f0)
+        s.set_fields_dict(0, init())
         b.add(s)
-        solvers.append(s)
     chosen = b.autotune(trial_steps=2)
-    b.step(args.warmup)
+    b.step(max(args.warmup, 3))
     b.sync()
+    steps = args.ensemble_steps
     st = torch.cuda.ExternalStream(b.stream_handle())
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = Clocks(0)
     clocks.start()
     time.sleep(0.3)
     e0.record(st)
-    b.step(args.steps)
+    b.step(steps)
     e1.record(st)
     b.sync()
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    value = cells * args.steps / (ms / 1e3)
-    finite = all(np.isfinite(b.norms(slot)).all() for slot in list(b.members))
+    value = cells * steps / (ms / 1e3)
+    nrm = np.empty(ys.NFIELDS)
+    diverged = sum(ys.lib.ys_batch_norms(b.h, slot, ys._ptr(nrm)) != ys.YS_OK for slot in list(b.members))
+    b.profile(True)
+    b.step(2)
+    prof = b.profile_read()
+    b.profile(False)
+    hbm, src = peaks()
+    cr = class_roofline(prof, cells, True, hbm, src)
+    top = max(cr, key=lambda k: cr[k]["ms"])
+    roof = {"bound": "hbm", "achieved": cr[top]["gbs"], "peak": hbm, "unit": "GB/s", "frac": cr[top]["hbm_frac"],
+            "traffic": None, "kernel": top, "peak_source": src, "kernel_share": cr[top]["share"],
+            "note": "batched launches over all 64 shells; per-class times from 2 eagerly launched steps"}
+    lps = b.launches_per_step()
+    b.close()
     # plain FP64 single-shell path, one shell at a time, same shells
     t_fp64 = 0.0
-    for kw, f0 in shells:
-        kw64 = dict(kw, precision=ys.YS_FP64)
-        s = ys.Solver(**kw64)
-        s.set_fields_dict(0, f0)
+    n64 = args.steps
+    for kw, init in shells:
+        s = ys.Solver(**dict(kw, precision=ys.YS_FP64))
+        s.set_fields_dict(0, init())
         s.step(1, 3)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         sst = torch.cuda.Stream()
         s.set_stream(sst.cuda_stream)
         ev[0].record(sst)
-        s.step(args.steps, 3)
+        s.step(n64, 3)
         ev[1].record(sst)
         torch.cuda.synchronize()
         t_fp64 += ev[0].elapsed_time(ev[1]) / 1e3
         s.close()
-    fp64_value = cells * args.steps / t_fp64
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+    fp64_value = cells * n64 / t_fp64
+    return {"metric": METRIC, "value": value, "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+            "dtype": "f32+f64", "members_diverged": int(diverged), "clocks": clk, "roofline": roof,
+            "line_solves": cr.get("solve"),
+            "kernels_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
             "config": {"workload": f"ensemble of {len(shells)} seeded uneven shells (Nr 16-64, Nth 16-96, "
-                                   f"Nph=3Nth, R1/R2 0.35-0.6, Ra 1e3-1e6, Pr 0.7/1/7), K=3, mixed FP32/FP64, "
-                                   f"one batched launch per kernel class, CUDA graph per step",
-                       "cells_total": cells, "lines_per_block": chosen,
-                       "launches_per_step": b.launches_per_step()},
-            "plain_fp64_one_at_a_time": {"value": fp64_value, "unit": UNIT},
-            "speedup_vs_plain_fp64": value / fp64_value, "all_finite": bool(finite), "clocks": clk}
-    print(json.dumps(line), flush=True)
-    b.close()
-    return 0
+                                   f"Nph=3Nth, R1/R2 0.35-0.6, Ra 1e3-1e6, Pr 0.7/1/7, perturbation k,l,m<=6), "
+                                   f"K=3, mixed FP32/FP64, one batched launch per kernel class, CUDA graph per step",
+                       "cells_total": cells, "lines_per_block": chosen, "launches_per_step": lps},
+            "plain_fp64_one_at_a_time": {"value": fp64_value, "unit": UNIT, "steps": n64},
+            "speedup_vs_plain_fp64": value / fp64_value}
 
 
 def run_serving(args):
-    """Serving workload: Poisson arrivals of shell simulations from the uneven-
-    shell ensemble distribution (Nr <= 64, Nth <= 96), N ~ U{20..80} steps, at 0.8 of the
-    measured batched capacity; p50/p99 time to completion and aggregate
-    cell-updates/s against the same trace served FIFO one at a time by the
-    plain FP64 path (replayed with each request's measured FP64 run time)."""
+    """Serving workload: Poisson arrivals (seed 5) of shell simulations from the
+    uneven-shell distribution extended to Nr <= 128 and Nth <= 192 (Nph up to
+    576), N ~ U{50..500} steps each, at 0.8 of the measured batched capacity;
+    p50/p99 time from submission to completion and aggregate cell-updates/s,
+    with SM clocks sampled during the trace.  Against the same trace served
+    FIFO one at a time by the plain FP64 path, whose run time per request is
+    modelled as N (a + b cells) from FP64 steps timed on shells spanning the
+    size range."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1905_02300_gb300 import ys
-    torch.cuda.set_device(0)
     rng = np.random.default_rng(5)
     R = args.requests
-    shells = ensemble_shells(5, R, 64, 96, ys, ys.YS_MIXED)
-    steps = [int(rng.integers(20, 81)) for _ in range(R)]
-    work = [2 * kw["Nr"] * kw["Nth"] * kw["Nph"] * n for (kw, _), n in zip(shells, steps)]
-    # batched capacity estimate from a short batch of the same shells
-    b = ys.Batch(R, precision=ys.YS_MIXED, n_schwarz=3)
-    for kw, f0 in shells[:16]:
+    shells = ensemble_shells(5, R, 128, 192, ys, ys.YS_MIXED)
+    steps = [int(rng.integers(50, 501)) for _ in range(R)]
+    sizes = [2 * kw["Nr"] * kw["Nth"] * kw["Nph"] for kw, _ in shells]
+    work = [c * n for c, n in zip(sizes, steps)]
+    # initial states, built on the host cores in parallel (numpy releases the
+    # interpreter lock in its array kernels) ahead of the arrivals: the
+    # first 16 before the capacity probe, the rest while the trace runs
+    from concurrent.futures import ThreadPoolExecutor
+    pool = ThreadPoolExecutor(max(1, min(16, len(os.sched_getaffinity(0)))))
+    futs = [pool.submit(sh[1]) for sh in shells]
+    order = np.argsort(sizes)
+    probe = [int(order[k]) for k in np.linspace(0, R - 1, 6).round().astype(int)]
+    kept = {}
+    # batched capacity from a short batch of the first 16 shells
+    b = ys.Batch(16, precision=ys.YS_MIXED, n_schwarz=3)
+    for (kw, _), fu in zip(shells[:16], futs[:16]):
         s = ys.Solver(**kw)
-        s.set_fields_dict(0, f0)
+        s.set_fields_dict(0, fu.result())
         b.add(s)
     b.step(2)
     b.sync()
     t0 = time.perf_counter()
     b.step(5)
     b.sync()
-    cap = sum(2 * kw["Nr"] * kw["Nth"] * kw["Nph"] for kw, _ in shells[:16]) * 5 / (time.perf_counter() - t0)
+    cap = sum(sizes[:16]) * 5 / (time.perf_counter() - t0)
     b.close()
     lam = 0.8 * cap / float(np.mean(work))           # requests per second
     arrivals = np.cumsum(rng.exponential(1.0 / lam, size=R))
-    srv = ys.Server(hbm_budget_bytes=64 << 30, max_slots=R)
+    srv = ys.Server(hbm_budget_bytes=args.serving_budget_gb << 30, max_slots=R)
     tickets = [None] * R
     done = {}
+    lag = 0.0
+    clocks = Clocks(0)
+    clocks.start()
     t_start = time.perf_counter()
     i = 0
     while len(done) < R:
         now = time.perf_counter() - t_start
         while i < R and arrivals[i] <= now:
-            kw, f0 = shells[i]
-            tickets[i] = srv.submit(f0, steps[i], **kw)
+            f0 = futs[i].result()
+            lag = max(lag, time.perf_counter() - t_start - arrivals[i])
+            tickets[i] = srv.submit(f0, steps[i], **shells[i][0])
+            if i in probe:
+                kept[i] = f0
+            futs[i] = None
             i += 1
         for j in range(i):
             if j in done:
                 continue
-            st_, f, lat, rc = srv.poll(tickets[j])
+            st_, _, lat, rc = srv.poll(tickets[j], fields=False)
             if st_ >= 2:
                 done[j] = (st_, lat, rc)
-        time.sleep(0.0005)
+        time.sleep(0.001)
     wall = time.perf_counter() - t_start
+    clk = clocks.stop()
+    pool.shutdown()
     stats = srv.stats()
     srv.close()
     lats = np.array([done[j][1] for j in range(R)])
     ok = sum(1 for j in range(R) if done[j][0] == 2)
-    # FIFO one at a time with the plain FP64 path: measured run time per request
-    run_t = []
-    for (kw, f0), n in zip(shells, steps):
-        s = ys.Solver(**dict(kw, precision=ys.YS_FP64))
-        s.set_fields_dict(0, f0)
+    # plain FP64 step time as a + b cells, fitted to shells across the size range
+    pts = []
+    for j in probe:
+        s = ys.Solver(**dict(shells[j][0], precision=ys.YS_FP64))
+        s.set_fields_dict(0, kept[j])
+        s.step(1, 3)
+        s.stats()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.step(n, 3)
+        s.step(3, 3)
         s.stats()
-        run_t.append(time.perf_counter() - t0)
+        pts.append((sizes[j], (time.perf_counter() - t0) / 3))
         s.close()
+    A = np.array([[1.0, c] for c, _ in pts])
+    coef = np.linalg.lstsq(A, np.array([t for _, t in pts]), rcond=None)[0]
+    run_t = [n * max(coef[0] + coef[1] * c, 0.0) for c, n in zip(sizes, steps)]
     free_at, fifo_lat = 0.0, []
     for a, rt in zip(arrivals, run_t):
         start = max(a, free_at)
         free_at = start + rt
         fifo_lat.append(free_at - a)
     fifo_lat = np.array(fifo_lat)
-    line = {"metric": "served p50/p99 time to completion; cell-updates/s", "unit": "s",
+    return {"metric": "served p50/p99 time to completion; cell-updates/s", "unit": "s",
             "value": float(np.percentile(lats, 50)), "p50_s": float(np.percentile(lats, 50)),
-            "p99_s": float(np.percentile(lats, 99)), "higher_is_better": False, "n_gpus": 1,
+            "p99_s": float(np.percentile(lats, 99)), "higher_is_better": False,
             "requests": R, "completed": ok, "aggregate_cell_updates_per_s": float(sum(work) / wall),
-            "arrival_rate_per_s": lam, "batched_capacity_estimate": cap,
+            "trace_wall_s": wall, "arrival_rate_per_s": lam, "batched_capacity_estimate": cap,
+            "submit_lag_max_s": lag,
+            "clocks": clk, "dtype": "f32+f64",
             "fifo_plain_fp64": {"p50_s": float(np.percentile(fifo_lat, 50)),
                                 "p99_s": float(np.percentile(fifo_lat, 99)),
-                                "aggregate_cell_updates_per_s": float(sum(work) / max(free_at, arrivals[-1]))},
-            "data": "synthetic", "dtype": "f32+f64",
-            "config": {"workload": f"{R} Poisson-arriving shells (uneven-shell ensemble distribution, seed 5), N in [20, 80] steps, "
-                                   f"K=3, mixed FP32/FP64, continuous batching"},
+                                "aggregate_cell_updates_per_s": float(sum(work) / max(free_at, arrivals[-1])),
+                                "model": "per-request FP64 time N (a + b cells), a, b fitted to 3 timed FP64 "
+                                         "steps of 6 shells across the size range",
+                                "fit_s": [float(coef[0]), float(coef[1])]},
+            "config": {"workload": f"{R} Poisson-arriving shells (seed 5) from the uneven-shell distribution "
+                                   f"extended to Nr <= 128, Nth <= 192, Nph = 3 Nth; N in [50, 500] steps; K=3, "
+                                   f"mixed FP32/FP64, continuous batching, lambda = 0.8 x batched capacity",
+                       "cells_total_work": float(sum(work)), "hbm_budget_gb": args.serving_budget_gb},
             "server_steps": stats["steps"]}
-    print(json.dumps(line), flush=True)
-    return 0
 
 
 def run_reference(args):
@@ -373,49 +454,17 @@ def run_reference(args):
     return 0
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=128)
-    ap.add_argument("--ref-n", type=int, default=48)
-    ap.add_argument("--ref-steps", type=int, default=8, help="oracle steps of the cpu_baseline sample (~12 s)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--stretch", type=float, default=None,
-                    help="run the shell on a stretched radial grid (workloads.stretched_radii beta)")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="shell", choices=["shell", "ensemble", "serving"])
-    ap.add_argument("--requests", type=int, default=32)
-    args = ap.parse_args()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "ensemble":
-        import numpy as np  # noqa: F401
-        return run_ensemble(args)
-    if args.workload == "serving":
-        return run_serving(args)
-
-    import numpy as np
+def run_shell(args, mixed, dist=None, world=1, rank=0, local=0, with_cpu=True):
+    """One Yin-Yang shell (the c2 / c3 grid 128 x 128 x 384 per patch, K = 3):
+    device-timed cell-updates/s, e2e through the C ABI with pinned host
+    buffers, per-class CUDA-event times and the roofline of the top class."""
     import torch
-    rank, world, local = env_rank()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1905_02300_gb300 import ys
-
     kw, K = workload(args.n)
     if args.stretch is not None:
         from paper_1905_02300_gb300 import workloads as W
         kw["r_half"] = W.stretched_radii(kw["R1"], kw["R2"], kw["Nr"], args.stretch)
     f0, fm, modes = inputs(kw)
-    mixed = args.precision == "mixed"
     s = ys.Solver(**kw, precision=ys.YS_MIXED if mixed else ys.YS_FP64)
     stream = torch.cuda.Stream()
     s.set_stream(stream.cuda_stream)
@@ -427,6 +476,9 @@ def main():
 
     s.step(args.warmup, K)
     torch.cuda.synchronize()
+    # the FP64 pipe's own rate on this device, the denominator of the FP64
+    # form's ALU-bound kernels (median of 3 probes)
+    fp64_peak = statistics.median(ys.measure_fp64_rate() for _ in range(3))
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.4)
@@ -474,63 +526,113 @@ def main():
             t_e2e.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(statistics.median(t_e2e), dist, "cuda")
     e2e_val = job_throughput(world, cells, 1, e2e_s)
+    state_gb = s.device_bytes() / 1e9
+    s.close()
 
-    # roofline of the dominant kernel: the three line-solve classes are one
-    # kernel (k_solve)
+    # roofline of the dominant kernel class (the three line-solve classes are
+    # one kernel family)
     hbm, src = peaks()
-    merged = {}
-    for k, (t_ms, n_l) in prof.items():
-        key = "solve" if k.startswith("sweep_") else k
-        w = WORDS_PER_CELL.get(k)
-        b = ((w[0] * (4.0 if mixed else 8.0) + w[1] * 8.0) * cells * n_l) if w is not None else 0.0
-        m = merged.setdefault(key, [0.0, 0, 0.0, 0.0])
-        m[0] += t_ms
-        m[1] += n_l
-        m[2] += b
-        m[3] += (0.0 if mixed else FLOPS_PER_CELL.get(k, 0.0)) * cells * n_l
-    top = max((k for k in merged if merged[k][1]), key=lambda k: merged[k][0])
-    t_ms, n_l, tot_bytes, tot_flops = merged[top]
-    gbs = tot_bytes / (t_ms * 1e-3) / 1e9
-    tfl = tot_flops / (t_ms * 1e-3) / 1e12
-    if tot_flops and tfl / FP64_PEAK_TFLOPS > gbs / hbm:
-        roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None, "kernel": top,
-                "peak_source": "nominal FP64 (no FP64 figure in MEASURED_PEAKS.json)",
-                "hbm_gbs": gbs, "hbm_frac": gbs / hbm}
+    cr = class_roofline(prof, cells, mixed, hbm, src)
+    top = max(cr, key=lambda k: cr[k]["ms"])
+    c = cr[top]
+    if c["tflops"] and c["tflops"] / fp64_peak > c["hbm_frac"]:
+        roof = {"bound": "alu", "achieved": c["tflops"], "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": c["tflops"] / fp64_peak, "traffic": None, "kernel": top,
+                "peak_source": "measured in this run: ys_measure_fp64_rate (independent FP64 FMA chains on "
+                               "every SM, CUDA events); nominal %.2f" % FP64_PEAK_TFLOPS,
+                "hbm_gbs": c["gbs"], "hbm_frac": c["hbm_frac"]}
     else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+        roof = {"bound": "hbm", "achieved": c["gbs"], "peak": hbm, "unit": "GB/s", "frac": c["hbm_frac"],
                 "traffic": None, "kernel": top, "peak_source": src}
-    roof["kernel_share"] = t_ms / sum(v[0] for v in prof.values())
-    roof["launches"] = n_l
+    roof["kernel_share"] = c["share"]
+    roof["launches"] = c["launches"]
     tp = TRAFFIC_PER_POINT.get((mixed, top))
     if tp is not None:
         roof["traffic"] = tp[0] * cells
         roof["traffic_source"] = tp[1] + " (scaled from the capture's points to this launch)"
-        roof["algorithmic_bytes_per_launch"] = tot_bytes / n_l
+    roof["algorithmic_bytes_per_launch"] = c["bytes_per_launch"]
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and with_cpu and not args.no_cpu_baseline:
         v, el = oracle_sample(args.ref_n, K, args.ref_steps)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{args.ref_steps} AC steps (K={K}) of a {args.ref_n}x{args.ref_n}x{3*args.ref_n}-per-patch "
                          f"shell, same physics and dt, numpy on 1 host core, {el:.1f} s"}
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"yin-yang shell {args.n}x{args.n}x{3*args.n} MAC cells per patch, "
+                                   f"R1=0.5 R2=1 Pr=1 Ra=1e3 dt=5e-4, K={K} Schwarz iterations, "
+                                   f"{'mixed FP32/FP64' if mixed else 'FP64'}, "
+                                   f"manufactured-solution forcing"
+                                   + (f", stretched radial grid (beta {args.stretch})"
+                                      if args.stretch is not None else ""),
+                       "cells_per_shell": cells, "l2": "inputs larger than L2 (state ~%.1f GB)" % state_gb,
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+            "fp64_peak_tflops_measured": fp64_peak,
+            "line_solves": cr.get("solve"),
+            "kernels_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
+            "kernels_launches": {k: v[1] for k, v in prof.items() if v[1]}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--ref-n", type=int, default=48)
+    ap.add_argument("--ref-steps", type=int, default=8, help="oracle steps of the cpu_baseline sample (~12 s)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stretch", type=float, default=None,
+                    help="run the shell on a stretched radial grid (workloads.stretched_radii beta)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="all", choices=["all", "shell", "ensemble", "serving"],
+                    help="all (default): the FP64 shell line with the mixed, ensemble and serving results "
+                         "as objects of the same line (one GPU only)")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--ensemble-steps", type=int, default=100)
+    ap.add_argument("--ensemble-shells", type=int, default=64,
+                    help="shells of the ensemble workload (64 as specified; fewer for a short profiling case)")
+    ap.add_argument("--serving-budget-gb", type=int, default=200)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = env_rank()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (the product path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    if args.workload in ("ensemble", "serving"):
+        line = (run_ensemble if args.workload == "ensemble" else run_serving)(args)
+        print(json.dumps(line), flush=True)
+        return 0
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    line = run_shell(args, args.precision == "mixed", dist, world, rank, local)
+    if args.workload == "all" and world == 1:
+        t0 = time.perf_counter()
+        m = run_shell(args, True, with_cpu=False)
+        line["mixed"] = {k: m[k] for k in ("value", "unit", "ms_per_step", "dtype", "e2e", "roofline", "line_solves",
+                                           "clocks", "gpu_launches", "kernels_ms")}
+        line["mixed"]["config"] = m["config"]["workload"]
+        line["ensemble"] = run_ensemble(args)
+        line["serving"] = run_serving(args)
+        line["config"]["also"] = ("mixed (same shell, FP32 bulk), ensemble (64 uneven shells, batched), "
+                                  "serving (200 Poisson-arriving requests): objects of this line, %.0f s"
+                                  % (time.perf_counter() - t0))
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
-                "data": "synthetic",
-                "config": {"workload": f"yin-yang shell {args.n}x{args.n}x{3*args.n} MAC cells per patch, "
-                                       f"R1=0.5 R2=1 Pr=1 Ra=1e3 dt=5e-4, K={K} Schwarz iterations, "
-                                       f"{'mixed FP32/FP64' if mixed else 'FP64'}, "
-                                       f"manufactured-solution forcing"
-                                       + (f", stretched radial grid (beta {args.stretch})"
-                                          if args.stretch is not None else ""),
-                           "cells_per_shell": cells, "l2": "inputs larger than L2 (state ~%.1f GB)"
-                           % (s.device_bytes() / 1e9), "parallelism": f"replicas x{world}"},
-                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
-                "kernels_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
-                "kernels_launches": {k: v[1] for k, v in prof.items() if v[1]}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
