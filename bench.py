@@ -284,7 +284,7 @@ def run_ensemble(args):
     top = max(cr, key=lambda k: cr[k]["ms"])
     roof = {"bound": "hbm", "achieved": cr[top]["gbs"], "peak": hbm, "unit": "GB/s", "frac": cr[top]["hbm_frac"],
             "traffic": None, "kernel": top, "peak_source": src, "kernel_share": cr[top]["share"],
-            "note": "batched launches over all 64 shells; per-class times from 2 eagerly launched steps"}
+            "note": f"batched launches over all {len(shells)} shells; per-class times from 2 eagerly launched steps"}
     lps = b.launches_per_step()
     b.close()
     # plain FP64 single-shell path, one shell at a time, same shells

@@ -55,7 +55,8 @@ enum MapId {
   M_EXTRAP = 0, M_EX0, M_EX1, M_EX2, M_EX3, M_WALLS, M_RING, M_RC, M_RR, M_RT, M_RP, M_LINE0,
   M_PSC0 = M_LINE0 + 12,   // warp-scan phi factorisations and solves (one line per warp), per unknown type
   M_VEC0 = M_PSC0 + 4,     // FP32 residuals, 4 phi-points per thread over flat groups, per unknown type
-  M_NUM = M_VEC0 + 4
+  M_PRES = M_VEC0 + 4,     // pressure updates over each shell's cells taken as one flat range
+  M_NUM = M_PRES + 1
 };
 
 namespace {
@@ -102,6 +103,17 @@ __device__ __forceinline__ StepAux<R> aux_of(const ShellDev<R> &D) {
     State<R> n, nm1, it;                                     \
     roles(D, n, nm1, it);
 
+// the same loop for kernels that need only the iterate's fields
+#define YS_BATCH_LOOP_IT(map, cap)                            \
+  const int total_w = (map).offs[cap];                       \
+  for (int w = blockIdx.x; w < total_w; w += gridDim.x) {    \
+    const int s = find_shell((map).offs, cap, w);            \
+    const int local = w - (map).offs[s];                     \
+    const int gxs = (map).gx[s];                             \
+    const int bx = local % gxs, by = local / gxs;            \
+    const ShellDev<R> &D = sh[s];                            \
+    R *const *itf = D.lev[(D.rot + 2) % 3].f;
+
 template <typename R>
 __global__ void kb_extrapolate(const ShellDev<R> *sh, WorkMap map, int cap) {
   YS_BATCH_LOOP(map, cap)
@@ -122,9 +134,9 @@ __global__ void kb_factorize(const ShellDev<R> *sh, WorkMap map, int cap, int lo
 
 template <typename R>
 __global__ void kb_solve(const ShellDev<R> *sh, WorkMap map, int cap, int loc, int dir, int final, int slot) {
-  YS_BATCH_LOOP(map, cap)
+  YS_BATCH_LOOP_IT(map, cap)
   R *const *F = D.fac[loc][dir];
-  bd::body_solve(D.S, loc, dir, final, F[0], F[1], F[2], D.B, D.W, it.f[slot], D.norm, slot, 3, bx, by);
+  bd::body_solve(D.S, loc, dir, final, F[0], F[1], F[2], D.B, D.W, itf[slot], D.norm, slot, 3, bx, by);
   }
 }
 
@@ -199,14 +211,34 @@ __global__ void kb_resid_u(const ShellDev<R> *sh, WorkMap map, int cap, int sys,
 // the contiguous range offs[s] .. offs[s+1]); kb_norm_sum adds them up per
 // shell.  No atomics here: a CTA's successive blocks belong to different
 // shells, and per-shell atomics from every CTA piled up on a few addresses.
-constexpr int kPresTpb = 128;
+// A block is kPresPts x kPresTpb consecutive cells of the shell's flat range
+// (phi fastest, rows one after another): short rows of small shells do not
+// leave most of a block idle, and the block's set-up (work-map search, shell
+// description) serves 4 cells a thread.
+constexpr int kPresTpb = 128, kPresPts = 4;
 template <typename R>
 __global__ void __launch_bounds__(kPresTpb) kb_pressure(const ShellDev<R> *sh, WorkMap map, int cap, int sys,
                                                         double *parts) {
   using V = typename Cmp<R>::type;
   __shared__ V ws[kPresTpb];
   YS_BATCH_LOOP(map, cap)
-  ws[threadIdx.x] = bd::body_pressure(D.S, sys, it, n, 3, bx, by);
+  (void)by;
+  const Layout &L = D.S.L;
+  const long ncell = 2L * L.Nr * L.Nt * L.Np;
+  V acc = (V)0.0;
+#pragma unroll
+  for (int u = 0; u < kPresPts; ++u) {
+    const long f = ((long)bx * kPresPts + u) * kPresTpb + threadIdx.x;
+    if (f < ncell) {
+      const int k = (int)(f % L.Np);
+      long r = f / L.Np;
+      const int j = (int)(r % L.Nt);
+      r /= L.Nt;
+      const int i = (int)(r % L.Nr), p = (int)(r / L.Nr);
+      acc += bd::body_pressure_at(D.S, sys, it, n, p, i, j, k);
+    }
+  }
+  ws[threadIdx.x] = acc;
   __syncthreads();
   if (threadIdx.x < 32) {
     V v = ws[threadIdx.x];
@@ -283,6 +315,8 @@ void grid_of(const ys_ctx *c, int map, int tpb_line, int &gx, int &gy) {
     int ni = L.Nr - (loc == LR), nj = L.Nt - (loc == LT), nk = L.Np - (loc == LP);
     gx = cdiv(nk, 128);
     gy = 2 * ni * nj;
+  } else if (map == M_PRES) {
+    gx = cdiv(2L * L.Nr * L.Nt * L.Np, (long)kPresTpb * kPresPts);
   } else if (map >= M_VEC0) {
     int loc = map - M_VEC0;
     int ni = L.Nr - (loc == LR), nj = L.Nt - (loc == LT);
@@ -430,7 +464,7 @@ int upload(ys_batch *b) {
   }
   // per-block pressure norm shares: grow the buffer to the pressure map's
   // blocks; the captured graph holds the old pointer, so drop it
-  const long need = b->hmaps[(size_t)M_RC * (2 * cap + 1) + cap];
+  const long need = b->hmaps[(size_t)M_PRES * (2 * cap + 1) + cap];
   if (need > b->parts_n) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     cudaFree(b->parts);
@@ -572,8 +606,8 @@ void enqueue_step(ys_batch *b) {
       }
       {
         BMark m(b, B_PRES);
-        kb_pressure<R><<<g128, kPresTpb, 0, st>>>(sh, map_of(b, M_RC), cap, sys, b->parts);
-        kb_norm_sum<R><<<cap, 256, 0, st>>>(sh, map_of(b, M_RC), cap, sys == 1 ? 4 : 8, b->parts);
+        kb_pressure<R><<<g128, kPresTpb, 0, st>>>(sh, map_of(b, M_PRES), cap, sys, b->parts);
+        kb_norm_sum<R><<<cap, 256, 0, st>>>(sh, map_of(b, M_PRES), cap, sys == 1 ? 4 : 8, b->parts);
       }
       nl += 2;
     }

@@ -808,12 +808,10 @@ __device__ __forceinline__ void body_resid_up_vec(Shell S, int sys, State<R> it,
 // caller accumulates shares over many cells, so that one atomic serves many
 // thousands of cells.
 template <typename R>
-__device__ __forceinline__ typename Cmp<R>::type body_pressure(Shell S, int sys, State<R> it, State<R> n,
-                                                               int patch_mask, int bx, int by) {
+__device__ __forceinline__ typename Cmp<R>::type body_pressure_at(Shell S, int sys, State<R> it, State<R> n,
+                                                                  int p, int i, int j, int k) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
-  int p, i, j, k;
-  if (!decode_point(L, LC, patch_mask, bx, by, p, i, j, k)) return (V)0.0;
   const long q = lidx(L, p, i, j, k);
   double D;
   if constexpr (sizeof(R) == sizeof(float)) {
@@ -845,6 +843,15 @@ __device__ __forceinline__ typename Cmp<R>::type body_pressure(Shell S, int sys,
   const bool ringcell = (j == 0 || j == L.Nt - 1 || k == 0 || k == L.Np - 1);
   if (S.step7 && ringcell) return (V)0.0;
   return rowc<V>(S, RT_DIV, i, j)[DV_W] * c * c;
+}
+
+// the pressure update of the cell of (bx, by) in a row-per-block grid
+template <typename R>
+__device__ __forceinline__ typename Cmp<R>::type body_pressure(Shell S, int sys, State<R> it, State<R> n,
+                                                               int patch_mask, int bx, int by) {
+  int p, i, j, k;
+  if (!decode_point(S.L, LC, patch_mask, bx, by, p, i, j, k)) return (typename Cmp<R>::type)0.0;
+  return body_pressure_at(S, sys, it, n, p, i, j, k);
 }
 
 // Warp sum of per-thread norm shares, scaled once and added to *dst by lane 0.
