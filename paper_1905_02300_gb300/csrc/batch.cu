@@ -4,7 +4,8 @@
 // kernel class of the AC step (Sec. 3.3, Sec. 4) is ONE persistent launch over
 // all member shells.  Each launch walks a work map kept in device memory: per
 // shell, the prefix sum of its block count and its grid width, so a CTA finds
-// the shell and block it executes by binary search.  Time-level rotation is a
+// the shell and block it executes by binary search (only when its next block
+// lies past the current shell's range: a CTA's blocks ascend).  Time-level rotation is a
 // device kernel, so one step, captured once as a CUDA graph, stays valid while
 // shells join and leave (only the device-resident maps and descriptors change).
 // Per-shell arithmetic and block decomposition do not depend on the other
@@ -94,6 +95,27 @@ __device__ __forceinline__ StepAux<R> aux_of(const ShellDev<R> &D) {
 
 #define YS_BATCH_LOOP(map, cap)                               \
   const int total_w = (map).offs[cap];                       \
+  int s_at = 0, s_beg = 0, s_end = 0, s_gx = 1;              \
+  for (int w = blockIdx.x; w < total_w; w += gridDim.x) {    \
+    if (w >= s_end) {                                        \
+      s_at = find_shell((map).offs, cap, w);                 \
+      s_beg = (map).offs[s_at];                              \
+      s_end = (map).offs[s_at + 1];                          \
+      s_gx = (map).gx[s_at];                                 \
+    }                                                        \
+    const int s = s_at;                                      \
+    const int local = w - s_beg;                             \
+    const int gxs = s_gx;                                    \
+    const int bx = local % gxs, by = local / gxs;            \
+    const ShellDev<R> &D = sh[s];                            \
+    State<R> n, nm1, it;                                     \
+    roles(D, n, nm1, it);
+
+// the loop with a binary search for every block, for kernels at their
+// register cap (the loop-carried shell range of YS_BATCH_LOOP made the
+// velocity residuals spill more and run 7% slower)
+#define YS_BATCH_LOOP_BS(map, cap)                            \
+  const int total_w = (map).offs[cap];                       \
   for (int w = blockIdx.x; w < total_w; w += gridDim.x) {    \
     const int s = find_shell((map).offs, cap, w);            \
     const int local = w - (map).offs[s];                     \
@@ -106,10 +128,17 @@ __device__ __forceinline__ StepAux<R> aux_of(const ShellDev<R> &D) {
 // the same loop for kernels that need only the iterate's fields
 #define YS_BATCH_LOOP_IT(map, cap)                            \
   const int total_w = (map).offs[cap];                       \
+  int s_at = 0, s_beg = 0, s_end = 0, s_gx = 1;              \
   for (int w = blockIdx.x; w < total_w; w += gridDim.x) {    \
-    const int s = find_shell((map).offs, cap, w);            \
-    const int local = w - (map).offs[s];                     \
-    const int gxs = (map).gx[s];                             \
+    if (w >= s_end) {                                        \
+      s_at = find_shell((map).offs, cap, w);                 \
+      s_beg = (map).offs[s_at];                              \
+      s_end = (map).offs[s_at + 1];                          \
+      s_gx = (map).gx[s_at];                                 \
+    }                                                        \
+    const int s = s_at;                                      \
+    const int local = w - s_beg;                             \
+    const int gxs = s_gx;                                    \
     const int bx = local % gxs, by = local / gxs;            \
     const ShellDev<R> &D = sh[s];                            \
     R *const *itf = D.lev[(D.rot + 2) % 3].f;
@@ -184,7 +213,7 @@ __global__ void __launch_bounds__(128, 4) kb_resid_T_vec(const ShellDev<R> *sh, 
 template <typename R>
 __global__ void __launch_bounds__(128, 4)
     kb_resid_u_vec(const ShellDev<R> *sh, WorkMap map, int cap, int sys, int comp) {
-  YS_BATCH_LOOP(map, cap)
+  YS_BATCH_LOOP_BS(map, cap)
   if (comp == 0)
     bd::body_resid_ur_vec<R, kVecNV, false, true>(D.S, sys, it, n, aux_of(D), D.B, 3, bx, by);
   else if (comp == 1)
@@ -224,17 +253,21 @@ __global__ void __launch_bounds__(kPresTpb) kb_pressure(const ShellDev<R> *sh, W
   YS_BATCH_LOOP(map, cap)
   (void)by;
   const Layout &L = D.S.L;
-  const long ncell = 2L * L.Nr * L.Nt * L.Np;
+  // 32-bit index arithmetic (a 64-bit division per index took more issue
+  // slots than the update itself): a shell's cells number below 2^32, since
+  // 2^32 cells of state would need more than a terabyte
+  const unsigned ncell = 2u * L.Nr * L.Nt * L.Np;
+  const unsigned np = L.Np, nt = L.Nt, nr = L.Nr;
   V acc = (V)0.0;
 #pragma unroll
   for (int u = 0; u < kPresPts; ++u) {
-    const long f = ((long)bx * kPresPts + u) * kPresTpb + threadIdx.x;
+    const unsigned f = ((unsigned)bx * kPresPts + u) * kPresTpb + threadIdx.x;
     if (f < ncell) {
-      const int k = (int)(f % L.Np);
-      long r = f / L.Np;
-      const int j = (int)(r % L.Nt);
-      r /= L.Nt;
-      const int i = (int)(r % L.Nr), p = (int)(r / L.Nr);
+      const int k = (int)(f % np);
+      unsigned r = f / np;
+      const int j = (int)(r % nt);
+      r /= nt;
+      const int i = (int)(r % nr), p = (int)(r / nr);
       acc += bd::body_pressure_at(D.S, sys, it, n, p, i, j, k);
     }
   }
@@ -384,6 +417,12 @@ struct ys_batch {
   std::vector<int> hmaps;
   cudaGraphExec_t exec = nullptr;
   bool dirty = true;              // maps / descriptors need upload
+  // phi scans: shared-memory positions per warp, bytes per CTA, and the
+  // persistent grids (as many CTAs as the SMs hold at once), set before a
+  // step is captured or launched eagerly (phi_grids)
+  int spw = 0;
+  size_t spw_bytes = 0;
+  int gp_solve = 0, gp_fact = 0;
   long launches = 0;
   // kernel-class timing (ys_batch_profile_*): profiled steps are launched
   // eagerly with an event pair around each launch instead of replaying the graph
@@ -520,6 +559,40 @@ struct BMark {
   }
 };
 
+// CTAs of a persistent launch: as many as the SMs hold at once (at most 8 a
+// SM; 4 a SM if the occupancy query fails)
+template <typename K>
+int resident_grid(K kernel, int threads, size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess || nb < 1) {
+    cudaGetLastError();
+    nb = 4;
+  }
+  return 152 * (nb > 8 ? 8 : nb);
+}
+
+// Shared memory and grids of the phi scans for the current members: the
+// longest line of the batch that fits the per-warp buffer (shells with longer
+// lines keep their forward results in W).  Called outside stream capture.
+template <typename R>
+void phi_grids(ys_batch *b) {
+  static std::atomic<unsigned long long> attr_done{0};
+  smem_attr_once(attr_done, kb_solve_phi<R>, bd::kScanSmemMax);
+  int spw = 0;
+  for (int s = 0; s < b->cap; ++s) {
+    if (!b->slot[s]) continue;
+    const int pad = bd::scan_pad(b->slot[s]->L.Np);
+    if (pad > spw && (size_t)bd::kScanWarps * pad * sizeof(R) <= (size_t)bd::kScanSmemMax) spw = pad;
+  }
+  const size_t bytes = (size_t)bd::kScanWarps * spw * sizeof(R);
+  if (b->gp_solve == 0 || bytes != b->spw_bytes) {
+    b->gp_solve = resident_grid(kb_solve_phi<R>, 32 * bd::kScanWarps, bytes);
+    b->gp_fact = resident_grid(kb_factorize_phi<R>, 32 * bd::kScanWarps, 0);
+  }
+  b->spw = spw;
+  b->spw_bytes = bytes;
+}
+
 // one AC step of every member shell (additive Schwarz, K iterations)
 template <typename R>
 void enqueue_step(ys_batch *b) {
@@ -528,18 +601,8 @@ void enqueue_step(ys_batch *b) {
   cudaStream_t st = b->stream;
   const int g128 = grid_size(128), g256 = grid_size(256), gl = grid_size(b->tpb_line);
   long nl = 0;
-  static std::atomic<unsigned long long> attr_done{0};
-  smem_attr_once(attr_done, kb_solve_phi<R>, bd::kScanSmemMax);
-  // shared-memory positions per warp of the phi solves: the longest line of the
-  // batch that fits; shells with longer lines keep their forward results in W
-  int spw = 0;
-  for (int s = 0; s < cap; ++s) {
-    if (!b->slot[s]) continue;
-    const int pad = bd::scan_pad(b->slot[s]->L.Np);
-    if (pad > spw && (size_t)bd::kScanWarps * pad * sizeof(R) <= (size_t)bd::kScanSmemMax) spw = pad;
-  }
-  const size_t spw_bytes = (size_t)bd::kScanWarps * spw * sizeof(R);
-  const int gp = 152 * 4;
+  const int spw = b->spw, gp = b->gp_solve, gpf = b->gp_fact;
+  const size_t spw_bytes = b->spw_bytes;
   {
     BMark m(b, B_EXTRAP);
     kb_extrapolate<R><<<g256, 256, 0, st>>>(sh, map_of(b, M_EXTRAP), cap);
@@ -549,7 +612,7 @@ void enqueue_step(ys_batch *b) {
     for (int dir = DR; dir <= DP; ++dir) {
       BMark m(b, B_FACTOR);
       if (dir == DP && bd::use_phi_scan<R>())
-        kb_factorize_phi<R><<<gp, 32 * bd::kScanWarps, 0, st>>>(sh, map_of(b, M_PSC0 + loc), cap, loc);
+        kb_factorize_phi<R><<<gpf, 32 * bd::kScanWarps, 0, st>>>(sh, map_of(b, M_PSC0 + loc), cap, loc);
       else
         kb_factorize<R><<<gl, b->tpb_line, 0, st>>>(sh, map_of(b, M_LINE0 + 3 * loc + dir), cap, loc, dir);
       ++nl;
@@ -657,9 +720,11 @@ int batch_step(ys_batch *b, int n) {
   }
   if (b->prof_on) {
     // profiled steps: the same launches, eagerly, with events around each
+    phi_grids<R>(b);
     for (int i = 0; i < n; ++i) enqueue_step<R>(b);
   } else {
     if (!b->exec) {
+      phi_grids<R>(b);
       int rc = capture<R>(b);
       if (rc) return rc;
     }

@@ -1518,13 +1518,14 @@ __device__ __forceinline__ void body_solve_phi_scan(Shell S, int loc, int final,
   const int warp = threadIdx.x >> 5;
   const int i0 = (loc == LR) ? 1 : 0, j0 = (loc == LT) ? 1 : 0, k0 = (loc == LP) ? 1 : 0;
   const int ni = L.Nr - i0, nj = L.Nt - j0;
-  const long line = (long)bx * kScanWarps + warp;
+  // 32-bit index arithmetic: a shell's lines number far below 2^31
+  const int line = bx * kScanWarps + warp;
   V acc = (V)0.0;
   double scale = 0.0;
-  if (line < 2L * ni * nj) {
-    const int j = j0 + (int)(line % nj);
-    const long rest = line / nj;
-    const int i = i0 + (int)(rest % ni), p = (int)(rest / ni);
+  if (line < 2 * ni * nj) {
+    const int j = j0 + line % nj;
+    const int rest = line / nj;
+    const int i = i0 + rest % ni, p = rest / ni;
     if ((patch_mask >> p) & 1) {
       const long q = lidx(L, p, i, j, 0);
       R *wbuf = (scan_pad(L.Np) <= smem_per_warp) ? smem + (long)warp * smem_per_warp : W + q;
@@ -1684,11 +1685,11 @@ __device__ __forceinline__ void body_factorize_phi_scan(Shell S, int loc, StepAu
   const int warp = threadIdx.x >> 5;
   const int i0 = (loc == LR) ? 1 : 0, j0 = (loc == LT) ? 1 : 0, k0 = (loc == LP) ? 1 : 0;
   const int ni = L.Nr - i0, nj = L.Nt - j0;
-  const long line = (long)bx * kScanWarps + warp;
-  if (line >= 2L * ni * nj) return;
-  const int j = j0 + (int)(line % nj);
-  const long rest = line / nj;
-  const int i = i0 + (int)(rest % ni), p = (int)(rest / ni);
+  const int line = bx * kScanWarps + warp;
+  if (line >= 2 * ni * nj) return;
+  const int j = j0 + line % nj;
+  const int rest = line / nj;
+  const int i = i0 + rest % ni, p = rest / ni;
   if (!((patch_mask >> p) & 1)) return;
   const long q = lidx(L, p, i, j, 0);
   switch (scan_ec(L.Np)) {
