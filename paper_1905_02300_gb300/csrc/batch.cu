@@ -57,7 +57,8 @@ enum MapId {
   M_PSC0 = M_LINE0 + 12,   // warp-scan phi factorisations and solves (one line per warp), per unknown type
   M_VEC0 = M_PSC0 + 4,     // FP32 residuals, 4 phi-points per thread over flat groups, per unknown type
   M_PRES = M_VEC0 + 4,     // pressure updates over each shell's cells taken as one flat range
-  M_NUM = M_PRES + 1
+  M_FAC0 = M_PRES + 1,     // line factorisations (r, theta; phi in FP64), kFacTpb lines per block
+  M_NUM = M_FAC0 + 12
 };
 
 namespace {
@@ -326,10 +327,19 @@ __global__ void kb_rotate(ShellDev<R> *sh, const int *active, int cap) {
 
 int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 
+// Lines per block of the batched line factorisations.  They keep their own
+// width: the autotuned width of the solves (often 32 lines, best for the
+// 128-register solves) made them 27% slower than 128 lines a block.
+constexpr int kFacTpb = 128;
+
 // per-shell block grid (gx, gy) of a map
 void grid_of(const ys_ctx *c, int map, int tpb_line, int &gx, int &gy) {
   const Layout &L = c->L;
   gy = 1;
+  if (map >= M_FAC0) {
+    map = M_LINE0 + (map - M_FAC0);
+    tpb_line = kFacTpb;
+  }
   if (map == M_EXTRAP) {
     gx = cdiv(L.total, kExtrapChunk);
   } else if (map >= M_EX0 && map <= M_EX3) {
@@ -614,7 +624,8 @@ void enqueue_step(ys_batch *b) {
       if (dir == DP && bd::use_phi_scan<R>())
         kb_factorize_phi<R><<<gpf, 32 * bd::kScanWarps, 0, st>>>(sh, map_of(b, M_PSC0 + loc), cap, loc);
       else
-        kb_factorize<R><<<gl, b->tpb_line, 0, st>>>(sh, map_of(b, M_LINE0 + 3 * loc + dir), cap, loc, dir);
+        kb_factorize<R><<<grid_size(kFacTpb), kFacTpb, 0, st>>>(sh, map_of(b, M_FAC0 + 3 * loc + dir), cap, loc,
+                                                                dir);
       ++nl;
     }
   auto solve = [&](int loc, int slot) {
