@@ -29,7 +29,7 @@ namespace {
 
 const char *kClassNames[K_NUM] = {"extrapolate", "forcing",  "exchange", "walls",   "ring",     "resid_T",
                                   "resid_u",     "sweep_r",  "sweep_t",  "sweep_p", "pressure", "pack",
-                                  "factorize",   "watch"};
+                                  "factorize",   "watch",    "sums"};
 
 }  // namespace
 
@@ -271,11 +271,19 @@ void iterate(ys_ctx *c, StepAux<R> ax, int mask) {
   State<R> &it = D.lev[2], &n = D.lev[0];
   LAUNCH(c, K_RES_T, 1, Launch<R>::resid_T(c->S, it, n, ax, D.B, mask, c->stream));
   solve_unknown<R>(c, LC, F_T, mask);
+  // FP64: the residuals read the two-level sums of the system's velocity,
+  // formed for all three components before the first residual and again for
+  // a component once its solve has changed it (the next residuals read it)
+  const bool sums = D.Sv[0] != nullptr;
+  const LevelSums<R> ls{{D.Sv[0], D.Sv[1], D.Sv[2]}};
   for (int sys = 1; sys <= 2; ++sys) {
     int o = (sys == 1) ? 0 : 4;
+    if (sums) LAUNCH(c, K_SUMS, 1, Launch<R>::sum_levels(c->L, sys, it, n, D.Sv, 7, c->stream));
     for (int comp = 0; comp < 3; ++comp) {
-      LAUNCH(c, K_RES_U, 1, Launch<R>::resid_u(c->S, sys, comp, it, n, ax, D.B, mask, c->stream));
+      LAUNCH(c, K_RES_U, 1, Launch<R>::resid_u(c->S, sys, comp, it, n, ax, D.B, mask, c->stream, ls));
       solve_unknown<R>(c, LR + comp, F_U1R + comp + o, mask);
+      if (sums && comp < 2)
+        LAUNCH(c, K_SUMS, 1, Launch<R>::sum_levels(c->L, sys, it, n, D.Sv, 1 << comp, c->stream));
     }
     LAUNCH(c, K_PRES, 2, Launch<R>::pressure(c->S, sys, it, n, c->norm, c->stage, mask, c->stream));
   }
@@ -466,6 +474,7 @@ char *carve(ys_ctx *c, Fields<R> &D, char *base) {
       for (int a = 0; a < 3; ++a) D.fac[loc][dir][a] = f + (fi++) * T;
   for (int loc = 0; loc < 4; ++loc)
     for (int dir = 0; dir < 3; ++dir) D.As[loc][dir] = (loc == dir + 1) ? nullptr : f + (fi++) * T;
+  for (int a = 0; a < 3; ++a) D.Sv[a] = (sizeof(R) == sizeof(double)) ? f + (fi++) * T : nullptr;
   for (int m = 0; m < kMaxModes; ++m)
     for (int a = 0; a < 4; ++a) D.modes[m][a] = nullptr;
   char *next = base + ((fi * T * sizeof(R) + 255) / 256) * 256;
@@ -475,8 +484,10 @@ char *carve(ys_ctx *c, Fields<R> &D, char *base) {
   return next + ((kPresFields * T * sizeof(double) + 255) / 256) * 256;
 }
 
-// number of bulk fields of one shell (3 x 7 levels, 3 a, 4 forcing, B, Cs, 36 factors, 9 sums of a)
+// number of bulk fields of one shell (3 x 7 levels, 3 a, 4 forcing, B, Cs, 36 factors, 9 sums of a),
+// and the FP64 form's 3 two-level sums of the velocity
 constexpr size_t kBulkFields = 3 * 7 + 3 + 4 + 2 + 36 + 9;
+constexpr size_t kSumFields64 = 3;
 
 // padded field layout of a shell (both patches)
 void set_layout(const ys_params *p, Layout &L) {
@@ -505,7 +516,8 @@ ShellPlan plan_shell(const Layout &L, bool mixed, size_t met_n, const size_t (&r
                      size_t xcount) {
   ShellPlan s{};
   const size_t Rsz = mixed ? sizeof(float) : sizeof(double);
-  const size_t bulk_bytes = ((kBulkFields * L.total * Rsz + 255) / 256) * 256;
+  const size_t nbulk = kBulkFields + (mixed ? 0 : kSumFields64);
+  const size_t bulk_bytes = ((nbulk * L.total * Rsz + 255) / 256) * 256;
   const size_t p_bytes = ((kPresFields * L.total * sizeof(double) + 255) / 256) * 256;
   size_t stage_elems = user_elems(L, LR);
   if (user_elems(L, LT) > stage_elems) stage_elems = user_elems(L, LT);

@@ -314,9 +314,14 @@ __device__ __forceinline__ double pres(const State<R> &it, const State<R> &n, in
 }
 
 // u_r at r-faces: nu (vector Laplacian), -advection (with the curvature
-// terms), -grad P, grad(div)/(2 chi), buoyancy, forcing
-template <typename R, bool kTab = false>
-__device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by) {
+// terms), -grad P, grad(div)/(2 chi), buoyancy, forcing.
+// kSum (the single-shell FP64 launches): the two-level sums S = psi + psi^n
+// of the system's three velocity components are read from Sv[0..2], fields
+// formed by k_sum_levels with the same addition, instead of being added here
+// at every stencil point (15 FP64 additions and 15 loads fewer a point).
+template <typename R, bool kTab = false, bool kSum = false>
+__device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by,
+                                               const R *const *Sv = nullptr) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
@@ -326,13 +331,25 @@ __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, Sta
   const R *xi = velf(it, sys, 0), *xn = velf(n, sys, 0);
   const R *yi = velf(it, sys, 1), *yn = velf(n, sys, 1);
   const R *zi = velf(it, sys, 2), *zn = velf(n, sys, 2);
-  const V S0 = Sm<V>(xi, xn, q);
-  const V Srp = Sm<V>(xi, xn, q + SI), Srm = Sm<V>(xi, xn, q - SI);
-  const V Stp = Sm<V>(xi, xn, q + P), Stm = Sm<V>(xi, xn, q - P);
-  const V Spp = Sm<V>(xi, xn, q + 1), Spm = Sm<V>(xi, xn, q - 1);
+  auto sx = [&](long qq) -> V {
+    if constexpr (kSum) return (V)Sv[0][qq];
+    else return Sm<V>(xi, xn, qq);
+  };
+  auto sy = [&](long qq) -> V {
+    if constexpr (kSum) return (V)Sv[1][qq];
+    else return Sm<V>(yi, yn, qq);
+  };
+  auto sz = [&](long qq) -> V {
+    if constexpr (kSum) return (V)Sv[2][qq];
+    else return Sm<V>(zi, zn, qq);
+  };
+  const V S0 = sx(q);
+  const V Srp = sx(q + SI), Srm = sx(q - SI);
+  const V Stp = sx(q + P), Stm = sx(q - P);
+  const V Spp = sx(q + 1), Spm = sx(q - 1);
   // u_theta and u_phi around the face: the two cells sharing it
-  const V y1 = Sm<V>(yi, yn, q + P), y0 = Sm<V>(yi, yn, q), ym1 = Sm<V>(yi, yn, q - SI + P), ym0 = Sm<V>(yi, yn, q - SI);
-  const V z1 = Sm<V>(zi, zn, q + 1), z0 = Sm<V>(zi, zn, q), zm1 = Sm<V>(zi, zn, q - SI + 1), zm0 = Sm<V>(zi, zn, q - SI);
+  const V y1 = sy(q + P), y0 = sy(q), ym1 = sy(q - SI + P), ym0 = sy(q - SI);
+  const V z1 = sz(q + 1), z0 = sz(q), zm1 = sz(q - SI + 1), zm0 = sz(q - SI);
   const R *A1 = ax.A[1], *A2 = ax.A[2];
   const V ar = (V)ax.A[0][q];
   const V sAt = kTab ? (V)ax.As[LR][DT][q] : ((V)A1[q - SI] + (V)A1[q - SI + P]) + (V)A1[q] + (V)A1[q + P];
@@ -364,8 +381,9 @@ __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, Sta
 }
 
 // u_theta at theta-faces
-template <typename R, bool kTab = false>
-__device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by) {
+template <typename R, bool kTab = false, bool kSum = false>
+__device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by,
+                                               const R *const *Sv = nullptr) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
@@ -375,13 +393,25 @@ __device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, Sta
   const R *wi = velf(it, sys, 0), *wn = velf(n, sys, 0);
   const R *xi = velf(it, sys, 1), *xn = velf(n, sys, 1);
   const R *zi = velf(it, sys, 2), *zn = velf(n, sys, 2);
-  const V S0 = Sm<V>(xi, xn, q);
-  const V Srp = Sm<V>(xi, xn, q + SI), Srm = Sm<V>(xi, xn, q - SI);
-  const V Stp = Sm<V>(xi, xn, q + P), Stm = Sm<V>(xi, xn, q - P);
-  const V Spp = Sm<V>(xi, xn, q + 1), Spm = Sm<V>(xi, xn, q - 1);
+  auto sw = [&](long qq) -> V {
+    if constexpr (kSum) return (V)Sv[0][qq];
+    else return Sm<V>(wi, wn, qq);
+  };
+  auto sx = [&](long qq) -> V {
+    if constexpr (kSum) return (V)Sv[1][qq];
+    else return Sm<V>(xi, xn, qq);
+  };
+  auto sz = [&](long qq) -> V {
+    if constexpr (kSum) return (V)Sv[2][qq];
+    else return Sm<V>(zi, zn, qq);
+  };
+  const V S0 = sx(q);
+  const V Srp = sx(q + SI), Srm = sx(q - SI);
+  const V Stp = sx(q + P), Stm = sx(q - P);
+  const V Spp = sx(q + 1), Spm = sx(q - 1);
   // u_r and u_phi around the face: the two cells sharing it
-  const V w1 = Sm<V>(wi, wn, q + SI), w0 = Sm<V>(wi, wn, q), wm1 = Sm<V>(wi, wn, q + SI - P), wm0 = Sm<V>(wi, wn, q - P);
-  const V z1 = Sm<V>(zi, zn, q + 1), z0 = Sm<V>(zi, zn, q), zm1 = Sm<V>(zi, zn, q - P + 1), zm0 = Sm<V>(zi, zn, q - P);
+  const V w1 = sw(q + SI), w0 = sw(q), wm1 = sw(q + SI - P), wm0 = sw(q - P);
+  const V z1 = sz(q + 1), z0 = sz(q), zm1 = sz(q - P + 1), zm0 = sz(q - P);
   const R *A0 = ax.A[0], *A2 = ax.A[2];
   const V sAr = kTab ? (V)ax.As[LT][DR][q] : ((V)A0[q - P] + (V)A0[q - P + SI]) + (V)A0[q] + (V)A0[q + SI];
   const V at = (V)ax.A[1][q];
@@ -411,8 +441,9 @@ __device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, Sta
 }
 
 // u_phi at phi-faces
-template <typename R, bool kTab = false>
-__device__ __forceinline__ void body_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by) {
+template <typename R, bool kTab = false, bool kSum = false>
+__device__ __forceinline__ void body_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by,
+                                               const R *const *Sv = nullptr) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
@@ -422,13 +453,25 @@ __device__ __forceinline__ void body_resid_up(Shell S, int sys, State<R> it, Sta
   const R *wi = velf(it, sys, 0), *wn = velf(n, sys, 0);
   const R *yi = velf(it, sys, 1), *yn = velf(n, sys, 1);
   const R *xi = velf(it, sys, 2), *xn = velf(n, sys, 2);
-  const V S0 = Sm<V>(xi, xn, q);
-  const V Srp = Sm<V>(xi, xn, q + SI), Srm = Sm<V>(xi, xn, q - SI);
-  const V Stp = Sm<V>(xi, xn, q + P), Stm = Sm<V>(xi, xn, q - P);
-  const V Spp = Sm<V>(xi, xn, q + 1), Spm = Sm<V>(xi, xn, q - 1);
+  auto sw = [&](long qq) -> V {
+    if constexpr (kSum) return (V)Sv[0][qq];
+    else return Sm<V>(wi, wn, qq);
+  };
+  auto sy = [&](long qq) -> V {
+    if constexpr (kSum) return (V)Sv[1][qq];
+    else return Sm<V>(yi, yn, qq);
+  };
+  auto sx = [&](long qq) -> V {
+    if constexpr (kSum) return (V)Sv[2][qq];
+    else return Sm<V>(xi, xn, qq);
+  };
+  const V S0 = sx(q);
+  const V Srp = sx(q + SI), Srm = sx(q - SI);
+  const V Stp = sx(q + P), Stm = sx(q - P);
+  const V Spp = sx(q + 1), Spm = sx(q - 1);
   // u_r and u_theta around the face: the two cells sharing it
-  const V w1 = Sm<V>(wi, wn, q + SI), w0 = Sm<V>(wi, wn, q), wm1 = Sm<V>(wi, wn, q - 1 + SI), wm0 = Sm<V>(wi, wn, q - 1);
-  const V y1 = Sm<V>(yi, yn, q + P), y0 = Sm<V>(yi, yn, q), ym1 = Sm<V>(yi, yn, q - 1 + P), ym0 = Sm<V>(yi, yn, q - 1);
+  const V w1 = sw(q + SI), w0 = sw(q), wm1 = sw(q - 1 + SI), wm0 = sw(q - 1);
+  const V y1 = sy(q + P), y0 = sy(q), ym1 = sy(q - 1 + P), ym0 = sy(q - 1);
   const R *A0 = ax.A[0], *A1 = ax.A[1];
   const V sAr = kTab ? (V)ax.As[LP][DR][q] : ((V)A0[q - 1] + (V)A0[q - 1 + SI]) + (V)A0[q] + (V)A0[q + SI];
   const V sAt = kTab ? (V)ax.As[LP][DT][q] : ((V)A1[q - 1] + (V)A1[q - 1 + P]) + (V)A1[q] + (V)A1[q + P];

@@ -14,7 +14,7 @@ namespace ys {
 // kernel classes for timing
 enum KClass {
   K_EXTRAP = 0, K_FORCE, K_EXCH, K_WALLS, K_RING, K_RES_T, K_RES_U, K_SWEEP_R, K_SWEEP_T, K_SWEEP_P, K_PRES,
-  K_PACK, K_FACTOR, K_WATCH, K_NUM
+  K_PACK, K_FACTOR, K_WATCH, K_SUMS, K_NUM
 };
 
 struct ProfRec {
@@ -31,6 +31,7 @@ struct Fields {
   R *B, *Cs;                 // right-hand-side work field, forward-sweep scratch of the line solves
   R *fac[4][3][3];           // per-step LU factors: fac[loc][dir] = {lo, 1/pivot, c'}
   R *As[4][3];               // per-step sums of the advecting velocity (StepAux::As)
+  R *Sv[3];                  // FP64: two-level sums of the current system's velocity (LevelSums), else null
   R *modes[kMaxModes][4];    // forcing modes
 };
 

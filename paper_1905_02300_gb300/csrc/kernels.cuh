@@ -55,6 +55,14 @@ struct StepAux {
   const R *As[4][3];
 };
 
+// Two-level sums S_c = u_c + u_c^n of one velocity system's components c
+// (r, theta, phi), whole padded fields: the FP64 single-shell velocity
+// residuals read them instead of adding the two levels at every stencil point.
+template <typename R>
+struct LevelSums {
+  const R *S[3];
+};
+
 // Separable forcing modes, passed by value: out_c = sum_m tau[m] F[m][c].
 constexpr int kMaxModes = 8;
 template <typename R>
@@ -85,8 +93,13 @@ struct Launch {
   // residual -F into B
   static void resid_T(const Shell &S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask,
                       cudaStream_t st);
+  // (FP64: ls holds the system's two-level sums, formed by sum_levels)
   static void resid_u(const Shell &S, int sys, int comp, State<R> it, State<R> n, StepAux<R> ax, R *B,
-                      int patch_mask, cudaStream_t st);
+                      int patch_mask, cudaStream_t st, LevelSums<R> ls = {});
+  // Sv[c] = it.u_c + n.u_c of system sys over the whole padded field, for the
+  // components c set in comp_mask (bit c)
+  static void sum_levels(const Layout &L, int sys, State<R> it, State<R> n, R *const Sv[3], int comp_mask,
+                         cudaStream_t st);
   // one line sweep of the factor (loc, dir); final sweeps add into dst and
   // accumulate the weighted squared increment into norm[slot]
   static void sweep(const Shell &S, int loc, int dir, bool final, StepAux<R> ax, R *B, R *Cs, R *dst,

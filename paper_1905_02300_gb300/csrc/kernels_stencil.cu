@@ -10,6 +10,7 @@
 // r, sin(theta), cos(theta) and their reciprocals).  Bulk arithmetic runs in
 // the storage type (FP64, or FP32 in the mixed form); pressures and the
 // divergence that updates them are FP64 in both forms.
+#include <type_traits>
 #include "bodies.cuh"
 
 namespace ys {
@@ -103,27 +104,30 @@ __global__ void __launch_bounds__(ResidOcc<R>::kTpbT)
 // ----------------------------------------------------------------- residual u
 template <typename R>
 __global__ void __launch_bounds__(ResidOcc<R>::kTpb, ResidOcc<R>::kMinCtas)
-    k_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
+    k_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask,
+               LevelSums<R> ls) {
   if constexpr (resid_nv<R>() == 1)
-    bd::body_resid_ur<R, true>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
+    bd::body_resid_ur<R, true, true>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y, ls.S);
   else
     bd::body_resid_ur_vec<R, resid_nv<R>()>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(ResidOcc<R>::kTpb, ResidOcc<R>::kMinCtas)
-    k_resid_ut(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
+    k_resid_ut(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask,
+               LevelSums<R> ls) {
   if constexpr (resid_nv<R>() == 1)
-    bd::body_resid_ut<R, true>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
+    bd::body_resid_ut<R, true, true>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y, ls.S);
   else
     bd::body_resid_ut_vec<R, resid_nv<R>()>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(ResidOcc<R>::kTpb, ResidOcc<R>::kMinCtas)
-    k_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
+    k_resid_up(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask,
+               LevelSums<R> ls) {
   if constexpr (resid_nv<R>() == 1)
-    bd::body_resid_up<R, true>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
+    bd::body_resid_up<R, true, true>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y, ls.S);
   else
     bd::body_resid_up_vec<R, resid_nv<R>()>(S, sys, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
 }
@@ -280,14 +284,59 @@ void Launch<R>::resid_T(const Shell &S, State<R> it, State<R> n, StepAux<R> ax, 
 
 template <typename R>
 void Launch<R>::resid_u(const Shell &S, int sys, int comp, State<R> it, State<R> n, StepAux<R> ax, R *B, int pm,
-                        cudaStream_t st) {
+                        cudaStream_t st, LevelSums<R> ls) {
   const ResidLaunch g = resid_launch(S.L, LR + comp, resid_nv<R>());
   if (comp == 0)
-    k_resid_ur<R><<<g.grid, g.tpb, 0, st>>>(S, sys, it, n, ax, B, pm);
+    k_resid_ur<R><<<g.grid, g.tpb, 0, st>>>(S, sys, it, n, ax, B, pm, ls);
   else if (comp == 1)
-    k_resid_ut<R><<<g.grid, g.tpb, 0, st>>>(S, sys, it, n, ax, B, pm);
+    k_resid_ut<R><<<g.grid, g.tpb, 0, st>>>(S, sys, it, n, ax, B, pm, ls);
   else
-    k_resid_up<R><<<g.grid, g.tpb, 0, st>>>(S, sys, it, n, ax, B, pm);
+    k_resid_up<R><<<g.grid, g.tpb, 0, st>>>(S, sys, it, n, ax, B, pm, ls);
+}
+
+// Sv[c] = a_c + b_c elementwise over whole fields (16-byte accesses; a
+// field's length is a multiple of 32 elements and its start 256-byte aligned)
+template <typename R>
+__global__ void k_sum_levels(long total, const R *a0, const R *b0, R *s0, const R *a1, const R *b1, R *s1,
+                             const R *a2, const R *b2, R *s2) {
+  constexpr int W = 16 / sizeof(R);
+  using Vec = typename std::conditional<sizeof(R) == 8, double2, float4>::type;
+  const long nv = total / W;
+  for (long v = (long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (long)gridDim.x * blockDim.x) {
+    const R *as[3] = {a0, a1, a2}, *bs[3] = {b0, b1, b2};
+    R *ss[3] = {s0, s1, s2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (!ss[c]) continue;
+      const Vec x = reinterpret_cast<const Vec *>(as[c])[v], y = reinterpret_cast<const Vec *>(bs[c])[v];
+      Vec z;
+      if constexpr (sizeof(R) == 8) {
+        z.x = x.x + y.x;
+        z.y = x.y + y.y;
+      } else {
+        z.x = x.x + y.x;
+        z.y = x.y + y.y;
+        z.z = x.z + y.z;
+        z.w = x.w + y.w;
+      }
+      reinterpret_cast<Vec *>(ss[c])[v] = z;
+    }
+  }
+}
+
+template <typename R>
+void Launch<R>::sum_levels(const Layout &L, int sys, State<R> it, State<R> n, R *const Sv[3], int comp_mask,
+                           cudaStream_t st) {
+  const int o = (sys == 1) ? F_U1R : F_U2R;
+  const R *a[3] = {}, *b[3] = {};
+  R *s[3] = {};
+  for (int c = 0; c < 3; ++c)
+    if ((comp_mask >> c) & 1) {
+      a[c] = it.f[o + c];
+      b[c] = n.f[o + c];
+      s[c] = Sv[c];
+    }
+  k_sum_levels<R><<<152 * 8, 256, 0, st>>>(L.total, a[0], b[0], s[0], a[1], b[1], s[1], a[2], b[2], s[2]);
 }
 
 template <typename R>
@@ -346,7 +395,8 @@ void norm_watch(double *norm, int k, cudaStream_t st) {
   template void Launch<R>::adv_sums(const Layout &, R *const[3], R *const[4][3], cudaStream_t);                   \
   template void Launch<R>::resid_T(const Shell &, State<R>, State<R>, StepAux<R>, R *, int, cudaStream_t);        \
   template void Launch<R>::resid_u(const Shell &, int, int, State<R>, State<R>, StepAux<R>, R *, int,             \
-                                   cudaStream_t);                                                                  \
+                                   cudaStream_t, LevelSums<R>);                                                    \
+  template void Launch<R>::sum_levels(const Layout &, int, State<R>, State<R>, R *const[3], int, cudaStream_t);    \
   template void Launch<R>::pressure(const Shell &, int, State<R>, State<R>, double *, double *, int, cudaStream_t); \
   template void Launch<R>::unpack(const Layout &, int, const double *, R *, const double *, cudaStream_t, R *);   \
   template void Launch<R>::pack(const Layout &, int, const R *, double *, const double *, cudaStream_t);
