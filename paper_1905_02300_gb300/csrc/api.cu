@@ -269,23 +269,40 @@ template <typename R>
 void iterate(ys_ctx *c, StepAux<R> ax, int mask) {
   Fields<R> &D = F<R>(c);
   State<R> &it = D.lev[2], &n = D.lev[0];
-  LAUNCH(c, K_RES_T, 1, Launch<R>::resid_T(c->S, it, n, ax, D.B, mask, c->stream));
-  solve_unknown<R>(c, LC, F_T, mask);
-  // FP64: the residuals read the two-level sums of the system's velocity,
-  // formed for all three components before the first residual and again for
-  // a component once its solve has changed it (the next residuals read it)
+  // FP64: residuals and pressure updates read two-level sums S = psi + psi^n
+  // (LevelSums) formed by whole-field passes: T's after the exchange and after
+  // its solve, a velocity system's three components before its first
+  // residual, and each component again once its solve has changed it
   const bool sums = D.Sv[0] != nullptr;
-  const LevelSums<R> ls{{D.Sv[0], D.Sv[1], D.Sv[2]}};
+  const LevelSums<R> ls{{D.Sv[0], D.Sv[1], D.Sv[2], D.Sv[3]}};
+  auto sum = [&](int sys, int comp_mask, bool with_T) {
+    SumJob<R> job{};
+    const int o = (sys == 1) ? F_U1R : F_U2R;
+    for (int f = 0; f < 3; ++f)
+      if ((comp_mask >> f) & 1) {
+        job.a[f] = it.f[o + f];
+        job.b[f] = n.f[o + f];
+        job.s[f] = D.Sv[f];
+      }
+    if (with_T) {
+      job.a[3] = it.f[F_T];
+      job.b[3] = n.f[F_T];
+      job.s[3] = D.Sv[3];
+    }
+    LAUNCH(c, K_SUMS, 1, Launch<R>::sum_levels(c->L, job, c->stream));
+  };
+  if (sums) sum(1, 0, true);
+  LAUNCH(c, K_RES_T, 1, Launch<R>::resid_T(c->S, it, n, ax, D.B, mask, c->stream, ls));
+  solve_unknown<R>(c, LC, F_T, mask);
   for (int sys = 1; sys <= 2; ++sys) {
     int o = (sys == 1) ? 0 : 4;
-    if (sums) LAUNCH(c, K_SUMS, 1, Launch<R>::sum_levels(c->L, sys, it, n, D.Sv, 7, c->stream));
+    if (sums) sum(sys, 7, sys == 1);
     for (int comp = 0; comp < 3; ++comp) {
       LAUNCH(c, K_RES_U, 1, Launch<R>::resid_u(c->S, sys, comp, it, n, ax, D.B, mask, c->stream, ls));
       solve_unknown<R>(c, LR + comp, F_U1R + comp + o, mask);
-      if (sums && comp < 2)
-        LAUNCH(c, K_SUMS, 1, Launch<R>::sum_levels(c->L, sys, it, n, D.Sv, 1 << comp, c->stream));
+      if (sums) sum(sys, 1 << comp, false);
     }
-    LAUNCH(c, K_PRES, 2, Launch<R>::pressure(c->S, sys, it, n, c->norm, c->stage, mask, c->stream));
+    LAUNCH(c, K_PRES, 2, Launch<R>::pressure(c->S, sys, it, n, c->norm, c->stage, mask, c->stream, ls));
   }
 }
 
@@ -474,7 +491,7 @@ char *carve(ys_ctx *c, Fields<R> &D, char *base) {
       for (int a = 0; a < 3; ++a) D.fac[loc][dir][a] = f + (fi++) * T;
   for (int loc = 0; loc < 4; ++loc)
     for (int dir = 0; dir < 3; ++dir) D.As[loc][dir] = (loc == dir + 1) ? nullptr : f + (fi++) * T;
-  for (int a = 0; a < 3; ++a) D.Sv[a] = (sizeof(R) == sizeof(double)) ? f + (fi++) * T : nullptr;
+  for (int a = 0; a < 4; ++a) D.Sv[a] = (sizeof(R) == sizeof(double)) ? f + (fi++) * T : nullptr;
   for (int m = 0; m < kMaxModes; ++m)
     for (int a = 0; a < 4; ++a) D.modes[m][a] = nullptr;
   char *next = base + ((fi * T * sizeof(R) + 255) / 256) * 256;
@@ -485,9 +502,9 @@ char *carve(ys_ctx *c, Fields<R> &D, char *base) {
 }
 
 // number of bulk fields of one shell (3 x 7 levels, 3 a, 4 forcing, B, Cs, 36 factors, 9 sums of a),
-// and the FP64 form's 3 two-level sums of the velocity
+// and the FP64 form's 4 two-level sums (velocity of the system being iterated, T)
 constexpr size_t kBulkFields = 3 * 7 + 3 + 4 + 2 + 36 + 9;
-constexpr size_t kSumFields64 = 3;
+constexpr size_t kSumFields64 = 4;
 
 // padded field layout of a shell (both patches)
 void set_layout(const ys_params *p, Layout &L) {

@@ -281,8 +281,9 @@ __device__ __forceinline__ void vst(R *__restrict__ p, const V (&v)[NV], int lan
 
 // temperature at cell centres: kappa Laplacian, advection, forcing, and in
 // the deviation form the conductive-profile source
-template <typename R, bool kTab = false>
-__device__ __forceinline__ void body_resid_T(Shell S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by) {
+template <typename R, bool kTab = false, bool kSum = false>
+__device__ __forceinline__ void body_resid_T(Shell S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by,
+                                             const R *ST = nullptr) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   int p, i, j, k;
@@ -290,10 +291,15 @@ __device__ __forceinline__ void body_resid_T(Shell S, State<R> it, State<R> n, S
   const long q = lidx(L, p, i, j, k), SI = L.SI, P = L.P;
   const V *c = rowc<V>(S, RT_T, i, j);
   const R *a = it.f[F_T], *b = n.f[F_T];
-  const V S0 = Sm<V>(a, b, q);
-  const V Srp = Sm<V>(a, b, q + SI), Srm = Sm<V>(a, b, q - SI);
-  const V Stp = Sm<V>(a, b, q + P), Stm = Sm<V>(a, b, q - P);
-  const V Spp = Sm<V>(a, b, q + 1), Spm = Sm<V>(a, b, q - 1);
+  // two-level sums: precomputed (kSum) or added here
+  auto sT = [&](long qq) -> V {
+    if constexpr (kSum) return (V)ST[qq];
+    else return Sm<V>(a, b, qq);
+  };
+  const V S0 = sT(q);
+  const V Srp = sT(q + SI), Srm = sT(q - SI);
+  const V Stp = sT(q + P), Stm = sT(q - P);
+  const V Spp = sT(q + 1), Spm = sT(q - 1);
   const V diff = c[T_RP] * (Srp - S0) - c[T_RM] * (S0 - Srm) + c[T_TP] * (Stp - S0) - c[T_TM] * (S0 - Stm) +
                  c[T_PP] * (Spp - (V)2.0 * S0 + Spm);
   const V sAr = kTab ? (V)ax.As[LC][DR][q] : (V)ax.A[0][q] + (V)ax.A[0][q + SI];
@@ -316,9 +322,10 @@ __device__ __forceinline__ double pres(const State<R> &it, const State<R> &n, in
 // u_r at r-faces: nu (vector Laplacian), -advection (with the curvature
 // terms), -grad P, grad(div)/(2 chi), buoyancy, forcing.
 // kSum (the single-shell FP64 launches): the two-level sums S = psi + psi^n
-// of the system's three velocity components are read from Sv[0..2], fields
-// formed by k_sum_levels with the same addition, instead of being added here
-// at every stencil point (15 FP64 additions and 15 loads fewer a point).
+// of the system's three velocity components and of T are read from
+// Sv[0..3] (LevelSums), fields formed by k_sum_levels with the same addition,
+// instead of being added here at every stencil point (17 FP64 additions and
+// 17 loads fewer a point).
 template <typename R, bool kTab = false, bool kSum = false>
 __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by,
                                                const R *const *Sv = nullptr) {
@@ -375,7 +382,10 @@ __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, Sta
   out += sAt * (c[UR_CV] * (((ym0 + ym1) + y0) + y1) - c[UR_AT] * (Stp - Stm));
   out += sAp * (c[UR_CV] * (((zm0 + zm1) + z0) + z1) - c[UR_AP] * (Spp - Spm));
   out -= c[UR_GPR] * (V)(pres(it, n, sys, q) - pres(it, n, sys, q - SI));
-  out += c[UR_BY] * (Sm<V>(it.f[F_T], n.f[F_T], q - SI) + Sm<V>(it.f[F_T], n.f[F_T], q));
+  if constexpr (kSum)
+    out += c[UR_BY] * ((V)Sv[3][q - SI] + (V)Sv[3][q]);
+  else
+    out += c[UR_BY] * (Sm<V>(it.f[F_T], n.f[F_T], q - SI) + Sm<V>(it.f[F_T], n.f[F_T], q));
   if (ax.fr) out += cs<V>(S, CS_DT) * (V)ax.fr[q];
   B[q] = (R)(out - ((V)xi[q] - (V)xn[q]));
 }
@@ -850,9 +860,10 @@ __device__ __forceinline__ void body_resid_up_vec(Shell S, int sys, State<R> it,
 // volume (norm_flush applies it); step-7 ring cells contribute nothing.  The
 // caller accumulates shares over many cells, so that one atomic serves many
 // thousands of cells.
-template <typename R>
+template <typename R, bool kSum = false>
 __device__ __forceinline__ typename Cmp<R>::type body_pressure_at(Shell S, int sys, State<R> it, State<R> n,
-                                                                  int p, int i, int j, int k) {
+                                                                  int p, int i, int j, int k,
+                                                                  const R *const *Sv = nullptr) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   const long q = lidx(L, p, i, j, k);
@@ -868,9 +879,14 @@ __device__ __forceinline__ typename Cmp<R>::type body_pressure_at(Shell S, int s
     const double *c = rowc<double>(S, RT_DIV, i, j);
     const R *ri = velf(it, sys, 0), *rn = velf(n, sys, 0), *ti = velf(it, sys, 1), *tn = velf(n, sys, 1);
     const R *pi = velf(it, sys, 2), *pn = velf(n, sys, 2);
-    D = (c[DV_R1] * Sm<double>(ri, rn, q + L.SI) - c[DV_R0] * Sm<double>(ri, rn, q)) +
-        (c[DV_T1] * Sm<double>(ti, tn, q + L.P) - c[DV_T0] * Sm<double>(ti, tn, q)) +
-        c[DV_P] * (Sm<double>(pi, pn, q + 1) - Sm<double>(pi, pn, q));
+    if constexpr (kSum)   // precomputed two-level sums (LevelSums)
+      D = (c[DV_R1] * (double)Sv[0][q + L.SI] - c[DV_R0] * (double)Sv[0][q]) +
+          (c[DV_T1] * (double)Sv[1][q + L.P] - c[DV_T0] * (double)Sv[1][q]) +
+          c[DV_P] * ((double)Sv[2][q + 1] - (double)Sv[2][q]);
+    else
+      D = (c[DV_R1] * Sm<double>(ri, rn, q + L.SI) - c[DV_R0] * Sm<double>(ri, rn, q)) +
+          (c[DV_T1] * Sm<double>(ti, tn, q + L.P) - c[DV_T0] * Sm<double>(ti, tn, q)) +
+          c[DV_P] * (Sm<double>(pi, pn, q + 1) - Sm<double>(pi, pn, q));
   }
   double pnew;
   double *dst;
@@ -889,12 +905,13 @@ __device__ __forceinline__ typename Cmp<R>::type body_pressure_at(Shell S, int s
 }
 
 // the pressure update of the cell of (bx, by) in a row-per-block grid
-template <typename R>
+template <typename R, bool kSum = false>
 __device__ __forceinline__ typename Cmp<R>::type body_pressure(Shell S, int sys, State<R> it, State<R> n,
-                                                               int patch_mask, int bx, int by) {
+                                                               int patch_mask, int bx, int by,
+                                                               const R *const *Sv = nullptr) {
   int p, i, j, k;
   if (!decode_point(S.L, LC, patch_mask, bx, by, p, i, j, k)) return (typename Cmp<R>::type)0.0;
-  return body_pressure_at(S, sys, it, n, p, i, j, k);
+  return body_pressure_at<R, kSum>(S, sys, it, n, p, i, j, k, Sv);
 }
 
 // Warp sum of per-thread norm shares, scaled once and added to *dst by lane 0.

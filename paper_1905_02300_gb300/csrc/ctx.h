@@ -31,7 +31,7 @@ struct Fields {
   R *B, *Cs;                 // right-hand-side work field, forward-sweep scratch of the line solves
   R *fac[4][3][3];           // per-step LU factors: fac[loc][dir] = {lo, 1/pivot, c'}
   R *As[4][3];               // per-step sums of the advecting velocity (StepAux::As)
-  R *Sv[3];                  // FP64: two-level sums of the current system's velocity (LevelSums), else null
+  R *Sv[4];                  // FP64: two-level sums (LevelSums: the iterated system's velocity, T), else null
   R *modes[kMaxModes][4];    // forcing modes
 };
 

@@ -55,12 +55,19 @@ struct StepAux {
   const R *As[4][3];
 };
 
-// Two-level sums S_c = u_c + u_c^n of one velocity system's components c
-// (r, theta, phi), whole padded fields: the FP64 single-shell velocity
-// residuals read them instead of adding the two levels at every stencil point.
+// Two-level sums S = psi + psi^n, whole padded fields: S[0..2] the velocity
+// components (r, theta, phi) of the system being iterated, S[3] the
+// temperature.  The FP64 single-shell residuals and pressure updates read
+// them instead of adding the two levels at every stencil point.
 template <typename R>
 struct LevelSums {
-  const R *S[3];
+  const R *S[4];
+};
+// up to four whole-field sums s[f] = a[f] + b[f] (null s[f]: unused)
+template <typename R>
+struct SumJob {
+  const R *a[4], *b[4];
+  R *s[4];
 };
 
 // Separable forcing modes, passed by value: out_c = sum_m tau[m] F[m][c].
@@ -92,14 +99,12 @@ struct Launch {
   static void ring(const Shell &S, const XTables &X, State<R> s, int patch_mask, cudaStream_t st);
   // residual -F into B
   static void resid_T(const Shell &S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask,
-                      cudaStream_t st);
+                      cudaStream_t st, LevelSums<R> ls = {});
   // (FP64: ls holds the system's two-level sums, formed by sum_levels)
   static void resid_u(const Shell &S, int sys, int comp, State<R> it, State<R> n, StepAux<R> ax, R *B,
                       int patch_mask, cudaStream_t st, LevelSums<R> ls = {});
-  // Sv[c] = it.u_c + n.u_c of system sys over the whole padded field, for the
-  // components c set in comp_mask (bit c)
-  static void sum_levels(const Layout &L, int sys, State<R> it, State<R> n, R *const Sv[3], int comp_mask,
-                         cudaStream_t st);
+  // the whole-field sums of `job` (LevelSums)
+  static void sum_levels(const Layout &L, SumJob<R> job, cudaStream_t st);
   // one line sweep of the factor (loc, dir); final sweeps add into dst and
   // accumulate the weighted squared increment into norm[slot]
   static void sweep(const Shell &S, int loc, int dir, bool final, StepAux<R> ax, R *B, R *Cs, R *dst,
@@ -117,7 +122,7 @@ struct Launch {
   static void mass_flux(const Shell &S, State<R> s, int patch_mask, double *acc, double alpha, double wsq,
                         double cw0, double cw1, double tol, cudaStream_t st);
   static void pressure(const Shell &S, int sys, State<R> it, State<R> n, double *norm, double *part,
-                       int patch_mask, cudaStream_t st);
+                       int patch_mask, cudaStream_t st, LevelSums<R> ls = {});
   // host layout <-> device layout; bg (FP64 per radial index, may be null) is
   // subtracted on the way in and added on the way out
   // user layout (device or mapped pinned host memory) -> padded field dst and,

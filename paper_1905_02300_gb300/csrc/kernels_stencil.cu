@@ -94,9 +94,9 @@ struct ResidOcc {
 
 template <typename R>
 __global__ void __launch_bounds__(ResidOcc<R>::kTpbT)
-    k_resid_T(Shell S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask) {
+    k_resid_T(Shell S, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, LevelSums<R> ls) {
   if constexpr (resid_nv<R>() == 1)
-    bd::body_resid_T<R, true>(S, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
+    bd::body_resid_T<R, true, true>(S, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y, ls.S[3]);
   else
     bd::body_resid_T_vec<R, resid_nv<R>()>(S, it, n, ax, B, patch_mask, blockIdx.x, blockIdx.y);
 }
@@ -144,14 +144,15 @@ template <typename R>
 __host__ __device__ constexpr int pres_rows() {
   return sizeof(R) == sizeof(float) ? 1 : 4;
 }
-template <typename R>
-__global__ void k_pressure(Shell S, int sys, State<R> it, State<R> n, double *part, int rows, int patch_mask) {
+template <typename R, bool kSum>
+__device__ __forceinline__ void pressure_cta(const Shell &S, int sys, const State<R> &it, const State<R> &n,
+                                             double *part, int rows, int patch_mask, const R *const *Sv) {
   using V = typename Cmp<R>::type;
   __shared__ V ws[TPB];
   V v = (V)0.0;
   for (int t = 0; t < pres_rows<R>(); ++t) {
     const int by = blockIdx.y * pres_rows<R>() + t;
-    if (by < rows) v += bd::body_pressure(S, sys, it, n, patch_mask, blockIdx.x, by);
+    if (by < rows) v += bd::body_pressure<R, kSum>(S, sys, it, n, patch_mask, blockIdx.x, by, Sv);
   }
   ws[threadIdx.x] = v;
   __syncthreads();
@@ -161,6 +162,17 @@ __global__ void k_pressure(Shell S, int sys, State<R> it, State<R> n, double *pa
     for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(0xffffffffu, w, off);
     if (threadIdx.x == 0) part[(long)blockIdx.y * gridDim.x + blockIdx.x] = (double)w;
   }
+}
+
+template <typename R>
+__global__ void k_pressure(Shell S, int sys, State<R> it, State<R> n, double *part, int rows, int patch_mask) {
+  pressure_cta<R, false>(S, sys, it, n, part, rows, patch_mask, nullptr);
+}
+
+// the FP64 form, reading the two-level sums of the velocity (LevelSums)
+__global__ void k_pressure_sum(Shell S, int sys, State<double> it, State<double> n, double *part, int rows,
+                               int patch_mask, LevelSums<double> ls) {
+  pressure_cta<double, true>(S, sys, it, n, part, rows, patch_mask, ls.S);
 }
 
 // dst += scale * sum(part[0, n)): CTAs take interleaved slices, one atomic each
@@ -277,9 +289,10 @@ void Launch<R>::combine_forcing(long total, Modes<R> modes, R *out[4], cudaStrea
 }
 
 template <typename R>
-void Launch<R>::resid_T(const Shell &S, State<R> it, State<R> n, StepAux<R> ax, R *B, int pm, cudaStream_t st) {
+void Launch<R>::resid_T(const Shell &S, State<R> it, State<R> n, StepAux<R> ax, R *B, int pm, cudaStream_t st,
+                        LevelSums<R> ls) {
   const ResidLaunch g = resid_launch(S.L, LC, resid_nv<R>());
-  k_resid_T<R><<<g.grid, g.tpb, 0, st>>>(S, it, n, ax, B, pm);
+  k_resid_T<R><<<g.grid, g.tpb, 0, st>>>(S, it, n, ax, B, pm, ls);
 }
 
 template <typename R>
@@ -294,21 +307,18 @@ void Launch<R>::resid_u(const Shell &S, int sys, int comp, State<R> it, State<R>
     k_resid_up<R><<<g.grid, g.tpb, 0, st>>>(S, sys, it, n, ax, B, pm, ls);
 }
 
-// Sv[c] = a_c + b_c elementwise over whole fields (16-byte accesses; a
+// s[f] = a[f] + b[f] elementwise over whole fields (16-byte accesses; a
 // field's length is a multiple of 32 elements and its start 256-byte aligned)
 template <typename R>
-__global__ void k_sum_levels(long total, const R *a0, const R *b0, R *s0, const R *a1, const R *b1, R *s1,
-                             const R *a2, const R *b2, R *s2) {
+__global__ void k_sum_levels(long total, SumJob<R> job) {
   constexpr int W = 16 / sizeof(R);
   using Vec = typename std::conditional<sizeof(R) == 8, double2, float4>::type;
   const long nv = total / W;
   for (long v = (long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (long)gridDim.x * blockDim.x) {
-    const R *as[3] = {a0, a1, a2}, *bs[3] = {b0, b1, b2};
-    R *ss[3] = {s0, s1, s2};
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (!ss[c]) continue;
-      const Vec x = reinterpret_cast<const Vec *>(as[c])[v], y = reinterpret_cast<const Vec *>(bs[c])[v];
+    for (int f = 0; f < 4; ++f) {
+      if (!job.s[f]) continue;
+      const Vec x = reinterpret_cast<const Vec *>(job.a[f])[v], y = reinterpret_cast<const Vec *>(job.b[f])[v];
       Vec z;
       if constexpr (sizeof(R) == 8) {
         z.x = x.x + y.x;
@@ -319,32 +329,25 @@ __global__ void k_sum_levels(long total, const R *a0, const R *b0, R *s0, const 
         z.z = x.z + y.z;
         z.w = x.w + y.w;
       }
-      reinterpret_cast<Vec *>(ss[c])[v] = z;
+      reinterpret_cast<Vec *>(job.s[f])[v] = z;
     }
   }
 }
 
 template <typename R>
-void Launch<R>::sum_levels(const Layout &L, int sys, State<R> it, State<R> n, R *const Sv[3], int comp_mask,
-                           cudaStream_t st) {
-  const int o = (sys == 1) ? F_U1R : F_U2R;
-  const R *a[3] = {}, *b[3] = {};
-  R *s[3] = {};
-  for (int c = 0; c < 3; ++c)
-    if ((comp_mask >> c) & 1) {
-      a[c] = it.f[o + c];
-      b[c] = n.f[o + c];
-      s[c] = Sv[c];
-    }
-  k_sum_levels<R><<<152 * 8, 256, 0, st>>>(L.total, a[0], b[0], s[0], a[1], b[1], s[1], a[2], b[2], s[2]);
+void Launch<R>::sum_levels(const Layout &L, SumJob<R> job, cudaStream_t st) {
+  k_sum_levels<R><<<152 * 8, 256, 0, st>>>(L.total, job);
 }
 
 template <typename R>
 void Launch<R>::pressure(const Shell &S, int sys, State<R> it, State<R> n, double *norm, double *part, int pm,
-                         cudaStream_t st) {
+                         cudaStream_t st, LevelSums<R> ls) {
   const dim3 g = point_grid(S.L, LC);
   const dim3 gp(g.x, (g.y + pres_rows<R>() - 1) / pres_rows<R>());
-  k_pressure<R><<<gp, TPB, 0, st>>>(S, sys, it, n, part, (int)g.y, pm);
+  if constexpr (sizeof(R) == sizeof(double))
+    k_pressure_sum<<<gp, TPB, 0, st>>>(S, sys, it, n, part, (int)g.y, pm, ls);
+  else
+    k_pressure<R><<<gp, TPB, 0, st>>>(S, sys, it, n, part, (int)g.y, pm);
   k_sum_parts<<<kSumCtas, 256, 0, st>>>(part, (long)gp.x * gp.y, S.dcs[CS_VOL], &norm[sys == 1 ? 4 : 8]);
 }
 
@@ -393,11 +396,13 @@ void norm_watch(double *norm, int k, cudaStream_t st) {
   template void Launch<R>::extrapolate(const Layout &, State<R>, State<R>, State<R>, R *[3], cudaStream_t);       \
   template void Launch<R>::combine_forcing(long, Modes<R>, R *[4], cudaStream_t);                                  \
   template void Launch<R>::adv_sums(const Layout &, R *const[3], R *const[4][3], cudaStream_t);                   \
-  template void Launch<R>::resid_T(const Shell &, State<R>, State<R>, StepAux<R>, R *, int, cudaStream_t);        \
+  template void Launch<R>::resid_T(const Shell &, State<R>, State<R>, StepAux<R>, R *, int, cudaStream_t,         \
+                                   LevelSums<R>);                                                                  \
   template void Launch<R>::resid_u(const Shell &, int, int, State<R>, State<R>, StepAux<R>, R *, int,             \
                                    cudaStream_t, LevelSums<R>);                                                    \
-  template void Launch<R>::sum_levels(const Layout &, int, State<R>, State<R>, R *const[3], int, cudaStream_t);    \
-  template void Launch<R>::pressure(const Shell &, int, State<R>, State<R>, double *, double *, int, cudaStream_t); \
+  template void Launch<R>::sum_levels(const Layout &, SumJob<R>, cudaStream_t);                                   \
+  template void Launch<R>::pressure(const Shell &, int, State<R>, State<R>, double *, double *, int, cudaStream_t,  \
+                                    LevelSums<R>);                                                                 \
   template void Launch<R>::unpack(const Layout &, int, const double *, R *, const double *, cudaStream_t, R *);   \
   template void Launch<R>::pack(const Layout &, int, const R *, double *, const double *, cudaStream_t);
 YS_INST_STENCIL(double)
