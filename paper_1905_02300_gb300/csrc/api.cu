@@ -234,14 +234,17 @@ const int kSweepClass[3] = {K_SWEEP_R, K_SWEEP_T, K_SWEEP_P};
 template <typename R>
 void solve_unknown(ys_ctx *c, int loc, int slot, int mask) {
   Fields<R> &D = F<R>(c);
-  State<R> &it = D.lev[2];
+  State<R> &it = D.lev[2], &n = D.lev[0];
+  // FP64: the final factor also refreshes the unknown's two-level sum
+  // (LevelSums: velocity component loc - LR, or T)
+  R *sum = D.Sv[0] ? D.Sv[loc == LC ? 3 : loc - LR] : nullptr;
   for (int s = 0; s < 3; ++s) {
     int dir = kOrder[loc][s];
     bool fin = (s == 2);
     R *const *Fc = D.fac[loc][dir];
     LAUNCH(c, kSweepClass[dir], 1,
            Launch<R>::solve(c->S, loc, dir, fin, Fc[0], Fc[1], Fc[2], D.B, D.Cs, it.f[slot], c->norm, slot, mask,
-                            c->stream));
+                            c->stream, fin ? n.f[slot] : nullptr, fin ? sum : nullptr));
   }
 }
 
@@ -270,9 +273,9 @@ void iterate(ys_ctx *c, StepAux<R> ax, int mask) {
   Fields<R> &D = F<R>(c);
   State<R> &it = D.lev[2], &n = D.lev[0];
   // FP64: residuals and pressure updates read two-level sums S = psi + psi^n
-  // (LevelSums) formed by whole-field passes: T's after the exchange and after
-  // its solve, a velocity system's three components before its first
-  // residual, and each component again once its solve has changed it
+  // (LevelSums), formed by whole-field passes (T's after the exchange, a
+  // velocity system's three components before its first residual) and
+  // refreshed by the final solve of each unknown, which changes it
   const bool sums = D.Sv[0] != nullptr;
   const LevelSums<R> ls{{D.Sv[0], D.Sv[1], D.Sv[2], D.Sv[3]}};
   auto sum = [&](int sys, int comp_mask, bool with_T) {
@@ -296,11 +299,10 @@ void iterate(ys_ctx *c, StepAux<R> ax, int mask) {
   solve_unknown<R>(c, LC, F_T, mask);
   for (int sys = 1; sys <= 2; ++sys) {
     int o = (sys == 1) ? 0 : 4;
-    if (sums) sum(sys, 7, sys == 1);
+    if (sums) sum(sys, 7, false);
     for (int comp = 0; comp < 3; ++comp) {
       LAUNCH(c, K_RES_U, 1, Launch<R>::resid_u(c->S, sys, comp, it, n, ax, D.B, mask, c->stream, ls));
       solve_unknown<R>(c, LR + comp, F_U1R + comp + o, mask);
-      if (sums) sum(sys, 1 << comp, false);
     }
     LAUNCH(c, K_PRES, 2, Launch<R>::pressure(c->S, sys, it, n, c->norm, c->stage, mask, c->stream, ls));
   }

@@ -1238,10 +1238,11 @@ __device__ __forceinline__ void solve_load_fwd(const R *__restrict__ B, const R 
     }
   }
 }
-template <int U, typename R, typename V>
+template <int U, bool kSum = false, typename R, typename V>
 __device__ __forceinline__ void solve_load_bwd(const R *__restrict__ W, const R *__restrict__ Cp,
                                                const R *__restrict__ dst, int final, long q0, long step, int m,
-                                               V (&w)[U], V (&c)[U], V (&o)[U]) {
+                                               V (&w)[U], V (&c)[U], V (&o)[U], const R *__restrict__ Pn = nullptr,
+                                               V *pn = nullptr) {
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const long qq = q0 + (long)(m - u) * step;
@@ -1249,6 +1250,7 @@ __device__ __forceinline__ void solve_load_bwd(const R *__restrict__ W, const R 
       w[u] = (V)W[qq];
       c[u] = (V)Cp[qq];
       o[u] = final ? (V)dst[qq] : (V)0.0;
+      if constexpr (kSum) pn[u] = (V)Pn[qq];
     }
   }
 }
@@ -1259,12 +1261,15 @@ __device__ __forceinline__ void solve_load_bwd(const R *__restrict__ W, const R 
 // the recurrence and of every store (separate arrays), so they are in flight
 // together.  Non-final factors write x to B (the next factor's right-hand
 // side); the final factor of an unknown adds x to the iterate and accumulates
-// the FP64 midpoint-rule norm of the increment (Sec. 5.1).
-template <typename R, bool kPf = false>
+// the FP64 midpoint-rule norm of the increment (Sec. 5.1).  kSum (final
+// factors of the FP64 single-shell launches): also Sout = new value + Pn, the
+// two-level sum the next residuals read (LevelSums), with their addition.
+template <typename R, bool kPf = false, bool kSum = false>
 __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final, const R *__restrict__ Lo,
                                            const R *__restrict__ Iv, const R *__restrict__ Cp, R *__restrict__ B,
                                            R *__restrict__ W, R *__restrict__ dst, double *norm, int slot,
-                                           int patch_mask, int bx, int by) {
+                                           int patch_mask, int bx, int by, const R *__restrict__ Pn = nullptr,
+                                           R *__restrict__ Sout = nullptr) {
   using V = typename Cmp<R>::type;
   // rows per register chunk: 8 in FP32; 4 in FP64, where 8 rows and the next
   // chunk's prefetch took 128 registers, too many for all lines of a
@@ -1312,14 +1317,14 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
     // along it (r^2, sin(theta) or 1), and scales once by the constant rest
     V x = d;
     V acc = (V)0.0;
-    V w[U], c[U], o[U];
-    if constexpr (kPf) solve_load_bwd<U>(W, Cp, dst, final, q0, step, n - 1, w, c, o);
+    V w[U], c[U], o[U], pn[kSum ? U : 1];
+    if constexpr (kPf) solve_load_bwd<U, kSum>(W, Cp, dst, final, q0, step, n - 1, w, c, o, Pn, pn);
     for (int m = n - 1; m >= 0; m -= U) {
-      V nw[U], nc[U], no[U];
+      V nw[U], nc[U], no[U], npn[kSum ? U : 1];
       if constexpr (kPf) {
-        if (m - U >= 0) solve_load_bwd<U>(W, Cp, dst, final, q0, step, m - U, nw, nc, no);
+        if (m - U >= 0) solve_load_bwd<U, kSum>(W, Cp, dst, final, q0, step, m - U, nw, nc, no, Pn, npn);
       } else {
-        solve_load_bwd<U>(W, Cp, dst, final, q0, step, m, w, c, o);
+        solve_load_bwd<U, kSum>(W, Cp, dst, final, q0, step, m, w, c, o, Pn, pn);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -1328,7 +1333,9 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
           long qq = q0 + (long)mm * step;
           if (mm < n - 1) x = w[u] - c[u] * x;
           if (final) {
-            dst[qq] = (R)(o[u] + x);
+            const R nv = (R)(o[u] + x);
+            dst[qq] = nv;
+            if constexpr (kSum) Sout[qq] = (R)((V)nv + pn[u]);
             const int row = ln.m0 + mm;
             if (dir == DR) {
               const V t = ((loc == LR) ? mt<V>(S, MT_NRF) : mt<V>(S, MT_NRC))[row] * x;
@@ -1349,6 +1356,7 @@ __device__ __forceinline__ void body_solve(Shell S, int loc, int dir, int final,
           w[u] = nw[u];
           c[u] = nc[u];
           o[u] = no[u];
+          if constexpr (kSum) pn[u] = npn[u];
         }
       }
     }
@@ -1437,11 +1445,12 @@ __device__ __forceinline__ void seg_store(R *__restrict__ p, bool full, int k, i
   }
 }
 
-template <int EC, typename R>
+template <int EC, bool kSum = false, typename R>
 __device__ __forceinline__ void solve_line_scan(int k0, int k1, int final, const R *__restrict__ Lo,
                                                 const R *__restrict__ Iv, const R *__restrict__ Cp,
                                                 R *__restrict__ B, R *__restrict__ wbuf, R *__restrict__ dst,
-                                                typename Cmp<R>::type &acc) {
+                                                typename Cmp<R>::type &acc, const R *__restrict__ Pn = nullptr,
+                                                R *__restrict__ Sout = nullptr) {
   using V = typename Cmp<R>::type;
   const int lane = threadIdx.x & 31;
   constexpr int CH = 32 * EC;
@@ -1541,6 +1550,14 @@ __device__ __forceinline__ void solve_line_scan(int k0, int k1, int final, const
         o[e] = o[e] + out[e];
       }
       seg_store<EC>(dst + k, full, k, k0, k1, o);
+      if constexpr (kSum) {
+        // the two-level sum of the stored new value (R = V here: FP64)
+        V pn[EC];
+        seg_load<EC>(Pn + k, full, k, k0, k1, pn);
+#pragma unroll
+        for (int e = 0; e < EC; ++e) pn[e] = o[e] + pn[e];
+        seg_store<EC>(Sout + k, full, k, k0, k1, pn);
+      }
     } else {
       seg_store<EC>(B + k, full, k, k0, k1, out);
     }
@@ -1567,12 +1584,13 @@ inline int phi_scan_ctas(const Layout &L, int loc) {
 
 // one phi line per warp; `smem_per_warp` positions of shared memory per warp
 // (0 or too few: the forward results go through W)
-template <typename R>
+template <typename R, bool kSum = false>
 __device__ __forceinline__ void body_solve_phi_scan(Shell S, int loc, int final, const R *__restrict__ Lo,
                                                     const R *__restrict__ Iv, const R *__restrict__ Cp,
                                                     R *__restrict__ B, R *__restrict__ W, R *__restrict__ dst,
                                                     double *norm, int slot, int patch_mask, int bx, R *smem,
-                                                    int smem_per_warp) {
+                                                    int smem_per_warp, const R *__restrict__ Pn = nullptr,
+                                                    R *__restrict__ Sout = nullptr) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   const int warp = threadIdx.x >> 5;
@@ -1591,13 +1609,16 @@ __device__ __forceinline__ void body_solve_phi_scan(Shell S, int loc, int final,
       R *wbuf = (scan_pad(L.Np) <= smem_per_warp) ? smem + (long)warp * smem_per_warp : W + q;
       switch (scan_ec(L.Np)) {
         case 4:
-          solve_line_scan<4>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc);
+          solve_line_scan<4, kSum>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc,
+                                          kSum ? Pn + q : nullptr, kSum ? Sout + q : nullptr);
           break;
         case 8:
-          solve_line_scan<8>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc);
+          solve_line_scan<8, kSum>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc,
+                                          kSum ? Pn + q : nullptr, kSum ? Sout + q : nullptr);
           break;
         default:
-          solve_line_scan<12>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc);
+          solve_line_scan<12, kSum>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc,
+                                          kSum ? Pn + q : nullptr, kSum ? Sout + q : nullptr);
           break;
       }
       if (final) {

@@ -114,8 +114,10 @@ struct Launch {
                         cudaStream_t st);
   // line solve with a stored factorisation (same conventions as sweep)
   // W: scratch for the forward sweep (distinct from B and dst)
+  // FP64 final factors given Sout: also Sout = new dst + Pn (LevelSums)
   static void solve(const Shell &S, int loc, int dir, bool final, const R *Lo, const R *Iv, const R *Cp, R *B,
-                    R *W, R *dst, double *norm, int slot, int patch_mask, cudaStream_t st);
+                    R *W, R *dst, double *norm, int slot, int patch_mask, cudaStream_t st, const R *Pn = nullptr,
+                    R *Sout = nullptr);
   // pressure update of system sys; part: scratch of one FP64 per cell block
   // (partial norms, summed into norm[4] or norm[8] by a second kernel)
   // Algorithm step 4 on the edge velocity of both systems (acc: 4 FP64 scratch)

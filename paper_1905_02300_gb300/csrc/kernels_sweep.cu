@@ -187,6 +187,15 @@ __global__ void k_solve(Shell S, int loc, int dir, int final, const R *__restric
   bd::body_solve<R, true>(S, loc, dir, final, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, blockIdx.x, blockIdx.y);
 }
 
+// final factor of the FP64 form, also writing the two-level sum Sout = dst + Pn
+__global__ void k_solve_sum(Shell S, int loc, int dir, const double *__restrict__ Lo,
+                            const double *__restrict__ Iv, const double *__restrict__ Cp, double *B, double *W,
+                            double *dst, double *norm, int slot, int patch_mask, const double *__restrict__ Pn,
+                            double *__restrict__ Sout) {
+  bd::body_solve<double, true, true>(S, loc, dir, 1, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, blockIdx.x,
+                                     blockIdx.y, Pn, Sout);
+}
+
 dim3 line_grid(const Layout &L, int loc, int dir) {
   int ni = L.Nr - (loc == LR ? 1 : 0);
   int nj = L.Nt - (loc == LT ? 1 : 0);
@@ -212,6 +221,15 @@ __global__ void k_solve_phi(Shell S, int loc, int final, const R *__restrict__ L
                           smem_per_warp);
 }
 
+__global__ void k_solve_phi_sum(Shell S, int loc, const double *__restrict__ Lo, const double *__restrict__ Iv,
+                                const double *__restrict__ Cp, double *B, double *W, double *dst, double *norm,
+                                int slot, int patch_mask, int smem_per_warp, const double *__restrict__ Pn,
+                                double *__restrict__ Sout) {
+  extern __shared__ __align__(16) unsigned char phi_smem[];
+  bd::body_solve_phi_scan<double, true>(S, loc, 1, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, blockIdx.x,
+                                        (double *)phi_smem, smem_per_warp, Pn, Sout);
+}
+
 template <typename R>
 void Launch<R>::sweep(const Shell &S, int loc, int dir, bool final, StepAux<R> ax, R *B, R *Cs, R *dst,
                       double *norm, int slot, int patch_mask, cudaStream_t st) {
@@ -232,17 +250,36 @@ void Launch<R>::factorize(const Shell &S, int loc, int dir, StepAux<R> ax, R *Lo
 
 template <typename R>
 void Launch<R>::solve(const Shell &S, int loc, int dir, bool final, const R *Lo, const R *Iv, const R *Cp, R *B,
-                      R *W, R *dst, double *norm, int slot, int patch_mask, cudaStream_t st) {
+                      R *W, R *dst, double *norm, int slot, int patch_mask, cudaStream_t st, const R *Pn,
+                      R *Sout) {
+  // FP64 final factors given a sum field: the launches that also write it
+  constexpr bool k64 = sizeof(R) == sizeof(double);
+  const bool with_sum = k64 && final && Sout != nullptr;
   if (dir == DP) {
     // forward results of each warp's line in shared memory when they fit
-    static std::atomic<unsigned long long> attr_done{0};
+    static std::atomic<unsigned long long> attr_done{0}, attr_sum_done{0};
     smem_attr_once(attr_done, k_solve_phi<R>, bd::kScanSmemMax);
     const int pad = bd::scan_pad(S.L.Np);
     const size_t bytes = (size_t)bd::kScanWarps * pad * sizeof(R);
     const bool fits = bytes <= (size_t)bd::kScanSmemMax;
+    if constexpr (k64) {
+      if (with_sum) {
+        smem_attr_once(attr_sum_done, k_solve_phi_sum, bd::kScanSmemMax);
+        k_solve_phi_sum<<<bd::phi_scan_ctas(S.L, loc), 32 * bd::kScanWarps, fits ? bytes : 0, st>>>(
+            S, loc, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, fits ? pad : 0, Pn, Sout);
+        return;
+      }
+    }
     k_solve_phi<R><<<bd::phi_scan_ctas(S.L, loc), 32 * bd::kScanWarps, fits ? bytes : 0, st>>>(
         S, loc, final ? 1 : 0, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, fits ? pad : 0);
     return;
+  }
+  if constexpr (k64) {
+    if (with_sum) {
+      k_solve_sum<<<line_grid(S.L, loc, dir), TPB, 0, st>>>(S, loc, dir, Lo, Iv, Cp, B, W, dst, norm, slot,
+                                                            patch_mask, Pn, Sout);
+      return;
+    }
   }
   k_solve<R><<<line_grid(S.L, loc, dir), TPB, 0, st>>>(S, loc, dir, final ? 1 : 0, Lo, Iv, Cp, B, W, dst, norm,
                                                         slot, patch_mask);
@@ -251,7 +288,7 @@ void Launch<R>::solve(const Shell &S, int loc, int dir, bool final, const R *Lo,
 #define YS_INST_SWEEP(R)                                                                                          \
   template void Launch<R>::factorize(const Shell &, int, int, StepAux<R>, R *, R *, R *, int, cudaStream_t);       \
   template void Launch<R>::solve(const Shell &, int, int, bool, const R *, const R *, const R *, R *, R *, R *,       \
-                                 double *, int, int, cudaStream_t);
+                                 double *, int, int, cudaStream_t, const R *, R *);
 YS_INST_SWEEP(double)
 YS_INST_SWEEP(float)
 template void Launch<double>::sweep(const Shell &, int, int, bool, StepAux<double>, double *, double *, double *,
