@@ -277,7 +277,11 @@ void iterate(ys_ctx *c, StepAux<R> ax, int mask) {
   // velocity system's three components before its first residual) and
   // refreshed by the final solve of each unknown, which changes it
   const bool sums = D.Sv[0] != nullptr;
-  const LevelSums<R> ls{{D.Sv[0], D.Sv[1], D.Sv[2], D.Sv[3]}};
+  // S[4]: the momentum pressure, p1^n itself for system 1, the field P2
+  // (formed after the first pressure update) for system 2
+  const LevelSums<R> lsys[2] = {{{D.Sv[0], D.Sv[1], D.Sv[2], D.Sv[3], (const R *)n.p[0]}},
+                                {{D.Sv[0], D.Sv[1], D.Sv[2], D.Sv[3], D.Sv[4]}}};
+  const LevelSums<R> &ls = lsys[0];
   auto sum = [&](int sys, int comp_mask, bool with_T) {
     SumJob<R> job{};
     const int o = (sys == 1) ? F_U1R : F_U2R;
@@ -301,10 +305,13 @@ void iterate(ys_ctx *c, StepAux<R> ax, int mask) {
     int o = (sys == 1) ? 0 : 4;
     if (sums) sum(sys, 7, false);
     for (int comp = 0; comp < 3; ++comp) {
-      LAUNCH(c, K_RES_U, 1, Launch<R>::resid_u(c->S, sys, comp, it, n, ax, D.B, mask, c->stream, ls));
+      LAUNCH(c, K_RES_U, 1, Launch<R>::resid_u(c->S, sys, comp, it, n, ax, D.B, mask, c->stream, lsys[sys - 1]));
       solve_unknown<R>(c, LR + comp, F_U1R + comp + o, mask);
     }
     LAUNCH(c, K_PRES, 2, Launch<R>::pressure(c->S, sys, it, n, c->norm, c->stage, mask, c->stream, ls));
+    if (sums && sys == 1)
+      LAUNCH(c, K_SUMS, 1,
+             Launch<R>::bootstrap_pressure(c->L, n.p[1], it.p[0], n.p[0], (double *)D.Sv[4], c->stream));
   }
 }
 
@@ -493,7 +500,7 @@ char *carve(ys_ctx *c, Fields<R> &D, char *base) {
       for (int a = 0; a < 3; ++a) D.fac[loc][dir][a] = f + (fi++) * T;
   for (int loc = 0; loc < 4; ++loc)
     for (int dir = 0; dir < 3; ++dir) D.As[loc][dir] = (loc == dir + 1) ? nullptr : f + (fi++) * T;
-  for (int a = 0; a < 4; ++a) D.Sv[a] = (sizeof(R) == sizeof(double)) ? f + (fi++) * T : nullptr;
+  for (int a = 0; a < kLevelSums; ++a) D.Sv[a] = (sizeof(R) == sizeof(double)) ? f + (fi++) * T : nullptr;
   for (int m = 0; m < kMaxModes; ++m)
     for (int a = 0; a < 4; ++a) D.modes[m][a] = nullptr;
   char *next = base + ((fi * T * sizeof(R) + 255) / 256) * 256;
@@ -504,9 +511,10 @@ char *carve(ys_ctx *c, Fields<R> &D, char *base) {
 }
 
 // number of bulk fields of one shell (3 x 7 levels, 3 a, 4 forcing, B, Cs, 36 factors, 9 sums of a),
-// and the FP64 form's 4 two-level sums (velocity of the system being iterated, T)
+// and the FP64 form's 5 LevelSums fields (velocity of the system being iterated, T, P2)
 constexpr size_t kBulkFields = 3 * 7 + 3 + 4 + 2 + 36 + 9;
-constexpr size_t kSumFields64 = 4;
+constexpr size_t kSumFields64 = kLevelSums;
+static_assert(sizeof(Fields<double>::Sv) == kSumFields64 * sizeof(double *), "one pointer per LevelSums field");
 
 // padded field layout of a shell (both patches)
 void set_layout(const ys_params *p, Layout &L) {

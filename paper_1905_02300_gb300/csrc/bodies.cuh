@@ -325,7 +325,7 @@ __device__ __forceinline__ double pres(const State<R> &it, const State<R> &n, in
 // of the system's three velocity components and of T are read from
 // Sv[0..3] (LevelSums), fields formed by k_sum_levels with the same addition,
 // instead of being added here at every stencil point (17 FP64 additions and
-// 17 loads fewer a point).
+// 17 loads fewer a point), and the momentum pressure from Sv[4].
 template <typename R, bool kTab = false, bool kSum = false>
 __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, State<R> n, StepAux<R> ax, R *B, int patch_mask, int bx, int by,
                                                const R *const *Sv = nullptr) {
@@ -381,7 +381,10 @@ __device__ __forceinline__ void body_resid_ur(Shell S, int sys, State<R> it, Sta
   // advection along theta / phi and the curvature term of the same advecting component
   out += sAt * (c[UR_CV] * (((ym0 + ym1) + y0) + y1) - c[UR_AT] * (Stp - Stm));
   out += sAp * (c[UR_CV] * (((zm0 + zm1) + z0) + z1) - c[UR_AP] * (Spp - Spm));
-  out -= c[UR_GPR] * (V)(pres(it, n, sys, q) - pres(it, n, sys, q - SI));
+  if constexpr (kSum)
+    out -= c[UR_GPR] * (V)((double)Sv[4][q] - (double)Sv[4][q - SI]);
+  else
+    out -= c[UR_GPR] * (V)(pres(it, n, sys, q) - pres(it, n, sys, q - SI));
   if constexpr (kSum)
     out += c[UR_BY] * ((V)Sv[3][q - SI] + (V)Sv[3][q]);
   else
@@ -445,7 +448,10 @@ __device__ __forceinline__ void body_resid_ut(Shell S, int sys, State<R> it, Sta
   // advection along theta / phi and the curvature term of the same advecting component
   out -= at * (c[UT_AT] * (Stp - Stm) + c[UT_CW] * (((wm0 + wm1) + w0) + w1));
   out += sAp * (c[UT_CP] * (((zm0 + zm1) + z0) + z1) - c[UT_AP] * (Spp - Spm));
-  out -= c[UT_GPR] * (V)(pres(it, n, sys, q) - pres(it, n, sys, q - P));
+  if constexpr (kSum)
+    out -= c[UT_GPR] * (V)((double)Sv[4][q] - (double)Sv[4][q - P]);
+  else
+    out -= c[UT_GPR] * (V)(pres(it, n, sys, q) - pres(it, n, sys, q - P));
   if (ax.ft) out += cs<V>(S, CS_DT) * (V)ax.ft[q];
   B[q] = (R)(out - ((V)xi[q] - (V)xn[q]));
 }
@@ -506,7 +512,10 @@ __device__ __forceinline__ void body_resid_up(Shell S, int sys, State<R> it, Sta
   // advection along phi and the curvature terms, all with the advecting a_phi
   out -= ap * (c[UP_AP] * (Spp - Spm) + c[UP_CW] * (((wm0 + wm1) + w0) + w1) +
                c[UP_CY] * (((ym0 + ym1) + y0) + y1));
-  out -= c[UP_GPR] * (V)(pres(it, n, sys, q) - pres(it, n, sys, q - 1));
+  if constexpr (kSum)
+    out -= c[UP_GPR] * (V)((double)Sv[4][q] - (double)Sv[4][q - 1]);
+  else
+    out -= c[UP_GPR] * (V)(pres(it, n, sys, q) - pres(it, n, sys, q - 1));
   if (ax.fp) out += cs<V>(S, CS_DT) * (V)ax.fp[q];
   B[q] = (R)(out - ((V)xi[q] - (V)xn[q]));
 }

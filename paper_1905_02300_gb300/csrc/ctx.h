@@ -22,6 +22,10 @@ struct ProfRec {
   cudaEvent_t a, b;
 };
 
+// FP64 LevelSums fields of a shell: the iterated system's three velocity
+// components, T, and the bootstrapped momentum pressure P2
+constexpr int kLevelSums = 5;
+
 // Typed device state of one shell.
 template <typename R>
 struct Fields {
@@ -31,7 +35,7 @@ struct Fields {
   R *B, *Cs;                 // right-hand-side work field, forward-sweep scratch of the line solves
   R *fac[4][3][3];           // per-step LU factors: fac[loc][dir] = {lo, 1/pivot, c'}
   R *As[4][3];               // per-step sums of the advecting velocity (StepAux::As)
-  R *Sv[4];                  // FP64: two-level sums (LevelSums: the iterated system's velocity, T), else null
+  R *Sv[kLevelSums];         // FP64: LevelSums fields (velocity of the iterated system, T, P2), else null
   R *modes[kMaxModes][4];    // forcing modes
 };
 

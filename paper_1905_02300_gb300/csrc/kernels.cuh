@@ -57,11 +57,13 @@ struct StepAux {
 
 // Two-level sums S = psi + psi^n, whole padded fields: S[0..2] the velocity
 // components (r, theta, phi) of the system being iterated, S[3] the
-// temperature.  The FP64 single-shell residuals and pressure updates read
-// them instead of adding the two levels at every stencil point.
+// temperature; S[4] the pressure entering that system's momentum rows
+// (P_1 = p_1^n, or the field P_2 = p_2^n + (p_1 - p_1^n)/2).  The FP64
+// single-shell residuals and pressure updates read them instead of forming
+// them at every stencil point.
 template <typename R>
 struct LevelSums {
-  const R *S[4];
+  const R *S[5];
 };
 // up to four whole-field sums s[f] = a[f] + b[f] (null s[f]: unused)
 template <typename R>
@@ -105,6 +107,9 @@ struct Launch {
                       int patch_mask, cudaStream_t st, LevelSums<R> ls = {});
   // the whole-field sums of `job` (LevelSums)
   static void sum_levels(const Layout &L, SumJob<R> job, cudaStream_t st);
+  // P2 = p2n + (p1 - p1n) / 2 over the whole padded field (LevelSums::S[4])
+  static void bootstrap_pressure(const Layout &L, const double *p2n, const double *p1, const double *p1n,
+                                 double *P2, cudaStream_t st);
   // one line sweep of the factor (loc, dir); final sweeps add into dst and
   // accumulate the weighted squared increment into norm[slot]
   static void sweep(const Shell &S, int loc, int dir, bool final, StepAux<R> ax, R *B, R *Cs, R *dst,

@@ -339,6 +339,26 @@ void Launch<R>::sum_levels(const Layout &L, SumJob<R> job, cudaStream_t st) {
   k_sum_levels<R><<<152 * 8, 256, 0, st>>>(L.total, job);
 }
 
+// P2 = p2n + (p1 - p1n) / 2, the expression of the momentum rows' pressure
+__global__ void k_bootstrap_pressure(long total, const double *p2n, const double *p1, const double *p1n,
+                                     double *P2) {
+  const long nv = total / 2;
+  for (long v = (long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (long)gridDim.x * blockDim.x) {
+    const double2 a = reinterpret_cast<const double2 *>(p2n)[v], b = reinterpret_cast<const double2 *>(p1)[v],
+                  c = reinterpret_cast<const double2 *>(p1n)[v];
+    double2 o;
+    o.x = a.x + 0.5 * (b.x - c.x);
+    o.y = a.y + 0.5 * (b.y - c.y);
+    reinterpret_cast<double2 *>(P2)[v] = o;
+  }
+}
+
+template <typename R>
+void Launch<R>::bootstrap_pressure(const Layout &L, const double *p2n, const double *p1, const double *p1n,
+                                   double *P2, cudaStream_t st) {
+  k_bootstrap_pressure<<<152 * 8, 256, 0, st>>>(L.total, p2n, p1, p1n, P2);
+}
+
 template <typename R>
 void Launch<R>::pressure(const Shell &S, int sys, State<R> it, State<R> n, double *norm, double *part, int pm,
                          cudaStream_t st, LevelSums<R> ls) {
@@ -401,6 +421,8 @@ void norm_watch(double *norm, int k, cudaStream_t st) {
   template void Launch<R>::resid_u(const Shell &, int, int, State<R>, State<R>, StepAux<R>, R *, int,             \
                                    cudaStream_t, LevelSums<R>);                                                    \
   template void Launch<R>::sum_levels(const Layout &, SumJob<R>, cudaStream_t);                                   \
+  template void Launch<R>::bootstrap_pressure(const Layout &, const double *, const double *, const double *,       \
+                                              double *, cudaStream_t);                                             \
   template void Launch<R>::pressure(const Shell &, int, State<R>, State<R>, double *, double *, int, cudaStream_t,  \
                                     LevelSums<R>);                                                                 \
   template void Launch<R>::unpack(const Layout &, int, const double *, R *, const double *, cudaStream_t, R *);   \

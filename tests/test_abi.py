@@ -77,8 +77,9 @@ def _layout_bytes(Nr, Nt, Np, mixed, rec_counts, line_count, x_count):
     include/ys.h: 75 bulk fields (3 levels x 7 unknowns, 3 advecting
     velocities, 4 forcing combinations, 2 work fields, 36 line-factor fields,
     9 per-step sums of the advecting velocity) of the precision's size, in
-    FP64 4 more (the two-level sums of the velocity and of T that the
-    residuals and pressure updates read), 6 FP64
+    FP64 5 more (the two-level sums of the velocity and of T and the
+    bootstrapped momentum pressure that the residuals and pressure updates
+    read), 6 FP64
     pressures, the 14 metric tables of max(Nr, Nth) + 6 entries (FP64 and
     FP32 pairs), the row tables (FP64 and FP32, each padded to 32 entries),
     the exchange entries (72 bytes each: 6 ints, 6 doubles), 4 deviation profiles of Nr + 2
@@ -91,7 +92,7 @@ def _layout_bytes(Nr, Nt, Np, mixed, rec_counts, line_count, x_count):
     met = 14 * (max(Nr, Nt) + 6)
     rows = sum((n + 31) // 32 * 32 for n in rec_counts) + (line_count + 31) // 32 * 32
     stage = 2 * max((Nr + 1) * Nt * Np, Nr * (Nt + 1) * Np, Nr * Nt * (Np + 1))
-    bulk = 75 if mixed else 79
+    bulk = 75 if mixed else 80
     return (r256(bulk * total * R) + r256(6 * total * 8) + r256(met * 8) + r256(2 * met * 4) + r256(rows * 8)
             + r256(rows * 4) + r256(x_count * 72) + r256(4 * (Nr + 2) * 8) + 256 + stage * 8)
 
