@@ -77,23 +77,24 @@ UNIT = "cell-updates/s"
 WORDS_PER_CELL = {
     "extrapolate": (36.0, 6.0), "resid_T": (7.0, 0.0), "resid_u": (35.0 / 3, 2.0), "sweep_r": (37.0 / 7, 0.0),
     "sweep_t": (37.0 / 7, 0.0), "sweep_p": (38.0 / 7, 0.0), "pressure": (6.0, 4.0), "factorize": (4.0, 0.0),
-    # FP64 two-level sums: 15 fields summed per iteration in 9 launches (T
-    # twice, each velocity system's three components, then each component
-    # after its solve), read 2 and write 1 word per field
-    "sums": (5.0, 0.0),
+    # FP64 passes per iteration: T's sums (1 field), each velocity system's
+    # three components (3 + 3 fields; read 2, write 1 word a field) and P2
+    # (read 3, write 1 FP64 word): 4 launches
+    "sums": (21.0 / 4, 4.0 / 4),
 }
 # FP64 operations per cell (hand count of the kernel formulas, FMA = 2, a
 # division = 1) for the FP64 form, whose kernels are bound by the FP64 pipe.
 # The sums of the advecting velocity are formed once per step (extrapolate
 # class) and the two-level sums psi + psi^n of T and the velocity in their own
 # class (sums), so neither is counted again in the residuals or the pressure.
-FLOPS_PER_CELL = {"resid_T": 32.0, "resid_u": 68.0 - 2.0 / 3, "pressure": 15.0, "factorize": 9.0, "sums": 5.0 / 3}
+FLOPS_PER_CELL = {"resid_T": 32.0, "resid_u": 68.0 - 2.0 / 3, "pressure": 15.0, "factorize": 9.0, "sums": 9.0 / 4}
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of GB300 (context; the bench measures its own)
 # DRAM bytes (read + write) per point of the top kernel class from one ncu
 # capture of its u_r launch on a smaller shell whose launch already exceeds L2
 # (traffic scales with the points processed); the bench reports it scaled to
 # one full launch.  Valid for the kernel code the capture was taken of.
 TRAFFIC_PER_POINT = {
+    (False, "resid_u"): (153.949e6 / (2 * 64 * 63 * 192), "profiles/k_resid_ur_fp64_64x64x192_full.md"),
     (True, "resid_u"): (518.40e6 / (2 * 112 * 111 * 336), "profiles/k_resid_ur_mixed_112x112x336_full.md"),
     # mean of the captured r, theta and phi solves of T (non-final, non-final, final)
     (True, "solve"): ((185.524e6 + 182.543e6 + 190.098e6) / (3 * 2 * 112 * 112 * 336),
