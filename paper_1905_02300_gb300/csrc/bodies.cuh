@@ -938,16 +938,27 @@ __device__ __forceinline__ void body_extrapolate(long q0, long q1, State<R> it, 
   using V = typename Cmp<R>::type;
   const int bulk[7] = {F_T, F_U1R, F_U1T, F_U1P, F_U2R, F_U2T, F_U2P};
   for (long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    // every load first: the stores below may alias the inputs as far as the
+    // compiler knows, so loads placed after a store would wait for it
+    V a[7], b[7];
+    double pa[2], pb[2];
 #pragma unroll
-    for (int b = 0; b < 7; ++b) {
-      int f = bulk[b];
-      it.f[f][q] = (R)((V)2.0 * (V)n.f[f][q] - (V)nm1.f[f][q]);
+    for (int k = 0; k < 7; ++k) {
+      a[k] = (V)n.f[bulk[k]][q];
+      b[k] = (V)nm1.f[bulk[k]][q];
     }
-    it.p[0][q] = 2.0 * n.p[0][q] - nm1.p[0][q];
-    it.p[1][q] = 2.0 * n.p[1][q] - nm1.p[1][q];
-    A0[q] = (R)((V)1.5 * (V)n.f[F_U2R][q] - (V)0.5 * (V)nm1.f[F_U2R][q]);
-    A1[q] = (R)((V)1.5 * (V)n.f[F_U2T][q] - (V)0.5 * (V)nm1.f[F_U2T][q]);
-    A2[q] = (R)((V)1.5 * (V)n.f[F_U2P][q] - (V)0.5 * (V)nm1.f[F_U2P][q]);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      pa[k] = n.p[k][q];
+      pb[k] = nm1.p[k][q];
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) it.f[bulk[k]][q] = (R)((V)2.0 * a[k] - b[k]);
+    it.p[0][q] = 2.0 * pa[0] - pb[0];
+    it.p[1][q] = 2.0 * pa[1] - pb[1];
+    A0[q] = (R)((V)1.5 * a[4] - (V)0.5 * b[4]);
+    A1[q] = (R)((V)1.5 * a[5] - (V)0.5 * b[5]);
+    A2[q] = (R)((V)1.5 * a[6] - (V)0.5 * b[6]);
   }
 }
 

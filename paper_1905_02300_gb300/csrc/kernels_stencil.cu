@@ -38,16 +38,22 @@ __global__ void k_adv_sums(long lo, long hi, long SI, long P, const R *__restric
                            const R *__restrict__ A2, R *cr, R *ct, R *cp, R *rt, R *rp, R *tr, R *tp, R *pr, R *pt) {
   using V = typename Cmp<R>::type;
   for (long q = lo + blockIdx.x * (long)blockDim.x + threadIdx.x; q < hi; q += (long)gridDim.x * blockDim.x) {
+    // every load before the first store (the outputs may alias the inputs as
+    // far as the compiler knows)
     const V a0 = (V)A0[q], a1 = (V)A1[q], a2 = (V)A2[q];
-    cr[q] = (R)(a0 + (V)A0[q + SI]);
-    ct[q] = (R)(a1 + (V)A1[q + P]);
-    cp[q] = (R)(a2 + (V)A2[q + 1]);
-    rt[q] = (R)((((V)A1[q - SI] + (V)A1[q - SI + P]) + a1) + (V)A1[q + P]);
-    rp[q] = (R)((((V)A2[q - SI] + (V)A2[q - SI + 1]) + a2) + (V)A2[q + 1]);
-    tr[q] = (R)((((V)A0[q - P] + (V)A0[q - P + SI]) + a0) + (V)A0[q + SI]);
-    tp[q] = (R)((((V)A2[q - P] + (V)A2[q - P + 1]) + a2) + (V)A2[q + 1]);
-    pr[q] = (R)((((V)A0[q - 1] + (V)A0[q - 1 + SI]) + a0) + (V)A0[q + SI]);
-    pt[q] = (R)((((V)A1[q - 1] + (V)A1[q - 1 + P]) + a1) + (V)A1[q + P]);
+    const V a0r = (V)A0[q + SI], a1t = (V)A1[q + P], a2p = (V)A2[q + 1];
+    const V a1m = (V)A1[q - SI], a1mt = (V)A1[q - SI + P], a2m = (V)A2[q - SI], a2mp = (V)A2[q - SI + 1];
+    const V a0t = (V)A0[q - P], a0tr = (V)A0[q - P + SI], a2t = (V)A2[q - P], a2tp = (V)A2[q - P + 1];
+    const V a0p = (V)A0[q - 1], a0pr = (V)A0[q - 1 + SI], a1p = (V)A1[q - 1], a1pt = (V)A1[q - 1 + P];
+    cr[q] = (R)(a0 + a0r);
+    ct[q] = (R)(a1 + a1t);
+    cp[q] = (R)(a2 + a2p);
+    rt[q] = (R)(((a1m + a1mt) + a1) + a1t);
+    rp[q] = (R)(((a2m + a2mp) + a2) + a2p);
+    tr[q] = (R)(((a0t + a0tr) + a0) + a0r);
+    tp[q] = (R)(((a2t + a2tp) + a2) + a2p);
+    pr[q] = (R)(((a0p + a0pr) + a0) + a0r);
+    pt[q] = (R)(((a1p + a1pt) + a1) + a1t);
   }
 }
 
@@ -62,12 +68,19 @@ __global__ void k_combine(long total, Modes<R> M, R *o0, R *o1, R *o2, R *o3) {
 #pragma unroll
   for (int m = 0; m < kMaxModes; ++m) tau[m] = (m < M.n) ? (V)M.tau[m] : (V)0.0;
   for (; q < total; q += stride) {
+    // every load before the first store (the outputs may alias the modes as
+    // far as the compiler knows)
+    V f[kMaxModes][4];
+#pragma unroll
+    for (int m = 0; m < kMaxModes; ++m)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) f[m][c] = (m < M.n) ? (V)M.F[m][c][q] : (V)0.0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       V acc = (V)0.0;
 #pragma unroll
       for (int m = 0; m < kMaxModes; ++m)
-        if (m < M.n) acc = acc + tau[m] * (V)M.F[m][c][q];
+        if (m < M.n) acc = acc + tau[m] * f[m][c];
       out[c][q] = (R)acc;
     }
   }
