@@ -242,9 +242,10 @@ void solve_unknown(ys_ctx *c, int loc, int slot, int mask) {
     int dir = kOrder[loc][s];
     bool fin = (s == 2);
     R *const *Fc = D.fac[loc][dir];
+    R *const *sg = (dir == DP && D.seg[loc][0]) ? D.seg[loc] : nullptr;
     LAUNCH(c, kSweepClass[dir], 1,
            Launch<R>::solve(c->S, loc, dir, fin, Fc[0], Fc[1], Fc[2], D.B, D.Cs, it.f[slot], c->norm, slot, mask,
-                            c->stream, fin ? n.f[slot] : nullptr, fin ? sum : nullptr));
+                            c->stream, fin ? n.f[slot] : nullptr, fin ? sum : nullptr, sg));
   }
 }
 
@@ -255,7 +256,9 @@ void factorize_all(ys_ctx *c, StepAux<R> ax) {
   for (int loc = LC; loc <= LP; ++loc)
     for (int dir = DR; dir <= DP; ++dir) {
       R *const *Fc = D.fac[loc][dir];
-      LAUNCH(c, K_FACTOR, 1, Launch<R>::factorize(c->S, loc, dir, ax, Fc[0], Fc[1], Fc[2], 3, c->stream));
+      // FP64 phi factors also get their lane-segment products (D.seg)
+      R *const *sg = (dir == DP && D.seg[loc][0]) ? D.seg[loc] : nullptr;
+      LAUNCH(c, K_FACTOR, sg ? 2 : 1, Launch<R>::factorize(c->S, loc, dir, ax, Fc[0], Fc[1], Fc[2], 3, c->stream, sg));
     }
 }
 
@@ -507,7 +510,13 @@ char *carve(ys_ctx *c, Fields<R> &D, char *base) {
   double *pp = (double *)next;
   for (int l = 0; l < 3; ++l)
     for (int q = 0; q < 2; ++q) D.lev[l].p[q] = pp + (2 * l + q) * T;
-  return next + ((kPresFields * T * sizeof(double) + 255) / 256) * 256;
+  next += ((kPresFields * T * sizeof(double) + 255) / 256) * 256;
+  // FP64: the phi factors' lane-segment products, 8 arrays of phi_seg_elems
+  const long ns = phi_seg_elems(c->L);
+  for (int loc = 0; loc < 4; ++loc)
+    for (int a = 0; a < 2; ++a) D.seg[loc][a] = (sizeof(R) == sizeof(double)) ? (R *)next + (2 * loc + a) * ns : nullptr;
+  if (sizeof(R) == sizeof(double)) next += ((8 * ns * sizeof(double) + 255) / 256) * 256;
+  return next;
 }
 
 // number of bulk fields of one shell (3 x 7 levels, 3 a, 4 forcing, B, Cs, 36 factors, 9 sums of a),
@@ -545,7 +554,8 @@ ShellPlan plan_shell(const Layout &L, bool mixed, size_t met_n, const size_t (&r
   const size_t Rsz = mixed ? sizeof(float) : sizeof(double);
   const size_t nbulk = kBulkFields + (mixed ? 0 : kSumFields64);
   const size_t bulk_bytes = ((nbulk * L.total * Rsz + 255) / 256) * 256;
-  const size_t p_bytes = ((kPresFields * L.total * sizeof(double) + 255) / 256) * 256;
+  const size_t p_bytes = ((kPresFields * L.total * sizeof(double) + 255) / 256) * 256 +
+                         (mixed ? 0 : ((8 * (size_t)phi_seg_elems(L) * sizeof(double) + 255) / 256) * 256);
   size_t stage_elems = user_elems(L, LR);
   if (user_elems(L, LT) > stage_elems) stage_elems = user_elems(L, LT);
   if (user_elems(L, LP) > stage_elems) stage_elems = user_elems(L, LP);

@@ -1465,12 +1465,13 @@ __device__ __forceinline__ void seg_store(R *__restrict__ p, bool full, int k, i
   }
 }
 
-template <int EC, bool kSum = false, typename R>
+template <int EC, bool kSum = false, bool kSeg = false, typename R>
 __device__ __forceinline__ void solve_line_scan(int k0, int k1, int final, const R *__restrict__ Lo,
                                                 const R *__restrict__ Iv, const R *__restrict__ Cp,
                                                 R *__restrict__ B, R *__restrict__ wbuf, R *__restrict__ dst,
                                                 typename Cmp<R>::type &acc, const R *__restrict__ Pn = nullptr,
-                                                R *__restrict__ Sout = nullptr) {
+                                                R *__restrict__ Sout = nullptr, const R *__restrict__ Aseg = nullptr,
+                                                const R *__restrict__ Gseg = nullptr) {
   using V = typename Cmp<R>::type;
   const int lane = threadIdx.x & 31;
   constexpr int CH = 32 * EC;
@@ -1488,15 +1489,22 @@ __device__ __forceinline__ void solve_line_scan(int k0, int k1, int final, const
       seg_load<EC>(Iv + k, full, k, k0, k1, iv);
 #pragma unroll
       for (int e = 0; e < EC; ++e) {
-        a[e] = -iv[e] * lo[e];
+        // kSeg: Lo holds a = -iv lo already (phi_segments)
+        a[e] = kSeg ? lo[e] : -iv[e] * lo[e];
         f[e] = iv[e] * b[e];
       }
     }
     V A = (V)1.0, F = (V)0.0;
+    if constexpr (kSeg) {
+      A = (V)Aseg[c * 32 + lane];
 #pragma unroll
-    for (int e = 0; e < EC; ++e) {
-      A = a[e] * A;
-      F = a[e] * F + f[e];
+      for (int e = 0; e < EC; ++e) F = a[e] * F + f[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < EC; ++e) {
+        A = a[e] * A;
+        F = a[e] * F + f[e];
+      }
     }
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -1536,10 +1544,16 @@ __device__ __forceinline__ void solve_line_scan(int k0, int k1, int final, const
       for (int e = 0; e < EC; ++e) g[e] = -cp[e];
     }
     V G = (V)1.0, X = (V)0.0;
+    if constexpr (kSeg) {
+      G = (V)Gseg[c * 32 + lane];
 #pragma unroll
-    for (int e = EC - 1; e >= 0; --e) {
-      G = g[e] * G;
-      X = g[e] * X + w[e];
+      for (int e = EC - 1; e >= 0; --e) X = g[e] * X + w[e];
+    } else {
+#pragma unroll
+      for (int e = EC - 1; e >= 0; --e) {
+        G = g[e] * G;
+        X = g[e] * X + w[e];
+      }
     }
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -1596,21 +1610,91 @@ inline __host__ __device__ int scan_pad(int Np) {
   const int ch = 32 * scan_ec(Np);
   return (Np + ch - 1) / ch * ch;
 }
+// lane segments of one phi line (32 per chunk) and the length of the FP64
+// lane-segment product arrays of one unknown (2 Nr Nt lines at most)
+inline __host__ __device__ int scan_segs(int Np) { return 32 * (scan_pad(Np) / (32 * scan_ec(Np))); }
+inline __host__ __device__ long phi_seg_elems(const Layout &L) { return 2L * L.Nr * L.Nt * scan_segs(L.Np); }
 // lines of a location type and the CTAs of body_solve_phi_scan for one shell
 inline int phi_scan_ctas(const Layout &L, int loc) {
   const long lines = 2L * (L.Nr - (loc == LR ? 1 : 0)) * (L.Nt - (loc == LT ? 1 : 0));
   return (int)((lines + kScanWarps - 1) / kScanWarps);
 }
 
+// Per-step lane-segment products of a phi factorisation (FP64 single-shell
+// solves, kSeg): for every chunk c and lane t of a line, the products over
+// the lane's segment of a_m = -iv_m lo_m (in the order the forward scan
+// multiplies them) and of g_m = -c'_m (in the backward order), which depend
+// on the factors only, so that each of the step's solves along phi reads them
+// instead of forming them; Lo is overwritten with a.  The arithmetic and the
+// masks are those of solve_line_scan, so the solves give the same results.
+template <int EC, typename R>
+__device__ __forceinline__ void segment_line(int k0, int k1, R *__restrict__ Lo, const R *__restrict__ Iv,
+                                             const R *__restrict__ Cp, R *__restrict__ Aseg,
+                                             R *__restrict__ Gseg) {
+  using V = typename Cmp<R>::type;
+  const int lane = threadIdx.x & 31;
+  constexpr int CH = 32 * EC;
+  const int nch = (k1 + CH - 1) / CH;
+  for (int c = 0; c < nch; ++c) {
+    const int k = c * CH + lane * EC;
+    const bool full = (k >= k0 && k + EC <= k1);
+    V lo[EC], iv[EC], cp[EC], a[EC];
+    seg_load<EC>(Lo + k, full, k, k0, k1, lo);
+    seg_load<EC>(Iv + k, full, k, k0, k1, iv);
+    seg_load<EC>(Cp + k, full, k, k0, k1, cp);
+    V A = (V)1.0, G = (V)1.0;
+#pragma unroll
+    for (int e = 0; e < EC; ++e) {
+      a[e] = -iv[e] * lo[e];
+      A = a[e] * A;
+    }
+#pragma unroll
+    for (int e = EC - 1; e >= 0; --e) G = -cp[e] * G;
+    Aseg[c * 32 + lane] = (R)A;
+    Gseg[c * 32 + lane] = (R)G;
+    seg_store<EC>(Lo + k, full, k, k0, k1, a);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void body_phi_segments(Shell S, int loc, R *__restrict__ Lo, const R *__restrict__ Iv,
+                                                  const R *__restrict__ Cp, R *__restrict__ Aseg,
+                                                  R *__restrict__ Gseg, int patch_mask, int bx) {
+  const Layout &L = S.L;
+  const int warp = threadIdx.x >> 5;
+  const int i0 = (loc == LR) ? 1 : 0, j0 = (loc == LT) ? 1 : 0, k0 = (loc == LP) ? 1 : 0;
+  const int ni = L.Nr - i0, nj = L.Nt - j0;
+  const int line = bx * kScanWarps + warp;
+  if (line >= 2 * ni * nj) return;
+  const int j = j0 + line % nj;
+  const int rest = line / nj;
+  const int i = i0 + rest % ni, p = rest / ni;
+  if (!((patch_mask >> p) & 1)) return;
+  const long q = lidx(L, p, i, j, 0);
+  const long so = (long)line * scan_segs(L.Np);
+  switch (scan_ec(L.Np)) {
+    case 4:
+      segment_line<4>(k0, L.Np, Lo + q, Iv + q, Cp + q, Aseg + so, Gseg + so);
+      break;
+    case 8:
+      segment_line<8>(k0, L.Np, Lo + q, Iv + q, Cp + q, Aseg + so, Gseg + so);
+      break;
+    default:
+      segment_line<12>(k0, L.Np, Lo + q, Iv + q, Cp + q, Aseg + so, Gseg + so);
+      break;
+  }
+}
+
 // one phi line per warp; `smem_per_warp` positions of shared memory per warp
 // (0 or too few: the forward results go through W)
-template <typename R, bool kSum = false>
+template <typename R, bool kSum = false, bool kSeg = false>
 __device__ __forceinline__ void body_solve_phi_scan(Shell S, int loc, int final, const R *__restrict__ Lo,
                                                     const R *__restrict__ Iv, const R *__restrict__ Cp,
                                                     R *__restrict__ B, R *__restrict__ W, R *__restrict__ dst,
                                                     double *norm, int slot, int patch_mask, int bx, R *smem,
                                                     int smem_per_warp, const R *__restrict__ Pn = nullptr,
-                                                    R *__restrict__ Sout = nullptr) {
+                                                    R *__restrict__ Sout = nullptr,
+                                                    const R *__restrict__ const *seg = nullptr) {
   using V = typename Cmp<R>::type;
   const Layout &L = S.L;
   const int warp = threadIdx.x >> 5;
@@ -1627,18 +1711,22 @@ __device__ __forceinline__ void body_solve_phi_scan(Shell S, int loc, int final,
     if ((patch_mask >> p) & 1) {
       const long q = lidx(L, p, i, j, 0);
       R *wbuf = (scan_pad(L.Np) <= smem_per_warp) ? smem + (long)warp * smem_per_warp : W + q;
+      const long so = (long)line * scan_segs(L.Np);   // this line's lane-segment products (kSeg)
       switch (scan_ec(L.Np)) {
         case 4:
-          solve_line_scan<4, kSum>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc,
-                                          kSum ? Pn + q : nullptr, kSum ? Sout + q : nullptr);
+          solve_line_scan<4, kSum, kSeg>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc,
+                                                kSum ? Pn + q : nullptr, kSum ? Sout + q : nullptr,
+                                                kSeg ? seg[0] + so : nullptr, kSeg ? seg[1] + so : nullptr);
           break;
         case 8:
-          solve_line_scan<8, kSum>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc,
-                                          kSum ? Pn + q : nullptr, kSum ? Sout + q : nullptr);
+          solve_line_scan<8, kSum, kSeg>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc,
+                                                kSum ? Pn + q : nullptr, kSum ? Sout + q : nullptr,
+                                                kSeg ? seg[0] + so : nullptr, kSeg ? seg[1] + so : nullptr);
           break;
         default:
-          solve_line_scan<12, kSum>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc,
-                                          kSum ? Pn + q : nullptr, kSum ? Sout + q : nullptr);
+          solve_line_scan<12, kSum, kSeg>(k0, L.Np, final, Lo + q, Iv + q, Cp + q, B + q, wbuf, dst + q, acc,
+                                                kSum ? Pn + q : nullptr, kSum ? Sout + q : nullptr,
+                                                kSeg ? seg[0] + so : nullptr, kSeg ? seg[1] + so : nullptr);
           break;
       }
       if (final) {

@@ -36,6 +36,7 @@ struct Fields {
   R *fac[4][3][3];           // per-step LU factors: fac[loc][dir] = {lo, 1/pivot, c'}
   R *As[4][3];               // per-step sums of the advecting velocity (StepAux::As)
   R *Sv[kLevelSums];         // FP64: LevelSums fields (velocity of the iterated system, T, P2), else null
+  R *seg[4][2];              // FP64: lane-segment products of each unknown's phi factor (a, g), else null
   R *modes[kMaxModes][4];    // forcing modes
 };
 

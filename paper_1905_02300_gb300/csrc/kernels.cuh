@@ -115,14 +115,17 @@ struct Launch {
   static void sweep(const Shell &S, int loc, int dir, bool final, StepAux<R> ax, R *B, R *Cs, R *dst,
                     double *norm, int slot, int patch_mask, cudaStream_t st);
   // per-step LU factorisation of the factor (loc, dir) into (Lo, Iv, Cp)
+  // (FP64 phi factors given seg = {products of a, of g}: also their
+  // lane-segment products, and Lo then holds a = -iv lo)
   static void factorize(const Shell &S, int loc, int dir, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask,
-                        cudaStream_t st);
+                        cudaStream_t st, R *const *seg = nullptr);
   // line solve with a stored factorisation (same conventions as sweep)
   // W: scratch for the forward sweep (distinct from B and dst)
-  // FP64 final factors given Sout: also Sout = new dst + Pn (LevelSums)
+  // FP64 final factors given Sout: also Sout = new dst + Pn (LevelSums);
+  // FP64 phi factors given seg: the solves with the lane-segment products
   static void solve(const Shell &S, int loc, int dir, bool final, const R *Lo, const R *Iv, const R *Cp, R *B,
                     R *W, R *dst, double *norm, int slot, int patch_mask, cudaStream_t st, const R *Pn = nullptr,
-                    R *Sout = nullptr);
+                    R *Sout = nullptr, R *const *seg = nullptr);
   // pressure update of system sys; part: scratch of one FP64 per cell block
   // (partial norms, summed into norm[4] or norm[8] by a second kernel)
   // Algorithm step 4 on the edge velocity of both systems (acc: 4 FP64 scratch)
@@ -138,6 +141,10 @@ struct Launch {
                      R *dst2 = nullptr);
   static void pack(const Layout &L, int loc, const R *src, double *dst, const double *bg, cudaStream_t st);
 };
+
+// length of one FP64 lane-segment product array of the phi factors
+// (Launch::factorize / solve with seg): 2 Nr Nt lines x 32 lanes per chunk
+long phi_seg_elems(const Layout &L);
 
 // FP64 pressure fields: host layout <-> device layout
 void unpack_p(const Layout &L, const double *src, double *dst, const double *bg, cudaStream_t st,

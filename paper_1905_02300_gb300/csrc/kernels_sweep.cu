@@ -221,13 +221,33 @@ __global__ void k_solve_phi(Shell S, int loc, int final, const R *__restrict__ L
                           smem_per_warp);
 }
 
+// FP64 phi solves reading the per-step lane-segment products (k_phi_segments);
+// the final ones also write the two-level sum Sout = dst + Pn
+struct PhiSegs {
+  const double *S[2];   // products of a (forward) and of g (backward)
+};
+__global__ void k_solve_phi_seg(Shell S, int loc, const double *__restrict__ Lo, const double *__restrict__ Iv,
+                                const double *__restrict__ Cp, double *B, double *W, double *dst, double *norm,
+                                int slot, int patch_mask, int smem_per_warp, PhiSegs sg) {
+  extern __shared__ __align__(16) unsigned char phi_smem[];
+  bd::body_solve_phi_scan<double, false, true>(S, loc, 0, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask,
+                                               blockIdx.x, (double *)phi_smem, smem_per_warp, nullptr, nullptr,
+                                               sg.S);
+}
+
 __global__ void k_solve_phi_sum(Shell S, int loc, const double *__restrict__ Lo, const double *__restrict__ Iv,
                                 const double *__restrict__ Cp, double *B, double *W, double *dst, double *norm,
                                 int slot, int patch_mask, int smem_per_warp, const double *__restrict__ Pn,
-                                double *__restrict__ Sout) {
+                                double *__restrict__ Sout, PhiSegs sg) {
   extern __shared__ __align__(16) unsigned char phi_smem[];
-  bd::body_solve_phi_scan<double, true>(S, loc, 1, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, blockIdx.x,
-                                        (double *)phi_smem, smem_per_warp, Pn, Sout);
+  bd::body_solve_phi_scan<double, true, true>(S, loc, 1, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, blockIdx.x,
+                                              (double *)phi_smem, smem_per_warp, Pn, Sout, sg.S);
+}
+
+// the lane-segment products of the FP64 phi factor of `loc` (after k_factorize)
+__global__ void k_phi_segments(Shell S, int loc, double *Lo, const double *Iv, const double *Cp, double *Aseg,
+                               double *Gseg, int patch_mask) {
+  bd::body_phi_segments<double>(S, loc, Lo, Iv, Cp, Aseg, Gseg, patch_mask, blockIdx.x);
 }
 
 template <typename R>
@@ -239,34 +259,48 @@ void Launch<R>::sweep(const Shell &S, int loc, int dir, bool final, StepAux<R> a
 
 template <typename R>
 void Launch<R>::factorize(const Shell &S, int loc, int dir, StepAux<R> ax, R *Lo, R *Iv, R *Cp, int patch_mask,
-                          cudaStream_t st) {
+                          cudaStream_t st, R *const *seg) {
   if (dir == DP && bd::use_phi_scan<R>()) {
     k_factorize_phi<R><<<bd::phi_scan_ctas(S.L, loc), 32 * bd::kScanWarps, 0, st>>>(S, loc, ax, Lo, Iv, Cp,
                                                                                    patch_mask);
     return;
   }
   k_factorize<R><<<line_grid(S.L, loc, dir), TPB, 0, st>>>(S, loc, dir, ax, Lo, Iv, Cp, patch_mask);
+  if constexpr (sizeof(R) == sizeof(double)) {
+    if (dir == DP && seg)
+      k_phi_segments<<<bd::phi_scan_ctas(S.L, loc), 32 * bd::kScanWarps, 0, st>>>(S, loc, Lo, Iv, Cp, seg[0], seg[1],
+                                                                                  patch_mask);
+  }
 }
 
 template <typename R>
 void Launch<R>::solve(const Shell &S, int loc, int dir, bool final, const R *Lo, const R *Iv, const R *Cp, R *B,
                       R *W, R *dst, double *norm, int slot, int patch_mask, cudaStream_t st, const R *Pn,
-                      R *Sout) {
+                      R *Sout, R *const *seg) {
   // FP64 final factors given a sum field: the launches that also write it
   constexpr bool k64 = sizeof(R) == sizeof(double);
   const bool with_sum = k64 && final && Sout != nullptr;
   if (dir == DP) {
     // forward results of each warp's line in shared memory when they fit
-    static std::atomic<unsigned long long> attr_done{0}, attr_sum_done{0};
+    static std::atomic<unsigned long long> attr_done{0}, attr_sum_done{0}, attr_seg_done{0};
     smem_attr_once(attr_done, k_solve_phi<R>, bd::kScanSmemMax);
     const int pad = bd::scan_pad(S.L.Np);
     const size_t bytes = (size_t)bd::kScanWarps * pad * sizeof(R);
     const bool fits = bytes <= (size_t)bd::kScanSmemMax;
     if constexpr (k64) {
-      if (with_sum) {
-        smem_attr_once(attr_sum_done, k_solve_phi_sum, bd::kScanSmemMax);
-        k_solve_phi_sum<<<bd::phi_scan_ctas(S.L, loc), 32 * bd::kScanWarps, fits ? bytes : 0, st>>>(
-            S, loc, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, fits ? pad : 0, Pn, Sout);
+      // FP64 phi factors with lane-segment products (factorize given seg):
+      // Lo holds a = -iv lo, so these factors take the segment solves only
+      if (seg) {
+        const PhiSegs sg{{seg[0], seg[1]}};
+        if (with_sum) {
+          smem_attr_once(attr_sum_done, k_solve_phi_sum, bd::kScanSmemMax);
+          k_solve_phi_sum<<<bd::phi_scan_ctas(S.L, loc), 32 * bd::kScanWarps, fits ? bytes : 0, st>>>(
+              S, loc, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, fits ? pad : 0, Pn, Sout, sg);
+        } else {
+          smem_attr_once(attr_seg_done, k_solve_phi_seg, bd::kScanSmemMax);
+          k_solve_phi_seg<<<bd::phi_scan_ctas(S.L, loc), 32 * bd::kScanWarps, fits ? bytes : 0, st>>>(
+              S, loc, Lo, Iv, Cp, B, W, dst, norm, slot, patch_mask, fits ? pad : 0, sg);
+        }
         return;
       }
     }
@@ -285,10 +319,13 @@ void Launch<R>::solve(const Shell &S, int loc, int dir, bool final, const R *Lo,
                                                         slot, patch_mask);
 }
 
+long phi_seg_elems(const Layout &L) { return bd::phi_seg_elems(L); }
+
 #define YS_INST_SWEEP(R)                                                                                          \
-  template void Launch<R>::factorize(const Shell &, int, int, StepAux<R>, R *, R *, R *, int, cudaStream_t);       \
+  template void Launch<R>::factorize(const Shell &, int, int, StepAux<R>, R *, R *, R *, int, cudaStream_t,         \
+                                     R *const *);                                                                  \
   template void Launch<R>::solve(const Shell &, int, int, bool, const R *, const R *, const R *, R *, R *, R *,       \
-                                 double *, int, int, cudaStream_t, const R *, R *);
+                                 double *, int, int, cudaStream_t, const R *, R *, R *const *);
 YS_INST_SWEEP(double)
 YS_INST_SWEEP(float)
 template void Launch<double>::sweep(const Shell &, int, int, bool, StepAux<double>, double *, double *, double *,

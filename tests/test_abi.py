@@ -79,8 +79,8 @@ def _layout_bytes(Nr, Nt, Np, mixed, rec_counts, line_count, x_count):
     9 per-step sums of the advecting velocity) of the precision's size, in
     FP64 5 more (the two-level sums of the velocity and of T and the
     bootstrapped momentum pressure that the residuals and pressure updates
-    read), 6 FP64
-    pressures, the 14 metric tables of max(Nr, Nth) + 6 entries (FP64 and
+    read), 6 FP64 pressures, in FP64 the phi factors' lane-segment products,
+    the 14 metric tables of max(Nr, Nth) + 6 entries (FP64 and
     FP32 pairs), the row tables (FP64 and FP32, each padded to 32 entries),
     the exchange entries (72 bytes each: 6 ints, 6 doubles), 4 deviation profiles of Nr + 2
     values, the norms and the staging buffer of the largest face-centred
@@ -93,7 +93,12 @@ def _layout_bytes(Nr, Nt, Np, mixed, rec_counts, line_count, x_count):
     rows = sum((n + 31) // 32 * 32 for n in rec_counts) + (line_count + 31) // 32 * 32
     stage = 2 * max((Nr + 1) * Nt * Np, Nr * (Nt + 1) * Np, Nr * Nt * (Np + 1))
     bulk = 75 if mixed else 80
-    return (r256(bulk * total * R) + r256(6 * total * 8) + r256(met * 8) + r256(2 * met * 4) + r256(rows * 8)
+    # FP64: 8 arrays of lane-segment products of the phi factors, 32 per
+    # chunk of 32 ec positions of each of 2 Nr Nt lines
+    ec = 4 if Np <= 128 else 8 if Np <= 256 else 12
+    chunks = -(-Np // (32 * ec))
+    segs = 0 if mixed else r256(8 * 2 * Nr * Nt * 32 * chunks * 8)
+    return (r256(bulk * total * R) + r256(6 * total * 8) + segs + r256(met * 8) + r256(2 * met * 4) + r256(rows * 8)
             + r256(rows * 4) + r256(x_count * 72) + r256(4 * (Nr + 2) * 8) + 256 + stage * 8)
 
 
