@@ -52,7 +52,8 @@ extern "C" {
 #define YS_ENOMEM 2     /* device or host allocation failed */
 #define YS_ECUDA 3      /* CUDA error (no device, launch failure, ...) */
 #define YS_EDIVERGED 4  /* NaN/Inf increment norms, or Schwarz increments that grew more than
-                           10^3-fold in one iteration: the state holds the diverged values */
+                           10^3-fold in one iteration past the step's first increment: the
+                           state holds the diverged values */
 #define YS_ETIMEOUT 5   /* a served request passed its deadline */
 #define YS_EAGAIN 6     /* result not ready yet */
 #define YS_EBUSY 7      /* admission refused: queue full */
@@ -193,10 +194,12 @@ int ys_set_time(ys_ctx *c, double t);
  * waits for the norms after every iteration).  Returns YS_EDIVERGED if one
  * of those norms is NaN or Inf, or if in any iteration of this call an
  * increment norm was not finite or, from the third iteration of a step on,
- * the largest one exceeded 10^3 times the previous iteration's (a
- * device-side watch after every iteration: a working defect correction
- * contracts from its second iteration on, so growth by three orders of
- * magnitude in one iteration means it diverges); the state then holds the
+ * the largest one exceeded both 10^3 times the previous iteration's and the
+ * step's first (a device-side watch after every iteration: a working defect
+ * correction contracts from its second iteration on, so growth by three
+ * orders of magnitude in one iteration past the first increment means it
+ * diverges; growth from a second increment already at the rounding level
+ * of the arithmetic stays below the first); the state then holds the
  * diverged values and the caller restarts from its own copy (ys_get_fields /
  * ys_set_fields restart exactly). */
 int ys_step(ys_ctx *c, int n_steps, int n_schwarz);
@@ -369,8 +372,8 @@ int ys_batch_sync(ys_batch *b);
 /* l2 increment norms (YS_NFIELDS) of the member's last iteration.  Returns
  * YS_EDIVERGED (norms still written) when one is not finite, or when, in a
  * step since the member joined the batch, its largest increment norm grew
- * more than 10^3-fold from one iteration to the next after the second (the
- * same watch as ys_step). */
+ * more than 10^3-fold from one iteration to the next after the second and
+ * past the step's first increment (the same watch as ys_step). */
 int ys_batch_norms(ys_batch *b, int slot, double *norms);
 /* Threads per block of the line-solve launches (lines per block): 32, 64,
  * 128 (default) or 256. */

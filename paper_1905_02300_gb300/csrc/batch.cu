@@ -384,12 +384,15 @@ void grid_of(const ys_ctx *c, int map, int tpb_line, int &gx, int &gy) {
 
 }  // namespace
 
+// per-member divergence watch words: previous norm, flag, first norm of the step
+constexpr int kWatchSlots = 3;
+
 // Divergence watch of every member after Schwarz iteration k (1-based) of a
-// step (the single-shell norm_watch per slot): watch[2 s] holds the largest
-// squared increment norm of the member's previous iteration, watch[2 s + 1]
+// step (the single-shell norm_watch per slot): watch[kWatchSlots s] holds the
+// largest squared increment norm of the member's previous iteration, the next
 // its sticky flag, set by a non-finite norm or, for k >= 3, by a norm above
-// kWatchGrowth times the previous iteration's.  Empty slots have zero norms
-// and never set it.
+// kWatchGrowth times the previous iteration's and above the step's first
+// (kept in the third).  Empty slots have zero norms and never set it.
 __global__ void kb_norm_watch(const double *norms, double *watch, int cap, int k) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= cap) return;
@@ -400,9 +403,11 @@ __global__ void kb_norm_watch(const double *norms, double *watch, int cap, int k
     if (!(v <= 1.79e308)) bad = true;
     else cur = fmax(cur, v);
   }
-  if (k >= 3 && cur > kWatchGrowth * kWatchGrowth * watch[2 * s]) bad = true;
-  if (bad) watch[2 * s + 1] = 1.0;
-  watch[2 * s] = cur;
+  double *w = watch + (size_t)kWatchSlots * s;
+  if (k == 1) w[2] = cur;
+  if (k >= 3 && cur > kWatchGrowth * kWatchGrowth * w[0] && cur > w[2]) bad = true;
+  if (bad) w[1] = 1.0;
+  w[0] = cur;
 }
 
 }  // namespace ys
@@ -421,7 +426,7 @@ struct ys_batch {
   int *maps = nullptr;            // M_NUM x (2 cap + 1) ints (device)
   int *active = nullptr;          // cap ints (device)
   double *norms = nullptr;        // cap x YS_NFIELDS (device)
-  double *watch = nullptr;        // cap x 2: divergence watch per member (device; kb_norm_watch)
+  double *watch = nullptr;        // cap x kWatchSlots: divergence watch per member (device; kb_norm_watch)
   double *parts = nullptr;        // per-block pressure norm shares (device), parts_n doubles
   long parts_n = 0;
   std::vector<int> hmaps;
@@ -789,8 +794,8 @@ int ys_batch_create(int capacity, int precision, int n_schwarz, ys_batch **out) 
       cudaMalloc(&b->shells, shell_bytes) != cudaSuccess || cudaMalloc(&b->maps, map_bytes) != cudaSuccess ||
       cudaMalloc(&b->active, sizeof(int) * capacity) != cudaSuccess ||
       cudaMalloc(&b->norms, sizeof(double) * YS_NFIELDS * capacity) != cudaSuccess ||
-      cudaMalloc(&b->watch, sizeof(double) * 2 * capacity) != cudaSuccess ||
-      cudaMemsetAsync(b->watch, 0, sizeof(double) * 2 * capacity, b->stream) != cudaSuccess) {
+      cudaMalloc(&b->watch, sizeof(double) * kWatchSlots * capacity) != cudaSuccess ||
+      cudaMemsetAsync(b->watch, 0, sizeof(double) * kWatchSlots * capacity, b->stream) != cudaSuccess) {
     cudaGetLastError();
     ys_batch_destroy(b);
     return YS_ENOMEM;
@@ -814,7 +819,8 @@ int ys_batch_add(ys_batch *b, ys_ctx *c, int *slot) {
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return YS_ECUDA;
   // a new member starts with a clear divergence watch (ordered after the
   // batch's queued steps, before its next one)
-  if (cudaMemsetAsync(b->watch + 2 * s, 0, 2 * sizeof(double), b->stream) != cudaSuccess) return YS_ECUDA;
+  if (cudaMemsetAsync(b->watch + (size_t)kWatchSlots * s, 0, kWatchSlots * sizeof(double), b->stream) != cudaSuccess)
+    return YS_ECUDA;
   b->slot[s] = c;
   b->rot[s] = 0;
   b->steps[s] = 0;
@@ -853,7 +859,8 @@ int ys_batch_norms(ys_batch *b, int s, double *norms) {
   double h[YS_NFIELDS], w[2];
   if (cudaMemcpyAsync(h, b->norms + (size_t)s * YS_NFIELDS, sizeof(h), cudaMemcpyDeviceToHost, b->stream) !=
           cudaSuccess ||
-      cudaMemcpyAsync(w, b->watch + 2 * s, sizeof(w), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(w, b->watch + (size_t)kWatchSlots * s, sizeof(w), cudaMemcpyDeviceToHost, b->stream) !=
+          cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return YS_ECUDA;
   bool bad = w[1] != 0.0;

@@ -407,7 +407,7 @@ void pack_p(const Layout &L, const double *src, double *dst, const double *bg, c
 // increment norms of iteration k (1-based) of the step just finished
 // (non-negative sums); `prev` holds the largest of iteration k - 1, `flag`
 // the sticky flag.
-__global__ void k_norm_watch(const double *norm, double *prev, double *flag, int k) {
+__global__ void k_norm_watch(const double *norm, double *prev, double *first, double *flag, int k) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double cur = 0.0;
   bool bad = false;
@@ -416,13 +416,14 @@ __global__ void k_norm_watch(const double *norm, double *prev, double *flag, int
     if (!(v <= 1.79e308)) bad = true;   // NaN or +Inf
     else cur = fmax(cur, v);
   }
-  if (k >= 3 && cur > kWatchGrowth * kWatchGrowth * *prev) bad = true;
+  if (k == 1) *first = cur;
+  if (k >= 3 && cur > kWatchGrowth * kWatchGrowth * *prev && cur > *first) bad = true;
   if (bad) *flag = 1.0;
   *prev = cur;
 }
 
 void norm_watch(double *norm, int k, cudaStream_t st) {
-  k_norm_watch<<<1, 32, 0, st>>>(norm, norm + kWatchPrev, norm + kWatchFlag, k);
+  k_norm_watch<<<1, 32, 0, st>>>(norm, norm + kWatchPrev, norm + kWatchFirst, norm + kWatchFlag, k);
 }
 
 #define YS_INST_STENCIL(R)                                                                                         \

@@ -39,11 +39,15 @@ constexpr int kMetricTables = 14;
 // the step in progress, and a sticky flag, kept beside the norm accumulators.
 // An iteration whose increment norms are not finite sets it, and so does,
 // from a step's third iteration on, a largest increment norm above
-// kWatchGrowth times the previous iteration's: a working defect correction
-// contracts from its second iteration on (the first may jump, e.g. where the
-// buoyancy of the first temperature increment starts the velocity), so
-// growth by three orders of magnitude in one iteration is divergence.
-constexpr int kWatchPrev = 24, kWatchFlag = 25;   // indices in the per-context norm buffer (32 doubles)
+// kWatchGrowth times the previous iteration's that is also above the step's
+// first increment: a working defect correction contracts from its second
+// iteration on (the first may jump, e.g. where the buoyancy of the first
+// temperature increment starts the velocity), so growth by three orders of
+// magnitude in one iteration past the first increment is divergence.  (An
+// iteration that has converged to the rounding level of its arithmetic can
+// grow by that much from a still smaller second increment, but stays far
+// below the first.)
+constexpr int kWatchPrev = 24, kWatchFlag = 25, kWatchFirst = 26;   // indices in the per-context norm buffer (32 doubles)
 constexpr double kWatchGrowth = 1e3;
 enum MetricTable {
   MT_RC = 0, MT_RF, MT_SC, MT_SF, MT_CC, MT_CF, MT_IRC, MT_IRF, MT_ISC, MT_ISF, MT_HC, MT_IHC, MT_NRC, MT_NRF
